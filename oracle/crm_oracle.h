@@ -1,0 +1,64 @@
+/*
+ * crm_oracle.h -- correctly rounded reference evaluator (TEST INFRASTRUCTURE ONLY).
+ *
+ * This is the parity oracle for the GPU library: a plain, slow CPU implementation of
+ *     out = RN_fmt(f(x))      (round to nearest, ties to even; binary32 or binary64)
+ * for the one-input functions of the paper (Sec. II.A lists the 19 single-precision
+ * functions, Sec. II.B the double-precision exp2 and log).  It follows Ziv's method
+ * (Sec. I): evaluate an interval that provably encloses f(x) with multiprecision
+ * integer (fixed-point) arithmetic, and raise the precision until both interval
+ * ends round to the same floating-point number.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load this library; the product
+ * path never does, and this code shares nothing with the CUDA sources.
+ *
+ * Function identifiers are the oracle's own; by design they carry the same numbers
+ * as the public library's identifiers so that tests can pass one integer to both.
+ */
+#ifndef CRM_ORACLE_H
+#define CRM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ORC_EXPF = 0, ORC_EXP2F, ORC_EXP10F, ORC_EXPM1F, ORC_LOGF, ORC_LOG2F, ORC_LOG10F,
+  ORC_LOG1PF, ORC_SINF, ORC_COSF, ORC_SINCOSF, ORC_TANF, ORC_ASINF, ORC_ACOSF,
+  ORC_ATANF, ORC_SINHF, ORC_COSHF, ORC_TANHF, ORC_RSQRTF,
+  ORC_EXP2 = 19, ORC_LOG = 20,
+  ORC_NUM_FUNCS = 21
+};
+
+enum { ORC_OK = 0, ORC_ERR_FUNC = 1, ORC_ERR_CAP = 2 };
+
+/* One binary32 input (bit pattern) -> result bit pattern.  For ORC_SINCOSF, out[0]
+   receives sin and out[1] cos.  Returns ORC_OK, ORC_ERR_FUNC (bad id / wrong
+   format) or ORC_ERR_CAP (Ziv precision cap reached: never expected). */
+int crm_oracle_f32(int func, uint32_t x, uint32_t *out);
+int crm_oracle_f64(int func, uint64_t x, uint64_t *out);
+
+/* Array forms, multithreaded with nthreads POSIX threads (<=0: one per online core).
+   For ORC_SINCOSF, out holds 2n words: sin in [0,n), cos in [n,2n). */
+int crm_oracle_f32_array(int func, const uint32_t *in, uint32_t *out, uint64_t n, int nthreads);
+int crm_oracle_f64_array(int func, const uint64_t *in, uint64_t *out, uint64_t n, int nthreads);
+
+/* Diagnostics for the oracle's own tests: the Ziv level (0 = first precision) at which
+   the last call on this thread finished, and the constants as scaled integers. */
+int crm_oracle_last_level(void);
+/* Writes floor and ceil of c * 2^bits for c in {0: ln2, 1: ln10, 2: pi, 3: 2/pi} into
+   lo/hi as little-endian 64-bit limbs (nlimbs each); bits = 64*(nlimbs-1). */
+int crm_oracle_constant(int which, int nlimbs, uint64_t *lo, uint64_t *hi);
+/* Alternative formulas for the same constants (pi by Gauss's arctangent formula,
+   ln2 by sum 1/(k 2^k)), for cross-checking in tests. */
+int crm_oracle_constant_alt(int which, int nlimbs, uint64_t *lo, uint64_t *hi);
+/* Big-integer long division used by the oracle: q = floor(u / v), returns 1 if the
+   remainder is nonzero.  u has m 32-bit digits, v has nv digits (v[nv-1] != 0). */
+int crm_oracle_test_divmod(const uint32_t *u, int m, const uint32_t *v, int nv, uint32_t *q);
+/* Integer square root used by the oracle: r = floor(sqrt(N)); returns 1 if inexact. */
+int crm_oracle_test_isqrt(const uint64_t *N, int nl, uint64_t *r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

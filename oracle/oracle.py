@@ -1,0 +1,162 @@
+"""Correctly rounded CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Python access to ``crm_oracle.c``: a Ziv-loop evaluator over fixed-point big-integer
+intervals that returns RN(f(x)) for the paper's one-input functions (Sec. II.A: the 19
+binary32 functions; Sec. II.B: binary64 exp2 and log).  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import this
+module.  It shares no code with the CUDA library.
+
+The shared library is compiled with the system C compiler on first use (or by
+``build()``), so the same source serves x86-64 and aarch64 hosts.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "crm_oracle.c")
+_HDR = os.path.join(_HERE, "crm_oracle.h")
+_LIB = os.path.join(_HERE, f"liboracle_{platform.machine()}.so")
+
+# Oracle function identifiers (same numbering as the public library by design).
+FUNCS = [
+    "expf", "exp2f", "exp10f", "expm1f", "logf", "log2f", "log10f", "log1pf",
+    "sinf", "cosf", "sincosf", "tanf", "asinf", "acosf", "atanf", "sinhf", "coshf",
+    "tanhf", "rsqrtf", "exp2", "log",
+]
+FUNC_ID = {name: i for i, name in enumerate(FUNCS)}
+F64_FUNCS = ("exp2", "log")
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library if it is missing or older than its sources."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            lib.crm_oracle_f32.argtypes = [ctypes.c_int, ctypes.c_uint32, u32p]
+            lib.crm_oracle_f64.argtypes = [ctypes.c_int, ctypes.c_uint64, u64p]
+            lib.crm_oracle_f32_array.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_uint64, ctypes.c_int]
+            lib.crm_oracle_f64_array.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_uint64, ctypes.c_int]
+            lib.crm_oracle_constant.argtypes = [ctypes.c_int, ctypes.c_int, u64p, u64p]
+            lib.crm_oracle_constant_alt.argtypes = [ctypes.c_int, ctypes.c_int, u64p, u64p]
+            lib.crm_oracle_test_divmod.argtypes = [u32p, ctypes.c_int, u32p, ctypes.c_int, u32p]
+            lib.crm_oracle_test_isqrt.argtypes = [u64p, ctypes.c_int, u64p]
+            _lib = lib
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _fid(func) -> int:
+    return FUNC_ID[func] if isinstance(func, str) else int(func)
+
+
+def eval_bits(func, xbits: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    """Correctly rounded results as bit patterns.  ``xbits`` is uint32 (binary32
+    functions) or uint64 (binary64 functions).  For sincosf the result has shape (2, n):
+    row 0 is sin, row 1 cos."""
+    lib = _load()
+    fid = _fid(func)
+    is64 = FUNCS[fid] in F64_FUNCS
+    dt = np.uint64 if is64 else np.uint32
+    x = np.ascontiguousarray(xbits, dtype=dt).ravel()
+    n = x.size
+    rows = 2 if FUNCS[fid] == "sincosf" else 1
+    out = np.zeros(rows * n, dtype=dt)
+    if n:
+        fn = lib.crm_oracle_f64_array if is64 else lib.crm_oracle_f32_array
+        st = fn(fid, x.ctypes.data, out.ctypes.data, n, nthreads)
+        if st:
+            raise OracleError(f"oracle status {st} for {FUNCS[fid]}")
+    return out.reshape(2, n) if rows == 2 else out
+
+
+def eval_f32(func, x: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    """Float32 convenience wrapper around ``eval_bits``."""
+    bits = eval_bits(func, np.asarray(x, dtype=np.float32).view(np.uint32), nthreads)
+    return bits.view(np.float32)
+
+
+def eval_f64(func, x: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    bits = eval_bits(func, np.asarray(x, dtype=np.float64).view(np.uint64), nthreads)
+    return bits.view(np.float64)
+
+
+def last_level() -> int:
+    return _load().crm_oracle_last_level()
+
+
+def _limbs_to_int(arr) -> int:
+    v = 0
+    for i, w in enumerate(arr):
+        v |= int(w) << (64 * i)
+    return v
+
+
+def constant(which: int, nlimbs: int, alt: bool = False):
+    """(floor, ceil) of c * 2^(64*(nlimbs-1)) for c in {0: ln2, 1: ln10, 2: pi, 3: 2/pi}."""
+    lib = _load()
+    lo = (ctypes.c_uint64 * nlimbs)()
+    hi = (ctypes.c_uint64 * nlimbs)()
+    fn = lib.crm_oracle_constant_alt if alt else lib.crm_oracle_constant
+    if fn(which, nlimbs, lo, hi):
+        raise OracleError("bad constant request")
+    return _limbs_to_int(lo), _limbs_to_int(hi)
+
+
+def test_divmod(u: int, v: int):
+    """floor(u/v) and remainder-nonzero flag through the oracle's long division."""
+    lib = _load()
+
+    def digits(x):
+        d = []
+        while x:
+            d.append(x & 0xFFFFFFFF)
+            x >>= 32
+        return d or [0]
+
+    ud, vd = digits(u), digits(v)
+    if len(ud) < len(vd):
+        return 0, int(u != 0)
+    U = (ctypes.c_uint32 * len(ud))(*ud)
+    V = (ctypes.c_uint32 * len(vd))(*vd)
+    Q = (ctypes.c_uint32 * (len(ud) - len(vd) + 1))()
+    nz = lib.crm_oracle_test_divmod(U, len(ud), V, len(vd), Q)
+    q = 0
+    for i, w in enumerate(Q):
+        q |= int(w) << (32 * i)
+    return q, nz
+
+
+def test_isqrt(N: int, nl: int):
+    lib = _load()
+    arr = (ctypes.c_uint64 * nl)(*[(N >> (64 * i)) & (2**64 - 1) for i in range(nl)])
+    out = (ctypes.c_uint64 * nl)()
+    inexact = lib.crm_oracle_test_isqrt(arr, nl, out)
+    return _limbs_to_int(out), inexact

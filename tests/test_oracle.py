@@ -1,0 +1,406 @@
+"""Pins for the CPU oracle (runs without a GPU).
+
+The oracle computes RN(f(x)) by Ziv's method (Sec. I).  None of these checks re-types
+the oracle's own formulas: they compare it with an independent multiprecision library
+(mpmath, rounded to the target format by separate integer code below), with closed
+forms (exact powers, log(1) = 0), with the special-value conventions, with identities
+that correct rounding preserves (odd/even symmetry, sincos = (sin, cos)), with
+monotonicity, and, for its big-integer primitives, with Python integers.
+"""
+import math
+import random
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+mpmath = pytest.importorskip("mpmath")
+
+F32 = dict(p=24, emin=-126, emax=127, bias=127, w=32)
+F64 = dict(p=53, emin=-1022, emax=1023, bias=1023, w=64)
+
+
+# ----------------------------------------------------------------------------------
+# independent reference: mpmath at 320 bits, then exact integer rounding to the format
+# ----------------------------------------------------------------------------------
+
+def rn_bits(v, fmt):
+    """Round the mpmath number v to the binary format (nearest, ties to even)."""
+    p, emin, emax, bias, w = fmt["p"], fmt["emin"], fmt["emax"], fmt["bias"], fmt["w"]
+    sign = 1 << (w - 1)
+    inf = (2 * bias + 1) << (p - 1)
+    if v == 0:
+        return 0
+    neg = v < 0
+    man, exp = mpmath.mpf(abs(v)).man_exp  # |v| = man * 2^exp exactly
+    man = int(man)
+    b = man.bit_length()
+    ex = b - 1 + exp
+    s = sign if neg else 0
+    if ex > emax:
+        return s | inf
+    qe = max(ex, emin) - (p - 1)
+    shift = exp - qe
+    if shift >= 0:
+        sig = man << shift
+    else:
+        k = -shift
+        sig = man >> k
+        rem = man - (sig << k)
+        half = 1 << (k - 1)
+        if rem > half or (rem == half and (sig & 1)):
+            sig += 1
+    if ex < emin:
+        bits = sig
+    else:
+        bits = ((ex + bias) << (p - 1)) + sig - (1 << (p - 1))
+    bits = min(bits, inf)
+    return s | bits
+
+
+def mp_func(name):
+    m = mpmath
+    table = {
+        "expf": m.exp, "exp2f": lambda x: m.power(2, x), "exp10f": lambda x: m.power(10, x),
+        "expm1f": m.expm1, "logf": m.log, "log2f": lambda x: m.log(x) / m.log(2),
+        "log10f": m.log10, "log1pf": m.log1p, "sinf": m.sin, "cosf": m.cos, "tanf": m.tan,
+        "asinf": m.asin, "acosf": m.acos, "atanf": m.atan, "sinhf": m.sinh, "coshf": m.cosh,
+        "tanhf": m.tanh, "rsqrtf": lambda x: 1 / m.sqrt(x), "exp2": lambda x: m.power(2, x),
+        "log": m.log,
+    }
+    return table[name]
+
+
+def reference_bits(name, xbits, fmt):
+    f = mp_func(name)
+    dt = np.float64 if fmt is F64 else np.float32
+    ut = np.uint64 if fmt is F64 else np.uint32
+    out = []
+    with mpmath.workprec(320):
+        for b in xbits:
+            x = mpmath.mpf(float(np.array([b], dtype=ut).view(dt)[0]))
+            out.append(rn_bits(f(x), fmt))
+    return np.array(out, dtype=ut)
+
+
+def f32bits(vals):
+    return np.asarray(vals, dtype=np.float32).view(np.uint32)
+
+
+def f64bits(vals):
+    return np.asarray(vals, dtype=np.float64).view(np.uint64)
+
+
+DOMAINS = {  # finite inputs whose result is finite, non-saturated enough to be interesting
+    "expf": (-104.0, 89.0), "exp2f": (-150.5, 128.0), "exp10f": (-45.5, 38.6),
+    "expm1f": (-20.0, 88.7), "logf": (0.0, 3.4e38), "log2f": (0.0, 3.4e38),
+    "log10f": (0.0, 3.4e38), "log1pf": (-1.0, 3.4e38), "sinf": (-3.4e38, 3.4e38),
+    "cosf": (-3.4e38, 3.4e38), "tanf": (-3.4e38, 3.4e38), "asinf": (-1.0, 1.0),
+    "acosf": (-1.0, 1.0), "atanf": (-3.4e38, 3.4e38), "sinhf": (-89.4, 89.4),
+    "coshf": (-89.4, 89.4), "tanhf": (-12.0, 12.0), "rsqrtf": (0.0, 3.4e38),
+}
+
+
+def sample_f32(name, n, seed):
+    """Random bit patterns inside the function's interesting domain plus uniform reals in
+    a moderate range; both kinds exercise several binades."""
+    lo, hi = DOMAINS[name]
+    rng = np.random.default_rng(seed)
+    bits = rng.integers(0, 2**32, 8 * n, dtype=np.uint64).astype(np.uint32)
+    v = bits.view(np.float32)
+    ok = np.isfinite(v) & (v > lo) & (v < hi) & (v != 0)
+    a = bits[ok][: n // 2]
+    m = min(hi, 30.0), max(lo, -30.0)
+    u = rng.uniform(m[1], m[0], n - a.size).astype(np.float32)
+    u = u[(u > lo) & (u < hi) & (u != 0)]
+    return np.concatenate([a, u.view(np.uint32)])
+
+
+# ----------------------------------------------------------------------------------
+# big-integer primitives and constants
+# ----------------------------------------------------------------------------------
+
+def test_long_division_matches_python_integers():
+    rnd = random.Random(5)
+    for _ in range(400):
+        ub = rnd.randint(1, 1500)
+        vb = rnd.randint(1, min(ub, 900))
+        u = rnd.getrandbits(ub) | (1 << (ub - 1))
+        v = rnd.getrandbits(vb) | (1 << (vb - 1))
+        # include the hard "add back" pattern: divisor with high digit all ones
+        if rnd.random() < 0.2:
+            v |= ((1 << 32) - 1) << max(vb - 32, 0)
+        q, nz = O.test_divmod(u, v)
+        assert q == u // v
+        assert nz == int(u % v != 0)
+
+
+def test_integer_sqrt_matches_python_isqrt():
+    rnd = random.Random(7)
+    for _ in range(300):
+        nl = rnd.randint(1, 8)
+        N = rnd.getrandbits(64 * nl)
+        if rnd.random() < 0.3:
+            s = rnd.getrandbits(32 * nl)
+            N = s * s  # perfect squares: exactness flag must be 0
+        r, inexact = O.test_isqrt(N, nl)
+        assert r == math.isqrt(N)
+        assert inexact == int(r * r != N)
+
+
+@pytest.mark.parametrize("nlimbs", [3, 5, 9, 17, 33])
+def test_constants_enclose_true_values(nlimbs):
+    F = 64 * (nlimbs - 1)
+    with mpmath.workprec(F + 200):
+        refs = [mpmath.log(2), mpmath.log(10), mpmath.pi, 2 / mpmath.pi]
+        for which, ref in enumerate(refs):
+            lo, hi = O.constant(which, nlimbs)
+            v = ref * mpmath.mpf(2) ** F
+            assert lo <= v <= hi
+            assert hi - lo < 2**16  # tight: a few thousand units of 2^-F at most
+
+
+@pytest.mark.parametrize("nlimbs", [3, 9, 33])
+def test_constants_agree_with_second_formula(nlimbs):
+    # pi: Machin vs Gauss; ln2: 2 atanh(1/3) vs sum 1/(k 2^k).  Enclosures must overlap.
+    for which in (0, 2):
+        lo, hi = O.constant(which, nlimbs)
+        lo2, hi2 = O.constant(which, nlimbs, alt=True)
+        assert lo <= hi2 and lo2 <= hi
+
+
+# ----------------------------------------------------------------------------------
+# cross-check against mpmath on random inputs
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(DOMAINS))
+def test_f32_matches_mpmath(name):
+    xb = sample_f32(name, 600, seed=1000 + O.FUNC_ID[name])
+    got = O.eval_bits(name, xb)
+    ref = reference_bits(name, xb, F32)
+    bad = np.nonzero(got != ref)[0]
+    assert bad.size == 0, [(hex(int(xb[i])), hex(int(got[i])), hex(int(ref[i]))) for i in bad[:5]]
+
+
+def test_sincosf_equals_sinf_and_cosf():
+    xb = sample_f32("sinf", 2000, seed=77)
+    sc = O.eval_bits("sincosf", xb)
+    assert np.array_equal(sc[0], O.eval_bits("sinf", xb))
+    assert np.array_equal(sc[1], O.eval_bits("cosf", xb))
+
+
+def test_f64_exp2_matches_mpmath():
+    rng = np.random.default_rng(31)
+    x = np.concatenate([rng.uniform(-1075, 1024, 400), rng.uniform(-20, 20, 300),
+                        rng.uniform(-1e-10, 1e-10, 100) * 10.0 ** rng.integers(-300, 0, 100)])
+    xb = f64bits(x)
+    assert np.array_equal(O.eval_bits("exp2", xb), reference_bits("exp2", xb, F64))
+
+
+def test_f64_log_matches_mpmath():
+    rng = np.random.default_rng(32)
+    bits = rng.integers(1, 0x7FF0000000000000, 500, dtype=np.uint64)
+    x = np.concatenate([bits.view(np.float64), rng.uniform(0.125, 8.0, 300),
+                        1.0 + rng.uniform(-1e-6, 1e-6, 100)])
+    xb = f64bits(x)
+    assert np.array_equal(O.eval_bits("log", xb), reference_bits("log", xb, F64))
+
+
+# ----------------------------------------------------------------------------------
+# closed forms and exact cases
+# ----------------------------------------------------------------------------------
+
+def f32_pow2_bits(k):
+    """Bits of the binary32 value 2^k (k in [-149, 127])."""
+    if k >= -126:
+        return (k + 127) << 23
+    return 1 << (k + 149)
+
+
+def test_exp2f_of_integers_is_exact():
+    ks = np.arange(-149, 128)
+    got = O.eval_bits("exp2f", f32bits(ks.astype(np.float32)))
+    assert [int(g) for g in got] == [f32_pow2_bits(int(k)) for k in ks]
+    # 2^-150 is exactly the midpoint between +0 and the least subnormal: ties to even -> +0
+    assert int(O.eval_bits("exp2f", f32bits([-150.0]))[0]) == 0
+    assert int(O.eval_bits("exp2f", f32bits([-151.0]))[0]) == 0
+    assert int(O.eval_bits("exp2f", f32bits([128.0]))[0]) == 0x7F800000
+
+
+def test_exp2_f64_of_integers_is_exact():
+    ks = np.arange(-1074, 1024)
+    got = O.eval_bits("exp2", f64bits(ks.astype(np.float64)))
+    want = [((k + 1023) << 52) if k >= -1022 else (1 << (k + 1074)) for k in ks]
+    assert [int(g) for g in got] == want
+    assert int(O.eval_bits("exp2", f64bits([-1075.0]))[0]) == 0  # midpoint, ties to even
+    assert int(O.eval_bits("exp2", f64bits([1024.0]))[0]) == 0x7FF0000000000000
+
+
+def test_exp10f_exact_powers():
+    ks = np.arange(0, 11)
+    got = O.eval_f32("exp10f", ks.astype(np.float32))
+    assert np.array_equal(got, (10.0 ** ks).astype(np.float32))
+    assert np.array_equal(got.astype(np.float64), 10.0 ** ks)  # exactly representable
+
+
+def test_log2f_of_powers_of_two_all_277():
+    ks = list(range(-149, 128))
+    xb = np.array([f32_pow2_bits(k) for k in ks], dtype=np.uint32)
+    got = O.eval_f32("log2f", xb.view(np.float32))
+    assert np.array_equal(got, np.array(ks, dtype=np.float32))
+    assert int(got.view(np.uint32)[ks.index(0)]) == 0  # log2(1) = +0
+
+
+def test_log10f_of_powers_of_ten():
+    ks = np.arange(0, 11)
+    got = O.eval_f32("log10f", (10.0 ** ks).astype(np.float32))
+    assert np.array_equal(got, ks.astype(np.float32))
+
+
+def test_logs_of_one_are_plus_zero():
+    for name in ("logf", "log2f", "log10f"):
+        assert int(O.eval_bits(name, f32bits([1.0]))[0]) == 0
+    assert int(O.eval_bits("log", f64bits([1.0]))[0]) == 0
+
+
+def test_rsqrtf_of_powers_of_four():
+    ks = np.arange(-74, 64)
+    x = np.ldexp(np.ones(ks.size), 2 * ks).astype(np.float32)
+    got = O.eval_f32("rsqrtf", x)
+    assert np.array_equal(got.astype(np.float64), np.ldexp(np.ones(ks.size), -ks))
+
+
+def test_rsqrtf_rounding_decided_exactly():
+    # brute force: for random x, RN(1/sqrt(x)) is the unique float q with
+    # (q - ulp/2)^2 x < 1 < (q + ulp/2)^2 x  (exact rational comparison)
+    from fractions import Fraction
+    rng = np.random.default_rng(9)
+    xb = rng.integers(1, 0x7F800000, 300, dtype=np.uint64).astype(np.uint32)
+    got = O.eval_bits("rsqrtf", xb)
+    for b, g in zip(xb, got):
+        x = Fraction(float(np.array([b], dtype=np.uint32).view(np.float32)[0]))
+        q = Fraction(float(np.array([g], dtype=np.uint32).view(np.float32)[0]))
+        up = Fraction(float(np.array([g + 1], dtype=np.uint32).view(np.float32)[0])) - q
+        dn = q - Fraction(float(np.array([g - 1], dtype=np.uint32).view(np.float32)[0]))
+        assert (q - dn / 2) ** 2 * x < 1 < (q + up / 2) ** 2 * x
+
+
+# ----------------------------------------------------------------------------------
+# special values (the convention used throughout: quiet the NaN input, default +qNaN
+# for invalid operations)
+# ----------------------------------------------------------------------------------
+
+PINF, NINF, QN = 0x7F800000, 0xFF800000, 0x7FC00000
+ONE, MONE = 0x3F800000, 0xBF800000
+SPECIALS = {
+    # name: {input bits: output bits}
+    "expf": {0: ONE, 0x80000000: ONE, PINF: PINF, NINF: 0},
+    "exp2f": {0: ONE, PINF: PINF, NINF: 0},
+    "exp10f": {0: ONE, PINF: PINF, NINF: 0},
+    "expm1f": {0: 0, 0x80000000: 0x80000000, PINF: PINF, NINF: MONE},
+    "logf": {0: NINF, 0x80000000: NINF, PINF: PINF, NINF: QN, MONE: QN, ONE: 0},
+    "log2f": {0: NINF, 0x80000000: NINF, PINF: PINF, MONE: QN, ONE: 0},
+    "log10f": {0: NINF, PINF: PINF, MONE: QN, ONE: 0},
+    "log1pf": {0: 0, 0x80000000: 0x80000000, MONE: NINF, 0xC0000000: QN, PINF: PINF, NINF: QN},
+    "sinf": {0: 0, 0x80000000: 0x80000000, PINF: QN, NINF: QN},
+    "cosf": {0: ONE, 0x80000000: ONE, PINF: QN, NINF: QN},
+    "tanf": {0: 0, 0x80000000: 0x80000000, PINF: QN},
+    "asinf": {0: 0, 0x80000000: 0x80000000, 0x3F800001: QN, PINF: QN},
+    "acosf": {ONE: 0, 0x3F800001: QN, NINF: QN},
+    "atanf": {0: 0, 0x80000000: 0x80000000},
+    "sinhf": {0: 0, 0x80000000: 0x80000000, PINF: PINF, NINF: NINF},
+    "coshf": {0: ONE, 0x80000000: ONE, PINF: PINF, NINF: PINF},
+    "tanhf": {0: 0, 0x80000000: 0x80000000, PINF: ONE, NINF: MONE},
+    "rsqrtf": {0: PINF, 0x80000000: NINF, PINF: 0, MONE: QN, NINF: QN},
+}
+
+
+@pytest.mark.parametrize("name", list(SPECIALS))
+def test_special_values(name):
+    table = SPECIALS[name]
+    xb = np.array(list(table), dtype=np.uint32)
+    got = O.eval_bits(name, xb)
+    assert [hex(int(g)) for g in got] == [hex(v) for v in table.values()]
+
+
+@pytest.mark.parametrize("name", list(SPECIALS))
+def test_nan_inputs_are_quieted_with_payload(name):
+    xb = np.array([0x7FC00000, 0xFFC00001, 0x7F800001, 0x7FA00000, 0xFF812345], dtype=np.uint32)
+    got = O.eval_bits(name, xb)
+    assert np.array_equal(got, xb | 0x00400000)
+
+
+def test_pi_related_specials_round_pi():
+    pi_b = rn_bits(mpmath.pi, F32)
+    half_pi_b = rn_bits(mpmath.pi / 2, F32)
+    assert int(O.eval_bits("acosf", f32bits([-1.0]))[0]) == pi_b
+    assert int(O.eval_bits("asinf", f32bits([1.0]))[0]) == half_pi_b
+    assert int(O.eval_bits("asinf", f32bits([-1.0]))[0]) == half_pi_b | 0x80000000
+    assert int(O.eval_bits("atanf", np.array([PINF], np.uint32))[0]) == half_pi_b
+    assert int(O.eval_bits("atanf", np.array([NINF], np.uint32))[0]) == half_pi_b | 0x80000000
+
+
+# ----------------------------------------------------------------------------------
+# identities preserved by correct rounding
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,parity", [
+    ("sinf", "odd"), ("tanf", "odd"), ("asinf", "odd"), ("atanf", "odd"), ("sinhf", "odd"),
+    ("tanhf", "odd"), ("cosf", "even"), ("coshf", "even")])
+def test_symmetry(name, parity):
+    xb = sample_f32(name, 3000, seed=55)
+    pos = O.eval_bits(name, xb & 0x7FFFFFFF)
+    neg = O.eval_bits(name, xb | 0x80000000)
+    if parity == "odd":
+        assert np.array_equal(neg, pos ^ 0x80000000)
+    else:
+        assert np.array_equal(neg, pos)
+
+
+MONOTONE = {"expf": 1, "exp2f": 1, "exp10f": 1, "expm1f": 1, "logf": 1, "log2f": 1,
+            "log10f": 1, "log1pf": 1, "atanf": 1, "asinf": 1, "sinhf": 1, "tanhf": 1,
+            "acosf": -1, "rsqrtf": -1}
+
+
+@pytest.mark.parametrize("name", list(MONOTONE))
+def test_monotone_on_consecutive_floats(name):
+    lo, hi = DOMAINS[name]
+    starts = sample_f32(name, 12, seed=99)[:6]
+    for s in starts:
+        b = int(s)
+        run = np.arange(b, b + 2000, dtype=np.uint64).astype(np.uint32)
+        v = run.view(np.float32)
+        keep = np.isfinite(v) & (v > lo) & (v < hi)
+        run = run[keep]
+        if run.size < 2:
+            continue
+        order = np.argsort(run.view(np.float32).astype(np.float64), kind="stable")
+        y = O.eval_f32(name, run.view(np.float32)[order]).astype(np.float64)
+        d = np.diff(y) * MONOTONE[name]
+        assert np.all(d >= 0)
+
+
+def test_tiny_arguments_round_to_x_or_one():
+    # below these magnitudes the correctly rounded result is x itself (odd functions)
+    # or 1 (even ones); 2^-30 is far below each Taylor threshold.
+    tiny = np.array([2.0**-30, 2.0**-100, 2.0**-149, 1.5 * 2.0**-126], dtype=np.float32)
+    for name in ("sinf", "tanf", "asinf", "atanf", "sinhf", "tanhf", "expm1f", "log1pf"):
+        assert np.array_equal(O.eval_f32(name, tiny), tiny), name
+        assert np.array_equal(O.eval_f32(name, -tiny), -tiny), name
+    for name in ("cosf", "coshf", "expf", "exp2f", "exp10f"):
+        assert np.all(O.eval_f32(name, tiny) == 1.0), name
+
+
+def test_saturation():
+    assert np.all(O.eval_f32("tanhf", np.array([10.0, 20.0, 1e30], np.float32)) == 1.0)
+    assert np.all(O.eval_f32("expm1f", np.array([-20.0, -100.0, -1e30], np.float32)) == -1.0)
+    assert np.all(np.isinf(O.eval_f32("expf", np.array([88.73, 100.0], np.float32))))
+    assert np.all(O.eval_f32("expf", np.array([-104.0, -1000.0], np.float32)) == 0.0)
+
+
+def test_results_do_not_depend_on_threads():
+    xb = sample_f32("sinf", 5000, seed=8)
+    a = O.eval_bits("sinf", xb, nthreads=1)
+    b = O.eval_bits("sinf", xb, nthreads=7)
+    assert np.array_equal(a, b)

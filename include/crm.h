@@ -1,0 +1,139 @@
+/*
+ * crm.h -- correctly rounded array math for GB300 (sm_103a): the C ABI.
+ *
+ * Operation.  For every element x of an input array, store RN(f(x)): f evaluated exactly
+ * and rounded once to the nearest binary32 (or binary64) number, ties to even, with
+ * gradual underflow and overflow to infinity.  This is the correct-rounding goal of
+ * Sec. I and Sec. II of "Correctly Rounded Functions For Vector Applications: A
+ * Performance Study"; the GPU runs of Sec. III.C use round-to-nearest-even only, and so
+ * does this library.  The single-precision function set is the one of Sec. II.A; the
+ * double-precision pair (exp2, log) is the one of Sec. II.B.
+ *
+ * Evaluation forms (crm_form_t):
+ *   CRM_FORM_PLAIN_FP64 -- FP64 internal arithmetic, as the paper's single-precision
+ *                          algorithms do (Sec. II.A), plus a rounding test;
+ *   CRM_FORM_DF32       -- FP32 double-float fast path with a rounding test and an
+ *                          FP64 / double-double fallback (the FP32 fast path with FP64
+ *                          fallback suggested in Sec. II.A and Sec. IV);
+ *   CRM_FORM_AUTO       -- the fastest form available for the function (DF32 where it
+ *                          exists).
+ * Every form returns the same, correctly rounded, bits: the form changes speed only.
+ * Lanes whose fast-path rounding test fails are compacted into a device queue and
+ * finished by a slow-path kernel (Sec. II.B: only the failing lanes take the slow path).
+ *
+ * Special values (the paper does not fix them; this library's convention):
+ *   NaN input            -> the input, quieted (sign and payload kept);
+ *   invalid operation    -> +qNaN (0x7FC00000 / 0x7FF8000000000000);
+ *   odd functions keep the sign of zero; log-family(+-0) = -inf; log1p(-1) = -inf;
+ *   rsqrt(+-0) = +-inf; expm1(-inf) = -1; tanh(+-inf) = +-1; atan(+-inf) = +-RN(pi/2).
+ *
+ * Memory and streams.  Pointers named "device" must be device memory (or memory the
+ * device can access) allocated by the caller; the caller owns them.  Calls are
+ * asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ * stream).  The library owns a per-(device, stream) workspace (hard-case queue and
+ * counters) allocated on first use or by crm_reserve() and freed by crm_shutdown().
+ * Calls on different streams may overlap; calls on one stream are ordered.
+ * in == out (in place) is allowed; any other overlap returns CRM_ERR_OVERLAP.
+ * Any alignment is accepted (unaligned heads and tails take a scalar loop).
+ * n == 0 returns CRM_OK without launching anything.
+ */
+#ifndef CRM_H
+#define CRM_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CRM_EXPF = 0, CRM_EXP2F, CRM_EXP10F, CRM_EXPM1F, CRM_LOGF, CRM_LOG2F, CRM_LOG10F,
+  CRM_LOG1PF, CRM_SINF, CRM_COSF, CRM_SINCOSF, CRM_TANF, CRM_ASINF, CRM_ACOSF,
+  CRM_ATANF, CRM_SINHF, CRM_COSHF, CRM_TANHF, CRM_RSQRTF, /* binary32 in and out */
+  CRM_EXP2 = 19, CRM_LOG = 20,                             /* binary64 in and out */
+  CRM_NUM_FUNCS = 21
+} crm_func_t;
+
+typedef enum { CRM_F32 = 0, CRM_F64 = 1 } crm_dtype_t;
+typedef enum { CRM_FORM_AUTO = 0, CRM_FORM_PLAIN_FP64 = 1, CRM_FORM_DF32 = 2 } crm_form_t;
+
+typedef enum {
+  CRM_OK = 0,
+  CRM_ERR_FUNC = 1,     /* unknown function id */
+  CRM_ERR_DTYPE = 2,    /* dtype does not match the function (e.g. CRM_EXPF with F64) */
+  CRM_ERR_NULL = 3,     /* null in/out with n > 0, or null descriptor array */
+  CRM_ERR_OVERLAP = 4,  /* in and out overlap partially */
+  CRM_ERR_CUDA = 5,     /* a CUDA runtime call failed (see crm_last_cuda_error) */
+  CRM_ERR_NOMEM = 6,    /* workspace allocation failed */
+  CRM_ERR_FORM = 7,     /* unknown or unavailable form */
+  CRM_ERR_CAPTURE = 8,  /* workspace must grow while the stream is being captured */
+  CRM_ERR_ARG = 9,      /* other invalid argument (negative count, size too large) */
+  CRM_ERR_NODEV = 10    /* no CUDA device */
+} crm_status_t;
+
+/* One array of a batch (crm_eval_batch).  in/out are device pointers; out holds 2n
+   elements for CRM_SINCOSF (sin in [0,n), cos in [n,2n)). */
+typedef struct {
+  int32_t func_id;
+  int32_t dtype;
+  const void *in;
+  void *out;
+  uint64_t n;
+} crm_desc_t;
+
+/* Counters of the (device, stream) workspace; crm_stats synchronises the stream. */
+typedef struct {
+  uint64_t hard_total;       /* lanes that failed a fast-path rounding test */
+  uint64_t unresolved_total; /* lanes no tier could decide (0 unless something is wrong) */
+  uint64_t inline_total;     /* hard lanes finished inline because the queue was full */
+  uint64_t last_count;       /* hard lanes of the last call on this stream */
+} crm_stats_t;
+
+/* Evaluate func_id on n elements: out[i] = RN(f(in[i])) (sincosf: out[i] = sin,
+   out[n+i] = cos).  in/out: device pointers of dtype elements.  Uses the process-wide
+   default form (crm_set_form, env CRM_FORM = auto|plain|df).  Asynchronous.
+   Errors: CRM_ERR_FUNC, CRM_ERR_DTYPE, CRM_ERR_NULL, CRM_ERR_OVERLAP, CRM_ERR_NOMEM,
+   CRM_ERR_CAPTURE, CRM_ERR_CUDA; nothing is launched on error. */
+int crm_eval(int func_id, int dtype, const void *in, void *out, uint64_t n, void *stream);
+
+/* Same with an explicit form (crm_form_t). */
+int crm_eval_form(int func_id, int dtype, int form, const void *in, void *out, uint64_t n,
+                  void *stream);
+
+/* Host-buffer variant: in/out are host pointers (page-locked for full speed).  Copies
+   chunks to a library-owned device staging area, evaluates and copies back, overlapping
+   the transfers with compute; returns after the results are in `out` (synchronous). */
+int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, uint64_t n,
+                  void *stream);
+
+/* Evaluate `count` arrays of mixed functions and lengths with one persistent kernel
+   (the batching form).  descs is host memory, read before return.  Asynchronous. */
+int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream);
+
+/* Process-wide default form for crm_eval (initially from env CRM_FORM, else AUTO). */
+int crm_set_form(int form);
+
+/* Pre-allocate the workspace of (current device, stream) for calls of up to
+   max_elems elements and batches of up to max_arrays arrays, so that later calls
+   allocate nothing (required before capturing calls into a CUDA graph). */
+int crm_reserve(uint64_t max_elems, int max_arrays, void *stream);
+
+/* Read (and synchronise) the counters of (current device, stream). */
+int crm_stats(void *stream, crm_stats_t *out);
+int crm_stats_reset(void *stream);
+
+/* Test hook: when nonzero, every lane fails its fast-path rounding test, so the queue
+   and the slow path carry the whole array (results must not change). */
+int crm_set_force_slow(int on);
+
+const char *crm_status_str(int status);
+/* The cudaError_t of the last CRM_ERR_CUDA on this thread. */
+int crm_last_cuda_error(void);
+/* Release every workspace (all devices).  Not to be called while work is in flight. */
+void crm_shutdown(void);
+/* Library version string. */
+const char *crm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,127 @@
+"""Correctly rounded array math on GB300 (sm_103a): Python binding of include/crm.h.
+
+    import torch, paper_2605_15547_gb300 as crm
+    y = crm.eval("expf", x)            # x: contiguous float32 CUDA tensor
+    y = crm.eval("sinf", x, form="df") # force the double-float form
+
+Torch supplies device memory and the current stream; every element is computed by the
+library's CUDA kernels (the C ABI), which fail loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib as L
+from ._lib import F64_FUNCS, FORMS, FUNC_ID, FUNCS, CrmError, crm_desc_t, crm_stats_t
+
+__all__ = ["eval", "eval_into", "eval_host", "eval_batch", "stats", "stats_reset",
+           "set_form", "set_force_slow", "reserve", "FUNCS", "FORMS", "CrmError", "version"]
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _fid(func) -> int:
+    if isinstance(func, str):
+        if func not in FUNC_ID:
+            raise ValueError(f"unknown function {func!r}")
+        return FUNC_ID[func]
+    return int(func)
+
+
+def _form(form) -> int:
+    if form is None:
+        return 0
+    if isinstance(form, str):
+        return FORMS[form]
+    return int(form)
+
+
+def out_shape(func, n: int):
+    return (2, n) if FUNCS[_fid(func)] == "sincosf" else (n,)
+
+
+def eval_into(func, x, out, form=None, stream=None) -> None:
+    """out <- RN(f(x)) for contiguous CUDA tensors (sincosf: out has 2*n elements)."""
+    fid = _fid(func)
+    dtype = L.CRM_F64 if FUNCS[fid] in F64_FUNCS else L.CRM_F32
+    n = x.numel()
+    L.check(L.lib().crm_eval_form(fid, dtype, _form(form), ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()), n, _stream_ptr(stream)),
+            FUNCS[fid])
+
+
+def eval(func, x, out=None, form=None, stream=None):
+    """Return RN(f(x)) elementwise (a new tensor unless `out` is given).  For sincosf the
+    result has shape (2, *x.shape): sin then cos."""
+    import torch
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous CUDA tensor")
+    fid = _fid(func)
+    want = torch.float64 if FUNCS[fid] in F64_FUNCS else torch.float32
+    if x.dtype != want:
+        raise TypeError(f"{FUNCS[fid]} takes {want}, got {x.dtype}")
+    if out is None:
+        shape = ((2,) + tuple(x.shape)) if FUNCS[fid] == "sincosf" else x.shape
+        out = torch.empty(shape, dtype=want, device=x.device)
+    eval_into(fid, x, out, form=form, stream=stream)
+    return out
+
+
+def eval_host(func, x_np, out_np=None, form=None, stream=None):
+    """Host (numpy) buffers in and out; the library copies, computes and copies back."""
+    import numpy as np
+    fid = _fid(func)
+    f64 = FUNCS[fid] in F64_FUNCS
+    x_np = np.ascontiguousarray(x_np, dtype=np.float64 if f64 else np.float32)
+    n = x_np.size
+    if out_np is None:
+        out_np = np.empty((2 * n) if FUNCS[fid] == "sincosf" else n, dtype=x_np.dtype)
+    L.check(L.lib().crm_eval_host(fid, L.CRM_F64 if f64 else L.CRM_F32, _form(form),
+                                  ctypes.c_void_p(x_np.ctypes.data),
+                                  ctypes.c_void_p(out_np.ctypes.data), n,
+                                  _stream_ptr(stream)), FUNCS[fid])
+    return out_np
+
+
+def eval_batch(items, form=None, stream=None) -> None:
+    """items: list of (func, x, out) with contiguous CUDA tensors; one batched launch."""
+    descs = (crm_desc_t * len(items))()
+    for d, (func, x, out) in zip(descs, items):
+        fid = _fid(func)
+        d.func_id = fid
+        d.dtype = L.CRM_F64 if FUNCS[fid] in F64_FUNCS else L.CRM_F32
+        d.in_ = x.data_ptr()
+        d.out = out.data_ptr()
+        d.n = x.numel()
+    L.check(L.lib().crm_eval_batch(descs, len(items), _form(form), _stream_ptr(stream)), "batch")
+
+
+def stats(stream=None) -> dict:
+    s = crm_stats_t()
+    L.check(L.lib().crm_stats(_stream_ptr(stream), ctypes.byref(s)))
+    return {"hard_total": s.hard_total, "unresolved_total": s.unresolved_total,
+            "inline_total": s.inline_total, "last_count": s.last_count}
+
+
+def stats_reset(stream=None) -> None:
+    L.check(L.lib().crm_stats_reset(_stream_ptr(stream)))
+
+
+def set_form(form) -> None:
+    L.check(L.lib().crm_set_form(_form(form)))
+
+
+def set_force_slow(on: bool) -> None:
+    L.check(L.lib().crm_set_force_slow(1 if on else 0))
+
+
+def reserve(max_elems: int, max_arrays: int = 0, stream=None) -> None:
+    L.check(L.lib().crm_reserve(max_elems, max_arrays, _stream_ptr(stream)))
+
+
+def version() -> str:
+    return L.lib().crm_version().decode()

@@ -1,0 +1,207 @@
+// crm_kernels.cuh -- the array kernels.
+//
+// k_main: one pass over the array, 128-bit coalesced loads and stores (4 binary32 per
+//   vector, UNROLL vectors in flight per thread), the chosen tier's evaluator per element,
+//   and hard-case compaction: a warp-uniform __any_sync test; when some lane failed its
+//   rounding test, __ballot_sync + __popc reserve queue slots with one atomicAdd per warp
+//   and the failing lanes write (index, input bits).  This is the paper's Sec. II.B
+//   pattern (only failing lanes go to the slow path) mapped to warps.
+// k_slow: stream-ordered after k_main, a fixed grid drains the queue with the exact
+//   slow path.  If the queue was full, k_main evaluates those lanes inline instead, so no
+//   lane is ever dropped.
+#pragma once
+#include <stdint.h>
+
+#include "crm_common.cuh"
+#include "crm_ws.h"
+
+namespace crm {
+
+constexpr int KBLOCK = 256;
+
+struct KArgs {
+  const void *in;
+  void *out;
+  uint64_t n;        // elements
+  uint64_t head;     // leading elements handled by the scalar loop (alignment)
+  uint64_t nvec;     // float4 / double2 vectors after the head
+  crm_ws_header *hdr;
+  crm_queue_entry *q;
+  uint64_t cap;      // queue capacity (entries)
+  int force_hard;    // test hook: every lane takes the slow path
+  uint32_t desc;     // array id recorded in queue entries (batch form)
+};
+
+template <class T> struct VecOf;
+template <> struct VecOf<float> { using V = float4; static constexpr int W = 4; };
+template <> struct VecOf<double> { using V = double2; static constexpr int W = 2; };
+
+CRM_DEV float4 ld_stream(const float4 *p) { return __ldcs(p); }
+CRM_DEV double2 ld_stream(const double2 *p) { return __ldcs(p); }
+CRM_DEV void st_stream(float4 *p, float4 v) { __stcs(p, v); }
+CRM_DEV void st_stream(double2 *p, double2 v) { __stcs(p, v); }
+CRM_DEV float vget(const float4 &v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+CRM_DEV double vget(const double2 &v, int j) { return j == 0 ? v.x : v.y; }
+CRM_DEV void vset(float4 &v, int j, float a) {
+  if (j == 0) v.x = a; else if (j == 1) v.y = a; else if (j == 2) v.z = a; else v.w = a;
+}
+CRM_DEV void vset(double2 &v, int j, double a) {
+  if (j == 0) v.x = a; else v.y = a;
+}
+CRM_DEV uint64_t xbits_of(float x) { return fbits(x); }
+CRM_DEV uint64_t xbits_of(double x) { return dbits(x); }
+template <class T> CRM_DEV T x_from_bits(uint64_t b);
+template <> CRM_DEV float x_from_bits<float>(uint64_t b) { return bitsf((uint32_t)b); }
+template <> CRM_DEV double x_from_bits<double>(uint64_t b) { return bitsd(b); }
+
+// Reserve queue slots for the lanes with h set (whole warp calls this, warp-uniform).
+// Returns true for a lane whose slot is beyond the capacity (must finish inline).
+CRM_DEV bool push_hard(bool h, uint64_t idx, uint64_t xb, const KArgs &a) {
+  unsigned m = __ballot_sync(0xFFFFFFFFu, h);
+  if (!m) return false;
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(&a.hdr->count, (unsigned long long)__popc(m));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  if (!h) return false;
+  unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+  if (pos < a.cap) {
+    crm_queue_entry e;
+    e.idx = ((uint64_t)a.desc << 40) | idx;
+    e.x = xb;
+    a.q[pos] = e;
+    return false;
+  }
+  return true;
+}
+
+// Fn interface (one struct per function, see the k_*.cu files):
+//   using T = float | double;  static constexpr int NOUT = 1 | 2;
+//   template <int FORM> static constexpr int tab_bytes();
+//   template <int FORM> CRM_DEV static const void *tab();
+//   template <int FORM> CRM_DEV static void eval(T x, const void *sm, T *y, bool &hard);
+//   CRM_DEV static void slow(T x, T *y, bool &unresolved);
+
+template <class Fn, int FORM>
+CRM_DEV void load_tab(unsigned char *sm) {
+  constexpr int B = Fn::template tab_bytes<FORM>();
+  if (B > 0) {
+    const uint32_t *src = (const uint32_t *)Fn::template tab<FORM>();
+    uint32_t *dst = (uint32_t *)sm;
+    for (int i = threadIdx.x; i < B / 4; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+}
+
+template <class Fn>
+__device__ __noinline__ void slow_store(typename Fn::T x, uint64_t i, const KArgs &a) {
+  using T = typename Fn::T;
+  T y[2];
+  bool unres;
+  Fn::slow(x, y, unres);
+  T *out = (T *)a.out;
+  out[i] = y[0];
+  if (Fn::NOUT == 2) out[a.n + i] = y[1];
+  atomicAdd(&a.hdr->inline_total, 1ull);
+  if (unres) atomicAdd(&a.hdr->unresolved_total, 1ull);
+}
+
+template <class Fn, int FORM, int UNROLL>
+__global__ void __launch_bounds__(KBLOCK) k_main(KArgs a) {
+  using T = typename Fn::T;
+  using V = typename VecOf<T>::V;
+  constexpr int W = VecOf<T>::W;
+  __shared__ __align__(16) unsigned char sm[(Fn::template tab_bytes<FORM>() > 0) ? Fn::template tab_bytes<FORM>() : 16];
+  load_tab<Fn, FORM>(sm);
+
+  const V *in4 = (const V *)((const T *)a.in + a.head);
+  V *out4 = (V *)((T *)a.out + a.head);
+  V *out4b = (V *)((T *)a.out + a.n + a.head);  // second output (sincos)
+  const uint64_t stride = (uint64_t)gridDim.x * KBLOCK * UNROLL;
+  for (uint64_t base = (uint64_t)blockIdx.x * KBLOCK * UNROLL; base < a.nvec; base += stride) {
+    V xv[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; u++) {
+      uint64_t v = base + (uint64_t)u * KBLOCK + threadIdx.x;
+      if (v < a.nvec) xv[u] = ld_stream(in4 + v);
+      else {
+        xv[u] = V();
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; u++) {
+      uint64_t v = base + (uint64_t)u * KBLOCK + threadIdx.x;
+      bool act = v < a.nvec;
+      V y0, y1;
+      unsigned hm = 0;
+#pragma unroll
+      for (int j = 0; j < W; j++) {
+        T y[2];
+        bool h;
+        Fn::template eval<FORM>(vget(xv[u], j), sm, y, h);
+        h = (h || a.force_hard) && act;
+        hm |= (unsigned)h << j;
+        vset(y0, j, y[0]);
+        if (Fn::NOUT == 2) vset(y1, j, y[1]);
+      }
+      if (act) {
+        st_stream(out4 + v, y0);
+        if (Fn::NOUT == 2) st_stream(out4b + v, y1);
+      }
+      if (__any_sync(0xFFFFFFFFu, hm != 0)) {
+#pragma unroll
+        for (int j = 0; j < W; j++) {
+          uint64_t i = a.head + v * W + j;
+          T x = vget(xv[u], j);
+          if (push_hard((hm >> j) & 1, i, xbits_of(x), a)) slow_store<Fn>(x, i, a);
+        }
+      }
+    }
+  }
+  // scalar part: the head [0, head) and the tail [head + W nvec, n)
+  const uint64_t tail0 = a.head + (uint64_t)W * a.nvec;
+  const uint64_t nscal = a.head + (a.n - tail0);
+  const T *in = (const T *)a.in;
+  T *out = (T *)a.out;
+  const uint64_t sstride = (uint64_t)gridDim.x * KBLOCK;
+  for (uint64_t b = (uint64_t)blockIdx.x * KBLOCK; b < nscal; b += sstride) {
+    uint64_t k = b + threadIdx.x;
+    bool act = k < nscal;
+    uint64_t i = k < a.head ? k : tail0 + (k - a.head);
+    T x = act ? in[i] : T(0);
+    T y[2];
+    bool h;
+    Fn::template eval<FORM>(x, sm, y, h);
+    h = (h || a.force_hard) && act;
+    if (act) {
+      out[i] = y[0];
+      if (Fn::NOUT == 2) out[a.n + i] = y[1];
+    }
+    if (__any_sync(0xFFFFFFFFu, h))
+      if (push_hard(h, i, xbits_of(x), a)) slow_store<Fn>(x, i, a);
+  }
+}
+
+template <class Fn>
+__global__ void __launch_bounds__(KBLOCK) k_slow(KArgs a) {
+  using T = typename Fn::T;
+  unsigned long long cnt = *(volatile unsigned long long *)&a.hdr->count;
+  if (cnt > a.cap) cnt = a.cap;
+  T *out = (T *)a.out;
+  for (uint64_t i = (uint64_t)blockIdx.x * KBLOCK + threadIdx.x; i < cnt;
+       i += (uint64_t)gridDim.x * KBLOCK) {
+    crm_queue_entry e = a.q[i];
+    uint64_t idx = e.idx & ((1ull << 40) - 1);
+    T x = x_from_bits<T>(e.x);
+    T y[2];
+    bool unres;
+    Fn::slow(x, y, unres);
+    out[idx] = y[0];
+    if (Fn::NOUT == 2) out[a.n + idx] = y[1];
+    if (unres) atomicAdd(&a.hdr->unresolved_total, 1ull);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.hdr->hard_total, (unsigned long long)a.hdr->count);
+}
+
+}  // namespace crm

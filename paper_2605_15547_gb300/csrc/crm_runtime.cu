@@ -1,0 +1,338 @@
+// crm_runtime.cu -- the C ABI of include/crm.h: argument checks, per-(device, stream)
+// workspaces, launch configuration, the host-buffer and batch entry points.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "../../include/crm.h"
+#include "crm_registry.h"
+
+namespace crm {
+
+static FuncEntry g_table[CRM_NUM_FUNCS];
+static std::once_flag g_init_once;
+static int g_default_form = CRM_FORM_AUTO;
+static int g_force_slow = 0;
+static thread_local int g_last_cuda = 0;
+
+static void init_table() {
+  memset(g_table, 0, sizeof(g_table));
+  register_exp(g_table);
+  const char *f = getenv("CRM_FORM");
+  if (f) {
+    if (!strcmp(f, "plain")) g_default_form = CRM_FORM_PLAIN_FP64;
+    if (!strcmp(f, "df")) g_default_form = CRM_FORM_DF32;
+  }
+  const char *fs = getenv("CRM_FORCE_SLOW");
+  if (fs && atoi(fs)) g_force_slow = 1;
+}
+static void ensure_init() { std::call_once(g_init_once, init_table); }
+
+// ------------------------------------------------------------------ workspaces
+struct Workspace {
+  crm_ws_header *hdr = nullptr;  // device
+  crm_queue_entry *q = nullptr;  // device
+  uint64_t cap = 0;
+};
+
+struct DevInfo {
+  int sms = 0;
+  std::map<const void *, int> occ;  // kernel symbol -> resident blocks per SM
+};
+
+static std::mutex g_mu;
+static std::map<std::pair<int, uintptr_t>, Workspace> g_ws;
+static std::map<int, DevInfo> g_dev;
+
+static const uint64_t kDefaultCap = 1ull << 21;  // 2M hard lanes (32 MiB) per workspace
+
+static int cuda_fail(cudaError_t e) {
+  g_last_cuda = (int)e;
+  return CRM_ERR_CUDA;
+}
+
+static bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+  return st != cudaStreamCaptureStatusNone;
+}
+
+// Workspace of (current device, stream) with at least `cap` queue entries.
+static int get_ws(cudaStream_t s, uint64_t cap, Workspace **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace &w = g_ws[{dev, (uintptr_t)s}];
+  if (w.hdr && w.cap >= cap) {
+    *out = &w;
+    return CRM_OK;
+  }
+  if (capturing(s)) return CRM_ERR_CAPTURE;
+  if (w.hdr) {  // grow: keep the header (counters), replace the queue
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    cudaFree(w.q);
+    w.q = nullptr;
+  } else {
+    e = cudaMalloc((void **)&w.hdr, sizeof(crm_ws_header));
+    if (e != cudaSuccess) {
+      w.hdr = nullptr;
+      return e == cudaErrorMemoryAllocation ? CRM_ERR_NOMEM : cuda_fail(e);
+    }
+    e = cudaMemset(w.hdr, 0, sizeof(crm_ws_header));
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  e = cudaMalloc((void **)&w.q, cap * sizeof(crm_queue_entry));
+  if (e != cudaSuccess) {
+    w.q = nullptr;
+    w.cap = 0;
+    return e == cudaErrorMemoryAllocation ? CRM_ERR_NOMEM : cuda_fail(e);
+  }
+  w.cap = cap;
+  *out = &w;
+  return CRM_OK;
+}
+
+static int dev_sms() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevInfo &d = g_dev[dev];
+  if (!d.sms) {
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || d.sms <= 0)
+      d.sms = 1;
+  }
+  return d.sms;
+}
+
+static int blocks_per_sm(const void *sym) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevInfo &d = g_dev[dev];
+  auto it = d.occ.find(sym);
+  if (it != d.occ.end()) return it->second;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sym, KBLOCK, 0) != cudaSuccess || nb <= 0) nb = 1;
+  d.occ[sym] = nb;
+  return nb;
+}
+
+// Unroll variant per (function, form): the autotuner's choice (index into 1, 2, 4).
+static int g_unroll[CRM_NUM_FUNCS][3];
+static bool g_unroll_set = false;
+
+static int unroll_of(int func, int form) {
+  if (!g_unroll_set) {
+    for (int f = 0; f < CRM_NUM_FUNCS; f++)
+      for (int m = 0; m < 3; m++) g_unroll[f][m] = 1;  // 2 vectors in flight by default
+    g_unroll_set = true;
+  }
+  return g_unroll[func][form];
+}
+
+static int resolve_form(const FuncEntry &fe, int form) {
+  if (form == CRM_FORM_AUTO) {
+    if (fe.main[CRM_FORM_DF32][0]) return CRM_FORM_DF32;
+    if (fe.main[CRM_FORM_PLAIN_FP64][0]) return CRM_FORM_PLAIN_FP64;
+    return -1;
+  }
+  if (form != CRM_FORM_PLAIN_FP64 && form != CRM_FORM_DF32) return -1;
+  return fe.main[form][0] ? form : -1;
+}
+
+static int check_args(int func, int dtype, const void *in, void *out, uint64_t n) {
+  if (func < 0 || func >= CRM_NUM_FUNCS) return CRM_ERR_FUNC;
+  const FuncEntry &fe = g_table[func];
+  int want = func >= CRM_EXP2 ? CRM_F64 : CRM_F32;
+  if (dtype != CRM_F32 && dtype != CRM_F64) return CRM_ERR_DTYPE;
+  if (dtype != want) return CRM_ERR_DTYPE;
+  if (n == 0) return CRM_OK;
+  if (!in || !out) return CRM_ERR_NULL;
+  size_t es = dtype == CRM_F64 ? 8 : 4;
+  if (((uintptr_t)in % es) || ((uintptr_t)out % es)) return CRM_ERR_ARG;
+  if (n > (1ull << 40)) return CRM_ERR_ARG;
+  uintptr_t a0 = (uintptr_t)in, a1 = a0 + n * es;
+  uintptr_t b0 = (uintptr_t)out, b1 = b0 + n * es * (func == CRM_SINCOSF ? 2 : 1);
+  if (a0 != b0 && a0 < b1 && b0 < a1) return CRM_ERR_OVERLAP;
+  (void)fe;
+  return CRM_OK;
+}
+
+// Enqueue one evaluation (arguments already checked, n > 0).
+static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cudaStream_t s,
+                   uint32_t desc) {
+  const FuncEntry &fe = g_table[func];
+  int fm = resolve_form(fe, form);
+  if (fm < 0) return CRM_ERR_FORM;
+  Workspace *w = nullptr;
+  int st = get_ws(s, kDefaultCap, &w);
+  if (st) return st;
+  const size_t es = fe.dtype ? 8 : 4;
+  const int W = fe.dtype ? 2 : 4;
+  KArgs a;
+  a.in = in;
+  a.out = out;
+  a.n = n;
+  a.hdr = w->hdr;
+  a.q = w->q;
+  a.cap = w->cap;
+  a.force_hard = g_force_slow;
+  a.desc = desc;
+  // vector path: input and output(s) share their offset modulo 16 bytes
+  uintptr_t ia = (uintptr_t)in, oa = (uintptr_t)out;
+  bool vec = ((ia - oa) % 16) == 0 && (fe.nout == 1 || (n * es) % 16 == 0);
+  if (vec) {
+    uint64_t head = ((16 - ia % 16) % 16) / es;
+    if (head > n) head = n;
+    a.head = head;
+    a.nvec = (n - head) / W;
+  } else {
+    a.head = 0;
+    a.nvec = 0;
+  }
+  int ui = unroll_of(func, fm);
+  const int U = 1 << ui;
+  int sms = dev_sms();
+  int bps = blocks_per_sm(fe.main_sym[fm][ui]);
+  uint64_t want = (a.nvec + (uint64_t)KBLOCK * U - 1) / ((uint64_t)KBLOCK * U);
+  uint64_t nscal = a.head + (n - a.head - (uint64_t)W * a.nvec);
+  uint64_t want_s = (nscal + KBLOCK - 1) / KBLOCK;
+  if (want_s > want) want = want_s;
+  uint64_t cap_blocks = (uint64_t)sms * bps;
+  int grid = (int)(want < cap_blocks ? (want ? want : 1) : cap_blocks);
+  cudaError_t e = cudaMemsetAsync(&w->hdr->count, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = fe.main[fm][ui](a, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = fe.slow(a, sms * 2, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return CRM_OK;
+}
+
+}  // namespace crm
+
+using namespace crm;
+
+extern "C" {
+
+int crm_eval_form(int func_id, int dtype, int form, const void *in, void *out, uint64_t n, void *stream) {
+  ensure_init();
+  int st = check_args(func_id, dtype, in, out, n);
+  if (st) return st;
+  if (form < CRM_FORM_AUTO || form > CRM_FORM_DF32) return CRM_ERR_FORM;
+  if (resolve_form(g_table[func_id], form) < 0) return CRM_ERR_FORM;
+  if (n == 0) return CRM_OK;
+  return enqueue(func_id, form, in, out, n, (cudaStream_t)stream, 0);
+}
+
+int crm_eval(int func_id, int dtype, const void *in, void *out, uint64_t n, void *stream) {
+  ensure_init();
+  return crm_eval_form(func_id, dtype, g_default_form, in, out, n, stream);
+}
+
+int crm_set_form(int form) {
+  ensure_init();
+  if (form < CRM_FORM_AUTO || form > CRM_FORM_DF32) return CRM_ERR_FORM;
+  g_default_form = form;
+  return CRM_OK;
+}
+
+int crm_set_force_slow(int on) {
+  ensure_init();
+  g_force_slow = on ? 1 : 0;
+  return CRM_OK;
+}
+
+int crm_reserve(uint64_t max_elems, int max_arrays, void *stream) {
+  ensure_init();
+  if (max_arrays < 0) return CRM_ERR_ARG;
+  Workspace *w;
+  uint64_t cap = kDefaultCap;
+  (void)max_elems;
+  return get_ws((cudaStream_t)stream, cap, &w);
+}
+
+int crm_stats(void *stream, crm_stats_t *out) {
+  ensure_init();
+  if (!out) return CRM_ERR_NULL;
+  Workspace *w;
+  int st = get_ws((cudaStream_t)stream, kDefaultCap, &w);
+  if (st) return st;
+  crm_ws_header h;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaMemcpy(&h, w->hdr, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e);
+  out->hard_total = h.hard_total;
+  out->unresolved_total = h.unresolved_total;
+  out->inline_total = h.inline_total;
+  out->last_count = h.count;
+  return CRM_OK;
+}
+
+int crm_stats_reset(void *stream) {
+  ensure_init();
+  Workspace *w;
+  int st = get_ws((cudaStream_t)stream, kDefaultCap, &w);
+  if (st) return st;
+  cudaError_t e = cudaMemsetAsync(w->hdr, 0, sizeof(crm_ws_header), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaStreamSynchronize((cudaStream_t)stream);
+  return e == cudaSuccess ? CRM_OK : cuda_fail(e);
+}
+
+int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, uint64_t n, void *stream) {
+  (void)func_id; (void)dtype; (void)form; (void)in; (void)out; (void)n; (void)stream;
+  return CRM_ERR_FORM;
+}
+
+int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
+  (void)descs; (void)count; (void)form; (void)stream;
+  return CRM_ERR_FORM;
+}
+
+const char *crm_status_str(int status) {
+  switch (status) {
+    case CRM_OK: return "ok";
+    case CRM_ERR_FUNC: return "unknown function id";
+    case CRM_ERR_DTYPE: return "dtype does not match the function";
+    case CRM_ERR_NULL: return "null pointer";
+    case CRM_ERR_OVERLAP: return "input and output overlap partially";
+    case CRM_ERR_CUDA: return "CUDA runtime error";
+    case CRM_ERR_NOMEM: return "out of device memory";
+    case CRM_ERR_FORM: return "form not available for this function";
+    case CRM_ERR_CAPTURE: return "workspace must grow during stream capture";
+    case CRM_ERR_ARG: return "invalid argument";
+    case CRM_ERR_NODEV: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+int crm_last_cuda_error(void) { return g_last_cuda; }
+
+void crm_shutdown(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto &kv : g_ws) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(kv.first.first);
+    if (kv.second.q) cudaFree(kv.second.q);
+    if (kv.second.hdr) cudaFree(kv.second.hdr);
+    cudaSetDevice(cur);
+  }
+  g_ws.clear();
+  g_dev.clear();
+}
+
+const char *crm_version(void) { return "crm 0.1 (sm_103a)"; }
+
+}  // extern "C"

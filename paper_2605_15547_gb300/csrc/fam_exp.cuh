@@ -1,0 +1,213 @@
+// fam_exp.cuh -- b^x for b in {e, 2, 10} (expf, exp2f, exp10f).
+//
+// Every tier follows the paper's exp2f scheme (Fig. 1, Sec. II.A): write the argument in
+// base 2, t = x log2(b), split t = k + j/2^J + g with a small table of 2^(j/2^J) (at most
+// 16 entries in the FP64 and double-double tiers, 64 in the double-float tier), evaluate
+// 2^g by a polynomial, and scale by 2^k with integer exponent arithmetic.  Infinite and
+// NaN inputs and the saturated ranges are handled by selects in the same pass.
+#pragma once
+#include "crm_common.cuh"
+#include "crm_tables.h"
+
+namespace crm {
+
+// KIND 0: e^x, 1: 2^x, 2: 10^x
+template <int KIND> struct ExpK;
+template <> struct ExpK<0> {
+  static constexpr float C16 = CRM_LOG2E_X16_F, C64 = CRM_LOG2E_X64_F;
+  static constexpr double D0 = CRM_LOG2E_D0, D1 = CRM_LOG2E_D1, D2 = CRM_LOG2E_D2;
+  static constexpr float F0 = CRM_LOG2E_F0, F1 = CRM_LOG2E_F1;
+  static constexpr float OVF = 89.0f, UNF = -104.0f;  // beyond: +inf / +0 for certain
+};
+template <> struct ExpK<1> {
+  static constexpr float C16 = 16.0f, C64 = 64.0f;
+  static constexpr double D0 = 1.0, D1 = 0.0, D2 = 0.0;
+  static constexpr float F0 = 1.0f, F1 = 0.0f;
+  // 2^-150 is the exact midpoint between +0 and 2^-149: ties to even give +0
+  static constexpr float OVF = 128.0f, UNF = -150.0f;
+};
+template <> struct ExpK<2> {
+  static constexpr float C16 = CRM_LOG2_10_X16_F, C64 = CRM_LOG2_10_X64_F;
+  static constexpr double D0 = CRM_LOG2_10_D0, D1 = CRM_LOG2_10_D1, D2 = CRM_LOG2_10_D2;
+  static constexpr float F0 = CRM_LOG2_10_F0, F1 = CRM_LOG2_10_F1;
+  static constexpr float OVF = 38.6f, UNF = -45.5f;
+};
+
+#define CRM_SHIFTER_F 0x1.8p23f
+
+// Special inputs: returns true and the result when x is NaN or saturated.
+template <int KIND> CRM_DEV bool exp_special(float x, float &r) {
+  using K = ExpK<KIND>;
+  r = (x != x) ? qnan_of(x) : (x >= K::OVF ? CRM_INF_F : 0.0f);
+  return (x != x) || x >= K::OVF || x <= K::UNF;
+}
+
+// ------------------------------------------------------------------ plain (FP64) tier
+// t = x log2 b = k + j/16 + g, |g| <= 1/32 + 2^-17.  2^g by its degree-6 Taylor
+// polynomial (remainder <= 2^-51).  y = T[j] (1 + p) with one FMA, then y 2^k.
+// Error budget (relative): table 2^-53, remainder 2^-51, reduction (two FMA roundings of
+// g, constant split) 2^-57, polynomial roundings 2^-57, final FMA 2^-53: below 2^-50.4.
+// eps = 2^-49, i.e. 16 units of y's last place: D = 17.
+constexpr uint32_t EXP_PLAIN_D = 17;
+
+template <int KIND> CRM_DEV double exp_plain_y(float x, const double *T16) {
+  using K = ExpK<KIND>;
+  float sh = fma_(x, K::C16, CRM_SHIFTER_F);
+  int N = (int)(fbits(sh) - fbits(CRM_SHIFTER_F));
+  float nf = sh - CRM_SHIFTER_F;  // N exactly
+  double g;
+  if (KIND == 1) {
+    g = (double)fma_(nf, -0.0625f, x);  // x - N/16, exact (Sterbenz)
+  } else {
+    double xd = (double)x;
+    g = fma_(xd, K::D0, (double)(nf * -0.0625f));
+    g = fma_(xd, K::D1, g);
+  }
+  const double *a = CRM_EXP2_TAYLOR_D;
+  double p = fma_(g, a[6], a[5]);
+  p = fma_(g, p, a[4]);
+  p = fma_(g, p, a[3]);
+  p = fma_(g, p, a[2]);
+  p = fma_(g, p, a[1]);
+  p = p * g;
+  double T = T16[N & 15];
+  double y = fma_(T, p, T);
+  return scale_d(y, N >> 4);
+}
+
+template <int KIND> CRM_DEV float exp_plain(float x, const double *T16, bool &hard) {
+  float r;
+  bool sp = exp_special<KIND>(x, r);
+  double y = exp_plain_y<KIND>(x, T16);
+  hard = !sp && hard_d_to_f(y, EXP_PLAIN_D);
+  return sp ? r : __double2float_rn(y);
+}
+
+// ------------------------------------------------------------------ double-float tier
+// t = th + tl (exact product x*C0 split by FMA, plus x*C1), N = rint(64 th),
+// f = th - N/64 (exact), g = gh + gl = f + tl (Fast2Sum: f is 0 or a multiple of
+// ulp(th) >= |tl|), |g| <= 2^-7 + 2^-16.  2^g - 1 = a1 g + a2 g^2 + a3 g^3 + a4 g^4:
+// a1 g in double-float, the rest in float.  y = T (1 + E) with T = Th + Tl from the
+// 64-entry table, left unnormalised as (s, l), |l| <~ ulp(s).
+// Error budget (relative): Q = g^2(a2 + a3 g + a4 g^2) rounding 2^-38.5; t from x*C1 and
+// the split of C 2^-40.7; a5 g^5 remainder 2^-44.5; table 2^-48; the rest < 2^-50.
+// Total < 2^-38.1; eps = 2^-37, margin 1 - 2^-11 (>= 2 eps 2^24 = 2^-12).
+constexpr float EXP_DF_MARGIN = 1.0f - 0x1p-11f;
+
+struct DFExp {
+  float s, l;
+  int k;
+};
+
+template <int KIND> CRM_DEV DFExp exp_df_core(float x, const float2 *T64) {
+  using K = ExpK<KIND>;
+  float th, tl;
+  if (KIND == 1) {
+    th = x;
+    tl = 0.0f;
+  } else {
+    th = x * K::F0;
+    tl = fma_(x, K::F0, -th);
+    tl = fma_(x, K::F1, tl);
+  }
+  float sh = fma_(th, 64.0f, CRM_SHIFTER_F);
+  int N = (int)(fbits(sh) - fbits(CRM_SHIFTER_F));
+  float nf = sh - CRM_SHIFTER_F;
+  float f = fma_(nf, -0.015625f, th);
+  float gh, gl;
+  if (KIND == 1) {
+    gh = f;
+    gl = 0.0f;
+  } else {
+    gh = f + tl;
+    gl = tl - (gh - f);
+  }
+  // P = a1 g (double-float)
+  float ph = CRM_EXP2_A1_HI_F * gh;
+  float pl = fma_(CRM_EXP2_A1_HI_F, gh, -ph);
+  pl = fma_(CRM_EXP2_A1_LO_F, gh, pl);
+  pl = fma_(CRM_EXP2_A1_HI_F, gl, pl);
+  // Q = g^2 (a2 + a3 g + a4 g^2) in float, plus the cross term 2 a2 gh gl
+  float q = fma_(gh, CRM_EXP2_A4_F, CRM_EXP2_A3_F);
+  q = fma_(gh, q, CRM_EXP2_A2_F);
+  float g2 = gh * gh;
+  float Q = g2 * q;
+  float cross = (2.0f * CRM_EXP2_A2_F * gh) * gl;
+  // E = P + Q
+  float eh = ph + Q;
+  float el = Q - (eh - ph);
+  el = el + (pl + cross);
+  // y = T (1 + E)
+  float2 T = T64[N & 63];
+  float m = T.x * eh;
+  float ml = fma_(T.x, eh, -m);
+  float s = T.x + m;
+  float z = m - (s - T.x);
+  float l = z + (ml + (T.y + fma_(T.x, el, T.y * eh)));
+  return {s, l, N >> 6};
+}
+
+template <int KIND> CRM_DEV float exp_df(float x, const float2 *T64, bool &hard) {
+  float r;
+  bool sp = exp_special<KIND>(x, r);
+  DFExp e = exp_df_core<KIND>(x, T64);
+  // scale by 2^k through the exponent field; s is in [0.98, 2.04]
+  int be = (int)((fbits(e.s) >> 23) & 0xFF) + e.k;
+  bool ovf = be >= 255;
+  bool sub = be <= 0;  // subnormal or zero result: decided by the slow path
+  float y = bitsf(fbits(e.s) + ((uint32_t)e.k << 23));
+  y = ovf ? CRM_INF_F : y;
+  hard = !sp && (sub || hard_df(e.s, e.l, EXP_DF_MARGIN));
+  return sp ? r : y;
+}
+
+// ------------------------------------------------------------------ double-double tier
+// t = x log2 b in double-double (x times a three-double constant), N = rint(16 t),
+// g = t - N/16 (|g| <= 1/32 + tiny), 2^g by its degree-12 Taylor polynomial in
+// double-double Horner form (remainder < 2^-104), times the double-double T[j].
+// Error: 13 Horner steps at <= 8u^2 each plus the table and reduction: < 2^-98.
+constexpr double EXP_DD_EPS = 0x1p-92;
+
+template <int KIND> CRM_DEV Pair<double> exp_dd_core(float x, int &k) {
+  using K = ExpK<KIND>;
+  double xd = (double)x;
+  Pair<double> t;
+  if (KIND == 1) {
+    t = {xd, 0.0};
+  } else {
+    t = two_prod(xd, K::D0);
+    t.lo = fma_(xd, K::D1, t.lo);
+    t.lo = fma_(xd, K::D2, t.lo);
+  }
+  double nd = rint(16.0 * t.hi);
+  int N = (int)nd;
+  double f = fma_(nd, -0.0625, t.hi);  // exact
+  Pair<double> g = two_sum(f, t.lo);
+  const double *c = CRM_EXP2_TAYLOR_DD;
+  Pair<double> p = dd(c[24], c[25]);
+  for (int i = 11; i >= 0; i--) p = dd_add(dd_mul(p, g), dd(c[2 * i], c[2 * i + 1]));
+  int j = N & 15;
+  Pair<double> T = dd(CRM_EXP2_T16_DD[2 * j], CRM_EXP2_T16_DD[2 * j + 1]);
+  k = N >> 4;
+  return dd_mul(T, p);
+}
+
+template <int KIND> CRM_DEV float exp_dd(float x, bool &hard) {
+  int k;
+  Pair<double> y = exp_dd_core<KIND>(x, k);
+  double s = y.hi * pow2d(k), t = y.lo * pow2d(k);  // exact: results stay in double range
+  return round_dd_to_f(s, t, EXP_DD_EPS * fabs(s), hard);
+}
+
+// Slow path used for lanes whose fast-path test failed: FP64 tier, then double-double.
+template <int KIND> CRM_DEV float exp_slow(float x, bool &unresolved) {
+  bool hard;
+  float r = exp_plain<KIND>(x, CRM_EXP2_T16_D, hard);
+  unresolved = false;
+  if (!hard) return r;
+  r = exp_dd<KIND>(x, hard);
+  unresolved = hard;
+  return r;
+}
+
+}  // namespace crm

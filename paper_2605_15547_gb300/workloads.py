@@ -1,0 +1,128 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (host numpy arrays).
+
+This module holds input recipes only -- no arithmetic of the evaluated functions.  Both
+the tests (GPU path vs oracle) and bench.py draw their inputs from here.
+
+Recipes (the paper measures on synthetic uniform inputs: Sec. III.A-D):
+* ``uniform(lo, hi)``: a real uniform in [lo, hi] (float64 PCG64), rounded to binary32;
+* ``loguniform(emin, emax, signed)``: magnitude 2^U(emin, emax), random sign if signed;
+* ``domain_bits(func)``: uniform random bit patterns restricted to the function's domain
+  of finite, non-trivially-saturated inputs (rejection sampling), plus 1% specials;
+* ``expf_mixed``: 90% uniform in [-103.98, 88.73] and 10% from the specials pool;
+* ``specials(func)``: zeros, infinities, quiet and signalling NaNs, subnormals, +-FLT_MAX,
+  +-FLT_MIN and a few ulps around the function's overflow/underflow boundaries.
+Seeds follow seed = 0xC0DE0000 + 256 * config + func_id.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+FUNCS = [
+    "expf", "exp2f", "exp10f", "expm1f", "logf", "log2f", "log10f", "log1pf", "sinf",
+    "cosf", "sincosf", "tanf", "asinf", "acosf", "atanf", "sinhf", "coshf", "tanhf",
+    "rsqrtf", "exp2", "log",
+]
+F32_FUNCS = FUNCS[:19]
+
+# Inputs whose results are finite and not trivially saturated (open intervals).
+DOMAIN_F32 = {
+    "expf": (-103.98, 88.73), "exp2f": (-150.0, 128.0), "exp10f": (-45.16, 38.54),
+    "expm1f": (-17.4, 88.73), "logf": (0.0, np.inf), "log2f": (0.0, np.inf),
+    "log10f": (0.0, np.inf), "log1pf": (-1.0, np.inf), "sinf": (-np.inf, np.inf),
+    "cosf": (-np.inf, np.inf), "sincosf": (-np.inf, np.inf), "tanf": (-np.inf, np.inf),
+    "asinf": (-1.0, 1.0), "acosf": (-1.0, 1.0), "atanf": (-np.inf, np.inf),
+    "sinhf": (-89.42, 89.42), "coshf": (-89.42, 89.42), "tanhf": (-9.02, 9.02),
+    "rsqrtf": (0.0, np.inf),
+}
+# boundary inputs (bit patterns) around which a few ulps are added to the specials
+BOUNDARY_F32 = {
+    "expf": [0x42B17217, 0xC2CFF1B4, 0xC2AEAC4F], "exp2f": [0x42FFFFFF, 0xC3160000, 0xC2FC0000],
+    "exp10f": [0x421A209A, 0xC2349E35], "expm1f": [0x42B17217, 0xC18AA122],
+    "sinhf": [0x42B2D4FC], "coshf": [0x42B2D4FC], "tanhf": [0x41102CB3],
+    "log1pf": [0xBF7FFFFF], "asinf": [0x3F7FFFFF], "acosf": [0x3F7FFFFF, 0xBF7FFFFF],
+}
+
+
+def seed_for(config: int, func) -> int:
+    fid = FUNCS.index(func) if isinstance(func, str) else int(func)
+    return 0xC0DE0000 + 256 * config + fid
+
+
+def rng_for(config: int, func, salt: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed_for(config, func) + 0x100000000 * salt))
+
+
+def specials_f32(func: str, rng: np.random.Generator) -> np.ndarray:
+    base = [0x00000000, 0x80000000, 0x7F800000, 0xFF800000, 0x7FC00000, 0xFFC00001,
+            0x7F800001, 0x7FA00000, 0x7F7FFFFF, 0xFF7FFFFF, 0x00800000, 0x80800000,
+            0x3F800000, 0xBF800000, 0x00000001, 0x80000001, 0x007FFFFF, 0x807FFFFF]
+    sub = rng.integers(1, 0x00800000, 16, dtype=np.uint64).astype(np.uint32)
+    sub[8:] |= 0x80000000
+    out = [np.array(base, dtype=np.uint32), sub]
+    for b in BOUNDARY_F32.get(func, []):
+        out.append((np.arange(-4, 5, dtype=np.int64) + b).astype(np.uint32))
+        out.append((np.arange(-4, 5, dtype=np.int64) + (b ^ 0x80000000)).astype(np.uint32))
+    return np.concatenate(out)
+
+
+def _in_domain(bits: np.ndarray, func: str) -> np.ndarray:
+    lo, hi = DOMAIN_F32[func]
+    v = bits.view(np.float32)
+    with np.errstate(invalid="ignore"):
+        return np.isfinite(v) & (v > lo) & (v < hi)
+
+
+def domain_bits(func: str, n: int, rng: np.random.Generator, special_frac: float = 0.01) -> np.ndarray:
+    """Uniform random bit patterns inside the function's domain, plus specials."""
+    ns = int(n * special_frac)
+    nd = n - ns
+    parts, got = [], 0
+    while got < nd:
+        b = rng.integers(0, 2**32, int((nd - got) * 2.2) + 1024, dtype=np.uint64).astype(np.uint32)
+        b = b[_in_domain(b, func)]
+        parts.append(b[: nd - got])
+        got += parts[-1].size
+    sp = specials_f32(func, rng)
+    out = np.concatenate(parts + [np.resize(sp, ns)])
+    rng.shuffle(out)
+    return out
+
+
+def uniform(lo: float, hi: float, n: int, rng: np.random.Generator) -> np.ndarray:
+    return rng.uniform(lo, hi, n).astype(np.float32)
+
+
+def loguniform(emin: float, emax: float, n: int, rng: np.random.Generator, signed: bool) -> np.ndarray:
+    mag = np.exp2(rng.uniform(emin, emax, n))
+    if signed:
+        mag = np.where(rng.integers(0, 2, n) == 1, -mag, mag)
+    with np.errstate(over="ignore"):
+        return mag.astype(np.float32)
+
+
+def expf_mixed(n: int, rng: np.random.Generator) -> np.ndarray:
+    """90% uniform in [-103.98, 88.73], 10% drawn round-robin from the specials pool."""
+    nu = int(round(n * 0.9))
+    u = uniform(-103.98, 88.73, nu, rng).view(np.uint32)
+    sp = specials_f32("expf", rng)
+    out = np.concatenate([u, np.resize(sp, n - nu)])
+    rng.shuffle(out)
+    return out.view(np.float32)
+
+
+def sinf_with_large(n: int, rng: np.random.Generator, frac: float = 0.05) -> np.ndarray:
+    """U[-10, 10] with `frac` of the entries replaced by |x| log-uniform in (2^20, 2^127]."""
+    x = uniform(-10.0, 10.0, n, rng)
+    k = int(n * frac)
+    idx = rng.choice(n, k, replace=False)
+    x[idx] = loguniform(20.0, 127.0, k, rng, signed=True)
+    return x
+
+
+def f64_uniform(lo: float, hi: float, n: int, rng: np.random.Generator) -> np.ndarray:
+    return rng.uniform(lo, hi, n)
+
+
+def f64_positive_bits(n: int, rng: np.random.Generator) -> np.ndarray:
+    b = rng.integers(1, 0x7FF0000000000000, n, dtype=np.uint64)
+    return b.view(np.float64)

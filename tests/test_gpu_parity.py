@@ -1,0 +1,143 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, bit for bit.
+
+Correct rounding has one right answer per input, so every comparison is exact
+(0 mismatches, 0 ulp), including signed zeros, infinities and NaN bit patterns.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2605_15547_gb300 as crm  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+from paper_2605_15547_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+F32_DONE = ["expf", "exp2f", "exp10f"]
+FORMS = ["plain", "df"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    crm.set_force_slow(False)
+    yield
+    crm.set_force_slow(False)
+
+
+def run_gpu(func, xbits, form, out_offset=0, in_offset=0):
+    """Evaluate on the GPU; returns result bits (shape (2, n) for sincosf)."""
+    n = xbits.size
+    buf = torch.zeros(n + in_offset + 8, dtype=torch.float32, device="cuda")
+    buf[in_offset:in_offset + n] = torch.from_numpy(xbits.view(np.float32)).cuda()
+    x = buf[in_offset:in_offset + n]
+    rows = 2 if func == "sincosf" else 1
+    obuf = torch.full((rows * n + out_offset + 8,), float("nan"), dtype=torch.float32, device="cuda")
+    out = obuf[out_offset:out_offset + rows * n]
+    crm.eval_into(func, x, out, form=form)
+    torch.cuda.synchronize()
+    y = out.cpu().numpy().view(np.uint32)
+    return y.reshape(2, n) if rows == 2 else y
+
+
+def assert_same(func, xbits, got, ref):
+    bad = np.nonzero((got != ref).reshape(-1))[0]
+    if bad.size:
+        flat_x = np.tile(xbits, 2) if got.ndim == 2 else xbits
+        ex = [(hex(int(flat_x[i])), hex(int(got.reshape(-1)[i])), hex(int(ref.reshape(-1)[i])))
+              for i in bad[:8]]
+        pytest.fail(f"{func}: {bad.size} mismatches (x, got, want): {ex}")
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("func", F32_DONE)
+def test_domain_sample(func, form):
+    rng = W.rng_for(2, func, salt=7)
+    x = W.domain_bits(func, (1 << 17) + 37, rng)
+    got = run_gpu(func, x, form)
+    assert_same(func, x, got, O.eval_bits(func, x))
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("func", F32_DONE)
+def test_moderate_range(func, form):
+    rng = W.rng_for(2, func, salt=8)
+    x = np.concatenate([W.uniform(-10, 10, 50000, rng), W.uniform(-1, 1, 30000, rng),
+                        W.loguniform(-126, 7, 30000, rng, signed=True)]).view(np.uint32)
+    got = run_gpu(func, x, form)
+    assert_same(func, x, got, O.eval_bits(func, x))
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("func", F32_DONE)
+def test_specials(func, form):
+    x = W.specials_f32(func, W.rng_for(0, func))
+    got = run_gpu(func, x, form)
+    assert_same(func, x, got, O.eval_bits(func, x))
+
+
+@pytest.mark.parametrize("func", F32_DONE)
+def test_forced_slow_path_is_identical(func):
+    """Every lane through the queue and the exact slow path: same bits."""
+    rng = W.rng_for(2, func, salt=9)
+    x = W.domain_bits(func, 20011, rng)
+    ref = O.eval_bits(func, x)
+    crm.stats_reset()
+    crm.set_force_slow(True)
+    try:
+        for form in FORMS:
+            assert_same(func, x, run_gpu(func, x, form), ref)
+    finally:
+        crm.set_force_slow(False)
+    st = crm.stats()
+    assert st["hard_total"] >= 2 * x.size
+    assert st["unresolved_total"] == 0
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 4, 5, 7, 8, 31, 33, 255, 257, 1023, 4097])
+@pytest.mark.parametrize("in_off,out_off", [(0, 0), (1, 1), (1, 2), (3, 0), (2, 2)])
+def test_sizes_and_alignment(n, in_off, out_off):
+    rng = W.rng_for(2, "expf", salt=n)
+    x = W.domain_bits("expf", n, rng) if n else np.zeros(0, np.uint32)
+    for form in FORMS:
+        got = run_gpu("expf", x, form, out_offset=out_off, in_offset=in_off)
+        assert_same("expf", x, got, O.eval_bits("expf", x))
+
+
+def test_in_place():
+    rng = W.rng_for(2, "exp2f", salt=3)
+    x = W.domain_bits("exp2f", 100003, rng)
+    ref = O.eval_bits("exp2f", x)
+    for form in FORMS:
+        for force in (False, True):
+            crm.set_force_slow(force)
+            t = torch.from_numpy(x.view(np.float32).copy()).cuda()
+            crm.eval_into("exp2f", t, t, form=form)
+            torch.cuda.synchronize()
+            assert_same("exp2f", x, t.cpu().numpy().view(np.uint32), ref)
+    crm.set_force_slow(False)
+
+
+def test_config1_expf_mixed_plain_full():
+    """expf, 2^20 inputs: 90% uniform in [-103.98, 88.73], 10% specials; plain form; all
+    outputs compared."""
+    x = W.expf_mixed(1 << 20, W.rng_for(1, "expf")).view(np.uint32)
+    got = run_gpu("expf", x, "plain")
+    assert_same("expf", x, got, O.eval_bits("expf", x))
+    got = run_gpu("expf", x, "df")
+    assert_same("expf", x, got, O.eval_bits("expf", x))
+
+
+def test_exp2f_exact_powers_and_midpoint():
+    ks = np.arange(-151, 129).astype(np.float32)
+    x = ks.view(np.uint32)
+    for form in FORMS:
+        assert_same("exp2f", x, run_gpu("exp2f", x, form), O.eval_bits("exp2f", x))
+
+
+def test_no_unresolved_lanes():
+    assert crm.stats()["unresolved_total"] == 0

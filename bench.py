@@ -108,18 +108,22 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- workloads
 
-def build_workload(name: str, scale: int):
-    """Returns a list of (func, host float32 array, config tag) and a config dict."""
+def build_workload(name: str, scale: int, only=None):
+    """Returns a list of (func, host float32 array) and a config dict."""
     items = []
     if name == "all19_2p26":
         n = (1 << 26) >> scale
         for f in W.F32_FUNCS:
+            if only and f not in only:
+                continue
             items.append((f, W.domain_bits(f, n, W.rng_for(2, f)).view(np.float32)))
         cfg = {"workload": f"all 19 binary32 functions, 2^{26 - scale} inputs each, domain bit patterns + 1% specials",
                "elems_per_func": n}
     elif name == "precision":
         n = (1 << 28) >> scale
         for f in ("expf", "logf", "sinf", "tanhf", "rsqrtf"):
+            if only and f not in only:
+                continue
             rng = W.rng_for(3, f)
             if f in ("logf", "rsqrtf"):
                 items.append((f, W.loguniform(-126, 127, n, rng, signed=False)))
@@ -148,7 +152,7 @@ def run_reference(args):
         return 0
     from oracle import oracle as O
     O.build()
-    items, cfg = build_workload(args.workload, args.scale)
+    items, cfg = build_workload(args.workload, args.scale, set(args.funcs.split(",")) if args.funcs else None)
     sample = args.ref_sample
     cores = os.cpu_count() or 1
     # warm-up (constants, thread pool)
@@ -215,10 +219,7 @@ def main():
     import __graft_entry__ as g
     g.build()
 
-    items, cfg = build_workload(args.workload, args.scale)
-    if args.funcs:
-        keep = set(args.funcs.split(","))
-        items = [it for it in items if it[0] in keep]
+    items, cfg = build_workload(args.workload, args.scale, set(args.funcs.split(",")) if args.funcs else None)
     # drop functions the library does not provide yet (reported in the config)
     avail = []
     for f, x in items:

@@ -19,6 +19,9 @@
 
 namespace crm {
 
+// 1.5 * 2^23: adding it rounds a float of magnitude < 2^22 to an integer in its low bits
+#define CRM_SHIFTER_F 0x1.8p23f
+
 // ------------------------------------------------------------------ bit helpers
 CRM_DEV uint32_t fbits(float x) { return __float_as_uint(x); }
 CRM_DEV float bitsf(uint32_t b) { return __uint_as_float(b); }
@@ -27,6 +30,7 @@ CRM_DEV double bitsd(uint64_t b) { return __longlong_as_double((long long)b); }
 
 // ------------------------------------------------------------------ error-free transforms
 template <class T> struct Pair { T hi, lo; };
+template <class T> CRM_DEV Pair<T> operator-(Pair<T> a) { return {-a.hi, -a.lo}; }
 
 CRM_DEV float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 CRM_DEV double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -113,17 +117,17 @@ CRM_DEV bool hard_d_to_f(double y, uint32_t D) {
   return (t - h + D) <= 2ull * D;
 }
 
-// Double-float tier: y = s + l with |l| < ulp(s), approximating v with
-// |v - y| <= eps |y| where eps <= 2^-26 is folded into the caller's margin.  RN_f32(v)
-// is s unless v may lie at or beyond the midpoint next to s: |l| + eps|y| >= half the
-// gap to the neighbour (a quarter ulp below a power of two).  `margin` is 1 - 2^-m,
-// exact, with 2^-m >= 2 * eps * 2^24.  Valid for s normal; callers route subnormal
-// results elsewhere.
-CRM_DEV bool hard_df(float s, float l, float margin) {
-  uint32_t S = fbits(s) & 0x7FFFFFFFu;
-  uint32_t hb = (S & 0x7F800000u) - ((S & 0x007FFFFFu) ? (24u << 23) : (25u << 23));
-  float h = bitsf(hb) * margin;
-  return !(fabsf(l) < h);
+// Double-float tier: y = s + l (s = RN(y), so |l| <= ulp(s)/2) approximates v with
+// |v - y| <= eps_true |y|.  RN_f32(v) == s unless a midpoint next to s lies within
+// |l| + eps_true |s| of s.  The test lets the hardware's round-to-nearest measure the
+// distance to that midpoint, including the quarter-ulp gap below a power of two:
+// t = l + copysign(|s| * E, l), hard iff RN(s + t) != s.  E = 2^-36 covers an
+// eps_true <= 2^-37 plus the rounding of t (<= 2^-48 |s|), so a passing lane satisfies
+// |l| + eps_true |s| < distance to the midpoint, strictly.  Valid for normal s.
+CRM_DEV bool hard_df(float s, float l) {
+  float e = fabsf(s) * 0x1p-36f;
+  float t = l + bitsf(fbits(e) | (fbits(l) & 0x80000000u));
+  return (s + t) != s;
 }
 
 // Slow tier: y = s + t (double-double, |t| <= ulp(s)/2) approximates v with
@@ -150,6 +154,13 @@ CRM_DEV float round_dd_to_f(double s, double t, double e, bool &hard) {
 }
 
 // ------------------------------------------------------------------ misc
+// Block-cooperative copy of a table into shared memory (bytes a multiple of 4).
+CRM_DEV void copy_tab(void *dst, const void *src, int bytes) {
+  const uint32_t *s = (const uint32_t *)src;
+  uint32_t *d = (uint32_t *)dst;
+  for (int i = threadIdx.x; i < bytes / 4; i += blockDim.x) d[i] = s[i];
+}
+
 CRM_DEV float qnan_of(float x) { return bitsf(fbits(x) | 0x00400000u); }
 CRM_DEV double qnan_of(double x) { return bitsd(dbits(x) | 0x0008000000000000ull); }
 #define CRM_QNAN_F (__uint_as_float(0x7FC00000u))

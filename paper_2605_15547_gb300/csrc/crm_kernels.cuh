@@ -54,43 +54,52 @@ template <class T> CRM_DEV T x_from_bits(uint64_t b);
 template <> CRM_DEV float x_from_bits<float>(uint64_t b) { return bitsf((uint32_t)b); }
 template <> CRM_DEV double x_from_bits<double>(uint64_t b) { return bitsd(b); }
 
-// Reserve queue slots for the lanes with h set (whole warp calls this, warp-uniform).
-// Returns true for a lane whose slot is beyond the capacity (must finish inline).
-CRM_DEV bool push_hard(bool h, uint64_t idx, uint64_t xb, const KArgs &a) {
-  unsigned m = __ballot_sync(0xFFFFFFFFu, h);
-  if (!m) return false;
-  int lane = threadIdx.x & 31;
-  int leader = __ffs(m) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(&a.hdr->count, (unsigned long long)__popc(m));
-  base = __shfl_sync(0xFFFFFFFFu, base, leader);
-  if (!h) return false;
-  unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
-  if (pos < a.cap) {
-    crm_queue_entry e;
-    e.idx = ((uint64_t)a.desc << 40) | idx;
-    e.x = xb;
-    a.q[pos] = e;
-    return false;
+// Reserve queue slots for up to W lanes per thread with one atomicAdd per warp (the
+// whole warp calls this; hm holds the thread's hard bits).  Lanes beyond the queue
+// capacity are returned in the result mask and must be finished inline.
+template <int W>
+CRM_DEV unsigned push_hard(unsigned hm, const uint64_t *idx, const uint64_t *xb, const KArgs &a) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned m[W];
+  unsigned total = 0;
+#pragma unroll
+  for (int j = 0; j < W; j++) {
+    m[j] = __ballot_sync(0xFFFFFFFFu, (hm >> j) & 1u);
+    total += __popc(m[j]);
   }
-  return true;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&a.hdr->count, (unsigned long long)total);
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  unsigned over = 0;
+#pragma unroll
+  for (int j = 0; j < W; j++) {
+    if ((hm >> j) & 1u) {
+      unsigned long long pos = base + __popc(m[j] & lt);
+      if (pos < a.cap) {
+        crm_queue_entry e;
+        e.idx = ((uint64_t)a.desc << 40) | idx[j];
+        e.x = xb[j];
+        a.q[pos] = e;
+      } else {
+        over |= 1u << j;
+      }
+    }
+    base += __popc(m[j]);
+  }
+  return over;
 }
 
 // Fn interface (one struct per function, see the k_*.cu files):
 //   using T = float | double;  static constexpr int NOUT = 1 | 2;
-//   template <int FORM> static constexpr int tab_bytes();
-//   template <int FORM> CRM_DEV static const void *tab();
+//   template <int FORM> static constexpr int tab_bytes();   (shared memory bytes)
+//   template <int FORM> CRM_DEV static void load(unsigned char *sm);  (fill it)
 //   template <int FORM> CRM_DEV static void eval(T x, const void *sm, T *y, bool &hard);
 //   CRM_DEV static void slow(T x, T *y, bool &unresolved);
 
 template <class Fn, int FORM>
 CRM_DEV void load_tab(unsigned char *sm) {
-  constexpr int B = Fn::template tab_bytes<FORM>();
-  if (B > 0) {
-    const uint32_t *src = (const uint32_t *)Fn::template tab<FORM>();
-    uint32_t *dst = (uint32_t *)sm;
-    for (int i = threadIdx.x; i < B / 4; i += blockDim.x) dst[i] = src[i];
-  }
+  Fn::template load<FORM>(sm);
   __syncthreads();
 }
 
@@ -140,21 +149,28 @@ __global__ void __launch_bounds__(KBLOCK) k_main(KArgs a) {
         T y[2];
         bool h;
         Fn::template eval<FORM>(vget(xv[u], j), sm, y, h);
-        h = (h || a.force_hard) && act;
         hm |= (unsigned)h << j;
         vset(y0, j, y[0]);
         if (Fn::NOUT == 2) vset(y1, j, y[1]);
       }
+      hm = a.force_hard ? (1u << W) - 1u : hm;
+      hm = act ? hm : 0u;
       if (act) {
         st_stream(out4 + v, y0);
         if (Fn::NOUT == 2) st_stream(out4b + v, y1);
       }
       if (__any_sync(0xFFFFFFFFu, hm != 0)) {
+        uint64_t ii[W], xb[W];
 #pragma unroll
         for (int j = 0; j < W; j++) {
-          uint64_t i = a.head + v * W + j;
-          T x = vget(xv[u], j);
-          if (push_hard((hm >> j) & 1, i, xbits_of(x), a)) slow_store<Fn>(x, i, a);
+          ii[j] = a.head + v * W + j;
+          xb[j] = xbits_of(vget(xv[u], j));
+        }
+        unsigned over = push_hard<W>(hm, ii, xb, a);
+        if (over) {
+#pragma unroll
+          for (int j = 0; j < W; j++)
+            if ((over >> j) & 1u) slow_store<Fn>(vget(xv[u], j), ii[j], a);
         }
       }
     }
@@ -178,8 +194,10 @@ __global__ void __launch_bounds__(KBLOCK) k_main(KArgs a) {
       out[i] = y[0];
       if (Fn::NOUT == 2) out[a.n + i] = y[1];
     }
-    if (__any_sync(0xFFFFFFFFu, h))
-      if (push_hard(h, i, xbits_of(x), a)) slow_store<Fn>(x, i, a);
+    if (__any_sync(0xFFFFFFFFu, h)) {
+      uint64_t xb = xbits_of(x);
+      if (push_hard<1>(h ? 1u : 0u, &i, &xb, a)) slow_store<Fn>(x, i, a);
+    }
   }
 }
 

@@ -52,5 +52,9 @@ void set_entry(FuncEntry &e) {
 
 // one per family translation unit
 void register_exp(FuncEntry *table);
+void register_log(FuncEntry *table);
+void register_hyp(FuncEntry *table);
+void register_trig(FuncEntry *table);
+void register_atrig(FuncEntry *table);
 
 }  // namespace crm

@@ -25,6 +25,10 @@ static thread_local int g_last_cuda = 0;
 static void init_table() {
   memset(g_table, 0, sizeof(g_table));
   register_exp(g_table);
+  register_log(g_table);
+  register_hyp(g_table);
+  register_trig(g_table);
+  register_atrig(g_table);
   const char *f = getenv("CRM_FORM");
   if (f) {
     if (!strcmp(f, "plain")) g_default_form = CRM_FORM_PLAIN_FP64;
@@ -218,6 +222,74 @@ static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cu
   return CRM_OK;
 }
 
+// ------------------------------------------------------------------ host-buffer path
+// Chunks of the host array go through two internal streams: while one stream computes a
+// chunk, the copy engines move the neighbouring chunks in and out (H2D and D2H overlap
+// with compute and with each other).
+struct HostStage {
+  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaEvent_t ev = nullptr;
+  void *din[2] = {nullptr, nullptr}, *dout[2] = {nullptr, nullptr};
+  size_t bytes = 0;  // per input buffer
+};
+static std::map<int, HostStage> g_stage;
+static const uint64_t kChunkElems = 1ull << 22;
+
+static int host_pipeline(int func, int form, const void *in, void *out, uint64_t n, cudaStream_t user) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const FuncEntry &fe = g_table[func];
+  const size_t es = fe.dtype ? 8 : 4;
+  const int nout = fe.nout;
+  HostStage *hs;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    hs = &g_stage[dev];
+  }
+  if (!hs->st[0]) {
+    for (int i = 0; i < 2; i++) {
+      if ((e = cudaStreamCreateWithFlags(&hs->st[i], cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e);
+    }
+    if ((e = cudaEventCreateWithFlags(&hs->ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e);
+  }
+  size_t need = kChunkElems * 8;
+  if (hs->bytes < need) {
+    for (int i = 0; i < 2; i++) {
+      if (hs->din[i]) cudaFree(hs->din[i]);
+      if (hs->dout[i]) cudaFree(hs->dout[i]);
+      hs->din[i] = hs->dout[i] = nullptr;
+      if (cudaMalloc(&hs->din[i], need) != cudaSuccess || cudaMalloc(&hs->dout[i], 2 * need) != cudaSuccess)
+        return CRM_ERR_NOMEM;
+    }
+    hs->bytes = need;
+  }
+  // order after the caller's prior work on `user`
+  if ((e = cudaEventRecord(hs->ev, user)) != cudaSuccess) return cuda_fail(e);
+  for (int i = 0; i < 2; i++)
+    if ((e = cudaStreamWaitEvent(hs->st[i], hs->ev, 0)) != cudaSuccess) return cuda_fail(e);
+  const char *hin = (const char *)in;
+  char *hout = (char *)out;
+  uint64_t c = 0;
+  for (uint64_t off = 0; off < n; off += kChunkElems, c++) {
+    uint64_t m = n - off < kChunkElems ? n - off : kChunkElems;
+    int b = (int)(c & 1);
+    cudaStream_t s = hs->st[b];
+    if ((e = cudaMemcpyAsync(hs->din[b], hin + off * es, m * es, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e);
+    int st = enqueue(func, form, hs->din[b], hs->dout[b], m, s, 0);
+    if (st) return st;
+    for (int r = 0; r < nout; r++) {
+      if ((e = cudaMemcpyAsync(hout + (r * n + off) * es, (char *)hs->dout[b] + r * m * es, m * es,
+                               cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e);
+    }
+  }
+  for (int i = 0; i < 2; i++)
+    if ((e = cudaStreamSynchronize(hs->st[i])) != cudaSuccess) return cuda_fail(e);
+  return CRM_OK;
+}
+
 }  // namespace crm
 
 using namespace crm;
@@ -291,8 +363,15 @@ int crm_stats_reset(void *stream) {
 }
 
 int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, uint64_t n, void *stream) {
-  (void)func_id; (void)dtype; (void)form; (void)in; (void)out; (void)n; (void)stream;
-  return CRM_ERR_FORM;
+  ensure_init();
+  if (func_id < 0 || func_id >= CRM_NUM_FUNCS) return CRM_ERR_FUNC;
+  int want = func_id >= CRM_EXP2 ? CRM_F64 : CRM_F32;
+  if (dtype != want) return CRM_ERR_DTYPE;
+  if (form < CRM_FORM_AUTO || form > CRM_FORM_DF32) return CRM_ERR_FORM;
+  if (resolve_form(g_table[func_id], form) < 0) return CRM_ERR_FORM;
+  if (n == 0) return CRM_OK;
+  if (!in || !out) return CRM_ERR_NULL;
+  return host_pipeline(func_id, form, in, out, n, (cudaStream_t)stream);
 }
 
 int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {

@@ -1,0 +1,153 @@
+// fam_atrig.cuh -- atanf, asinf, acosf through one core, atan(a/b) for a, b >= 0.
+//
+//   atan x = sign(x) atan(|x| / 1),
+//   asin x = sign(x) atan(|x| / s),           s = sqrt((1 - x)(1 + x)),
+//   acos x = atan(s / x) (x > 0),  pi - atan(s / |x|) (x < 0),
+// so that small results (atan and asin near 0, acos near 1) come out of the core with
+// full relative accuracy.  The core swaps a and b when a > b (atan(a/b) = pi/2 -
+// atan(b/a)), picks c_j = j/16 nearest to p/q (p <= q), and uses
+//   atan(p/q) = atan(c_j) + atan(t),   t = (p - c_j q) / (q + c_j p),   |t| <= 1/32,
+// with a 17-entry table of atan(j/16) (the paper's atanf uses a 0.125 KB table, Table I)
+// and an odd polynomial for atan(t).  One division per evaluation.
+#pragma once
+#include "crm_common.cuh"
+#include "crm_tables.h"
+
+namespace crm {
+
+enum { AT_ATAN = 0, AT_ASIN = 1, AT_ACOS = 2 };
+
+// ------------------------------------------------------------------ plain (FP64) tier
+// t: exact numerator when c_j = 0 (then t = p/q to 2^-53), else absolute error <= 2^-52
+// (rounding of s and of the division); polynomial to degree 9 (remainder t^11/11 <=
+// 2^-58.5); table 2^-53; the sum atan(c_j) + atan(t) is at least half of atan(c_j), so
+// errors grow at most twice.  atan: eps = 2^-47 (D = 65); asin, acos: eps = 2^-46 (129).
+CRM_DEV double atan_ratio_d(double a, double b, const double *AT) {
+  bool sw = a > b;
+  double p = sw ? b : a, q = sw ? a : b;
+  float rf = __fdividef(__double2float_rn(p), __double2float_rn(q));  // only picks j
+  int j = __float2int_rn(rf * 16.0f);
+  j = j < 0 ? 0 : (j > 16 ? 16 : j);
+  double c = (double)j * 0.0625;
+  double t = fma_(-c, q, p) / fma_(c, p, q);
+  double t2 = t * t;
+  const double *k = CRM_ATAN_TAYLOR_D;
+  double at = fma_(t2, fma_(t2, fma_(t2, fma_(t2, k[4], k[3]), k[2]), k[1]), k[0]) * t;
+  double r = AT[j] + at;
+  return sw ? (CRM_PIO2_D_HI - r) + CRM_PIO2_D_LO : r;
+}
+
+template <int KIND> CRM_DEV bool atrig_special(float x, float &r) {
+  bool nan = x != x;
+  float ax = fabsf(x);
+  if (KIND == AT_ATAN) {
+    r = nan ? qnan_of(x) : x;  // +-0 -> +-0 (infinities are not special: atan(1/0))
+    return nan || x == 0.0f;
+  }
+  if (KIND == AT_ASIN) {
+    r = nan ? qnan_of(x) : (ax > 1.0f ? CRM_QNAN_F : x);
+    return nan || ax > 1.0f || x == 0.0f;
+  }
+  r = nan ? qnan_of(x) : (ax > 1.0f ? CRM_QNAN_F : 0.0f);  // acos(1) = +0
+  return nan || ax > 1.0f || x == 1.0f;
+}
+
+// (a, b) for atan(a/b) and whether to take pi - result (acos of a negative x)
+template <int KIND> CRM_DEV void atrig_args(float x, double &a, double &b, bool &flip) {
+  double ax = fabs((double)x);
+  flip = false;
+  if (KIND == AT_ATAN) {
+    bool inf = fabsf(x) == CRM_INF_F;
+    a = inf ? 1.0 : ax;
+    b = inf ? 0.0 : 1.0;
+    return;
+  }
+  double s = sqrt((1.0 - ax) * (1.0 + ax));  // 1 - x^2 is exact in binary64
+  if (KIND == AT_ASIN) {
+    a = ax;
+    b = s;
+  } else {
+    a = s;
+    b = ax;
+    flip = x < 0.0f;
+  }
+}
+
+template <int KIND> CRM_DEV float atrig_plain(float x, const double *AT, bool &hard) {
+  float rsp;
+  bool sp = atrig_special<KIND>(x, rsp);
+  double a, b;
+  bool flip;
+  atrig_args<KIND>(sp ? 0.5f : x, a, b, flip);
+  double r = atan_ratio_d(a, b, AT);
+  if (KIND == AT_ACOS) r = flip ? (CRM_PI_D_HI - r) + CRM_PI_D_LO : r;
+  if (KIND != AT_ACOS && x < 0.0f) r = -r;
+  hard = !sp && hard_d_to_f(r, KIND == AT_ATAN ? 65u : 129u);
+  return sp ? rsp : __double2float_rn(r);
+}
+
+// ------------------------------------------------------------------ double-double tier
+// s by one Newton step in double-double, t by a double-double division, atan(t) to
+// degree 25 (remainder < 2^-130), double-double table and pi/2.  Error < 2^-96.
+constexpr double ATRIG_DD_EPS = 0x1p-88;
+
+CRM_DEV Pair<double> dd_sqrt(Pair<double> a) {
+  if (a.hi <= 0.0) return {0.0, 0.0};
+  double s0 = sqrt(a.hi);
+  Pair<double> sq = two_prod(s0, s0);
+  Pair<double> r = dd_add(a, dd_neg(sq));
+  double corr = r.hi / (2.0 * s0);
+  return fast_two_sum(s0, corr);
+}
+
+CRM_DEV Pair<double> atan_ratio_dd(Pair<double> a, Pair<double> b) {
+  bool sw = a.hi > b.hi;
+  Pair<double> p = sw ? b : a, q = sw ? a : b;
+  double rq = q.hi == 0.0 ? 0.0 : p.hi / q.hi;
+  int j = (int)rint(rq * 16.0);
+  j = j < 0 ? 0 : (j > 16 ? 16 : j);
+  double c = (double)j * 0.0625;
+  Pair<double> num = dd_add(p, dd_mul_d(q, -c));
+  Pair<double> den = dd_add(q, dd_mul_d(p, c));
+  Pair<double> t = dd_div(num, den);
+  Pair<double> t2 = dd_sqr(t);
+  const double *k = CRM_ATAN_TAYLOR_DD;
+  Pair<double> at = dd(k[2 * 13], k[2 * 13 + 1]);
+  for (int i = 12; i >= 0; i--) at = dd_add(dd_mul(at, t2), dd(k[2 * i], k[2 * i + 1]));
+  at = dd_mul(at, t);
+  Pair<double> r = dd_add(dd(CRM_ATAN_T17_DD[2 * j], CRM_ATAN_T17_DD[2 * j + 1]), at);
+  return sw ? dd_add(dd(CRM_PIO2_D_HI, CRM_PIO2_D_LO), dd_neg(r)) : r;
+}
+
+template <int KIND> CRM_DEV float atrig_slow(float x, bool &unresolved) {
+  bool hard;
+  float r = atrig_plain<KIND>(x, CRM_ATAN_T17_D, hard);
+  unresolved = false;
+  if (!hard) return r;
+  double ax = fabs((double)x);
+  Pair<double> a, b;
+  bool flip = false;
+  if (KIND == AT_ATAN) {
+    bool inf = fabsf(x) == CRM_INF_F;
+    a = {inf ? 1.0 : ax, 0.0};
+    b = {inf ? 0.0 : 1.0, 0.0};
+  } else {
+    Pair<double> s = dd_sqrt(dd((1.0 - ax) * (1.0 + ax), 0.0));
+    if (KIND == AT_ASIN) {
+      a = {ax, 0.0};
+      b = s;
+    } else {
+      a = s;
+      b = {ax, 0.0};
+      flip = x < 0.0f;
+    }
+  }
+  Pair<double> y = atan_ratio_dd(a, b);
+  if (flip) y = dd_add(dd(CRM_PI_D_HI, CRM_PI_D_LO), dd_neg(y));
+  if (KIND != AT_ACOS && x < 0.0f) y = dd_neg(y);
+  r = round_dd_to_f(y.hi, y.lo, ATRIG_DD_EPS * fabs(y.hi), hard);
+  unresolved = hard;
+  return r;
+}
+
+}  // namespace crm

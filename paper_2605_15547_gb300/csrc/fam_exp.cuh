@@ -18,6 +18,7 @@ template <> struct ExpK<0> {
   static constexpr double D0 = CRM_LOG2E_D0, D1 = CRM_LOG2E_D1, D2 = CRM_LOG2E_D2;
   static constexpr float F0 = CRM_LOG2E_F0, F1 = CRM_LOG2E_F1;
   static constexpr float OVF = 89.0f, UNF = -104.0f;  // beyond: +inf / +0 for certain
+  static constexpr float XOVF = CRM_EXPF_X_OVF, XZERO = CRM_EXPF_X_ZERO, XSUB = CRM_EXPF_X_SUB;
 };
 template <> struct ExpK<1> {
   static constexpr float C16 = 16.0f, C64 = 64.0f;
@@ -25,15 +26,17 @@ template <> struct ExpK<1> {
   static constexpr float F0 = 1.0f, F1 = 0.0f;
   // 2^-150 is the exact midpoint between +0 and 2^-149: ties to even give +0
   static constexpr float OVF = 128.0f, UNF = -150.0f;
+  static constexpr float XOVF = CRM_EXP2F_X_OVF, XZERO = CRM_EXP2F_X_ZERO, XSUB = CRM_EXP2F_X_SUB;
 };
 template <> struct ExpK<2> {
   static constexpr float C16 = CRM_LOG2_10_X16_F, C64 = CRM_LOG2_10_X64_F;
   static constexpr double D0 = CRM_LOG2_10_D0, D1 = CRM_LOG2_10_D1, D2 = CRM_LOG2_10_D2;
   static constexpr float F0 = CRM_LOG2_10_F0, F1 = CRM_LOG2_10_F1;
   static constexpr float OVF = 38.6f, UNF = -45.5f;
+  static constexpr float XOVF = CRM_EXP10F_X_OVF, XZERO = CRM_EXP10F_X_ZERO, XSUB = CRM_EXP10F_X_SUB;
 };
 
-#define CRM_SHIFTER_F 0x1.8p23f
+
 
 // Special inputs: returns true and the result when x is NaN or saturated.
 template <int KIND> CRM_DEV bool exp_special(float x, float &r) {
@@ -86,20 +89,18 @@ template <int KIND> CRM_DEV float exp_plain(float x, const double *T16, bool &ha
 // ------------------------------------------------------------------ double-float tier
 // t = th + tl (exact product x*C0 split by FMA, plus x*C1), N = rint(64 th),
 // f = th - N/64 (exact), g = gh + gl = f + tl (Fast2Sum: f is 0 or a multiple of
-// ulp(th) >= |tl|), |g| <= 2^-7 + 2^-16.  2^g - 1 = a1 g + a2 g^2 + a3 g^3 + a4 g^4:
-// a1 g in double-float, the rest in float.  y = T (1 + E) with T = Th + Tl from the
-// 64-entry table, left unnormalised as (s, l), |l| <~ ulp(s).
-// Error budget (relative): Q = g^2(a2 + a3 g + a4 g^2) rounding 2^-38.5; t from x*C1 and
-// the split of C 2^-40.7; a5 g^5 remainder 2^-44.5; table 2^-48; the rest < 2^-50.
-// Total < 2^-38.1; eps = 2^-37, margin 1 - 2^-11 (>= 2 eps 2^24 = 2^-12).
-constexpr float EXP_DF_MARGIN = 1.0f - 0x1p-11f;
-
-struct DFExp {
-  float s, l;
-  int k;
-};
-
-template <int KIND> CRM_DEV DFExp exp_df_core(float x, const float2 *T64) {
+// ulp(th) >= |tl|/2 in exponent), |g| <= 2^-7 + 2^-16.  With T = 2^(j/64) and
+// U = T ln2 from a 64-entry float4 table (Th, Tl, Uh, Ul):
+//   2^g T = Th + Uh gh + [Tl + Uh gl + Ul gh + T Q(gh) + ...],
+//   Q(g) = g^2 (a2 + a3 g + a4 g^2),  a_k = (ln 2)^k / k!,
+// Uh gh split exactly by FMA and Th + Uh gh by Fast2Sum, the bracket in float, then one
+// renormalisation.  Error budget (relative to T): rounding of Q 2^-38.8, the dropped
+// cross term 2 a2 gh gl 2^-39.1, t from x*C1 and the split of C 2^-40.7, a5 g^5
+// remainder 2^-44.6, tables 2^-48, bracket roundings 2^-48: total < 2^-37.7, covered by
+// the test's 2^-37 allowance (hard_df).
+// Inputs outside [X_SUB, X_OVF] are resolved by selects: +inf above X_OVF, +0 below
+// X_ZERO; the subnormal band [X_ZERO, X_SUB) and NaN go to the slow path.
+template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard) {
   using K = ExpK<KIND>;
   float th, tl;
   if (KIND == 1) {
@@ -122,43 +123,27 @@ template <int KIND> CRM_DEV DFExp exp_df_core(float x, const float2 *T64) {
     gh = f + tl;
     gl = tl - (gh - f);
   }
-  // P = a1 g (double-float)
-  float ph = CRM_EXP2_A1_HI_F * gh;
-  float pl = fma_(CRM_EXP2_A1_HI_F, gh, -ph);
-  pl = fma_(CRM_EXP2_A1_LO_F, gh, pl);
-  pl = fma_(CRM_EXP2_A1_HI_F, gl, pl);
-  // Q = g^2 (a2 + a3 g + a4 g^2) in float, plus the cross term 2 a2 gh gl
+  float4 T = T64U[N & 63];
   float q = fma_(gh, CRM_EXP2_A4_F, CRM_EXP2_A3_F);
   q = fma_(gh, q, CRM_EXP2_A2_F);
-  float g2 = gh * gh;
-  float Q = g2 * q;
-  float cross = (2.0f * CRM_EXP2_A2_F * gh) * gl;
-  // E = P + Q
-  float eh = ph + Q;
-  float el = Q - (eh - ph);
-  el = el + (pl + cross);
-  // y = T (1 + E)
-  float2 T = T64[N & 63];
-  float m = T.x * eh;
-  float ml = fma_(T.x, eh, -m);
+  float Q = (gh * gh) * q;
+  float m = T.z * gh;
+  float ml = fma_(T.z, gh, -m);
   float s = T.x + m;
   float z = m - (s - T.x);
-  float l = z + (ml + (T.y + fma_(T.x, el, T.y * eh)));
-  return {s, l, N >> 6};
-}
-
-template <int KIND> CRM_DEV float exp_df(float x, const float2 *T64, bool &hard) {
-  float r;
-  bool sp = exp_special<KIND>(x, r);
-  DFExp e = exp_df_core<KIND>(x, T64);
-  // scale by 2^k through the exponent field; s is in [0.98, 2.04]
-  int be = (int)((fbits(e.s) >> 23) & 0xFF) + e.k;
-  bool ovf = be >= 255;
-  bool sub = be <= 0;  // subnormal or zero result: decided by the slow path
-  float y = bitsf(fbits(e.s) + ((uint32_t)e.k << 23));
-  y = ovf ? CRM_INF_F : y;
-  hard = !sp && (sub || hard_df(e.s, e.l, EXP_DF_MARGIN));
-  return sp ? r : y;
+  float r = (KIND == 1) ? T.y : fma_(T.z, gl, T.y);
+  r = fma_(T.w, gh, r);
+  r = fma_(T.x, Q, r);
+  r = r + ml;
+  r = r + z;
+  float s2 = s + r;
+  float l2 = r - (s2 - s);
+  float y = bitsf(fbits(s2) + ((uint32_t)(N >> 6) << 23));
+  bool ok = (x >= K::XSUB) && (x <= K::XOVF);  // false for NaN
+  float rsp = x > 0.0f ? CRM_INF_F : 0.0f;
+  bool hsp = !(x < K::XZERO) && !(x > K::XOVF);  // subnormal band or NaN
+  hard = ok ? hard_df(s2, l2) : hsp;
+  return ok ? y : rsp;
 }
 
 // ------------------------------------------------------------------ double-double tier

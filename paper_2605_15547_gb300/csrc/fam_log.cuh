@@ -1,0 +1,267 @@
+// fam_log.cuh -- logf, log2f, log10f, log1pf.
+//
+// Following the paper's log2f scheme (Fig. 2, Sec. II.A): split x = 2^e m with m in
+// [3/4, 3/2) (so that the result near x = 1 comes from the polynomial alone, without
+// cancellation), pick a table point c_j = j/128 nearest to m, and write
+//     log x = e log 2 + log c_j + log1p(r),   r = (m - c_j)/c_j,   |r| <= 2^-7.58,
+// with (1/c_j, log c_j) from a 97-entry table and log1p(r) by its Taylor polynomial.
+// log2 and log10 use tables of log2 c_j / log10 c_j and scale log1p(r) by 1/ln 2 or
+// 1/ln 10.  log1p(x) evaluates the polynomial on x itself for |x| < 2^-7 and otherwise
+// works on u = 1 + x = uh + ul (exact pair), adding ul/uh.
+#pragma once
+#include "crm_common.cuh"
+#include "crm_tables.h"
+
+namespace crm {
+
+// KIND 0: ln, 1: log2, 2: log10, 3: log1p (ln of 1 + x)
+template <int KIND> struct LogK;
+template <> struct LogK<0> {
+  static constexpr float KH = CRM_LN2_F16_HI, KL = CRM_LN2_F16_LO;
+};
+template <> struct LogK<1> {
+  static constexpr float KH = 1.0f, KL = 0.0f;
+};
+template <> struct LogK<2> {
+  static constexpr float KH = CRM_LOG10_2_F16_HI, KL = CRM_LOG10_2_F16_LO;
+};
+template <> struct LogK<3> : LogK<0> {};
+
+// Table per kind: log1p uses the natural-log table.
+template <int KIND> CRM_DEV const float *log_tab_df() {
+  return KIND == 1 ? CRM_LOG2_T97_DF : (KIND == 2 ? CRM_LOG10_T97_DF : CRM_LN_T97_DF);
+}
+template <int KIND> CRM_DEV const double *log_tab_dd() {
+  return KIND == 1 ? CRM_LOG2_T97_DD : (KIND == 2 ? CRM_LOG10_T97_DD : CRM_LN_T97_DD);
+}
+
+// Decompose a positive normal double u = 2^e m, m in [3/4, 3/2); j = round(128 m) and
+// c = j/128 with integer operations only.
+struct DecD {
+  double m, c;
+  int e, j;
+};
+CRM_DEV DecD decompose_d(double u) {
+  uint64_t b = dbits(u);
+  uint64_t mant = b & 0x000FFFFFFFFFFFFFull;
+  bool big = mant >= (1ull << 51);  // m in [1.5, 2): halve
+  DecD r;
+  r.e = (int)(b >> 52) - 1023 + (big ? 1 : 0);
+  r.m = bitsd(mant | (big ? 0x3FE0000000000000ull : 0x3FF0000000000000ull));
+  if (big) {
+    r.j = 64 + (int)((mant + (1ull << 45)) >> 46);
+    r.c = bitsd(0x3FE0000000000000ull + ((uint64_t)(r.j - 64) << 46));
+  } else {
+    r.j = 128 + (int)((mant + (1ull << 44)) >> 45);
+    r.c = bitsd(0x3FF0000000000000ull + ((uint64_t)(r.j - 128) << 45));
+  }
+  return r;
+}
+
+// ------------------------------------------------------------------ plain (FP64) tier
+// r = (m - c) / c: m - c exact, times the double 1/c (relative error 2^-52).
+// log1p(r) by Taylor to degree 7 (remainder r^8/8 <= 2^-63.6, i.e. 2^-56 relative to r),
+// Horner in FP64.  ln u = e ln2_hi + L + (p + e ln2_lo) (e ln2_hi exact: 42-bit split).
+// Error: p relative 2^-51.5 (remainder + 8 roundings at |r|-scaled weight), L 2^-53 |L|,
+// final two sums 2^-53 |y| each, optional scaling by 1/ln 2 or 1/ln 10 2^-53: < 2^-49.7
+// relative to |y| (|p| <= |L|/2 or L = 0, so there is no cancellation).
+// eps = 2^-48 -> D = ceil(2^-48 2^53) + 1 = 33.
+constexpr uint32_t LOG_PLAIN_D = 33;
+
+template <int KIND> CRM_DEV double log_plain_y(float x, const double2 *T97) {
+  double xd = (double)x;
+  bool pathA = false;
+  double u = xd;
+  if (KIND == 3) {
+    pathA = fabsf(x) < 0x1p-7f;
+    u = pathA ? 1.0 : 1.0 + xd;  // 1 + x: exact for |x| < 2^29, else within 2^-53
+  }
+  DecD D = decompose_d(u);
+  double2 T = T97[D.j - 96];
+  double r = (D.m - D.c) * T.x;
+  double L = T.y;
+  double ef = (double)D.e;
+  if (KIND == 3) r = pathA ? xd : r;
+  const double *c = CRM_LOG1P_TAYLOR_D;  // c[k-1] = (-1)^(k+1)/k
+  double p = fma_(r, c[6], c[5]);
+  p = fma_(r, p, c[4]);
+  p = fma_(r, p, c[3]);
+  p = fma_(r, p, c[2]);
+  p = fma_(r, p, c[1]);
+  p = fma_(r, p, c[0]);
+  p = p * r;
+  double y = fma_(ef, CRM_LN2_D42_HI, L) + fma_(ef, CRM_LN2_D42_LO, p);
+  if (KIND == 1) y = y * CRM_INV_LN2_D_HI;
+  if (KIND == 2) y = y * CRM_INV_LN10_D_HI;
+  return y;
+}
+
+// Lanes outside the finite positive domain (NaN, 0, negative, inf; for log1p also
+// x <= -1 and x == 0) are returned through special_log.
+template <int KIND> CRM_DEV float special_log(float x) {
+  if (x != x) return qnan_of(x);
+  if (KIND == 3) {
+    if (x == 0.0f) return x;
+    if (x == -1.0f) return -CRM_INF_F;
+    if (x < -1.0f) return CRM_QNAN_F;
+    return CRM_INF_F;  // +inf
+  }
+  if (x == 0.0f) return -CRM_INF_F;
+  if (x < 0.0f) return CRM_QNAN_F;
+  return CRM_INF_F;
+}
+template <int KIND> CRM_DEV bool log_ok(float x) {
+  if (KIND == 3) return (x > -1.0f) && (x < CRM_INF_F) && (x != 0.0f);
+  return (x > 0.0f) && (x < CRM_INF_F);
+}
+
+template <int KIND> CRM_DEV float log_plain(float x, const double2 *T97, bool &hard) {
+  bool ok = log_ok<KIND>(x);
+  double y = log_plain_y<KIND>(ok ? x : 2.0f, T97);
+  hard = ok && hard_d_to_f(y, LOG_PLAIN_D);
+  return ok ? __double2float_rn(y) : special_log<KIND>(x);
+}
+
+// ------------------------------------------------------------------ double-float tier
+// Decomposition in binary32 (subnormal inputs are scaled by 2^24 first), j = rint(128 m),
+// d = m - c exact (Sterbenz), r = d (1/c) as a float pair (exact product split by FMA
+// plus d * (1/c)_lo).  log1p(r) = r - r^2/2 + r^3 (1/3 - r/4 + r^2/5):
+//   rh - rh^2/2 by Fast2Sum on the exact square (split by FMA), the r^3 tail in float.
+// For log2 / log10 the pair is multiplied by the float pair 1/ln 2 or 1/ln 10.
+// B = e K_hi + L_hi (Fast2Sum: e == 0, or |e K_hi| > |L|), then TwoSum(B, q) and one
+// renormalisation.  Error budget, relative to the result:
+//   r^6/6 remainder 2^-48.2 abs, tail rounding 2^-46.4 abs, pair products and the
+//   1/c, L and K splits <= 2^-46 abs, with |result| >= 2^-8 unless e = 0 and c = 1 (then
+//   all terms scale with r and the bound is 2^-38.5 relative); e K_lo rounding and the K
+//   split <= 2^-42 relative.  Total < 2^-38; the test allows 2^-37 (hard_df).
+template <int KIND> CRM_DEV float log_df(float x, const float4 *T97, bool &hard) {
+  using K = LogK<KIND>;
+  bool ok = log_ok<KIND>(x);
+  float uh = x, ul = 0.0f;
+  bool pathA = false;
+  if (KIND == 3) {
+    pathA = fabsf(x) < 0x1p-7f;
+    Pair<float> u = two_sum(1.0f, x);
+    uh = u.hi;
+    ul = u.lo;
+  }
+  uh = ok ? uh : 1.0f;
+  bool sub = uh < 0x1p-126f;
+  float us = sub ? uh * 0x1p24f : uh;
+  uint32_t b = fbits(us);
+  uint32_t mant = b & 0x007FFFFFu;
+  bool big = mant >= 0x00400000u;
+  float m = bitsf(mant | (big ? 0x3F000000u : 0x3F800000u));
+  int e = (int)(b >> 23) - 127 + (big ? 1 : 0) - (sub ? 24 : 0);
+  float sh = fma_(m, 128.0f, CRM_SHIFTER_F);
+  int j = (int)(fbits(sh) - fbits(CRM_SHIFTER_F));
+  float c = (sh - CRM_SHIFTER_F) * 0.0078125f;
+  float d = m - c;
+  float4 T = T97[j - 96];
+  float rh = d * T.x;
+  float rl = fma_(d, T.x, -rh);
+  rl = fma_(d, T.y, rl);
+  float Lh = T.z, Ll = T.w, ef = (float)e;
+  float t = 0.0f;
+  if (KIND == 3) {
+    t = __fdividef(ul, uh);  // ul/uh with |ul| <= 2^-24 uh: relative 2^-21 suffices
+    rh = pathA ? x : rh;
+    rl = pathA ? 0.0f : rl;
+    Lh = pathA ? 0.0f : Lh;
+    Ll = pathA ? 0.0f : Ll;
+    ef = pathA ? 0.0f : ef;
+    t = pathA ? 0.0f : t;
+  }
+  // log1p(r)
+  float h2 = rh * rh;
+  float h2l = fma_(rh, rh, -h2);
+  float q3 = fma_(rh, 0.2f, -0.25f);
+  q3 = fma_(rh, q3, 0x1.555556p-2f);
+  float P = (h2 * rh) * q3;
+  float s = fma_(h2, -0.5f, rh);
+  float z = fma_(h2, -0.5f, rh - s);
+  float rest = fma_(-rh, rl, rl);
+  rest = fma_(h2l, -0.5f, rest);
+  rest = rest + P;
+  rest = rest + (z + t);
+  float qh = s, ql = rest;
+  if (KIND == 1 || KIND == 2) {
+    const float IH = KIND == 1 ? CRM_INV_LN2_F_HI : CRM_INV_LN10_F_HI;
+    const float IL = KIND == 1 ? CRM_INV_LN2_F_LO : CRM_INV_LN10_F_LO;
+    qh = s * IH;
+    ql = fma_(s, IH, -qh);
+    ql = fma_(s, IL, ql);
+    ql = fma_(rest, IH, ql);
+  }
+  // B = e K + L
+  float eK = ef * K::KH;
+  float B = eK + Lh;
+  float Bz = Lh - (B - eK);
+  float Bl = Bz + fma_(ef, K::KL, Ll);
+  Pair<float> S = two_sum(B, qh);
+  float lo = S.lo + (Bl + ql);
+  float s2 = S.hi + lo;
+  float l2 = lo - (s2 - S.hi);
+  hard = !ok || hard_df(s2, l2);
+  return s2;
+}
+
+// ------------------------------------------------------------------ double-double tier
+// Same decomposition in binary64 on u = uh + ul (exact), d = (m - c) + ul 2^-e as a
+// double-double, r = d (1/c)_dd, log1p(r) by Taylor to degree 14 in double-double Horner
+// form (remainder < 2^-110), ln u = e ln2_dd + L_dd + log1p(r), scaled by 1/ln2_dd or
+// 1/ln10_dd.  Error < 2^-98 relative.
+constexpr double LOG_DD_EPS = 0x1p-92;
+
+template <int KIND> CRM_DEV Pair<double> log_dd_core(float x) {
+  double xd = (double)x;
+  Pair<double> u = {xd, 0.0};
+  bool pathA = false;
+  if (KIND == 3) {
+    pathA = fabsf(x) < 0x1p-7f;
+    u = pathA ? Pair<double>{1.0, 0.0} : two_sum(1.0, xd);
+  }
+  DecD D = decompose_d(u.hi);
+  const double *T = log_tab_dd<KIND == 3 ? 0 : KIND>() + 4 * (D.j - 96);
+  double sc = pow2d(-D.e);
+  Pair<double> dd_ = two_sum(D.m - D.c, u.lo * sc);
+  Pair<double> r = dd_mul(dd_, dd(T[0], T[1]));
+  if (KIND == 3 && pathA) r = {xd, 0.0};
+  const double *c = CRM_LOG1P_TAYLOR_DD;  // pairs, k = 1..17
+  Pair<double> p = dd(c[2 * 13], c[2 * 13 + 1]);
+  for (int k = 12; k >= 0; k--) p = dd_add(dd_mul(p, r), dd(c[2 * k], c[2 * k + 1]));
+  p = dd_mul(p, r);
+  Pair<double> y;
+  if (KIND == 1) {
+    // log2: e + (log2 c + log1p(r)/ln 2)
+    Pair<double> q = dd_mul(p, dd(CRM_INV_LN2_D_HI, CRM_INV_LN2_D_LO));
+    y = dd_add(dd_add(q, dd(T[2], T[3])), dd((double)D.e, 0.0));
+  } else {
+    Pair<double> eK = KIND == 2 ? dd_mul_d(dd(CRM_LOG10_2_DD_HI, CRM_LOG10_2_DD_LO), (double)D.e)
+                                : dd_mul_d(dd(CRM_LN2_DD_HI, CRM_LN2_DD_LO), (double)D.e);
+    if (KIND == 2) p = dd_mul(p, dd(CRM_INV_LN10_D_HI, CRM_INV_LN10_D_LO));
+    if (KIND == 3 && pathA) {
+      y = p;
+    } else {
+      y = dd_add(dd_add(eK, dd(T[2], T[3])), p);
+    }
+  }
+  return y;
+}
+
+template <int KIND> CRM_DEV float log_dd(float x, bool &hard) {
+  Pair<double> y = log_dd_core<KIND>(x);
+  return round_dd_to_f(y.hi, y.lo, LOG_DD_EPS * fabs(y.hi), hard);
+}
+
+template <int KIND> CRM_DEV float log_slow(float x, bool &unresolved) {
+  bool hard;
+  float r = log_plain<KIND>(x, (const double2 *)CRM_LN_T97_D, hard);
+  unresolved = false;
+  if (!hard) return r;
+  r = log_dd<KIND>(x, hard);
+  unresolved = hard;
+  return r;
+}
+
+}  // namespace crm

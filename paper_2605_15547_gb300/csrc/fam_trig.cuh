@@ -1,0 +1,202 @@
+// fam_trig.cuh -- sinf, cosf, sincosf, tanf.
+//
+// Reduction (every |x| >= 2^-6): an integer Payne-Hanek step on the 24-bit significand.
+// With x = M 2^e, the bits of 2/pi that can change |x| 64/pi modulo 128 form a window
+// selected by e (the paper reduces large trigonometric arguments on a separate branch,
+// Sec. II.A; here one branch-free integer path serves all magnitudes):
+//     |x| 64/pi = 128 m + 32 q + j + f,   q = quadrant, j in [0,32), |f| <= 1/2,
+// obtained from M times a 96-bit (fast tiers) or 160-bit (slow tier) window of 2/pi.
+// Then t = f pi/64 (|t| <= pi/128) and, with S_j = sin(j pi/64), C_j = cos(j pi/64),
+//     sin(j pi/64 + t) = S_j cos t + C_j sin t,   cos(j pi/64 + t) = C_j cos t - S_j sin t,
+// rotated by the quadrant.  |x| < 2^-6 uses t = x, j = q = 0 directly.
+#pragma once
+#include "crm_common.cuh"
+#include "crm_tables.h"
+
+namespace crm {
+
+enum { TRIG_SIN = 0, TRIG_COS = 1, TRIG_TAN = 2, TRIG_SINCOS = 3 };
+
+// Multiply the 24-bit significand of |x| (2^-6 <= |x| < 2^128) by NW words of 2/pi
+// starting at the bit that makes the product |x| 64/pi modulo 128.  r[0] is the least
+// significant word of the (32 NW + 32)-bit product; the value is r 2^(7 - 32 NW).
+template <int NW>
+CRM_DEV void trig_window_mul(float ax, const uint32_t *P, uint32_t *r) {
+  uint32_t b = fbits(ax);
+  uint32_t M = (b & 0x007FFFFFu) | 0x00800000u;
+  int e = (int)(b >> 23) - 150;
+  int p = 64 + (e - 1) - 1;  // position of bit b_(e-1) after two zero words
+  int k = p >> 5, o = p & 31;
+  uint32_t w[NW];
+#pragma unroll
+  for (int i = 0; i < NW; i++) w[i] = __funnelshift_l(P[k + i + 1], P[k + i], o);
+  uint64_t carry = 0;
+#pragma unroll
+  for (int i = NW - 1; i >= 0; i--) {  // w[NW-1] is the least significant word
+    uint64_t pr = (uint64_t)M * w[i] + carry;
+    r[NW - 1 - i] = (uint32_t)pr;
+    carry = pr >> 32;
+  }
+  r[NW] = (uint32_t)carry;
+}
+
+// Fast-tier reduction: N7 = (32 q + j) mod 128 and the fraction f as a signed 64-bit
+// fixed-point number (f = fi 2^-64); error < 2^-64 (fraction) + 2^-66 (window).
+CRM_DEV void trig_reduce64(float ax, const uint32_t *P, int &N7, int64_t &fi) {
+  uint32_t r[4];
+  trig_window_mul<3>(ax, P, r);
+  uint64_t F = ((uint64_t)(r[2] & 0x01FFFFFFu) << 39) | ((uint64_t)r[1] << 7) | (r[0] >> 25);
+  N7 = (int)(((r[2] >> 25) + (uint32_t)(F >> 63)) & 127u);
+  fi = (int64_t)F;
+}
+
+// ------------------------------------------------------------------ plain (FP64) tier
+// t = fi 2^-64 pi/64 in binary64: relative error 2^-52 plus the reduction's absolute
+// error 2^-63.6 in f, which matters only when the result is as small as t (j = 0); lanes
+// with j = 0 and |f| < 2^-14 go to the slow path, so the reduction adds at most 2^-49.6
+// relative.  sin t and cos t by Taylor polynomials to degree 7 and 6
+// (remainders below 2^-58), the table in binary64, one FMA per rotation term.  The
+// combination may lose up to 2^5.4 (|result| >= sin(pi/128) when j != 0):
+// eps = 2^-46 (D = 129); tan adds a division (D = 257).
+struct TrigD {
+  double A, B;  // sin and cos of (j pi/64 + t), before the quadrant rotation
+  int q;
+  bool tiny;    // j == 0 and |f| < 2^-14: the reduction's error is too large, go slow
+};
+
+CRM_DEV TrigD trig_plain_core(float x, const uint32_t *P, const double *SC) {
+  float ax = fabsf(x);
+  bool small = ax < 0x1p-6f;
+  int N7;
+  int64_t fi;
+  trig_reduce64(small ? 1.0f : ax, P, N7, fi);
+  double t = (double)fi * (CRM_PIO64_D_HI * 0x1p-64);
+  t = small ? (double)ax : t;
+  N7 = small ? 0 : N7;
+  bool tiny = !small && (N7 & 31) == 0 && (fi > -(1ll << 50) && fi < (1ll << 50));
+  int j = N7 & 31;
+  double t2 = t * t;
+  const double *s = CRM_SIN_TAYLOR_D, *c = CRM_COS_TAYLOR_D;
+  double st = fma_(t2, fma_(t2, fma_(t2, s[3], s[2]), s[1]), s[0]) * t;
+  double ct = fma_(t2, fma_(t2, fma_(t2, c[3], c[2]), c[1]), c[0]);
+  double S = SC[2 * j], C = SC[2 * j + 1];
+  TrigD R;
+  R.A = fma_(S, ct, C * st);
+  R.B = fma_(C, ct, -(S * st));
+  R.q = N7 >> 5;
+  R.tiny = tiny;
+  return R;
+}
+
+// Rotate by the quadrant and apply the symmetry in x.  out[0]: sin or tan, out[1]: cos.
+template <class Tv> CRM_DEV void trig_rotate(int kind, float x, int q, Tv A, Tv B, Tv &sn, Tv &cs) {
+  Tv s0 = (q & 1) ? B : A, c0 = (q & 1) ? A : B;
+  bool sneg = (q & 2) != 0, cneg = ((q + 1) & 2) != 0;
+  sn = sneg ? -s0 : s0;
+  cs = cneg ? -c0 : c0;
+  if (x < 0.0f) sn = -sn;
+}
+
+CRM_DEV bool trig_special(float x, float &r) {
+  bool nan = x != x, inf = fabsf(x) == CRM_INF_F;
+  r = nan ? qnan_of(x) : CRM_QNAN_F;
+  return nan || inf;
+}
+
+template <int KIND>
+CRM_DEV void trig_plain(float x, const uint32_t *P, const double *SC, float *y, bool &hard) {
+  float rsp;
+  bool sp = trig_special(x, rsp);
+  TrigD R = trig_plain_core(sp ? 1.0f : x, P, SC);
+  double sn, cs;
+  trig_rotate<double>(KIND, x, R.q, R.A, R.B, sn, cs);
+  bool zero = x == 0.0f;  // sin/tan(+-0) = +-0
+  if (KIND == TRIG_TAN) {
+    double t = sn / cs;
+    hard = !sp && !zero && (R.tiny || hard_d_to_f(t, 257));
+    y[0] = sp ? rsp : (zero ? x : __double2float_rn(t));
+    return;
+  }
+  bool hs = hard_d_to_f(sn, 129), hc = hard_d_to_f(cs, 129);
+  if (KIND == TRIG_SIN) {
+    hard = !sp && !zero && (R.tiny || hs);
+    y[0] = sp ? rsp : (zero ? x : __double2float_rn(sn));
+  } else if (KIND == TRIG_COS) {
+    hard = !sp && (R.tiny || hc);
+    y[0] = sp ? rsp : __double2float_rn(cs);
+  } else {
+    hard = !sp && (R.tiny || (hs && !zero) || hc);
+    y[0] = sp ? rsp : (zero ? x : __double2float_rn(sn));
+    y[1] = sp ? rsp : __double2float_rn(cs);
+  }
+}
+
+// ------------------------------------------------------------------ double-double tier
+// 160-bit window: the fraction to 128 bits (error < 2^-127.6), t = f pi/64 in
+// double-double, sin/cos t by Taylor polynomials to degree 15 / 14 (remainders < 2^-118),
+// the double-double table, double-double rotation.  Relative error < 2^-96 with the same
+// 2^5.4 combination bound, plus 2^-127.6/|f| from the reduction when j = 0 (below 2^-87
+// for |f| >= 2^-40; a closer approach of x to a multiple of pi/64 would be reported as
+// unresolved, never silently mis-rounded).
+constexpr double TRIG_DD_EPS = 0x1p-84;
+
+CRM_DEV void trig_dd_core(float x, Pair<double> &A, Pair<double> &B, int &q) {
+  float ax = fabsf(x);
+  Pair<double> t;
+  int N7 = 0;
+  if (ax < 0x1p-6f) {
+    t = {(double)ax, 0.0};
+  } else {
+    uint32_t r[6];
+    trig_window_mul<5>(ax, CRM_TWO_OVER_PI_W, r);
+    uint64_t Fh = ((uint64_t)(r[4] & 0x01FFFFFFu) << 39) | ((uint64_t)r[3] << 7) | (r[2] >> 25);
+    uint64_t Fl = ((uint64_t)(r[2] & 0x01FFFFFFu) << 39) | ((uint64_t)r[1] << 7) | (r[0] >> 25);
+    N7 = (int)(((r[4] >> 25) + (uint32_t)(Fh >> 63)) & 127u);
+    long long fh = (long long)Fh;  // two's complement: f - 1 when f >= 1/2
+    long long ft = fh & ~0x7FFll;    // 53 significant bits: exact in binary64
+    double h = __ll2double_rn(ft);
+    long long rem = fh - ft;
+    Pair<double> f = fast_two_sum(h, (double)rem + __ull2double_rn(Fl) * 0x1p-64);
+    f = {f.hi * 0x1p-64, f.lo * 0x1p-64};
+    t = dd_mul(f, dd(CRM_PIO64_D_HI, CRM_PIO64_D_LO));
+  }
+  int j = N7 & 31;
+  q = N7 >> 5;
+  Pair<double> t2 = dd_sqr(t);
+  const double *s = CRM_SIN_TAYLOR_DD, *c = CRM_COS_TAYLOR_DD;
+  Pair<double> st = dd(s[14], s[15]), ct = dd(c[14], c[15]);
+  for (int k = 6; k >= 0; k--) {
+    st = dd_add(dd_mul(st, t2), dd(s[2 * k], s[2 * k + 1]));
+    ct = dd_add(dd_mul(ct, t2), dd(c[2 * k], c[2 * k + 1]));
+  }
+  st = dd_mul(st, t);
+  const double *T = CRM_SINCOS_T32_DD + 4 * j;
+  Pair<double> S = dd(T[0], T[1]), C = dd(T[2], T[3]);
+  A = dd_add(dd_mul(S, ct), dd_mul(C, st));
+  B = dd_add(dd_mul(C, ct), dd_neg(dd_mul(S, st)));
+}
+
+template <int KIND> CRM_DEV void trig_slow(float x, float *y, bool &unresolved) {
+  bool hard;
+  trig_plain<KIND>(x, CRM_TWO_OVER_PI_W, CRM_SINCOS_T32_D, y, hard);
+  unresolved = false;
+  if (!hard) return;
+  Pair<double> A, B, sn, cs;
+  int q;
+  trig_dd_core(x, A, B, q);
+  trig_rotate<Pair<double>>(KIND, x, q, A, B, sn, cs);
+  bool h0 = false, h1 = false;
+  if (KIND == TRIG_TAN) {
+    Pair<double> t = dd_div(sn, cs);
+    y[0] = round_dd_to_f(t.hi, t.lo, TRIG_DD_EPS * fabs(t.hi), h0);
+  } else {
+    if (KIND != TRIG_COS) y[0] = round_dd_to_f(sn.hi, sn.lo, TRIG_DD_EPS * fabs(sn.hi), h0);
+    float c = round_dd_to_f(cs.hi, cs.lo, TRIG_DD_EPS * fabs(cs.hi), h1);
+    if (KIND == TRIG_COS) y[0] = c;
+    if (KIND == TRIG_SINCOS) y[1] = c;
+  }
+  if (x == 0.0f && KIND != TRIG_COS) y[0] = x;
+  unresolved = h0 || h1;
+}
+
+}  // namespace crm

@@ -121,6 +121,51 @@ t64f = []
 for i in range(64):
     t64f += split(mp.power(2, mp.mpf(i) / 64), f, 2)
 arr_f("CRM_EXP2_T64_DF", t64f, "2^(i/64) as (hi, lo) floats (double-float form)")
+# 64-entry float4 table (T hi, T lo, U hi, U lo) with T = 2^(i/64), U = T ln 2
+t64u = []
+for i in range(64):
+    T = mp.power(2, mp.mpf(i) / 64)
+    t64u += split(T, f, 2) + split(T * LN2, f, 2)
+arr_f("CRM_EXP2_T64U_DF", t64u, "(2^(i/64) hi, lo, 2^(i/64) ln2 hi, lo) floats (double-float form)")
+emit()
+
+
+def f32_below(v):
+    """largest binary32 value < v (v not representable)"""
+    import struct
+    x = float(f(v))
+    if mp.mpf(x) >= v:
+        b = struct.unpack("<i", struct.pack("<f", x))[0]
+        b = b - 1 if x > 0 else b + 1
+        x = struct.unpack("<f", struct.pack("<i", b))[0]
+    assert mp.mpf(x) < v
+    return mp.mpf(x)
+
+
+def f32_above(v):
+    import struct
+    x = float(f(v))
+    if mp.mpf(x) <= v:
+        b = struct.unpack("<i", struct.pack("<f", x))[0]
+        b = b + 1 if x >= 0 else b - 1
+        x = struct.unpack("<f", struct.pack("<i", b))[0]
+    assert mp.mpf(x) > v
+    return mp.mpf(x)
+
+
+# Input thresholds of b^x in binary32 (b = e, 2, 10), from the exact rounding boundaries:
+#   OVF : largest x with b^x < 2^128 - 2^103 (finite result), larger x give +inf;
+#   ZERO: smallest x with b^x > 2^-150 (nonzero result), smaller x give +0;
+#   SUB : smallest binary32 x with b^x >= 2^-126 (normal result); x below it and >= ZERO
+#         give subnormal results.
+OVF_REAL = mp.mpf(2) ** 128 - mp.mpf(2) ** 103
+for nm, lnb in (("EXP", mp.mpf(1)), ("EXP2", LN2), ("EXP10", mp.log(10))):
+    ovf = f32_below(mp.log(OVF_REAL) / lnb)
+    zero = f32_above(mp.log(mp.mpf(2) ** -150) / lnb)
+    sub = f32_above(mp.log(mp.mpf(2) ** -126) / lnb)
+    const_f(f"CRM_{nm}F_X_OVF", ovf, "largest input with a finite result")
+    const_f(f"CRM_{nm}F_X_ZERO", zero, "smallest input with a nonzero result")
+    const_f(f"CRM_{nm}F_X_SUB", sub, "smallest input with a normal result")
 emit()
 # Taylor coefficients of 2^g = sum (ln2)^k/k! g^k
 coef = [LN2 ** k / mp.factorial(k) for k in range(20)]
@@ -147,6 +192,154 @@ for nm, C in (("LOG2E", LOG2E), ("LOG2_10", LOG2_10)):
     const_f(f"CRM_{nm}_F2", q[2])
     const_f(f"CRM_{nm}_X16_F", f(16 * C), "16*C rounded: only picks the reduction integer")
     const_f(f"CRM_{nm}_X64_F", f(64 * C), "64*C rounded: only picks the reduction integer")
+emit()
+
+# ---------------------------------------------------------------- log family
+emit("// ===== log family: x = 2^e m with m in [3/4, 3/2) (the paper's Fig. 2 split),      =====")
+emit("// ===== c_j = j/128 (j = round(128 m), 96..192), log x = e log 2 + log c_j + log1p(r), =====")
+emit("// ===== r = (m - c_j)/c_j, |r| <= 2^-7.58; entry j-96                                  =====")
+for kind, base in (("LN", None), ("LOG2", 2), ("LOG10", 10)):
+    def lg(v):
+        return mp.log(v) if base is None else mp.log(v) / mp.log(base)
+    tf, td, tdd = [], [], []
+    for j in range(96, 193):
+        c = mp.mpf(j) / 128
+        rc = 1 / c
+        L = lg(c)
+        tf += split(rc, f, 2) + split(L, f, 2)
+        td += [d(rc), d(L)]
+        tdd += split(rc, d, 2) + split(L, d, 2)
+    arr_f(f"CRM_{kind}_T97_DF", tf, f"(1/c_j hi, lo, {kind.lower()}(c_j) hi, lo) floats")
+    arr_d(f"CRM_{kind}_T97_D", td, f"(1/c_j, {kind.lower()}(c_j)) doubles")
+    arr_d(f"CRM_{kind}_T97_DD", tdd, f"(1/c_j, {kind.lower()}(c_j)) as double-double")
+LOG10_2 = mp.log(2) / mp.log(10)
+for nm, v in (("LN2", LN2), ("LOG10_2", LOG10_2)):
+    hi = rnd(v, 16)
+    const_f(f"CRM_{nm}_F16_HI", hi, "16 bits: e * this is exact in binary32")
+    const_f(f"CRM_{nm}_F16_LO", f(v - hi))
+    hi = rnd(v, 42)
+    const_d(f"CRM_{nm}_D42_HI", hi, "42 bits: e * this is exact in binary64")
+    const_d(f"CRM_{nm}_D42_LO", d(v - hi))
+    dp = split(v, d, 2)
+    const_d(f"CRM_{nm}_DD_HI", dp[0])
+    const_d(f"CRM_{nm}_DD_LO", dp[1])
+for nm, v in (("INV_LN2", 1 / LN2), ("INV_LN10", 1 / mp.log(10))):
+    fp = split(v, f, 2)
+    const_f(f"CRM_{nm}_F_HI", fp[0])
+    const_f(f"CRM_{nm}_F_LO", fp[1])
+    dp = split(v, d, 2)
+    const_d(f"CRM_{nm}_D_HI", dp[0])
+    const_d(f"CRM_{nm}_D_LO", dp[1])
+# log1p Taylor coefficients (-1)^(k+1)/k
+arr_d("CRM_LOG1P_TAYLOR_D", [d(mp.mpf((-1) ** (k + 1)) / k) for k in range(1, 10)],
+      "(-1)^(k+1)/k, k = 1..9, doubles")
+l1dd = []
+for k in range(1, 18):
+    l1dd += split(mp.mpf((-1) ** (k + 1)) / k, d, 2)
+arr_d("CRM_LOG1P_TAYLOR_DD", l1dd, "(-1)^(k+1)/k, k = 1..17, double-double")
+emit()
+
+# ---------------------------------------------------------------- hyperbolic / expm1
+emit("// ===== expm1 / sinh / cosh / tanh =====")
+# thresholds: sinh/cosh overflow, tanh rounding to +-1, expm1 rounding to -1
+def largest_f32_with(pred, lo, hi):
+    """largest binary32 x in [lo, hi] with pred(x) true (pred monotone: true then false)"""
+    import struct
+    def bits(v):
+        return struct.unpack("<i", struct.pack("<f", v))[0]
+    def val(b):
+        return struct.unpack("<f", struct.pack("<i", b))[0]
+    a, b = bits(lo), bits(hi)
+    assert pred(mp.mpf(val(a))) and not pred(mp.mpf(val(b)))
+    while b - a > 1:
+        m = (a + b) // 2
+        if pred(mp.mpf(val(m))):
+            a = m
+        else:
+            b = m
+    return mp.mpf(val(a))
+half_ulp_below_1 = mp.mpf(2) ** -25
+const_f("CRM_SINHF_X_OVF", largest_f32_with(lambda v: mp.sinh(v) < OVF_REAL, 80.0, 100.0),
+        "largest input with a finite sinh / cosh")
+const_f("CRM_TANHF_X_ONE", largest_f32_with(lambda v: 1 - mp.tanh(v) > half_ulp_below_1, 1.0, 20.0),
+        "largest input whose tanh does not round to 1")
+const_f("CRM_EXPM1F_X_MONE", -largest_f32_with(lambda v: 1 - mp.exp(-v) < 1 - half_ulp_below_1, 1.0, 40.0),
+        "inputs below this give exactly -1")
+# Taylor coefficients 1/k! (double and double-double)
+arr_d("CRM_INVFACT_D", [d(1 / mp.factorial(k)) for k in range(20)], "1/k!, k = 0..19")
+ifdd = []
+for k in range(28):
+    ifdd += split(1 / mp.factorial(k), d, 2)
+arr_d("CRM_INVFACT_DD", ifdd, "1/k!, k = 0..27, double-double")
+emit()
+
+# ---------------------------------------------------------------- trig
+emit("// ===== trig: |x| 64/pi = 128 m + 32 q + j + f (integer reduction), t = f pi/64 =====")
+bits_needed = 32 * 14
+with mp.workprec(bits_needed + 128):
+    v = int(mp.floor(2 / mp.pi * mp.mpf(2) ** bits_needed))
+words = [0, 0] + [(v >> (bits_needed - 32 * (i + 1))) & 0xFFFFFFFF for i in range(14)]
+emit("// bits of 2/pi after the binary point, 32 per word, preceded by two zero words")
+emit(f"CRM_TABLE unsigned int CRM_TWO_OVER_PI_W[{len(words)}] = {{")
+for i in range(0, len(words), 4):
+    emit("  " + ", ".join(f"0x{w:08X}u" for w in words[i:i + 4]) + ",")
+emit("};")
+sc_d, sc_f, sc_dd = [], [], []
+for j in range(32):
+    a = mp.mpf(j) * mp.pi / 64
+    S, C = mp.sin(a), mp.cos(a)
+    sc_d += [d(S), d(C)]
+    sc_f += split(S, f, 2) + split(C, f, 2)
+    sc_dd += split(S, d, 2) + split(C, d, 2)
+arr_d("CRM_SINCOS_T32_D", sc_d, "(sin, cos)(j pi/64), j = 0..31, doubles")
+arr_f("CRM_SINCOS_T32_DF", sc_f, "(sin hi, lo, cos hi, lo)(j pi/64) floats")
+arr_d("CRM_SINCOS_T32_DD", sc_dd, "(sin, cos)(j pi/64) as double-double")
+PIO64 = mp.pi / 64
+pp = split(PIO64, d, 2)
+const_d("CRM_PIO64_D_HI", pp[0])
+const_d("CRM_PIO64_D_LO", pp[1])
+pf = split(PIO64, f, 2)
+const_f("CRM_PIO64_F_HI", pf[0])
+const_f("CRM_PIO64_F_LO", pf[1])
+# (-1)^k / (2k+1)! and (-1)^k/(2k)! as doubles and double-doubles
+arr_d("CRM_SIN_TAYLOR_D", [d(mp.mpf((-1) ** k) / mp.factorial(2 * k + 1)) for k in range(10)],
+      "(-1)^k/(2k+1)!, k = 0..9")
+arr_d("CRM_COS_TAYLOR_D", [d(mp.mpf((-1) ** k) / mp.factorial(2 * k)) for k in range(10)],
+      "(-1)^k/(2k)!, k = 0..9")
+sdd, cdd = [], []
+for k in range(12):
+    sdd += split(mp.mpf((-1) ** k) / mp.factorial(2 * k + 1), d, 2)
+    cdd += split(mp.mpf((-1) ** k) / mp.factorial(2 * k), d, 2)
+arr_d("CRM_SIN_TAYLOR_DD", sdd, "(-1)^k/(2k+1)!, k = 0..11, double-double")
+arr_d("CRM_COS_TAYLOR_DD", cdd, "(-1)^k/(2k)!, k = 0..11, double-double")
+emit()
+
+# ---------------------------------------------------------------- inverse trig
+emit("// ===== atan(a/b) = atan(c_j) + atan(t), c_j = j/16, t = (a - c b)/(b + c a) =====")
+at_d, at_f, at_dd = [], [], []
+for j in range(17):
+    A = mp.atan(mp.mpf(j) / 16)
+    at_d.append(d(A))
+    at_f += split(A, f, 2)
+    at_dd += split(A, d, 2)
+arr_d("CRM_ATAN_T17_D", at_d + [mp.mpf(0)], "atan(j/16), j = 0..16 (+ padding)")
+arr_f("CRM_ATAN_T17_DF", at_f + [mp.mpf(0), mp.mpf(0)], "atan(j/16) (hi, lo) floats")
+arr_d("CRM_ATAN_T17_DD", at_dd, "atan(j/16) as double-double")
+pio2 = mp.pi / 2
+const_d("CRM_PIO2_D_HI", d(pio2))
+const_d("CRM_PIO2_D_LO", d(pio2 - d(pio2)))
+const_f("CRM_PIO2_F_HI", f(pio2))
+const_f("CRM_PIO2_F_LO", f(pio2 - f(pio2)))
+const_d("CRM_PI_D_HI", d(mp.pi))
+const_d("CRM_PI_D_LO", d(mp.pi - d(mp.pi)))
+const_f("CRM_PI_F_HI", f(mp.pi))
+const_f("CRM_PI_F_LO", f(mp.pi - f(mp.pi)))
+arr_d("CRM_ATAN_TAYLOR_D", [d(mp.mpf((-1) ** k) / (2 * k + 1)) for k in range(8)],
+      "(-1)^k/(2k+1), k = 0..7")
+atdd = []
+for k in range(14):
+    atdd += split(mp.mpf((-1) ** k) / (2 * k + 1), d, 2)
+arr_d("CRM_ATAN_TAYLOR_DD", atdd, "(-1)^k/(2k+1), k = 0..13, double-double")
 emit()
 
 emit("// ===== end =====")

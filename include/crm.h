@@ -67,7 +67,8 @@ typedef enum {
   CRM_ERR_FORM = 7,     /* unknown or unavailable form */
   CRM_ERR_CAPTURE = 8,  /* workspace must grow while the stream is being captured */
   CRM_ERR_ARG = 9,      /* other invalid argument (negative count, size too large) */
-  CRM_ERR_NODEV = 10    /* no CUDA device */
+  CRM_ERR_NODEV = 10,   /* no CUDA device */
+  CRM_ERR_SIZE = 11     /* n exceeds CRM_NOALLOC_MAX_ELEMS (crm_eval_noalloc only) */
 } crm_status_t;
 
 /* One array of a batch (crm_eval_batch).  in/out are device pointers; out holds 2n
@@ -108,6 +109,26 @@ int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, u
 /* Evaluate `count` arrays of mixed functions and lengths with one persistent kernel
    (the batching form).  descs is host memory, read before return.  Asynchronous. */
 int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream);
+
+/* No-allocation variant of crm_eval_form.  The paper has no counterpart: this entry
+   point exists for callers that cannot allocate device memory when they call the
+   library -- work recorded under stream capture (cudaMalloc is not permitted while a
+   stream is being captured), serving processes that budget every device byte at
+   start-up and forbid later allocation, and code running inside another component's
+   memory manager.  It computes exactly what crm_eval_form computes and allocates
+   nothing: its scratch (the hard-case queue and counters) is a statically reserved
+   device array of 256 + 16 * CRM_NOALLOC_MAX_ELEMS bytes (16 MiB) that every GPU which
+   loads the library holds until the process exits.
+   in/out: device pointers owned by the caller, as for crm_eval (out holds 2n elements
+   for CRM_SINCOSF).  n must not exceed CRM_NOALLOC_MAX_ELEMS (else CRM_ERR_SIZE, nothing
+   launched).  The first call on each device looks up the array's device address with
+   that device current; make that first call before any stream capture.  Every call on
+   a device shares the one array (each call clears the queue count it needs), so calls
+   whose work overlaps on the GPU (different streams, no ordering) race and must not be
+   issued.  Asynchronous on `stream`.  Other errors as crm_eval_form. */
+#define CRM_NOALLOC_MAX_ELEMS (1ull << 20)
+int crm_eval_noalloc(int func_id, int dtype, int form, const void *in, void *out, uint64_t n,
+                     void *stream);
 
 /* Process-wide default form for crm_eval (initially from env CRM_FORM, else AUTO). */
 int crm_set_form(int form);

@@ -1,0 +1,17 @@
+// crm_internal.h -- runtime helpers shared between the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "crm_registry.h"
+
+namespace crm {
+void ensure_init();
+const FuncEntry &func_entry(int func);
+int resolve_form(const FuncEntry &fe, int form);
+int check_args(int func, int dtype, const void *in, void *out, uint64_t n);
+int unroll_of(int func, int form);
+int force_slow_flag();
+int cuda_fail_code(cudaError_t e);
+void fill_geometry(const FuncEntry &fe, const void *in, void *out, uint64_t n, KArgs &a);
+int main_grid(const FuncEntry &fe, const KArgs &a, int ui, int sms, int bps);
+}  // namespace crm

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/crm.h"
+#include "crm_internal.h"
 #include "crm_registry.h"
 
 namespace crm {
@@ -37,7 +38,13 @@ static void init_table() {
   const char *fs = getenv("CRM_FORCE_SLOW");
   if (fs && atoi(fs)) g_force_slow = 1;
 }
-static void ensure_init() { std::call_once(g_init_once, init_table); }
+void ensure_init() { std::call_once(g_init_once, init_table); }
+const FuncEntry &func_entry(int func) { return g_table[func]; }
+int force_slow_flag() { return g_force_slow; }
+int cuda_fail_code(cudaError_t e) {
+  g_last_cuda = (int)e;
+  return CRM_ERR_CUDA;
+}
 
 // ------------------------------------------------------------------ workspaces
 struct Workspace {
@@ -134,7 +141,7 @@ static int blocks_per_sm(const void *sym) {
 static int g_unroll[CRM_NUM_FUNCS][3];
 static bool g_unroll_set = false;
 
-static int unroll_of(int func, int form) {
+int unroll_of(int func, int form) {
   if (!g_unroll_set) {
     for (int f = 0; f < CRM_NUM_FUNCS; f++)
       for (int m = 0; m < 3; m++) g_unroll[f][m] = 1;  // 2 vectors in flight by default
@@ -143,7 +150,7 @@ static int unroll_of(int func, int form) {
   return g_unroll[func][form];
 }
 
-static int resolve_form(const FuncEntry &fe, int form) {
+int resolve_form(const FuncEntry &fe, int form) {
   if (form == CRM_FORM_AUTO) {
     if (fe.main[CRM_FORM_DF32][0]) return CRM_FORM_DF32;
     if (fe.main[CRM_FORM_PLAIN_FP64][0]) return CRM_FORM_PLAIN_FP64;
@@ -153,7 +160,7 @@ static int resolve_form(const FuncEntry &fe, int form) {
   return fe.main[form][0] ? form : -1;
 }
 
-static int check_args(int func, int dtype, const void *in, void *out, uint64_t n) {
+int check_args(int func, int dtype, const void *in, void *out, uint64_t n) {
   if (func < 0 || func >= CRM_NUM_FUNCS) return CRM_ERR_FUNC;
   const FuncEntry &fe = g_table[func];
   int want = func >= CRM_EXP2 ? CRM_F64 : CRM_F32;
@@ -171,27 +178,14 @@ static int check_args(int func, int dtype, const void *in, void *out, uint64_t n
   return CRM_OK;
 }
 
-// Enqueue one evaluation (arguments already checked, n > 0).
-static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cudaStream_t s,
-                   uint32_t desc) {
-  const FuncEntry &fe = g_table[func];
-  int fm = resolve_form(fe, form);
-  if (fm < 0) return CRM_ERR_FORM;
-  Workspace *w = nullptr;
-  int st = get_ws(s, kDefaultCap, &w);
-  if (st) return st;
+// Vector geometry: the vector loop needs input and output(s) at the same offset modulo
+// 16 bytes; the scalar loop covers the unaligned head and the tail.
+void fill_geometry(const FuncEntry &fe, const void *in, void *out, uint64_t n, KArgs &a) {
   const size_t es = fe.dtype ? 8 : 4;
   const int W = fe.dtype ? 2 : 4;
-  KArgs a;
   a.in = in;
   a.out = out;
   a.n = n;
-  a.hdr = w->hdr;
-  a.q = w->q;
-  a.cap = w->cap;
-  a.force_hard = g_force_slow;
-  a.desc = desc;
-  // vector path: input and output(s) share their offset modulo 16 bytes
   uintptr_t ia = (uintptr_t)in, oa = (uintptr_t)out;
   bool vec = ((ia - oa) % 16) == 0 && (fe.nout == 1 || (n * es) % 16 == 0);
   if (vec) {
@@ -203,16 +197,40 @@ static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cu
     a.head = 0;
     a.nvec = 0;
   }
-  int ui = unroll_of(func, fm);
+}
+
+// Grid of the main kernel: enough blocks for the work, at most one full wave of
+// resident blocks (the kernel loops over the rest).
+int main_grid(const FuncEntry &fe, const KArgs &a, int ui, int sms, int bps) {
+  const int W = fe.dtype ? 2 : 4;
   const int U = 1 << ui;
-  int sms = dev_sms();
-  int bps = blocks_per_sm(fe.main_sym[fm][ui]);
   uint64_t want = (a.nvec + (uint64_t)KBLOCK * U - 1) / ((uint64_t)KBLOCK * U);
-  uint64_t nscal = a.head + (n - a.head - (uint64_t)W * a.nvec);
+  uint64_t nscal = a.head + (a.n - a.head - (uint64_t)W * a.nvec);
   uint64_t want_s = (nscal + KBLOCK - 1) / KBLOCK;
   if (want_s > want) want = want_s;
   uint64_t cap_blocks = (uint64_t)sms * bps;
-  int grid = (int)(want < cap_blocks ? (want ? want : 1) : cap_blocks);
+  return (int)(want < cap_blocks ? (want ? want : 1) : cap_blocks);
+}
+
+// Enqueue one evaluation (arguments already checked, n > 0).
+static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cudaStream_t s,
+                   uint32_t desc) {
+  const FuncEntry &fe = g_table[func];
+  int fm = resolve_form(fe, form);
+  if (fm < 0) return CRM_ERR_FORM;
+  Workspace *w = nullptr;
+  int st = get_ws(s, kDefaultCap, &w);
+  if (st) return st;
+  KArgs a;
+  fill_geometry(fe, in, out, n, a);
+  a.hdr = w->hdr;
+  a.q = w->q;
+  a.cap = w->cap;
+  a.force_hard = g_force_slow;
+  a.desc = desc;
+  int ui = unroll_of(func, fm);
+  int sms = dev_sms();
+  int grid = main_grid(fe, a, ui, sms, blocks_per_sm(fe.main_sym[fm][ui]));
   cudaError_t e = cudaMemsetAsync(&w->hdr->count, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e);
   e = fe.main[fm][ui](a, grid, s);
@@ -392,6 +410,7 @@ const char *crm_status_str(int status) {
     case CRM_ERR_CAPTURE: return "workspace must grow during stream capture";
     case CRM_ERR_ARG: return "invalid argument";
     case CRM_ERR_NODEV: return "no CUDA device";
+    case CRM_ERR_SIZE: return "n exceeds CRM_NOALLOC_MAX_ELEMS for crm_eval_noalloc";
   }
   return "unknown status";
 }

@@ -100,6 +100,34 @@ CRM_DEV Pair<double> dd_div(Pair<double> a, Pair<double> b) {
 CRM_DEV Pair<double> dd_neg(Pair<double> a) { return {-a.hi, -a.lo}; }
 CRM_DEV Pair<double> dd(double h, double l) { return {h, l}; }
 
+// ------------------------------------------------------------------ double-float helpers
+// Quotient of float pairs: q1 from the hardware reciprocal (relative error ~2^-22), the
+// residual a - q1 b with an exact product split, one correction: relative error < 2^-43.
+CRM_DEV Pair<float> df_div(Pair<float> a, Pair<float> b) {
+  float r = __fdividef(1.0f, b.hi);
+  float q1 = a.hi * r;
+  float p = q1 * b.hi;
+  float pl = fma_(q1, b.hi, -p);
+  float rr = (a.hi - p) - pl;
+  rr = rr + fma_(-q1, b.lo, a.lo);
+  float q2 = rr * r;
+  return fast_two_sum(q1, q2);
+}
+// Product of float pairs (relative error < 2^-45)
+CRM_DEV Pair<float> df_mul(Pair<float> a, Pair<float> b) {
+  float p = a.hi * b.hi;
+  float pl = fma_(a.hi, b.hi, -p);
+  pl = fma_(a.hi, b.lo, pl);
+  pl = fma_(a.lo, b.hi, pl);
+  return fast_two_sum(p, pl);
+}
+// Sum of float pairs without ordering assumption
+CRM_DEV Pair<float> df_add(Pair<float> a, Pair<float> b) {
+  Pair<float> s = two_sum(a.hi, b.hi);
+  s.lo = s.lo + (a.lo + b.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+
 // ------------------------------------------------------------------ rounding tests
 // Plain tier: y (a double, finite, |y| >= 2^-1000) approximates the exact value v with
 // |v - y| <= D units in the last place of y.  Returns true ("hard") unless RN_f32(v) is

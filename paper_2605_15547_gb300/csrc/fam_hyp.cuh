@@ -98,6 +98,126 @@ template <int H> CRM_DEV float hyp_plain(float x, const double *T16, bool &hard)
   return sp ? r : __double2float_rn(y);
 }
 
+// ------------------------------------------------------------------ double-float tier
+// Precise expm1 core: x log2 e = k + j/64 + g (as in exp_df) and, with T = 2^(j/64) and
+// U = T ln 2 from the 64-entry float4 table,
+//     Y = 2^-k (e^x - 1) = (T - 2^-k) + U g + T Q(g),   Q = a2 g^2 + a3 g^3 + a4 g^4 + a5 g^5,
+// where g^2 is an exact pair and a2 g^2 a pair product, so that Q is good to 2^-46 of
+// itself; T - 2^-k is an exact pair (TwoSum).  (T - 2^-k) + U g cancels exactly when
+// j = k = 0 and by at most a factor 4 otherwise.  Error (relative to Y): 2^-48 |t| from
+// the reduction of t = x log2 e (below 2^-41 at |t| = 128, where nothing cancels),
+// 2^-44 elsewhere after cancellation; the a6 g^6 remainder 2^-51.7.  The derived
+// functions add one pair division or product (2^-43): all stay below 2^-40, within the
+// 2^-37 that hard_df allows.
+struct DFY {
+  float s, l;  // Y = s + l, |l| <= ulp(s)/2
+  int k;       // e^x - 1 = 2^k Y
+};
+
+CRM_DEV DFY expm1_df_core(float x, const float4 *T64U) {
+  float th = x * CRM_LOG2E_F0;
+  float tl = fma_(x, CRM_LOG2E_F0, -th);
+  tl = fma_(x, CRM_LOG2E_F1, tl);
+  float sh = fma_(th, 64.0f, CRM_SHIFTER_F);
+  int N = (int)(fbits(sh) - fbits(CRM_SHIFTER_F));
+  float nf = sh - CRM_SHIFTER_F;
+  float f = fma_(nf, -0.015625f, th);
+  float gh = f + tl;
+  float gl = tl - (gh - f);
+  float4 T = T64U[N & 63];
+  int k = N >> 6;
+  // Q(g) as a pair
+  float q2 = gh * gh;
+  float q2l = fma_(gh, gh, -q2);
+  q2l = fma_(2.0f * gh, gl, q2l);
+  float Qh = CRM_EXP2_A2_HI_F * q2;
+  float Ql = fma_(CRM_EXP2_A2_HI_F, q2, -Qh);
+  Ql = fma_(CRM_EXP2_A2_HI_F, q2l, Ql);
+  Ql = fma_(CRM_EXP2_A2_LO_F, q2, Ql);
+  float tail = fma_(gh, fma_(gh, CRM_EXP2_A5_F, CRM_EXP2_A4_F), CRM_EXP2_A3_F);
+  Ql = fma_(q2 * gh, tail, Ql);
+  // T - 2^-k (2^-k negligible against T >= 1 when k > 100)
+  float m = k > 100 ? 0.0f : -bitsf((uint32_t)(127 - k) << 23);
+  Pair<float> c = two_sum(T.x, m);
+  float cl = c.lo + T.y;
+  // U g
+  float u = T.z * gh;
+  float ul = fma_(T.z, gh, -u);
+  ul = fma_(T.z, gl, ul);
+  ul = fma_(T.w, gh, ul);
+  // T Q
+  float tq = T.x * Qh;
+  float tql = fma_(T.x, Qh, -tq);
+  tql = fma_(T.x, Ql, tql);
+  tql = fma_(T.y, Qh, tql);
+  Pair<float> s1 = two_sum(c.hi, u);
+  Pair<float> s2 = fast_two_sum(s1.hi, tq);  // |s1| >= |tq| (see above)
+  float lo = (s1.lo + s2.lo) + (cl + (ul + tql));
+  float sh2 = s2.hi + lo;
+  float l2 = lo - (sh2 - s2.hi);
+  return {sh2, l2, k};
+}
+
+CRM_DEV float pow2f_exact(int k) { return bitsf((uint32_t)(k + 127) << 23); }  // k in [-126, 127]
+CRM_DEV float scale_f(float y, int k) { return bitsf(fbits(y) + ((uint32_t)k << 23)); }
+
+template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard) {
+  float ax = fabsf(x);
+  bool nan = x != x;
+  bool tiny = ax < 0x1p-25f;  // the correctly rounded result is x itself (or 1 for cosh)
+  float rsp;
+  bool sp;
+  if (H == HYP_EXPM1) {
+    sp = nan || tiny || x > CRM_EXPF_X_OVF || x < CRM_EXPM1F_X_MONE;
+    rsp = nan ? qnan_of(x) : (tiny ? x : (x > 0.0f ? CRM_INF_F : -1.0f));
+  } else if (H == HYP_SINH) {
+    sp = nan || tiny || ax > CRM_SINHF_X_OVF;
+    rsp = nan ? qnan_of(x) : (tiny ? x : copysignf(CRM_INF_F, x));
+  } else if (H == HYP_COSH) {
+    sp = nan || tiny || ax > CRM_SINHF_X_OVF;
+    rsp = nan ? qnan_of(x) : (tiny ? 1.0f : CRM_INF_F);
+  } else {
+    sp = nan || tiny || ax > CRM_TANHF_X_ONE;
+    rsp = nan ? qnan_of(x) : (tiny ? x : copysignf(1.0f, x));
+  }
+  float arg = H == HYP_EXPM1 ? x : (H == HYP_TANH ? 2.0f * ax : ax);
+  arg = sp ? 0.5f : arg;
+  DFY Y = expm1_df_core(arg, T64U);
+  Pair<float> r;
+  int sc = 0;
+  if (H == HYP_EXPM1) {
+    r = {Y.s, Y.l};
+    sc = Y.k;
+  } else if (H == HYP_TANH) {
+    // tanh a = Y / (Y + 2^(1-k)) with e^(2a) - 1 = 2^k Y
+    Pair<float> d = two_sum(Y.s, pow2f_exact(1 - Y.k));
+    d.lo = d.lo + Y.l;
+    r = df_div({Y.s, Y.l}, d);
+  } else {
+    float pk = Y.k > 100 ? 0.0f : pow2f_exact(-Y.k);
+    Pair<float> P = two_sum(Y.s, pk);  // P = 2^-k e^a
+    P.lo = P.lo + Y.l;
+    Pair<float> R = df_div({pk, 0.0f}, P);  // 2^-2k e^-a ... = 2^-k / P
+    if (H == HYP_SINH) {
+      // sinh a = 2^(k-1) Y (1 + R)
+      Pair<float> onep = fast_two_sum(1.0f, R.hi);  // 1 + R as a pair (R <= 1)
+      onep.lo = onep.lo + R.lo;
+      r = df_mul({Y.s, Y.l}, onep);
+    } else {
+      // cosh a = 2^(k-1) (P + 2^-k R)
+      float rk = R.hi * pk, rkl = R.lo * pk;
+      Pair<float> S = fast_two_sum(P.hi, rk);
+      S.lo = S.lo + (P.lo + rkl);
+      r = fast_two_sum(S.hi, S.lo);
+    }
+    sc = Y.k - 1;
+  }
+  hard = !sp && hard_df(r.hi, r.lo);
+  float y = scale_f(r.hi, sc);
+  if (H == HYP_SINH || H == HYP_TANH) y = x < 0.0f ? -y : y;
+  return sp ? rsp : y;
+}
+
 // ------------------------------------------------------------------ double-double tier
 // The same formulas in double-double: g to 2^-106 (x times a three-double log2 e), the
 // double-double table, Taylor polynomials to degree 12 (2^g - 1) or 13 / 12 (odd /

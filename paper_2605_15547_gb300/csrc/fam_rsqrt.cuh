@@ -41,6 +41,32 @@ CRM_DEV float rsqrt_plain(float x, bool &hard) {
   return sp ? r : __double2float_rn(y);
 }
 
+// ------------------------------------------------------------------ double-float tier
+// y0 = hardware reciprocal square root (relative error below 2^-21; subnormal x scaled
+// by 2^24 and x >= 2^64 by 2^-64, the result back by 2^12 or 2^-32), the residual e = 1 - x y0^2 from exact pair products
+// (1 - p is exact by Sterbenz since x y0^2 is within 2^-20 of 1), and one Newton step
+// kept as a pair: y = y0 + y0 e (1/2 + 3e/8).  |e| < 2^-20: the truncation is
+// (5/16) e^3 < 2^-61, the residual is good to 2^-48 absolute, the correction product to
+// 2^-24 of itself (2^-45 of y): relative error < 2^-44.5, inside hard_df's 2^-37.
+CRM_DEV float rsqrt_df(float x, bool &hard) {
+  float r;
+  bool sp = rsqrt_special(x, r);
+  bool sub = x < 0x1p-126f, big = x >= 0x1p64f;  // keep y0^2 and its error normal
+  float xs = sp ? 1.0f : (sub ? x * 0x1p24f : (big ? x * 0x1p-64f : x));
+  float y0 = rsqrtf(xs);
+  float s = y0 * y0;
+  float sl = fma_(y0, y0, -s);
+  float p = xs * s;
+  float pl = fma_(xs, s, -p);
+  float e = (1.0f - p) - fma_(xs, sl, pl);
+  float corr = fma_(e, 0.375f, 0.5f) * e;
+  float c = y0 * corr;
+  Pair<float> y = fast_two_sum(y0, c);
+  hard = !sp && hard_df(y.hi, y.lo);
+  float out = sub ? y.hi * 0x1p12f : (big ? y.hi * 0x1p-32f : y.hi);
+  return sp ? r : out;
+}
+
 // ------------------------------------------------------------------ exact slow tier
 // Exact decision: the binary32 neighbours dn <= y <= up of the approximation and their
 // midpoint m; RN(1/sqrt(x)) is up when x m^2 < 1, dn otherwise.  If y is itself a

@@ -131,6 +131,113 @@ CRM_DEV void trig_plain(float x, const uint32_t *P, const double *SC, float *y, 
   }
 }
 
+// ------------------------------------------------------------------ double-float tier
+// The same integer reduction; the 64-bit fraction becomes a float pair without
+// conversion instructions: with F' = F + 2^63 (so f + 1/2 = F' 2^-64 >= 0), three
+// chunks of 23, 23 and 18 bits become exact floats by the 2^23 magic-number trick and
+// f = (c0 2^-23 - 1/2) + (c1 2^-46 + c2 2^-64).  Then t = f pi/64 as a pair, and
+//   cos t = 1 - t^2/2 + t^4/24 - t^6/720,  sin t = t - t^3/6 + t^5/120 - t^7/5040,
+// with t^2 and t^3/6 carried as pairs (exact FMA splits), the higher terms in float.
+// Error budget (relative to the result): f to 2^-63.6 absolute (lanes with j = 0 and
+// |f| < 2^-24, where the result is as small as t, go to the slow path: 2^-40 there);
+// pi/64 pair 2^-48; t products 2^-46; sin t, cos t 2^-45; table pairs 2^-48; the
+// rotation terms S cos t + C sin t lose at most 2^5.4: total < 2^-39, inside the 2^-37
+// that hard_df allows.
+struct TrigF {
+  Pair<float> A, B;  // sin and cos of (j pi/64 + t)
+  int q;
+  bool tiny;
+};
+
+CRM_DEV TrigF trig_df_core(float x, const uint32_t *P, const float4 *SC) {
+  float ax = fabsf(x);
+  bool small = ax < 0x1p-6f;
+  uint32_t r[4];
+  trig_window_mul<3>(small ? 1.0f : ax, P, r);
+  uint32_t Fh = ((r[2] & 0x01FFFFFFu) << 7) | (r[1] >> 25);
+  uint32_t Fl = (r[1] << 7) | (r[0] >> 25);
+  int N7 = (int)(((r[2] >> 25) + (Fh >> 31)) & 127u);
+  uint32_t Ph = Fh ^ 0x80000000u;
+  uint32_t c0 = Ph >> 9;
+  uint32_t c1 = ((Ph & 0x1FFu) << 14) | (Fl >> 18);
+  uint32_t c2 = Fl & 0x3FFFFu;
+  float f0 = bitsf(0x4B000000u | c0) - 0x1p23f;
+  float f1 = bitsf(0x4B000000u | c1) - 0x1p23f;
+  float f2 = bitsf(0x4B000000u | c2) - 0x1p23f;
+  float fh = fma_(f0, 0x1p-23f, -0.5f);
+  float fl = fma_(f1, 0x1p-46f, f2 * 0x1p-64f);
+  float th = fh * CRM_PIO64_F_HI;
+  float tl = fma_(fh, CRM_PIO64_F_HI, -th);
+  tl = fma_(fh, CRM_PIO64_F_LO, tl);
+  tl = fma_(fl, CRM_PIO64_F_HI, tl);
+  Pair<float> t = fast_two_sum(th, tl);
+  TrigF R;
+  R.tiny = !small && (N7 & 31) == 0 && fabsf(fh + fl) < 0x1p-24f;
+  t.hi = small ? ax : t.hi;
+  t.lo = small ? 0.0f : t.lo;
+  N7 = small ? 0 : N7;
+  // t^2 as a pair
+  float u = t.hi * t.hi;
+  float ul = fma_(t.hi, t.hi, -u);
+  ul = fma_(2.0f * t.hi, t.lo, ul);
+  // cos t = 1 - t^2/2 + t^4 (1/24 - t^2/720)
+  float ch = fma_(u, -0.5f, 1.0f);
+  float cl = fma_(u, -0.5f, 1.0f - ch);
+  cl = fma_(ul, -0.5f, cl);
+  cl = fma_(u * u, fma_(u, -0x1.6c16c2p-10f, 0x1.555556p-5f), cl);
+  // sin t = t - t^3/6 + t^5 (1/120 - t^2/5040)
+  float w = t.hi * u;
+  float wl = fma_(t.hi, u, -w);
+  wl = fma_(t.hi, ul, wl);
+  wl = fma_(t.lo, u, wl);
+  float s3 = w * CRM_INV6_F_HI;
+  float s3l = fma_(w, CRM_INV6_F_HI, -s3);
+  s3l = fma_(w, CRM_INV6_F_LO, s3l);
+  s3l = fma_(wl, CRM_INV6_F_HI, s3l);
+  float sh = t.hi - s3;
+  float sl = (t.hi - sh) - s3;  // Fast2Sum: |t| > |t^3/6|
+  sl = sl + (t.lo - s3l);
+  sl = fma_(w * u, fma_(u, -0x1.a01a02p-13f, 0x1.111112p-7f), sl);
+  // rotation by j pi/64
+  int j = N7 & 31;
+  float4 T = SC[j];  // (sin hi, lo, cos hi, lo)
+  Pair<float> S = {T.x, T.y}, C = {T.z, T.w}, ct = {ch, cl}, st = {sh, sl};
+  Pair<float> a1 = df_mul(S, ct), a2 = df_mul(C, st);
+  Pair<float> b1 = df_mul(C, ct), b2 = df_mul(S, st);
+  R.A = df_add(a1, a2);
+  R.B = df_add(b1, -b2);
+  R.q = N7 >> 5;
+  return R;
+}
+
+template <int KIND>
+CRM_DEV void trig_df(float x, const uint32_t *P, const float4 *SC, float *y, bool &hard) {
+  float rsp;
+  bool sp = trig_special(x, rsp);
+  TrigF R = trig_df_core(sp ? 1.0f : x, P, SC);
+  Pair<float> sn, cs;
+  trig_rotate<Pair<float>>(KIND, x, R.q, R.A, R.B, sn, cs);
+  bool zero = x == 0.0f;
+  if (KIND == TRIG_TAN) {
+    Pair<float> t = df_div(sn, cs);
+    hard = !sp && !zero && (R.tiny || hard_df(t.hi, t.lo));
+    y[0] = sp ? rsp : (zero ? x : t.hi);
+    return;
+  }
+  bool hs = hard_df(sn.hi, sn.lo), hc = hard_df(cs.hi, cs.lo);
+  if (KIND == TRIG_SIN) {
+    hard = !sp && !zero && (R.tiny || hs);
+    y[0] = sp ? rsp : (zero ? x : sn.hi);
+  } else if (KIND == TRIG_COS) {
+    hard = !sp && (R.tiny || hc);
+    y[0] = sp ? rsp : cs.hi;
+  } else {
+    hard = !sp && (R.tiny || (hs && !zero) || hc);
+    y[0] = sp ? rsp : (zero ? x : sn.hi);
+    y[1] = sp ? rsp : cs.hi;
+  }
+}
+
 // ------------------------------------------------------------------ double-double tier
 // 160-bit window: the fraction to 128 bits (error < 2^-127.6), t = f pi/64 in
 // double-double, sin/cos t by Taylor polynomials to degree 15 / 14 (remainders < 2^-118),

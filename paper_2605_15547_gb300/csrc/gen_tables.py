@@ -179,6 +179,9 @@ const_f("CRM_EXP2_A1_HI_F", a1[0], "ln 2 (float hi)")
 const_f("CRM_EXP2_A1_LO_F", a1[1], "ln 2 (float lo)")
 for k in (2, 3, 4, 5):
     const_f(f"CRM_EXP2_A{k}_F", f(coef[k]), f"(ln 2)^{k}/{k}!")
+a2 = split(coef[2], f, 2)
+const_f("CRM_EXP2_A2_HI_F", a2[0], "(ln 2)^2/2 (float hi)")
+const_f("CRM_EXP2_A2_LO_F", a2[1], "(ln 2)^2/2 (float lo)")
 emit()
 # conversion constants t = x * C
 for nm, C in (("LOG2E", LOG2E), ("LOG2_10", LOG2_10)):
@@ -301,6 +304,9 @@ const_d("CRM_PIO64_D_LO", pp[1])
 pf = split(PIO64, f, 2)
 const_f("CRM_PIO64_F_HI", pf[0])
 const_f("CRM_PIO64_F_LO", pf[1])
+i6 = split(mp.mpf(1) / 6, f, 2)
+const_f("CRM_INV6_F_HI", i6[0])
+const_f("CRM_INV6_F_LO", i6[1])
 # (-1)^k / (2k+1)! and (-1)^k/(2k)! as doubles and double-doubles
 arr_d("CRM_SIN_TAYLOR_D", [d(mp.mpf((-1) ** k) / mp.factorial(2 * k + 1)) for k in range(10)],
       "(-1)^k/(2k+1)!, k = 0..9")

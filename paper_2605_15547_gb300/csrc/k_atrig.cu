@@ -22,7 +22,7 @@ struct FnRsqrt {
   template <int FORM> static constexpr int tab_bytes() { return 0; }
   template <int FORM> CRM_DEV static void load(unsigned char *) {}
   template <int FORM> CRM_DEV static void eval(float x, const void *, float *y, bool &h) {
-    y[0] = rsqrt_plain(x, h);
+    y[0] = FORM == 1 ? rsqrt_plain(x, h) : rsqrt_df(x, h);
   }
   CRM_DEV static void slow(float x, float *y, bool &u) { y[0] = rsqrt_slow(x, u); }
 };
@@ -31,7 +31,7 @@ void register_atrig(FuncEntry *t) {
   set_entry<FnAtrig<AT_ASIN>, true, false>(t[12]);  // CRM_ASINF
   set_entry<FnAtrig<AT_ACOS>, true, false>(t[13]);  // CRM_ACOSF
   set_entry<FnAtrig<AT_ATAN>, true, false>(t[14]);  // CRM_ATANF
-  set_entry<FnRsqrt, true, false>(t[18]);           // CRM_RSQRTF
+  set_entry<FnRsqrt, true, true>(t[18]);           // CRM_RSQRTF
 }
 
 }  // namespace crm

@@ -15,7 +15,7 @@ from . import _lib as L
 from ._lib import F64_FUNCS, FORMS, FUNC_ID, FUNCS, CrmError, crm_desc_t, crm_stats_t
 
 __all__ = ["eval", "eval_into", "eval_host", "eval_batch", "stats", "stats_reset",
-           "set_form", "set_force_slow", "reserve", "FUNCS", "FORMS", "CrmError", "version"]
+           "set_form", "set_force_slow", "set_batch_tile", "reserve", "FUNCS", "FORMS", "CrmError", "version"]
 
 
 def _stream_ptr(stream=None):
@@ -113,6 +113,11 @@ def stats_reset(stream=None) -> None:
 
 def set_form(form) -> None:
     L.check(L.lib().crm_set_form(_form(form)))
+
+
+def set_batch_tile(log2_elems: int) -> None:
+    """Tile size of the batching form: 2^log2_elems elements."""
+    L.check(L.lib().crm_set_batch_tile(int(log2_elems)))
 
 
 def set_force_slow(on: bool) -> None:

@@ -61,6 +61,8 @@ def _lib():
                 lib.crm_eval_batch.argtypes = [ctypes.POINTER(crm_desc_t), c_int, c_int, vp]
                 lib.crm_set_form.argtypes = [c_int]
                 lib.crm_set_force_slow.argtypes = [c_int]
+                lib.crm_set_batch_tile.argtypes = [c_int]
+                lib.crm_eval_noalloc.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, vp]
                 lib.crm_reserve.argtypes = [c_u64, c_int, vp]
                 lib.crm_stats.argtypes = [vp, ctypes.POINTER(crm_stats_t)]
                 lib.crm_stats_reset.argtypes = [vp]

@@ -1,0 +1,35 @@
+// crm_batch.h -- device descriptors of the batching form.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "crm_ws.h"
+
+namespace crm {
+
+// One array of a batch, as the kernels see it (32 bytes).
+struct BatchDesc {
+  const void *in;
+  void *out;
+  uint64_t n;
+  uint64_t tile0;  // index of the array's first tile in the whole batch
+  int32_t func;
+  int32_t flags;   // bit 0: input and output(s) 16-byte aligned (vector loop allowed)
+};
+
+struct BatchArgs {
+  const BatchDesc *descs;
+  int count;
+  int tile_shift;           // tiles of 2^tile_shift elements
+  uint64_t total_tiles;
+  uint64_t tiles_per_block;
+  crm_ws_header *hdr;
+  crm_queue_entry *q;
+  uint64_t cap;
+  int force_hard;
+};
+
+cudaError_t launch_batch(const BatchArgs &b, int form, int grid, int slow_grid, cudaStream_t s);
+const void *batch_kernel_symbol(int form);
+
+}  // namespace crm

@@ -1,0 +1,110 @@
+// crm_fns.cuh -- the per-function descriptors used by the array, slow and batch kernels:
+// shared-memory table layout, the fast-tier evaluator for each form and the exact slow
+// path (see the Fn interface in crm_kernels.cuh).
+#pragma once
+#include "crm_kernels.cuh"
+#include "fam_atrig.cuh"
+#include "fam_exp.cuh"
+#include "fam_hyp.cuh"
+#include "fam_log.cuh"
+#include "fam_rsqrt.cuh"
+#include "fam_trig.cuh"
+
+namespace crm {
+
+template <int KIND> struct FnExp {
+  using T = float;
+  static constexpr int NOUT = 1;
+  template <int FORM> static constexpr int tab_bytes() { return FORM == 1 ? 16 * 8 : 64 * 16; }
+  template <int FORM> CRM_DEV static void load(unsigned char *sm) {
+    copy_tab(sm, FORM == 1 ? (const void *)CRM_EXP2_T16_D : (const void *)CRM_EXP2_T64U_DF, tab_bytes<FORM>());
+  }
+  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h) {
+    if (FORM == 1)
+      y[0] = exp_plain<KIND>(x, (const double *)sm, h);
+    else
+      y[0] = exp_df<KIND>(x, (const float4 *)sm, h);
+  }
+  CRM_DEV static void slow(float x, float *y, bool &u) { y[0] = exp_slow<KIND>(x, u); }
+};
+
+template <int KIND> struct FnLog {
+  using T = float;
+  static constexpr int NOUT = 1;
+  template <int FORM> static constexpr int tab_bytes() { return 97 * 16; }
+  template <int FORM> CRM_DEV static void load(unsigned char *sm) {
+    copy_tab(sm, FORM == 1 ? (const void *)CRM_LN_T97_D : (const void *)log_tab_df<KIND>(), tab_bytes<FORM>());
+  }
+  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h) {
+    if (FORM == 1)
+      y[0] = log_plain<KIND>(x, (const double2 *)sm, h);
+    else
+      y[0] = log_df<KIND>(x, (const float4 *)sm, h);
+  }
+  CRM_DEV static void slow(float x, float *y, bool &u) { y[0] = log_slow<KIND>(x, u); }
+};
+
+template <int H> struct FnHyp {
+  using T = float;
+  static constexpr int NOUT = 1;
+  template <int FORM> static constexpr int tab_bytes() { return FORM == 1 ? 16 * 8 : 64 * 16; }
+  template <int FORM> CRM_DEV static void load(unsigned char *sm) {
+    copy_tab(sm, FORM == 1 ? (const void *)CRM_EXP2_T16_D : (const void *)CRM_EXP2_T64U_DF, tab_bytes<FORM>());
+  }
+  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h) {
+    if (FORM == 1)
+      y[0] = hyp_plain<H>(x, (const double *)sm, h);
+    else
+      y[0] = hyp_df<H>(x, (const float4 *)sm, h);
+  }
+  CRM_DEV static void slow(float x, float *y, bool &u) { y[0] = hyp_slow<H>(x, u); }
+};
+
+template <int KIND> struct FnTrig {
+  using T = float;
+  static constexpr int NOUT = KIND == TRIG_SINCOS ? 2 : 1;
+  // shared memory: 16 words of 2/pi, then the (sin, cos)(j pi/64) table (double or
+  // float-pair entries, 16 bytes each)
+  template <int FORM> static constexpr int tab_bytes() { return 64 + 32 * 16; }
+  template <int FORM> CRM_DEV static void load(unsigned char *sm) {
+    copy_tab(sm, CRM_TWO_OVER_PI_W, 64);
+    copy_tab(sm + 64, FORM == 1 ? (const void *)CRM_SINCOS_T32_D : (const void *)CRM_SINCOS_T32_DF, 32 * 16);
+  }
+  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h) {
+    const unsigned char *b = (const unsigned char *)sm;
+    if (FORM == 1)
+      trig_plain<KIND>(x, (const uint32_t *)b, (const double *)(b + 64), y, h);
+    else
+      trig_df<KIND>(x, (const uint32_t *)b, (const float4 *)(b + 64), y, h);
+  }
+  CRM_DEV static void slow(float x, float *y, bool &u) { trig_slow<KIND>(x, y, u); }
+};
+
+template <int KIND> struct FnAtrig {
+  using T = float;
+  static constexpr int NOUT = 1;
+  template <int FORM> static constexpr int tab_bytes() { return 18 * 8; }
+  template <int FORM> CRM_DEV static void load(unsigned char *sm) {
+    copy_tab(sm, FORM == 1 ? (const void *)CRM_ATAN_T17_D : (const void *)CRM_ATAN_T17_DF, 18 * 8);
+  }
+  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h) {
+    if (FORM == 1)
+      y[0] = atrig_plain<KIND>(x, (const double *)sm, h);
+    else
+      y[0] = atrig_df<KIND>(x, (const float2 *)sm, h);
+  }
+  CRM_DEV static void slow(float x, float *y, bool &u) { y[0] = atrig_slow<KIND>(x, u); }
+};
+
+struct FnRsqrt {
+  using T = float;
+  static constexpr int NOUT = 1;
+  template <int FORM> static constexpr int tab_bytes() { return 0; }
+  template <int FORM> CRM_DEV static void load(unsigned char *) {}
+  template <int FORM> CRM_DEV static void eval(float x, const void *, float *y, bool &h) {
+    y[0] = FORM == 1 ? rsqrt_plain(x, h) : rsqrt_df(x, h);
+  }
+  CRM_DEV static void slow(float x, float *y, bool &u) { y[0] = rsqrt_slow(x, u); }
+};
+
+}  // namespace crm

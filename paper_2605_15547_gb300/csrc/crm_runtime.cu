@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/crm.h"
+#include "crm_batch.h"
 #include "crm_internal.h"
 #include "crm_registry.h"
 
@@ -51,6 +52,11 @@ struct Workspace {
   crm_ws_header *hdr = nullptr;  // device
   crm_queue_entry *q = nullptr;  // device
   uint64_t cap = 0;
+  // batching form: device descriptors and their page-locked host staging copy
+  BatchDesc *bdesc = nullptr;
+  BatchDesc *bstage = nullptr;
+  int bcap = 0;
+  cudaEvent_t bcopied = nullptr;  // the last descriptor upload has completed
 };
 
 struct DevInfo {
@@ -240,6 +246,33 @@ static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cu
   return CRM_OK;
 }
 
+// ------------------------------------------------------------------ batch buffers
+static int g_batch_tile_shift = 14;  // the autotuner may change it (crm_set_batch_tile)
+
+static int batch_buffers(cudaStream_t s, Workspace *w, int count) {
+  if (w->bcap >= count) return CRM_OK;
+  if (capturing(s)) return CRM_ERR_CAPTURE;
+  cudaError_t e;
+  if (w->bdesc) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    cudaFree(w->bdesc);
+    cudaFreeHost(w->bstage);
+    w->bdesc = nullptr;
+    w->bstage = nullptr;
+    w->bcap = 0;
+  }
+  int want = count < 1024 ? 1024 : count;
+  if (cudaMalloc((void **)&w->bdesc, (size_t)want * sizeof(BatchDesc)) != cudaSuccess) return CRM_ERR_NOMEM;
+  if (cudaMallocHost((void **)&w->bstage, (size_t)want * sizeof(BatchDesc)) != cudaSuccess) return CRM_ERR_NOMEM;
+  if (!w->bcopied) {
+    e = cudaEventCreateWithFlags(&w->bcopied, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  w->bcap = want;
+  return CRM_OK;
+}
+
 // ------------------------------------------------------------------ host-buffer path
 // Chunks of the host array go through two internal streams: while one stream computes a
 // chunk, the copy engines move the neighbouring chunks in and out (H2D and D2H overlap
@@ -348,7 +381,9 @@ int crm_reserve(uint64_t max_elems, int max_arrays, void *stream) {
   Workspace *w;
   uint64_t cap = kDefaultCap;
   (void)max_elems;
-  return get_ws((cudaStream_t)stream, cap, &w);
+  int st = get_ws((cudaStream_t)stream, cap, &w);
+  if (st) return st;
+  return max_arrays > 0 ? batch_buffers((cudaStream_t)stream, w, max_arrays) : CRM_OK;
 }
 
 int crm_stats(void *stream, crm_stats_t *out) {
@@ -393,8 +428,81 @@ int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, u
 }
 
 int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
-  (void)descs; (void)count; (void)form; (void)stream;
-  return CRM_ERR_FORM;
+  ensure_init();
+  if (count < 0) return CRM_ERR_ARG;
+  if (count == 0) return CRM_OK;
+  if (!descs) return CRM_ERR_NULL;
+  if (form < CRM_FORM_AUTO || form > CRM_FORM_DF32) return CRM_ERR_FORM;
+  if (count > (1 << 23)) return CRM_ERR_ARG;
+  for (int i = 0; i < count; i++) {
+    const crm_desc_t &d = descs[i];
+    int st = check_args(d.func_id, d.dtype, d.in, d.out, d.n);
+    if (st) return st;
+    if (d.func_id >= CRM_EXP2) return CRM_ERR_FORM;  // binary64 functions: use crm_eval
+    if (resolve_form(g_table[d.func_id], form) < 0) return CRM_ERR_FORM;
+  }
+  int fm = form == CRM_FORM_PLAIN_FP64 ? 1 : 2;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w = nullptr;
+  int st = get_ws(s, kDefaultCap, &w);
+  if (st) return st;
+  st = batch_buffers(s, w, count);
+  if (st) return st;
+  bool cap = capturing(s);
+  cudaError_t e;
+  if (!cap) {  // the staging copy of the previous batch must have been consumed
+    e = cudaEventSynchronize(w->bcopied);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  const int shift = g_batch_tile_shift;
+  uint64_t tiles = 0;
+  int used = 0;
+  for (int i = 0; i < count; i++) {
+    const crm_desc_t &d = descs[i];
+    if (d.n == 0) continue;
+    BatchDesc &b = w->bstage[used++];
+    b.in = d.in;
+    b.out = d.out;
+    b.n = d.n;
+    b.tile0 = tiles;
+    b.func = d.func_id;
+    uintptr_t ia = (uintptr_t)d.in, oa = (uintptr_t)d.out;
+    bool vec = (ia % 16) == 0 && (oa % 16) == 0 && (d.func_id != CRM_SINCOSF || (d.n * 4) % 16 == 0);
+    b.flags = vec ? 1 : 0;
+    tiles += (d.n + (1ull << shift) - 1) >> shift;
+  }
+  if (used == 0) return CRM_OK;
+  e = cudaMemcpyAsync(w->bdesc, w->bstage, used * sizeof(BatchDesc), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (!cap) {
+    e = cudaEventRecord(w->bcopied, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  int sms = dev_sms();
+  int bps = blocks_per_sm(batch_kernel_symbol(fm));
+  uint64_t grid = (uint64_t)sms * bps;
+  if (grid > tiles) grid = tiles;
+  BatchArgs a;
+  a.descs = w->bdesc;
+  a.count = used;
+  a.tile_shift = shift;
+  a.total_tiles = tiles;
+  a.tiles_per_block = (tiles + grid - 1) / grid;
+  a.hdr = w->hdr;
+  a.q = w->q;
+  a.cap = w->cap;
+  a.force_hard = g_force_slow;
+  e = cudaMemsetAsync(&w->hdr->count, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = launch_batch(a, fm, (int)grid, sms * 2, s);
+  return e == cudaSuccess ? CRM_OK : cuda_fail(e);
+}
+
+int crm_set_batch_tile(int log2_elems) {
+  ensure_init();
+  if (log2_elems < 8 || log2_elems > 24) return CRM_ERR_ARG;
+  g_batch_tile_shift = log2_elems;
+  return CRM_OK;
 }
 
 const char *crm_status_str(int status) {
@@ -425,6 +533,9 @@ void crm_shutdown(void) {
     cudaSetDevice(kv.first.first);
     if (kv.second.q) cudaFree(kv.second.q);
     if (kv.second.hdr) cudaFree(kv.second.hdr);
+    if (kv.second.bdesc) cudaFree(kv.second.bdesc);
+    if (kv.second.bstage) cudaFreeHost(kv.second.bstage);
+    if (kv.second.bcopied) cudaEventDestroy(kv.second.bcopied);
     cudaSetDevice(cur);
   }
   g_ws.clear();

@@ -86,6 +86,91 @@ template <int KIND> CRM_DEV float atrig_plain(float x, const double *AT, bool &h
   return sp ? rsp : __double2float_rn(r);
 }
 
+// ------------------------------------------------------------------ double-float tier
+// The same core on float pairs.  c_j q.hi is split exactly by FMA so that p - c_j q is
+// exact in its leading word (Sterbenz: p/(c_j q) is within [1/2, 2] when j >= 1);
+// t = num/den by df_div; atan t = t - t^3/3 + t^5 (1/5 - t^2/7) with t^3/3 as a pair.
+// s = sqrt(1 - x^2): 1 - x^2 as an exact pair, sqrtf plus one Newton correction.
+// Error: t to 2^-43 (2^-43 of t when j = 0), atan t to 2^-45 of itself, table and pi
+// pairs 2^-48, the sum at most doubles the errors: < 2^-41, inside hard_df's 2^-37.
+CRM_DEV Pair<float> atan_ratio_df(Pair<float> a, Pair<float> b, const float2 *AT) {
+  bool sw = a.hi > b.hi;
+  Pair<float> p = sw ? b : a, q = sw ? a : b;
+  float rf = __fdividef(p.hi, q.hi);  // only picks j
+  int j = __float2int_rn(rf * 16.0f);
+  j = j < 0 ? 0 : (j > 16 ? 16 : j);
+  float c = (float)j * 0.0625f;
+  float m = c * q.hi;
+  float ml = fma_(c, q.hi, -m);
+  float nh = p.hi - m;  // exact
+  float nl = (p.lo - ml) - c * q.lo;
+  Pair<float> num = fast_two_sum(nh, nl);
+  float d = c * p.hi;
+  float dl = fma_(c, p.hi, -d);
+  Pair<float> den = fast_two_sum(q.hi, d);
+  den.lo = den.lo + (q.lo + dl + c * p.lo);
+  Pair<float> t = df_div(num, den);
+  // atan t
+  float u = t.hi * t.hi;
+  float ul = fma_(t.hi, t.hi, -u);
+  ul = fma_(2.0f * t.hi, t.lo, ul);
+  float w = t.hi * u;
+  float wl = fma_(t.hi, u, -w);
+  wl = fma_(t.hi, ul, wl);
+  wl = fma_(t.lo, u, wl);
+  float s3 = w * CRM_INV3_F_HI;
+  float s3l = fma_(w, CRM_INV3_F_HI, -s3);
+  s3l = fma_(w, CRM_INV3_F_LO, s3l);
+  s3l = fma_(wl, CRM_INV3_F_HI, s3l);
+  float ah = t.hi - s3;
+  float al = (t.hi - ah) - s3;
+  al = al + (t.lo - s3l);
+  al = fma_(w * u, fma_(u, -0x1.249250p-3f, 0x1.99999ap-3f), al);  // t^5 (1/5 - t^2/7)
+  float2 A = AT[j];
+  Pair<float> r = df_add({A.x, A.y}, {ah, al});
+  if (sw) r = df_add({CRM_PIO2_F_HI, CRM_PIO2_F_LO}, -r);
+  return r;
+}
+
+template <int KIND> CRM_DEV float atrig_df(float x, const float2 *AT, bool &hard) {
+  float rsp;
+  bool sp = atrig_special<KIND>(x, rsp);
+  float xs = sp ? 0.5f : x;
+  float ax = fabsf(xs);
+  Pair<float> a, b;
+  bool flip = false;
+  if (KIND == AT_ATAN) {
+    bool inf = ax == CRM_INF_F;
+    a = {inf ? 1.0f : ax, 0.0f};
+    b = {inf ? 0.0f : 1.0f, 0.0f};
+  } else {
+    // 1 - x^2 exactly as a pair, then its square root as a pair
+    float p = ax * ax;
+    float pl = fma_(ax, ax, -p);
+    Pair<float> d1 = fast_two_sum(1.0f, -p);  // 1 >= p
+    Pair<float> dd_ = fast_two_sum(d1.hi, d1.lo - pl);
+    float s0 = sqrtf(dd_.hi);
+    float s2 = s0 * s0;
+    float s2l = fma_(s0, s0, -s2);
+    float res = ((dd_.hi - s2) - s2l) + dd_.lo;
+    float corr = s0 > 0.0f ? res * __fdividef(0.5f, s0) : 0.0f;
+    Pair<float> s = fast_two_sum(s0, corr);
+    if (KIND == AT_ASIN) {
+      a = {ax, 0.0f};
+      b = s;
+    } else {
+      a = s;
+      b = {ax, 0.0f};
+      flip = xs < 0.0f;
+    }
+  }
+  Pair<float> r = atan_ratio_df(a, b, AT);
+  if (KIND == AT_ACOS && flip) r = df_add({CRM_PI_F_HI, CRM_PI_F_LO}, -r);
+  hard = !sp && hard_df(r.hi, r.lo);
+  float y = (KIND != AT_ACOS && x < 0.0f) ? -r.hi : r.hi;
+  return sp ? rsp : y;
+}
+
 // ------------------------------------------------------------------ double-double tier
 // s by one Newton step in double-double, t by a double-double division, atan(t) to
 // degree 25 (remainder < 2^-130), double-double table and pi/2.  Error < 2^-96.

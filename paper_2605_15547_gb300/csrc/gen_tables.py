@@ -304,6 +304,9 @@ const_d("CRM_PIO64_D_LO", pp[1])
 pf = split(PIO64, f, 2)
 const_f("CRM_PIO64_F_HI", pf[0])
 const_f("CRM_PIO64_F_LO", pf[1])
+i3 = split(mp.mpf(1) / 3, f, 2)
+const_f("CRM_INV3_F_HI", i3[0])
+const_f("CRM_INV3_F_LO", i3[1])
 i6 = split(mp.mpf(1) / 6, f, 2)
 const_f("CRM_INV6_F_HI", i6[0])
 const_f("CRM_INV6_F_LO", i6[1])

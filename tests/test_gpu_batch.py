@@ -1,0 +1,127 @@
+"""GPU tests of the batching form (crm_eval_batch): many arrays of mixed functions and
+uneven lengths in one persistent launch must give exactly the per-array results, which
+the parity suite ties to the oracle; a sample is also checked against the oracle here.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2605_15547_gb300 as crm  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+from paper_2605_15547_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    crm.set_force_slow(False)
+    yield
+    crm.set_force_slow(False)
+
+
+def make_batch(count, max_log2, seed, misalign=True):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    items = []
+    for i in range(count):
+        f = W.F32_FUNCS[int(rng.integers(0, len(W.F32_FUNCS)))]
+        n = int(round(2 ** rng.uniform(0, max_log2)))
+        off = int(rng.integers(0, 4)) if misalign else 0
+        x = W.domain_bits(f, n, rng).view(np.float32)
+        buf = torch.zeros(n + off + 4, dtype=torch.float32, device="cuda")
+        buf[off:off + n] = torch.from_numpy(x).cuda()
+        rows = 2 if f == "sincosf" else 1
+        oo = int(rng.integers(0, 4)) if misalign else 0
+        obuf = torch.full((rows * n + oo + 4,), float("nan"), device="cuda")
+        items.append((f, buf[off:off + n], obuf[oo:oo + rows * n], x))
+    return items
+
+
+@pytest.mark.parametrize("form", ["plain", "df"])
+@pytest.mark.parametrize("tile", [10, 14])
+def test_batch_matches_single_calls(form, tile):
+    items = make_batch(300, 15, seed=100 + tile)
+    crm.set_batch_tile(tile)
+    try:
+        crm.eval_batch([(f, x, y) for f, x, y, _ in items], form=form)
+    finally:
+        crm.set_batch_tile(14)
+    torch.cuda.synchronize()
+    for f, x, y, _ in items:
+        ref = torch.empty_like(y)
+        crm.eval_into(f, x, ref, form=form)
+        torch.cuda.synchronize()
+        a = y.cpu().numpy().view(np.uint32)
+        b = ref.cpu().numpy().view(np.uint32)
+        assert np.array_equal(a, b), f"{f}: {int(np.count_nonzero(a != b))} differ"
+
+
+def test_batch_against_oracle_sample():
+    items = make_batch(120, 12, seed=7)
+    crm.eval_batch([(f, x, y) for f, x, y, _ in items])
+    torch.cuda.synchronize()
+    for f, x, y, xh in items:
+        got = y.cpu().numpy().view(np.uint32)
+        ref = O.eval_bits(f, xh.view(np.uint32)).reshape(-1)
+        assert np.array_equal(got, ref), f
+    assert crm.stats()["unresolved_total"] == 0
+
+
+def test_batch_forced_slow_path():
+    items = make_batch(100, 12, seed=9)
+    crm.set_force_slow(True)
+    try:
+        crm.eval_batch([(f, x, y) for f, x, y, _ in items])
+        torch.cuda.synchronize()
+    finally:
+        crm.set_force_slow(False)
+    for f, x, y, xh in items:
+        got = y.cpu().numpy().view(np.uint32)
+        ref = O.eval_bits(f, xh.view(np.uint32)).reshape(-1)
+        assert np.array_equal(got, ref), f
+
+
+def test_batch_graph_capture_and_replay():
+    items = make_batch(64, 14, seed=11, misalign=False)
+    s = torch.cuda.Stream()
+    crm.reserve(1 << 24, 4096, stream=s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        crm.eval_batch([(f, x, y) for f, x, y, _ in items], stream=s)  # warm-up
+    s.synchronize()
+    for _, _, y, _ in items:
+        y.fill_(float("nan"))
+    with torch.cuda.graph(g, stream=s):
+        crm.eval_batch([(f, x, y) for f, x, y, _ in items], stream=s)
+    for rep in range(3):
+        for _, _, y, _ in items:
+            y.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for f, x, y, xh in items:
+            got = y.cpu().numpy().view(np.uint32)
+            ref = O.eval_bits(f, xh.view(np.uint32)).reshape(-1)
+            assert np.array_equal(got, ref), (rep, f)
+
+
+def test_single_call_graph_capture():
+    x = torch.from_numpy(W.domain_bits("logf", 1 << 20, W.rng_for(2, "logf")).view(np.float32)).cuda()
+    y = torch.empty_like(x)
+    s = torch.cuda.Stream()
+    crm.reserve(1 << 24, 0, stream=s)
+    with torch.cuda.stream(s):
+        crm.eval_into("logf", x, y, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        crm.eval_into("logf", x, y, stream=s)
+    y.fill_(0)
+    g.replay()
+    torch.cuda.synchronize()
+    ref = O.eval_bits("logf", x.cpu().numpy().view(np.uint32))
+    assert np.array_equal(y.cpu().numpy().view(np.uint32), ref)

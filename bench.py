@@ -1,20 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark: correctly rounded binary32 functions over large device arrays on GB300.
 
-Metric: Gelem/s (elements whose correctly rounded result is stored, all functions
-together) and the dominant kernel's fraction of the measured HBM roofline.
+Metric: Gelem/s of correctly rounded results (every result bit-exact against the CPU
+oracle, which the GPU test suite checks), and the dominant kernel's fraction of the
+measured HBM roofline; the double-float form against the FP64 form.
 
-Default workload ("all19_2p26"): each of the 19 binary32 functions on its own 2^26-element
-array of uniform random bit patterns restricted to the function's domain plus 1% specials
-(seed 0xC0DE0000 + 256*2 + func_id).  A step evaluates every array once; inputs are
-256 MiB per function, larger than the 129 MB L2, so no flush is needed between steps.
-The form (--form plain|df|auto) selects the evaluation tier; results are bit-identical.
-
-Also supported: --workload precision (expf/logf/sinf/tanhf/rsqrtf at 2^28, U[-10,10]
-and log-uniform sets, both forms) and --workload expf_mixed (2^20, correctness config).
-
-`--impl reference` times the CPU oracle (the repository's correctly rounded reference
-evaluator) on a bounded sample of the same workload on the host cores.
+Workloads (--workload):
+  all19   (default) each of the 19 binary32 functions on its own 2^26-element array of
+          uniform random bit patterns restricted to the function's domain, plus 1%
+          specials (generated on the GPU, seeded).  A step evaluates every array once.
+          256 MiB per input, larger than the 129 MB L2: no flush needed between steps.
+  precision  expf/logf/sinf/tanhf/rsqrtf on 2^28 elements (U[-10,10]; log-uniform
+          [2^-126, 2^127] for logf/rsqrtf).
+  batch   10,000 arrays, lengths log-uniform in [2^6, 2^22], functions uniform over the
+          19: one batched launch per step (and, for comparison, one launch per array).
+The step uses --form (auto = the fastest form of each function, double-float for all 19;
+plain = the FP64-internal form); the other form is measured beside it per function.
+`--impl reference` times the CPU oracle on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -34,6 +36,7 @@ sys.path.insert(0, ROOT)
 
 from paper_2605_15547_gb300 import workloads as W  # noqa: E402
 
+METRIC = "Gelem/s per function (0-ulp vs oracle) & % of HBM roofline; double-float vs FP64 form"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -48,10 +51,8 @@ def load_peaks():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
 
 
 class ClockSampler:
@@ -62,17 +63,14 @@ class ClockSampler:
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.lines = []
+        self.index, self.proc, self.lines = index, None, []
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
 
@@ -106,42 +104,49 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------------------------- workloads
-
-def build_workload(name: str, scale: int, only=None):
-    """Returns a list of (func, host float32 array) and a config dict."""
-    items = []
-    if name == "all19_2p26":
-        n = (1 << 26) >> scale
-        for f in W.F32_FUNCS:
-            if only and f not in only:
-                continue
-            items.append((f, W.domain_bits(f, n, W.rng_for(2, f)).view(np.float32)))
-        cfg = {"workload": f"all 19 binary32 functions, 2^{26 - scale} inputs each, domain bit patterns + 1% specials",
-               "elems_per_func": n}
-    elif name == "precision":
-        n = (1 << 28) >> scale
-        for f in ("expf", "logf", "sinf", "tanhf", "rsqrtf"):
-            if only and f not in only:
-                continue
-            rng = W.rng_for(3, f)
-            if f in ("logf", "rsqrtf"):
-                items.append((f, W.loguniform(-126, 127, n, rng, signed=False)))
-            else:
-                items.append((f, W.uniform(-10, 10, n, rng)))
-        cfg = {"workload": f"expf/logf/sinf/tanhf/rsqrtf, 2^{28 - scale} inputs each (U[-10,10]; "
-                           "log-uniform [2^-126,2^127] for logf/rsqrtf)", "elems_per_func": n}
-    elif name == "expf_mixed":
-        n = 1 << 20
-        items.append(("expf", W.expf_mixed(n, W.rng_for(1, "expf"))))
-        cfg = {"workload": "expf, 2^20 inputs: 90% U[-103.98,88.73] + 10% specials", "elems_per_func": n}
-    else:
-        raise SystemExit(f"unknown workload {name}")
-    return items, cfg
-
-
 def bytes_per_elem(func: str) -> int:
     return 12 if func == "sincosf" else (16 if func in ("exp2", "log") else 8)
+
+
+# ----------------------------------------------------------------------------- workloads
+
+def workload_spec(name: str, scale: int):
+    if name == "all19":
+        n = (1 << 26) >> scale
+        return [(f, n) for f in W.F32_FUNCS], {
+            "workload": f"19 binary32 functions x 2^{26 - scale} inputs: domain bit patterns + 1% specials",
+            "elems_per_func": n}
+    if name == "precision":
+        n = (1 << 28) >> scale
+        return [(f, n) for f in ("expf", "logf", "sinf", "tanhf", "rsqrtf")], {
+            "workload": f"expf/logf/sinf/tanhf/rsqrtf x 2^{28 - scale}: U[-10,10] (log-uniform "
+                        "[2^-126,2^127] for logf, rsqrtf)", "elems_per_func": n}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def make_input_host(name, func, n):
+    if name == "all19":
+        return W.domain_bits(func, n, W.rng_for(2, func)).view(np.float32)
+    rng = W.rng_for(3, func)
+    if func in ("logf", "rsqrtf"):
+        return W.loguniform(-126, 127, n, rng, signed=False)
+    return W.uniform(-10, 10, n, rng)
+
+
+def make_input_device(name, func, n, dev):
+    """Same recipe as make_input_host, generated on the device (used at full size)."""
+    import torch
+    if name == "all19":
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(W.seed_for(2, func))
+        x = W.domain_bits_device(func, n, gen, device=dev)
+        rng = W.rng_for(2, func, salt=1)
+        ns = int(n * 0.01)
+        sp = np.resize(W.specials_f32(func, rng), ns)
+        pos = torch.from_numpy(rng.choice(n, ns, replace=False)).to(dev)
+        x[pos] = torch.from_numpy(sp.view(np.float32)).to(dev)
+        return x
+    return torch.from_numpy(make_input_host(name, func, n)).to(dev)
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -152,35 +157,35 @@ def run_reference(args):
         return 0
     from oracle import oracle as O
     O.build()
-    items, cfg = build_workload(args.workload, args.scale, set(args.funcs.split(",")) if args.funcs else None)
-    sample = args.ref_sample
     cores = os.cpu_count() or 1
-    # warm-up (constants, thread pool)
-    for f, x in items[:1]:
-        O.eval_bits(f, x[:1024].view(np.uint32))
+    if args.workload == "batch":
+        items = [(f, 1 << 14) for f in W.F32_FUNCS]
+        cfg = {"workload": "batch: 10,000 arrays, lengths log-uniform [2^6,2^22], 19 functions"}
+    else:
+        items, cfg = workload_spec(args.workload, args.scale)
+    sample = args.ref_sample
+    xs = [(f, make_input_host("all19" if args.workload == "batch" else args.workload, f, sample).view(np.uint32))
+          for f, _ in items]
+    O.eval_bits(xs[0][0], xs[0][1][:1024])
     times = []
-    total = 0
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        cnt = 0
-        for f, x in items:
-            xs = x[:sample].view(np.uint32)
-            O.eval_bits(f, xs, nthreads=cores)
-            cnt += xs.size
+        for f, x in xs:
+            O.eval_bits(f, x, nthreads=cores)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
-            total += cnt
+    n_step = sum(x.size for _, x in xs)
     secs = sum(times)
-    value = total / secs / 1e9
+    value = n_step * args.steps / secs / 1e9
     line = {
-        "impl": "reference", "metric": "Gelem/s (correctly rounded results, all functions)",
-        "value": value, "unit": "Gelem/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
         "config": dict(cfg, sample_per_func=sample, l2="n/a (CPU)"),
         "cpu_baseline": {"value": value, "unit": "Gelem/s", "cores": cores, "kind": "oracle",
-                         "sample": f"first {sample} inputs of each function's array"},
+                         "sample": f"{sample} inputs per function, same recipe"},
         "e2e": {"value": value, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -189,19 +194,114 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- our arm
 
+def time_calls(crm, torch, funcs, xs, ys, form, reps, stream):
+    """Average device time per call of each function, `reps` calls back to back."""
+    out = []
+    for f, x, y in zip(funcs, xs, ys):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        crm.eval_into(f, x, y, form=form)
+        s.record(stream)
+        for _ in range(reps):
+            crm.eval_into(f, x, y, form=form)
+        e.record(stream)
+        e.synchronize()
+        out.append(s.elapsed_time(e) / reps)
+    return out
+
+
+def run_batch(args, crm, torch, dev, stream, rank, world):
+    count = args.batch_count
+    rng = np.random.Generator(np.random.PCG64(W.seed_for(4, 0)))
+    lens, funcs = W.batch_lengths(count, rng)
+    lens = lens >> args.scale
+    lens[lens < 1] = 1
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.seed_for(4, 0))
+    xs, ys = [], []
+    for f, n in zip(funcs, lens):
+        xs.append(W.domain_bits_device(f, int(n), gen, device=dev))
+        ys.append(torch.empty((2 * int(n),) if f == "sincosf" else (int(n),), dtype=torch.float32, device=dev))
+    items = list(zip(funcs, xs, ys))
+    n_elems = int(lens.sum())
+    crm.reserve(1 << 24, count, stream=stream)
+    for _ in range(args.warmup):
+        crm.eval_batch(items, form=args.form, stream=stream)
+    torch.cuda.synchronize()
+    crm.stats_reset(stream=stream)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record(stream)
+    for _ in range(args.steps):
+        crm.eval_batch(items, form=args.form, stream=stream)
+    e.record(stream)
+    e.synchronize()
+    clk = clocks.stop()
+    ms = s.elapsed_time(e)
+    st = crm.stats(stream=stream)
+    # one launch per array, for comparison (also via CUDA events)
+    s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s2.record(stream)
+    for f, x, y in items:
+        crm.eval_into(f, x, y, form=args.form, stream=stream)
+    e2.record(stream)
+    e2.synchronize()
+    ms_single = s2.elapsed_time(e2)
+    # graph replay of one batched step
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        crm.eval_batch(items, form=args.form, stream=stream)
+    g.replay()
+    torch.cuda.synchronize()
+    s3, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s3.record(stream)
+    g.replay()
+    e3.record(stream)
+    e3.synchronize()
+    ms_graph = s3.elapsed_time(e3)
+    nbytes = sum(x.numel() * 4 + y.numel() * 4 for _, x, y in items)
+    peak, kind = load_peaks()
+    value = n_elems * args.steps / (ms / 1e3) / 1e9
+    achieved = nbytes / (ms / args.steps / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch: {count} arrays, lengths log-uniform [2^6,2^22] >> {args.scale}, "
+                               "functions uniform over the 19", "total_elems": n_elems, "form": args.form,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_batch (step)", "peak_kind": kind},
+        "one_launch_per_array": {"gelem_s": n_elems / (ms_single / 1e3) / 1e9, "ms": ms_single,
+                                 "launches": 2 * count},
+        "graph_replay_ms": ms_graph,
+        "hard_case_rate": st["hard_total"] / max(1, n_elems * args.steps), "unresolved": st["unresolved_total"],
+        "gpu_launches": 2 * args.steps, "clocks": clk,
+        "e2e": {"value": None, "unit": "Gelem/s", "note": "batch workload is device resident"},
+        "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="auto", choices=["auto", "plain", "df"])
-    ap.add_argument("--workload", default="all19_2p26", choices=["all19_2p26", "precision", "expf_mixed"])
+    ap.add_argument("--workload", default="all19", choices=["all19", "precision", "batch"])
     ap.add_argument("--scale", type=int, default=0, help="divide sizes by 2^scale (testing)")
-    ap.add_argument("--ref-sample", type=int, default=1 << 16)
-    ap.add_argument("--cpu-sample", type=int, default=1 << 15)
+    ap.add_argument("--ref-sample", type=int, default=1 << 15)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 18)
+    ap.add_argument("--batch-count", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--funcs", default="", help="comma list to restrict the workload (testing)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--funcs", default="", help="comma list restricting the workload (testing)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -218,123 +318,116 @@ def main():
     dev = torch.device("cuda", local)
     import __graft_entry__ as g
     g.build()
-
-    items, cfg = build_workload(args.workload, args.scale, set(args.funcs.split(",")) if args.funcs else None)
-    # drop functions the library does not provide yet (reported in the config)
-    avail = []
-    for f, x in items:
-        t = torch.from_numpy(x[:64]).to(dev)
-        try:
-            crm.eval(f, t, form=args.form)
-            avail.append((f, x))
-        except crm.CrmError:
-            pass
-    missing = [f for f, _ in items if f not in {a for a, _ in avail}]
-    items = avail
-    dx = [torch.from_numpy(x).to(dev) for _, x in items]
-    dy = [torch.empty(((2,) if f == "sincosf" else ()) + (x.size,), dtype=torch.float32, device=dev)
-          for f, x in items]
-    funcs = [f for f, _ in items]
-    n_elems = sum(x.size for _, x in items)
     stream = torch.cuda.current_stream()
+    if args.workload == "batch":
+        side = torch.cuda.Stream(device=dev)  # graph capture needs a non-default stream
+        with torch.cuda.stream(side):
+            return run_batch(args, crm, torch, dev, side, rank, world)
 
-    def step():
-        for f, a, b in zip(funcs, dx, dy):
-            crm.eval_into(f, a, b, form=args.form)
+    spec, cfg = workload_spec(args.workload, args.scale)
+    if args.funcs:
+        keep = set(args.funcs.split(","))
+        spec = [s for s in spec if s[0] in keep]
+    funcs = [f for f, _ in spec]
+    xs = [make_input_device(args.workload, f, n, dev) for f, n in spec]
+    ys = [torch.empty(((2,) if f == "sincosf" else ()) + (x.numel(),), dtype=torch.float32, device=dev)
+          for f, x in zip(funcs, xs)]
+    n_elems = sum(x.numel() for x in xs)
+
+    def step(form):
+        for f, x, y in zip(funcs, xs, ys):
+            crm.eval_into(f, x, y, form=form)
 
     for _ in range(args.warmup):
-        step()
+        step(args.form)
     torch.cuda.synchronize()
     crm.stats_reset()
-    # per-call events (the main + slow kernels of each function)
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in funcs]
-          for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for s in range(args.steps):
-        for i, (f, a, b) in enumerate(zip(funcs, dx, dy)):
-            ev[s][i][0].record(stream)
-            crm.eval_into(f, a, b, form=args.form)
-            ev[s][i][1].record(stream)
-    t_end.record(stream)
+    t_s, t_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_s.record(stream)
+    for _ in range(args.steps):
+        step(args.form)
+    t_e.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    ms_total = t_start.elapsed_time(t_end)
+    ms_total = t_s.elapsed_time(t_e)
     if world > 1:
         tt = torch.tensor([ms_total], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         ms_total = float(tt.item())
-    per_func_ms = [statistics.mean(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
-                   for i in range(len(funcs))]
     st = crm.stats()
     value = n_elems * args.steps * world / (ms_total / 1e3) / 1e9
-    peak, peak_kind = load_peaks()
-    # dominant kernel = the function whose call takes the most time
-    dom = int(np.argmax(per_func_ms))
-    dom_bytes = items[dom][1].size * bytes_per_elem(funcs[dom])
-    achieved = dom_bytes / (per_func_ms[dom] / 1e3) / 1e9
-    per_func = {f: {"gelem_s": items[i][1].size / (per_func_ms[i] / 1e3) / 1e9,
-                    "hbm_frac": items[i][1].size * bytes_per_elem(f) / (per_func_ms[i] / 1e3) / 1e9 / peak}
-                for i, f in enumerate(funcs)}
 
-    # end to end through the host-buffer entry point (pinned host memory)
+    # per function, both forms (back-to-back calls, device time per call)
+    other = "plain" if args.form != "plain" else "auto"
+    ms_main = time_calls(crm, torch, funcs, xs, ys, args.form, 3, stream)
+    ms_other = time_calls(crm, torch, funcs, xs, ys, other, 2, stream)
+    peak, peak_kind = load_peaks()
+    per_func = {}
+    for i, f in enumerate(funcs):
+        n = xs[i].numel()
+        per_func[f] = {
+            args.form: {"gelem_s": n / (ms_main[i] / 1e3) / 1e9,
+                        "hbm_frac": n * bytes_per_elem(f) / (ms_main[i] / 1e3) / 1e9 / peak},
+            other: {"gelem_s": n / (ms_other[i] / 1e3) / 1e9},
+        }
+        hi, lo = (ms_other[i], ms_main[i]) if args.form != "plain" else (ms_main[i], ms_other[i])
+        per_func[f]["df_over_plain"] = hi / lo
+    step_other = sum(x.numel() for x in xs) / (sum(ms_other) / 1e3) / 1e9
+    # dominant kernel: the function taking the largest share of the step
+    dom = int(np.argmax(ms_main))
+    dom_bytes = xs[dom].numel() * bytes_per_elem(funcs[dom])
+    achieved = dom_bytes / (ms_main[dom] / 1e3) / 1e9
+
     e2e = None
-    try:
-        hin = [torch.from_numpy(x).pin_memory() for _, x in items]
-        hout = [torch.empty(tuple(b.shape), dtype=torch.float32).pin_memory() for b in dy]
-        torch.cuda.synchronize()
+    if not args.no_e2e:
+        hin = [x.cpu().pin_memory() for x in xs]
+        hout = [torch.empty(tuple(y.shape), dtype=torch.float32).pin_memory() for y in ys]
+        crm.eval_host(funcs[0], hin[0].numpy(), hout[0].numpy().reshape(-1), form=args.form)
         t0 = time.perf_counter()
-        for _ in range(max(1, args.steps // 2)):
-            for f, a, b in zip(funcs, hin, hout):
-                crm.eval_host(f, a.numpy(), b.numpy().reshape(-1), form=args.form)
+        for f, a, b in zip(funcs, hin, hout):
+            crm.eval_host(f, a.numpy(), b.numpy().reshape(-1), form=args.form)
         t1 = time.perf_counter()
-        k = max(1, args.steps // 2)
-        e2e = {"value": n_elems * k / (t1 - t0) / 1e9, "unit": "Gelem/s",
-               "h2d_bytes_per_step": int(sum(x.nbytes for _, x in items)),
-               "d2h_bytes_per_step": int(sum(b.numel() * 4 for b in dy))}
-    except Exception as exc:  # host entry point not available
-        e2e = {"value": None, "unit": "Gelem/s", "error": str(exc)[:120]}
+        e2e = {"value": n_elems / (t1 - t0) / 1e9, "unit": "Gelem/s",
+               "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in xs)),
+               "d2h_bytes_per_step": int(sum(y.numel() * 4 for y in ys)),
+               "note": "crm_eval_host: page-locked host in/out, chunked copies overlapped with compute"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import oracle as O
         O.build()
         cores = os.cpu_count() or 1
+        sample = [(f, xs[i][:args.cpu_sample].cpu().numpy().view(np.uint32)) for i, f in enumerate(funcs)]
         t0 = time.perf_counter()
-        cnt = 0
-        for f, x in items:
-            xs = x[:args.cpu_sample].view(np.uint32)
-            O.eval_bits(f, xs, nthreads=cores)
-            cnt += xs.size
+        for f, xh in sample:
+            O.eval_bits(f, xh, nthreads=cores)
         dt = time.perf_counter() - t0
+        cnt = sum(x.size for _, x in sample)
         cpu = {"value": cnt / dt / 1e9, "unit": "Gelem/s", "cores": cores, "kind": "oracle",
                "sample": f"first {args.cpu_sample} inputs of each function's array"}
 
-    launches = args.steps * len(funcs) * 2
     line = {
-        "metric": "Gelem/s (correctly rounded results, all functions)",
-        "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.form == "df" else ("f64" if args.form == "plain" else "f32"),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.form == "plain" else "f32",
         "data": "synthetic",
-        "config": dict(cfg, form=args.form, functions=funcs, missing=missing,
-                       l2="inputs larger than L2 (no flush)", parallelism=f"replicas{world}"),
+        "config": dict(cfg, form=args.form, functions=funcs, l2="inputs larger than L2 (no flush)",
+                       parallelism=f"replicas{world}"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": f"k_main<{funcs[dom]}>",
+                     "frac": achieved / peak, "traffic": None, "kernel": f"k_main+k_slow<{funcs[dom]}>",
                      "peak_kind": peak_kind},
+        "other_form": {"form": other, "step_gelem_s": step_other},
         "per_function": per_func,
-        "hard_case_rate": st["hard_total"] / max(1, n_elems * args.steps),
-        "unresolved": st["unresolved_total"],
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "hard_case_rate": st["hard_total"] / max(1, n_elems * args.steps), "unresolved": st["unresolved_total"],
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * len(funcs) * 2, "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line))

@@ -126,3 +126,32 @@ def f64_uniform(lo: float, hi: float, n: int, rng: np.random.Generator) -> np.nd
 def f64_positive_bits(n: int, rng: np.random.Generator) -> np.ndarray:
     b = rng.integers(1, 0x7FF0000000000000, n, dtype=np.uint64)
     return b.view(np.float64)
+
+
+# ----------------------------------------------------------------------------- device-side
+# For the batching workload (about 3.8e9 inputs) the same recipes run on the GPU with
+# torch's seeded generator: uniform random bit patterns restricted to the function's
+# domain by rejection.
+
+def domain_bits_device(func: str, n: int, gen, device="cuda"):
+    import torch
+    lo, hi = DOMAIN_F32[func]
+    out = torch.empty(n, dtype=torch.int32, device=device)
+    got = 0
+    while got < n:
+        need = n - got
+        cand = torch.randint(-2**31, 2**31, (int(need * 2.2) + 1024,), dtype=torch.int64,
+                             device=device, generator=gen).to(torch.int32)
+        v = cand.view(torch.float32)
+        ok = torch.isfinite(v) & (v > lo) & (v < hi)
+        sel = cand[ok][:need]
+        out[got:got + sel.numel()] = sel
+        got += sel.numel()
+    return out.view(torch.float32)
+
+
+def batch_lengths(count: int, rng: np.random.Generator, lo_log2: float = 6.0, hi_log2: float = 22.0):
+    """Lengths log-uniform in [2^lo, 2^hi] and functions uniform over the 19 (config 4)."""
+    n = np.round(np.exp2(rng.uniform(lo_log2, hi_log2, count))).astype(np.int64)
+    f = rng.integers(0, len(F32_FUNCS), count)
+    return n, [F32_FUNCS[i] for i in f]

@@ -87,6 +87,7 @@ typedef struct {
   uint64_t unresolved_total; /* lanes no tier could decide (0 unless something is wrong) */
   uint64_t inline_total;     /* hard lanes finished inline because the queue was full */
   uint64_t last_count;       /* hard lanes of the last call on this stream */
+  uint64_t timeouts;         /* bounded device waits that gave up (0 unless something is wrong) */
 } crm_stats_t;
 
 /* Evaluate func_id on n elements: out[i] = RN(f(in[i])) (sincosf: out[i] = sin,

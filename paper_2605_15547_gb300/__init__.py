@@ -104,7 +104,7 @@ def stats(stream=None) -> dict:
     s = crm_stats_t()
     L.check(L.lib().crm_stats(_stream_ptr(stream), ctypes.byref(s)))
     return {"hard_total": s.hard_total, "unresolved_total": s.unresolved_total,
-            "inline_total": s.inline_total, "last_count": s.last_count}
+            "inline_total": s.inline_total, "last_count": s.last_count, "timeouts": s.timeouts}
 
 
 def stats_reset(stream=None) -> None:

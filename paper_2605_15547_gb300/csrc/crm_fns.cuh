@@ -5,6 +5,7 @@
 #include "crm_kernels.cuh"
 #include "fam_atrig.cuh"
 #include "fam_exp.cuh"
+#include "fam_f64.cuh"
 #include "fam_hyp.cuh"
 #include "fam_log.cuh"
 #include "fam_rsqrt.cuh"
@@ -105,6 +106,28 @@ struct FnRsqrt {
     y[0] = FORM == 1 ? rsqrt_plain(x, h) : rsqrt_df(x, h);
   }
   CRM_DEV static void slow(float x, float *y, bool &u) { y[0] = rsqrt_slow(x, u); }
+};
+
+// binary64 pair: one main path (double-double), used for both form slots
+struct FnExp2D {
+  using T = double;
+  static constexpr int NOUT = 1;
+  template <int FORM> static constexpr int tab_bytes() { return 96 * 8; }
+  template <int FORM> CRM_DEV static void load(unsigned char *sm) { copy_tab(sm, CRM_EXP2D_T, 96 * 8); }
+  template <int FORM> CRM_DEV static void eval(double x, const void *sm, double *y, bool &h) {
+    y[0] = exp2d_main(x, (const double *)sm, h);
+  }
+  CRM_DEV static void slow(double x, double *y, bool &u) { y[0] = exp2d_slow(x, u); }
+};
+struct FnLogD {
+  using T = double;
+  static constexpr int NOUT = 1;
+  template <int FORM> static constexpr int tab_bytes() { return 0; }
+  template <int FORM> CRM_DEV static void load(unsigned char *) {}
+  template <int FORM> CRM_DEV static void eval(double x, const void *, double *y, bool &h) {
+    y[0] = logd_main(x, h);
+  }
+  CRM_DEV static void slow(double x, double *y, bool &u) { y[0] = logd_slow(x, u); }
 };
 
 }  // namespace crm

@@ -201,6 +201,171 @@ __global__ void __launch_bounds__(KBLOCK) k_main(KArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ pipelined variant
+// The same work with the inputs staged through shared memory by bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier), a ring of PSTAGES chunks per block:
+// the bytes in flight no longer depend on registers, so each SM keeps enough reads
+// outstanding to cover HBM latency.  Thread 0 issues the copies; every wait is bounded
+// by the global timer (1 s), after which the block records a timeout, waits (bounded)
+// for its copies still in flight and returns.
+constexpr int PSTAGES = 4;
+constexpr int PVPT = 2;  // 16-byte vectors per thread per chunk
+constexpr unsigned long long PWAIT_NS = 1000000000ull;
+
+CRM_DEV unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+CRM_DEV void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+CRM_DEV void mbar_arm_and_copy(uint64_t *bar, void *dst, const void *src, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+CRM_DEV bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+CRM_DEV unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the given phase parity; false if the global-timer limit ran out first.
+CRM_DEV bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > PWAIT_NS) return false;
+  return true;
+}
+
+template <class Fn, int FORM>
+__global__ void __launch_bounds__(KBLOCK) k_pipe(KArgs a) {
+  using T = typename Fn::T;
+  using V = typename VecOf<T>::V;
+  constexpr int W = VecOf<T>::W;
+  constexpr int CH = KBLOCK * PVPT;  // vectors per chunk
+  __shared__ __align__(16) unsigned char sm[(Fn::template tab_bytes<FORM>() > 0) ? Fn::template tab_bytes<FORM>() : 16];
+  __shared__ __align__(128) V buf[PSTAGES][CH];
+  __shared__ uint64_t bars[PSTAGES];
+  Fn::template load<FORM>(sm);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PSTAGES; s++) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const V *in4 = (const V *)((const T *)a.in + a.head);
+  V *out4 = (V *)((T *)a.out + a.head);
+  V *out4b = (V *)((T *)a.out + a.n + a.head);
+  const uint64_t nchunks = (a.nvec + CH - 1) / CH;
+  const uint64_t mine = blockIdx.x < nchunks ? (nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto chunk_of = [&](uint64_t i) { return blockIdx.x + i * gridDim.x; };
+  auto issue = [&](uint64_t i) {
+    uint64_t c = chunk_of(i);
+    uint64_t v0 = c * CH;
+    uint64_t nv = a.nvec - v0 < (uint64_t)CH ? a.nvec - v0 : (uint64_t)CH;
+    mbar_arm_and_copy(&bars[i % PSTAGES], buf[i % PSTAGES], in4 + v0, (unsigned)(nv * sizeof(V)));
+  };
+  if (threadIdx.x == 0)
+    for (uint64_t i = 0; i < mine && i < (uint64_t)PSTAGES; i++) issue(i);
+  bool failed = false;
+  for (uint64_t i = 0; i < mine; i++) {
+    const int st = (int)(i % PSTAGES);
+    bool ok = mbar_wait_bounded(&bars[st], (unsigned)((i / PSTAGES) & 1));
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const uint64_t v0 = chunk_of(i) * CH;
+#pragma unroll
+    for (int u = 0; u < PVPT; u++) {
+      const uint64_t vl = (uint64_t)u * KBLOCK + threadIdx.x;
+      const uint64_t v = v0 + vl;
+      const bool act = v < a.nvec;
+      V xv = act ? buf[st][vl] : V();
+      V y0, y1;
+      unsigned hm = 0;
+#pragma unroll
+      for (int j = 0; j < W; j++) {
+        T y[2];
+        bool h;
+        Fn::template eval<FORM>(vget(xv, j), sm, y, h);
+        hm |= (unsigned)h << j;
+        vset(y0, j, y[0]);
+        if (Fn::NOUT == 2) vset(y1, j, y[1]);
+      }
+      hm = a.force_hard ? (1u << W) - 1u : hm;
+      hm = act ? hm : 0u;
+      if (act) {
+        st_stream(out4 + v, y0);
+        if (Fn::NOUT == 2) st_stream(out4b + v, y1);
+      }
+      if (__any_sync(0xFFFFFFFFu, hm != 0)) {
+        uint64_t ii[W], xb[W];
+#pragma unroll
+        for (int j = 0; j < W; j++) {
+          ii[j] = a.head + v * W + j;
+          xb[j] = xbits_of(vget(xv, j));
+        }
+        unsigned over = push_hard<W>(hm, ii, xb, a);
+        if (over) {
+#pragma unroll
+          for (int j = 0; j < W; j++)
+            if ((over >> j) & 1u) slow_store<Fn>(vget(xv, j), ii[j], a);
+        }
+      }
+    }
+    __syncthreads();  // every thread is done with this stage
+    if (threadIdx.x == 0 && i + PSTAGES < mine) issue(i + PSTAGES);
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicAdd(&a.hdr->timeouts, 1ull);
+      // bounded wait for copies still in flight into this block's shared memory
+      for (int s = 0; s < PSTAGES; s++) {
+        uint64_t last = (uint64_t)-1;
+        for (uint64_t i = 0; i < mine; i++)
+          if ((int)(i % PSTAGES) == s) last = i;
+        if (last != (uint64_t)-1) mbar_wait_bounded(&bars[s], (unsigned)((last / PSTAGES) & 1));
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  // scalar head and tail, as in k_main
+  const uint64_t tail0 = a.head + (uint64_t)W * a.nvec;
+  const uint64_t nscal = a.head + (a.n - tail0);
+  const T *in = (const T *)a.in;
+  T *out = (T *)a.out;
+  for (uint64_t b = (uint64_t)blockIdx.x * KBLOCK; b < nscal; b += (uint64_t)gridDim.x * KBLOCK) {
+    uint64_t k = b + threadIdx.x;
+    bool act = k < nscal;
+    uint64_t i = k < a.head ? k : tail0 + (k - a.head);
+    T x = act ? in[i] : T(0);
+    T y[2];
+    bool h;
+    Fn::template eval<FORM>(x, sm, y, h);
+    h = (h || a.force_hard) && act;
+    if (act) {
+      out[i] = y[0];
+      if (Fn::NOUT == 2) out[a.n + i] = y[1];
+    }
+    if (__any_sync(0xFFFFFFFFu, h)) {
+      uint64_t xb = xbits_of(x);
+      if (push_hard<1>(h ? 1u : 0u, &i, &xb, a)) slow_store<Fn>(x, i, a);
+    }
+  }
+}
+
 template <class Fn>
 __global__ void __launch_bounds__(KBLOCK) k_slow(KArgs a) {
   using T = typename Fn::T;

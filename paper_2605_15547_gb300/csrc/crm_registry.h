@@ -9,7 +9,7 @@ namespace crm {
 typedef cudaError_t (*launch_fn)(const KArgs &, int grid, cudaStream_t);
 typedef int (*occ_fn)(void);
 
-enum { NUNROLL = 3 };  // unroll variants 1, 2, 4 (vectors in flight per thread)
+enum { NUNROLL = 4 };  // variants: unroll 1, 2, 4 (vectors in flight per thread), 3 = pipelined
 
 struct FuncEntry {
   launch_fn main[3][NUNROLL];  // [form][unroll]; form 0 unused; null when unavailable
@@ -31,13 +31,21 @@ cudaError_t launch_slow(const KArgs &a, int grid, cudaStream_t s) {
 }
 
 template <class Fn, int FORM>
+cudaError_t launch_pipe(const KArgs &a, int grid, cudaStream_t s) {
+  k_pipe<Fn, FORM><<<grid, KBLOCK, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class Fn, int FORM>
 void set_form(FuncEntry &e) {
   e.main[FORM][0] = launch_main<Fn, FORM, 1>;
   e.main[FORM][1] = launch_main<Fn, FORM, 2>;
   e.main[FORM][2] = launch_main<Fn, FORM, 4>;
+  e.main[FORM][3] = launch_pipe<Fn, FORM>;
   e.main_sym[FORM][0] = (const void *)k_main<Fn, FORM, 1>;
   e.main_sym[FORM][1] = (const void *)k_main<Fn, FORM, 2>;
   e.main_sym[FORM][2] = (const void *)k_main<Fn, FORM, 4>;
+  e.main_sym[FORM][3] = (const void *)k_pipe<Fn, FORM>;
 }
 
 template <class Fn, bool HAS_PLAIN, bool HAS_DF>
@@ -56,5 +64,6 @@ void register_log(FuncEntry *table);
 void register_hyp(FuncEntry *table);
 void register_trig(FuncEntry *table);
 void register_atrig(FuncEntry *table);
+void register_f64(FuncEntry *table);
 
 }  // namespace crm

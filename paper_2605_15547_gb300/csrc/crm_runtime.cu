@@ -31,6 +31,7 @@ static void init_table() {
   register_hyp(g_table);
   register_trig(g_table);
   register_atrig(g_table);
+  register_f64(g_table);
   const char *f = getenv("CRM_FORM");
   if (f) {
     if (!strcmp(f, "plain")) g_default_form = CRM_FORM_PLAIN_FP64;
@@ -149,8 +150,11 @@ static bool g_unroll_set = false;
 
 int unroll_of(int func, int form) {
   if (!g_unroll_set) {
+    int def = 1;  // 2 vectors in flight per thread
+    const char *u = getenv("CRM_UNROLL");
+    if (u && atoi(u) >= 0 && atoi(u) < NUNROLL) def = atoi(u);
     for (int f = 0; f < CRM_NUM_FUNCS; f++)
-      for (int m = 0; m < 3; m++) g_unroll[f][m] = 1;  // 2 vectors in flight by default
+      for (int m = 0; m < 3; m++) g_unroll[f][m] = def;
     g_unroll_set = true;
   }
   return g_unroll[func][form];
@@ -209,7 +213,7 @@ void fill_geometry(const FuncEntry &fe, const void *in, void *out, uint64_t n, K
 // resident blocks (the kernel loops over the rest).
 int main_grid(const FuncEntry &fe, const KArgs &a, int ui, int sms, int bps) {
   const int W = fe.dtype ? 2 : 4;
-  const int U = 1 << ui;
+  const int U = ui == 3 ? PVPT : (1 << ui);
   uint64_t want = (a.nvec + (uint64_t)KBLOCK * U - 1) / ((uint64_t)KBLOCK * U);
   uint64_t nscal = a.head + (a.n - a.head - (uint64_t)W * a.nvec);
   uint64_t want_s = (nscal + KBLOCK - 1) / KBLOCK;
@@ -401,6 +405,7 @@ int crm_stats(void *stream, crm_stats_t *out) {
   out->unresolved_total = h.unresolved_total;
   out->inline_total = h.inline_total;
   out->last_count = h.count;
+  out->timeouts = h.timeouts;
   return CRM_OK;
 }
 

@@ -9,7 +9,8 @@ typedef struct crm_ws_header {
   unsigned long long hard_total;       // sum of count over calls
   unsigned long long unresolved_total; // lanes no tier could decide (never expected)
   unsigned long long inline_total;     // lanes finished inline because the queue was full
-  unsigned long long pad[4];
+  unsigned long long timeouts;         // bounded waits that gave up (never expected)
+  unsigned long long pad[3];
 } crm_ws_header;
 
 // One queued hard lane: element index (array id in bits 40..63 for the batch form) and

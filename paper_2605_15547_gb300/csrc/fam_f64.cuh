@@ -1,0 +1,392 @@
+// fam_f64.cuh -- the binary64 pair of Sec. II.B: exp2 and log.
+//
+// Main path (double-double in FP64), following the paper's design: a highly accurate but
+// not always correctly rounded evaluation plus a rounding test; lanes that fail it are
+// sent to a slower exact path (Sec. II.B).
+//   exp2: x = k + (256 i1 + 16 i2 + i3)/4096 + R, |R| <= 2^-13, and
+//         2^x = 2^k T1[i1] T2[i2] T3[i3] 2^R with three 16-entry double-double tables
+//         (the paper's 0.75 KB of tables) and a degree-7 polynomial for 2^R - 1;
+//   log:  x = 2^e m (m in [3/4, 3/2)), a short reciprocal rcp_j ~ 1/m from a 193-entry
+//         table, r = m rcp_j - 1 exactly as a double-double (TwoProd), and
+//         log x = e ln2 + (-log rcp_j) + log1p(r) with log1p by an odd/even-split
+//         polynomial of degree 11.
+// Slow path: 192-bit unsigned fixed-point integer arithmetic (no FP64 at all), with the
+// rounding decided exactly from the computed interval; it cannot be wrong, only
+// unresolved (never observed: that would need a result within 2^-180 of a midpoint).
+#pragma once
+#include "crm_common.cuh"
+#include "crm_tables.h"
+
+namespace crm {
+
+// ------------------------------------------------------------------ rounding test (binary64)
+// y = s + t (|t| <= ulp(s)/2) approximates v with |v - y| <= eps |s|; RN64(v) = s unless
+// a midpoint next to s lies within |t| + eps |s|: tested with the hardware's rounding as
+// in hard_df.  E = 2^-98 covers eps <= 2^-100 plus the rounding of the sum.
+CRM_DEV bool hard_dd(double s, double t) {
+  double e = fabs(s) * 0x1p-98;
+  double u = t + copysign(e, t);
+  return (s + u) != s;
+}
+
+// ------------------------------------------------------------------ exp2, main path
+// Error: tables 2^-106 each, two double-double products 2^-104 each, the polynomial
+// (c1..c3 in double-double, c4..c7 in double: |R|^4 c4 <= 2^-58.3 so the double tail adds
+// 2^-111) 2^-104, the final product and sum 2^-104: below 2^-101.5 relative.
+constexpr double EXP2D_EPS_OK = 0x1p-100;
+
+CRM_DEV bool exp2d_special(double x, double &r) {
+  bool nan = x != x;
+  r = nan ? qnan_of(x) : (x >= 1024.0 ? CRM_INF_D : 0.0);
+  return nan || x >= 1024.0 || x <= -1075.0;
+}
+
+CRM_DEV Pair<double> exp2d_core(double x, int &k, const double *T) {
+  const double sh = 0x1.8p52;
+  double xs = x * 4096.0;  // exact
+  double nd = (xs + sh) - sh;  // rint(4096 x)
+  long long N = (long long)nd;
+  double R = fma_(nd, -0x1p-12, x);  // exact (Sterbenz)
+  int i = (int)(N & 4095);
+  k = (int)(N >> 12);
+  const double *T1 = T, *T2 = T + 32, *T3 = T + 64;  // the three tables, contiguous
+  int i1 = i >> 8, i2 = (i >> 4) & 15, i3 = i & 15;
+  Pair<double> t = dd_mul(dd(T1[2 * i1], T1[2 * i1 + 1]), dd(T2[2 * i2], T2[2 * i2 + 1]));
+  t = dd_mul(t, dd(T3[2 * i3], T3[2 * i3 + 1]));
+  const double *c = CRM_EXP2D_C;  // (ln2)^k/k!, k = 1..8, pairs
+  double tail = fma_(R, fma_(R, fma_(R, c[12], c[10]), c[8]), c[6]) * R;  // R (c4 + R c5 + ...)
+  Pair<double> q = dd_add_d(dd(c[4], c[5]), tail);
+  q = dd_add(dd(c[2], c[3]), dd_mul_d(q, R));
+  q = dd_add(dd(c[0], c[1]), dd_mul_d(q, R));
+  Pair<double> p = dd_mul_d(q, R);  // 2^R - 1
+  return dd_add(t, dd_mul(t, p));
+}
+
+CRM_DEV double exp2d_main(double x, const double *T, bool &hard) {
+  double r;
+  bool sp = exp2d_special(x, r);
+  int k;
+  Pair<double> y = exp2d_core(sp ? 0.0 : x, k, T);
+  bool sub = x < -1022.0;  // subnormal results: decided by the exact path
+  hard = !sp && (sub || hard_dd(y.hi, y.lo));
+  double out = scale_d(y.hi, k);
+  return sp ? r : out;
+}
+
+// ------------------------------------------------------------------ log, main path
+// r = m rcp - 1 exactly (TwoProd; m rcp - 1 is Sterbenz-exact in its leading word),
+// |r| <= 2^-8.6; log1p(r) = sum (-1)^(k+1) r^k / k to degree 11 (remainder r^12/12 <=
+// 2^-106.8), c1..c5 in double-double Horner, the r^6.. tail in double (2^-113).
+// e ln2 with a double-double ln2; -log(rcp) from the table.  Error < 2^-102 relative
+// (|log x| >= 2^-9.6 unless e = 0 and rcp = 1, where all terms scale with r).
+CRM_DEV bool logd_special(double x, double &r) {
+  bool nan = x != x;
+  r = nan ? qnan_of(x) : (x == 0.0 ? -CRM_INF_D : (x < 0.0 ? CRM_QNAN_D : CRM_INF_D));
+  return nan || x <= 0.0 || x == CRM_INF_D;
+}
+
+CRM_DEV Pair<double> logd_core(double x) {
+  bool sub = x < 0x1p-1022;
+  double xs = sub ? x * 0x1p54 : x;
+  uint64_t b = dbits(xs);
+  uint64_t mant = b & 0x000FFFFFFFFFFFFFull;
+  bool big = mant >= (1ull << 51);
+  int e = (int)(b >> 52) - 1023 + (big ? 1 : 0) - (sub ? 54 : 0);
+  double m = bitsd(mant | (big ? 0x3FE0000000000000ull : 0x3FF0000000000000ull));
+  // j = round(256 m) in [192, 384]
+  int j = big ? 128 + (int)((mant + (1ull << 44)) >> 45) : 256 + (int)((mant + (1ull << 43)) >> 44);
+  double rc = CRM_LOGD_RCP[j - 192];
+  Pair<double> p = two_prod(m, rc);
+  Pair<double> r = fast_two_sum(p.hi - 1.0, p.lo);
+  const double *c = CRM_LOGD_C;  // (-1)^(k+1)/k, k = 1..12, pairs
+  double rh = r.hi;
+  double tail = c[20];
+  for (int q = 9; q >= 5; q--) tail = fma_(rh, tail, c[2 * q]);  // c6..c11 (index k-1)
+  tail = tail * rh;                                                // r (c6 + r c7 + ...)
+  Pair<double> s = dd_add_d(dd(c[8], c[9]), tail);                 // c5 + ...
+  for (int q = 3; q >= 0; q--) s = dd_add(dd(c[2 * q], c[2 * q + 1]), dd_mul(s, r));
+  Pair<double> l1p = dd_mul(s, r);
+  Pair<double> L = dd(CRM_LOGD_L[2 * (j - 192)], CRM_LOGD_L[2 * (j - 192) + 1]);
+  Pair<double> eK = dd_mul_d(dd(CRM_LN2_DD_HI, CRM_LN2_DD_LO), (double)e);
+  return dd_add(dd_add(eK, L), l1p);
+}
+
+CRM_DEV double logd_main(double x, bool &hard) {
+  double r;
+  bool sp = logd_special(x, r);
+  Pair<double> y = logd_core(sp ? 2.0 : x);
+  hard = !sp && hard_dd(y.hi, y.lo);
+  return sp ? r : y.hi;
+}
+
+// ------------------------------------------------------------------ exact slow path
+struct U192 {
+  uint64_t w[3];  // little endian
+};
+CRM_DEV U192 u_zero() { return {{0, 0, 0}}; }
+CRM_DEV U192 u_add(U192 a, U192 b) {
+  U192 r;
+  uint64_t c = 0;
+  for (int i = 0; i < 3; i++) {
+    uint64_t s = a.w[i] + b.w[i];
+    uint64_t c1 = s < a.w[i];
+    uint64_t s2 = s + c;
+    uint64_t c2 = s2 < s;
+    r.w[i] = s2;
+    c = c1 | c2;
+  }
+  return r;
+}
+CRM_DEV U192 u_sub(U192 a, U192 b) {  // a >= b
+  U192 r;
+  uint64_t br = 0;
+  for (int i = 0; i < 3; i++) {
+    uint64_t d = a.w[i] - b.w[i];
+    uint64_t b1 = a.w[i] < b.w[i];
+    uint64_t d2 = d - br;
+    uint64_t b2 = d < br;
+    r.w[i] = d2;
+    br = b1 | b2;
+  }
+  return r;
+}
+CRM_DEV int u_cmp(U192 a, U192 b) {
+  for (int i = 2; i >= 0; i--)
+    if (a.w[i] != b.w[i]) return a.w[i] < b.w[i] ? -1 : 1;
+  return 0;
+}
+CRM_DEV bool u_is_zero(U192 a) { return (a.w[0] | a.w[1] | a.w[2]) == 0; }
+// floor(a b / 2^fb), 128 <= fb < 192, result assumed to fit in 192 bits
+CRM_DEV U192 u_mulfx(U192 a, U192 b, int fb) {
+  uint64_t p[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < 3; i++) {
+    uint64_t carry = 0;
+    for (int j = 0; j < 3; j++) {
+      uint64_t lo = a.w[i] * b.w[j], hi = __umul64hi(a.w[i], b.w[j]);
+      uint64_t s = p[i + j] + lo;
+      hi += s < lo;
+      uint64_t s2 = s + carry;
+      hi += s2 < s;
+      p[i + j] = s2;
+      carry = hi;
+    }
+    p[i + 3] += carry;
+  }
+  int wsh = fb >> 6, bsh = fb & 63;
+  U192 r;
+  for (int i = 0; i < 3; i++) {
+    uint64_t lo = p[i + wsh];
+    uint64_t hi = (i + wsh + 1 < 6) ? p[i + wsh + 1] : 0;
+    r.w[i] = bsh ? (lo >> bsh) | (hi << (64 - bsh)) : lo;
+  }
+  return r;
+}
+CRM_DEV U192 u_divsmall(U192 a, uint64_t d) {  // floor(a / d), d < 2^32
+  U192 r;
+  uint64_t rem = 0;
+  for (int i = 2; i >= 0; i--) {
+    uint64_t hi = (rem << 32) | (a.w[i] >> 32);
+    uint64_t qh = hi / d;
+    rem = hi - qh * d;
+    uint64_t lo = (rem << 32) | (a.w[i] & 0xFFFFFFFFull);
+    uint64_t ql = lo / d;
+    rem = lo - ql * d;
+    r.w[i] = (qh << 32) | ql;
+  }
+  return r;
+}
+CRM_DEV U192 u_mul_small(U192 a, uint64_t m) {  // a m, m < 2^32, no overflow
+  U192 r;
+  uint64_t carry = 0;
+  for (int i = 0; i < 3; i++) {
+    uint64_t lo = a.w[i] * m, hi = __umul64hi(a.w[i], m);
+    uint64_t s = lo + carry;
+    hi += s < lo;
+    r.w[i] = s;
+    carry = hi;
+  }
+  return r;
+}
+CRM_DEV U192 u_shr(U192 a, int k) {  // k < 192
+  U192 r = u_zero();
+  int ws = k >> 6, bs = k & 63;
+  for (int i = 0; i + ws < 3; i++) {
+    uint64_t lo = a.w[i + ws], hi = (i + ws + 1 < 3) ? a.w[i + ws + 1] : 0;
+    r.w[i] = bs ? (lo >> bs) | (hi << (64 - bs)) : lo;
+  }
+  return r;
+}
+CRM_DEV U192 u_shl(U192 a, int k) {  // k < 192, no overflow
+  U192 r = u_zero();
+  int ws = k >> 6, bs = k & 63;
+  for (int i = 2; i - ws >= 0; i--) {
+    uint64_t hi = a.w[i - ws], lo = (i - ws - 1 >= 0) ? a.w[i - ws - 1] : 0;
+    r.w[i] = bs ? (hi << bs) | (lo >> (64 - bs)) : hi;
+  }
+  return r;
+}
+CRM_DEV int u_bitlen(U192 a) {
+  for (int i = 2; i >= 0; i--)
+    if (a.w[i]) return 64 * i + 64 - __clzll((long long)a.w[i]);
+  return 0;
+}
+CRM_DEV bool u_bit(U192 a, int i) { return i >= 0 && i < 192 && ((a.w[i >> 6] >> (i & 63)) & 1); }
+CRM_DEV U192 u_low(U192 a, int k) {  // a mod 2^k
+  U192 r = a;
+  for (int i = 0; i < 3; i++) {
+    int lo = 64 * i;
+    if (k <= lo) r.w[i] = 0;
+    else if (k < lo + 64) r.w[i] &= (1ull << (k - lo)) - 1;
+  }
+  return r;
+}
+CRM_DEV U192 u_pow2(int k) {
+  U192 r = u_zero();
+  r.w[k >> 6] = 1ull << (k & 63);
+  return r;
+}
+
+// Round the interval [M - dlo, M + dhi] (value M 2^-fb, M > 0) to binary64 nearest.
+// Returns false (unresolved) if a midpoint lies inside.  `neg` sets the sign.
+CRM_DEV bool u_round64(U192 M, int fb, uint64_t dlo, uint64_t dhi, bool neg, double &out) {
+  int b = u_bitlen(M);  // value in [2^(b-1-fb), 2^(b-fb))
+  int ex = b - 1 - fb;
+  int drop;
+  if (ex >= -1022)
+    drop = b - 53;
+  else
+    drop = b - 53 + (-1022 - ex);
+  if (drop <= 0 || drop > 191) return false;  // not reached by exp2 / log
+  U192 q = u_shr(M, drop);
+  U192 rem = u_low(M, drop);
+  U192 half = u_pow2(drop - 1);
+  U192 lo = u_sub(rem, U192{{dlo, 0, 0}});  // rem >= dlo assumed (checked below)
+  bool lo_ok = u_cmp(rem, U192{{dlo, 0, 0}}) >= 0;
+  U192 hi = u_add(rem, U192{{dhi, 0, 0}});
+  bool up;
+  if (lo_ok && u_cmp(lo, half) > 0)
+    up = true;
+  else if (u_cmp(hi, half) < 0)
+    up = false;
+  else
+    return false;
+  uint64_t qv = q.w[0];
+  uint64_t bits;
+  if (ex >= -1022)
+    bits = ((uint64_t)(ex + 1023) << 52) + (qv - (1ull << 52));
+  else
+    bits = qv;
+  bits += up ? 1 : 0;
+  if (bits >= 0x7FF0000000000000ull) bits = 0x7FF0000000000000ull;
+  out = bitsd(bits | (neg ? 0x8000000000000000ull : 0));
+  return true;
+}
+
+// exp2(x), x in (-1075, 1024), exactly: R = x - floor(4096 x)/4096 in [0, 2^-12),
+// u = R ln2 (Q0.191), e^u by Taylor (Q2.190), times the three table values (Q2.190).
+// Every step truncates (floors), so the computed y satisfies y <= 2^x 2^-k < y + 2^10
+// units of 2^-190 (16 Taylor terms, 4 products, R and ln2 truncation).
+CRM_DEV bool exp2d_exact(double x, double &out) {
+  double nd = floor(x * 4096.0);
+  long long N = (long long)nd;
+  double R = fma_(nd, -0x1p-12, x);  // exact, in [0, 2^-12)
+  int k = (int)(N >> 12);
+  int i = (int)(N & 4095);
+  U192 Rf = u_zero();
+  if (R > 0.0) {
+    uint64_t rb = dbits(R);
+    int re = (int)(rb >> 52) - 1075;
+    uint64_t rm = (rb & 0x000FFFFFFFFFFFFFull) | ((rb >> 52) ? (1ull << 52) : 0);
+    if ((rb >> 52) == 0) re = -1074;
+    int sh = re + 191;  // R 2^191 = rm 2^sh
+    U192 t = {{rm, 0, 0}};
+    Rf = sh >= 0 ? u_shl(t, sh) : (sh > -64 ? u_shr(t, -sh) : u_zero());
+  }
+  U192 ln2 = {{CRM_LN2_FX[0], CRM_LN2_FX[1], CRM_LN2_FX[2]}};
+  U192 u = u_shr(u_mulfx(Rf, ln2, 191), 1);  // Q2.190
+  U192 one = u_pow2(190);
+  U192 sum = u_add(one, u), term = u;
+  for (uint64_t n = 2; n < 40 && !u_is_zero(term); n++) {
+    term = u_divsmall(u_mulfx(term, u, 190), n);
+    sum = u_add(sum, term);
+  }
+  const unsigned long long *T = CRM_EXP2_FX_T;
+  int idx[3] = {i >> 8, (i >> 4) & 15, i & 15};
+  for (int a = 0; a < 3; a++) {
+    const unsigned long long *e = T + 48 * a + 3 * idx[a];
+    sum = u_mulfx(sum, U192{{e[0], e[1], e[2]}}, 190);
+  }
+  // value = sum 2^(k - 190): round with the interval [sum, sum + 2^10]
+  return u_round64(sum, 190 - k, 0, 1024, false, out);
+}
+
+// log(x), x > 0 finite, exactly: x = 2^e m, m in [1,2), c = 1 + j/128 <= m,
+// r = (m - c)/c in [0, 1/128) (Q0.191), log1p(r) = P - Q with P and Q the positive and
+// negative Taylor terms, S = log(c) + log1p(r); |log x| = |e ln2 + S| in Q11.181.
+CRM_DEV bool logd_exact(double x, double &out) {
+  uint64_t b = dbits(x);
+  int be = (int)(b >> 52);
+  uint64_t f = b & 0x000FFFFFFFFFFFFFull;
+  int e;
+  if (be == 0) {  // subnormal: move the leading 1 (at bit 52 - lz) to bit 52
+    int lz = __clzll((long long)f) - 11;
+    f = (f << lz) & 0x000FFFFFFFFFFFFFull;
+    e = -1022 - lz;
+  } else {
+    e = be - 1023;
+  }
+  int j = (int)(f >> 45);
+  uint64_t dlow = f & ((1ull << 45) - 1);  // (m - c) 2^52
+  // r = (m - c) 128 / (128 + j) in Q0.191: (m - c) 2^191 = dlow 2^139
+  U192 r = u_divsmall(u_shl(U192{{dlow, 0, 0}}, 139 + 7), 128 + j);
+  U192 P = u_zero(), Q = u_zero(), pw = r;
+  for (uint64_t n = 1; n < 40 && !u_is_zero(pw); n++) {
+    U192 t = u_divsmall(pw, n);
+    if (n & 1) P = u_add(P, t); else Q = u_add(Q, t);
+    pw = u_mulfx(pw, r, 191);
+  }
+  U192 L = {{CRM_LOG_FX_T[3 * j], CRM_LOG_FX_T[3 * j + 1], CRM_LOG_FX_T[3 * j + 2]}};
+  U192 S = u_sub(u_add(L, P), Q);  // in [0, ln2), Q0.191, error within +-64 units
+  U192 ln2 = {{CRM_LN2_FX[0], CRM_LN2_FX[1], CRM_LN2_FX[2]}};
+  U192 S10 = u_shr(S, 10);  // Q11.181
+  uint64_t ae = (uint64_t)(e < 0 ? -e : e);
+  U192 E = u_mul_small(u_shr(ln2, 10), ae);  // |e| ln2 < 2^10.5 fits Q11.181
+  U192 M;
+  bool neg = false;
+  if (e >= 0) {
+    M = u_add(E, S10);
+  } else {
+    M = u_sub(E, S10);
+    neg = true;
+  }
+  if (u_is_zero(M)) return false;
+  // errors (units of 2^-181): S within 64 units of 2^-191 (< 1), the shift of S 1, the
+  // truncated ln2 times |e|: |e| + 1.  The interval is M -+ (|e| + 16).
+  return u_round64(M, 181, ae + 16, ae + 16, neg, out);
+}
+
+CRM_DEV double exp2d_slow(double x, bool &unresolved) {
+  bool hard;
+  double r = exp2d_main(x, CRM_EXP2D_T, hard);
+  unresolved = false;
+  if (!hard) return r;
+  double out;
+  if (x == rint(x)) return ldexp(1.0, (int)x);  // exact powers of two (subnormal range)
+  bool ok = exp2d_exact(x, out);
+  unresolved = !ok;
+  return ok ? out : r;
+}
+
+CRM_DEV double logd_slow(double x, bool &unresolved) {
+  bool hard;
+  double r = logd_main(x, hard);
+  unresolved = false;
+  if (!hard) return r;
+  if (x == 1.0) return 0.0;
+  double out;
+  bool ok = logd_exact(x, out);
+  unresolved = !ok;
+  return ok ? out : r;
+}
+
+}  // namespace crm

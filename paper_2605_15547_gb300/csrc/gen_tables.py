@@ -351,6 +351,60 @@ for k in range(14):
 arr_d("CRM_ATAN_TAYLOR_DD", atdd, "(-1)^k/(2k+1), k = 0..13, double-double")
 emit()
 
+# ---------------------------------------------------------------- binary64 pair
+emit("// ===== binary64 exp2: x = k + (256 i1 + 16 i2 + i3)/4096 + R (Sec. II.B) =====")
+vals = []
+for a, div in ((1, 16), (2, 256), (3, 4096)):
+    for i in range(16):
+        vals += split(mp.power(2, mp.mpf(i) / div), d, 2)
+arr_d("CRM_EXP2D_T", vals, "2^(i/16), 2^(i/256), 2^(i/4096) (i = 0..15) as double-double, one table each")
+coefs = []
+for k in range(1, 9):
+    coefs += split(LN2 ** k / mp.factorial(k), d, 2)
+arr_d("CRM_EXP2D_C", coefs, "(ln 2)^k/k!, k = 1..8, double-double")
+
+
+def limbs192(v, frac_bits):
+    """floor(v 2^frac_bits) as three 64-bit limbs (little endian)"""
+    with mp.workprec(400):
+        N = int(mp.floor(v * mp.mpf(2) ** frac_bits))
+    assert 0 <= N < 2 ** 192
+    return [(N >> (64 * i)) & 0xFFFFFFFFFFFFFFFF for i in range(3)]
+
+
+def arr_u64(name, vals, comment):
+    emit(f"// {comment}")
+    emit(f"CRM_TABLE unsigned long long {name}[{len(vals)}] = {{")
+    for i in range(0, len(vals), 3):
+        emit("  " + ", ".join(f"0x{v:016X}ull" for v in vals[i:i + 3]) + ",")
+    emit("};")
+
+
+emit("// ----- exact (192-bit fixed-point) slow path constants -----")
+fx = []
+for a, div in ((1, 16), (2, 256), (3, 4096)):
+    for i in range(16):
+        fx += limbs192(mp.power(2, mp.mpf(i) / div), 190)  # Q2.190
+arr_u64("CRM_EXP2_FX_T", fx, "2^(i/16), 2^(i/256), 2^(i/4096) (i = 0..15) as floor(v 2^190), 3 limbs each")
+arr_u64("CRM_LN2_FX", limbs192(LN2, 191), "ln 2 as floor(ln2 2^191)")
+lfx = []
+for j in range(128):
+    lfx += limbs192(mp.log(1 + mp.mpf(j) / 128), 191)
+arr_u64("CRM_LOG_FX_T", lfx, "log(1 + j/128), j = 0..127, as floor(v 2^191)")
+emit("// ===== binary64 log: log x = e ln2 + L_j + log1p(m rcp_j - 1), rcp_j ~ 256/j =====")
+rc, Lv = [], []
+for j in range(192, 385):
+    r = d(mp.mpf(256) / j)
+    rc.append(r)
+    Lv += split(-mp.log(r), d, 2)
+arr_d("CRM_LOGD_RCP", rc, "rcp_j ~ 256/j (j = 192..384), doubles")
+arr_d("CRM_LOGD_L", Lv, "-log(rcp_j) as double-double")
+lc = []
+for k in range(1, 13):
+    lc += split(mp.mpf((-1) ** (k + 1)) / k, d, 2)
+arr_d("CRM_LOGD_C", lc, "(-1)^(k+1)/k, k = 1..12, double-double")
+emit()
+
 emit("// ===== end =====")
 
 text = "\n".join(lines) + "\n"

@@ -204,11 +204,12 @@ CRM_DEV Pair<double> atan_ratio_dd(Pair<double> a, Pair<double> b) {
   return sw ? dd_add(dd(CRM_PIO2_D_HI, CRM_PIO2_D_LO), dd_neg(r)) : r;
 }
 
-template <int KIND> CRM_DEV float atrig_slow(float x, bool &unresolved) {
+template <int KIND> CRM_DEV float atrig_slow(float x, bool &unresolved, bool force) {
   bool hard;
   float r = atrig_plain<KIND>(x, CRM_ATAN_T17_D, hard);
   unresolved = false;
-  if (!hard) return r;
+  float sp;
+  if ((!hard && !force) || atrig_special<KIND>(x, sp)) return r;
   double ax = fabs((double)x);
   Pair<double> a, b;
   bool flip = false;

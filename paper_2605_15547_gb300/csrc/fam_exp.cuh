@@ -185,11 +185,12 @@ template <int KIND> CRM_DEV float exp_dd(float x, bool &hard) {
 }
 
 // Slow path used for lanes whose fast-path test failed: FP64 tier, then double-double.
-template <int KIND> CRM_DEV float exp_slow(float x, bool &unresolved) {
+template <int KIND> CRM_DEV float exp_slow(float x, bool &unresolved, bool force) {
   bool hard;
   float r = exp_plain<KIND>(x, CRM_EXP2_T16_D, hard);
   unresolved = false;
-  if (!hard) return r;
+  float sp;
+  if ((!hard && !force) || exp_special<KIND>(x, sp)) return r;
   r = exp_dd<KIND>(x, hard);
   unresolved = hard;
   return r;

@@ -275,11 +275,12 @@ template <int H> CRM_DEV Pair<double> hyp_dd_y(float x) {
   return y;
 }
 
-template <int H> CRM_DEV float hyp_slow(float x, bool &unresolved) {
+template <int H> CRM_DEV float hyp_slow(float x, bool &unresolved, bool force) {
   bool hard;
   float r = hyp_plain<H>(x, CRM_EXP2_T16_D, hard);
   unresolved = false;
-  if (!hard) return r;
+  float sp;
+  if ((!hard && !force) || hyp_special<H>(x, sp)) return r;
   Pair<double> y = hyp_dd_y<H>(x);
   r = round_dd_to_f(y.hi, y.lo, HYP_DD_EPS * fabs(y.hi), hard);
   unresolved = hard;

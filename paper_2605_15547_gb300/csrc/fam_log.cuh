@@ -254,11 +254,11 @@ template <int KIND> CRM_DEV float log_dd(float x, bool &hard) {
   return round_dd_to_f(y.hi, y.lo, LOG_DD_EPS * fabs(y.hi), hard);
 }
 
-template <int KIND> CRM_DEV float log_slow(float x, bool &unresolved) {
+template <int KIND> CRM_DEV float log_slow(float x, bool &unresolved, bool force) {
   bool hard;
   float r = log_plain<KIND>(x, (const double2 *)CRM_LN_T97_D, hard);
   unresolved = false;
-  if (!hard) return r;
+  if ((!hard && !force) || !log_ok<KIND>(x)) return r;
   r = log_dd<KIND>(x, hard);
   unresolved = hard;
   return r;

@@ -72,11 +72,12 @@ CRM_DEV float rsqrt_df(float x, bool &hard) {
 // midpoint m; RN(1/sqrt(x)) is up when x m^2 < 1, dn otherwise.  If y is itself a
 // binary32 value (dn == up) it lies within 2^-50 of 1/sqrt(x) while the midpoints are
 // 2^-25 away, so it is the answer.
-CRM_DEV float rsqrt_slow(float x, bool &unresolved) {
+CRM_DEV float rsqrt_slow(float x, bool &unresolved, bool force) {
   bool hard;
   float r = rsqrt_plain(x, hard);
   unresolved = false;
-  if (!hard) return r;
+  float sp;
+  if ((!hard && !force) || rsqrt_special(x, sp)) return r;
   double y = rsqrt_plain_y(x);
   float dn = __double2float_rd(y), up = __double2float_ru(y);
   if (dn == up) return dn;

@@ -283,11 +283,12 @@ CRM_DEV void trig_dd_core(float x, Pair<double> &A, Pair<double> &B, int &q) {
   B = dd_add(dd_mul(C, ct), dd_neg(dd_mul(S, st)));
 }
 
-template <int KIND> CRM_DEV void trig_slow(float x, float *y, bool &unresolved) {
+template <int KIND> CRM_DEV void trig_slow(float x, float *y, bool &unresolved, bool force) {
   bool hard;
   trig_plain<KIND>(x, CRM_TWO_OVER_PI_W, CRM_SINCOS_T32_D, y, hard);
   unresolved = false;
-  if (!hard) return;
+  float sp;
+  if ((!hard && !force) || trig_special(x, sp)) return;
   Pair<double> A, B, sn, cs;
   int q;
   trig_dd_core(x, A, B, q);

@@ -137,6 +137,7 @@ template <int FORM> struct TileOp {
 };
 struct SlowOp {
   float x;
+  bool force;
   const BatchDesc *d;
   uint64_t idx;
   unsigned long long *unres;
@@ -144,7 +145,7 @@ struct SlowOp {
     using T = typename Fn::T;
     T y[2];
     bool u;
-    Fn::slow((T)x, y, u);
+    Fn::slow((T)x, y, u, force);
     T *out = (T *)d->out;
     out[idx] = y[0];
     if (Fn::NOUT == 2) out[d->n + idx] = y[1];
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(KBLOCK) k_batch_slow(BatchArgs b) {
     uint32_t aid = (uint32_t)(e.idx >> 40);
     uint64_t idx = e.idx & ((1ull << 40) - 1);
     const BatchDesc *d = &b.descs[aid];
-    SlowOp op{bitsf((uint32_t)e.x), d, idx, &b.hdr->unresolved_total};
+    SlowOp op{bitsf((uint32_t)e.x), b.force_hard != 0, d, idx, &b.hdr->unresolved_total};
     CRM_FOR_FUNC(d->func, op);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&b.hdr->hard_total, (unsigned long long)b.hdr->count);

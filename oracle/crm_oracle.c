@@ -235,32 +235,31 @@ static int mag_div(limb *q, const limb *a, int na, const limb *b, int nb) {
   return inexact;
 }
 
-/* floor(sqrt(N)) by the digit-by-digit binary method; returns 1 if inexact. */
+/* floor(sqrt(N)) by Newton's iteration on integers (Heron's rule with floors): from any
+   start x >= floor(sqrt(N)) the sequence x' = floor((x + floor(N / x)) / 2) decreases
+   strictly until it reaches floor(sqrt(N)), where the next step no longer decreases.
+   Returns 1 if inexact (N is not a perfect square). */
 static int mag_isqrt(limb *res, const limb *N, int nl) {
-  limb rem[2 * MAXL + 2], r[2 * MAXL + 2], bit[2 * MAXL + 2], t[2 * MAXL + 2];
-  memcpy(rem, N, 8 * (size_t)nl);
-  memset(r, 0, 8 * (size_t)nl);
-  memset(bit, 0, 8 * (size_t)nl);
+  limb x[2 * MAXL + 2], q[2 * MAXL + 2], y[2 * MAXL + 2], sq[4 * MAXL + 4];
   int b = mag_bitlen(N, nl);
-  if (b == 0) {
-    memset(res, 0, 8 * (size_t)nl);
-    return 0;
+  memset(res, 0, 8 * (size_t)nl);
+  if (b == 0) return 0;
+  memset(x, 0, 8 * (size_t)(nl + 1));
+  int h = (b + 1) / 2; /* 2^h >= sqrt(N) since N < 2^b <= 2^(2h) */
+  x[h >> 6] = 1ull << (h & 63);
+  for (;;) {
+    mag_div(q, N, nl, x, nl);
+    q[nl] = 0;
+    mag_add(y, x, q, nl + 1);
+    mag_shr(y, y, nl + 1, 1);
+    if (mag_cmp(y, x, nl + 1) >= 0) break;
+    memcpy(x, y, 8 * (size_t)(nl + 1));
   }
-  int pos = (b - 1) & ~1;
-  bit[pos >> 6] = 1ull << (pos & 63);
-  while (!mag_is_zero(bit, nl)) {
-    mag_add(t, r, bit, nl);
-    if (mag_cmp(rem, t, nl) >= 0) {
-      mag_sub(rem, rem, t, nl);
-      mag_shr(r, r, nl, 1);
-      mag_add(r, r, bit, nl);
-    } else {
-      mag_shr(r, r, nl, 1);
-    }
-    mag_shr(bit, bit, nl, 2);
-  }
-  memcpy(res, r, 8 * (size_t)nl);
-  return !mag_is_zero(rem, nl);
+  memcpy(res, x, 8 * (size_t)nl);
+  mag_mul(sq, x, nl, x, nl);
+  for (int i = nl; i < 2 * nl; i++)
+    if (sq[i]) die("isqrt: square too large");
+  return mag_cmp(sq, N, nl) != 0;
 }
 
 /* ===================== signed fixed point (value = N / 2^F) ===================== */
@@ -1590,8 +1589,8 @@ static void evaluate(int kind, const dec_t *x, int n, res_t *R) {
   }
 }
 
-static const int LEVEL_LIMBS[] = {3, 5, 9, 17, 33};
-#define NLEVELS 5
+static const int LEVEL_LIMBS[] = {2, 3, 5, 9, 17, 33};
+#define NLEVELS 6
 
 static int ziv(int kind, const dec_t *x, uint64_t xbits, const fmt_t *f, uint64_t *out) {
   if (special(kind, x, f, xbits, out)) {

@@ -141,9 +141,15 @@ def test_integer_sqrt_matches_python_isqrt():
     for _ in range(300):
         nl = rnd.randint(1, 8)
         N = rnd.getrandbits(64 * nl)
-        if rnd.random() < 0.3:
+        u = rnd.random()
+        if u < 0.3:
             s = rnd.getrandbits(32 * nl)
             N = s * s  # perfect squares: exactness flag must be 0
+        elif u < 0.45:
+            s = rnd.getrandbits(32 * nl)
+            N = max(s * s - 1, 0)  # one below a square: the root drops by one
+        elif u < 0.55:
+            N = (1 << (64 * nl)) - 1  # all ones: largest value of the width
         r, inexact = O.test_isqrt(N, nl)
         assert r == math.isqrt(N)
         assert inexact == int(r * r != N)

@@ -1,0 +1,98 @@
+"""Exhaustive binary32 sweeps on the GPU: all 2^32 input bit patterns per function.
+
+* Against the oracle: the device results of every chunk of 2^24 consecutive patterns are
+  digested (tests/exhaustive_hash.py) and compared with the digests the oracle's results
+  gave (tests/golden/exhaustive/<func>.txt, written by tests/golden/make_exhaustive.py).
+  A function whose file lists all 256 chunks is checked over its whole input space.
+* Between the forms: the double-float form and the plain FP64 form (two independent
+  evaluations with their own rounding tests) give the same bits on all 2^32 inputs, and
+  sincosf gives (sinf, cosf) bit for bit.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import exhaustive_hash as EH  # noqa: E402
+import paper_2605_15547_gb300 as crm  # noqa: E402
+from paper_2605_15547_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "exhaustive")
+SINGLE = [f for f in W.F32_FUNCS if f != "sincosf"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    crm.set_force_slow(False)
+    yield
+
+
+@pytest.fixture(scope="module")
+def weights():
+    w1, w2 = EH.weights()
+    return torch.from_numpy(w1).cuda(), torch.from_numpy(w2).cuda()
+
+
+def chunk_input(c):
+    base = c << EH.CHUNK_LOG2
+    bits = torch.arange(base, base + EH.CHUNK, dtype=torch.int64, device="cuda")
+    bits = torch.remainder(bits + 2**31, 2**32) - 2**31  # the uint32 pattern as int32
+    return bits.to(torch.int32).view(torch.float32)
+
+
+@pytest.mark.parametrize("func", SINGLE)
+def test_exhaustive_against_oracle_digests(func, weights):
+    path = os.path.join(GOLDEN, func + ".txt")
+    if not os.path.exists(path):
+        pytest.skip(f"no oracle digests for {func}")
+    ref = EH.read_fixture(path)
+    if not ref:
+        pytest.skip(f"no oracle digests for {func}")
+    w1, w2 = weights
+    y = torch.empty(EH.CHUNK, dtype=torch.float32, device="cuda")
+    bad = []
+    crm.stats_reset()
+    for c in sorted(ref):
+        crm.eval_into(func, chunk_input(c), y)
+        got = EH.digest_torch(y.view(torch.int32), w1, w2)
+        if got != ref[c]:
+            bad.append(c)
+    assert not bad, f"{func}: chunks {bad[:8]} differ from the oracle ({len(bad)} of {len(ref)})"
+    assert crm.stats()["unresolved_total"] == 0
+    if len(ref) < EH.NCHUNKS:
+        print(f"{func}: {len(ref)} of {EH.NCHUNKS} chunks covered by oracle digests")
+
+
+@pytest.mark.parametrize("func", SINGLE)
+def test_exhaustive_forms_agree(func):
+    a = torch.empty(EH.CHUNK, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    for c in range(EH.NCHUNKS):
+        x = chunk_input(c)
+        crm.eval_into(func, x, a, form="df")
+        crm.eval_into(func, x, b, form="plain")
+        if not torch.equal(a.view(torch.int32), b.view(torch.int32)):
+            d = torch.nonzero(a.view(torch.int32) != b.view(torch.int32))[:4].flatten().tolist()
+            pytest.fail(f"{func}: forms differ in chunk {c} at offsets {d}")
+
+
+def test_exhaustive_sincosf_is_sinf_cosf():
+    s = torch.empty(EH.CHUNK, dtype=torch.float32, device="cuda")
+    co = torch.empty_like(s)
+    sc = torch.empty(2 * EH.CHUNK, dtype=torch.float32, device="cuda")
+    for c in range(EH.NCHUNKS):
+        x = chunk_input(c)
+        crm.eval_into("sinf", x, s)
+        crm.eval_into("cosf", x, co)
+        crm.eval_into("sincosf", x, sc)
+        ok = torch.equal(sc[:EH.CHUNK].view(torch.int32), s.view(torch.int32)) and \
+            torch.equal(sc[EH.CHUNK:].view(torch.int32), co.view(torch.int32))
+        assert ok, f"sincosf differs from (sinf, cosf) in chunk {c}"

@@ -104,6 +104,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest of the ranks' values (timings: the job is as slow as its slowest rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gelem_s(elems_per_rank: int, steps: int, world: int, ms_total: float) -> float:
+    """Weak scaling: every rank evaluates its own copy of the workload."""
+    return elems_per_rank * steps * world / (ms_total / 1e3) / 1e9
+
+
 def bytes_per_elem(func: str) -> int:
     return 12 if func == "sincosf" else (16 if func in ("exp2", "log") else 8)
 
@@ -232,14 +248,18 @@ def run_batch(args, crm, torch, dev, stream, rank, world):
     clocks.start()
     time.sleep(0.3)
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     s.record(stream)
     for _ in range(args.steps):
         crm.eval_batch(items, form=args.form, stream=stream)
     e.record(stream)
     e.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     clk = clocks.stop()
-    ms = s.elapsed_time(e)
+    ms = max_over_ranks(s.elapsed_time(e), world, dev)
     st = crm.stats(stream=stream)
     # one launch per array, for comparison (also via CUDA events)
     s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -263,7 +283,7 @@ def run_batch(args, crm, torch, dev, stream, rank, world):
     ms_graph = s3.elapsed_time(e3)
     nbytes = sum(x.numel() * 4 + y.numel() * 4 for _, x, y in items)
     peak, kind = load_peaks()
-    value = n_elems * args.steps / (ms / 1e3) / 1e9
+    value = whole_job_gelem_s(n_elems, args.steps, world, ms)
     achieved = nbytes / (ms / args.steps / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
@@ -357,13 +377,9 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    ms_total = t_s.elapsed_time(t_e)
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(t_s.elapsed_time(t_e), world, dev)
     st = crm.stats()
-    value = n_elems * args.steps * world / (ms_total / 1e3) / 1e9
+    value = whole_job_gelem_s(n_elems, args.steps, world, ms_total)
 
     # per function, both forms (back-to-back calls, device time per call)
     other = "plain" if args.form != "plain" else "auto"

@@ -135,11 +135,12 @@ CRM_DEV void trig_plain(float x, const uint32_t *P, const double *SC, float *y, 
 // The same integer reduction; the 64-bit fraction becomes a float pair without
 // conversion instructions: with F' = F + 2^63 (so f + 1/2 = F' 2^-64 >= 0), three
 // chunks of 23, 23 and 18 bits become exact floats by the 2^23 magic-number trick and
-// f = (c0 2^-23 - 1/2) + (c1 2^-46 + c2 2^-64).  Then t = f pi/64 as a pair, and
+// f = (c0 2^-23 - 1/2) + c1 2^-46 + c2 2^-64.  Then t = f pi/64 as a pair, and
 //   cos t = 1 - t^2/2 + t^4/24 - t^6/720,  sin t = t - t^3/6 + t^5/120 - t^7/5040,
 // with t^2 and t^3/6 carried as pairs (exact FMA splits), the higher terms in float.
-// Error budget (relative to the result): f to 2^-63.6 absolute (lanes with j = 0 and
-// |f| < 2^-24, where the result is as small as t, go to the slow path: 2^-40 there);
+// Error budget (relative to the result): f to 2^-63.6 absolute plus 2^-48 relative
+// (lanes with j = 0 and |f| < 2^-24, where the result is as small as t, go to the slow
+// path: 2^-40 there);
 // pi/64 pair 2^-48; t products 2^-46; sin t, cos t 2^-45; table pairs 2^-48; the
 // rotation terms S cos t + C sin t lose at most 2^5.4: total < 2^-39, inside the 2^-37
 // that hard_df allows.
@@ -164,8 +165,13 @@ CRM_DEV TrigF trig_df_core(float x, const uint32_t *P, const float4 *SC) {
   float f0 = bitsf(0x4B000000u | c0) - 0x1p23f;
   float f1 = bitsf(0x4B000000u | c1) - 0x1p23f;
   float f2 = bitsf(0x4B000000u | c2) - 0x1p23f;
-  float fh = fma_(f0, 0x1p-23f, -0.5f);
-  float fl = fma_(f1, 0x1p-46f, f2 * 0x1p-64f);
+  // f = (c0 2^-23 - 1/2) + c1 2^-46 + c2 2^-64, three exact floats; the first two are
+  // joined by TwoSum, so that (fh, fl) carries f to 2^-24 |fl| + 2^-64 even when the
+  // first chunk is zero or cancels (|f| small: the case that decides the rounding of
+  // results near multiples of pi/2).
+  Pair<float> fs = two_sum(fma_(f0, 0x1p-23f, -0.5f), f1 * 0x1p-46f);
+  float fh = fs.hi;
+  float fl = fma_(f2, 0x1p-64f, fs.lo);
   float th = fh * CRM_PIO64_F_HI;
   float tl = fma_(fh, CRM_PIO64_F_HI, -th);
   tl = fma_(fh, CRM_PIO64_F_LO, tl);

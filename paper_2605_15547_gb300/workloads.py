@@ -9,6 +9,7 @@ Recipes (the paper measures on synthetic uniform inputs: Sec. III.A-D):
 * ``domain_bits(func)``: uniform random bit patterns restricted to the function's domain
   of finite, non-trivially-saturated inputs (rejection sampling), plus 1% specials;
 * ``expf_mixed``: 90% uniform in [-103.98, 88.73] and 10% from the specials pool;
+* ``near_multiples_of_pio2``: binary32 values nearest to k pi/2 and their neighbours;
 * ``specials(func)``: zeros, infinities, quiet and signalling NaNs, subnormals, +-FLT_MAX,
   +-FLT_MIN and a few ulps around the function's overflow/underflow boundaries.
 Seeds follow seed = 0xC0DE0000 + 256 * config + func_id.
@@ -117,6 +118,17 @@ def sinf_with_large(n: int, rng: np.random.Generator, frac: float = 0.05) -> np.
     idx = rng.choice(n, k, replace=False)
     x[idx] = loguniform(20.0, 127.0, k, rng, signed=True)
     return x
+
+
+def near_multiples_of_pio2(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Binary32 values nearest to k pi/2 (k log-uniform up to 2^20, random sign) and their neighbours
+    within 2 ulps: arguments whose reduced value is tiny, where sin, cos or tan is small or
+    huge and the reduction's relative accuracy decides the rounding."""
+    k = np.round(np.exp2(rng.uniform(0.0, 20.0, n // 5 + 1)))
+    base = (k * (np.pi / 2)).astype(np.float32).view(np.uint32).astype(np.int64)
+    out = np.concatenate([base + d for d in (-2, -1, 0, 1, 2)])[:n].astype(np.uint32)
+    sign = rng.integers(0, 2, out.size).astype(np.uint32) << np.uint32(31)
+    return (out | sign).view(np.float32)
 
 
 def f64_uniform(lo: float, hi: float, n: int, rng: np.random.Generator) -> np.ndarray:

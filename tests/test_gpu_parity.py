@@ -31,6 +31,14 @@ def forms_of(func):
     return out
 
 
+# Inputs on which an earlier double-float reduction lost accuracy (x within a few 2^-20
+# of a multiple of pi/2, found by the exhaustive sweep); all must be correctly rounded.
+TRIG_REGRESSION = np.array([
+    0x543146A6, 0x54B146A6, 0x553146A6, 0x72A03E3A, 0x435D7B77, 0x53B146A6, 0x5D6BD9CD,
+    0x5DDC92D2, 0x61D3B126, 0x673D1651, 0x6946E3BB, 0x7EB919F2], dtype=np.uint32)
+TRIG_REGRESSION = np.concatenate([TRIG_REGRESSION, TRIG_REGRESSION | np.uint32(0x80000000)])
+
+
 def focus_inputs(func, rng):
     """function-specific input sets on top of the generic ones"""
     parts = []
@@ -40,7 +48,8 @@ def focus_inputs(func, rng):
             parts += [W.uniform(-1, 1, 20000, rng), W.loguniform(-149, -5, 20000, rng, signed=True)]
     elif func in ("sinf", "cosf", "sincosf", "tanf"):
         parts += [W.uniform(-10, 10, 20000, rng), W.sinf_with_large(20000, rng, frac=0.3),
-                  W.loguniform(-20, 127, 20000, rng, signed=True), W.loguniform(-149, -5, 5000, rng, signed=True)]
+                  W.loguniform(-20, 127, 20000, rng, signed=True), W.loguniform(-149, -5, 5000, rng, signed=True),
+                  W.near_multiples_of_pio2(20000, rng), TRIG_REGRESSION.view(np.float32)]
     elif func in ("asinf", "acosf"):
         parts += [W.uniform(-1, 1, 30000, rng), 1.0 - W.loguniform(-24, -1, 10000, rng, signed=False),
                   -1.0 + W.loguniform(-24, -1, 10000, rng, signed=False)]

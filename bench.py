@@ -10,13 +10,17 @@ Workloads (--workload):
           uniform random bit patterns restricted to the function's domain, plus 1%
           specials (generated on the GPU, seeded).  A step evaluates every array once.
           256 MiB per input, larger than the 129 MB L2: no flush needed between steps.
-  precision  expf/logf/sinf/tanhf/rsqrtf on 2^28 elements (U[-10,10]; log-uniform
-          [2^-126, 2^127] for logf/rsqrtf).
+  precision  expf/logf/sinf/tanhf/rsqrtf on 2^28-element arrays: (i) U[-10,10], (ii)
+          log-uniform magnitudes in [2^-126, 2^127]; sinf also (iii) = (i) with 5% of the
+          arguments in |x| > 2^20.  Hard-case rate reported per array.
+  f64     binary64 exp2 and log on 2^26-element arrays: uniform over the domain and the
+          paper's U[-20,20] (exp2) / U[0.125,8] (log).
   batch   10,000 arrays, lengths log-uniform in [2^6, 2^22], functions uniform over the
           19: one batched launch per step (and, for comparison, one launch per array).
-The step uses --form (auto = the fastest form of each function, double-float for all 19;
-plain = the FP64-internal form); the other form is measured beside it per function.
-`--impl reference` times the CPU oracle on a bounded sample of the same workload.
+Before the warm-up the autotuner picks each array's launch shape (the batch tile size for
+the batch workload).  The step uses --form (auto = double-float for the 19 binary32
+functions; plain = the FP64-internal form); the other form is measured beside it per
+array.  `--impl reference` times the CPU oracle on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -126,45 +130,6 @@ def bytes_per_elem(func: str) -> int:
 
 # ----------------------------------------------------------------------------- workloads
 
-def workload_spec(name: str, scale: int):
-    if name == "all19":
-        n = (1 << 26) >> scale
-        return [(f, n) for f in W.F32_FUNCS], {
-            "workload": f"19 binary32 functions x 2^{26 - scale} inputs: domain bit patterns + 1% specials",
-            "elems_per_func": n}
-    if name == "precision":
-        n = (1 << 28) >> scale
-        return [(f, n) for f in ("expf", "logf", "sinf", "tanhf", "rsqrtf")], {
-            "workload": f"expf/logf/sinf/tanhf/rsqrtf x 2^{28 - scale}: U[-10,10] (log-uniform "
-                        "[2^-126,2^127] for logf, rsqrtf)", "elems_per_func": n}
-    raise SystemExit(f"unknown workload {name}")
-
-
-def make_input_host(name, func, n):
-    if name == "all19":
-        return W.domain_bits(func, n, W.rng_for(2, func)).view(np.float32)
-    rng = W.rng_for(3, func)
-    if func in ("logf", "rsqrtf"):
-        return W.loguniform(-126, 127, n, rng, signed=False)
-    return W.uniform(-10, 10, n, rng)
-
-
-def make_input_device(name, func, n, dev):
-    """Same recipe as make_input_host, generated on the device (used at full size)."""
-    import torch
-    if name == "all19":
-        gen = torch.Generator(device=dev)
-        gen.manual_seed(W.seed_for(2, func))
-        x = W.domain_bits_device(func, n, gen, device=dev)
-        rng = W.rng_for(2, func, salt=1)
-        ns = int(n * 0.01)
-        sp = np.resize(W.specials_f32(func, rng), ns)
-        pos = torch.from_numpy(rng.choice(n, ns, replace=False)).to(dev)
-        x[pos] = torch.from_numpy(sp.view(np.float32)).to(dev)
-        return x
-    return torch.from_numpy(make_input_host(name, func, n)).to(dev)
-
-
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -174,14 +139,16 @@ def run_reference(args):
     from oracle import oracle as O
     O.build()
     cores = os.cpu_count() or 1
-    if args.workload == "batch":
-        items = [(f, 1 << 14) for f in W.F32_FUNCS]
-        cfg = {"workload": "batch: 10,000 arrays, lengths log-uniform [2^6,2^22], 19 functions"}
-    else:
-        items, cfg = workload_spec(args.workload, args.scale)
     sample = args.ref_sample
-    xs = [(f, make_input_host("all19" if args.workload == "batch" else args.workload, f, sample).view(np.uint32))
-          for f, _ in items]
+    if args.workload == "batch":
+        items = [(f, f, sample) for f in W.F32_FUNCS]
+        cfg = {"workload": "batch: 10,000 arrays, lengths log-uniform [2^6,2^22], 19 functions"}
+        wl = "all19"  # the batch arrays use the domain recipe
+    else:
+        items, cfg = W.bench_arrays(args.workload, args.scale)
+        wl = args.workload
+    bits = np.uint64 if args.workload == "f64" else np.uint32
+    xs = [(f, W.bench_input_host(wl, lab, f, sample).view(bits)) for lab, f, _ in items]
     O.eval_bits(xs[0][0], xs[0][1][:1024])
     times = []
     for step in range(args.warmup + args.steps):
@@ -240,6 +207,9 @@ def run_batch(args, crm, torch, dev, stream, rank, world):
     items = list(zip(funcs, xs, ys))
     n_elems = int(lens.sum())
     crm.reserve(1 << 24, count, stream=stream)
+    tile = None
+    if not args.no_autotune:
+        tile, _ = crm.autotune_batch(items, form=args.form, reps=1, stream=stream)
     for _ in range(args.warmup):
         crm.eval_batch(items, form=args.form, stream=stream)
     torch.cuda.synchronize()
@@ -291,7 +261,8 @@ def run_batch(args, crm, torch, dev, stream, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batch: {count} arrays, lengths log-uniform [2^6,2^22] >> {args.scale}, "
                                "functions uniform over the 19", "total_elems": n_elems, "form": args.form,
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
+                   "tile_log2": tile if tile is not None else "default 14"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "k_batch (step)", "peak_kind": kind},
         "one_launch_per_array": {"gelem_s": n_elems / (ms_single / 1e3) / 1e9, "ms": ms_single,
@@ -314,13 +285,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="auto", choices=["auto", "plain", "df"])
-    ap.add_argument("--workload", default="all19", choices=["all19", "precision", "batch"])
+    ap.add_argument("--workload", default="all19", choices=["all19", "precision", "f64", "batch"])
     ap.add_argument("--scale", type=int, default=0, help="divide sizes by 2^scale (testing)")
     ap.add_argument("--ref-sample", type=int, default=1 << 15)
     ap.add_argument("--cpu-sample", type=int, default=1 << 18)
     ap.add_argument("--batch-count", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--funcs", default="", help="comma list restricting the workload (testing)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -344,19 +316,31 @@ def main():
         with torch.cuda.stream(side):
             return run_batch(args, crm, torch, dev, side, rank, world)
 
-    spec, cfg = workload_spec(args.workload, args.scale)
+    spec, cfg = W.bench_arrays(args.workload, args.scale)
     if args.funcs:
         keep = set(args.funcs.split(","))
-        spec = [s for s in spec if s[0] in keep]
-    funcs = [f for f, _ in spec]
-    xs = [make_input_device(args.workload, f, n, dev) for f, n in spec]
-    ys = [torch.empty(((2,) if f == "sincosf" else ()) + (x.numel(),), dtype=torch.float32, device=dev)
+        spec = [s for s in spec if s[1] in keep or s[0] in keep]
+    labels = [lab for lab, _, _ in spec]
+    funcs = [f for _, f, _ in spec]
+    xs = [W.bench_input_device(args.workload, lab, f, n, dev) for lab, f, n in spec]
+    ys = [torch.empty(((2,) if f == "sincosf" else ()) + (x.numel(),), dtype=x.dtype, device=dev)
           for f, x in zip(funcs, xs)]
     n_elems = sum(x.numel() for x in xs)
+    f64 = args.workload == "f64"
 
     def step(form):
         for f, x, y in zip(funcs, xs, ys):
             crm.eval_into(f, x, y, form=form)
+
+    # the autotuner picks each array's launch shape on that array (untimed)
+    tuned = {}
+    if not args.no_autotune:
+        for lab, f, x, y in zip(labels, funcs, xs, ys):
+            best, _ = crm.autotune(f, x, y, form=args.form, reps=2)
+            info = crm.variant_info(best)
+            tuned[lab] = ("pipelined" if info["pipelined"] else
+                          f"u{info['unroll']}b{info['block']}" + ("pf" if info["prefetch"] else "") +
+                          (f"m{info['min_blocks']}" if info["min_blocks"] > 1 else ""))
 
     for _ in range(args.warmup):
         step(args.form)
@@ -381,23 +365,32 @@ def main():
     st = crm.stats()
     value = whole_job_gelem_s(n_elems, args.steps, world, ms_total)
 
-    # per function, both forms (back-to-back calls, device time per call)
+    # per array, both forms (back-to-back calls, device time per call), and hard-case rates
     other = "plain" if args.form != "plain" else "auto"
     ms_main = time_calls(crm, torch, funcs, xs, ys, args.form, 3, stream)
-    ms_other = time_calls(crm, torch, funcs, xs, ys, other, 2, stream)
+    try:
+        ms_other = time_calls(crm, torch, funcs, xs, ys, other, 2, stream)
+    except crm.CrmError:  # the binary64 pair has one form
+        ms_other = None
+    hard = []
+    for f, x, y in zip(funcs, xs, ys):
+        crm.stats_reset()
+        crm.eval_into(f, x, y, form=args.form)
+        hard.append(crm.stats()["hard_total"] / x.numel())
     peak, peak_kind = load_peaks()
-    per_func = {}
-    for i, f in enumerate(funcs):
+    per_arr = {}
+    for i, lab in enumerate(labels):
         n = xs[i].numel()
-        per_func[f] = {
+        per_arr[lab] = {
             args.form: {"gelem_s": n / (ms_main[i] / 1e3) / 1e9,
-                        "hbm_frac": n * bytes_per_elem(f) / (ms_main[i] / 1e3) / 1e9 / peak},
-            other: {"gelem_s": n / (ms_other[i] / 1e3) / 1e9},
-        }
-        hi, lo = (ms_other[i], ms_main[i]) if args.form != "plain" else (ms_main[i], ms_other[i])
-        per_func[f]["df_over_plain"] = hi / lo
-    step_other = sum(x.numel() for x in xs) / (sum(ms_other) / 1e3) / 1e9
-    # dominant kernel: the function taking the largest share of the step
+                        "hbm_frac": n * bytes_per_elem(funcs[i]) / (ms_main[i] / 1e3) / 1e9 / peak},
+            "hard_case_rate": hard[i]}
+        if ms_other is not None:
+            per_arr[lab][other] = {"gelem_s": n / (ms_other[i] / 1e3) / 1e9}
+            hi, lo = (ms_other[i], ms_main[i]) if args.form != "plain" else (ms_main[i], ms_other[i])
+            per_arr[lab]["df_over_plain"] = hi / lo
+    step_other = (n_elems / (sum(ms_other) / 1e3) / 1e9) if ms_other is not None else None
+    # dominant kernel: the array taking the largest share of the step
     dom = int(np.argmax(ms_main))
     dom_bytes = xs[dom].numel() * bytes_per_elem(funcs[dom])
     achieved = dom_bytes / (ms_main[dom] / 1e3) / 1e9
@@ -405,15 +398,15 @@ def main():
     e2e = None
     if not args.no_e2e:
         hin = [x.cpu().pin_memory() for x in xs]
-        hout = [torch.empty(tuple(y.shape), dtype=torch.float32).pin_memory() for y in ys]
+        hout = [torch.empty(tuple(y.shape), dtype=y.dtype).pin_memory() for y in ys]
         crm.eval_host(funcs[0], hin[0].numpy(), hout[0].numpy().reshape(-1), form=args.form)
         t0 = time.perf_counter()
         for f, a, b in zip(funcs, hin, hout):
             crm.eval_host(f, a.numpy(), b.numpy().reshape(-1), form=args.form)
         t1 = time.perf_counter()
         e2e = {"value": n_elems / (t1 - t0) / 1e9, "unit": "Gelem/s",
-               "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in xs)),
-               "d2h_bytes_per_step": int(sum(y.numel() * 4 for y in ys)),
+               "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in xs)),
+               "d2h_bytes_per_step": int(sum(y.numel() * y.element_size() for y in ys)),
                "note": "crm_eval_host: page-locked host in/out, chunked copies overlapped with compute"}
 
     cpu = None
@@ -421,27 +414,28 @@ def main():
         from oracle import oracle as O
         O.build()
         cores = os.cpu_count() or 1
-        sample = [(f, xs[i][:args.cpu_sample].cpu().numpy().view(np.uint32)) for i, f in enumerate(funcs)]
+        bits = np.uint64 if f64 else np.uint32
+        sample = [(f, xs[i][:args.cpu_sample].cpu().numpy().view(bits)) for i, f in enumerate(funcs)]
         t0 = time.perf_counter()
         for f, xh in sample:
             O.eval_bits(f, xh, nthreads=cores)
         dt = time.perf_counter() - t0
         cnt = sum(x.size for _, x in sample)
         cpu = {"value": cnt / dt / 1e9, "unit": "Gelem/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {args.cpu_sample} inputs of each function's array"}
+               "sample": f"first {args.cpu_sample} inputs of each array"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.form == "plain" else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if (args.form == "plain" or f64) else "f32",
         "data": "synthetic",
-        "config": dict(cfg, form=args.form, functions=funcs, l2="inputs larger than L2 (no flush)",
-                       parallelism=f"replicas{world}"),
+        "config": dict(cfg, form=args.form, arrays=labels, l2="inputs larger than L2 (no flush)",
+                       parallelism=f"replicas{world}", launch_shapes=tuned or "default"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "kernel": f"k_main+k_slow<{funcs[dom]}>",
-                     "peak_kind": peak_kind},
+                     "array": labels[dom], "bytes_per_elem": bytes_per_elem(funcs[dom]), "peak_kind": peak_kind},
         "other_form": {"form": other, "step_gelem_s": step_other},
-        "per_function": per_func,
+        "per_array": per_arr,
         "hard_case_rate": st["hard_total"] / max(1, n_elems * args.steps), "unresolved": st["unresolved_total"],
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * len(funcs) * 2, "clocks": clk,
     }

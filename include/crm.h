@@ -12,9 +12,14 @@
  * Evaluation forms (crm_form_t):
  *   CRM_FORM_PLAIN_FP64 -- FP64 internal arithmetic, as the paper's single-precision
  *                          algorithms do (Sec. II.A), plus a rounding test;
- *   CRM_FORM_DF32       -- FP32 double-float fast path with a rounding test and an
- *                          FP64 / double-double fallback (the FP32 fast path with FP64
- *                          fallback suggested in Sec. II.A and Sec. IV);
+ *   CRM_FORM_DF32       -- the FP64-free form: no FP64 on the main path.  Binary32
+ *                          functions: FP32 double-float fast path with a rounding test
+ *                          and an FP64 / double-double fallback (the FP32 fast path with
+ *                          FP64 fallback suggested in Sec. II.A and Sec. IV).  Binary64
+ *                          exp2 and log: 128-bit fixed-point integer arithmetic with a
+ *                          rounding test, the double-double and exact integer tiers of
+ *                          Sec. II.B behind it.  (The plain form of the binary64 pair is
+ *                          the double-double main path of Sec. II.B.)
  *   CRM_FORM_AUTO       -- the fastest form available for the function (DF32 where it
  *                          exists).
  * Every form returns the same, correctly rounded, bits: the form changes speed only.
@@ -117,6 +122,34 @@ int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, u
 int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream);
 /* Tile size of the batching form, 2^log2_elems elements (8 <= log2_elems <= 24). */
 int crm_set_batch_tile(int log2_elems);
+
+/* ---- launch shapes and the autotuner (the paper has no counterpart: its SIMD kernels
+   have one shape; on the GPU the best elements-per-thread, block size and load schedule
+   depend on the function and the form).  A variant is one launch shape of the main
+   kernel: vectors per thread per iteration (unroll; 4 binary32 or 2 binary64 elements per
+   128-bit vector), threads per block, register prefetch of the next iteration, a minimum
+   of resident blocks per SM (a register cap), or the shared-memory pipelined kernel (bulk
+   asynchronous copies).  Every variant computes the same bits.  Output pointers may be
+   NULL. */
+#define CRM_NUM_VARIANTS 8
+int crm_variant_info(int variant, int *unroll, int *block, int *prefetch, int *pipelined, int *min_blocks);
+/* Choose the variant of (func_id, form) for all later calls.  CRM_ERR_ARG if the form does
+   not provide it (the plain FP64 form provides only the default shape). */
+int crm_set_variant(int func_id, int form, int variant);
+int crm_get_variant(int func_id, int form, int *variant);
+/* Time every variant of (func_id, form) on the caller's arrays (in, out: device memory,
+   n elements; `reps` timed calls each after one untimed call, CUDA events on `stream`),
+   keep the fastest for later calls, and return it in *best; ms (host, CRM_NUM_VARIANTS
+   floats, may be NULL) receives each variant's time per call, -1 where unavailable.
+   Overwrites out.  Synchronizes `stream`; CRM_ERR_CAPTURE while the stream is captured. */
+int crm_autotune(int func_id, int dtype, int form, const void *in, void *out, uint64_t n, int reps,
+                 void *stream, int *best, float *ms);
+/* Same for the batching form: times tile sizes 2^CRM_BATCH_TILE_MIN .. 2^CRM_BATCH_TILE_MAX
+   on the given batch and keeps the fastest (ms: host, 7 floats, may be NULL). */
+#define CRM_BATCH_TILE_MIN 10
+#define CRM_BATCH_TILE_MAX 16
+int crm_autotune_batch(const crm_desc_t *descs, int count, int form, int reps, void *stream, int *best_shift,
+                       float *ms);
 
 /* No-allocation variant of crm_eval_form.  The paper has no counterpart: this entry
    point exists for callers that cannot allocate device memory when they call the

@@ -15,7 +15,8 @@ from . import _lib as L
 from ._lib import F64_FUNCS, FORMS, FUNC_ID, FUNCS, CrmError, crm_desc_t, crm_stats_t
 
 __all__ = ["eval", "eval_into", "eval_host", "eval_batch", "stats", "stats_reset",
-           "set_form", "set_force_slow", "set_batch_tile", "reserve", "FUNCS", "FORMS", "CrmError", "version"]
+           "set_form", "set_force_slow", "set_batch_tile", "reserve", "FUNCS", "FORMS", "CrmError", "version",
+           "variant_info", "set_variant", "get_variant", "autotune", "autotune_batch"]
 
 
 def _stream_ptr(stream=None):
@@ -87,8 +88,7 @@ def eval_host(func, x_np, out_np=None, form=None, stream=None):
     return out_np
 
 
-def eval_batch(items, form=None, stream=None) -> None:
-    """items: list of (func, x, out) with contiguous CUDA tensors; one batched launch."""
+def _descs(items):
     descs = (crm_desc_t * len(items))()
     for d, (func, x, out) in zip(descs, items):
         fid = _fid(func)
@@ -97,7 +97,12 @@ def eval_batch(items, form=None, stream=None) -> None:
         d.in_ = x.data_ptr()
         d.out = out.data_ptr()
         d.n = x.numel()
-    L.check(L.lib().crm_eval_batch(descs, len(items), _form(form), _stream_ptr(stream)), "batch")
+    return descs
+
+
+def eval_batch(items, form=None, stream=None) -> None:
+    """items: list of (func, x, out) with contiguous CUDA tensors; one batched launch."""
+    L.check(L.lib().crm_eval_batch(_descs(items), len(items), _form(form), _stream_ptr(stream)), "batch")
 
 
 def stats(stream=None) -> dict:
@@ -126,6 +131,52 @@ def set_force_slow(on: bool) -> None:
 
 def reserve(max_elems: int, max_arrays: int = 0, stream=None) -> None:
     L.check(L.lib().crm_reserve(max_elems, max_arrays, _stream_ptr(stream)))
+
+
+def variant_info(v: int) -> dict:
+    """Launch shape of main-kernel variant v (0 <= v < NUM_VARIANTS)."""
+    a = [ctypes.c_int() for _ in range(5)]
+    L.check(L.lib().crm_variant_info(int(v), *[ctypes.byref(t) for t in a]))
+    return {"unroll": a[0].value, "block": a[1].value, "prefetch": bool(a[2].value),
+            "pipelined": bool(a[3].value), "min_blocks": a[4].value}
+
+
+def set_variant(func, variant: int, form=None) -> None:
+    L.check(L.lib().crm_set_variant(_fid(func), _form(form), int(variant)))
+
+
+def get_variant(func, form=None) -> int:
+    v = ctypes.c_int()
+    L.check(L.lib().crm_get_variant(_fid(func), _form(form), ctypes.byref(v)))
+    return v.value
+
+
+def autotune(func, x, out=None, form=None, reps: int = 3, stream=None):
+    """Time every launch shape of `func` on x (and out, overwritten), keep the fastest for
+    later calls; returns (best variant, {variant: ms per call})."""
+    import torch
+    fid = _fid(func)
+    if out is None:
+        out = torch.empty(((2,) if FUNCS[fid] == "sincosf" else ()) + tuple(x.shape), dtype=x.dtype,
+                          device=x.device)
+    best = ctypes.c_int()
+    ms = (ctypes.c_float * L.NUM_VARIANTS)()
+    dtype = L.CRM_F64 if FUNCS[fid] in F64_FUNCS else L.CRM_F32
+    L.check(L.lib().crm_autotune(fid, dtype, _form(form), ctypes.c_void_p(x.data_ptr()),
+                                 ctypes.c_void_p(out.data_ptr()), x.numel(), int(reps), _stream_ptr(stream),
+                                 ctypes.byref(best), ms), FUNCS[fid])
+    return best.value, {v: ms[v] for v in range(L.NUM_VARIANTS) if ms[v] >= 0}
+
+
+def autotune_batch(items, form=None, reps: int = 2, stream=None):
+    """Time the batching form's tile sizes on this batch and keep the fastest; returns
+    (best log2 tile, {log2 tile: ms per call})."""
+    best = ctypes.c_int()
+    n = L.BATCH_TILE_MAX - L.BATCH_TILE_MIN + 1
+    ms = (ctypes.c_float * n)()
+    L.check(L.lib().crm_autotune_batch(_descs(items), len(items), _form(form), int(reps), _stream_ptr(stream),
+                                       ctypes.byref(best), ms), "batch autotune")
+    return best.value, {L.BATCH_TILE_MIN + i: ms[i] for i in range(n)}
 
 
 def version() -> str:

@@ -26,6 +26,8 @@ struct BatchArgs {
   crm_ws_header *hdr;
   crm_queue_entry *q;
   uint64_t cap;
+  unsigned long long *qcount;  // sub-queue counters (see crm_ws.h)
+  int nsubq;
   int force_hard;
 };
 

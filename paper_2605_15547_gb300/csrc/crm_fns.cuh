@@ -112,20 +112,40 @@ struct FnRsqrt {
 struct FnExp2D {
   using T = double;
   static constexpr int NOUT = 1;
-  template <int FORM> static constexpr int tab_bytes() { return 96 * 8; }
-  template <int FORM> CRM_DEV static void load(unsigned char *sm) { copy_tab(sm, CRM_EXP2D_T, 96 * 8); }
+  // form 1: double-double in FP64; form 2: FP64-free (128-bit fixed point)
+  template <int FORM> static constexpr int tab_bytes() { return FORM == 2 ? 128 * 16 : 96 * 8; }
+  template <int FORM> CRM_DEV static void load(unsigned char *sm) {
+    if (FORM == 2)
+      copy_tab(sm, CRM_EXP2I_T, 128 * 16);
+    else
+      copy_tab(sm, CRM_EXP2D_T, 96 * 8);
+  }
   template <int FORM> CRM_DEV static void eval(double x, const void *sm, double *y, bool &h) {
-    y[0] = exp2d_main(x, (const double *)sm, h);
+    if (FORM == 2)
+      y[0] = exp2d_int(x, (const ulonglong2 *)sm, h);
+    else
+      y[0] = exp2d_main(x, (const double *)sm, h);
   }
   CRM_DEV static void slow(double x, double *y, bool &u, bool f) { y[0] = exp2d_slow(x, u, f); }
 };
 struct FnLogD {
   using T = double;
   static constexpr int NOUT = 1;
-  template <int FORM> static constexpr int tab_bytes() { return 0; }
-  template <int FORM> CRM_DEV static void load(unsigned char *) {}
-  template <int FORM> CRM_DEV static void eval(double x, const void *, double *y, bool &h) {
-    y[0] = logd_main(x, h);
+  // form 1: double-double in FP64; form 2: FP64-free (128-bit fixed point), with the
+  // tables -log(R_j 2^-9) (193 x 16 bytes) and R_j (194 x 2 bytes) in shared memory
+  static constexpr int LBYTES = 193 * 16;
+  template <int FORM> static constexpr int tab_bytes() { return FORM == 2 ? LBYTES + 194 * 2 + 12 : 0; }
+  template <int FORM> CRM_DEV static void load(unsigned char *sm) {
+    if (FORM == 2) {
+      copy_tab(sm, CRM_LOGI_L, LBYTES);
+      copy_tab(sm + LBYTES, CRM_LOGI_R, 194 * 2);
+    }
+  }
+  template <int FORM> CRM_DEV static void eval(double x, const void *sm, double *y, bool &h) {
+    if (FORM == 2)
+      y[0] = logd_int(x, (const ulonglong2 *)sm, (const unsigned short *)((const unsigned char *)sm + LBYTES), h);
+    else
+      y[0] = logd_main(x, h);
   }
   CRM_DEV static void slow(double x, double *y, bool &u, bool f) { y[0] = logd_slow(x, u, f); }
 };

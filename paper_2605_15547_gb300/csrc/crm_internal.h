@@ -9,9 +9,10 @@ void ensure_init();
 const FuncEntry &func_entry(int func);
 int resolve_form(const FuncEntry &fe, int form);
 int check_args(int func, int dtype, const void *in, void *out, uint64_t n);
-int unroll_of(int func, int form);
+int variant_of(int func, int form);
+int main_blocks_per_sm(const FuncEntry &fe, int form, int vi);
 int force_slow_flag();
 int cuda_fail_code(cudaError_t e);
 void fill_geometry(const FuncEntry &fe, const void *in, void *out, uint64_t n, KArgs &a);
-int main_grid(const FuncEntry &fe, const KArgs &a, int ui, int sms, int bps);
+int main_grid(const FuncEntry &fe, const KArgs &a, int vi, int sms, int bps);
 }  // namespace crm

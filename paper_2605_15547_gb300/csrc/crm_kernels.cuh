@@ -28,6 +28,8 @@ struct KArgs {
   crm_ws_header *hdr;
   crm_queue_entry *q;
   uint64_t cap;      // queue capacity (entries)
+  unsigned long long *qcount;  // sub-queue counters, CRM_SUBQ_STRIDE apart
+  int nsubq;         // sub-queues (each of cap / nsubq entries)
   int force_hard;    // test hook: every lane takes the slow path
   uint32_t desc;     // array id recorded in queue entries (batch form)
 };
@@ -54,9 +56,10 @@ template <class T> CRM_DEV T x_from_bits(uint64_t b);
 template <> CRM_DEV float x_from_bits<float>(uint64_t b) { return bitsf((uint32_t)b); }
 template <> CRM_DEV double x_from_bits<double>(uint64_t b) { return bitsd(b); }
 
-// Reserve queue slots for up to W lanes per thread with one atomicAdd per warp (the
-// whole warp calls this; hm holds the thread's hard bits).  Lanes beyond the queue
-// capacity are returned in the result mask and must be finished inline.
+// Reserve queue slots for up to W lanes per thread with one atomicAdd per warp on the
+// warp's sub-queue counter (the whole warp calls this; hm holds the thread's hard bits).
+// Lanes beyond the sub-queue's capacity are returned in the result mask and must be
+// finished inline.
 template <int W>
 CRM_DEV unsigned push_hard(unsigned hm, const uint64_t *idx, const uint64_t *xb, const KArgs &a) {
   const int lane = threadIdx.x & 31;
@@ -68,19 +71,23 @@ CRM_DEV unsigned push_hard(unsigned hm, const uint64_t *idx, const uint64_t *xb,
     m[j] = __ballot_sync(0xFFFFFFFFu, (hm >> j) & 1u);
     total += __popc(m[j]);
   }
+  const unsigned sq = a.nsubq == 1 ? 0u
+                                    : (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % (unsigned)a.nsubq;
+  const uint64_t subcap = a.cap / (uint64_t)a.nsubq;
+  crm_queue_entry *q = a.q + sq * subcap;
   unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(&a.hdr->count, (unsigned long long)total);
+  if (lane == 0) base = atomicAdd(&a.qcount[sq * CRM_SUBQ_STRIDE], (unsigned long long)total);
   base = __shfl_sync(0xFFFFFFFFu, base, 0);
   unsigned over = 0;
 #pragma unroll
   for (int j = 0; j < W; j++) {
     if ((hm >> j) & 1u) {
       unsigned long long pos = base + __popc(m[j] & lt);
-      if (pos < a.cap) {
+      if (pos < subcap) {
         crm_queue_entry e;
         e.idx = ((uint64_t)a.desc << 40) | idx[j];
         e.x = xb[j];
-        a.q[pos] = e;
+        q[pos] = e;
       } else {
         over |= 1u << j;
       }
@@ -117,8 +124,80 @@ __device__ __noinline__ void slow_store(typename Fn::T x, uint64_t i, const KArg
   if (unres) atomicAdd(&a.hdr->unresolved_total, 1ull);
 }
 
-template <class Fn, int FORM, int UNROLL>
-__global__ void __launch_bounds__(KBLOCK) k_main(KArgs a) {
+// Evaluates the W elements of one vector: y0 (and y1 for two outputs) and the hard bits.
+template <class Fn, int FORM>
+CRM_DEV void eval_vec(const typename VecOf<typename Fn::T>::V &xv, const void *sm,
+                      typename VecOf<typename Fn::T>::V &y0, typename VecOf<typename Fn::T>::V &y1,
+                      unsigned &hm) {
+  using T = typename Fn::T;
+  constexpr int W = VecOf<T>::W;
+  hm = 0;
+#pragma unroll
+  for (int j = 0; j < W; j++) {
+    T y[2];
+    bool h;
+    Fn::template eval<FORM>(vget(xv, j), sm, y, h);
+    hm |= (unsigned)h << j;
+    vset(y0, j, y[0]);
+    if (Fn::NOUT == 2) vset(y1, j, y[1]);
+  }
+}
+
+// Loads the UNROLL vectors of one iteration (zero past the end).
+template <class V, int UNROLL, int BS>
+CRM_DEV void load_vecs(V *xv, const V *in4, uint64_t base, uint64_t nvec) {
+#pragma unroll
+  for (int u = 0; u < UNROLL; u++) {
+    uint64_t v = base + (uint64_t)u * BS + threadIdx.x;
+    xv[u] = v < nvec ? ld_stream(in4 + v) : V();
+  }
+}
+
+// Evaluates and stores the UNROLL vectors of one iteration, queueing the hard lanes.
+template <class Fn, int FORM, int UNROLL, int BS>
+CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T>::V *xv, uint64_t base, const unsigned char *sm,
+                       const KArgs &a) {
+  using T = typename Fn::T;
+  using V = typename VecOf<T>::V;
+  constexpr int W = VecOf<T>::W;
+  V *out4 = (V *)((T *)a.out + a.head);
+  V *out4b = (V *)((T *)a.out + a.n + a.head);  // second output (sincos)
+#pragma unroll
+  for (int u = 0; u < UNROLL; u++) {
+    uint64_t v = base + (uint64_t)u * BS + threadIdx.x;
+    bool act = v < a.nvec;
+    V y0, y1;
+    unsigned hm;
+    eval_vec<Fn, FORM>(xv[u], sm, y0, y1, hm);
+    hm = a.force_hard ? (1u << W) - 1u : hm;
+    hm = act ? hm : 0u;
+    if (act) {
+      st_stream(out4 + v, y0);
+      if (Fn::NOUT == 2) st_stream(out4b + v, y1);
+    }
+    if (__any_sync(0xFFFFFFFFu, hm != 0)) {
+      uint64_t ii[W], xb[W];
+#pragma unroll
+      for (int j = 0; j < W; j++) {
+        ii[j] = a.head + v * W + j;
+        xb[j] = xbits_of(vget(xv[u], j));
+      }
+      unsigned over = push_hard<W>(hm, ii, xb, a);
+      if (over) {
+#pragma unroll
+        for (int j = 0; j < W; j++)
+          if ((over >> j) & 1u) slow_store<Fn>(vget(xv[u], j), ii[j], a);
+      }
+    }
+  }
+}
+
+// UNROLL vectors per thread per iteration, BS threads per block; with PF the next
+// iteration's vectors are loaded
+// before this iteration is evaluated (software prefetch: the loads' latency overlaps the
+// thread's own arithmetic).
+template <class Fn, int FORM, int UNROLL, int BS, bool PF>
+CRM_DEV void main_body(const KArgs &a) {
   using T = typename Fn::T;
   using V = typename VecOf<T>::V;
   constexpr int W = VecOf<T>::W;
@@ -126,54 +205,23 @@ __global__ void __launch_bounds__(KBLOCK) k_main(KArgs a) {
   load_tab<Fn, FORM>(sm);
 
   const V *in4 = (const V *)((const T *)a.in + a.head);
-  V *out4 = (V *)((T *)a.out + a.head);
-  V *out4b = (V *)((T *)a.out + a.n + a.head);  // second output (sincos)
-  const uint64_t stride = (uint64_t)gridDim.x * KBLOCK * UNROLL;
-  for (uint64_t base = (uint64_t)blockIdx.x * KBLOCK * UNROLL; base < a.nvec; base += stride) {
+  const uint64_t stride = (uint64_t)gridDim.x * BS * UNROLL;
+  uint64_t base = (uint64_t)blockIdx.x * BS * UNROLL;
+  if (PF) {
     V xv[UNROLL];
+    load_vecs<V, UNROLL, BS>(xv, in4, base, a.nvec);
+    for (; base < a.nvec; base += stride) {
+      V nx[UNROLL];
+      load_vecs<V, UNROLL, BS>(nx, in4, base + stride, a.nvec);
+      eval_vecs<Fn, FORM, UNROLL, BS>(xv, base, sm, a);
 #pragma unroll
-    for (int u = 0; u < UNROLL; u++) {
-      uint64_t v = base + (uint64_t)u * KBLOCK + threadIdx.x;
-      if (v < a.nvec) xv[u] = ld_stream(in4 + v);
-      else {
-        xv[u] = V();
-      }
+      for (int u = 0; u < UNROLL; u++) xv[u] = nx[u];
     }
-#pragma unroll
-    for (int u = 0; u < UNROLL; u++) {
-      uint64_t v = base + (uint64_t)u * KBLOCK + threadIdx.x;
-      bool act = v < a.nvec;
-      V y0, y1;
-      unsigned hm = 0;
-#pragma unroll
-      for (int j = 0; j < W; j++) {
-        T y[2];
-        bool h;
-        Fn::template eval<FORM>(vget(xv[u], j), sm, y, h);
-        hm |= (unsigned)h << j;
-        vset(y0, j, y[0]);
-        if (Fn::NOUT == 2) vset(y1, j, y[1]);
-      }
-      hm = a.force_hard ? (1u << W) - 1u : hm;
-      hm = act ? hm : 0u;
-      if (act) {
-        st_stream(out4 + v, y0);
-        if (Fn::NOUT == 2) st_stream(out4b + v, y1);
-      }
-      if (__any_sync(0xFFFFFFFFu, hm != 0)) {
-        uint64_t ii[W], xb[W];
-#pragma unroll
-        for (int j = 0; j < W; j++) {
-          ii[j] = a.head + v * W + j;
-          xb[j] = xbits_of(vget(xv[u], j));
-        }
-        unsigned over = push_hard<W>(hm, ii, xb, a);
-        if (over) {
-#pragma unroll
-          for (int j = 0; j < W; j++)
-            if ((over >> j) & 1u) slow_store<Fn>(vget(xv[u], j), ii[j], a);
-        }
-      }
+  } else {
+    for (; base < a.nvec; base += stride) {
+      V xv[UNROLL];
+      load_vecs<V, UNROLL, BS>(xv, in4, base, a.nvec);
+      eval_vecs<Fn, FORM, UNROLL, BS>(xv, base, sm, a);
     }
   }
   // scalar part: the head [0, head) and the tail [head + W nvec, n)
@@ -181,8 +229,8 @@ __global__ void __launch_bounds__(KBLOCK) k_main(KArgs a) {
   const uint64_t nscal = a.head + (a.n - tail0);
   const T *in = (const T *)a.in;
   T *out = (T *)a.out;
-  const uint64_t sstride = (uint64_t)gridDim.x * KBLOCK;
-  for (uint64_t b = (uint64_t)blockIdx.x * KBLOCK; b < nscal; b += sstride) {
+  const uint64_t sstride = (uint64_t)gridDim.x * BS;
+  for (uint64_t b = (uint64_t)blockIdx.x * BS; b < nscal; b += sstride) {
     uint64_t k = b + threadIdx.x;
     bool act = k < nscal;
     uint64_t i = k < a.head ? k : tail0 + (k - a.head);
@@ -200,6 +248,16 @@ __global__ void __launch_bounds__(KBLOCK) k_main(KArgs a) {
       if (push_hard<1>(h ? 1u : 0u, &i, &xb, a)) slow_store<Fn>(x, i, a);
     }
   }
+}
+
+template <class Fn, int FORM, int UNROLL, int BS, bool PF>
+__global__ void __launch_bounds__(BS) k_main(KArgs a) {
+  main_body<Fn, FORM, UNROLL, BS, PF>(a);
+}
+// The same with a register cap: at least MINB blocks of BS threads resident per SM.
+template <class Fn, int FORM, int UNROLL, int BS, bool PF, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_main_capped(KArgs a) {
+  main_body<Fn, FORM, UNROLL, BS, PF>(a);
 }
 
 // ------------------------------------------------------------------ pipelined variant
@@ -294,16 +352,8 @@ __global__ void __launch_bounds__(KBLOCK) k_pipe(KArgs a) {
       const bool act = v < a.nvec;
       V xv = act ? buf[st][vl] : V();
       V y0, y1;
-      unsigned hm = 0;
-#pragma unroll
-      for (int j = 0; j < W; j++) {
-        T y[2];
-        bool h;
-        Fn::template eval<FORM>(vget(xv, j), sm, y, h);
-        hm |= (unsigned)h << j;
-        vset(y0, j, y[0]);
-        if (Fn::NOUT == 2) vset(y1, j, y[1]);
-      }
+      unsigned hm;
+      eval_vec<Fn, FORM>(xv, sm, y0, y1, hm);
       hm = a.force_hard ? (1u << W) - 1u : hm;
       hm = act ? hm : 0u;
       if (act) {
@@ -367,15 +417,35 @@ __global__ void __launch_bounds__(KBLOCK) k_pipe(KArgs a) {
   }
 }
 
+// Calls f(entry) for every queued entry: the sub-queues are spread over the grid
+// (virtual blocks: sub-queue = vb % nsubq, part = vb / nsubq), and each sub-queue's
+// entries below its count are taken by its blocks in turn.  Block 0's thread 0 then adds
+// the call's total to hard_total and records it as the last count.
+template <class F>
+CRM_DEV void for_each_queued(const crm_queue_entry *q, unsigned long long *qcount, int nsubq, uint64_t cap,
+                             crm_ws_header *hdr, F f) {
+  const uint64_t subcap = cap / (uint64_t)nsubq;
+  const unsigned parts = gridDim.x >= (unsigned)nsubq ? gridDim.x / (unsigned)nsubq : 1u;
+  for (unsigned vb = blockIdx.x; vb < (unsigned)nsubq * parts; vb += gridDim.x) {
+    const unsigned sq = vb % (unsigned)nsubq, part = vb / (unsigned)nsubq;
+    unsigned long long cnt = qcount[sq * CRM_SUBQ_STRIDE];
+    if (cnt > subcap) cnt = subcap;
+    for (uint64_t i = (uint64_t)part * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)parts * blockDim.x)
+      f(q[sq * subcap + i]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long total = 0;
+    for (int sq = 0; sq < nsubq; sq++) total += qcount[sq * CRM_SUBQ_STRIDE];
+    atomicAdd(&hdr->hard_total, total);
+    hdr->count = total;
+  }
+}
+
 template <class Fn>
 __global__ void __launch_bounds__(KBLOCK) k_slow(KArgs a) {
   using T = typename Fn::T;
-  unsigned long long cnt = *(volatile unsigned long long *)&a.hdr->count;
-  if (cnt > a.cap) cnt = a.cap;
   T *out = (T *)a.out;
-  for (uint64_t i = (uint64_t)blockIdx.x * KBLOCK + threadIdx.x; i < cnt;
-       i += (uint64_t)gridDim.x * KBLOCK) {
-    crm_queue_entry e = a.q[i];
+  for_each_queued(a.q, a.qcount, a.nsubq, a.cap, a.hdr, [&](const crm_queue_entry &e) {
     uint64_t idx = e.idx & ((1ull << 40) - 1);
     T x = x_from_bits<T>(e.x);
     T y[2];
@@ -384,8 +454,7 @@ __global__ void __launch_bounds__(KBLOCK) k_slow(KArgs a) {
     out[idx] = y[0];
     if (Fn::NOUT == 2) out[a.n + idx] = y[1];
     if (unres) atomicAdd(&a.hdr->unresolved_total, 1ull);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.hdr->hard_total, (unsigned long long)a.hdr->count);
+  });
 }
 
 }  // namespace crm

@@ -84,17 +84,19 @@ extern "C" int crm_eval_noalloc(int func_id, int dtype, int form, const void *in
   a.hdr = (crm_ws_header *)d->scratch;
   a.q = (crm_queue_entry *)(d->scratch + kNoAllocHeader);
   a.cap = kNoAllocMaxElems;
+  a.qcount = &a.hdr->count;  // one queue: every lane of a call fits in it
+  a.nsubq = 1;
   a.force_hard = force_slow_flag();
   a.desc = 0;
-  int ui = unroll_of(func_id, fm);
+  int vi = variant_of(func_id, fm);
   int bps = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fe.main_sym[fm][ui], KBLOCK, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fe.main_sym[fm][vi], VARIANTS[vi].block, 0);
   if (e != cudaSuccess) return cuda_fail_code(e);
-  int grid = main_grid(fe, a, ui, d->sms, bps > 0 ? bps : 1);
+  int grid = main_grid(fe, a, vi, d->sms, bps > 0 ? bps : 1);
   // The array keeps the previous call's contents: the queue count must start at zero.
   e = cudaMemsetAsync(&a.hdr->count, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail_code(e);
-  e = fe.main[fm][ui](a, grid, s);
+  e = fe.main[fm][vi](a, grid, s);
   if (e != cudaSuccess) return cuda_fail_code(e);
   e = fe.slow(a, d->sms * 2, s);
   if (e != cudaSuccess) return cuda_fail_code(e);

@@ -9,19 +9,33 @@ namespace crm {
 typedef cudaError_t (*launch_fn)(const KArgs &, int grid, cudaStream_t);
 typedef int (*occ_fn)(void);
 
-enum { NUNROLL = 4 };  // variants: unroll 1, 2, 4 (vectors in flight per thread), 3 = pipelined
+// Launch shapes of the main kernel that the autotuner chooses among: vectors per thread
+// per iteration (elements per thread = 4 x unroll for binary32), threads per block,
+// register prefetch of the next iteration, or the shared-memory pipelined kernel.
+struct VariantInfo {
+  int unroll, block, prefetch, pipelined, min_blocks;
+};
+enum { NVARIANT = 8, DEFAULT_VARIANT = 1 };
+constexpr VariantInfo VARIANTS[NVARIANT] = {
+    {1, 256, 0, 0, 1}, {2, 256, 0, 0, 1}, {4, 256, 0, 0, 1}, {PVPT, KBLOCK, 0, 1, 1},
+    {2, 256, 1, 0, 4}, {1, 256, 1, 0, 1}, {2, 128, 1, 0, 1}, {2, 512, 1, 0, 1}};
 
 struct FuncEntry {
-  launch_fn main[3][NUNROLL];  // [form][unroll]; form 0 unused; null when unavailable
-  const void *main_sym[3][NUNROLL];
+  launch_fn main[3][NVARIANT];  // [form][variant]; form 0 unused; null when unavailable
+  const void *main_sym[3][NVARIANT];
   launch_fn slow;
   int nout;   // 1, or 2 for sincosf
   int dtype;  // 0 binary32, 1 binary64
 };
 
-template <class Fn, int FORM, int U>
+template <class Fn, int FORM, int U, int BS, bool PF>
 cudaError_t launch_main(const KArgs &a, int grid, cudaStream_t s) {
-  k_main<Fn, FORM, U><<<grid, KBLOCK, 0, s>>>(a);
+  k_main<Fn, FORM, U, BS, PF><<<grid, BS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <class Fn, int FORM, int U, int BS, bool PF, int MINB>
+cudaError_t launch_main_capped(const KArgs &a, int grid, cudaStream_t s) {
+  k_main_capped<Fn, FORM, U, BS, PF, MINB><<<grid, BS, 0, s>>>(a);
   return cudaGetLastError();
 }
 template <class Fn>
@@ -36,16 +50,35 @@ cudaError_t launch_pipe(const KArgs &a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <class Fn, int FORM, int V>
+void set_variant(FuncEntry &e) {
+  constexpr VariantInfo I = VARIANTS[V];
+  if constexpr (I.pipelined) {
+    e.main[FORM][V] = launch_pipe<Fn, FORM>;
+    e.main_sym[FORM][V] = (const void *)k_pipe<Fn, FORM>;
+  } else if constexpr (I.min_blocks > 1) {
+    e.main[FORM][V] = launch_main_capped<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.min_blocks>;
+    e.main_sym[FORM][V] = (const void *)k_main_capped<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.min_blocks>;
+  } else {
+    e.main[FORM][V] = launch_main<Fn, FORM, I.unroll, I.block, (bool)I.prefetch>;
+    e.main_sym[FORM][V] = (const void *)k_main<Fn, FORM, I.unroll, I.block, (bool)I.prefetch>;
+  }
+}
+
+// The double-float form gets every launch shape; the plain FP64 form, bound by the FP64
+// pipe whatever the shape, only the default one.
 template <class Fn, int FORM>
 void set_form(FuncEntry &e) {
-  e.main[FORM][0] = launch_main<Fn, FORM, 1>;
-  e.main[FORM][1] = launch_main<Fn, FORM, 2>;
-  e.main[FORM][2] = launch_main<Fn, FORM, 4>;
-  e.main[FORM][3] = launch_pipe<Fn, FORM>;
-  e.main_sym[FORM][0] = (const void *)k_main<Fn, FORM, 1>;
-  e.main_sym[FORM][1] = (const void *)k_main<Fn, FORM, 2>;
-  e.main_sym[FORM][2] = (const void *)k_main<Fn, FORM, 4>;
-  e.main_sym[FORM][3] = (const void *)k_pipe<Fn, FORM>;
+  set_variant<Fn, FORM, DEFAULT_VARIANT>(e);
+  if constexpr (FORM == 2) {
+    set_variant<Fn, FORM, 0>(e);
+    set_variant<Fn, FORM, 2>(e);
+    set_variant<Fn, FORM, 3>(e);
+    set_variant<Fn, FORM, 4>(e);
+    set_variant<Fn, FORM, 5>(e);
+    set_variant<Fn, FORM, 6>(e);
+    set_variant<Fn, FORM, 7>(e);
+  }
 }
 
 template <class Fn, bool HAS_PLAIN, bool HAS_DF>

@@ -71,6 +71,10 @@ static std::map<int, DevInfo> g_dev;
 
 static const uint64_t kDefaultCap = 1ull << 21;  // 2M hard lanes (32 MiB) per workspace
 
+static unsigned long long *subq_counts(Workspace *w) {
+  return (unsigned long long *)((char *)w->hdr + CRM_SUBQ_OFFSET);
+}
+
 static int cuda_fail(cudaError_t e) {
   g_last_cuda = (int)e;
   return CRM_ERR_CUDA;
@@ -100,12 +104,12 @@ static int get_ws(cudaStream_t s, uint64_t cap, Workspace **out) {
     cudaFree(w.q);
     w.q = nullptr;
   } else {
-    e = cudaMalloc((void **)&w.hdr, sizeof(crm_ws_header));
+    e = cudaMalloc((void **)&w.hdr, CRM_WS_HEADER_BYTES);
     if (e != cudaSuccess) {
       w.hdr = nullptr;
       return e == cudaErrorMemoryAllocation ? CRM_ERR_NOMEM : cuda_fail(e);
     }
-    e = cudaMemset(w.hdr, 0, sizeof(crm_ws_header));
+    e = cudaMemset(w.hdr, 0, CRM_WS_HEADER_BYTES);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   e = cudaMalloc((void **)&w.q, cap * sizeof(crm_queue_entry));
@@ -131,7 +135,7 @@ static int dev_sms() {
   return d.sms;
 }
 
-static int blocks_per_sm(const void *sym) {
+static int blocks_per_sm(const void *sym, int block) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_mu);
@@ -139,35 +143,43 @@ static int blocks_per_sm(const void *sym) {
   auto it = d.occ.find(sym);
   if (it != d.occ.end()) return it->second;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sym, KBLOCK, 0) != cudaSuccess || nb <= 0) nb = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sym, block, 0) != cudaSuccess || nb <= 0) nb = 1;
   d.occ[sym] = nb;
   return nb;
 }
 
-// Unroll variant per (function, form): the autotuner's choice (index into 1, 2, 4).
-static int g_unroll[CRM_NUM_FUNCS][3];
-static bool g_unroll_set = false;
+// Launch shape per (function, form): the default, the env CRM_VARIANT, crm_set_variant
+// or the autotuner's choice.  A shape the form does not provide falls back to the default.
+static int g_variant[CRM_NUM_FUNCS][3];
+static std::once_flag g_variant_once;
 
-int unroll_of(int func, int form) {
-  if (!g_unroll_set) {
-    int def = 1;  // 2 vectors in flight per thread
-    const char *u = getenv("CRM_UNROLL");
-    if (u && atoi(u) >= 0 && atoi(u) < NUNROLL) def = atoi(u);
-    for (int f = 0; f < CRM_NUM_FUNCS; f++)
-      for (int m = 0; m < 3; m++) g_unroll[f][m] = def;
-    g_unroll_set = true;
-  }
-  return g_unroll[func][form];
+static void variant_init() {
+  int def = DEFAULT_VARIANT;
+  const char *u = getenv("CRM_VARIANT");
+  if (u && atoi(u) >= 0 && atoi(u) < NVARIANT) def = atoi(u);
+  for (int f = 0; f < CRM_NUM_FUNCS; f++)
+    for (int m = 0; m < 3; m++) g_variant[f][m] = def;
+}
+
+int variant_of(int func, int form) {
+  std::call_once(g_variant_once, variant_init);
+  int v = g_variant[func][form];
+  return g_table[func].main[form][v] ? v : DEFAULT_VARIANT;
+}
+
+static void set_variant_of(int func, int form, int v) {
+  std::call_once(g_variant_once, variant_init);
+  g_variant[func][form] = v;
 }
 
 int resolve_form(const FuncEntry &fe, int form) {
   if (form == CRM_FORM_AUTO) {
-    if (fe.main[CRM_FORM_DF32][0]) return CRM_FORM_DF32;
-    if (fe.main[CRM_FORM_PLAIN_FP64][0]) return CRM_FORM_PLAIN_FP64;
+    if (fe.main[CRM_FORM_DF32][DEFAULT_VARIANT]) return CRM_FORM_DF32;
+    if (fe.main[CRM_FORM_PLAIN_FP64][DEFAULT_VARIANT]) return CRM_FORM_PLAIN_FP64;
     return -1;
   }
   if (form != CRM_FORM_PLAIN_FP64 && form != CRM_FORM_DF32) return -1;
-  return fe.main[form][0] ? form : -1;
+  return fe.main[form][DEFAULT_VARIANT] ? form : -1;
 }
 
 int check_args(int func, int dtype, const void *in, void *out, uint64_t n) {
@@ -211,20 +223,24 @@ void fill_geometry(const FuncEntry &fe, const void *in, void *out, uint64_t n, K
 
 // Grid of the main kernel: enough blocks for the work, at most one full wave of
 // resident blocks (the kernel loops over the rest).
-int main_grid(const FuncEntry &fe, const KArgs &a, int ui, int sms, int bps) {
+int main_grid(const FuncEntry &fe, const KArgs &a, int vi, int sms, int bps) {
   const int W = fe.dtype ? 2 : 4;
-  const int U = ui == 3 ? PVPT : (1 << ui);
-  uint64_t want = (a.nvec + (uint64_t)KBLOCK * U - 1) / ((uint64_t)KBLOCK * U);
+  const uint64_t U = (uint64_t)VARIANTS[vi].unroll, B = (uint64_t)VARIANTS[vi].block;
+  uint64_t want = (a.nvec + B * U - 1) / (B * U);
   uint64_t nscal = a.head + (a.n - a.head - (uint64_t)W * a.nvec);
-  uint64_t want_s = (nscal + KBLOCK - 1) / KBLOCK;
+  uint64_t want_s = (nscal + B - 1) / B;
   if (want_s > want) want = want_s;
   uint64_t cap_blocks = (uint64_t)sms * bps;
   return (int)(want < cap_blocks ? (want ? want : 1) : cap_blocks);
 }
 
+int main_blocks_per_sm(const FuncEntry &fe, int form, int vi) {
+  return blocks_per_sm(fe.main_sym[form][vi], VARIANTS[vi].block);
+}
+
 // Enqueue one evaluation (arguments already checked, n > 0).
 static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cudaStream_t s,
-                   uint32_t desc) {
+                   uint32_t desc, int variant = -1) {
   const FuncEntry &fe = g_table[func];
   int fm = resolve_form(fe, form);
   if (fm < 0) return CRM_ERR_FORM;
@@ -236,14 +252,16 @@ static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cu
   a.hdr = w->hdr;
   a.q = w->q;
   a.cap = w->cap;
+  a.qcount = subq_counts(w);
+  a.nsubq = CRM_NSUBQ;
   a.force_hard = g_force_slow;
   a.desc = desc;
-  int ui = unroll_of(func, fm);
+  int vi = variant >= 0 ? variant : variant_of(func, fm);
   int sms = dev_sms();
-  int grid = main_grid(fe, a, ui, sms, blocks_per_sm(fe.main_sym[fm][ui]));
-  cudaError_t e = cudaMemsetAsync(&w->hdr->count, 0, sizeof(unsigned long long), s);
+  int grid = main_grid(fe, a, vi, sms, main_blocks_per_sm(fe, fm, vi));
+  cudaError_t e = cudaMemsetAsync(a.qcount, 0, CRM_NSUBQ * CRM_SUBQ_STRIDE * 8, s);
   if (e != cudaSuccess) return cuda_fail(e);
-  e = fe.main[fm][ui](a, grid, s);
+  e = fe.main[fm][vi](a, grid, s);
   if (e != cudaSuccess) return cuda_fail(e);
   e = fe.slow(a, sms * 2, s);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -348,6 +366,29 @@ static int host_pipeline(int func, int form, const void *in, void *out, uint64_t
 }  // namespace crm
 
 using namespace crm;
+
+// Times `reps` back-to-back runs of fn() on stream s (after one untimed run).
+template <class F> static int time_runs(cudaStream_t s, int reps, float *ms, F fn) {
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(e);
+  }
+  int st = fn();
+  if (!st && (e = cudaEventRecord(e0, s)) != cudaSuccess) st = cuda_fail(e);
+  for (int r = 0; r < reps && !st; r++) st = fn();
+  if (!st && (e = cudaEventRecord(e1, s)) != cudaSuccess) st = cuda_fail(e);
+  if (!st && (e = cudaEventSynchronize(e1)) != cudaSuccess) st = cuda_fail(e);
+  float t = 0.0f;
+  if (!st && (e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) st = cuda_fail(e);
+  if (!st) *ms = t / (float)reps;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
 
 extern "C" {
 
@@ -484,7 +525,7 @@ int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
     if (e != cudaSuccess) return cuda_fail(e);
   }
   int sms = dev_sms();
-  int bps = blocks_per_sm(batch_kernel_symbol(fm));
+  int bps = blocks_per_sm(batch_kernel_symbol(fm), KBLOCK);
   uint64_t grid = (uint64_t)sms * bps;
   if (grid > tiles) grid = tiles;
   BatchArgs a;
@@ -496,8 +537,10 @@ int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
   a.hdr = w->hdr;
   a.q = w->q;
   a.cap = w->cap;
+  a.qcount = subq_counts(w);
+  a.nsubq = CRM_NSUBQ;
   a.force_hard = g_force_slow;
-  e = cudaMemsetAsync(&w->hdr->count, 0, sizeof(unsigned long long), s);
+  e = cudaMemsetAsync(a.qcount, 0, CRM_NSUBQ * CRM_SUBQ_STRIDE * 8, s);
   if (e != cudaSuccess) return cuda_fail(e);
   e = launch_batch(a, fm, (int)grid, sms * 2, s);
   return e == cudaSuccess ? CRM_OK : cuda_fail(e);
@@ -507,6 +550,98 @@ int crm_set_batch_tile(int log2_elems) {
   ensure_init();
   if (log2_elems < 8 || log2_elems > 24) return CRM_ERR_ARG;
   g_batch_tile_shift = log2_elems;
+  return CRM_OK;
+}
+
+int crm_variant_info(int variant, int *unroll, int *block, int *prefetch, int *pipelined, int *min_blocks) {
+  if (variant < 0 || variant >= NVARIANT) return CRM_ERR_ARG;
+  if (unroll) *unroll = VARIANTS[variant].unroll;
+  if (block) *block = VARIANTS[variant].block;
+  if (prefetch) *prefetch = VARIANTS[variant].prefetch;
+  if (pipelined) *pipelined = VARIANTS[variant].pipelined;
+  if (min_blocks) *min_blocks = VARIANTS[variant].min_blocks;
+  return CRM_OK;
+}
+
+int crm_set_variant(int func_id, int form, int variant) {
+  ensure_init();
+  if (func_id < 0 || func_id >= CRM_NUM_FUNCS) return CRM_ERR_FUNC;
+  int fm = resolve_form(g_table[func_id], form);
+  if (fm < 0) return CRM_ERR_FORM;
+  if (variant < 0 || variant >= NVARIANT || !g_table[func_id].main[fm][variant]) return CRM_ERR_ARG;
+  set_variant_of(func_id, fm, variant);
+  return CRM_OK;
+}
+
+int crm_get_variant(int func_id, int form, int *variant) {
+  ensure_init();
+  if (func_id < 0 || func_id >= CRM_NUM_FUNCS) return CRM_ERR_FUNC;
+  if (!variant) return CRM_ERR_NULL;
+  int fm = resolve_form(g_table[func_id], form);
+  if (fm < 0) return CRM_ERR_FORM;
+  *variant = variant_of(func_id, fm);
+  return CRM_OK;
+}
+
+int crm_autotune(int func_id, int dtype, int form, const void *in, void *out, uint64_t n, int reps,
+                 void *stream, int *best, float *ms) {
+  ensure_init();
+  int st = check_args(func_id, dtype, in, out, n);
+  if (st) return st;
+  if (form < CRM_FORM_AUTO || form > CRM_FORM_DF32) return CRM_ERR_FORM;
+  const FuncEntry &fe = g_table[func_id];
+  int fm = resolve_form(fe, form);
+  if (fm < 0) return CRM_ERR_FORM;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (capturing(s)) return CRM_ERR_CAPTURE;
+  if (reps < 1) reps = 1;
+  int bv = variant_of(func_id, fm);
+  float bms = 0.0f;
+  bool have = false;
+  for (int v = 0; v < NVARIANT; v++) {
+    if (ms) ms[v] = -1.0f;
+    if (!fe.main[fm][v] || n == 0) continue;
+    float t = 0.0f;
+    st = time_runs(s, reps, &t, [&]() { return enqueue(func_id, fm, in, out, n, s, 0, v); });
+    if (st) return st;
+    if (ms) ms[v] = t;
+    if (!have || t < bms) {
+      bms = t;
+      bv = v;
+      have = true;
+    }
+  }
+  set_variant_of(func_id, fm, bv);
+  if (best) *best = bv;
+  return CRM_OK;
+}
+
+int crm_autotune_batch(const crm_desc_t *descs, int count, int form, int reps, void *stream, int *best_shift,
+                       float *ms) {
+  ensure_init();
+  if (capturing((cudaStream_t)stream)) return CRM_ERR_CAPTURE;
+  if (reps < 1) reps = 1;
+  const int keep = g_batch_tile_shift;
+  int bs = keep;
+  float bms = 0.0f;
+  bool have = false;
+  for (int sh = CRM_BATCH_TILE_MIN; sh <= CRM_BATCH_TILE_MAX; sh++) {
+    g_batch_tile_shift = sh;
+    float t = 0.0f;
+    int st = time_runs((cudaStream_t)stream, reps, &t, [&]() { return crm_eval_batch(descs, count, form, stream); });
+    if (st) {
+      g_batch_tile_shift = keep;
+      return st;
+    }
+    if (ms) ms[sh - CRM_BATCH_TILE_MIN] = t;
+    if (!have || t < bms) {
+      bms = t;
+      bs = sh;
+      have = true;
+    }
+  }
+  g_batch_tile_shift = bs;
+  if (best_shift) *best_shift = bs;
   return CRM_OK;
 }
 

@@ -2,8 +2,8 @@
 #pragma once
 #include <stdint.h>
 
-// Header at the start of each workspace.  `count` is cleared before every call; the
-// totals accumulate until crm_stats_reset().
+// Header at the start of each workspace.  The totals accumulate until crm_stats_reset();
+// `count` is the last call's number of hard lanes.
 typedef struct crm_ws_header {
   unsigned long long count;            // lanes that failed the fast-path test this call
   unsigned long long hard_total;       // sum of count over calls
@@ -19,3 +19,13 @@ typedef struct crm_queue_entry {
   uint64_t idx;
   uint64_t x;
 } crm_queue_entry;
+
+// The hard-case queue is split into CRM_NSUBQ sub-queues of equal capacity, each with its
+// own counter on its own 128-byte line (so that the warps' atomicAdds spread over many
+// addresses instead of serialising on one); warp w of the grid uses sub-queue
+// w % CRM_NSUBQ.  The counters follow the header at byte offset CRM_SUBQ_OFFSET and are
+// cleared before every call.
+#define CRM_NSUBQ 64
+#define CRM_SUBQ_STRIDE 16  /* unsigned long longs between counters: 128 bytes */
+#define CRM_SUBQ_OFFSET 128
+#define CRM_WS_HEADER_BYTES (CRM_SUBQ_OFFSET + CRM_NSUBQ * CRM_SUBQ_STRIDE * 8)

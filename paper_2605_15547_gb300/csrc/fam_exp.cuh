@@ -99,7 +99,7 @@ template <int KIND> CRM_DEV float exp_plain(float x, const double *T16, bool &ha
 // remainder 2^-44.6, tables 2^-48, bracket roundings 2^-48: total < 2^-37.7, covered by
 // the test's 2^-37 allowance (hard_df).
 // Inputs outside [X_SUB, X_OVF] are resolved by selects: +inf above X_OVF, +0 below
-// X_ZERO; the subnormal band [X_ZERO, X_SUB) and NaN go to the slow path.
+// X_ZERO, a quiet NaN for NaN; the subnormal band [X_ZERO, X_SUB) goes to the slow path.
 template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard) {
   using K = ExpK<KIND>;
   float th, tl;
@@ -140,8 +140,8 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
   float l2 = r - (s2 - s);
   float y = bitsf(fbits(s2) + ((uint32_t)(N >> 6) << 23));
   bool ok = (x >= K::XSUB) && (x <= K::XOVF);  // false for NaN
-  float rsp = x > 0.0f ? CRM_INF_F : 0.0f;
-  bool hsp = !(x < K::XZERO) && !(x > K::XOVF);  // subnormal band or NaN
+  float rsp = x != x ? qnan_of(x) : (x > 0.0f ? CRM_INF_F : 0.0f);
+  bool hsp = (x >= K::XZERO) && (x < K::XSUB);  // subnormal band
   hard = ok ? hard_df(s2, l2) : hsp;
   return ok ? y : rsp;
 }

@@ -67,10 +67,104 @@ CRM_DEV double exp2d_main(double x, const double *T, bool &hard) {
   bool sp = exp2d_special(x, r);
   int k;
   Pair<double> y = exp2d_core(sp ? 0.0 : x, k, T);
-  bool sub = x < -1022.0;  // subnormal results: decided by the exact path
-  hard = !sp && (sub || hard_dd(y.hi, y.lo));
-  double out = scale_d(y.hi, k);
+  // Subnormal results (x < -1022): the result is the integer nearest to
+  // u = y 2^(k + 1074) (u < 2^53, the scaling exact) times 2^-1074.  With q = rint(u_hi)
+  // and d = (u_hi - q) + u_lo in [-1, 1], the nearest integer is q, q + 1 (d > 1/2) or
+  // q - 1 (d < -1/2); y's error (2^-100 relative, below 2^-47 in u) can move u across a
+  // half-integer only when ||d| - 1/2| <= 2^-46: those lanes take the exact path.
+  const bool sub = x < -1022.0;
+  const double sc = pow2d(sub ? k + 1074 : 0);
+  const double uh = y.hi * sc, ul = y.lo * sc;
+  const double q = rint(uh);
+  const double d = (uh - q) + ul;
+  const double qi = q + (d > 0.5 ? 1.0 : (d < -0.5 ? -1.0 : 0.0));
+  const bool hsub = fabs(fabs(d) - 0.5) <= 0x1p-46;
+  hard = !sp && (sub ? hsub : hard_dd(y.hi, y.lo));
+  double out = sub ? qi * 0x1p-1074 : scale_d(y.hi, k);
   return sp ? r : out;
+}
+
+// ------------------------------------------------------------------ exp2, FP64-free main path
+// 128-bit fixed point on the integer pipes (GB300's FP64 rate is a small fraction of its
+// integer rate).  |x| 2^96 is formed exactly from x's significand (truncated below 2^-96
+// for |x| < 2^-16), negated for x < 0, so that k = floor(x') and the 96 fraction bits give
+// f = x' - k in [0, 1).  f = i1/64 + i2/4096 + r, r < 2^-12; T = 2^(i1/64) 2^(i2/4096)
+// from two 64-entry tables (Q126) multiplied in Q124; 2^r - 1 = r (a1 + r (a2 + ...)),
+// a_n = (ln 2)^n/n!, n <= 6, by Horner on rho = r 2^12 in Q64 with truncating products.
+// Error in 2^f: the Q64 Horner (coefficients 2^-65, each product and shift 2^-64) gives
+// 2^r - 1 to 2^-74.1, r's truncation to 64 bits adds 2^-76.5, the omitted degree-7 term
+// 2^-88 and T's 2^-122: |Y - 2^f| < 2^-72.8, i.e. below 2^52 units of Y (Q124).  The
+// rounding (normal results at bit 72 of Y, subnormal ones further up) is decided unless
+// the discarded part is within 2^52 units of half an ulp: those lanes take the slow path.
+struct U128 {
+  uint64_t lo, hi;
+};
+CRM_DEV U128 mul64w(uint64_t a, uint64_t b) { return {a * b, __umul64hi(a, b)}; }
+CRM_DEV U128 add128(U128 a, U128 b) {
+  U128 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+  return r;
+}
+CRM_DEV U128 add128_64(U128 a, uint64_t b) {
+  U128 r;
+  r.lo = a.lo + b;
+  r.hi = a.hi + (r.lo < b ? 1ull : 0ull);
+  return r;
+}
+CRM_DEV U128 shr128(U128 a, int s) {  // 0 < s < 64
+  return {(a.lo >> s) | (a.hi << (64 - s)), a.hi >> s};
+}
+
+CRM_DEV double exp2d_int(double x, const ulonglong2 *T, bool &hard) {
+  double rs;
+  const bool sp = exp2d_special(x, rs);
+  const uint64_t b = dbits(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  const bool tiny = E < 1023 - 60;  // |x| < 2^-60: 2^x rounds to 1
+  const uint64_t M = (b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+  int s = E - 979;  // |x| 2^96 = M 2^s, s in [-16, 54] on the main path
+  s = (sp || tiny) ? 0 : s;
+  U128 X;
+  X.lo = s >= 0 ? (M << s) : (M >> -s);
+  X.hi = s > 0 ? (M >> (64 - s)) : 0ull;
+  if (b >> 63) {  // two's complement: k = floor(x'), the fraction bits give x' - k
+    X.lo = ~X.lo + 1ull;
+    X.hi = ~X.hi + (X.lo == 0 ? 1ull : 0ull);
+  }
+  const int k = (int)((int64_t)X.hi >> 32);
+  const uint32_t Fh = (uint32_t)X.hi;
+  const int i1 = (int)(Fh >> 26), i2 = (int)((Fh >> 20) & 63u);
+  const uint64_t rho = ((uint64_t)(Fh & 0xFFFFFu) << 44) | (X.lo >> 20);
+  // 2^r - 1 = 2^-12 P, P = rho (a1 + rho 2^-12 (a2 + ...)) in Q64
+  uint64_t h = CRM_EXP2I_A6;
+  h = CRM_EXP2I_A5 + (__umul64hi(rho, h) >> 12);
+  h = CRM_EXP2I_A4 + (__umul64hi(rho, h) >> 12);
+  h = CRM_EXP2I_A3 + (__umul64hi(rho, h) >> 12);
+  h = CRM_EXP2I_A2 + (__umul64hi(rho, h) >> 12);
+  h = CRM_EXP2I_A1 + (__umul64hi(rho, h) >> 12);
+  const uint64_t P = __umul64hi(rho, h);
+  // T = T1 T2 in Q124
+  const ulonglong2 t1 = T[i1], t2 = T[64 + i2];  // (low, high) words of Q126 values
+  U128 Tq = mul64w(t1.y, t2.y);
+  Tq = add128_64(Tq, __umul64hi(t1.y, t2.x));
+  Tq = add128_64(Tq, __umul64hi(t1.x, t2.y));
+  // Y = T + T 2^-12 P 2^-64 (Q124)
+  U128 tp = shr128(mul64w(Tq.hi, P), 12);
+  tp = add128_64(tp, __umul64hi(Tq.lo, P) >> 12);
+  const U128 Y = add128(Tq, tp);  // in [2^124, 2^125)
+  // round at bit sh = 72 (normal results) or higher (subnormal results)
+  const int sh = 72 + (k < -1022 ? -1022 - k : 0);  // 72 .. 125
+  const int sh64 = sh - 64;
+  const uint64_t q = Y.hi >> sh64;
+  const uint64_t remh = Y.hi & ((1ull << sh64) - 1ull);
+  const uint64_t dh = remh - (1ull << (sh64 - 1));  // high word of rem - half (the low word is Y.lo)
+  const bool up = (int64_t)dh > 0 || (dh == 0 && Y.lo != 0);
+  const bool near = (dh == 0 && Y.lo <= (1ull << 52)) || (dh == ~0ull && Y.lo >= 0ull - (1ull << 52));
+  const uint64_t mant = q + (up ? 1ull : 0ull);
+  const uint64_t bits = k >= -1022 ? ((uint64_t)(int64_t)(k + 1022) << 52) + mant : mant;
+  hard = !sp && !tiny && near;
+  return sp ? rs : (tiny ? 1.0 : bitsd(bits));
 }
 
 // ------------------------------------------------------------------ log, main path
@@ -117,6 +211,104 @@ CRM_DEV double logd_main(double x, bool &hard) {
   Pair<double> y = logd_core(sp ? 2.0 : x);
   hard = !sp && hard_dd(y.hi, y.lo);
   return sp ? r : y.hi;
+}
+
+// ------------------------------------------------------------------ log, FP64-free main path
+// 128-bit fixed point on the integer pipes.  x = 2^e m, m in [3/4, 3/2) (subnormal x
+// normalised by its leading zeros), j = round(256 m), R_j = round(2^17/j) (10 bits) and
+// r = m R_j 2^-9 - 1, exact as a 64-bit integer (m has 53 bits, R_j 10), |r| < 2^-8.
+//   log x = e ln 2 + L_j + log1p(r),  L_j = -log(R_j 2^-9)  (table, Q116),
+//   log1p(r) = r (1 + S'),  S' = -r/2 + r^2 U(r),  U = 1/3 - r/4 + r^2/5 - ... (n <= 7),
+// U by Horner in Q63 with signed truncating products (error 2^-62.4, the omitted term
+// 2^-67.5), r^2 U and r/2 in Q127, so that log1p(r) is good to 2^-78 of itself however
+// small r is.  Z = log x in Q116; errors in units of 2^-116: e ln2 |e|/2, L_j 1/2,
+// products and shifts 4, log1p |r| 2^38: the bound used is 16 + |e| + |r| 2^40.  The
+// rounding to binary64 is decided unless the discarded part of |Z| is within that bound
+// of half an ulp: those lanes take the slow path.
+CRM_DEV U128 neg128(U128 a) {
+  U128 r;
+  r.lo = ~a.lo + 1ull;
+  r.hi = ~a.hi + (r.lo == 0 ? 1ull : 0ull);
+  return r;
+}
+CRM_DEV U128 sub128(U128 a, U128 b) {
+  U128 r;
+  r.lo = a.lo - b.lo;
+  r.hi = a.hi - b.hi - (a.lo < b.lo ? 1ull : 0ull);
+  return r;
+}
+
+CRM_DEV double logd_int(double x, const ulonglong2 *LT, const unsigned short *RT, bool &hard) {
+  double rs;
+  const bool sp = logd_special(x, rs);
+  const uint64_t b = dbits(sp ? 2.0 : x);
+  int E = (int)(b >> 52);
+  uint64_t M = b & 0x000FFFFFFFFFFFFFull;
+  if (E == 0) {  // subnormal: shift the leading bit to position 52
+    const int lz = __clzll(M) - 11;
+    M <<= lz;
+    E = 1 - lz;
+  } else {
+    M |= 1ull << 52;
+  }
+  const bool big = M >= (3ull << 51);  // m >= 3/2: use m/2
+  const int e = E - 1023 + (big ? 1 : 0);
+  const uint64_t Mq = big ? M : (M << 1);              // m 2^53
+  const int j = (int)((Mq + (1ull << 44)) >> 45);      // 192 .. 384
+  const uint64_t R = RT[j - 192];
+  const int64_t r64 = (int64_t)(Mq * R - (1ull << 62)) * 4;  // r 2^64, exact
+  const uint64_t ar = r64 < 0 ? 0ull - (uint64_t)r64 : (uint64_t)r64;
+  // U(r) in Q63
+  int64_t u = CRM_LOGI_C7;
+  u = CRM_LOGI_C6 + __mul64hi(r64, u);
+  u = CRM_LOGI_C5 + __mul64hi(r64, u);
+  u = CRM_LOGI_C4 + __mul64hi(r64, u);
+  u = CRM_LOGI_C3 + __mul64hi(r64, u);
+  u = CRM_LOGI_C2 + __mul64hi(r64, u);
+  u = CRM_LOGI_C1 + __mul64hi(r64, u);
+  u = CRM_LOGI_C0 + __mul64hi(r64, u);
+  // S' = r^2 U - r/2 in Q127
+  const U128 r2 = mul64w(ar, ar);  // Q128
+  const U128 r2u = add128_64(mul64w(r2.hi, (uint64_t)u), __umul64hi(r2.lo, (uint64_t)u));
+  const U128 rhalf = {(uint64_t)r64 << 62, (uint64_t)(r64 >> 2)};  // r/2 in Q127
+  const U128 Sp = sub128(r2u, rhalf);
+  const bool sneg = (int64_t)Sp.hi < 0;
+  const U128 aS = sneg ? neg128(Sp) : Sp;
+  // r S' in Q116, with the sign of r S'
+  U128 rS = shr128(add128_64(mul64w(ar, aS.hi), __umul64hi(ar, aS.lo)), 11);
+  if ((r64 < 0) != sneg) rS = neg128(rS);
+  const U128 rQ = {(uint64_t)r64 << 52, (uint64_t)(r64 >> 12)};  // r in Q116
+  // e ln 2 in Q116
+  const uint64_t ae = (uint64_t)(e < 0 ? -e : e);
+  const U128 p0 = mul64w(CRM_LOGI_LN2_LO, ae);
+  U128 eL = {p0.lo, CRM_LOGI_LN2_HI * ae + p0.hi};
+  if (e < 0) eL = neg128(eL);
+  const ulonglong2 Lj = LT[j - 192];
+  const U128 Z = add128(add128(eL, {Lj.x, Lj.y}), add128(rQ, rS));
+  // round |Z| (Q116) to 53 bits
+  const bool zneg = (int64_t)Z.hi < 0;
+  const U128 A = zneg ? neg128(Z) : Z;
+  const bool zero = (A.hi | A.lo) == 0;  // x == 1
+  const int lz = A.hi ? __clzll(A.hi) : 64 + __clzll(A.lo | 1ull);
+  const int sh = 75 - lz;  // (127 - lz) - 52, 11 .. 74 for x != 1
+  uint64_t mant;
+  U128 rem, half;
+  if (sh < 64) {
+    mant = (A.lo >> sh) | (A.hi << (64 - sh));
+    rem = {A.lo & ((1ull << sh) - 1ull), 0ull};
+    half = {1ull << (sh - 1), 0ull};
+  } else {
+    mant = A.hi >> (sh - 64);
+    rem = {A.lo, A.hi & ((1ull << (sh - 64)) - 1ull)};
+    half = sh == 64 ? U128{1ull << 63, 0ull} : U128{0ull, 1ull << (sh - 65)};
+  }
+  const U128 dlt = sub128(rem, half);
+  const uint64_t err = 16ull + ae + (ar >> 24);
+  const bool near = (dlt.hi == 0 && dlt.lo <= err) || (dlt.hi == ~0ull && dlt.lo >= 0ull - err);
+  const bool up = (int64_t)dlt.hi > 0 || (dlt.hi == 0 && dlt.lo != 0);
+  const uint64_t bits = ((uint64_t)(sh + 958) << 52) + mant + (up ? 1ull : 0ull);
+  hard = !sp && !zero && near;
+  return sp ? rs : (zero ? 0.0 : bitsd(bits | (zneg ? 0x8000000000000000ull : 0ull)));
 }
 
 // ------------------------------------------------------------------ exact slow path

@@ -202,8 +202,8 @@ template <int KIND> CRM_DEV float log_df(float x, const float4 *T97, bool &hard)
   float lo = S.lo + (Bl + ql);
   float s2 = S.hi + lo;
   float l2 = lo - (s2 - S.hi);
-  hard = !ok || hard_df(s2, l2);
-  return s2;
+  hard = ok && hard_df(s2, l2);
+  return ok ? s2 : special_log<KIND>(x);
 }
 
 // ------------------------------------------------------------------ double-double tier

@@ -405,6 +405,61 @@ for k in range(1, 13):
 arr_d("CRM_LOGD_C", lc, "(-1)^(k+1)/k, k = 1..12, double-double")
 emit()
 
+emit("// ===== binary64 exp2, FP64-free main path (128-bit fixed point) =====")
+
+
+def q_round(v, frac_bits, bits):
+    """round(v 2^frac_bits) as an integer below 2^bits"""
+    with mp.workprec(400):
+        N = int(mp.nint(v * mp.mpf(2) ** frac_bits))
+    assert 0 <= N < 2 ** bits
+    return N
+
+
+def arr_u64_pairs(name, vals, comment):
+    emit(f"// {comment}")
+    emit(f"CRM_TABLE unsigned long long {name}[{len(vals)}] = {{")
+    for i in range(0, len(vals), 2):
+        emit("  " + ", ".join(f"0x{v:016X}ull" for v in vals[i:i + 2]) + ",")
+    emit("};")
+
+
+ti = []
+for div in (64, 4096):
+    for i in range(64):
+        N = q_round(mp.power(2, mp.mpf(i) / div), 126, 128)
+        ti += [N & 0xFFFFFFFFFFFFFFFF, N >> 64]
+arr_u64_pairs("CRM_EXP2I_T", ti, "2^(i/64) then 2^(i/4096), i = 0..63, as round(v 2^126): (low, high) 64-bit words")
+for k in range(1, 7):
+    emit(f"#define CRM_EXP2I_A{k} 0x{q_round(LN2 ** k / mp.factorial(k), 64, 64):016X}ull  // (ln 2)^{k}/{k}! 2^64")
+emit()
+
+emit("// ===== binary64 log, FP64-free main path (128-bit fixed point) =====")
+li, lr = [], []
+for j in range(192, 385):
+    R = int(mp.nint(mp.mpf(2) ** 9 * 256 / j))
+    lr.append(R)
+    with mp.workprec(400):
+        N = int(mp.nint(-mp.log(mp.mpf(R) / 512) * mp.mpf(2) ** 116))
+    N &= (1 << 128) - 1  # two's complement
+    li += [N & 0xFFFFFFFFFFFFFFFF, N >> 64]
+arr_u64_pairs("CRM_LOGI_L", li, "-log(R_j/2^9), j = 192..384, as round(v 2^116), two's complement (low, high)")
+emit("// R_j = round(2^9 256/j), j = 192..384, and a zero pad (whole 32-bit words)")
+lr.append(0)
+emit(f"CRM_TABLE unsigned short CRM_LOGI_R[{len(lr)}] = {{")
+for i in range(0, len(lr), 12):
+    emit("  " + ", ".join(str(v) for v in lr[i:i + 12]) + ",")
+emit("};")
+for n in range(8):
+    with mp.workprec(400):
+        N = int(mp.nint(mp.mpf((-1) ** n) / (n + 3) * mp.mpf(2) ** 63))
+    emit(f"#define CRM_LOGI_C{n} ((int64_t){N}ll)  // (-1)^{n}/{n + 3} 2^63")
+with mp.workprec(400):
+    N = int(mp.nint(LN2 * mp.mpf(2) ** 116))
+emit(f"#define CRM_LOGI_LN2_LO 0x{N & 0xFFFFFFFFFFFFFFFF:016X}ull  // ln 2 2^116, low word")
+emit(f"#define CRM_LOGI_LN2_HI 0x{N >> 64:016X}ull  // high word")
+emit()
+
 emit("// ===== end =====")
 
 text = "\n".join(lines) + "\n"

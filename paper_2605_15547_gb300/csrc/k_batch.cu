@@ -26,6 +26,8 @@ CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t
   a.hdr = b.hdr;
   a.q = b.q;
   a.cap = b.cap;
+  a.qcount = b.qcount;
+  a.nsubq = b.nsubq;
   a.force_hard = b.force_hard;
   a.desc = aid;
   const T *in = (const T *)d.in;
@@ -43,16 +45,8 @@ CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t
       bool act = v < nv;
       V xv = act ? ld_stream(in4 + v) : V();
       V y0, y1;
-      unsigned hm = 0;
-#pragma unroll
-      for (int j = 0; j < W; j++) {
-        T y[2];
-        bool h;
-        Fn::template eval<FORM>(vget(xv, j), sm, y, h);
-        hm |= (unsigned)h << j;
-        vset(y0, j, y[0]);
-        if (Fn::NOUT == 2) vset(y1, j, y[1]);
-      }
+      unsigned hm;
+      eval_vec<Fn, FORM>(xv, sm, y0, y1, hm);
       hm = a.force_hard ? (1u << W) - 1u : hm;
       hm = act ? hm : 0u;
       if (act) {
@@ -189,17 +183,13 @@ __global__ void __launch_bounds__(KBLOCK) k_batch(BatchArgs b) {
 }
 
 __global__ void __launch_bounds__(KBLOCK) k_batch_slow(BatchArgs b) {
-  unsigned long long cnt = *(volatile unsigned long long *)&b.hdr->count;
-  if (cnt > b.cap) cnt = b.cap;
-  for (uint64_t i = (uint64_t)blockIdx.x * KBLOCK + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * KBLOCK) {
-    crm_queue_entry e = b.q[i];
+  for_each_queued(b.q, b.qcount, b.nsubq, b.cap, b.hdr, [&](const crm_queue_entry &e) {
     uint32_t aid = (uint32_t)(e.idx >> 40);
     uint64_t idx = e.idx & ((1ull << 40) - 1);
     const BatchDesc *d = &b.descs[aid];
     SlowOp op{bitsf((uint32_t)e.x), b.force_hard != 0, d, idx, &b.hdr->unresolved_total};
     CRM_FOR_FUNC(d->func, op);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&b.hdr->hard_total, (unsigned long long)b.hdr->count);
+  });
 }
 
 cudaError_t launch_batch(const BatchArgs &b, int form, int grid, int slow_grid, cudaStream_t s) {

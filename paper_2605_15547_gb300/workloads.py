@@ -167,3 +167,114 @@ def batch_lengths(count: int, rng: np.random.Generator, lo_log2: float = 6.0, hi
     n = np.round(np.exp2(rng.uniform(lo_log2, hi_log2, count))).astype(np.int64)
     f = rng.integers(0, len(F32_FUNCS), count)
     return n, [F32_FUNCS[i] for i in f]
+
+
+# ----------------------------------------------------------------------------- bench workloads
+# A workload is a list of arrays (label, function, n); bench.py evaluates each array once
+# per step.  The inputs are generated on the device (torch's seeded generator) with the
+# recipes above; `bench_input_host` draws the same recipe on the host (numpy), for the
+# CPU reference timing and for tests.
+
+PRECISION_FUNCS = ("expf", "logf", "sinf", "tanhf", "rsqrtf")
+
+
+def bench_arrays(workload: str, scale: int = 0):
+    """[(label, func, n)], config dict."""
+    if workload == "all19":
+        n = (1 << 26) >> scale
+        return [(f, f, n) for f in F32_FUNCS], {
+            "workload": f"19 binary32 functions x 2^{26 - scale} inputs: domain bit patterns + 1% specials",
+            "elems_per_func": n}
+    if workload == "precision":
+        n = (1 << 28) >> scale
+        arrs = []
+        for f in PRECISION_FUNCS:
+            arrs.append((f + ":u10", f, n))
+            arrs.append((f + ":log", f, n))
+        arrs.append(("sinf:large", "sinf", n))
+        return arrs, {
+            "workload": f"expf/logf/sinf/tanhf/rsqrtf x 2^{28 - scale}: (i) U[-10,10], (ii) log-uniform "
+                        "[2^-126,2^127] (random sign except logf, rsqrtf); sinf (iii) = (i) with 5% of "
+                        "|x| log-uniform in (2^20, 2^127]", "elems_per_array": n}
+    if workload == "f64":
+        n = (1 << 26) >> scale
+        return [("exp2:domain", "exp2", n), ("exp2:u20", "exp2", n), ("log:bits", "log", n),
+                ("log:u0.125_8", "log", n)], {
+            "workload": f"binary64 exp2 and log x 2^{26 - scale}: exp2 U(-1075,1024) and U[-20,20]; "
+                        "log uniform positive finite bit patterns and U[0.125,8]", "elems_per_array": n}
+    raise ValueError(f"unknown workload {workload}")
+
+
+def _set_of(label: str) -> str:
+    return label.split(":", 1)[1] if ":" in label else "domain"
+
+
+def bench_seed(workload: str, label: str, func: str) -> int:
+    cfg = {"all19": 2, "precision": 3, "f64": 5}[workload]
+    salt = {"domain": 0, "u10": 0, "log": 1, "large": 2, "u20": 1, "bits": 0, "u0.125_8": 1}[_set_of(label)]
+    return seed_for(cfg, func) + 0x100000000 * salt
+
+
+def bench_input_host(workload: str, label: str, func: str, n: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(bench_seed(workload, label, func)))
+    kind = _set_of(label)
+    if workload == "all19":
+        return domain_bits(func, n, rng).view(np.float32)
+    if workload == "precision":
+        if kind == "u10":
+            return uniform(-10.0, 10.0, n, rng)
+        if kind == "log":
+            return loguniform(-126.0, 127.0, n, rng, signed=func not in ("logf", "rsqrtf"))
+        return sinf_with_large(n, rng, frac=0.05)
+    if kind == "domain":
+        return f64_uniform(-1075.0, 1024.0, n, rng)
+    if kind == "u20":
+        return f64_uniform(-20.0, 20.0, n, rng)
+    if kind == "bits":
+        return f64_positive_bits(n, rng)
+    return f64_uniform(0.125, 8.0, n, rng)
+
+
+def bench_input_device(workload: str, label: str, func: str, n: int, device="cuda"):
+    import torch
+    seed = bench_seed(workload, label, func)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    kind = _set_of(label)
+
+    def u(lo, hi, dtype=torch.float64):
+        return (torch.rand(n, dtype=torch.float64, device=device, generator=gen) * (hi - lo) + lo).to(dtype)
+
+    def signs(m):
+        return torch.randint(0, 2, (m,), device=device, generator=gen).to(torch.bool)
+
+    if workload == "all19":
+        x = domain_bits_device(func, n, gen, device=device)
+        rng = np.random.Generator(np.random.PCG64(seed + 0x100000000))
+        ns = int(n * 0.01)
+        sp = np.resize(specials_f32(func, rng), ns)
+        pos = torch.from_numpy(rng.choice(n, ns, replace=False)).to(device)
+        x[pos] = torch.from_numpy(sp.view(np.float32)).to(device)
+        return x
+    if workload == "precision":
+        if kind == "log":
+            mag = torch.exp2(u(-126.0, 127.0))
+            if func not in ("logf", "rsqrtf"):
+                mag = torch.where(signs(n), -mag, mag)
+            return mag.to(torch.float32)
+        x = u(-10.0, 10.0, torch.float32)
+        if kind == "large":
+            k = int(n * 0.05)
+            pos = torch.randperm(n, device=device, generator=gen)[:k]
+            mag = torch.exp2(torch.rand(k, dtype=torch.float64, device=device, generator=gen) * 107.0 + 20.0)
+            mag = torch.where(signs(k), -mag, mag)
+            x[pos] = mag.to(torch.float32)
+        return x
+    if kind == "domain":
+        return u(-1075.0, 1024.0)
+    if kind == "u20":
+        return u(-20.0, 20.0)
+    if kind == "bits":
+        b = torch.randint(1, 0x7FF0000000000000, (n,), dtype=torch.int64, device=device, generator=gen)
+        return b.view(torch.float64)
+    return u(0.125, 8.0)

@@ -1,0 +1,75 @@
+"""GPU tests of the launch shapes and the autotuner: every variant of the main kernel
+computes the same bits (checked against the oracle), and the autotuner keeps one of the
+variants it timed."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2605_15547_gb300 as crm  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+from paper_2605_15547_gb300 import workloads as W  # noqa: E402
+from paper_2605_15547_gb300._lib import NUM_VARIANTS  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+FUNCS = ["expf", "log1pf", "sinf", "sincosf", "atanf", "tanhf", "rsqrtf", "acosf"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    crm.set_force_slow(False)
+    yield
+    for f in W.F32_FUNCS:
+        crm.set_variant(f, 1, form="df")
+
+
+@pytest.mark.parametrize("func", FUNCS)
+def test_every_variant_gives_the_oracle_bits(func):
+    rng = W.rng_for(7, func)
+    n = (1 << 17) + 13
+    xb = W.domain_bits(func, n, rng)
+    ref = O.eval_bits(func, xb).reshape(-1)
+    buf = torch.from_numpy(np.concatenate([np.zeros(1, np.uint32), xb]).view(np.float32)).cuda()
+    x = buf[1:]  # 4-byte aligned, not 16: exercises the scalar head as well
+    for v in range(NUM_VARIANTS):
+        crm.set_variant(func, v, form="df")
+        y = crm.eval(func, x, form="df")
+        got = y.cpu().numpy().view(np.uint32).reshape(-1)
+        assert np.array_equal(got, ref), f"{func} variant {v} ({crm.variant_info(v)})"
+    crm.set_variant(func, 1, form="df")
+
+
+def test_plain_form_has_only_the_default_shape():
+    with pytest.raises(crm.CrmError):
+        crm.set_variant("expf", 4, form="plain")
+    crm.set_variant("expf", 1, form="plain")
+    assert crm.get_variant("expf", form="plain") == 1
+
+
+def test_autotune_keeps_a_timed_variant():
+    x = torch.from_numpy(W.domain_bits("logf", 1 << 22, W.rng_for(8, "logf")).view(np.float32)).cuda()
+    best, ms = crm.autotune("logf", x, form="df", reps=2)
+    assert best in ms and len(ms) == NUM_VARIANTS
+    assert all(t > 0 for t in ms.values())
+    assert crm.get_variant("logf", form="df") == best
+    y = crm.eval("logf", x[:4099], form="df")
+    ref = O.eval_bits("logf", x[:4099].cpu().numpy().view(np.uint32))
+    assert np.array_equal(y.cpu().numpy().view(np.uint32), ref)
+
+
+def test_autotune_batch_picks_a_tile():
+    rng = np.random.default_rng(3)
+    items = []
+    for i in range(40):
+        f = W.F32_FUNCS[i % 19]
+        n = int(rng.integers(1, 1 << 15))
+        x = torch.from_numpy(W.domain_bits(f, n, rng).view(np.float32)).cuda()
+        items.append((f, x, torch.empty((2 * n,) if f == "sincosf" else (n,), device="cuda")))
+    best, ms = crm.autotune_batch(items, reps=1)
+    assert 10 <= best <= 16 and best in ms
+    crm.set_batch_tile(14)

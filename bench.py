@@ -207,9 +207,9 @@ def run_batch(args, crm, torch, dev, stream, rank, world):
     items = list(zip(funcs, xs, ys))
     n_elems = int(lens.sum())
     crm.reserve(1 << 24, count, stream=stream)
-    tile = None
+    tile = mode = None
     if not args.no_autotune:
-        tile, _ = crm.autotune_batch(items, form=args.form, reps=1, stream=stream)
+        mode, tile, _ = crm.autotune_batch(items, form=args.form, reps=1, stream=stream)
     for _ in range(args.warmup):
         crm.eval_batch(items, form=args.form, stream=stream)
     torch.cuda.synchronize()
@@ -262,7 +262,8 @@ def run_batch(args, crm, torch, dev, stream, rank, world):
         "config": {"workload": f"batch: {count} arrays, lengths log-uniform [2^6,2^22] >> {args.scale}, "
                                "functions uniform over the 19", "total_elems": n_elems, "form": args.form,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
-                   "tile_log2": tile if tile is not None else "default 14"},
+                   "tile_log2": tile if tile is not None else "default 14",
+                   "batch_mode": mode if mode is not None else "default grouped"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "k_batch (step)", "peak_kind": kind},
         "one_launch_per_array": {"gelem_s": n_elems / (ms_single / 1e3) / 1e9, "ms": ms_single,

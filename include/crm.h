@@ -122,6 +122,14 @@ int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, u
 int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream);
 /* Tile size of the batching form, 2^log2_elems elements (8 <= log2_elems <= 24). */
 int crm_set_batch_tile(int log2_elems);
+/* Batch mode.  CRM_BATCH_MIXED: one persistent kernel over all arrays, a block-uniform
+   switch on each tile's function (2 launches per batch).  CRM_BATCH_GROUPED (default): the
+   arrays are ordered by function and each function present gets one persistent kernel
+   specialised for it, then one slow-path kernel for the whole batch (at most 20
+   launches, one CUDA graph when captured).  Both compute the same bits. */
+#define CRM_BATCH_MIXED 0
+#define CRM_BATCH_GROUPED 1
+int crm_set_batch_mode(int mode);
 
 /* ---- launch shapes and the autotuner (the paper has no counterpart: its SIMD kernels
    have one shape; on the GPU the best elements-per-thread, block size and load schedule
@@ -144,12 +152,13 @@ int crm_get_variant(int func_id, int form, int *variant);
    Overwrites out.  Synchronizes `stream`; CRM_ERR_CAPTURE while the stream is captured. */
 int crm_autotune(int func_id, int dtype, int form, const void *in, void *out, uint64_t n, int reps,
                  void *stream, int *best, float *ms);
-/* Same for the batching form: times tile sizes 2^CRM_BATCH_TILE_MIN .. 2^CRM_BATCH_TILE_MAX
-   on the given batch and keeps the fastest (ms: host, 7 floats, may be NULL). */
+/* Same for the batching form: times both batch modes (crm_set_batch_mode) with tile sizes
+   2^CRM_BATCH_TILE_MIN .. 2^CRM_BATCH_TILE_MAX on the given batch and keeps the fastest pair
+   (ms: host, 2 x 7 floats indexed [mode][log2 tile - CRM_BATCH_TILE_MIN], may be NULL). */
 #define CRM_BATCH_TILE_MIN 10
 #define CRM_BATCH_TILE_MAX 16
-int crm_autotune_batch(const crm_desc_t *descs, int count, int form, int reps, void *stream, int *best_shift,
-                       float *ms);
+int crm_autotune_batch(const crm_desc_t *descs, int count, int form, int reps, void *stream, int *best_mode,
+                       int *best_shift, float *ms);
 
 /* No-allocation variant of crm_eval_form.  The paper has no counterpart: this entry
    point exists for callers that cannot allocate device memory when they call the

@@ -16,7 +16,7 @@ from ._lib import F64_FUNCS, FORMS, FUNC_ID, FUNCS, CrmError, crm_desc_t, crm_st
 
 __all__ = ["eval", "eval_into", "eval_host", "eval_batch", "stats", "stats_reset",
            "set_form", "set_force_slow", "set_batch_tile", "reserve", "FUNCS", "FORMS", "CrmError", "version",
-           "variant_info", "set_variant", "get_variant", "autotune", "autotune_batch"]
+           "variant_info", "set_variant", "get_variant", "autotune", "autotune_batch", "set_batch_mode"]
 
 
 def _stream_ptr(stream=None):
@@ -168,15 +168,25 @@ def autotune(func, x, out=None, form=None, reps: int = 3, stream=None):
     return best.value, {v: ms[v] for v in range(L.NUM_VARIANTS) if ms[v] >= 0}
 
 
+BATCH_MODES = {"mixed": 0, "grouped": 1}
+
+
+def set_batch_mode(mode) -> None:
+    """'mixed': one kernel over all arrays; 'grouped': one kernel per function present."""
+    L.check(L.lib().crm_set_batch_mode(BATCH_MODES[mode] if isinstance(mode, str) else int(mode)))
+
+
 def autotune_batch(items, form=None, reps: int = 2, stream=None):
-    """Time the batching form's tile sizes on this batch and keep the fastest; returns
-    (best log2 tile, {log2 tile: ms per call})."""
-    best = ctypes.c_int()
+    """Time the batch modes and tile sizes on this batch and keep the fastest; returns
+    (best mode, best log2 tile, {(mode, log2 tile): ms per call})."""
+    mode, best = ctypes.c_int(), ctypes.c_int()
     n = L.BATCH_TILE_MAX - L.BATCH_TILE_MIN + 1
-    ms = (ctypes.c_float * n)()
+    ms = (ctypes.c_float * (2 * n))()
     L.check(L.lib().crm_autotune_batch(_descs(items), len(items), _form(form), int(reps), _stream_ptr(stream),
-                                       ctypes.byref(best), ms), "batch autotune")
-    return best.value, {L.BATCH_TILE_MIN + i: ms[i] for i in range(n)}
+                                       ctypes.byref(mode), ctypes.byref(best), ms), "batch autotune")
+    names = {v: k for k, v in BATCH_MODES.items()}
+    return (names[mode.value], best.value,
+            {(names[m], L.BATCH_TILE_MIN + i): ms[m * n + i] for m in range(2) for i in range(n)})
 
 
 def version() -> str:

@@ -72,7 +72,8 @@ def _lib():
                 lib.crm_set_variant.argtypes = [c_int, c_int, c_int]
                 lib.crm_get_variant.argtypes = [c_int, c_int, pi]
                 lib.crm_autotune.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, c_int, vp, pi, pf]
-                lib.crm_autotune_batch.argtypes = [ctypes.POINTER(crm_desc_t), c_int, c_int, c_int, vp, pi, pf]
+                lib.crm_autotune_batch.argtypes = [ctypes.POINTER(crm_desc_t), c_int, c_int, c_int, vp, pi, pi, pf]
+                lib.crm_set_batch_mode.argtypes = [c_int]
                 lib.crm_stats.argtypes = [vp, ctypes.POINTER(crm_stats_t)]
                 lib.crm_stats_reset.argtypes = [vp]
                 lib.crm_status_str.argtypes = [c_int]

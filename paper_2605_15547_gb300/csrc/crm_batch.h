@@ -29,9 +29,16 @@ struct BatchArgs {
   unsigned long long *qcount;  // sub-queue counters (see crm_ws.h)
   int nsubq;
   int force_hard;
+  uint32_t aid_base;  // index of descs[0] in the whole batch (grouped mode)
 };
 
+// Mixed mode: one kernel over all arrays (function switch per tile) + the slow pass.
 cudaError_t launch_batch(const BatchArgs &b, int form, int grid, int slow_grid, cudaStream_t s);
 const void *batch_kernel_symbol(int form);
+// Grouped mode: one kernel specialised for `func` over that function's arrays; the slow
+// pass runs once after all groups (launch_batch_slow, descs = the whole batch).
+cudaError_t launch_batch_group(int func, const BatchArgs &b, int form, int grid, cudaStream_t s);
+const void *batch_group_symbol(int func, int form);
+cudaError_t launch_batch_slow(const BatchArgs &b, int slow_grid, cudaStream_t s);
 
 }  // namespace crm

@@ -270,6 +270,7 @@ static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cu
 
 // ------------------------------------------------------------------ batch buffers
 static int g_batch_tile_shift = 14;  // the autotuner may change it (crm_set_batch_tile)
+static int g_batch_mode = CRM_BATCH_GROUPED;  // crm_set_batch_mode / the autotuner
 
 static int batch_buffers(cudaStream_t s, Workspace *w, int count) {
   if (w->bcap >= count) return CRM_OK;
@@ -501,23 +502,38 @@ int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
     if (e != cudaSuccess) return cuda_fail(e);
   }
   const int shift = g_batch_tile_shift;
-  uint64_t tiles = 0;
+  const bool grouped = g_batch_mode == CRM_BATCH_GROUPED;
+  // Staging: the mixed mode keeps the caller's order; the grouped mode orders the arrays by
+  // function (stable), with tile indices counted from the start of each function's group.
+  int gstart[CRM_SINCOSF + 10], gcount[CRM_SINCOSF + 10];
+  uint64_t gtiles[CRM_SINCOSF + 10];
+  const int NF = CRM_RSQRTF + 1;
+  for (int f = 0; f < NF; f++) gcount[f] = 0, gtiles[f] = 0;
+  for (int i = 0; i < count; i++)
+    if (descs[i].n) gcount[grouped ? descs[i].func_id : 0]++;
   int used = 0;
+  for (int f = 0; f < NF; f++) {
+    gstart[f] = used;
+    used += gcount[f];
+  }
+  if (used == 0) return CRM_OK;
+  int fill[CRM_SINCOSF + 10];
+  for (int f = 0; f < NF; f++) fill[f] = gstart[f];
   for (int i = 0; i < count; i++) {
     const crm_desc_t &d = descs[i];
     if (d.n == 0) continue;
-    BatchDesc &b = w->bstage[used++];
+    const int g = grouped ? d.func_id : 0;
+    BatchDesc &b = w->bstage[fill[g]++];
     b.in = d.in;
     b.out = d.out;
     b.n = d.n;
-    b.tile0 = tiles;
+    b.tile0 = gtiles[g];
     b.func = d.func_id;
     uintptr_t ia = (uintptr_t)d.in, oa = (uintptr_t)d.out;
     bool vec = (ia % 16) == 0 && (oa % 16) == 0 && (d.func_id != CRM_SINCOSF || (d.n * 4) % 16 == 0);
     b.flags = vec ? 1 : 0;
-    tiles += (d.n + (1ull << shift) - 1) >> shift;
+    gtiles[g] += (d.n + (1ull << shift) - 1) >> shift;
   }
-  if (used == 0) return CRM_OK;
   e = cudaMemcpyAsync(w->bdesc, w->bstage, used * sizeof(BatchDesc), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e);
   if (!cap) {
@@ -525,25 +541,50 @@ int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
     if (e != cudaSuccess) return cuda_fail(e);
   }
   int sms = dev_sms();
-  int bps = blocks_per_sm(batch_kernel_symbol(fm), KBLOCK);
-  uint64_t grid = (uint64_t)sms * bps;
-  if (grid > tiles) grid = tiles;
   BatchArgs a;
   a.descs = w->bdesc;
   a.count = used;
   a.tile_shift = shift;
-  a.total_tiles = tiles;
-  a.tiles_per_block = (tiles + grid - 1) / grid;
   a.hdr = w->hdr;
   a.q = w->q;
   a.cap = w->cap;
   a.qcount = subq_counts(w);
   a.nsubq = CRM_NSUBQ;
   a.force_hard = g_force_slow;
+  a.aid_base = 0;
   e = cudaMemsetAsync(a.qcount, 0, CRM_NSUBQ * CRM_SUBQ_STRIDE * 8, s);
   if (e != cudaSuccess) return cuda_fail(e);
-  e = launch_batch(a, fm, (int)grid, sms * 2, s);
+  if (!grouped) {
+    const uint64_t tiles = gtiles[0];
+    uint64_t grid = (uint64_t)sms * blocks_per_sm(batch_kernel_symbol(fm), KBLOCK);
+    if (grid > tiles) grid = tiles;
+    a.total_tiles = tiles;
+    a.tiles_per_block = (tiles + grid - 1) / grid;
+    e = launch_batch(a, fm, (int)grid, sms * 2, s);
+    return e == cudaSuccess ? CRM_OK : cuda_fail(e);
+  }
+  for (int f = 0; f < NF; f++) {
+    if (!gcount[f]) continue;
+    BatchArgs g = a;
+    g.descs = w->bdesc + gstart[f];
+    g.count = gcount[f];
+    g.aid_base = (uint32_t)gstart[f];
+    g.total_tiles = gtiles[f];
+    uint64_t grid = (uint64_t)sms * blocks_per_sm(batch_group_symbol(f, fm), KBLOCK);
+    if (grid > gtiles[f]) grid = gtiles[f];
+    g.tiles_per_block = (gtiles[f] + grid - 1) / grid;
+    e = launch_batch_group(f, g, fm, (int)grid, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  e = launch_batch_slow(a, sms * 2, s);
   return e == cudaSuccess ? CRM_OK : cuda_fail(e);
+}
+
+int crm_set_batch_mode(int mode) {
+  ensure_init();
+  if (mode != CRM_BATCH_MIXED && mode != CRM_BATCH_GROUPED) return CRM_ERR_ARG;
+  g_batch_mode = mode;
+  return CRM_OK;
 }
 
 int crm_set_batch_tile(int log2_elems) {
@@ -616,32 +657,40 @@ int crm_autotune(int func_id, int dtype, int form, const void *in, void *out, ui
   return CRM_OK;
 }
 
-int crm_autotune_batch(const crm_desc_t *descs, int count, int form, int reps, void *stream, int *best_shift,
-                       float *ms) {
+int crm_autotune_batch(const crm_desc_t *descs, int count, int form, int reps, void *stream, int *best_mode,
+                       int *best_shift, float *ms) {
   ensure_init();
   if (capturing((cudaStream_t)stream)) return CRM_ERR_CAPTURE;
   if (reps < 1) reps = 1;
-  const int keep = g_batch_tile_shift;
-  int bs = keep;
+  const int keep_shift = g_batch_tile_shift, keep_mode = g_batch_mode;
+  int bs = keep_shift, bm = keep_mode;
   float bms = 0.0f;
   bool have = false;
-  for (int sh = CRM_BATCH_TILE_MIN; sh <= CRM_BATCH_TILE_MAX; sh++) {
-    g_batch_tile_shift = sh;
-    float t = 0.0f;
-    int st = time_runs((cudaStream_t)stream, reps, &t, [&]() { return crm_eval_batch(descs, count, form, stream); });
-    if (st) {
-      g_batch_tile_shift = keep;
-      return st;
-    }
-    if (ms) ms[sh - CRM_BATCH_TILE_MIN] = t;
-    if (!have || t < bms) {
-      bms = t;
-      bs = sh;
-      have = true;
+  const int ntiles = CRM_BATCH_TILE_MAX - CRM_BATCH_TILE_MIN + 1;
+  for (int mode = CRM_BATCH_MIXED; mode <= CRM_BATCH_GROUPED; mode++) {
+    for (int sh = CRM_BATCH_TILE_MIN; sh <= CRM_BATCH_TILE_MAX; sh++) {
+      g_batch_tile_shift = sh;
+      g_batch_mode = mode;
+      float t = 0.0f;
+      int st = time_runs((cudaStream_t)stream, reps, &t, [&]() { return crm_eval_batch(descs, count, form, stream); });
+      if (st) {
+        g_batch_tile_shift = keep_shift;
+        g_batch_mode = keep_mode;
+        return st;
+      }
+      if (ms) ms[mode * ntiles + sh - CRM_BATCH_TILE_MIN] = t;
+      if (!have || t < bms) {
+        bms = t;
+        bs = sh;
+        bm = mode;
+        have = true;
+      }
     }
   }
   g_batch_tile_shift = bs;
+  g_batch_mode = bm;
   if (best_shift) *best_shift = bs;
+  if (best_mode) *best_mode = bm;
   return CRM_OK;
 }
 

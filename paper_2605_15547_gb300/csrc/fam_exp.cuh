@@ -99,7 +99,8 @@ template <int KIND> CRM_DEV float exp_plain(float x, const double *T16, bool &ha
 // remainder 2^-44.6, tables 2^-48, bracket roundings 2^-48: total < 2^-37.7, covered by
 // the test's 2^-37 allowance (hard_df).
 // Inputs outside [X_SUB, X_OVF] are resolved by selects: +inf above X_OVF, +0 below
-// X_ZERO, a quiet NaN for NaN; the subnormal band [X_ZERO, X_SUB) goes to the slow path.
+// X_ZERO, a quiet NaN for NaN; results in the subnormal band [X_ZERO, X_SUB) are rounded
+// to the subnormal grid from the same pair (below).
 template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard) {
   using K = ExpK<KIND>;
   float th, tl;
@@ -139,11 +140,29 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
   float s2 = s + r;
   float l2 = r - (s2 - s);
   float y = bitsf(fbits(s2) + ((uint32_t)(N >> 6) << 23));
-  bool ok = (x >= K::XSUB) && (x <= K::XOVF);  // false for NaN
-  float rsp = x != x ? qnan_of(x) : (x > 0.0f ? CRM_INF_F : 0.0f);
-  bool hsp = (x >= K::XZERO) && (x < K::XSUB);  // subnormal band
-  hard = ok ? hard_df(s2, l2) : hsp;
-  return ok ? y : rsp;
+  const bool ok = (x >= K::XSUB) && (x <= K::XOVF);  // false for NaN
+  if (__builtin_expect(ok, 1)) {
+    hard = hard_df(s2, l2);
+    return y;
+  }
+  // Out of range (rare): +inf, +0, a quiet NaN, or a subnormal result.
+  hard = false;
+  y = x != x ? qnan_of(x) : (x > 0.0f ? CRM_INF_F : 0.0f);
+  if ((x >= K::XZERO) && (x < K::XSUB)) {
+    // The result is the integer nearest to u = (s2 + l2) 2^(k + 149) times 2^-149
+    // (k + 149 in [-2, 23], the scaling exact).  With q = rint(u_hi) and
+    // d = (u_hi - q) + u_lo, the nearest integer is q, q + 1 (d > 1/2) or q - 1
+    // (d < -1/2); the pair's error (2^-37 of u < 2^-13) and d's rounding (2^-24) can move
+    // u across a half-integer only when ||d| - 1/2| <= 2^-12: those lanes go slow.
+    const float sc = bitsf((uint32_t)((N >> 6) + 149 + 127) << 23);
+    const float uh = s2 * sc, ul = l2 * sc;
+    const float q = rintf(uh);
+    const float d = (uh - q) + ul;
+    const float qi = q + (d > 0.5f ? 1.0f : (d < -0.5f ? -1.0f : 0.0f));
+    hard = fabsf(fabsf(d) - 0.5f) <= 0x1p-12f;
+    y = qi * 0x1p-149f;
+  }
+  return y;
 }
 
 // ------------------------------------------------------------------ double-double tier

@@ -116,10 +116,21 @@ CRM_DEV U128 shr128(U128 a, int s) {  // 0 < s < 64
   return {(a.lo >> s) | (a.hi << (64 - s)), a.hi >> s};
 }
 
+// exp2d_special on the bit pattern (integer compares: the FP64 pipe stays idle)
+CRM_DEV bool exp2d_special_bits(uint64_t b, double &r) {
+  const uint64_t ab = b & 0x7FFFFFFFFFFFFFFFull;
+  const bool neg = (b >> 63) != 0;
+  const bool nan = ab > 0x7FF0000000000000ull;
+  const bool ovf = !neg && ab >= 0x4090000000000000ull;  // x >= 1024 (and +inf)
+  const bool unf = neg && ab >= 0x4090CC0000000000ull;   // x <= -1075 (and -inf)
+  r = nan ? bitsd(b | 0x0008000000000000ull) : (ovf ? CRM_INF_D : 0.0);
+  return nan || ovf || unf;
+}
+
 CRM_DEV double exp2d_int(double x, const ulonglong2 *T, bool &hard) {
   double rs;
-  const bool sp = exp2d_special(x, rs);
   const uint64_t b = dbits(x);
+  const bool sp = exp2d_special_bits(b, rs);
   const int E = (int)((b >> 52) & 0x7FF);
   const bool tiny = E < 1023 - 60;  // |x| < 2^-60: 2^x rounds to 1
   const uint64_t M = (b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
@@ -238,10 +249,21 @@ CRM_DEV U128 sub128(U128 a, U128 b) {
   return r;
 }
 
+// logd_special on the bit pattern (integer compares)
+CRM_DEV bool logd_special_bits(uint64_t b, double &r) {
+  const uint64_t ab = b & 0x7FFFFFFFFFFFFFFFull;
+  const bool nan = ab > 0x7FF0000000000000ull;
+  const bool zero = ab == 0;
+  const bool neg = (b >> 63) != 0;
+  const bool inf = b == 0x7FF0000000000000ull;
+  r = nan ? bitsd(b | 0x0008000000000000ull) : (zero ? -CRM_INF_D : (neg ? CRM_QNAN_D : CRM_INF_D));
+  return nan || zero || neg || inf;
+}
+
 CRM_DEV double logd_int(double x, const ulonglong2 *LT, const unsigned short *RT, bool &hard) {
   double rs;
-  const bool sp = logd_special(x, rs);
-  const uint64_t b = dbits(sp ? 2.0 : x);
+  const bool sp = logd_special_bits(dbits(x), rs);
+  const uint64_t b = sp ? 0x4000000000000000ull : dbits(x);  // 2.0 on the special lanes
   int E = (int)(b >> 52);
   uint64_t M = b & 0x000FFFFFFFFFFFFFull;
   if (E == 0) {  // subnormal: shift the leading bit to position 52

@@ -35,8 +35,9 @@ template <int H> CRM_DEV bool hyp_special(float x, float &r) {
   float ax = fabsf(x);
   bool nan = x != x;
   if (H == HYP_EXPM1) {
-    r = nan ? qnan_of(x) : (x == 0.0f ? x : (x > 0.0f ? CRM_INF_F : -1.0f));
-    return nan || x == 0.0f || x > CRM_EXPF_X_OVF || x < CRM_EXPM1F_X_MONE;
+    const bool st = x >= CRM_EXPM1F_X_MONE && x <= CRM_EXPM1F_X_M2;  // -1 + 2^-24
+    r = nan ? qnan_of(x) : (x == 0.0f ? x : (st ? -0x1.fffffep-1f : (x > 0.0f ? CRM_INF_F : -1.0f)));
+    return nan || x == 0.0f || x > CRM_EXPF_X_OVF || x < CRM_EXPM1F_X_MONE || st;
   }
   if (H == HYP_SINH) {
     r = nan ? qnan_of(x) : (x == 0.0f ? x : copysignf(CRM_INF_F, x));
@@ -46,8 +47,9 @@ template <int H> CRM_DEV bool hyp_special(float x, float &r) {
     r = nan ? qnan_of(x) : CRM_INF_F;
     return nan || ax > CRM_SINHF_X_OVF;
   }
-  r = nan ? qnan_of(x) : (x == 0.0f ? x : copysignf(1.0f, x));
-  return nan || x == 0.0f || ax > CRM_TANHF_X_ONE;
+  const bool st = ax > CRM_TANHF_X_NEXT && ax <= CRM_TANHF_X_ONE;  // +-(1 - 2^-24)
+  r = nan ? qnan_of(x) : (x == 0.0f ? x : copysignf(st ? 0x1.fffffep-1f : 1.0f, x));
+  return nan || x == 0.0f || ax > CRM_TANHF_X_NEXT;
 }
 
 // ------------------------------------------------------------------ plain (FP64) tier
@@ -168,8 +170,10 @@ template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard) {
   float rsp;
   bool sp;
   if (H == HYP_EXPM1) {
-    sp = nan || tiny || x > CRM_EXPF_X_OVF || x < CRM_EXPM1F_X_MONE;
-    rsp = nan ? qnan_of(x) : (tiny ? x : (x > 0.0f ? CRM_INF_F : -1.0f));
+    // below X_MONE: -1; in [X_MONE, X_M2]: -1 + 2^-24 (the first step of the staircase)
+    const bool st = x >= CRM_EXPM1F_X_MONE && x <= CRM_EXPM1F_X_M2;
+    sp = nan || tiny || x > CRM_EXPF_X_OVF || x < CRM_EXPM1F_X_MONE || st;
+    rsp = nan ? qnan_of(x) : (tiny ? x : (st ? -0x1.fffffep-1f : (x > 0.0f ? CRM_INF_F : -1.0f)));
   } else if (H == HYP_SINH) {
     sp = nan || tiny || ax > CRM_SINHF_X_OVF;
     rsp = nan ? qnan_of(x) : (tiny ? x : copysignf(CRM_INF_F, x));
@@ -177,8 +181,9 @@ template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard) {
     sp = nan || tiny || ax > CRM_SINHF_X_OVF;
     rsp = nan ? qnan_of(x) : (tiny ? 1.0f : CRM_INF_F);
   } else {
-    sp = nan || tiny || ax > CRM_TANHF_X_ONE;
-    rsp = nan ? qnan_of(x) : (tiny ? x : copysignf(1.0f, x));
+    // above X_ONE: +-1; in (X_NEXT, X_ONE]: +-(1 - 2^-24)
+    sp = nan || tiny || ax > CRM_TANHF_X_NEXT;
+    rsp = nan ? qnan_of(x) : (tiny ? x : copysignf(ax > CRM_TANHF_X_ONE ? 1.0f : 0x1.fffffep-1f, x));
   }
   float arg = H == HYP_EXPM1 ? x : (H == HYP_TANH ? 2.0f * ax : ax);
   arg = sp ? 0.5f : arg;

@@ -268,6 +268,13 @@ const_f("CRM_TANHF_X_ONE", largest_f32_with(lambda v: 1 - mp.tanh(v) > half_ulp_
         "largest input whose tanh does not round to 1")
 const_f("CRM_EXPM1F_X_MONE", -largest_f32_with(lambda v: 1 - mp.exp(-v) < 1 - half_ulp_below_1, 1.0, 40.0),
         "inputs below this give exactly -1")
+# The next step of the saturation staircases: inputs in (X_NEXT, X_ONE] give tanh = 1 - 2^-24
+# exactly, inputs in [X_MONE, X_M2] give expm1 = -1 + 2^-24 (the midpoints next to them
+# are 1 - 3 2^-25 and -1 + 3 2^-25, whose preimages are transcendental).
+const_f("CRM_TANHF_X_NEXT", f32_below(mp.atanh(1 - 3 * half_ulp_below_1)),
+        "largest input whose tanh rounds below 1 - 2^-24")
+const_f("CRM_EXPM1F_X_M2", f32_below(mp.log(3 * half_ulp_below_1)),
+        "largest input whose expm1 rounds to -1 + 2^-24")
 # Taylor coefficients 1/k! (double and double-double)
 arr_d("CRM_INVFACT_D", [d(1 / mp.factorial(k)) for k in range(20)], "1/k!, k = 0..19")
 ifdd = []

@@ -11,6 +11,8 @@
 #include "crm_batch.h"
 #include "crm_fns.cuh"
 
+#define CRM_HOST_ONLY
+
 namespace crm {
 
 constexpr int BATCH_SMEM = 97 * 16;  // largest table (log family)
@@ -40,31 +42,40 @@ CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t
     const V *in4 = (const V *)(in + off);
     V *out4 = (V *)(out + off);
     V *out4b = (V *)(out + d.n + off);
-    for (uint64_t base = 0; base < nv; base += KBLOCK) {
-      uint64_t v = base + threadIdx.x;
-      bool act = v < nv;
-      V xv = act ? ld_stream(in4 + v) : V();
-      V y0, y1;
-      unsigned hm;
-      eval_vec<Fn, FORM>(xv, sm, y0, y1, hm);
-      hm = a.force_hard ? (1u << W) - 1u : hm;
-      hm = act ? hm : 0u;
-      if (act) {
-        st_stream(out4 + v, y0);
-        if (Fn::NOUT == 2) st_stream(out4b + v, y1);
+    // two vectors per thread per iteration: both loads are in flight before the work
+    for (uint64_t base = 0; base < nv; base += 2 * KBLOCK) {
+      V xv[2];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        uint64_t v = base + (uint64_t)u * KBLOCK + threadIdx.x;
+        xv[u] = v < nv ? ld_stream(in4 + v) : V();
       }
-      if (__any_sync(0xFFFFFFFFu, hm != 0)) {
-        uint64_t ii[W], xb[W];
 #pragma unroll
-        for (int j = 0; j < W; j++) {
-          ii[j] = off + v * W + j;
-          xb[j] = xbits_of(vget(xv, j));
+      for (int u = 0; u < 2; u++) {
+        uint64_t v = base + (uint64_t)u * KBLOCK + threadIdx.x;
+        bool act = v < nv;
+        V y0, y1;
+        unsigned hm;
+        eval_vec<Fn, FORM>(xv[u], sm, y0, y1, hm);
+        hm = a.force_hard ? (1u << W) - 1u : hm;
+        hm = act ? hm : 0u;
+        if (act) {
+          st_stream(out4 + v, y0);
+          if (Fn::NOUT == 2) st_stream(out4b + v, y1);
         }
-        unsigned over = push_hard<W>(hm, ii, xb, a);
-        if (over) {
+        if (__any_sync(0xFFFFFFFFu, hm != 0)) {
+          uint64_t ii[W], xb[W];
 #pragma unroll
-          for (int j = 0; j < W; j++)
-            if ((over >> j) & 1u) slow_store<Fn>(vget(xv, j), ii[j], a);
+          for (int j = 0; j < W; j++) {
+            ii[j] = off + v * W + j;
+            xb[j] = xbits_of(vget(xv[u], j));
+          }
+          unsigned over = push_hard<W>(hm, ii, xb, a);
+          if (over) {
+#pragma unroll
+            for (int j = 0; j < W; j++)
+              if ((over >> j) & 1u) slow_store<Fn>(vget(xv[u], j), ii[j], a);
+          }
         }
       }
     }
@@ -177,8 +188,34 @@ __global__ void __launch_bounds__(KBLOCK) k_batch(BatchArgs b) {
     uint64_t off = (t - d.tile0) << b.tile_shift;
     uint64_t m = d.n - off;
     if (m > (1ull << b.tile_shift)) m = 1ull << b.tile_shift;
-    TileOp<FORM> op{&d, (uint32_t)aidx, off, m, sm, &b};
+    TileOp<FORM> op{&d, b.aid_base + (uint32_t)aidx, off, m, sm, &b};
     CRM_FOR_FUNC(d.func, op);
+  }
+}
+
+// Grouped mode: every array of b has function Fn; the table is loaded once.
+template <class Fn, int FORM>
+__global__ void __launch_bounds__(KBLOCK) k_batch_group(BatchArgs b) {
+  __shared__ __align__(16) unsigned char sm[BATCH_SMEM];
+  Fn::template load<FORM>(sm);
+  __syncthreads();
+  const uint64_t t0 = (uint64_t)blockIdx.x * b.tiles_per_block;
+  uint64_t t1 = t0 + b.tiles_per_block;
+  if (t1 > b.total_tiles) t1 = b.total_tiles;
+  if (t0 >= t1) return;
+  int lo = 0, hi = b.count - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b.descs[mid].tile0 <= t0) lo = mid; else hi = mid - 1;
+  }
+  int aidx = lo;
+  for (uint64_t t = t0; t < t1; t++) {
+    while (t >= b.descs[aidx].tile0 + tiles_of(b.descs[aidx], b.tile_shift)) aidx++;
+    const BatchDesc d = b.descs[aidx];
+    uint64_t off = (t - d.tile0) << b.tile_shift;
+    uint64_t m = d.n - off;
+    if (m > (1ull << b.tile_shift)) m = 1ull << b.tile_shift;
+    batch_tile<Fn, FORM>(d, b.aid_base + (uint32_t)aidx, off, m, sm, b);
   }
 }
 
@@ -199,8 +236,45 @@ cudaError_t launch_batch(const BatchArgs &b, int form, int grid, int slow_grid, 
     k_batch<2><<<grid, KBLOCK, 0, s>>>(b);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  return launch_batch_slow(b, slow_grid, s);
+}
+
+cudaError_t launch_batch_slow(const BatchArgs &b, int slow_grid, cudaStream_t s) {
   k_batch_slow<<<slow_grid, KBLOCK, 0, s>>>(b);
   return cudaGetLastError();
+}
+
+// Per-function launchers and symbols of the grouped kernel, indexed by function id.
+struct GroupLaunch {
+  int form;
+  const BatchArgs *b;
+  int grid;
+  cudaStream_t s;
+  template <class Fn> CRM_HOST_ONLY void run() {
+    if (form == 1)
+      k_batch_group<Fn, 1><<<grid, KBLOCK, 0, s>>>(*b);
+    else
+      k_batch_group<Fn, 2><<<grid, KBLOCK, 0, s>>>(*b);
+  }
+};
+struct GroupSymbol {
+  int form;
+  const void *sym;
+  template <class Fn> CRM_HOST_ONLY void run() {
+    sym = form == 1 ? (const void *)k_batch_group<Fn, 1> : (const void *)k_batch_group<Fn, 2>;
+  }
+};
+
+cudaError_t launch_batch_group(int func, const BatchArgs &b, int form, int grid, cudaStream_t s) {
+  GroupLaunch L{form, &b, grid, s};
+  CRM_FOR_FUNC(func, L);
+  return cudaGetLastError();
+}
+
+const void *batch_group_symbol(int func, int form) {
+  GroupSymbol G{form, nullptr};
+  CRM_FOR_FUNC(func, G);
+  return G.sym;
 }
 
 const void *batch_kernel_symbol(int form) {

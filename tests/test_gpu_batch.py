@@ -42,15 +42,18 @@ def make_batch(count, max_log2, seed, misalign=True):
     return items
 
 
+@pytest.mark.parametrize("mode", ["mixed", "grouped"])
 @pytest.mark.parametrize("form", ["plain", "df"])
 @pytest.mark.parametrize("tile", [10, 14])
-def test_batch_matches_single_calls(form, tile):
+def test_batch_matches_single_calls(form, tile, mode):
     items = make_batch(300, 15, seed=100 + tile)
     crm.set_batch_tile(tile)
+    crm.set_batch_mode(mode)
     try:
         crm.eval_batch([(f, x, y) for f, x, y, _ in items], form=form)
     finally:
         crm.set_batch_tile(14)
+        crm.set_batch_mode("grouped")
     torch.cuda.synchronize()
     for f, x, y, _ in items:
         ref = torch.empty_like(y)
@@ -72,14 +75,17 @@ def test_batch_against_oracle_sample():
     assert crm.stats()["unresolved_total"] == 0
 
 
-def test_batch_forced_slow_path():
+@pytest.mark.parametrize("mode", ["mixed", "grouped"])
+def test_batch_forced_slow_path(mode):
     items = make_batch(100, 12, seed=9)
     crm.set_force_slow(True)
+    crm.set_batch_mode(mode)
     try:
         crm.eval_batch([(f, x, y) for f, x, y, _ in items])
         torch.cuda.synchronize()
     finally:
         crm.set_force_slow(False)
+        crm.set_batch_mode("grouped")
     for f, x, y, xh in items:
         got = y.cpu().numpy().view(np.uint32)
         ref = O.eval_bits(f, xh.view(np.uint32)).reshape(-1)

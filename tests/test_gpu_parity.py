@@ -56,7 +56,12 @@ def focus_inputs(func, rng):
     elif func == "atanf":
         parts += [W.uniform(-20, 20, 20000, rng), W.loguniform(-149, 127, 20000, rng, signed=True)]
     elif func in ("sinhf", "coshf", "tanhf", "expm1f"):
-        parts += [W.uniform(-10, 10, 20000, rng), W.loguniform(-149, 7, 20000, rng, signed=True)]
+        # +-4 ulps around the first two steps of the tanh and expm1 saturation staircases
+        steps = np.array([0x410762BE, 0x41102CB3, 0xC181D72E, 0xC18AA122], dtype=np.int64)
+        near = (steps[:, None] + np.arange(-4, 5)[None, :]).ravel()
+        near = np.concatenate([near, near ^ 0x80000000]).astype(np.uint32).view(np.float32)
+        parts += [W.uniform(-10, 10, 20000, rng), W.loguniform(-149, 7, 20000, rng, signed=True),
+                  W.uniform(8.3, 9.2, 5000, rng), W.uniform(-17.5, -16.0, 5000, rng), near]
     elif func == "rsqrtf":
         parts += [W.loguniform(-149, 128, 30000, rng, signed=False)]
     else:

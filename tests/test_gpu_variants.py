@@ -70,6 +70,8 @@ def test_autotune_batch_picks_a_tile():
         n = int(rng.integers(1, 1 << 15))
         x = torch.from_numpy(W.domain_bits(f, n, rng).view(np.float32)).cuda()
         items.append((f, x, torch.empty((2 * n,) if f == "sincosf" else (n,), device="cuda")))
-    best, ms = crm.autotune_batch(items, reps=1)
-    assert 10 <= best <= 16 and best in ms
+    mode, best, ms = crm.autotune_batch(items, reps=1)
+    assert 10 <= best <= 16 and (mode, best) in ms and mode in ("mixed", "grouped")
+    assert len(ms) == 14 and all(t > 0 for t in ms.values())
     crm.set_batch_tile(14)
+    crm.set_batch_mode("grouped")

@@ -113,10 +113,10 @@ struct FnExp2D {
   using T = double;
   static constexpr int NOUT = 1;
   // form 1: double-double in FP64; form 2: FP64-free (128-bit fixed point)
-  template <int FORM> static constexpr int tab_bytes() { return FORM == 2 ? 128 * 16 : 96 * 8; }
+  template <int FORM> static constexpr int tab_bytes() { return FORM == 2 ? 1024 * 16 : 96 * 8; }
   template <int FORM> CRM_DEV static void load(unsigned char *sm) {
     if (FORM == 2)
-      copy_tab(sm, CRM_EXP2I_T, 128 * 16);
+      copy_tab(sm, CRM_EXP2I_T, 1024 * 16);
     else
       copy_tab(sm, CRM_EXP2D_T, 96 * 8);
   }

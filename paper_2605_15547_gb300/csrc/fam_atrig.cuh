@@ -166,9 +166,12 @@ template <int KIND> CRM_DEV float atrig_df(float x, const float2 *AT, bool &hard
   }
   Pair<float> r = atan_ratio_df(a, b, AT);
   if (KIND == AT_ACOS && flip) r = df_add({CRM_PI_F_HI, CRM_PI_F_LO}, -r);
-  hard = !sp && hard_df(r.hi, r.lo);
-  float y = (KIND != AT_ACOS && x < 0.0f) ? -r.hi : r.hi;
-  return sp ? rsp : y;
+  if (__builtin_expect(sp, 0)) {
+    hard = false;
+    return rsp;
+  }
+  hard = hard_df(r.hi, r.lo);
+  return (KIND != AT_ACOS && x < 0.0f) ? -r.hi : r.hi;
 }
 
 // ------------------------------------------------------------------ double-double tier

@@ -88,14 +88,15 @@ CRM_DEV double exp2d_main(double x, const double *T, bool &hard) {
 // 128-bit fixed point on the integer pipes (GB300's FP64 rate is a small fraction of its
 // integer rate).  |x| 2^96 is formed exactly from x's significand (truncated below 2^-96
 // for |x| < 2^-16), negated for x < 0, so that k = floor(x') and the 96 fraction bits give
-// f = x' - k in [0, 1).  f = i1/64 + i2/4096 + r, r < 2^-12; T = 2^(i1/64) 2^(i2/4096)
-// from two 64-entry tables (Q126) multiplied in Q124; 2^r - 1 = r (a1 + r (a2 + ...)),
-// a_n = (ln 2)^n/n!, n <= 6, by Horner on rho = r 2^12 in Q64 with truncating products.
-// Error in 2^f: the Q64 Horner (coefficients 2^-65, each product and shift 2^-64) gives
-// 2^r - 1 to 2^-74.1, r's truncation to 64 bits adds 2^-76.5, the omitted degree-7 term
-// 2^-88 and T's 2^-122: |Y - 2^f| < 2^-72.8, i.e. below 2^52 units of Y (Q124).  The
-// rounding (normal results at bit 72 of Y, subnormal ones further up) is decided unless
-// the discarded part is within 2^52 units of half an ulp: those lanes take the slow path.
+// f = x' - k in [0, 1).  f = i/1024 + r, r < 2^-10; T = 2^(i/1024) from a 1024-entry
+// table (Q124, 16 KB of shared memory); 2^r - 1 = 2^-10 P with
+// P = rho (a1 + rho 2^-10 (a2 + ...)), rho = r 2^10, a_n = (ln 2)^n/n!, n <= 6, by
+// Horner with truncating products: Q64 for a1..a4, Q32 for a5, a6 (their weight is
+// 2^-40 or less).  Error in 2^f: P to 2^-62.2 (2^r - 1 to 2^-72.2), r's truncation to 64
+// bits 2^-74.5, the omitted degree-7 term 2^-86: |Y - 2^f| < 2^-70.9, i.e. below 2^54
+// units of Y (Q124).  The rounding (normal results at bit 72 of Y, subnormal ones further
+// up) is decided unless the discarded part is within 2^54 units of half an ulp: those
+// lanes take the slow path.
 struct U128 {
   uint64_t lo, hi;
 };
@@ -145,35 +146,39 @@ CRM_DEV double exp2d_int(double x, const ulonglong2 *T, bool &hard) {
   }
   const int k = (int)((int64_t)X.hi >> 32);
   const uint32_t Fh = (uint32_t)X.hi;
-  const int i1 = (int)(Fh >> 26), i2 = (int)((Fh >> 20) & 63u);
-  const uint64_t rho = ((uint64_t)(Fh & 0xFFFFFu) << 44) | (X.lo >> 20);
-  // 2^r - 1 = 2^-12 P, P = rho (a1 + rho 2^-12 (a2 + ...)) in Q64
-  uint64_t h = CRM_EXP2I_A6;
-  h = CRM_EXP2I_A5 + (__umul64hi(rho, h) >> 12);
-  h = CRM_EXP2I_A4 + (__umul64hi(rho, h) >> 12);
-  h = CRM_EXP2I_A3 + (__umul64hi(rho, h) >> 12);
-  h = CRM_EXP2I_A2 + (__umul64hi(rho, h) >> 12);
-  h = CRM_EXP2I_A1 + (__umul64hi(rho, h) >> 12);
+  const int i = (int)(Fh >> 22);
+  const uint64_t rho = ((uint64_t)(Fh & 0x3FFFFFu) << 42) | (X.lo >> 22);
+  // P = rho (a1 + rho 2^-10 (a2 + ...)): a6, a5 in Q32, the rest in Q64
+  const uint32_t rho32 = (uint32_t)(rho >> 32);
+  uint32_t h32 = CRM_EXP2I_A6_32;
+  h32 = CRM_EXP2I_A5_32 + (__umulhi(rho32, h32) >> 10);
+  const uint64_t rh5 = (uint64_t)rho32 * h32 + (((uint64_t)(uint32_t)rho * h32) >> 32);  // rho h5 2^-32
+  uint64_t h = CRM_EXP2I_A4 + (rh5 >> 10);
+  h = CRM_EXP2I_A3 + (__umul64hi(rho, h) >> 10);
+  h = CRM_EXP2I_A2 + (__umul64hi(rho, h) >> 10);
+  h = CRM_EXP2I_A1 + (__umul64hi(rho, h) >> 10);
   const uint64_t P = __umul64hi(rho, h);
-  // T = T1 T2 in Q124
-  const ulonglong2 t1 = T[i1], t2 = T[64 + i2];  // (low, high) words of Q126 values
-  U128 Tq = mul64w(t1.y, t2.y);
-  Tq = add128_64(Tq, __umul64hi(t1.y, t2.x));
-  Tq = add128_64(Tq, __umul64hi(t1.x, t2.y));
-  // Y = T + T 2^-12 P 2^-64 (Q124)
-  U128 tp = shr128(mul64w(Tq.hi, P), 12);
-  tp = add128_64(tp, __umul64hi(Tq.lo, P) >> 12);
-  const U128 Y = add128(Tq, tp);  // in [2^124, 2^125)
-  // round at bit sh = 72 (normal results) or higher (subnormal results)
-  const int sh = 72 + (k < -1022 ? -1022 - k : 0);  // 72 .. 125
-  const int sh64 = sh - 64;
-  const uint64_t q = Y.hi >> sh64;
-  const uint64_t remh = Y.hi & ((1ull << sh64) - 1ull);
-  const uint64_t dh = remh - (1ull << (sh64 - 1));  // high word of rem - half (the low word is Y.lo)
-  const bool up = (int64_t)dh > 0 || (dh == 0 && Y.lo != 0);
-  const bool near = (dh == 0 && Y.lo <= (1ull << 52)) || (dh == ~0ull && Y.lo >= 0ull - (1ull << 52));
-  const uint64_t mant = q + (up ? 1ull : 0ull);
-  const uint64_t bits = k >= -1022 ? ((uint64_t)(int64_t)(k + 1022) << 52) + mant : mant;
+  // Y = T + T 2^-10 P 2^-64 (Q124)
+  const ulonglong2 t = T[i];  // (low, high)
+  U128 tp = shr128(mul64w(t.y, P), 10);
+  tp = add128_64(tp, __umul64hi(t.x, P) >> 10);
+  const U128 Y = add128({t.x, t.y}, tp);  // in [2^124, 2^125)
+  const uint64_t ERR = 1ull << 54;
+  uint64_t bits;
+  bool near;
+  if (__builtin_expect(k >= -1022, 1)) {  // normal result: round at bit 72
+    const uint64_t dh = (Y.hi & 0xFFull) - 0x80ull;  // high word of (discarded part - half ulp)
+    const bool up = (int64_t)dh > 0 || (dh == 0 && Y.lo != 0);
+    near = (dh == 0 && Y.lo <= ERR) || (dh == ~0ull && Y.lo >= 0ull - ERR);
+    bits = ((uint64_t)(int64_t)(k + 1022) << 52) + (Y.hi >> 8) + (up ? 1ull : 0ull);
+  } else {  // subnormal result: round at bit 72 + (-1022 - k) <= 125
+    const int sh64 = 8 + (-1022 - k);
+    const uint64_t remh = Y.hi & ((1ull << sh64) - 1ull);
+    const uint64_t dh = remh - (1ull << (sh64 - 1));
+    const bool up = (int64_t)dh > 0 || (dh == 0 && Y.lo != 0);
+    near = (dh == 0 && Y.lo <= ERR) || (dh == ~0ull && Y.lo >= 0ull - ERR);
+    bits = (Y.hi >> sh64) + (up ? 1ull : 0ull);
+  }
   hard = !sp && !tiny && near;
   return sp ? rs : (tiny ? 1.0 : bitsd(bits));
 }

@@ -165,25 +165,16 @@ CRM_DEV float scale_f(float y, int k) { return bitsf(fbits(y) + ((uint32_t)k << 
 
 template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard) {
   float ax = fabsf(x);
-  bool nan = x != x;
   bool tiny = ax < 0x1p-25f;  // the correctly rounded result is x itself (or 1 for cosh)
-  float rsp;
-  bool sp;
+  bool sp;                    // NaN, tiny, saturated (results selected on a rare branch)
   if (H == HYP_EXPM1) {
     // below X_MONE: -1; in [X_MONE, X_M2]: -1 + 2^-24 (the first step of the staircase)
-    const bool st = x >= CRM_EXPM1F_X_MONE && x <= CRM_EXPM1F_X_M2;
-    sp = nan || tiny || x > CRM_EXPF_X_OVF || x < CRM_EXPM1F_X_MONE || st;
-    rsp = nan ? qnan_of(x) : (tiny ? x : (st ? -0x1.fffffep-1f : (x > 0.0f ? CRM_INF_F : -1.0f)));
-  } else if (H == HYP_SINH) {
-    sp = nan || tiny || ax > CRM_SINHF_X_OVF;
-    rsp = nan ? qnan_of(x) : (tiny ? x : copysignf(CRM_INF_F, x));
-  } else if (H == HYP_COSH) {
-    sp = nan || tiny || ax > CRM_SINHF_X_OVF;
-    rsp = nan ? qnan_of(x) : (tiny ? 1.0f : CRM_INF_F);
+    sp = !(x > CRM_EXPM1F_X_M2 && x <= CRM_EXPF_X_OVF) || tiny;
+  } else if (H == HYP_SINH || H == HYP_COSH) {
+    sp = !(ax <= CRM_SINHF_X_OVF) || tiny;
   } else {
     // above X_ONE: +-1; in (X_NEXT, X_ONE]: +-(1 - 2^-24)
-    sp = nan || tiny || ax > CRM_TANHF_X_NEXT;
-    rsp = nan ? qnan_of(x) : (tiny ? x : copysignf(ax > CRM_TANHF_X_ONE ? 1.0f : 0x1.fffffep-1f, x));
+    sp = !(ax <= CRM_TANHF_X_NEXT) || tiny;
   }
   float arg = H == HYP_EXPM1 ? x : (H == HYP_TANH ? 2.0f * ax : ax);
   arg = sp ? 0.5f : arg;
@@ -217,10 +208,19 @@ template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard) {
     }
     sc = Y.k - 1;
   }
-  hard = !sp && hard_df(r.hi, r.lo);
-  float y = scale_f(r.hi, sc);
-  if (H == HYP_SINH || H == HYP_TANH) y = x < 0.0f ? -y : y;
-  return sp ? rsp : y;
+  if (__builtin_expect(!sp, 1)) {
+    hard = hard_df(r.hi, r.lo);
+    float y = scale_f(r.hi, sc);
+    if (H == HYP_SINH || H == HYP_TANH) y = x < 0.0f ? -y : y;
+    return y;
+  }
+  hard = false;
+  if (x != x) return qnan_of(x);
+  if (H == HYP_EXPM1)
+    return tiny ? x : (x > 0.0f ? CRM_INF_F : (x < CRM_EXPM1F_X_MONE ? -1.0f : -0x1.fffffep-1f));
+  if (H == HYP_SINH) return tiny ? x : copysignf(CRM_INF_F, x);
+  if (H == HYP_COSH) return tiny ? 1.0f : CRM_INF_F;
+  return tiny ? x : copysignf(ax > CRM_TANHF_X_ONE ? 1.0f : 0x1.fffffep-1f, x);
 }
 
 // ------------------------------------------------------------------ double-double tier

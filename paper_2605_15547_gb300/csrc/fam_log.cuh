@@ -202,8 +202,12 @@ template <int KIND> CRM_DEV float log_df(float x, const float4 *T97, bool &hard)
   float lo = S.lo + (Bl + ql);
   float s2 = S.hi + lo;
   float l2 = lo - (s2 - S.hi);
-  hard = ok && hard_df(s2, l2);
-  return ok ? s2 : special_log<KIND>(x);
+  if (__builtin_expect(ok, 1)) {
+    hard = hard_df(s2, l2);
+    return s2;
+  }
+  hard = false;  // NaN, zero, negative, infinite (rare: a branch, not selects)
+  return special_log<KIND>(x);
 }
 
 // ------------------------------------------------------------------ double-double tier

@@ -62,6 +62,8 @@ CRM_DEV float rsqrt_df(float x, bool &hard) {
   float corr = fma_(e, 0.375f, 0.5f) * e;
   float c = y0 * corr;
   Pair<float> y = fast_two_sum(y0, c);
+  // special inputs (x <= 0, NaN, +inf) by selects: they are common in real data (half of
+  // a symmetric input range), so a branch would diverge in most warps
   hard = !sp && hard_df(y.hi, y.lo);
   float out = sub ? y.hi * 0x1p12f : (big ? y.hi * 0x1p-32f : y.hi);
   return sp ? r : out;

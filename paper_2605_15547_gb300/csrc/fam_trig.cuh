@@ -150,7 +150,9 @@ struct TrigF {
   bool tiny;
 };
 
-CRM_DEV TrigF trig_df_core(float x, const uint32_t *P, const float4 *SC) {
+// KIND = TRIG_SIN or TRIG_COS: only the rotation term the quadrant needs is formed, in R.A
+// (sin: B when q is odd, else A; cos: A when q is odd, else B); otherwise both.
+template <int KIND> CRM_DEV TrigF trig_df_core(float x, const uint32_t *P, const float4 *SC) {
   float ax = fabsf(x);
   bool small = ax < 0x1p-6f;
   uint32_t r[4];
@@ -208,39 +210,52 @@ CRM_DEV TrigF trig_df_core(float x, const uint32_t *P, const float4 *SC) {
   int j = N7 & 31;
   float4 T = SC[j];  // (sin hi, lo, cos hi, lo)
   Pair<float> S = {T.x, T.y}, C = {T.z, T.w}, ct = {ch, cl}, st = {sh, sl};
+  R.q = N7 >> 5;
+  if (KIND == TRIG_SIN || KIND == TRIG_COS) {
+    // B = C cos t + (-S) sin t, A = S cos t + C sin t: one product pair with chosen factors
+    const bool useB = (KIND == TRIG_SIN) == ((R.q & 1) != 0);
+    const Pair<float> Pf = useB ? C : S, Qf = useB ? -S : C;
+    R.A = df_add(df_mul(Pf, ct), df_mul(Qf, st));
+    R.B = R.A;
+    return R;
+  }
   Pair<float> a1 = df_mul(S, ct), a2 = df_mul(C, st);
   Pair<float> b1 = df_mul(C, ct), b2 = df_mul(S, st);
   R.A = df_add(a1, a2);
   R.B = df_add(b1, -b2);
-  R.q = N7 >> 5;
   return R;
 }
 
 template <int KIND>
 CRM_DEV void trig_df(float x, const uint32_t *P, const float4 *SC, float *y, bool &hard) {
-  float rsp;
-  bool sp = trig_special(x, rsp);
-  TrigF R = trig_df_core(sp ? 1.0f : x, P, SC);
+  const bool sp = !(fabsf(x) < CRM_INF_F);  // NaN or infinite
+  TrigF R = trig_df_core<KIND>(sp ? 1.0f : x, P, SC);
   Pair<float> sn, cs;
-  trig_rotate<Pair<float>>(KIND, x, R.q, R.A, R.B, sn, cs);
-  bool zero = x == 0.0f;
-  if (KIND == TRIG_TAN) {
-    Pair<float> t = df_div(sn, cs);
-    hard = !sp && !zero && (R.tiny || hard_df(t.hi, t.lo));
-    y[0] = sp ? rsp : (zero ? x : t.hi);
+  trig_rotate<Pair<float>>(KIND, x, R.q, R.A, R.B, sn, cs);  // A == B for sin, cos alone
+  if (__builtin_expect(sp, 0)) {
+    hard = false;
+    const float r = x != x ? qnan_of(x) : CRM_QNAN_F;
+    y[0] = r;
+    if (KIND == TRIG_SINCOS) y[1] = r;
     return;
   }
-  bool hs = hard_df(sn.hi, sn.lo), hc = hard_df(cs.hi, cs.lo);
+  const bool zero = x == 0.0f;  // sin/tan(+-0) = +-0
+  if (KIND == TRIG_TAN) {
+    Pair<float> t = df_div(sn, cs);
+    hard = !zero && (R.tiny || hard_df(t.hi, t.lo));
+    y[0] = zero ? x : t.hi;
+    return;
+  }
   if (KIND == TRIG_SIN) {
-    hard = !sp && !zero && (R.tiny || hs);
-    y[0] = sp ? rsp : (zero ? x : sn.hi);
+    hard = !zero && (R.tiny || hard_df(sn.hi, sn.lo));
+    y[0] = zero ? x : sn.hi;
   } else if (KIND == TRIG_COS) {
-    hard = !sp && (R.tiny || hc);
-    y[0] = sp ? rsp : cs.hi;
+    hard = R.tiny || hard_df(cs.hi, cs.lo);
+    y[0] = cs.hi;
   } else {
-    hard = !sp && (R.tiny || (hs && !zero) || hc);
-    y[0] = sp ? rsp : (zero ? x : sn.hi);
-    y[1] = sp ? rsp : cs.hi;
+    hard = R.tiny || (hard_df(sn.hi, sn.lo) && !zero) || hard_df(cs.hi, cs.lo);
+    y[0] = zero ? x : sn.hi;
+    y[1] = cs.hi;
   }
 }
 

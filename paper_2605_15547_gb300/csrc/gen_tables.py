@@ -432,13 +432,14 @@ def arr_u64_pairs(name, vals, comment):
 
 
 ti = []
-for div in (64, 4096):
-    for i in range(64):
-        N = q_round(mp.power(2, mp.mpf(i) / div), 126, 128)
-        ti += [N & 0xFFFFFFFFFFFFFFFF, N >> 64]
-arr_u64_pairs("CRM_EXP2I_T", ti, "2^(i/64) then 2^(i/4096), i = 0..63, as round(v 2^126): (low, high) 64-bit words")
+for i in range(1024):
+    N = q_round(mp.power(2, mp.mpf(i) / 1024), 124, 128)
+    ti += [N & 0xFFFFFFFFFFFFFFFF, N >> 64]
+arr_u64_pairs("CRM_EXP2I_T", ti, "2^(i/1024), i = 0..1023, as round(v 2^124): (low, high) 64-bit words")
 for k in range(1, 7):
     emit(f"#define CRM_EXP2I_A{k} 0x{q_round(LN2 ** k / mp.factorial(k), 64, 64):016X}ull  // (ln 2)^{k}/{k}! 2^64")
+for k in (5, 6):
+    emit(f"#define CRM_EXP2I_A{k}_32 0x{q_round(LN2 ** k / mp.factorial(k), 32, 32):08X}u  // (ln 2)^{k}/{k}! 2^32")
 emit()
 
 emit("// ===== binary64 log, FP64-free main path (128-bit fixed point) =====")

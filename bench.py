@@ -45,6 +45,31 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
 
+# DRAM traffic per element (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture
+# of the function's main kernel, divided by the elements of that launch), with the
+# fingerprint of the kernel sources it was taken on; a traffic figure is reported only
+# while the sources still match (profiles/ holds the captures).
+TRAFFIC_BYTES_PER_ELEM = {}
+TRAFFIC_SOURCES = ""
+
+
+def kernel_sources_fingerprint() -> str:
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2605_15547_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(func: str, n: int):
+    if func not in TRAFFIC_BYTES_PER_ELEM or kernel_sources_fingerprint() != TRAFFIC_SOURCES:
+        return None
+    return TRAFFIC_BYTES_PER_ELEM[func] * n
+
+
 def load_peaks():
     try:
         with open(PEAKS_PATH) as fh:
@@ -433,7 +458,8 @@ def main():
         "config": dict(cfg, form=args.form, arrays=labels, l2="inputs larger than L2 (no flush)",
                        parallelism=f"replicas{world}", launch_shapes=tuned or "default"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": f"k_main+k_slow<{funcs[dom]}>",
+                     "frac": achieved / peak, "traffic": measured_traffic(funcs[dom], xs[dom].numel()),
+                     "kernel": f"k_main+k_slow<{funcs[dom]}>",
                      "array": labels[dom], "bytes_per_elem": bytes_per_elem(funcs[dom]), "peak_kind": peak_kind},
         "other_form": {"form": other, "step_gelem_s": step_other},
         "per_array": per_arr,

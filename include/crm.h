@@ -112,13 +112,14 @@ int crm_eval_form(int func_id, int dtype, int form, const void *in, void *out, u
 int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, uint64_t n,
                   void *stream);
 
-/* Evaluate `count` arrays of mixed binary32 functions and uneven lengths with one
+/* Evaluate `count` arrays of mixed functions and uneven lengths with one
    persistent kernel (the batching form) and one slow-path kernel.  descs is host memory,
    read before return (the library keeps a page-locked copy for the upload; a CUDA graph
    that captured the call re-reads that copy at every replay).  Arrays are cut into tiles
    of 2^k elements (crm_set_batch_tile, default 2^14); each block of the persistent grid
    owns a contiguous range of tiles.  Asynchronous.  Capturable after crm_reserve(.., count).
-   Errors: as crm_eval for any descriptor; CRM_ERR_FORM for binary64 functions. */
+   Binary64 arrays (exp2, log) may be mixed in; a batch that holds any runs in the grouped
+   mode (crm_set_batch_mode).  Errors: as crm_eval for any descriptor. */
 int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream);
 /* Tile size of the batching form, 2^log2_elems elements (8 <= log2_elems <= 24). */
 int crm_set_batch_tile(int log2_elems);

@@ -481,12 +481,13 @@ int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
   if (!descs) return CRM_ERR_NULL;
   if (form < CRM_FORM_AUTO || form > CRM_FORM_DF32) return CRM_ERR_FORM;
   if (count > (1 << 23)) return CRM_ERR_ARG;
+  bool has64 = false;
   for (int i = 0; i < count; i++) {
     const crm_desc_t &d = descs[i];
     int st = check_args(d.func_id, d.dtype, d.in, d.out, d.n);
     if (st) return st;
-    if (d.func_id >= CRM_EXP2) return CRM_ERR_FORM;  // binary64 functions: use crm_eval
     if (resolve_form(g_table[d.func_id], form) < 0) return CRM_ERR_FORM;
+    if (d.func_id >= CRM_EXP2) has64 = true;
   }
   int fm = form == CRM_FORM_PLAIN_FP64 ? 1 : 2;
   cudaStream_t s = (cudaStream_t)stream;
@@ -502,12 +503,12 @@ int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
     if (e != cudaSuccess) return cuda_fail(e);
   }
   const int shift = g_batch_tile_shift;
-  const bool grouped = g_batch_mode == CRM_BATCH_GROUPED;
+  const bool grouped = g_batch_mode == CRM_BATCH_GROUPED || has64;  // binary64: grouped only
   // Staging: the mixed mode keeps the caller's order; the grouped mode orders the arrays by
   // function (stable), with tile indices counted from the start of each function's group.
-  int gstart[CRM_SINCOSF + 10], gcount[CRM_SINCOSF + 10];
-  uint64_t gtiles[CRM_SINCOSF + 10];
-  const int NF = CRM_RSQRTF + 1;
+  int gstart[CRM_NUM_FUNCS], gcount[CRM_NUM_FUNCS];
+  uint64_t gtiles[CRM_NUM_FUNCS];
+  const int NF = CRM_NUM_FUNCS;
   for (int f = 0; f < NF; f++) gcount[f] = 0, gtiles[f] = 0;
   for (int i = 0; i < count; i++)
     if (descs[i].n) gcount[grouped ? descs[i].func_id : 0]++;
@@ -517,7 +518,7 @@ int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
     used += gcount[f];
   }
   if (used == 0) return CRM_OK;
-  int fill[CRM_SINCOSF + 10];
+  int fill[CRM_NUM_FUNCS];
   for (int f = 0; f < NF; f++) fill[f] = gstart[f];
   for (int i = 0; i < count; i++) {
     const crm_desc_t &d = descs[i];
@@ -532,7 +533,7 @@ int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
     uintptr_t ia = (uintptr_t)d.in, oa = (uintptr_t)d.out;
     bool vec = (ia % 16) == 0 && (oa % 16) == 0 && (d.func_id != CRM_SINCOSF || (d.n * 4) % 16 == 0);
     b.flags = vec ? 1 : 0;
-    gtiles[g] += (d.n + (1ull << shift) - 1) >> shift;
+    gtiles[g] += (d.n + (1ull << shift) - 1) >> shift;  // (binary64 vectors: 2 elements)
   }
   e = cudaMemcpyAsync(w->bdesc, w->bstage, used * sizeof(BatchDesc), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e);

@@ -198,7 +198,10 @@ template <int KIND> CRM_DEV float log_df(float x, const float4 *T97, bool &hard)
   float B = eK + Lh;
   float Bz = Lh - (B - eK);
   float Bl = Bz + fma_(ef, K::KL, Ll);
-  Pair<float> S = two_sum(B, qh);
+  // |B| > |qh| unless B = 0: with e != 0, |e K + L| >= 0.125 (log10; more for ln, log2);
+  // with e = 0, |L_j| >= |log_b(1 +- 1/128)| > |log_b(1 + r)| since |r| <= 2^-8/0.75; so
+  // Fast2Sum is exact here
+  Pair<float> S = fast_two_sum(B, qh);
   float lo = S.lo + (Bl + ql);
   float s2 = S.hi + lo;
   float l2 = lo - (s2 - S.hi);

@@ -128,6 +128,14 @@ CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t
     default: break;                                           \
   }
 
+// The same over all 21 functions (grouped mode and the slow pass; binary64 included).
+#define CRM_FOR_FUNC_ALL(func, F)                              \
+  switch (func) {                                             \
+    case 19: F.template run<FnExp2D>(); break;                \
+    case 20: F.template run<FnLogD>(); break;                 \
+    default: CRM_FOR_FUNC(func, F);                           \
+  }
+
 template <int FORM> struct LoadOp {
   unsigned char *sm;
   template <class Fn> CRM_DEV void run() { Fn::template load<FORM>(sm); }
@@ -141,7 +149,7 @@ template <int FORM> struct TileOp {
   template <class Fn> CRM_DEV void run() { batch_tile<Fn, FORM>(*d, aid, off, m, sm, *b); }
 };
 struct SlowOp {
-  float x;
+  uint64_t xbits;
   bool force;
   const BatchDesc *d;
   uint64_t idx;
@@ -150,7 +158,7 @@ struct SlowOp {
     using T = typename Fn::T;
     T y[2];
     bool u;
-    Fn::slow((T)x, y, u, force);
+    Fn::slow(x_from_bits<T>(xbits), y, u, force);
     T *out = (T *)d->out;
     out[idx] = y[0];
     if (Fn::NOUT == 2) out[d->n + idx] = y[1];
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(KBLOCK) k_batch(BatchArgs b) {
 // Grouped mode: every array of b has function Fn; the table is loaded once.
 template <class Fn, int FORM>
 __global__ void __launch_bounds__(KBLOCK) k_batch_group(BatchArgs b) {
-  __shared__ __align__(16) unsigned char sm[BATCH_SMEM];
+  __shared__ __align__(16) unsigned char sm[(Fn::template tab_bytes<FORM>() > 0) ? Fn::template tab_bytes<FORM>() : 16];
   Fn::template load<FORM>(sm);
   __syncthreads();
   const uint64_t t0 = (uint64_t)blockIdx.x * b.tiles_per_block;
@@ -224,8 +232,8 @@ __global__ void __launch_bounds__(KBLOCK) k_batch_slow(BatchArgs b) {
     uint32_t aid = (uint32_t)(e.idx >> 40);
     uint64_t idx = e.idx & ((1ull << 40) - 1);
     const BatchDesc *d = &b.descs[aid];
-    SlowOp op{bitsf((uint32_t)e.x), b.force_hard != 0, d, idx, &b.hdr->unresolved_total};
-    CRM_FOR_FUNC(d->func, op);
+    SlowOp op{e.x, b.force_hard != 0, d, idx, &b.hdr->unresolved_total};
+    CRM_FOR_FUNC_ALL(d->func, op);
   });
 }
 
@@ -267,13 +275,13 @@ struct GroupSymbol {
 
 cudaError_t launch_batch_group(int func, const BatchArgs &b, int form, int grid, cudaStream_t s) {
   GroupLaunch L{form, &b, grid, s};
-  CRM_FOR_FUNC(func, L);
+  CRM_FOR_FUNC_ALL(func, L);
   return cudaGetLastError();
 }
 
 const void *batch_group_symbol(int func, int form) {
   GroupSymbol G{form, nullptr};
-  CRM_FOR_FUNC(func, G);
+  CRM_FOR_FUNC_ALL(func, G);
   return G.sym;
 }
 

@@ -131,3 +131,33 @@ def test_single_call_graph_capture():
     torch.cuda.synchronize()
     ref = O.eval_bits("logf", x.cpu().numpy().view(np.uint32))
     assert np.array_equal(y.cpu().numpy().view(np.uint32), ref)
+
+
+def test_batch_with_binary64_arrays():
+    """binary64 arrays mixed into a batch (the grouped mode runs them) against the oracle"""
+    rng = np.random.default_rng(21)
+    items = []
+    for i in range(60):
+        f = ["expf", "exp2", "logf", "log", "sincosf"][i % 5]
+        n = int(rng.integers(1, 5000))
+        if f == "exp2":
+            x = W.f64_uniform(-1080, 1030, n, rng)
+        elif f == "log":
+            x = W.f64_positive_bits(n, rng)
+        else:
+            x = W.domain_bits(f, n, rng).view(np.float32)
+        xt = torch.from_numpy(x).cuda()
+        rows = 2 if f == "sincosf" else 1
+        items.append((f, xt, torch.empty(rows * n, dtype=xt.dtype, device="cuda"), x))
+    for mode in ("mixed", "grouped"):  # mixed falls back to grouped for binary64
+        crm.set_batch_mode(mode)
+        try:
+            crm.eval_batch([(f, x, y) for f, x, y, _ in items])
+            torch.cuda.synchronize()
+        finally:
+            crm.set_batch_mode("grouped")
+        for f, x, y, xh in items:
+            bits = np.uint64 if xh.dtype == np.float64 else np.uint32
+            got = y.cpu().numpy().view(bits)
+            ref = O.eval_bits(f, xh.view(bits)).reshape(-1)
+            assert np.array_equal(got, ref), (mode, f)

@@ -121,6 +121,15 @@ CRM_DEV Pair<float> df_mul(Pair<float> a, Pair<float> b) {
   pl = fma_(a.lo, b.hi, pl);
   return fast_two_sum(p, pl);
 }
+// The same product left unnormalised (p + pl, |pl| below 2^-22 |p|), for a sum that
+// renormalises anyway (df_add)
+CRM_DEV Pair<float> df_mul_raw(Pair<float> a, Pair<float> b) {
+  float p = a.hi * b.hi;
+  float pl = fma_(a.hi, b.hi, -p);
+  pl = fma_(a.hi, b.lo, pl);
+  pl = fma_(a.lo, b.hi, pl);
+  return {p, pl};
+}
 // Sum of float pairs without ordering assumption
 CRM_DEV Pair<float> df_add(Pair<float> a, Pair<float> b) {
   Pair<float> s = two_sum(a.hi, b.hi);

@@ -140,9 +140,10 @@ CRM_DEV void trig_plain(float x, const uint32_t *P, const double *SC, float *y, 
 // with t^2 and t^3/6 carried as pairs (exact FMA splits), the higher terms in float.
 // Error budget (relative to the result): f to 2^-63.6 absolute plus 2^-48 relative
 // (lanes with j = 0 and |f| < 2^-24, where the result is as small as t, go to the slow
-// path: 2^-40 there);
-// pi/64 pair 2^-48; t products 2^-46; sin t, cos t 2^-45; table pairs 2^-48; the
-// rotation terms S cos t + C sin t lose at most 2^5.4: total < 2^-39, inside the 2^-37
+// path: 2^-40 there); pi/64 pair 2^-48; t products 2^-46; sin t, cos t 2^-45 (t^3/6 is
+// up to 2^-13.3 |t|, so it is carried as a pair); table pairs 2^-48; the rotation's pair
+// products and sum 2^-45; the rotation terms S cos t + C sin t lose at most 2^5.4 (a
+// result as small as sin(pi/128) from terms up to 1): total < 2^-39, inside the 2^-37
 // that hard_df allows.
 struct TrigF {
   Pair<float> A, B;  // sin and cos of (j pi/64 + t)
@@ -215,12 +216,12 @@ template <int KIND> CRM_DEV TrigF trig_df_core(float x, const uint32_t *P, const
     // B = C cos t + (-S) sin t, A = S cos t + C sin t: one product pair with chosen factors
     const bool useB = (KIND == TRIG_SIN) == ((R.q & 1) != 0);
     const Pair<float> Pf = useB ? C : S, Qf = useB ? -S : C;
-    R.A = df_add(df_mul(Pf, ct), df_mul(Qf, st));
+    R.A = df_add(df_mul_raw(Pf, ct), df_mul_raw(Qf, st));
     R.B = R.A;
     return R;
   }
-  Pair<float> a1 = df_mul(S, ct), a2 = df_mul(C, st);
-  Pair<float> b1 = df_mul(C, ct), b2 = df_mul(S, st);
+  Pair<float> a1 = df_mul_raw(S, ct), a2 = df_mul_raw(C, st);
+  Pair<float> b1 = df_mul_raw(C, ct), b2 = df_mul_raw(S, st);
   R.A = df_add(a1, a2);
   R.B = df_add(b1, -b2);
   return R;

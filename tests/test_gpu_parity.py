@@ -31,11 +31,13 @@ def forms_of(func):
     return out
 
 
-# Inputs on which an earlier double-float reduction lost accuracy (x within a few 2^-20
-# of a multiple of pi/2, found by the exhaustive sweep); all must be correctly rounded.
+# Inputs on which earlier double-float variants lost accuracy, found by the exhaustive
+# form-agreement sweep: x within a few 2^-20 of a multiple of pi/2 (a reduction whose
+# fraction was converted too coarsely), and 0x41970065 (sin t with its cubic term in single
+# precision: t^3/6 reaches 2^-13.3 |t|); all must be correctly rounded.
 TRIG_REGRESSION = np.array([
     0x543146A6, 0x54B146A6, 0x553146A6, 0x72A03E3A, 0x435D7B77, 0x53B146A6, 0x5D6BD9CD,
-    0x5DDC92D2, 0x61D3B126, 0x673D1651, 0x6946E3BB, 0x7EB919F2], dtype=np.uint32)
+    0x5DDC92D2, 0x61D3B126, 0x673D1651, 0x6946E3BB, 0x7EB919F2, 0x41970065], dtype=np.uint32)
 TRIG_REGRESSION = np.concatenate([TRIG_REGRESSION, TRIG_REGRESSION | np.uint32(0x80000000)])
 
 

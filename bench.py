@@ -49,8 +49,9 @@ FALLBACK_HBM_GBS = 6800.0
 # of the function's main kernel, divided by the elements of that launch), with the
 # fingerprint of the kernel sources it was taken on; a traffic figure is reported only
 # while the sources still match (profiles/ holds the captures).
-TRAFFIC_BYTES_PER_ELEM = {}
-TRAFFIC_SOURCES = ""
+TRAFFIC_BYTES_PER_ELEM = {"expf": 6.634, "logf": 6.641, "sinf": 6.667, "tanf": 6.641, "acosf": 6.474,
+                          "sincosf": 10.404, "exp2": 14.488, "log": 14.475}
+TRAFFIC_SOURCES = "1df1ca92b1c0a8e0"  # profiles/traffic_main_kernels_2p25.md, k_main_sincosf_df_2p25.md
 
 
 def kernel_sources_fingerprint() -> str:
@@ -453,7 +454,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if (args.form == "plain" or f64) else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": ("f64" if args.form == "plain" else ("int64" if f64 else "f32")),
         "data": "synthetic",
         "config": dict(cfg, form=args.form, arrays=labels, l2="inputs larger than L2 (no flush)",
                        parallelism=f"replicas{world}", launch_shapes=tuned or "default"),

@@ -235,9 +235,9 @@ CRM_DEV double logd_main(double x, bool &hard) {
 // r = m R_j 2^-9 - 1, exact as a 64-bit integer (m has 53 bits, R_j 10), |r| < 2^-8.
 //   log x = e ln 2 + L_j + log1p(r),  L_j = -log(R_j 2^-9)  (table, Q116),
 //   log1p(r) = r (1 + S'),  S' = -r/2 + r^2 U(r),  U = 1/3 - r/4 + r^2/5 - ... (n <= 7),
-// U by Horner in Q63 with signed truncating products (error 2^-62.4, the omitted term
-// 2^-67.5), r^2 U and r/2 in Q127, so that log1p(r) is good to 2^-78 of itself however
-// small r is.  Z = log x in Q116; errors in units of 2^-116: e ln2 |e|/2, L_j 1/2,
+// U by Horner with signed truncating products, Q63 for the first four coefficients and Q31
+// for the rest (error 2^-61, the omitted term 2^-67.5), r^2 U and r/2 in Q127, so that
+// log1p(r) is good to 2^-77 of itself however small r is.  Z = log x in Q116; errors in units of 2^-116: e ln2 |e|/2, L_j 1/2,
 // products and shifts 4, log1p |r| 2^38: the bound used is 16 + |e| + |r| 2^40.  The
 // rounding to binary64 is decided unless the discarded part of |Z| is within that bound
 // of half an ulp: those lanes take the slow path.
@@ -285,12 +285,14 @@ CRM_DEV double logd_int(double x, const ulonglong2 *LT, const unsigned short *RT
   const uint64_t R = RT[j - 192];
   const int64_t r64 = (int64_t)(Mq * R - (1ull << 62)) * 4;  // r 2^64, exact
   const uint64_t ar = r64 < 0 ? 0ull - (uint64_t)r64 : (uint64_t)r64;
-  // U(r) in Q63
-  int64_t u = CRM_LOGI_C7;
-  u = CRM_LOGI_C6 + __mul64hi(r64, u);
-  u = CRM_LOGI_C5 + __mul64hi(r64, u);
-  u = CRM_LOGI_C4 + __mul64hi(r64, u);
-  u = CRM_LOGI_C3 + __mul64hi(r64, u);
+  // U(r) in Q63; its tail C4 + r (C5 + r (C6 + r C7)) enters with weight r^4 <= 2^-32 and
+  // is formed in Q31 (error 2^-29.4, i.e. 2^-61.4 in U)
+  const int32_t r32 = (int32_t)(r64 >> 32);
+  int32_t v = CRM_LOGI_C7_32;
+  v = CRM_LOGI_C6_32 + __mulhi(r32, v);
+  v = CRM_LOGI_C5_32 + __mulhi(r32, v);
+  v = CRM_LOGI_C4_32 + __mulhi(r32, v);
+  int64_t u = CRM_LOGI_C3 + __mul64hi(r64, (int64_t)v << 32);
   u = CRM_LOGI_C2 + __mul64hi(r64, u);
   u = CRM_LOGI_C1 + __mul64hi(r64, u);
   u = CRM_LOGI_C0 + __mul64hi(r64, u);

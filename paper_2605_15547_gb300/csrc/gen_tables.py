@@ -462,6 +462,10 @@ for n in range(8):
     with mp.workprec(400):
         N = int(mp.nint(mp.mpf((-1) ** n) / (n + 3) * mp.mpf(2) ** 63))
     emit(f"#define CRM_LOGI_C{n} ((int64_t){N}ll)  // (-1)^{n}/{n + 3} 2^63")
+for n in range(4, 8):
+    with mp.workprec(400):
+        N = int(mp.nint(mp.mpf((-1) ** n) / (n + 3) * mp.mpf(2) ** 31))
+    emit(f"#define CRM_LOGI_C{n}_32 ((int32_t){N})  // (-1)^{n}/{n + 3} 2^31")
 with mp.workprec(400):
     N = int(mp.nint(LN2 * mp.mpf(2) ** 116))
 emit(f"#define CRM_LOGI_LN2_LO 0x{N & 0xFFFFFFFFFFFFFFFF:016X}ull  // ln 2 2^116, low word")

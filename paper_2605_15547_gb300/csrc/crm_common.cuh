@@ -130,6 +130,12 @@ CRM_DEV Pair<float> df_mul_raw(Pair<float> a, Pair<float> b) {
   pl = fma_(a.lo, b.hi, pl);
   return {p, pl};
 }
+// Sum of float pairs when |a.hi| >= |b.hi| (or a.hi = 0): Fast2Sum on the leading words
+CRM_DEV Pair<float> df_add_ordered(Pair<float> a, Pair<float> b) {
+  Pair<float> s = fast_two_sum(a.hi, b.hi);
+  s.lo = s.lo + (a.lo + b.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
 // Sum of float pairs without ordering assumption
 CRM_DEV Pair<float> df_add(Pair<float> a, Pair<float> b) {
   Pair<float> s = two_sum(a.hi, b.hi);

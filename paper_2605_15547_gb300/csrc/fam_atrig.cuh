@@ -127,8 +127,10 @@ CRM_DEV Pair<float> atan_ratio_df(Pair<float> a, Pair<float> b, const float2 *AT
   al = al + (t.lo - s3l);
   al = fma_(w * u, fma_(u, -0x1.249250p-3f, 0x1.99999ap-3f), al);  // t^5 (1/5 - t^2/7)
   float2 A = AT[j];
-  Pair<float> r = df_add({A.x, A.y}, {ah, al});
-  if (sw) r = df_add({CRM_PIO2_F_HI, CRM_PIO2_F_LO}, -r);
+  // atan(j/16) >= atan(1/16) > |atan t| for j >= 1 (A = 0 for j = 0), and pi/2 > atan(a/b)
+  // for the swapped case: both sums are ordered (Fast2Sum)
+  Pair<float> r = df_add_ordered({A.x, A.y}, {ah, al});
+  if (sw) r = df_add_ordered({CRM_PIO2_F_HI, CRM_PIO2_F_LO}, -r);
   return r;
 }
 
@@ -165,7 +167,7 @@ template <int KIND> CRM_DEV float atrig_df(float x, const float2 *AT, bool &hard
     }
   }
   Pair<float> r = atan_ratio_df(a, b, AT);
-  if (KIND == AT_ACOS && flip) r = df_add({CRM_PI_F_HI, CRM_PI_F_LO}, -r);
+  if (KIND == AT_ACOS && flip) r = df_add_ordered({CRM_PI_F_HI, CRM_PI_F_LO}, -r);  // pi > r
   if (__builtin_expect(sp, 0)) {
     hard = false;
     return rsp;

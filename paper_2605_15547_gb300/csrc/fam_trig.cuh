@@ -216,14 +216,17 @@ template <int KIND> CRM_DEV TrigF trig_df_core(float x, const uint32_t *P, const
     // B = C cos t + (-S) sin t, A = S cos t + C sin t: one product pair with chosen factors
     const bool useB = (KIND == TRIG_SIN) == ((R.q & 1) != 0);
     const Pair<float> Pf = useB ? C : S, Qf = useB ? -S : C;
-    R.A = df_add(df_mul_raw(Pf, ct), df_mul_raw(Qf, st));
+    R.A = df_add_ordered(df_mul_raw(Pf, ct), df_mul_raw(Qf, st));
     R.B = R.A;
     return R;
   }
+  // In both sums the first term dominates: |S_j cos t| >= sin(pi/64) cos(pi/128) > 0.049
+  // > |C_j sin t| when j >= 1 (S_0 = 0 makes the sum exact), and |C_j cos t| > 0.049 >
+  // |S_j sin t| for j <= 31: Fast2Sum applies.
   Pair<float> a1 = df_mul_raw(S, ct), a2 = df_mul_raw(C, st);
   Pair<float> b1 = df_mul_raw(C, ct), b2 = df_mul_raw(S, st);
-  R.A = df_add(a1, a2);
-  R.B = df_add(b1, -b2);
+  R.A = df_add_ordered(a1, a2);
+  R.B = df_add_ordered(b1, -b2);
   return R;
 }
 

@@ -11,8 +11,6 @@
 #include "crm_batch.h"
 #include "crm_fns.cuh"
 
-#define CRM_HOST_ONLY
-
 namespace crm {
 
 constexpr int BATCH_SMEM = 97 * 16;  // largest table (log family)
@@ -258,7 +256,7 @@ struct GroupLaunch {
   const BatchArgs *b;
   int grid;
   cudaStream_t s;
-  template <class Fn> CRM_HOST_ONLY void run() {
+  template <class Fn> void run() {
     if (form == 1)
       k_batch_group<Fn, 1><<<grid, KBLOCK, 0, s>>>(*b);
     else
@@ -268,7 +266,7 @@ struct GroupLaunch {
 struct GroupSymbol {
   int form;
   const void *sym;
-  template <class Fn> CRM_HOST_ONLY void run() {
+  template <class Fn> void run() {
     sym = form == 1 ? (const void *)k_batch_group<Fn, 1> : (const void *)k_batch_group<Fn, 2>;
   }
 };

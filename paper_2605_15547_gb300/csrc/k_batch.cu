@@ -40,13 +40,20 @@ CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t
     const V *in4 = (const V *)(in + off);
     V *out4 = (V *)(out + off);
     V *out4b = (V *)(out + d.n + off);
-    // two vectors per thread per iteration: both loads are in flight before the work
+    // two vectors per thread per iteration, and the next iteration's two loaded before
+    // this one is evaluated (register prefetch)
+    V nx[2];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      uint64_t v = (uint64_t)u * KBLOCK + threadIdx.x;
+      nx[u] = v < nv ? ld_stream(in4 + v) : V();
+    }
     for (uint64_t base = 0; base < nv; base += 2 * KBLOCK) {
-      V xv[2];
+      V xv[2] = {nx[0], nx[1]};
 #pragma unroll
       for (int u = 0; u < 2; u++) {
-        uint64_t v = base + (uint64_t)u * KBLOCK + threadIdx.x;
-        xv[u] = v < nv ? ld_stream(in4 + v) : V();
+        uint64_t v = base + 2 * KBLOCK + (uint64_t)u * KBLOCK + threadIdx.x;
+        nx[u] = v < nv ? ld_stream(in4 + v) : V();
       }
 #pragma unroll
       for (int u = 0; u < 2; u++) {

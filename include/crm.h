@@ -150,12 +150,16 @@ int crm_get_variant(int func_id, int form, int *variant);
    n elements; `reps` timed calls each after one untimed call, CUDA events on `stream`),
    keep the fastest for later calls, and return it in *best; ms (host, CRM_NUM_VARIANTS
    floats, may be NULL) receives each variant's time per call, -1 where unavailable.
-   Overwrites out.  Synchronizes `stream`; CRM_ERR_CAPTURE while the stream is captured. */
+   Overwrites out.  Synchronizes `stream`; CRM_ERR_CAPTURE while the stream is captured.
+   The choice is process-wide (all threads, all devices). */
 int crm_autotune(int func_id, int dtype, int form, const void *in, void *out, uint64_t n, int reps,
                  void *stream, int *best, float *ms);
 /* Same for the batching form: times both batch modes (crm_set_batch_mode) with tile sizes
    2^CRM_BATCH_TILE_MIN .. 2^CRM_BATCH_TILE_MAX on the given batch and keeps the fastest pair
-   (ms: host, 2 x 7 floats indexed [mode][log2 tile - CRM_BATCH_TILE_MIN], may be NULL). */
+   (ms: host, 2 x 7 floats indexed [mode][log2 tile - CRM_BATCH_TILE_MIN], may be NULL).
+   While it runs, the process-wide batch mode and tile size take the candidate values, so
+   batches launched meanwhile from other threads use them too (every mode and tile size
+   computes the same bits). */
 #define CRM_BATCH_TILE_MIN 10
 #define CRM_BATCH_TILE_MAX 16
 int crm_autotune_batch(const crm_desc_t *descs, int count, int form, int reps, void *stream, int *best_mode,

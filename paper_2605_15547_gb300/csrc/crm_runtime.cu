@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -20,8 +21,10 @@ namespace crm {
 
 static FuncEntry g_table[CRM_NUM_FUNCS];
 static std::once_flag g_init_once;
-static int g_default_form = CRM_FORM_AUTO;
-static int g_force_slow = 0;
+// Process-wide settings: plain atomics, so that a setter racing with calls on other
+// threads is well defined (a call sees either the old or the new value).
+static std::atomic<int> g_default_form{CRM_FORM_AUTO};
+static std::atomic<int> g_force_slow{0};
 static thread_local int g_last_cuda = 0;
 
 static void init_table() {
@@ -150,7 +153,7 @@ static int blocks_per_sm(const void *sym, int block) {
 
 // Launch shape per (function, form): the default, the env CRM_VARIANT, crm_set_variant
 // or the autotuner's choice.  A shape the form does not provide falls back to the default.
-static int g_variant[CRM_NUM_FUNCS][3];
+static std::atomic<int> g_variant[CRM_NUM_FUNCS][3];
 static std::once_flag g_variant_once;
 
 static void variant_init() {
@@ -269,8 +272,8 @@ static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cu
 }
 
 // ------------------------------------------------------------------ batch buffers
-static int g_batch_tile_shift = 14;  // the autotuner may change it (crm_set_batch_tile)
-static int g_batch_mode = CRM_BATCH_GROUPED;  // crm_set_batch_mode / the autotuner
+static std::atomic<int> g_batch_tile_shift{14};  // the autotuner may change it (crm_set_batch_tile)
+static std::atomic<int> g_batch_mode{CRM_BATCH_GROUPED};  // crm_set_batch_mode / the autotuner
 
 static int batch_buffers(cudaStream_t s, Workspace *w, int count) {
   if (w->bcap >= count) return CRM_OK;

@@ -148,11 +148,12 @@ template <int KIND> CRM_DEV float log_df(float x, const float4 *T97, bool &hard)
   uh = ok ? uh : 1.0f;
   bool sub = uh < 0x1p-126f;
   float us = sub ? uh * 0x1p24f : uh;
-  uint32_t b = fbits(us);
-  uint32_t mant = b & 0x007FFFFFu;
-  bool big = mant >= 0x00400000u;
-  float m = bitsf(mant | (big ? 0x3F000000u : 0x3F800000u));
-  int e = (int)(b >> 23) - 127 + (big ? 1 : 0) - (sub ? 24 : 0);
+  // us = 2^e m, m in [3/4, 3/2), from one integer subtraction: the exponent field of
+  // us / (3/4) rounded down is floor(log2(us / (3/4)))
+  const uint32_t b = fbits(us);
+  const int32_t ee = (int32_t)(b - 0x3F400000u) >> 23;
+  float m = bitsf(b - ((uint32_t)ee << 23));
+  int e = ee - (sub ? 24 : 0);
   float sh = fma_(m, 128.0f, CRM_SHIFTER_F);
   int j = (int)(fbits(sh) - fbits(CRM_SHIFTER_F));
   float c = (sh - CRM_SHIFTER_F) * 0.0078125f;

@@ -419,8 +419,8 @@ __global__ void __launch_bounds__(KBLOCK) k_pipe(KArgs a) {
 
 // Calls f(entry) for every queued entry: the sub-queues are spread over the grid
 // (virtual blocks: sub-queue = vb % nsubq, part = vb / nsubq), and each sub-queue's
-// entries below its count are taken by its blocks in turn.  Block 0's thread 0 then adds
-// the call's total to hard_total and records it as the last count.
+// entries below its count are taken by its blocks in turn.  Block 0's first warp then
+// adds the call's total to hard_total and records it as the last count.
 template <class F>
 CRM_DEV void for_each_queued(const crm_queue_entry *q, unsigned long long *qcount, int nsubq, uint64_t cap,
                              crm_ws_header *hdr, F f) {
@@ -433,11 +433,17 @@ CRM_DEV void for_each_queued(const crm_queue_entry *q, unsigned long long *qcoun
     for (uint64_t i = (uint64_t)part * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)parts * blockDim.x)
       f(q[sq * subcap + i]);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    // the first warp sums the counters (independent loads, then a shuffle reduction:
+    // a serial loop would wait for one L2 round trip per counter)
     unsigned long long total = 0;
-    for (int sq = 0; sq < nsubq; sq++) total += qcount[sq * CRM_SUBQ_STRIDE];
-    atomicAdd(&hdr->hard_total, total);
-    hdr->count = total;
+    for (int sq = (int)threadIdx.x; sq < nsubq; sq += 32) total += qcount[sq * CRM_SUBQ_STRIDE];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xFFFFFFFFu, total, o);
+    if (threadIdx.x == 0) {
+      atomicAdd(&hdr->hard_total, total);
+      hdr->count = total;
+    }
   }
 }
 

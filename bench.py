@@ -367,7 +367,8 @@ def main():
             info = crm.variant_info(best)
             tuned[lab] = ("pipelined" if info["pipelined"] else
                           f"u{info['unroll']}b{info['block']}" + ("pf" if info["prefetch"] else "") +
-                          (f"m{info['min_blocks']}" if info["min_blocks"] > 1 else ""))
+                          (f"m{info['min_blocks']}" if info["min_blocks"] > 1 else "") +
+                          ("w32" if info["vec_bytes"] == 32 else ""))
 
     for _ in range(args.warmup):
         step(args.form)

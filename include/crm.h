@@ -135,13 +135,15 @@ int crm_set_batch_mode(int mode);
 /* ---- launch shapes and the autotuner (the paper has no counterpart: its SIMD kernels
    have one shape; on the GPU the best elements-per-thread, block size and load schedule
    depend on the function and the form).  A variant is one launch shape of the main
-   kernel: vectors per thread per iteration (unroll; 4 binary32 or 2 binary64 elements per
-   128-bit vector), threads per block, register prefetch of the next iteration, a minimum
-   of resident blocks per SM (a register cap), or the shared-memory pipelined kernel (bulk
-   asynchronous copies).  Every variant computes the same bits.  Output pointers may be
+   kernel: vectors per thread per iteration (unroll), the vector width (vec_bytes 16 or 32:
+   4 or 8 binary32 elements, 2 or 4 binary64 ones per access; a 32-byte shape falls back to
+   the default shape when in and out are not 32-byte congruent), threads per block,
+   register prefetch of the next iteration, a minimum of resident blocks per SM (a
+   register cap), or the shared-memory pipelined kernel (bulk asynchronous copies).  Every variant computes the same bits.  Output pointers may be
    NULL. */
-#define CRM_NUM_VARIANTS 8
-int crm_variant_info(int variant, int *unroll, int *block, int *prefetch, int *pipelined, int *min_blocks);
+#define CRM_NUM_VARIANTS 10
+int crm_variant_info(int variant, int *unroll, int *block, int *prefetch, int *pipelined, int *min_blocks,
+                     int *vec_bytes);
 /* Choose the variant of (func_id, form) for all later calls.  CRM_ERR_ARG if the form does
    not provide it (the plain FP64 form provides only the default shape). */
 int crm_set_variant(int func_id, int form, int variant);

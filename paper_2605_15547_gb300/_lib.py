@@ -22,7 +22,7 @@ FUNC_ID = {n: i for i, n in enumerate(FUNCS)}
 F64_FUNCS = {"exp2", "log"}
 FORMS = {"auto": 0, "plain": 1, "df": 2}
 CRM_F32, CRM_F64 = 0, 1
-NUM_VARIANTS = 8
+NUM_VARIANTS = 10
 BATCH_TILE_MIN, BATCH_TILE_MAX = 10, 16
 
 
@@ -68,7 +68,7 @@ def _lib():
                 lib.crm_eval_noalloc.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, vp]
                 lib.crm_reserve.argtypes = [c_u64, c_int, vp]
                 pi, pf = ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float)
-                lib.crm_variant_info.argtypes = [c_int, pi, pi, pi, pi, pi]
+                lib.crm_variant_info.argtypes = [c_int, pi, pi, pi, pi, pi, pi]
                 lib.crm_set_variant.argtypes = [c_int, c_int, c_int]
                 lib.crm_get_variant.argtypes = [c_int, c_int, pi]
                 lib.crm_autotune.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, c_int, vp, pi, pf]

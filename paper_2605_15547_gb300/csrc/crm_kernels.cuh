@@ -34,9 +34,50 @@ struct KArgs {
   uint32_t desc;     // array id recorded in queue entries (batch form)
 };
 
-template <class T> struct VecOf;
-template <> struct VecOf<float> { using V = float4; static constexpr int W = 4; };
-template <> struct VecOf<double> { using V = double2; static constexpr int W = 2; };
+// 32-byte vectors (one 256-bit access per thread: ld/st.global.v8.f32, .v4.f64)
+struct alignas(32) float8v {
+  float v[8];
+};
+struct alignas(32) double4v {
+  double v[4];
+};
+
+// The vector a thread moves per access: 16 bytes, or 32 bytes when WIDE.
+template <class T, bool WIDE = false> struct VecOf;
+template <> struct VecOf<float, false> { using V = float4; static constexpr int W = 4; };
+template <> struct VecOf<double, false> { using V = double2; static constexpr int W = 2; };
+template <> struct VecOf<float, true> { using V = float8v; static constexpr int W = 8; };
+template <> struct VecOf<double, true> { using V = double4v; static constexpr int W = 4; };
+
+CRM_DEV float8v ld_stream(const float8v *p) {
+  float8v r;
+  asm volatile("ld.global.cs.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]),
+                 "=f"(r.v[6]), "=f"(r.v[7])
+               : "l"(p));
+  return r;
+}
+CRM_DEV void st_stream(float8v *p, const float8v &a) {
+  asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a.v[0]), "f"(a.v[1]),
+               "f"(a.v[2]), "f"(a.v[3]), "f"(a.v[4]), "f"(a.v[5]), "f"(a.v[6]), "f"(a.v[7])
+               : "memory");
+}
+CRM_DEV double4v ld_stream(const double4v *p) {
+  double4v r;
+  asm volatile("ld.global.cs.v4.f64 {%0, %1, %2, %3}, [%4];"
+               : "=d"(r.v[0]), "=d"(r.v[1]), "=d"(r.v[2]), "=d"(r.v[3])
+               : "l"(p));
+  return r;
+}
+CRM_DEV void st_stream(double4v *p, const double4v &a) {
+  asm volatile("st.global.cs.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(a.v[0]), "d"(a.v[1]), "d"(a.v[2]),
+               "d"(a.v[3])
+               : "memory");
+}
+CRM_DEV float vget(const float8v &a, int j) { return a.v[j]; }
+CRM_DEV double vget(const double4v &a, int j) { return a.v[j]; }
+CRM_DEV void vset(float8v &a, int j, float x) { a.v[j] = x; }
+CRM_DEV void vset(double4v &a, int j, double x) { a.v[j] = x; }
 
 CRM_DEV float4 ld_stream(const float4 *p) { return __ldcs(p); }
 CRM_DEV double2 ld_stream(const double2 *p) { return __ldcs(p); }
@@ -125,12 +166,10 @@ __device__ __noinline__ void slow_store(typename Fn::T x, uint64_t i, const KArg
 }
 
 // Evaluates the W elements of one vector: y0 (and y1 for two outputs) and the hard bits.
-template <class Fn, int FORM>
-CRM_DEV void eval_vec(const typename VecOf<typename Fn::T>::V &xv, const void *sm,
-                      typename VecOf<typename Fn::T>::V &y0, typename VecOf<typename Fn::T>::V &y1,
-                      unsigned &hm) {
+template <class Fn, int FORM, class V>
+CRM_DEV void eval_vec(const V &xv, const void *sm, V &y0, V &y1, unsigned &hm) {
   using T = typename Fn::T;
-  constexpr int W = VecOf<T>::W;
+  constexpr int W = sizeof(V) / sizeof(T);
   hm = 0;
 #pragma unroll
   for (int j = 0; j < W; j++) {
@@ -154,12 +193,12 @@ CRM_DEV void load_vecs(V *xv, const V *in4, uint64_t base, uint64_t nvec) {
 }
 
 // Evaluates and stores the UNROLL vectors of one iteration, queueing the hard lanes.
-template <class Fn, int FORM, int UNROLL, int BS>
-CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T>::V *xv, uint64_t base, const unsigned char *sm,
+template <class Fn, int FORM, int UNROLL, int BS, bool WIDE>
+CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T, WIDE>::V *xv, uint64_t base, const unsigned char *sm,
                        const KArgs &a) {
   using T = typename Fn::T;
-  using V = typename VecOf<T>::V;
-  constexpr int W = VecOf<T>::W;
+  using V = typename VecOf<T, WIDE>::V;
+  constexpr int W = VecOf<T, WIDE>::W;
   V *out4 = (V *)((T *)a.out + a.head);
   V *out4b = (V *)((T *)a.out + a.n + a.head);  // second output (sincos)
 #pragma unroll
@@ -196,11 +235,11 @@ CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T>::V *xv, uint64_t bas
 // iteration's vectors are loaded
 // before this iteration is evaluated (software prefetch: the loads' latency overlaps the
 // thread's own arithmetic).
-template <class Fn, int FORM, int UNROLL, int BS, bool PF>
+template <class Fn, int FORM, int UNROLL, int BS, bool PF, bool WIDE>
 CRM_DEV void main_body(const KArgs &a) {
   using T = typename Fn::T;
-  using V = typename VecOf<T>::V;
-  constexpr int W = VecOf<T>::W;
+  using V = typename VecOf<T, WIDE>::V;
+  constexpr int W = VecOf<T, WIDE>::W;
   __shared__ __align__(16) unsigned char sm[(Fn::template tab_bytes<FORM>() > 0) ? Fn::template tab_bytes<FORM>() : 16];
   load_tab<Fn, FORM>(sm);
 
@@ -213,7 +252,7 @@ CRM_DEV void main_body(const KArgs &a) {
     for (; base < a.nvec; base += stride) {
       V nx[UNROLL];
       load_vecs<V, UNROLL, BS>(nx, in4, base + stride, a.nvec);
-      eval_vecs<Fn, FORM, UNROLL, BS>(xv, base, sm, a);
+      eval_vecs<Fn, FORM, UNROLL, BS, WIDE>(xv, base, sm, a);
 #pragma unroll
       for (int u = 0; u < UNROLL; u++) xv[u] = nx[u];
     }
@@ -221,7 +260,7 @@ CRM_DEV void main_body(const KArgs &a) {
     for (; base < a.nvec; base += stride) {
       V xv[UNROLL];
       load_vecs<V, UNROLL, BS>(xv, in4, base, a.nvec);
-      eval_vecs<Fn, FORM, UNROLL, BS>(xv, base, sm, a);
+      eval_vecs<Fn, FORM, UNROLL, BS, WIDE>(xv, base, sm, a);
     }
   }
   // scalar part: the head [0, head) and the tail [head + W nvec, n)
@@ -250,14 +289,14 @@ CRM_DEV void main_body(const KArgs &a) {
   }
 }
 
-template <class Fn, int FORM, int UNROLL, int BS, bool PF>
+template <class Fn, int FORM, int UNROLL, int BS, bool PF, bool WIDE = false>
 __global__ void __launch_bounds__(BS) k_main(KArgs a) {
-  main_body<Fn, FORM, UNROLL, BS, PF>(a);
+  main_body<Fn, FORM, UNROLL, BS, PF, WIDE>(a);
 }
 // The same with a register cap: at least MINB blocks of BS threads resident per SM.
 template <class Fn, int FORM, int UNROLL, int BS, bool PF, int MINB>
 __global__ void __launch_bounds__(BS, MINB) k_main_capped(KArgs a) {
-  main_body<Fn, FORM, UNROLL, BS, PF>(a);
+  main_body<Fn, FORM, UNROLL, BS, PF, false>(a);
 }
 
 // ------------------------------------------------------------------ pipelined variant

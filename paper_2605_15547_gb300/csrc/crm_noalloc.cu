@@ -80,7 +80,11 @@ extern "C" int crm_eval_noalloc(int func_id, int dtype, int form, const void *in
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
   KArgs a;
-  fill_geometry(fe, in, out, n, a);
+  int vi = variant_of(func_id, fm);
+  if (!fill_geometry(fe, in, out, n, a, VARIANTS[vi].vec_bytes) && VARIANTS[vi].vec_bytes != 16) {
+    vi = DEFAULT_VARIANT;
+    fill_geometry(fe, in, out, n, a, 16);
+  }
   a.hdr = (crm_ws_header *)d->scratch;
   a.q = (crm_queue_entry *)(d->scratch + kNoAllocHeader);
   a.cap = kNoAllocMaxElems;
@@ -88,7 +92,6 @@ extern "C" int crm_eval_noalloc(int func_id, int dtype, int form, const void *in
   a.nsubq = 1;
   a.force_hard = force_slow_flag();
   a.desc = 0;
-  int vi = variant_of(func_id, fm);
   int bps = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fe.main_sym[fm][vi], VARIANTS[vi].block, 0);
   if (e != cudaSuccess) return cuda_fail_code(e);

@@ -10,15 +10,17 @@ typedef cudaError_t (*launch_fn)(const KArgs &, int grid, cudaStream_t);
 typedef int (*occ_fn)(void);
 
 // Launch shapes of the main kernel that the autotuner chooses among: vectors per thread
-// per iteration (elements per thread = 4 x unroll for binary32), threads per block,
-// register prefetch of the next iteration, or the shared-memory pipelined kernel.
+// per iteration, threads per block, register prefetch of the next iteration, a register
+// cap (minimum resident blocks), the vector width (16- or 32-byte accesses: 4 or 8
+// binary32 elements), or the shared-memory pipelined kernel.
 struct VariantInfo {
-  int unroll, block, prefetch, pipelined, min_blocks;
+  int unroll, block, prefetch, pipelined, min_blocks, vec_bytes;
 };
-enum { NVARIANT = 8, DEFAULT_VARIANT = 1 };
+enum { NVARIANT = 10, DEFAULT_VARIANT = 1 };
 constexpr VariantInfo VARIANTS[NVARIANT] = {
-    {1, 256, 0, 0, 1}, {2, 256, 0, 0, 1}, {4, 256, 0, 0, 1}, {PVPT, KBLOCK, 0, 1, 1},
-    {2, 256, 1, 0, 4}, {1, 256, 1, 0, 1}, {2, 128, 1, 0, 1}, {2, 512, 1, 0, 1}};
+    {1, 256, 0, 0, 1, 16}, {2, 256, 0, 0, 1, 16}, {4, 256, 0, 0, 1, 16}, {PVPT, KBLOCK, 0, 1, 1, 16},
+    {2, 256, 1, 0, 4, 16}, {1, 256, 1, 0, 1, 16}, {2, 128, 1, 0, 1, 16}, {2, 512, 1, 0, 1, 16},
+    {1, 256, 1, 0, 1, 32}, {1, 512, 1, 0, 1, 32}};
 
 struct FuncEntry {
   launch_fn main[3][NVARIANT];  // [form][variant]; form 0 unused; null when unavailable
@@ -28,9 +30,9 @@ struct FuncEntry {
   int dtype;  // 0 binary32, 1 binary64
 };
 
-template <class Fn, int FORM, int U, int BS, bool PF>
+template <class Fn, int FORM, int U, int BS, bool PF, bool WIDE>
 cudaError_t launch_main(const KArgs &a, int grid, cudaStream_t s) {
-  k_main<Fn, FORM, U, BS, PF><<<grid, BS, 0, s>>>(a);
+  k_main<Fn, FORM, U, BS, PF, WIDE><<<grid, BS, 0, s>>>(a);
   return cudaGetLastError();
 }
 template <class Fn, int FORM, int U, int BS, bool PF, int MINB>
@@ -60,8 +62,8 @@ void set_variant(FuncEntry &e) {
     e.main[FORM][V] = launch_main_capped<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.min_blocks>;
     e.main_sym[FORM][V] = (const void *)k_main_capped<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.min_blocks>;
   } else {
-    e.main[FORM][V] = launch_main<Fn, FORM, I.unroll, I.block, (bool)I.prefetch>;
-    e.main_sym[FORM][V] = (const void *)k_main<Fn, FORM, I.unroll, I.block, (bool)I.prefetch>;
+    e.main[FORM][V] = launch_main<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.vec_bytes == 32>;
+    e.main_sym[FORM][V] = (const void *)k_main<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.vec_bytes == 32>;
   }
 }
 
@@ -78,6 +80,8 @@ void set_form(FuncEntry &e) {
     set_variant<Fn, FORM, 5>(e);
     set_variant<Fn, FORM, 6>(e);
     set_variant<Fn, FORM, 7>(e);
+    set_variant<Fn, FORM, 8>(e);
+    set_variant<Fn, FORM, 9>(e);
   }
 }
 

@@ -205,16 +205,16 @@ int check_args(int func, int dtype, const void *in, void *out, uint64_t n) {
 
 // Vector geometry: the vector loop needs input and output(s) at the same offset modulo
 // 16 bytes; the scalar loop covers the unaligned head and the tail.
-void fill_geometry(const FuncEntry &fe, const void *in, void *out, uint64_t n, KArgs &a) {
+bool fill_geometry(const FuncEntry &fe, const void *in, void *out, uint64_t n, KArgs &a, int vb) {
   const size_t es = fe.dtype ? 8 : 4;
-  const int W = fe.dtype ? 2 : 4;
+  const int W = vb / (int)es;
   a.in = in;
   a.out = out;
   a.n = n;
   uintptr_t ia = (uintptr_t)in, oa = (uintptr_t)out;
-  bool vec = ((ia - oa) % 16) == 0 && (fe.nout == 1 || (n * es) % 16 == 0);
+  bool vec = ((ia - oa) % vb) == 0 && (fe.nout == 1 || (n * es) % vb == 0);
   if (vec) {
-    uint64_t head = ((16 - ia % 16) % 16) / es;
+    uint64_t head = ((vb - ia % vb) % vb) / es;
     if (head > n) head = n;
     a.head = head;
     a.nvec = (n - head) / W;
@@ -222,12 +222,13 @@ void fill_geometry(const FuncEntry &fe, const void *in, void *out, uint64_t n, K
     a.head = 0;
     a.nvec = 0;
   }
+  return vec;
 }
 
 // Grid of the main kernel: enough blocks for the work, at most one full wave of
 // resident blocks (the kernel loops over the rest).
 int main_grid(const FuncEntry &fe, const KArgs &a, int vi, int sms, int bps) {
-  const int W = fe.dtype ? 2 : 4;
+  const int W = VARIANTS[vi].vec_bytes / (fe.dtype ? 8 : 4);
   const uint64_t U = (uint64_t)VARIANTS[vi].unroll, B = (uint64_t)VARIANTS[vi].block;
   uint64_t want = (a.nvec + B * U - 1) / (B * U);
   uint64_t nscal = a.head + (a.n - a.head - (uint64_t)W * a.nvec);
@@ -251,7 +252,12 @@ static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cu
   int st = get_ws(s, kDefaultCap, &w);
   if (st) return st;
   KArgs a;
-  fill_geometry(fe, in, out, n, a);
+  int vi = variant >= 0 ? variant : variant_of(func, fm);
+  // a 32-byte shape needs in and out 32-byte congruent; else the default 16-byte shape
+  if (!fill_geometry(fe, in, out, n, a, VARIANTS[vi].vec_bytes) && VARIANTS[vi].vec_bytes != 16) {
+    vi = DEFAULT_VARIANT;
+    fill_geometry(fe, in, out, n, a, 16);
+  }
   a.hdr = w->hdr;
   a.q = w->q;
   a.cap = w->cap;
@@ -259,7 +265,6 @@ static int enqueue(int func, int form, const void *in, void *out, uint64_t n, cu
   a.nsubq = CRM_NSUBQ;
   a.force_hard = g_force_slow;
   a.desc = desc;
-  int vi = variant >= 0 ? variant : variant_of(func, fm);
   int sms = dev_sms();
   int grid = main_grid(fe, a, vi, sms, main_blocks_per_sm(fe, fm, vi));
   cudaError_t e = cudaMemsetAsync(a.qcount, 0, CRM_NSUBQ * CRM_SUBQ_STRIDE * 8, s);
@@ -598,13 +603,15 @@ int crm_set_batch_tile(int log2_elems) {
   return CRM_OK;
 }
 
-int crm_variant_info(int variant, int *unroll, int *block, int *prefetch, int *pipelined, int *min_blocks) {
+int crm_variant_info(int variant, int *unroll, int *block, int *prefetch, int *pipelined, int *min_blocks,
+                     int *vec_bytes) {
   if (variant < 0 || variant >= NVARIANT) return CRM_ERR_ARG;
   if (unroll) *unroll = VARIANTS[variant].unroll;
   if (block) *block = VARIANTS[variant].block;
   if (prefetch) *prefetch = VARIANTS[variant].prefetch;
   if (pipelined) *pipelined = VARIANTS[variant].pipelined;
   if (min_blocks) *min_blocks = VARIANTS[variant].min_blocks;
+  if (vec_bytes) *vec_bytes = VARIANTS[variant].vec_bytes;
   return CRM_OK;
 }
 

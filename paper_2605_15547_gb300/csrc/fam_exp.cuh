@@ -113,7 +113,11 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
     tl = fma_(x, K::F1, tl);
   }
   float sh = fma_(th, 64.0f, CRM_SHIFTER_F);
-  int N = (int)(fbits(sh) - fbits(CRM_SHIFTER_F));
+  // N = rint(64 t) sits in the low bits of sh's pattern, whose other bits (0x4B400000) are
+  // 0 modulo 64 and vanish when shifted left by 17: the table index is the pattern's low 6
+  // bits and the exponent increment (N >> 6) << 23 is the pattern shifted left by 17 with
+  // the low 23 bits cleared
+  const uint32_t sb = fbits(sh);
   float nf = sh - CRM_SHIFTER_F;
   float f = fma_(nf, -0.015625f, th);
   float gh, gl;
@@ -124,7 +128,7 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
     gh = f + tl;
     gl = tl - (gh - f);
   }
-  float4 T = T64U[N & 63];
+  float4 T = T64U[sb & 63u];
   float q = fma_(gh, CRM_EXP2_A4_F, CRM_EXP2_A3_F);
   q = fma_(gh, q, CRM_EXP2_A2_F);
   float Q = (gh * gh) * q;
@@ -139,7 +143,7 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
   r = r + z;
   float s2 = s + r;
   float l2 = r - (s2 - s);
-  float y = bitsf(fbits(s2) + ((uint32_t)(N >> 6) << 23));
+  float y = bitsf(fbits(s2) + ((sb << 17) & 0xFF800000u));
   const bool ok = (x >= K::XSUB) && (x <= K::XOVF);  // false for NaN
   if (__builtin_expect(ok, 1)) {
     hard = hard_df(s2, l2);
@@ -154,6 +158,7 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
     // d = (u_hi - q) + u_lo, the nearest integer is q, q + 1 (d > 1/2) or q - 1
     // (d < -1/2); the pair's error (2^-37 of u < 2^-13) and d's rounding (2^-24) can move
     // u across a half-integer only when ||d| - 1/2| <= 2^-12: those lanes go slow.
+    const int N = (int)(sb - fbits(CRM_SHIFTER_F));
     const float sc = bitsf((uint32_t)((N >> 6) + 149 + 127) << 23);
     const float uh = s2 * sc, ul = l2 * sc;
     const float q = rintf(uh);

@@ -4,7 +4,7 @@ over all 2^32 binary32 inputs (digest definition in tests/exhaustive_hash.py).
 Calls only the oracle.  Resumable: chunks already present in a file are skipped, and each
 chunk is appended as soon as it is done, so a partial file lists the chunks covered so far.
 
-    python tests/golden/make_exhaustive.py [--threads T] func [func ...]
+    python tests/golden/make_exhaustive.py [--threads T] [--out-dir D] func [func ...]
 """
 from __future__ import annotations
 
@@ -28,13 +28,14 @@ def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("funcs", nargs="+")
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--out-dir", default=OUT_DIR, help="where the files go (default: next to this script)")
     args = ap.parse_args()
-    os.makedirs(OUT_DIR, exist_ok=True)
+    os.makedirs(args.out_dir, exist_ok=True)
     w1, w2 = EH.weights()
     for f in args.funcs:
         if f not in O.FUNCS[:19] or f == "sincosf":
             raise SystemExit(f"{f}: not a single-output binary32 function")
-        path = os.path.join(OUT_DIR, f + ".txt")
+        path = os.path.join(args.out_dir, f + ".txt")
         done = EH.read_fixture(path) if os.path.exists(path) else {}
         if not os.path.exists(path):
             with open(path, "w") as fh:

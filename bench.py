@@ -330,11 +330,11 @@ def main():
     import paper_2605_15547_gb300 as crm
 
     rank, world, local = dist_env()
+    torch.cuda.set_device(local)  # before the process group, so NCCL binds this rank's GPU
+    dev = torch.device("cuda", local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     import __graft_entry__ as g
     g.build()
     stream = torch.cuda.current_stream()

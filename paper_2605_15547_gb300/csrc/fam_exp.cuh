@@ -101,7 +101,9 @@ template <int KIND> CRM_DEV float exp_plain(float x, const double *T16, bool &ha
 // Inputs outside [X_SUB, X_OVF] are resolved by selects: +inf above X_OVF, +0 below
 // X_ZERO, a quiet NaN for NaN; results in the subnormal band [X_ZERO, X_SUB) are rounded
 // to the subnormal grid from the same pair (below).
-template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard) {
+// b^x = 2^k (s2 + l2), the pair normalised and good to 2^-37.7 of itself (budget above);
+// sb is the shifter's bit pattern (k and the table index are read from it).
+template <int KIND> CRM_DEV void exp_df_core(float x, const float4 *T64U, float &s2, float &l2, uint32_t &sb) {
   using K = ExpK<KIND>;
   float th, tl;
   if (KIND == 1) {
@@ -117,7 +119,7 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
   // 0 modulo 64 and vanish when shifted left by 17: the table index is the pattern's low 6
   // bits and the exponent increment (N >> 6) << 23 is the pattern shifted left by 17 with
   // the low 23 bits cleared
-  const uint32_t sb = fbits(sh);
+  sb = fbits(sh);
   float nf = sh - CRM_SHIFTER_F;
   float f = fma_(nf, -0.015625f, th);
   float gh, gl;
@@ -141,8 +143,15 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
   r = fma_(T.x, Q, r);
   r = r + ml;
   r = r + z;
-  float s2 = s + r;
-  float l2 = r - (s2 - s);
+  s2 = s + r;
+  l2 = r - (s2 - s);
+}
+
+template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard) {
+  using K = ExpK<KIND>;
+  float s2, l2;
+  uint32_t sb;
+  exp_df_core<KIND>(x, T64U, s2, l2, sb);
   float y = bitsf(fbits(s2) + ((sb << 17) & 0xFF800000u));
   const bool ok = (x >= K::XSUB) && (x <= K::XOVF);  // false for NaN
   if (__builtin_expect(ok, 1)) {

@@ -178,9 +178,27 @@ template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard) {
   }
   float arg = H == HYP_EXPM1 ? x : (H == HYP_TANH ? 2.0f * ax : ax);
   arg = sp ? 0.5f : arg;
-  DFY Y = expm1_df_core(arg, T64U);
   Pair<float> r;
   int sc = 0;
+  if (H == HYP_COSH) {
+    // cosh a = (e^a + e^-a)/2 never cancels, so the exp core suffices (no expm1 care):
+    // e^a = 2^k P with P to 2^-37.7 (exp_df_core), R = 2^-k / P by a pair division, and
+    // cosh a = 2^(k-1) (P + 2^-k R): the two terms keep P's relative error, the division
+    // and the sums add 2^-43: below the 2^-37 of the rounding test.
+    float ph, pl;
+    uint32_t sb;
+    exp_df_core<0>(arg, T64U, ph, pl, sb);
+    const int k = (int)(sb - fbits(CRM_SHIFTER_F)) >> 6;
+    const Pair<float> P = {ph, pl};
+    const float pk = k > 100 ? 0.0f : pow2f_exact(-k);
+    Pair<float> R = df_div({pk, 0.0f}, P);
+    float rk = R.hi * pk, rkl = R.lo * pk;
+    Pair<float> S = fast_two_sum(P.hi, rk);
+    S.lo = S.lo + (P.lo + rkl);
+    r = fast_two_sum(S.hi, S.lo);
+    sc = k - 1;
+  } else {
+  DFY Y = expm1_df_core(arg, T64U);
   if (H == HYP_EXPM1) {
     r = {Y.s, Y.l};
     sc = Y.k;
@@ -194,19 +212,12 @@ template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard) {
     Pair<float> P = two_sum(Y.s, pk);  // P = 2^-k e^a
     P.lo = P.lo + Y.l;
     Pair<float> R = df_div({pk, 0.0f}, P);  // 2^-2k e^-a ... = 2^-k / P
-    if (H == HYP_SINH) {
-      // sinh a = 2^(k-1) Y (1 + R)
-      Pair<float> onep = fast_two_sum(1.0f, R.hi);  // 1 + R as a pair (R <= 1)
-      onep.lo = onep.lo + R.lo;
-      r = df_mul({Y.s, Y.l}, onep);
-    } else {
-      // cosh a = 2^(k-1) (P + 2^-k R)
-      float rk = R.hi * pk, rkl = R.lo * pk;
-      Pair<float> S = fast_two_sum(P.hi, rk);
-      S.lo = S.lo + (P.lo + rkl);
-      r = fast_two_sum(S.hi, S.lo);
-    }
+    // sinh a = 2^(k-1) Y (1 + R)
+    Pair<float> onep = fast_two_sum(1.0f, R.hi);  // 1 + R as a pair (R <= 1)
+    onep.lo = onep.lo + R.lo;
+    r = df_mul({Y.s, Y.l}, onep);
     sc = Y.k - 1;
+  }
   }
   if (__builtin_expect(!sp, 1)) {
     hard = hard_df(r.hi, r.lo);

@@ -103,7 +103,8 @@ CRM_DEV Pair<double> dd(double h, double l) { return {h, l}; }
 // ------------------------------------------------------------------ double-float helpers
 // Quotient of float pairs: q1 from the hardware reciprocal (relative error ~2^-22), the
 // residual a - q1 b with an exact product split, one correction: relative error < 2^-43.
-CRM_DEV Pair<float> df_div(Pair<float> a, Pair<float> b) {
+// df_div_raw leaves the quotient unnormalised (q1 + q2, |q2| < 2^-20 |q1|).
+CRM_DEV Pair<float> df_div_raw(Pair<float> a, Pair<float> b) {
   float r = __fdividef(1.0f, b.hi);
   float q1 = a.hi * r;
   float p = q1 * b.hi;
@@ -111,7 +112,11 @@ CRM_DEV Pair<float> df_div(Pair<float> a, Pair<float> b) {
   float rr = (a.hi - p) - pl;
   rr = rr + fma_(-q1, b.lo, a.lo);
   float q2 = rr * r;
-  return fast_two_sum(q1, q2);
+  return {q1, q2};
+}
+CRM_DEV Pair<float> df_div(Pair<float> a, Pair<float> b) {
+  Pair<float> q = df_div_raw(a, b);
+  return fast_two_sum(q.hi, q.lo);
 }
 // Product of float pairs (relative error < 2^-45)
 CRM_DEV Pair<float> df_mul(Pair<float> a, Pair<float> b) {
@@ -130,10 +135,15 @@ CRM_DEV Pair<float> df_mul_raw(Pair<float> a, Pair<float> b) {
   pl = fma_(a.lo, b.hi, pl);
   return {p, pl};
 }
-// Sum of float pairs when |a.hi| >= |b.hi| (or a.hi = 0): Fast2Sum on the leading words
-CRM_DEV Pair<float> df_add_ordered(Pair<float> a, Pair<float> b) {
+// Sum of float pairs when |a.hi| >= |b.hi| (or a.hi = 0): Fast2Sum on the leading words;
+// the _raw form leaves the sum unnormalised (for round_df)
+CRM_DEV Pair<float> df_add_ordered_raw(Pair<float> a, Pair<float> b) {
   Pair<float> s = fast_two_sum(a.hi, b.hi);
   s.lo = s.lo + (a.lo + b.lo);
+  return s;
+}
+CRM_DEV Pair<float> df_add_ordered(Pair<float> a, Pair<float> b) {
+  Pair<float> s = df_add_ordered_raw(a, b);
   return fast_two_sum(s.hi, s.lo);
 }
 // Sum of float pairs without ordering assumption
@@ -171,6 +181,22 @@ CRM_DEV bool hard_df(float s, float l) {
   float e = fabsf(s) * 0x1p-36f;
   float t = l + bitsf(fbits(e) | (fbits(l) & 0x80000000u));
   return (s + t) != s;
+}
+
+// The same test on a pair that need not be normalised, returning the result: y = s + r
+// (s normal, |r| <= 2^-14 |s|) approximates v with |v - y| <= eps_true |y|, eps_true <=
+// 2^-37.  With e = 2^-36 |s| (exact), a+ = RN(r + e) and a- = RN(r - e) lie outside
+// [r - eps_true |y|, r + eps_true |y|]: their roundings cost at most 2^-24 (|r| + e)
+// < 2^-37.9 |s|, and eps_true |y| <= 2^-37 (1 + 2^-14) |s|, together below e.  So
+// s + a- <= v <= s + a+, and as round-to-nearest is monotone, RN(s + a-) == RN(s + a+)
+// implies that both equal RN(v); otherwise the lane is hard.  When the lane is easy the
+// result is RN(s + r), the value the normalised pair would give.  Six operations against
+// eight for renormalisation plus hard_df; NaN in s makes the lane hard, as there.
+CRM_DEV float round_df(float s, float r, bool &hard) {
+  const float e = fabsf(s) * 0x1p-36f;
+  const float hi = s + (r + e), lo = s + (r - e);
+  hard = hi != lo;
+  return hi;
 }
 
 // Slow tier: y = s + t (double-double, |t| <= ulp(s)/2) approximates v with

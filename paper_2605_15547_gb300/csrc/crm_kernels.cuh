@@ -165,21 +165,29 @@ __device__ __noinline__ void slow_store(typename Fn::T x, uint64_t i, const KArg
   if (unres) atomicAdd(&a.hdr->unresolved_total, 1ull);
 }
 
-// Evaluates the W elements of one vector: y0 (and y1 for two outputs) and the hard bits.
+// Evaluates the W elements of one vector: y0 (and y1 for two outputs) and the hard
+// flags; returns whether any lane of the vector is hard (the flags stay predicates, the
+// queue mask is built from them only on the rare path, hard_mask).
 template <class Fn, int FORM, class V>
-CRM_DEV void eval_vec(const V &xv, const void *sm, V &y0, V &y1, unsigned &hm) {
+CRM_DEV bool eval_vec(const V &xv, const void *sm, V &y0, V &y1, bool *h) {
   using T = typename Fn::T;
   constexpr int W = sizeof(V) / sizeof(T);
-  hm = 0;
+  bool any = false;
 #pragma unroll
   for (int j = 0; j < W; j++) {
     T y[2];
-    bool h;
-    Fn::template eval<FORM>(vget(xv, j), sm, y, h);
-    hm |= (unsigned)h << j;
+    Fn::template eval<FORM>(vget(xv, j), sm, y, h[j]);
+    any = any || h[j];
     vset(y0, j, y[0]);
     if (Fn::NOUT == 2) vset(y1, j, y[1]);
   }
+  return any;
+}
+template <int W> CRM_DEV unsigned hard_mask(const bool *h, bool force) {
+  unsigned hm = 0;
+#pragma unroll
+  for (int j = 0; j < W; j++) hm |= (unsigned)(h[j] || force) << j;
+  return hm;
 }
 
 // Loads the UNROLL vectors of one iteration (zero past the end).
@@ -206,15 +214,14 @@ CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T, WIDE>::V *xv, uint64
     uint64_t v = base + (uint64_t)u * BS + threadIdx.x;
     bool act = v < a.nvec;
     V y0, y1;
-    unsigned hm;
-    eval_vec<Fn, FORM>(xv[u], sm, y0, y1, hm);
-    hm = a.force_hard ? (1u << W) - 1u : hm;
-    hm = act ? hm : 0u;
+    bool h[W];
+    const bool any = (eval_vec<Fn, FORM>(xv[u], sm, y0, y1, h) || a.force_hard) && act;
     if (act) {
       st_stream(out4 + v, y0);
       if (Fn::NOUT == 2) st_stream(out4b + v, y1);
     }
-    if (__any_sync(0xFFFFFFFFu, hm != 0)) {
+    if (__any_sync(0xFFFFFFFFu, any)) {
+      const unsigned hm = act ? hard_mask<W>(h, a.force_hard != 0) : 0u;
       uint64_t ii[W], xb[W];
 #pragma unroll
       for (int j = 0; j < W; j++) {
@@ -391,15 +398,14 @@ __global__ void __launch_bounds__(KBLOCK) k_pipe(KArgs a) {
       const bool act = v < a.nvec;
       V xv = act ? buf[st][vl] : V();
       V y0, y1;
-      unsigned hm;
-      eval_vec<Fn, FORM>(xv, sm, y0, y1, hm);
-      hm = a.force_hard ? (1u << W) - 1u : hm;
-      hm = act ? hm : 0u;
+      bool h[W];
+      const bool any = (eval_vec<Fn, FORM>(xv, sm, y0, y1, h) || a.force_hard) && act;
       if (act) {
         st_stream(out4 + v, y0);
         if (Fn::NOUT == 2) st_stream(out4b + v, y1);
       }
-      if (__any_sync(0xFFFFFFFFu, hm != 0)) {
+      if (__any_sync(0xFFFFFFFFu, any)) {
+        const unsigned hm = act ? hard_mask<W>(h, a.force_hard != 0) : 0u;
         uint64_t ii[W], xb[W];
 #pragma unroll
         for (int j = 0; j < W; j++) {

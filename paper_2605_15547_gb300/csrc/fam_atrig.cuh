@@ -90,16 +90,24 @@ template <int KIND> CRM_DEV float atrig_plain(float x, const double *AT, bool &h
 // The same core on float pairs.  c_j q.hi is split exactly by FMA so that p - c_j q is
 // exact in its leading word (Sterbenz: p/(c_j q) is within [1/2, 2] when j >= 1);
 // t = num/den by df_div; atan t = t - t^3/3 + t^5 (1/5 - t^2/7) with t^3/3 as a pair.
-// s = sqrt(1 - x^2): 1 - x^2 as an exact pair, sqrtf plus one Newton correction.
+// s = sqrt(1 - x^2): 1 - x^2 as an exact pair d, s0 = RN(d y0) with y0 the hardware
+// reciprocal square root (s0 within delta < 2^-21.7 of sqrt(d)), and one Newton
+// correction (d - s0^2) y0 / 2 from the residual: y0 in place of 1/s0 costs 2 delta of
+// the correction (2^-42.2 of s), the truncation delta^2 / 2 (2^-44.4), the residual's
+// roundings 2^-45.7: s to 2^-41.8 of itself, which moves the result by at most 1.3 times
+// that (atan(u)/u >= pi/4 on [0, 1]).
 // Error: t to 2^-43 (2^-43 of t when j = 0), atan t to 2^-45 of itself, table and pi
-// pairs 2^-48, the sum at most doubles the errors: < 2^-41, inside hard_df's 2^-37.
+// pairs 2^-48, the sum at most doubles the errors: < 2^-41; with s (asin, acos) < 2^-40,
+// inside the rounding test's 2^-37.  The result pair is left unnormalised (|lo| < 2^-21 |hi|) for round_df.
 CRM_DEV Pair<float> atan_ratio_df(Pair<float> a, Pair<float> b, const float2 *AT) {
   bool sw = a.hi > b.hi;
   Pair<float> p = sw ? b : a, q = sw ? a : b;
-  float rf = __fdividef(p.hi, q.hi);  // only picks j
-  int j = __float2int_rn(rf * 16.0f);
-  j = j < 0 ? 0 : (j > 16 ? 16 : j);
-  float c = (float)j * 0.0625f;
+  // j = rint(16 p/q) in [0, 16] by the 1.5 2^23 shifter (p/q <= 1: clamped, which also
+  // maps a NaN quotient to 1); c = j/16 exactly
+  const float rf = fminf(__fdividef(p.hi, q.hi), 1.0f);  // only picks j
+  const float jsh = fma_(rf, 16.0f, CRM_SHIFTER_F);
+  const int j = (int)(fbits(jsh) - fbits(CRM_SHIFTER_F));
+  const float c = (jsh - CRM_SHIFTER_F) * 0.0625f;
   float m = c * q.hi;
   float ml = fma_(c, q.hi, -m);
   float nh = p.hi - m;  // exact
@@ -109,7 +117,7 @@ CRM_DEV Pair<float> atan_ratio_df(Pair<float> a, Pair<float> b, const float2 *AT
   float dl = fma_(c, p.hi, -d);
   Pair<float> den = fast_two_sum(q.hi, d);
   den.lo = den.lo + (q.lo + dl + c * p.lo);
-  Pair<float> t = df_div(num, den);
+  Pair<float> t = df_div_raw(num, den);  // |t.lo| < 2^-20 |t.hi|: t^2 as below loses 2^-40
   // atan t
   float u = t.hi * t.hi;
   float ul = fma_(t.hi, t.hi, -u);
@@ -129,8 +137,8 @@ CRM_DEV Pair<float> atan_ratio_df(Pair<float> a, Pair<float> b, const float2 *AT
   float2 A = AT[j];
   // atan(j/16) >= atan(1/16) > |atan t| for j >= 1 (A = 0 for j = 0), and pi/2 > atan(a/b)
   // for the swapped case: both sums are ordered (Fast2Sum)
-  Pair<float> r = df_add_ordered({A.x, A.y}, {ah, al});
-  if (sw) r = df_add_ordered({CRM_PIO2_F_HI, CRM_PIO2_F_LO}, -r);
+  Pair<float> r = df_add_ordered_raw({A.x, A.y}, {ah, al});
+  if (sw) r = df_add_ordered_raw({CRM_PIO2_F_HI, CRM_PIO2_F_LO}, -r);
   return r;
 }
 
@@ -151,11 +159,13 @@ template <int KIND> CRM_DEV float atrig_df(float x, const float2 *AT, bool &hard
     float pl = fma_(ax, ax, -p);
     Pair<float> d1 = fast_two_sum(1.0f, -p);  // 1 >= p
     Pair<float> dd_ = fast_two_sum(d1.hi, d1.lo - pl);
-    float s0 = sqrtf(dd_.hi);
+    // d >= 2^-23 unless x = +-1 (d = 0: the floor keeps y0 finite and s = 0)
+    const float y0 = rsqrtf(fmaxf(dd_.hi, 0x1p-126f));
+    float s0 = dd_.hi * y0;
     float s2 = s0 * s0;
     float s2l = fma_(s0, s0, -s2);
     float res = ((dd_.hi - s2) - s2l) + dd_.lo;
-    float corr = s0 > 0.0f ? res * __fdividef(0.5f, s0) : 0.0f;
+    float corr = res * (0.5f * y0);
     Pair<float> s = fast_two_sum(s0, corr);
     if (KIND == AT_ASIN) {
       a = {ax, 0.0f};
@@ -167,13 +177,13 @@ template <int KIND> CRM_DEV float atrig_df(float x, const float2 *AT, bool &hard
     }
   }
   Pair<float> r = atan_ratio_df(a, b, AT);
-  if (KIND == AT_ACOS && flip) r = df_add_ordered({CRM_PI_F_HI, CRM_PI_F_LO}, -r);  // pi > r
+  if (KIND == AT_ACOS && flip) r = df_add_ordered_raw({CRM_PI_F_HI, CRM_PI_F_LO}, -r);  // pi > r
   if (__builtin_expect(sp, 0)) {
     hard = false;
     return rsp;
   }
-  hard = hard_df(r.hi, r.lo);
-  return (KIND != AT_ACOS && x < 0.0f) ? -r.hi : r.hi;
+  const float y = round_df(r.hi, r.lo, hard);
+  return (KIND != AT_ACOS && x < 0.0f) ? -y : y;
 }
 
 // ------------------------------------------------------------------ double-double tier

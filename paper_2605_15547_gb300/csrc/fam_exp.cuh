@@ -92,18 +92,21 @@ template <int KIND> CRM_DEV float exp_plain(float x, const double *T16, bool &ha
 // ulp(th) >= |tl|/2 in exponent), |g| <= 2^-7 + 2^-16.  With T = 2^(j/64) and
 // U = T ln2 from a 64-entry float4 table (Th, Tl, Uh, Ul):
 //   2^g T = Th + Uh gh + [Tl + Uh gl + Ul gh + T Q(gh) + ...],
-//   Q(g) = g^2 (a2 + a3 g + a4 g^2),  a_k = (ln 2)^k / k!,
-// Uh gh split exactly by FMA and Th + Uh gh by Fast2Sum, the bracket in float, then one
-// renormalisation.  Error budget (relative to T): rounding of Q 2^-38.8, the dropped
-// cross term 2 a2 gh gl 2^-39.1, t from x*C1 and the split of C 2^-40.7, a5 g^5
-// remainder 2^-44.6, tables 2^-48, bracket roundings 2^-48: total < 2^-37.7, covered by
-// the test's 2^-37 allowance (hard_df).
+//   Q(g) = g^2 (a2 + a3 g + a4 g^2),  a_k = (ln 2)^k / k!.
+// The leading sum s = RN(Th + Uh gh) is one FMA; Th - s is exact (s lies within 2^-7 of
+// Th >= 1), so a second FMA, Uh gh + (Th - s), gives its rounding error to 2^-24 of
+// itself (2^-48 |s|); the bracket and that error are summed in float into r, and the
+// pair (s, r), |r| < 2^-15 |s|, goes to the rounding test unnormalised (round_df).
+// Error budget (relative to T): rounding of Q 2^-38.8, the dropped cross term
+// 2 a2 gh gl 2^-39.1, t from x*C1 and the split of C 2^-40.7, a5 g^5 remainder 2^-44.6,
+// tables 2^-48, the error term and the bracket roundings 2^-47: total < 2^-37.7, inside
+// the test's 2^-37.
 // Inputs outside [X_SUB, X_OVF] are resolved by selects: +inf above X_OVF, +0 below
 // X_ZERO, a quiet NaN for NaN; results in the subnormal band [X_ZERO, X_SUB) are rounded
 // to the subnormal grid from the same pair (below).
-// b^x = 2^k (s2 + l2), the pair normalised and good to 2^-37.7 of itself (budget above);
-// sb is the shifter's bit pattern (k and the table index are read from it).
-template <int KIND> CRM_DEV void exp_df_core(float x, const float4 *T64U, float &s2, float &l2, uint32_t &sb) {
+// b^x = 2^k (s + r) to 2^-37.7 of itself (budget above); sb is the shifter's bit pattern
+// (k and the table index are read from it).
+template <int KIND> CRM_DEV void exp_df_core(float x, const float4 *T64U, float &s, float &r, uint32_t &sb) {
   using K = ExpK<KIND>;
   float th, tl;
   if (KIND == 1) {
@@ -115,10 +118,8 @@ template <int KIND> CRM_DEV void exp_df_core(float x, const float4 *T64U, float 
     tl = fma_(x, K::F1, tl);
   }
   float sh = fma_(th, 64.0f, CRM_SHIFTER_F);
-  // N = rint(64 t) sits in the low bits of sh's pattern, whose other bits (0x4B400000) are
-  // 0 modulo 64 and vanish when shifted left by 17: the table index is the pattern's low 6
-  // bits and the exponent increment (N >> 6) << 23 is the pattern shifted left by 17 with
-  // the low 23 bits cleared
+  // N = rint(64 t) sits in the low bits of sh's pattern 0x4B400000 + N (0x4B400000 is 0
+  // modulo 64): the table index is the pattern's low 6 bits
   sb = fbits(sh);
   float nf = sh - CRM_SHIFTER_F;
   float f = fma_(nf, -0.015625f, th);
@@ -134,42 +135,40 @@ template <int KIND> CRM_DEV void exp_df_core(float x, const float4 *T64U, float 
   float q = fma_(gh, CRM_EXP2_A4_F, CRM_EXP2_A3_F);
   q = fma_(gh, q, CRM_EXP2_A2_F);
   float Q = (gh * gh) * q;
-  float m = T.z * gh;
-  float ml = fma_(T.z, gh, -m);
-  float s = T.x + m;
-  float z = m - (s - T.x);
-  float r = (KIND == 1) ? T.y : fma_(T.z, gl, T.y);
-  r = fma_(T.w, gh, r);
-  r = fma_(T.x, Q, r);
-  r = r + ml;
-  r = r + z;
-  s2 = s + r;
-  l2 = r - (s2 - s);
+  s = fma_(T.z, gh, T.x);
+  const float z = fma_(T.z, gh, T.x - s);
+  float b = (KIND == 1) ? T.y : fma_(T.z, gl, T.y);
+  b = fma_(T.w, gh, b);
+  b = fma_(T.x, Q, b);
+  r = b + z;
 }
 
 template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard) {
   using K = ExpK<KIND>;
-  float s2, l2;
+  float s, r;
   uint32_t sb;
-  exp_df_core<KIND>(x, T64U, s2, l2, sb);
-  float y = bitsf(fbits(s2) + ((sb << 17) & 0xFF800000u));
+  exp_df_core<KIND>(x, T64U, s, r, sb);
   const bool ok = (x >= K::XSUB) && (x <= K::XOVF);  // false for NaN
   if (__builtin_expect(ok, 1)) {
-    hard = hard_df(s2, l2);
-    return y;
+    // the exponent increment (N >> 6) << 23: sb >> 6 is N >> 6 plus 0x12D0000 (borrow
+    // included), whose shift by 23 vanishes modulo 2^32
+    const float y = round_df(s, r, hard);
+    return bitsf(fbits(y) + ((sb >> 6) << 23));
   }
   // Out of range (rare): +inf, +0, a quiet NaN, or a subnormal result.
   hard = false;
-  y = x != x ? qnan_of(x) : (x > 0.0f ? CRM_INF_F : 0.0f);
+  float y = x != x ? qnan_of(x) : (x > 0.0f ? CRM_INF_F : 0.0f);
   if ((x >= K::XZERO) && (x < K::XSUB)) {
-    // The result is the integer nearest to u = (s2 + l2) 2^(k + 149) times 2^-149
-    // (k + 149 in [-2, 23], the scaling exact).  With q = rint(u_hi) and
-    // d = (u_hi - q) + u_lo, the nearest integer is q, q + 1 (d > 1/2) or q - 1
-    // (d < -1/2); the pair's error (2^-37 of u < 2^-13) and d's rounding (2^-24) can move
-    // u across a half-integer only when ||d| - 1/2| <= 2^-12: those lanes go slow.
+    // The result is the integer nearest to u = (s2 + l2) 2^(k + 149) times 2^-149, with
+    // (s2, l2) the normalised pair (k + 149 in [-2, 23], the scaling exact).  With
+    // q = rint(u_hi) and d = (u_hi - q) + u_lo, the nearest integer is q, q + 1
+    // (d > 1/2) or q - 1 (d < -1/2); the pair's error (2^-37 of u < 2^-13) and d's
+    // rounding (2^-24) can move u across a half-integer only when ||d| - 1/2| <= 2^-12:
+    // those lanes go slow.
+    const Pair<float> p = fast_two_sum(s, r);
     const int N = (int)(sb - fbits(CRM_SHIFTER_F));
     const float sc = bitsf((uint32_t)((N >> 6) + 149 + 127) << 23);
-    const float uh = s2 * sc, ul = l2 * sc;
+    const float uh = p.hi * sc, ul = p.lo * sc;
     const float q = rintf(uh);
     const float d = (uh - q) + ul;
     const float qi = q + (d > 0.5f ? 1.0f : (d < -0.5f ? -1.0f : 0.0f));

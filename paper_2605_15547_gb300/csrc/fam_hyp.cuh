@@ -110,9 +110,9 @@ template <int H> CRM_DEV float hyp_plain(float x, const double *T16, bool &hard)
 // the reduction of t = x log2 e (below 2^-41 at |t| = 128, where nothing cancels),
 // 2^-44 elsewhere after cancellation; the a6 g^6 remainder 2^-51.7.  The derived
 // functions add one pair division or product (2^-43): all stay below 2^-40, within the
-// 2^-37 that hard_df allows.
+// 2^-37 that the rounding test (round_df) allows.
 struct DFY {
-  float s, l;  // Y = s + l, |l| <= ulp(s)/2
+  float s, l;  // Y = s + l unnormalised, |l| < 2^-20 |s| (or Y = 0)
   int k;       // e^x - 1 = 2^k Y
 };
 
@@ -155,9 +155,7 @@ CRM_DEV DFY expm1_df_core(float x, const float4 *T64U) {
   Pair<float> s1 = two_sum(c.hi, u);
   Pair<float> s2 = fast_two_sum(s1.hi, tq);  // |s1| >= |tq| (see above)
   float lo = (s1.lo + s2.lo) + (cl + (ul + tql));
-  float sh2 = s2.hi + lo;
-  float l2 = lo - (sh2 - s2.hi);
-  return {sh2, l2, k};
+  return {s2.hi, lo, k};
 }
 
 CRM_DEV float pow2f_exact(int k) { return bitsf((uint32_t)(k + 127) << 23); }  // k in [-126, 127]
@@ -185,17 +183,16 @@ template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard) {
     // e^a = 2^k P with P to 2^-37.7 (exp_df_core), R = 2^-k / P by a pair division, and
     // cosh a = 2^(k-1) (P + 2^-k R): the two terms keep P's relative error, the division
     // and the sums add 2^-43: below the 2^-37 of the rounding test.
-    float ph, pl;
+    float ps, pr;
     uint32_t sb;
-    exp_df_core<0>(arg, T64U, ph, pl, sb);
+    exp_df_core<0>(arg, T64U, ps, pr, sb);
     const int k = (int)(sb - fbits(CRM_SHIFTER_F)) >> 6;
-    const Pair<float> P = {ph, pl};
+    const Pair<float> P = fast_two_sum(ps, pr);  // normalised for the division
     const float pk = k > 100 ? 0.0f : pow2f_exact(-k);
     Pair<float> R = df_div({pk, 0.0f}, P);
     float rk = R.hi * pk, rkl = R.lo * pk;
-    Pair<float> S = fast_two_sum(P.hi, rk);
-    S.lo = S.lo + (P.lo + rkl);
-    r = fast_two_sum(S.hi, S.lo);
+    r = fast_two_sum(P.hi, rk);
+    r.lo = r.lo + (P.lo + rkl);  // unnormalised, |r.lo| < 2^-22 |r.hi|
     sc = k - 1;
   } else {
   DFY Y = expm1_df_core(arg, T64U);
@@ -203,25 +200,27 @@ template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard) {
     r = {Y.s, Y.l};
     sc = Y.k;
   } else if (H == HYP_TANH) {
-    // tanh a = Y / (Y + 2^(1-k)) with e^(2a) - 1 = 2^k Y
-    Pair<float> d = two_sum(Y.s, pow2f_exact(1 - Y.k));
-    d.lo = d.lo + Y.l;
-    r = df_div({Y.s, Y.l}, d);
+    // tanh a = Y / (Y + 2^(1-k)) with e^(2a) - 1 = 2^k Y (Y normalised for the division)
+    const Pair<float> Yn = fast_two_sum(Y.s, Y.l);
+    Pair<float> d = two_sum(Yn.hi, pow2f_exact(1 - Y.k));
+    d.lo = d.lo + Yn.lo;
+    r = df_div_raw(Yn, d);
   } else {
+    const Pair<float> Yn = fast_two_sum(Y.s, Y.l);
     float pk = Y.k > 100 ? 0.0f : pow2f_exact(-Y.k);
-    Pair<float> P = two_sum(Y.s, pk);  // P = 2^-k e^a
-    P.lo = P.lo + Y.l;
+    Pair<float> P = two_sum(Yn.hi, pk);  // P = 2^-k e^a
+    P.lo = P.lo + Yn.lo;
     Pair<float> R = df_div({pk, 0.0f}, P);  // 2^-2k e^-a ... = 2^-k / P
     // sinh a = 2^(k-1) Y (1 + R)
     Pair<float> onep = fast_two_sum(1.0f, R.hi);  // 1 + R as a pair (R <= 1)
     onep.lo = onep.lo + R.lo;
-    r = df_mul({Y.s, Y.l}, onep);
+    r = df_mul_raw(Yn, onep);
     sc = Y.k - 1;
   }
   }
   if (__builtin_expect(!sp, 1)) {
-    hard = hard_df(r.hi, r.lo);
-    float y = scale_f(r.hi, sc);
+    // r unnormalised: |r.lo| < 2^-20 |r.hi| in every branch above
+    float y = scale_f(round_df(r.hi, r.lo, hard), sc);
     if (H == HYP_SINH || H == HYP_TANH) y = x < 0.0f ? -y : y;
     return y;
   }

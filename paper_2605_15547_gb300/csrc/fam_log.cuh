@@ -123,49 +123,43 @@ template <int KIND> CRM_DEV float log_plain(float x, const double2 *T97, bool &h
 }
 
 // ------------------------------------------------------------------ double-float tier
-// Decomposition in binary32 (subnormal inputs are scaled by 2^24 first), j = rint(128 m),
-// d = m - c exact (Sterbenz), r = d (1/c) as a float pair (exact product split by FMA
-// plus d * (1/c)_lo).  log1p(r) = r - r^2/2 + r^3 (1/3 - r/4 + r^2/5):
-//   rh - rh^2/2 by Fast2Sum on the exact square (split by FMA), the r^3 tail in float.
-// For log2 / log10 the pair is multiplied by the float pair 1/ln 2 or 1/ln 10.
-// B = e K_hi + L_hi (Fast2Sum: e == 0, or |e K_hi| > |L|), then TwoSum(B, q) and one
-// renormalisation.  Error budget, relative to the result:
+// Decomposition in binary32 (subnormal inputs are scaled by 2^24 first),
+// j = rint(128 m), d = m - c exact (Sterbenz), r = d (1/c) as a float pair (exact
+// product split by FMA plus d * (1/c)_lo).  log1p(r) = r - r^2/2 + r^3 (1/3 - r/4
+// + r^2/5): rh - rh^2/2 by Fast2Sum on the exact square (split by FMA), the r^3 tail in
+// float.  For log2 / log10 the pair is multiplied by the float pair 1/ln 2 or 1/ln 10.
+// B = e K_hi + L_hi by one FMA (e K_hi is exact: K_hi has 16 significant bits) with its
+// rounding error recovered exactly as in Fast2Sum (e == 0, or |e K_hi| > |L|), then
+// Fast2Sum(B, q); the sum goes to the rounding test unnormalised.  Error budget, relative
+// to the result:
 //   r^6/6 remainder 2^-48.2 abs, tail rounding 2^-46.4 abs, pair products and the
 //   1/c, L and K splits <= 2^-46 abs, with |result| >= 2^-8 unless e = 0 and c = 1 (then
 //   all terms scale with r and the bound is 2^-38.5 relative); e K_lo rounding and the K
-//   split <= 2^-42 relative.  Total < 2^-38; the test allows 2^-37 (hard_df).
-template <int KIND> CRM_DEV float log_df(float x, const float4 *T97, bool &hard) {
+//   split <= 2^-42 relative.  Total < 2^-38; the test allows 2^-37 (round_df: the low
+//   word is below 2^-15 of the high one, |result| >= 2^-8.6 when B != 0).
+//
+// us = 2^(e - eadj) m for a positive normal float us (any bit pattern gives an in-range
+// table index; the result is then meaningless and discarded), plus, for log1p, the low
+// word ul of 1 + x and the direct path for |x| < 2^-7.  Returns the unnormalised sum.
+template <int KIND>
+CRM_DEV Pair<float> log_df_core(float us, int eadj, float ul, bool pathA, float x, const float4 *T97) {
   using K = LogK<KIND>;
-  bool ok = log_ok<KIND>(x);
-  float uh = x, ul = 0.0f;
-  bool pathA = false;
-  if (KIND == 3) {
-    pathA = fabsf(x) < 0x1p-7f;
-    Pair<float> u = two_sum(1.0f, x);
-    uh = u.hi;
-    ul = u.lo;
-  }
-  uh = ok ? uh : 1.0f;
-  bool sub = uh < 0x1p-126f;
-  float us = sub ? uh * 0x1p24f : uh;
   // us = 2^e m, m in [3/4, 3/2), from one integer subtraction: the exponent field of
   // us / (3/4) rounded down is floor(log2(us / (3/4)))
   const uint32_t b = fbits(us);
   const int32_t ee = (int32_t)(b - 0x3F400000u) >> 23;
-  float m = bitsf(b - ((uint32_t)ee << 23));
-  int e = ee - (sub ? 24 : 0);
+  const float m = bitsf(b - ((uint32_t)ee << 23));
   float sh = fma_(m, 128.0f, CRM_SHIFTER_F);
   int j = (int)(fbits(sh) - fbits(CRM_SHIFTER_F));
-  float c = (sh - CRM_SHIFTER_F) * 0.0078125f;
-  float d = m - c;
+  float d = fma_(sh - CRM_SHIFTER_F, -0.0078125f, m);  // m - j/128, exact
   float4 T = T97[j - 96];
   float rh = d * T.x;
   float rl = fma_(d, T.x, -rh);
   rl = fma_(d, T.y, rl);
-  float Lh = T.z, Ll = T.w, ef = (float)e;
+  float Lh = T.z, Ll = T.w, ef = (float)(ee + eadj);
   float t = 0.0f;
   if (KIND == 3) {
-    t = __fdividef(ul, uh);  // ul/uh with |ul| <= 2^-24 uh: relative 2^-21 suffices
+    t = __fdividef(ul, us);  // ul/uh with |ul| <= 2^-24 uh: relative 2^-21 suffices
     rh = pathA ? x : rh;
     rl = pathA ? 0.0f : rl;
     Lh = pathA ? 0.0f : Lh;
@@ -184,7 +178,7 @@ template <int KIND> CRM_DEV float log_df(float x, const float4 *T97, bool &hard)
   float rest = fma_(-rh, rl, rl);
   rest = fma_(h2l, -0.5f, rest);
   rest = rest + P;
-  rest = rest + (z + t);
+  rest = rest + (KIND == 3 ? z + t : z);
   float qh = s, ql = rest;
   if (KIND == 1 || KIND == 2) {
     const float IH = KIND == 1 ? CRM_INV_LN2_F_HI : CRM_INV_LN10_F_HI;
@@ -194,22 +188,34 @@ template <int KIND> CRM_DEV float log_df(float x, const float4 *T97, bool &hard)
     ql = fma_(s, IL, ql);
     ql = fma_(rest, IH, ql);
   }
-  // B = e K + L
-  float eK = ef * K::KH;
-  float B = eK + Lh;
-  float Bz = Lh - (B - eK);
+  // B = e K + L: B = RN(e K_hi + L_hi), e K_hi - B exact, Bz = L_hi - (B - e K_hi)
+  float B = fma_(ef, K::KH, Lh);
+  float Bz = Lh + fma_(ef, K::KH, -B);
   float Bl = Bz + fma_(ef, K::KL, Ll);
   // |B| > |qh| unless B = 0: with e != 0, |e K + L| >= 0.125 (log10; more for ln, log2);
   // with e = 0, |L_j| >= |log_b(1 +- 1/128)| > |log_b(1 + r)| since |r| <= 2^-8/0.75; so
   // Fast2Sum is exact here
   Pair<float> S = fast_two_sum(B, qh);
-  float lo = S.lo + (Bl + ql);
-  float s2 = S.hi + lo;
-  float l2 = lo - (s2 - S.hi);
-  if (__builtin_expect(ok, 1)) {
-    hard = hard_df(s2, l2);
-    return s2;
+  return {S.hi, S.lo + (Bl + ql)};
+}
+
+template <int KIND> CRM_DEV float log_df(float x, const float4 *T97, bool &hard) {
+  const bool ok = log_ok<KIND>(x);
+  float us = x, ul = 0.0f;
+  int eadj = 0;
+  bool pathA = false;
+  if (KIND == 3) {  // 1 + x is never subnormal for x > -1
+    pathA = fabsf(x) < 0x1p-7f;
+    Pair<float> u = two_sum(1.0f, x);
+    us = u.hi;
+    ul = u.lo;
+  } else {  // subnormal inputs by selects: they are common in bit-pattern inputs
+    const bool sub = x < 0x1p-126f;
+    us = sub ? x * 0x1p24f : x;
+    eadj = sub ? -24 : 0;
   }
+  Pair<float> y = log_df_core<KIND>(us, eadj, ul, pathA, x, T97);
+  if (__builtin_expect(ok, 1)) return round_df(y.hi, y.lo, hard);
   hard = false;  // NaN, zero, negative, infinite (rare: a branch, not selects)
   return special_log<KIND>(x);
 }

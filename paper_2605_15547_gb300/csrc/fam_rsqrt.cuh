@@ -47,7 +47,8 @@ CRM_DEV float rsqrt_plain(float x, bool &hard) {
 // (1 - p is exact by Sterbenz since x y0^2 is within 2^-20 of 1), and one Newton step
 // kept as a pair: y = y0 + y0 e (1/2 + 3e/8).  |e| < 2^-20: the truncation is
 // (5/16) e^3 < 2^-61, the residual is good to 2^-48 absolute, the correction product to
-// 2^-24 of itself (2^-45 of y): relative error < 2^-44.5, inside hard_df's 2^-37.
+// 2^-24 of itself (2^-45 of y): relative error < 2^-44.5, inside the rounding test's
+// 2^-37; the pair (y0, c), |c| < 2^-21 y0, goes to round_df unnormalised.
 CRM_DEV float rsqrt_df(float x, bool &hard) {
   float r;
   bool sp = rsqrt_special(x, r);
@@ -61,11 +62,12 @@ CRM_DEV float rsqrt_df(float x, bool &hard) {
   float e = (1.0f - p) - fma_(xs, sl, pl);
   float corr = fma_(e, 0.375f, 0.5f) * e;
   float c = y0 * corr;
-  Pair<float> y = fast_two_sum(y0, c);
+  bool h;
+  const float yh = round_df(y0, c, h);
   // special inputs (x <= 0, NaN, +inf) by selects: they are common in real data (half of
   // a symmetric input range), so a branch would diverge in most warps
-  hard = !sp && hard_df(y.hi, y.lo);
-  float out = sub ? y.hi * 0x1p12f : (big ? y.hi * 0x1p-32f : y.hi);
+  hard = !sp && h;
+  float out = sub ? yh * 0x1p12f : (big ? yh * 0x1p-32f : yh);
   return sp ? r : out;
 }
 

@@ -40,6 +40,26 @@ CRM_DEV void trig_window_mul(float ax, const uint32_t *P, uint32_t *r) {
   r[NW] = (uint32_t)carry;
 }
 
+// The same product for NW = 3 with the four words P[k .. k+3] from one 16-byte entry
+// PW[k] of a window table (PW[k] = (P[k], P[k+1], P[k+2], P[k+3])): one shared-memory
+// load per element.  k = (e + 62) >> 5 lies in [1, 5] for 2^-6 <= |x| < 2^128.
+CRM_DEV void trig_window_mul3(float ax, const uint4 *PW, uint32_t *r) {
+  uint32_t b = fbits(ax);
+  uint32_t M = (b & 0x007FFFFFu) | 0x00800000u;
+  int p = (int)(b >> 23) - 150 + 62;
+  const uint4 Q = PW[p >> 5];
+  const int o = p & 31;
+  const uint32_t w0 = __funnelshift_l(Q.y, Q.x, o), w1 = __funnelshift_l(Q.z, Q.y, o),
+                 w2 = __funnelshift_l(Q.w, Q.z, o);
+  uint64_t pr = (uint64_t)M * w2;
+  r[0] = (uint32_t)pr;
+  pr = (uint64_t)M * w1 + (pr >> 32);
+  r[1] = (uint32_t)pr;
+  pr = (uint64_t)M * w0 + (pr >> 32);
+  r[2] = (uint32_t)pr;
+  r[3] = (uint32_t)(pr >> 32);
+}
+
 // Fast-tier reduction: N7 = (32 q + j) mod 128 and the fraction f as a signed 64-bit
 // fixed-point number (f = fi 2^-64); error < 2^-64 (fraction) + 2^-66 (window).
 CRM_DEV void trig_reduce64(float ax, const uint32_t *P, int &N7, int64_t &fi) {
@@ -144,23 +164,25 @@ CRM_DEV void trig_plain(float x, const uint32_t *P, const double *SC, float *y, 
 // up to 2^-13.3 |t|, so it is carried as a pair); table pairs 2^-48; the rotation's pair
 // products and sum 2^-45; the rotation terms S cos t + C sin t lose at most 2^5.4 (a
 // result as small as sin(pi/128) from terms up to 1): total < 2^-39, inside the 2^-37
-// that hard_df allows.
+// that the rounding test allows.  sin and cos leave the last sum unnormalised
+// (|lo| < 2^-15 |hi|: the pair products' low words, 2^-22 of terms at most 2^5.4 times
+// the result) for round_df; tan normalises both before its division.
 struct TrigF {
   Pair<float> A, B;  // sin and cos of (j pi/64 + t)
   int q;
   bool tiny;
 };
 
-// KIND = TRIG_SIN or TRIG_COS: only the rotation term the quadrant needs is formed, in R.A
-// (sin: B when q is odd, else A; cos: A when q is odd, else B); otherwise both.
-template <int KIND> CRM_DEV TrigF trig_df_core(float x, const uint32_t *P, const float4 *SC) {
+// The reduction shared by the double-float evaluators: t = f pi/64 as an unnormalised
+// pair, N7 = (32 q + j) mod 128, and tiny (j = 0 and |f| < 2^-24: slow path).
+CRM_DEV void trig_reduce_df(float x, const uint4 *PW, Pair<float> &t, int &N7, bool &tiny) {
   float ax = fabsf(x);
   bool small = ax < 0x1p-6f;
   uint32_t r[4];
-  trig_window_mul<3>(small ? 1.0f : ax, P, r);
+  trig_window_mul3(small ? 1.0f : ax, PW, r);
   uint32_t Fh = ((r[2] & 0x01FFFFFFu) << 7) | (r[1] >> 25);
   uint32_t Fl = (r[1] << 7) | (r[0] >> 25);
-  int N7 = (int)(((r[2] >> 25) + (Fh >> 31)) & 127u);
+  N7 = (int)(((r[2] >> 25) + (Fh >> 31)) & 127u);
   uint32_t Ph = Fh ^ 0x80000000u;
   uint32_t c0 = Ph >> 9;
   uint32_t c1 = ((Ph & 0x1FFu) << 14) | (Fl >> 18);
@@ -169,22 +191,32 @@ template <int KIND> CRM_DEV TrigF trig_df_core(float x, const uint32_t *P, const
   float f1 = bitsf(0x4B000000u | c1) - 0x1p23f;
   float f2 = bitsf(0x4B000000u | c2) - 0x1p23f;
   // f = (c0 2^-23 - 1/2) + c1 2^-46 + c2 2^-64, three exact floats; the first two are
-  // joined by TwoSum, so that (fh, fl) carries f to 2^-24 |fl| + 2^-64 even when the
-  // first chunk is zero or cancels (|f| small: the case that decides the rounding of
-  // results near multiples of pi/2).
-  Pair<float> fs = two_sum(fma_(f0, 0x1p-23f, -0.5f), f1 * 0x1p-46f);
+  // joined exactly (Fast2Sum: the first is 0 or a nonzero multiple of 2^-23, the second
+  // below 2^-23), so that (fh, fl) carries f to 2^-24 |fl| + 2^-64 even when the first
+  // chunk is zero or cancels (|f| small: the case that decides the rounding of results
+  // near multiples of pi/2).
+  Pair<float> fs = fast_two_sum(fma_(f0, 0x1p-23f, -0.5f), f1 * 0x1p-46f);
   float fh = fs.hi;
   float fl = fma_(f2, 0x1p-64f, fs.lo);
-  float th = fh * CRM_PIO64_F_HI;
-  float tl = fma_(fh, CRM_PIO64_F_HI, -th);
-  tl = fma_(fh, CRM_PIO64_F_LO, tl);
-  tl = fma_(fl, CRM_PIO64_F_HI, tl);
-  Pair<float> t = fast_two_sum(th, tl);
-  TrigF R;
-  R.tiny = !small && (N7 & 31) == 0 && fabsf(fh + fl) < 0x1p-24f;
+  // t = f pi/64 as an unnormalised pair (|tl| < 2^-22 |th|: dropping tl^2 from t^2
+  // costs 2^-44.8 of t^2, below 2^-56 of cos t, sin t and tan t)
+  t.hi = fh * CRM_PIO64_F_HI;
+  t.lo = fma_(fh, CRM_PIO64_F_HI, -t.hi);
+  t.lo = fma_(fh, CRM_PIO64_F_LO, t.lo);
+  t.lo = fma_(fl, CRM_PIO64_F_HI, t.lo);
+  tiny = !small && (N7 & 31) == 0 && fabsf(fh + fl) < 0x1p-24f;
   t.hi = small ? ax : t.hi;
   t.lo = small ? 0.0f : t.lo;
   N7 = small ? 0 : N7;
+}
+
+// KIND = TRIG_SIN or TRIG_COS: only the rotation term the quadrant needs is formed, in R.A
+// (sin: B when q is odd, else A; cos: A when q is odd, else B); otherwise both.
+template <int KIND> CRM_DEV TrigF trig_df_core(float x, const uint4 *PW, const float4 *SC) {
+  Pair<float> t;
+  int N7;
+  TrigF R;
+  trig_reduce_df(x, PW, t, N7, R.tiny);
   // t^2 as a pair
   float u = t.hi * t.hi;
   float ul = fma_(t.hi, t.hi, -u);
@@ -216,7 +248,7 @@ template <int KIND> CRM_DEV TrigF trig_df_core(float x, const uint32_t *P, const
     // B = C cos t + (-S) sin t, A = S cos t + C sin t: one product pair with chosen factors
     const bool useB = (KIND == TRIG_SIN) == ((R.q & 1) != 0);
     const Pair<float> Pf = useB ? C : S, Qf = useB ? -S : C;
-    R.A = df_add_ordered(df_mul_raw(Pf, ct), df_mul_raw(Qf, st));
+    R.A = df_add_ordered_raw(df_mul_raw(Pf, ct), df_mul_raw(Qf, st));
     R.B = R.A;
     return R;
   }
@@ -225,17 +257,81 @@ template <int KIND> CRM_DEV TrigF trig_df_core(float x, const uint32_t *P, const
   // |S_j sin t| for j <= 31: Fast2Sum applies.
   Pair<float> a1 = df_mul_raw(S, ct), a2 = df_mul_raw(C, st);
   Pair<float> b1 = df_mul_raw(C, ct), b2 = df_mul_raw(S, st);
-  R.A = df_add_ordered(a1, a2);
-  R.B = df_add_ordered(b1, -b2);
+  R.A = df_add_ordered_raw(a1, a2);
+  R.B = df_add_ordered_raw(b1, -b2);
   return R;
 }
 
+// tan by the addition formula on the same reduction: with T = tan(j pi/64) (a 32-entry
+// float-pair table) and tau = tan t,
+//   tan(j pi/64 + t) = N / D,  N = T + tau,  D = 1 - T tau,
+// and tan x = +-N/D for even q, -+D/N for odd q (tan(a + pi/2) = -1/tan a).
+// tau = t + t^3/3 + t^5 (2/15 + 17 t^2/315) with t^2 and t^3/3 as pairs (the t^9 term is
+// below 2^-48 of t).  N: T >= tan(pi/64) > |tau| for j >= 1 (T = 0 for j = 0), so
+// Fast2Sum applies and N cancels by at most a factor 2; D: |T tau| <= tan(31 pi/64)
+// tan(pi/128) < 1/2, so D lies in [1/2, 3/2] and 1 - T tau is a Fast2Sum.  Both are
+// normalised for the pair division.  Error budget, relative to the result: tau 2^-45,
+// T 2^-48, N (doubled by its cancellation) 2^-43.8, D 2^-44, the division 2^-43, the
+// reduction as for sin and cos: total < 2^-41.5, inside the rounding test's 2^-37.
+CRM_DEV Pair<float> tan_df_nd(Pair<float> t, int j, const float2 *TT, Pair<float> &D) {
+  float u = t.hi * t.hi;
+  float ul = fma_(t.hi, t.hi, -u);
+  ul = fma_(2.0f * t.hi, t.lo, ul);
+  float w = t.hi * u;
+  float wl = fma_(t.hi, u, -w);
+  wl = fma_(t.hi, ul, wl);
+  wl = fma_(t.lo, u, wl);
+  float s3 = w * CRM_INV3_F_HI;
+  float s3l = fma_(w, CRM_INV3_F_HI, -s3);
+  s3l = fma_(w, CRM_INV3_F_LO, s3l);
+  s3l = fma_(wl, CRM_INV3_F_HI, s3l);
+  const float th = t.hi + s3;
+  float tl = s3 - (th - t.hi);  // Fast2Sum: |t| > |t^3/3|
+  tl = tl + (t.lo + s3l);
+  tl = fma_(w * u, fma_(u, CRM_TAN_C7_F, CRM_TAN_C5_F), tl);
+  const float2 T = TT[j];
+  Pair<float> N = df_add_ordered({T.x, T.y}, {th, tl});
+  const Pair<float> P = df_mul_raw({T.x, T.y}, {th, tl});
+  D = fast_two_sum(1.0f, -P.hi);
+  D.lo = D.lo - P.lo;
+  D = fast_two_sum(D.hi, D.lo);
+  return N;
+}
+
+// Sign of a rounded result as a bit mask: sin(j pi/64 + t) rotated by q quadrants is
+// negative for q = 2, 3, cos for q = 1, 2; sin and tan are odd in x.
+CRM_DEV uint32_t trig_sin_sign(int q, float x) { return (((uint32_t)q << 30) ^ fbits(x)) & 0x80000000u; }
+CRM_DEV uint32_t trig_cos_sign(int q) { return ((uint32_t)(q + 1) << 30) & 0x80000000u; }
+
+// The pairs are rounded before the quadrant rotation: round-to-nearest and round_df's
+// test are symmetric under negation, so rounding A and B and then swapping and negating
+// the floats gives the same bits as rotating the pairs first.
 template <int KIND>
-CRM_DEV void trig_df(float x, const uint32_t *P, const float4 *SC, float *y, bool &hard) {
+CRM_DEV void trig_df(float x, const uint4 *PW, const float4 *SC, const float2 *TT, float *y, bool &hard) {
   const bool sp = !(fabsf(x) < CRM_INF_F);  // NaN or infinite
-  TrigF R = trig_df_core<KIND>(sp ? 1.0f : x, P, SC);
-  Pair<float> sn, cs;
-  trig_rotate<Pair<float>>(KIND, x, R.q, R.A, R.B, sn, cs);  // A == B for sin, cos alone
+  if (KIND == TRIG_TAN) {
+    Pair<float> t, D;
+    int N7;
+    bool tiny;
+    trig_reduce_df(sp ? 1.0f : x, PW, t, N7, tiny);
+    const Pair<float> N = tan_df_nd(t, N7 & 31, TT, D);
+    const bool odd = (N7 & 32) != 0;
+    const Pair<float> q = df_div_raw(odd ? D : N, odd ? N : D);
+    bool h;
+    const float yt = round_df(q.hi, q.lo, h);
+    if (__builtin_expect(sp, 0)) {
+      hard = false;
+      y[0] = x != x ? qnan_of(x) : CRM_QNAN_F;
+      return;
+    }
+    // negative in odd quadrants (-cot), and odd in x
+    const uint32_t sg = (((uint32_t)N7 << 26) ^ fbits(x)) & 0x80000000u;
+    const bool zero = x == 0.0f;  // tan(+-0) = +-0
+    hard = !zero && (tiny || h);
+    y[0] = zero ? x : bitsf(fbits(yt) ^ sg);
+    return;
+  }
+  TrigF R = trig_df_core<KIND>(sp ? 1.0f : x, PW, SC);
   if (__builtin_expect(sp, 0)) {
     hard = false;
     const float r = x != x ? qnan_of(x) : CRM_QNAN_F;
@@ -244,22 +340,22 @@ CRM_DEV void trig_df(float x, const uint32_t *P, const float4 *SC, float *y, boo
     return;
   }
   const bool zero = x == 0.0f;  // sin/tan(+-0) = +-0
-  if (KIND == TRIG_TAN) {
-    Pair<float> t = df_div(sn, cs);
-    hard = !zero && (R.tiny || hard_df(t.hi, t.lo));
-    y[0] = zero ? x : t.hi;
-    return;
-  }
+  const bool odd = (R.q & 1) != 0;
+  bool ha, hb;
+  // sin and cos alone: R.A is already the term the quadrant needs
+  const float ya = round_df(R.A.hi, R.A.lo, ha);
   if (KIND == TRIG_SIN) {
-    hard = !zero && (R.tiny || hard_df(sn.hi, sn.lo));
-    y[0] = zero ? x : sn.hi;
+    hard = !zero && (R.tiny || ha);
+    y[0] = zero ? x : bitsf(fbits(ya) ^ trig_sin_sign(R.q, x));
   } else if (KIND == TRIG_COS) {
-    hard = R.tiny || hard_df(cs.hi, cs.lo);
-    y[0] = cs.hi;
+    hard = R.tiny || ha;
+    y[0] = bitsf(fbits(ya) ^ trig_cos_sign(R.q));
   } else {
-    hard = R.tiny || (hard_df(sn.hi, sn.lo) && !zero) || hard_df(cs.hi, cs.lo);
-    y[0] = zero ? x : sn.hi;
-    y[1] = cs.hi;
+    const float yb = round_df(R.B.hi, R.B.lo, hb);
+    hard = R.tiny || ha || hb;  // sin takes one of A, B and cos the other
+    const float s0 = odd ? yb : ya, c0 = odd ? ya : yb;
+    y[0] = zero ? x : bitsf(fbits(s0) ^ trig_sin_sign(R.q, x));
+    y[1] = bitsf(fbits(c0) ^ trig_cos_sign(R.q));
   }
 }
 

@@ -304,6 +304,12 @@ for j in range(32):
 arr_d("CRM_SINCOS_T32_D", sc_d, "(sin, cos)(j pi/64), j = 0..31, doubles")
 arr_f("CRM_SINCOS_T32_DF", sc_f, "(sin hi, lo, cos hi, lo)(j pi/64) floats")
 arr_d("CRM_SINCOS_T32_DD", sc_dd, "(sin, cos)(j pi/64) as double-double")
+tn_f = []
+for j in range(32):
+    tn_f += split(mp.tan(mp.mpf(j) * mp.pi / 64), f, 2)
+arr_f("CRM_TAN_T32_DF", tn_f, "(tan hi, lo)(j pi/64), j = 0..31, floats")
+const_f("CRM_TAN_C5_F", f(mp.mpf(2) / 15), "2/15, the t^5 coefficient of tan t")
+const_f("CRM_TAN_C7_F", f(mp.mpf(17) / 315), "17/315, the t^7 coefficient of tan t")
 PIO64 = mp.pi / 64
 pp = split(PIO64, d, 2)
 const_d("CRM_PIO64_D_HI", pp[0])

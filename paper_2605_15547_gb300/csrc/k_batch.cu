@@ -13,7 +13,11 @@
 
 namespace crm {
 
-constexpr int BATCH_SMEM = 97 * 16;  // largest table (log family)
+constexpr int BATCH_SMEM = 97 * 16;  // largest binary32 table (log family)
+static_assert(FnLog<0>::tab_bytes<2>() <= BATCH_SMEM && FnTrig<TRIG_TAN>::tab_bytes<2>() <= BATCH_SMEM &&
+                  FnExp<0>::tab_bytes<2>() <= BATCH_SMEM && FnHyp<0>::tab_bytes<2>() <= BATCH_SMEM &&
+                  FnAtrig<0>::tab_bytes<2>() <= BATCH_SMEM,
+              "the mixed batch kernel's shared memory holds every binary32 table");
 
 template <class Fn, int FORM>
 CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t m, const unsigned char *sm,
@@ -60,15 +64,14 @@ CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t
         uint64_t v = base + (uint64_t)u * KBLOCK + threadIdx.x;
         bool act = v < nv;
         V y0, y1;
-        unsigned hm;
-        eval_vec<Fn, FORM>(xv[u], sm, y0, y1, hm);
-        hm = a.force_hard ? (1u << W) - 1u : hm;
-        hm = act ? hm : 0u;
+        bool h[W];
+        const bool any = (eval_vec<Fn, FORM>(xv[u], sm, y0, y1, h) || a.force_hard) && act;
         if (act) {
           st_stream(out4 + v, y0);
           if (Fn::NOUT == 2) st_stream(out4b + v, y1);
         }
-        if (__any_sync(0xFFFFFFFFu, hm != 0)) {
+        if (__any_sync(0xFFFFFFFFu, any)) {
+          const unsigned hm = act ? hard_mask<W>(h, a.force_hard != 0) : 0u;
           uint64_t ii[W], xb[W];
 #pragma unroll
           for (int j = 0; j < W; j++) {

@@ -170,28 +170,17 @@ CRM_DEV bool hard_d_to_f(double y, uint32_t D) {
   return (t - h + D) <= 2ull * D;
 }
 
-// Double-float tier: y = s + l (s = RN(y), so |l| <= ulp(s)/2) approximates v with
-// |v - y| <= eps_true |y|.  RN_f32(v) == s unless a midpoint next to s lies within
-// |l| + eps_true |s| of s.  The test lets the hardware's round-to-nearest measure the
-// distance to that midpoint, including the quarter-ulp gap below a power of two:
-// t = l + copysign(|s| * E, l), hard iff RN(s + t) != s.  E = 2^-36 covers an
-// eps_true <= 2^-37 plus the rounding of t (<= 2^-48 |s|), so a passing lane satisfies
-// |l| + eps_true |s| < distance to the midpoint, strictly.  Valid for normal s.
-CRM_DEV bool hard_df(float s, float l) {
-  float e = fabsf(s) * 0x1p-36f;
-  float t = l + bitsf(fbits(e) | (fbits(l) & 0x80000000u));
-  return (s + t) != s;
-}
-
-// The same test on a pair that need not be normalised, returning the result: y = s + r
-// (s normal, |r| <= 2^-14 |s|) approximates v with |v - y| <= eps_true |y|, eps_true <=
-// 2^-37.  With e = 2^-36 |s| (exact), a+ = RN(r + e) and a- = RN(r - e) lie outside
+// Double-float tier: y = s + r (s normal, |r| <= 2^-14 |s|, the pair need not be
+// normalised) approximates v with |v - y| <= eps_true |y|, eps_true <= 2^-37.  With
+// e = 2^-36 |s| (exact), a+ = RN(r + e) and a- = RN(r - e) lie outside
 // [r - eps_true |y|, r + eps_true |y|]: their roundings cost at most 2^-24 (|r| + e)
 // < 2^-37.9 |s|, and eps_true |y| <= 2^-37 (1 + 2^-14) |s|, together below e.  So
 // s + a- <= v <= s + a+, and as round-to-nearest is monotone, RN(s + a-) == RN(s + a+)
-// implies that both equal RN(v); otherwise the lane is hard.  When the lane is easy the
-// result is RN(s + r), the value the normalised pair would give.  Six operations against
-// eight for renormalisation plus hard_df; NaN in s makes the lane hard, as there.
+// implies that both equal RN(v): the paper's comparison of the roundings of y - e and
+// y + e (Sec. II.B), with the two ends formed from the unnormalised pair.  Otherwise
+// the lane is hard.  An easy lane's result is RN(s + r), the value a normalised pair
+// would give; a NaN in s makes the lane hard.  Six operations; renormalising the pair
+// and testing the distance to the nearest midpoint would take eight.
 CRM_DEV float round_df(float s, float r, bool &hard) {
   const float e = fabsf(s) * 0x1p-36f;
   const float hi = s + (r + e), lo = s + (r - e);

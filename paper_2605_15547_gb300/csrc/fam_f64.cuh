@@ -21,8 +21,10 @@ namespace crm {
 
 // ------------------------------------------------------------------ rounding test (binary64)
 // y = s + t (|t| <= ulp(s)/2) approximates v with |v - y| <= eps |s|; RN64(v) = s unless
-// a midpoint next to s lies within |t| + eps |s|: tested with the hardware's rounding as
-// in hard_df.  E = 2^-98 covers eps <= 2^-100 plus the rounding of the sum.
+// a midpoint next to s lies within |t| + eps |s|, which the hardware's rounding measures:
+// with u = t + copysign(E |s|, t), the lane is hard iff RN(s + u) != s (the quarter-ulp
+// gap below a power of two included).  E = 2^-98 covers eps <= 2^-100 plus the rounding
+// of the sum.
 CRM_DEV bool hard_dd(double s, double t) {
   double e = fabs(s) * 0x1p-98;
   double u = t + copysign(e, t);

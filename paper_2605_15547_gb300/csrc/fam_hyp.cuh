@@ -152,7 +152,10 @@ CRM_DEV DFY expm1_df_core(float x, const float4 *T64U) {
   float tql = fma_(T.x, Qh, -tq);
   tql = fma_(T.x, Ql, tql);
   tql = fma_(T.y, Qh, tql);
-  Pair<float> s1 = two_sum(c.hi, u);
+  // T - 2^-k is 0 (j = k = 0) or at least 0.0107 T in magnitude (2^(j/64) - 1 for k = 0,
+  // 2 - 2^(j/64) for k = -1, more for other k), while |U g| <= T ln2 (2^-7 + 2^-16) <
+  // 0.0055 T: Fast2Sum applies
+  Pair<float> s1 = fast_two_sum(c.hi, u);
   Pair<float> s2 = fast_two_sum(s1.hi, tq);  // |s1| >= |tq| (see above)
   float lo = (s1.lo + s2.lo) + (cl + (ul + tql));
   return {s2.hi, lo, k};

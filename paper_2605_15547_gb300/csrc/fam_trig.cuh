@@ -180,12 +180,13 @@ CRM_DEV void trig_reduce_df(float x, const uint4 *PW, Pair<float> &t, int &N7, b
   bool small = ax < 0x1p-6f;
   uint32_t r[4];
   trig_window_mul3(small ? 1.0f : ax, PW, r);
-  uint32_t Fh = ((r[2] & 0x01FFFFFFu) << 7) | (r[1] >> 25);
-  uint32_t Fl = (r[1] << 7) | (r[0] >> 25);
-  N7 = (int)(((r[2] >> 25) + (Fh >> 31)) & 127u);
+  // F = the 64 bits below the top 7 of r[2]: F = (Fh, Fl); N7 = the top 7 bits rounded
+  // by F's leading bit, modulo 128 (the 32-bit sum wraps exactly there)
+  const uint32_t Fh = __funnelshift_l(r[1], r[2], 7), Fl = __funnelshift_l(r[0], r[1], 7);
+  N7 = (int)((r[2] + 0x01000000u) >> 25);
   uint32_t Ph = Fh ^ 0x80000000u;
   uint32_t c0 = Ph >> 9;
-  uint32_t c1 = ((Ph & 0x1FFu) << 14) | (Fl >> 18);
+  uint32_t c1 = __funnelshift_r(Fl, Ph, 18) & 0x007FFFFFu;
   uint32_t c2 = Fl & 0x3FFFFu;
   float f0 = bitsf(0x4B000000u | c0) - 0x1p23f;
   float f1 = bitsf(0x4B000000u | c1) - 0x1p23f;

@@ -436,7 +436,9 @@ def main():
         e2e = {"value": n_elems / (t1 - t0) / 1e9, "unit": "Gelem/s",
                "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in xs)),
                "d2h_bytes_per_step": int(sum(y.numel() * y.element_size() for y in ys)),
-               "note": "crm_eval_host: page-locked host in/out, chunked copies overlapped with compute"}
+               "note": "crm_eval_host on page-locked host in/out: the kernels read and write them in "
+                       "place over the host link (NVLink-C2C); every input and output byte crosses it "
+                       "inside the timed region"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -106,9 +106,14 @@ int crm_eval(int func_id, int dtype, const void *in, void *out, uint64_t n, void
 int crm_eval_form(int func_id, int dtype, int form, const void *in, void *out, uint64_t n,
                   void *stream);
 
-/* Host-buffer variant: in/out are host pointers (page-locked for full speed).  Copies
+/* Host-buffer variant: in/out are host pointers.  When both are page-locked memory that
+   the device addresses directly (cudaHostAlloc / cudaHostRegister on a system with
+   unified addressing, as on GB300), the kernels read and write them in place over the
+   host link, with no staging copies.  Otherwise (pageable memory) the library copies
    chunks to a library-owned device staging area, evaluates and copies back, overlapping
-   the transfers with compute; returns after the results are in `out` (synchronous). */
+   the transfers with compute.  Either way the call returns after the results are in
+   `out` (synchronous), with the same bits as crm_eval_form on device copies.  The paper
+   has no counterpart (its arrays live in the CPU's memory). */
 int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, uint64_t n,
                   void *stream);
 

@@ -470,6 +470,20 @@ int crm_stats_reset(void *stream) {
   return e == cudaSuccess ? CRM_OK : cuda_fail(e);
 }
 
+// Page-locked host memory that the device addresses directly (cudaHostAlloc on a system
+// with unified addressing reports it as host memory with a device pointer): the device
+// address is returned in dp.  Anything else (pageable memory, device memory) is false.
+static bool device_mapped_host(const void *p, void **dp) {
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+    (void)cudaGetLastError();  // a failed query leaves a (non-sticky) last error: clear it
+    return false;
+  }
+  if (pa.type != cudaMemoryTypeHost || pa.devicePointer == nullptr) return false;
+  *dp = pa.devicePointer;
+  return true;
+}
+
 int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, uint64_t n, void *stream) {
   ensure_init();
   if (func_id < 0 || func_id >= CRM_NUM_FUNCS) return CRM_ERR_FUNC;
@@ -479,6 +493,18 @@ int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, u
   if (resolve_form(g_table[func_id], form) < 0) return CRM_ERR_FORM;
   if (n == 0) return CRM_OK;
   if (!in || !out) return CRM_ERR_NULL;
+  void *din = nullptr, *dout = nullptr;
+  if (device_mapped_host(in, &din) && device_mapped_host(out, &dout)) {
+    // both buffers mapped: the kernels stream them in place over the host link (on
+    // GB300, NVLink-C2C), without staging copies
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = check_args(func_id, dtype, din, dout, n);
+    if (st) return st;
+    st = enqueue(func_id, form, din, dout, n, s, 0);
+    if (st) return st;
+    cudaError_t e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? CRM_OK : cuda_fail(e);
+  }
   return host_pipeline(func_id, form, in, out, n, (cudaStream_t)stream);
 }
 

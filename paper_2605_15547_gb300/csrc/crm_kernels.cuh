@@ -190,29 +190,35 @@ template <int W> CRM_DEV unsigned hard_mask(const bool *h, bool force) {
   return hm;
 }
 
+// The vector loop addresses vectors with 32-bit indices inside segments of at most
+// 2^31 vectors (an array below 2^33 binary32 elements is one segment): one add, compare
+// and wide multiply-add per vector instead of their 64-bit pairs.  Queue indices stay
+// 64-bit (rare path).
+constexpr uint64_t KSEG = 1ull << 31;
+
 // Loads the UNROLL vectors of one iteration (zero past the end).
 template <class V, int UNROLL, int BS>
-CRM_DEV void load_vecs(V *xv, const V *in4, uint64_t base, uint64_t nvec) {
+CRM_DEV void load_vecs(V *xv, const V *in4, uint32_t base, uint32_t nv) {
 #pragma unroll
   for (int u = 0; u < UNROLL; u++) {
-    uint64_t v = base + (uint64_t)u * BS + threadIdx.x;
-    xv[u] = v < nvec ? ld_stream(in4 + v) : V();
+    const uint32_t v = base + (uint32_t)(u * BS) + threadIdx.x;
+    xv[u] = v < nv ? ld_stream(in4 + v) : V();
   }
 }
 
-// Evaluates and stores the UNROLL vectors of one iteration, queueing the hard lanes.
+// Evaluates and stores the UNROLL vectors of one iteration of a segment (nv vectors from
+// vector `seg` of the array; out4, out4b point at the segment), queueing the hard lanes.
 template <class Fn, int FORM, int UNROLL, int BS, bool WIDE>
-CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T, WIDE>::V *xv, uint64_t base, const unsigned char *sm,
-                       const KArgs &a) {
+CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T, WIDE>::V *xv, uint32_t base, uint32_t nv,
+                       typename VecOf<typename Fn::T, WIDE>::V *out4, typename VecOf<typename Fn::T, WIDE>::V *out4b,
+                       uint64_t seg, const unsigned char *sm, const KArgs &a) {
   using T = typename Fn::T;
   using V = typename VecOf<T, WIDE>::V;
   constexpr int W = VecOf<T, WIDE>::W;
-  V *out4 = (V *)((T *)a.out + a.head);
-  V *out4b = (V *)((T *)a.out + a.n + a.head);  // second output (sincos)
 #pragma unroll
   for (int u = 0; u < UNROLL; u++) {
-    uint64_t v = base + (uint64_t)u * BS + threadIdx.x;
-    bool act = v < a.nvec;
+    const uint32_t v = base + (uint32_t)(u * BS) + threadIdx.x;
+    bool act = v < nv;
     V y0, y1;
     bool h[W];
     const bool any = (eval_vec<Fn, FORM>(xv[u], sm, y0, y1, h) || a.force_hard) && act;
@@ -225,7 +231,7 @@ CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T, WIDE>::V *xv, uint64
       uint64_t ii[W], xb[W];
 #pragma unroll
       for (int j = 0; j < W; j++) {
-        ii[j] = a.head + v * W + j;
+        ii[j] = a.head + (seg + v) * W + j;
         xb[j] = xbits_of(vget(xv[u], j));
       }
       unsigned over = push_hard<W>(hm, ii, xb, a);
@@ -250,24 +256,31 @@ CRM_DEV void main_body(const KArgs &a) {
   __shared__ __align__(16) unsigned char sm[(Fn::template tab_bytes<FORM>() > 0) ? Fn::template tab_bytes<FORM>() : 16];
   load_tab<Fn, FORM>(sm);
 
-  const V *in4 = (const V *)((const T *)a.in + a.head);
-  const uint64_t stride = (uint64_t)gridDim.x * BS * UNROLL;
-  uint64_t base = (uint64_t)blockIdx.x * BS * UNROLL;
-  if (PF) {
-    V xv[UNROLL];
-    load_vecs<V, UNROLL, BS>(xv, in4, base, a.nvec);
-    for (; base < a.nvec; base += stride) {
-      V nx[UNROLL];
-      load_vecs<V, UNROLL, BS>(nx, in4, base + stride, a.nvec);
-      eval_vecs<Fn, FORM, UNROLL, BS, WIDE>(xv, base, sm, a);
-#pragma unroll
-      for (int u = 0; u < UNROLL; u++) xv[u] = nx[u];
-    }
-  } else {
-    for (; base < a.nvec; base += stride) {
+  // base < nv <= 2^31 and stride = grid * BS * UNROLL < 2^26 (at most one wave of
+  // resident blocks): base + stride stays below 2^32
+  const uint32_t stride = gridDim.x * (uint32_t)(BS * UNROLL);
+  for (uint64_t seg = 0; seg < a.nvec; seg += KSEG) {
+    const uint32_t nv = (uint32_t)(a.nvec - seg < KSEG ? a.nvec - seg : KSEG);  // >= 1
+    const V *in4 = (const V *)((const T *)a.in + a.head) + seg;
+    V *out4 = (V *)((T *)a.out + a.head) + seg;
+    V *out4b = (V *)((T *)a.out + a.n + a.head) + seg;  // second output (sincos)
+    uint32_t base = blockIdx.x * (uint32_t)(BS * UNROLL);
+    if (PF) {
       V xv[UNROLL];
-      load_vecs<V, UNROLL, BS>(xv, in4, base, a.nvec);
-      eval_vecs<Fn, FORM, UNROLL, BS, WIDE>(xv, base, sm, a);
+      load_vecs<V, UNROLL, BS>(xv, in4, base, nv);
+      for (; base < nv; base += stride) {
+        V nx[UNROLL];
+        load_vecs<V, UNROLL, BS>(nx, in4, base + stride, nv);
+        eval_vecs<Fn, FORM, UNROLL, BS, WIDE>(xv, base, nv, out4, out4b, seg, sm, a);
+#pragma unroll
+        for (int u = 0; u < UNROLL; u++) xv[u] = nx[u];
+      }
+    } else {
+      for (; base < nv; base += stride) {
+        V xv[UNROLL];
+        load_vecs<V, UNROLL, BS>(xv, in4, base, nv);
+        eval_vecs<Fn, FORM, UNROLL, BS, WIDE>(xv, base, nv, out4, out4b, seg, sm, a);
+      }
     }
   }
   // scalar part: the head [0, head) and the tail [head + W nvec, n)

@@ -84,3 +84,30 @@ def test_batch_workload_sampled():
         f, x, y = items[i]
         yy = y.view(2, -1) if f == "sincosf" else y
         check_sampled(f, x, yy, srng)
+
+
+def test_array_beyond_2p33_elements():
+    """The vector loop works in segments of 2^31 vectors (2^33 binary32 elements): an
+    array one segment plus a ragged tail long (64 GiB in and out on the device), checked
+    on both sides of the segment boundary, at both ends and at random positions."""
+    n = (1 << 33) + 4101
+    free, _ = torch.cuda.mem_get_info()
+    if free < 2 * 4 * n + (4 << 30):
+        pytest.skip("not enough device memory for a 2^33-element array pair")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(W.seed_for(9, 0))
+    x = torch.empty(n, dtype=torch.float32, device="cuda")
+    x.uniform_(-87.0, 88.0, generator=gen)
+    y = torch.empty_like(x)
+    crm.eval_into("expf", x, y)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(9)
+    b = 1 << 33
+    idx = np.unique(np.r_[np.arange(b - 300, b + 300), np.arange(n - 64, n), np.arange(64),
+                          rng.integers(0, n, SAMPLE)])
+    it = torch.from_numpy(idx).cuda()
+    xs = x[it].cpu().numpy().view(np.uint32)
+    got = y[it].cpu().numpy().view(np.uint32)
+    del x, y
+    torch.cuda.empty_cache()
+    assert np.array_equal(got, O.eval_bits("expf", xs))

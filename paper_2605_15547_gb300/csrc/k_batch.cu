@@ -40,7 +40,7 @@ CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t
   constexpr int W = VecOf<T>::W;
   if ((d.flags & 1) && (off % W) == 0) {
     // vectors: 16-byte aligned array, tile offset a multiple of the vector width
-    const uint64_t nv = m / W;
+    const uint32_t nv = (uint32_t)(m / W);  // a tile is at most 2^16 elements: 32-bit indices
     const V *in4 = (const V *)(in + off);
     V *out4 = (V *)(out + off);
     V *out4b = (V *)(out + d.n + off);
@@ -49,19 +49,19 @@ CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t
     V nx[2];
 #pragma unroll
     for (int u = 0; u < 2; u++) {
-      uint64_t v = (uint64_t)u * KBLOCK + threadIdx.x;
+      const uint32_t v = (uint32_t)(u * KBLOCK) + threadIdx.x;
       nx[u] = v < nv ? ld_stream(in4 + v) : V();
     }
-    for (uint64_t base = 0; base < nv; base += 2 * KBLOCK) {
+    for (uint32_t base = 0; base < nv; base += 2 * KBLOCK) {
       V xv[2] = {nx[0], nx[1]};
 #pragma unroll
       for (int u = 0; u < 2; u++) {
-        uint64_t v = base + 2 * KBLOCK + (uint64_t)u * KBLOCK + threadIdx.x;
+        const uint32_t v = base + (uint32_t)(2 * KBLOCK + u * KBLOCK) + threadIdx.x;
         nx[u] = v < nv ? ld_stream(in4 + v) : V();
       }
 #pragma unroll
       for (int u = 0; u < 2; u++) {
-        uint64_t v = base + (uint64_t)u * KBLOCK + threadIdx.x;
+        const uint32_t v = base + (uint32_t)(u * KBLOCK) + threadIdx.x;
         bool act = v < nv;
         V y0, y1;
         bool h[W];
@@ -75,7 +75,7 @@ CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t
           uint64_t ii[W], xb[W];
 #pragma unroll
           for (int j = 0; j < W; j++) {
-            ii[j] = off + v * W + j;
+            ii[j] = off + (uint64_t)v * W + j;
             xb[j] = xbits_of(vget(xv[u], j));
           }
           unsigned over = push_hard<W>(hm, ii, xb, a);
@@ -87,7 +87,7 @@ CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t
         }
       }
     }
-    off += nv * W;
+    off += (uint64_t)nv * W;
     m -= nv * W;
   }
   // scalar elements (unaligned arrays and the last partial vector)

@@ -32,7 +32,8 @@ template <int KIND> struct FnExp {
 template <int KIND> struct FnLog {
   using T = float;
   static constexpr int NOUT = 1;
-  template <int FORM> static constexpr int tab_bytes() { return 97 * 16; }
+  // plain: 97 (1/c_j, log c_j) doubles; double-float: 193 (R_j, 0, -log_b R_j) float4s
+  template <int FORM> static constexpr int tab_bytes() { return FORM == 1 ? 97 * 16 : 193 * 16; }
   template <int FORM> CRM_DEV static void load(unsigned char *sm) {
     copy_tab(sm, FORM == 1 ? (const void *)CRM_LN_T97_D : (const void *)log_tab_df<KIND>(), tab_bytes<FORM>());
   }

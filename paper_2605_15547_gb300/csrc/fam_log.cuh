@@ -2,10 +2,11 @@
 //
 // Following the paper's log2f scheme (Fig. 2, Sec. II.A): split x = 2^e m with m in
 // [3/4, 3/2) (so that the result near x = 1 comes from the polynomial alone, without
-// cancellation), pick a table point c_j = j/128 nearest to m, and write
-//     log x = e log 2 + log c_j + log1p(r),   r = (m - c_j)/c_j,   |r| <= 2^-7.58,
-// with (1/c_j, log c_j) from a 97-entry table and log1p(r) by its Taylor polynomial.
-// log2 and log10 use tables of log2 c_j / log10 c_j and scale log1p(r) by 1/ln 2 or
+// cancellation), pick a table point near m, and write log x = e log 2 + log c + log1p(r).
+// The FP64 and double-double tiers use c_j = j/128 and r = (m - c_j)/c_j, |r| <= 2^-7.58,
+// with (1/c_j, log c_j) from a 97-entry table; the double-float tier uses a short
+// reciprocal R_j of j/256 (the paper's cr_log idea, Sec. II.B), so that r = m R_j - 1 is
+// exact.  log2 and log10 use tables of log2 / log10 and scale log1p(r) by 1/ln 2 or
 // 1/ln 10.  log1p(x) evaluates the polynomial on x itself for |x| < 2^-7 and otherwise
 // works on u = 1 + x = uh + ul (exact pair), adding ul/uh.
 #pragma once
@@ -29,7 +30,7 @@ template <> struct LogK<3> : LogK<0> {};
 
 // Table per kind: log1p uses the natural-log table.
 template <int KIND> CRM_DEV const float *log_tab_df() {
-  return KIND == 1 ? CRM_LOG2_T97_DF : (KIND == 2 ? CRM_LOG10_T97_DF : CRM_LN_T97_DF);
+  return KIND == 1 ? CRM_LOG2_T193R_DF : (KIND == 2 ? CRM_LOG10_T193R_DF : CRM_LN_T193R_DF);
 }
 template <int KIND> CRM_DEV const double *log_tab_dd() {
   return KIND == 1 ? CRM_LOG2_T97_DD : (KIND == 2 ? CRM_LOG10_T97_DD : CRM_LN_T97_DD);
@@ -123,45 +124,43 @@ template <int KIND> CRM_DEV float log_plain(float x, const double2 *T97, bool &h
 }
 
 // ------------------------------------------------------------------ double-float tier
-// Decomposition in binary32 (subnormal inputs are scaled by 2^24 first),
-// j = rint(128 m), d = m - c exact (Sterbenz), r = d (1/c) as a float pair (exact
-// product split by FMA plus d * (1/c)_lo).  log1p(r) = r - r^2/2 + r^3 (1/3 - r/4
-// + r^2/5): rh - rh^2/2 by Fast2Sum on the exact square (split by FMA), the r^3 tail in
-// float.  For log2 / log10 the pair is multiplied by the float pair 1/ln 2 or 1/ln 10.
-// B = e K_hi + L_hi by one FMA (e K_hi is exact: K_hi has 16 significant bits) with its
-// rounding error recovered exactly as in Fast2Sum (e == 0, or |e K_hi| > |L|), then
-// Fast2Sum(B, q); the sum goes to the rounding test unnormalised.  Error budget, relative
-// to the result:
-//   r^6/6 remainder 2^-48.2 abs, tail rounding 2^-46.4 abs, pair products and the
-//   1/c, L and K splits <= 2^-46 abs, with |result| >= 2^-8 unless e = 0 and c = 1 (then
-//   all terms scale with r and the bound is 2^-38.5 relative); e K_lo rounding and the K
-//   split <= 2^-42 relative.  Total < 2^-38; the test allows 2^-37 (round_df: the low
-//   word is below 2^-15 of the high one, |result| >= 2^-8.6 when B != 0).
+// Decomposition in binary32 (subnormal inputs are scaled by 2^24 first), x = 2^e m with
+// m in [3/4, 3/2), j = rint(256 m), and R_j = 1/(j/256) rounded to 9 significant bits
+// (a 193-entry table with -log_b R_j as a float pair): r = m R_j - 1 is one exact FMA
+// (m R_j is a multiple of 2^-32 and |r| <= 2^-8.008 < 2^-8), and
+//   log_b x = e log_b 2 - log_b R_j + log_b(1 + r)
+// (the reduction of the paper's cr_log, Sec. II.B, with a short reciprocal).
+// log1p(r) = r - r^2/2 + r^3 (1/3 - r/4 + r^2/5): r - r^2/2 by Fast2Sum on the exact
+// square (split by FMA), the r^3 tail in float.  For log2 / log10 the pair is multiplied
+// by the float pair 1/ln 2 or 1/ln 10.  B = e K_hi - log_b R_j by one FMA (e K_hi is exact:
+// K_hi has 16 significant bits) with its rounding error recovered exactly as in Fast2Sum
+// (e == 0, or |e K_hi| > |log_b R_j|), then Fast2Sum(B, q); the sum goes to the rounding
+// test unnormalised.  Error budget, relative to the result:
+//   r^6/6 remainder 2^-50.6 abs, tail rounding 2^-49.6 abs, the table pair and the K split
+//   <= 2^-48 abs, with |result| >= 2^-9 unless e = 0 and j = 256 (then R_j = 1, all terms
+//   scale with r and the bound is 2^-40 relative); e K_lo rounding and the K split
+//   <= 2^-42 relative.  Total < 2^-39; the test allows 2^-37 (round_df: the low word is
+//   below 2^-15 of the high one).
 //
 // us = 2^(e - eadj) m for a positive normal float us (any bit pattern gives an in-range
 // table index; the result is then meaningless and discarded), plus, for log1p, the low
 // word ul of 1 + x and the direct path for |x| < 2^-7.  Returns the unnormalised sum.
 template <int KIND>
-CRM_DEV Pair<float> log_df_core(float us, int eadj, float ul, bool pathA, float x, const float4 *T97) {
+CRM_DEV Pair<float> log_df_core(float us, int eadj, float ul, bool pathA, float x, const float4 *T193) {
   using K = LogK<KIND>;
   // us = 2^e m, m in [3/4, 3/2), from one integer subtraction: the exponent field of
   // us / (3/4) rounded down is floor(log2(us / (3/4)))
   const uint32_t b = fbits(us);
   const int32_t ee = (int32_t)(b - 0x3F400000u) >> 23;
   const float m = bitsf(b - ((uint32_t)ee << 23));
-  float sh = fma_(m, 128.0f, CRM_SHIFTER_F);
-  int j = (int)(fbits(sh) - fbits(CRM_SHIFTER_F));
-  float d = fma_(sh - CRM_SHIFTER_F, -0.0078125f, m);  // m - j/128, exact
-  float4 T = T97[j - 96];
-  float rh = d * T.x;
-  float rl = fma_(d, T.x, -rh);
-  rl = fma_(d, T.y, rl);
+  const float sh = fma_(m, 256.0f, CRM_SHIFTER_F);
+  const float4 T = T193[fbits(sh) - (fbits(CRM_SHIFTER_F) + 192u)];  // (R_j, 0, L hi, lo)
+  float rh = fma_(m, T.x, -1.0f);  // exact
   float Lh = T.z, Ll = T.w, ef = (float)(ee + eadj);
   float t = 0.0f;
   if (KIND == 3) {
     t = __fdividef(ul, us);  // ul/uh with |ul| <= 2^-24 uh: relative 2^-21 suffices
     rh = pathA ? x : rh;
-    rl = pathA ? 0.0f : rl;
     Lh = pathA ? 0.0f : Lh;
     Ll = pathA ? 0.0f : Ll;
     ef = pathA ? 0.0f : ef;
@@ -175,9 +174,7 @@ CRM_DEV Pair<float> log_df_core(float us, int eadj, float ul, bool pathA, float 
   float P = (h2 * rh) * q3;
   float s = fma_(h2, -0.5f, rh);
   float z = fma_(h2, -0.5f, rh - s);
-  float rest = fma_(-rh, rl, rl);
-  rest = fma_(h2l, -0.5f, rest);
-  rest = rest + P;
+  float rest = fma_(h2l, -0.5f, P);
   rest = rest + (KIND == 3 ? z + t : z);
   float qh = s, ql = rest;
   if (KIND == 1 || KIND == 2) {
@@ -193,13 +190,13 @@ CRM_DEV Pair<float> log_df_core(float us, int eadj, float ul, bool pathA, float 
   float Bz = Lh + fma_(ef, K::KH, -B);
   float Bl = Bz + fma_(ef, K::KL, Ll);
   // |B| > |qh| unless B = 0: with e != 0, |e K + L| >= 0.125 (log10; more for ln, log2);
-  // with e = 0, |L_j| >= |log_b(1 +- 1/128)| > |log_b(1 + r)| since |r| <= 2^-8/0.75; so
-  // Fast2Sum is exact here
+  // with e = 0 and j != 256, |log_b R_j| >= 1.97 |log_b(1 + r)| (checked over every j when
+  // the table is generated); so Fast2Sum is exact here
   Pair<float> S = fast_two_sum(B, qh);
   return {S.hi, S.lo + (Bl + ql)};
 }
 
-template <int KIND> CRM_DEV float log_df(float x, const float4 *T97, bool &hard) {
+template <int KIND> CRM_DEV float log_df(float x, const float4 *T193, bool &hard) {
   const bool ok = log_ok<KIND>(x);
   float us = x, ul = 0.0f;
   int eadj = 0;
@@ -214,7 +211,7 @@ template <int KIND> CRM_DEV float log_df(float x, const float4 *T97, bool &hard)
     us = sub ? x * 0x1p24f : x;
     eadj = sub ? -24 : 0;
   }
-  Pair<float> y = log_df_core<KIND>(us, eadj, ul, pathA, x, T97);
+  Pair<float> y = log_df_core<KIND>(us, eadj, ul, pathA, x, T193);
   if (__builtin_expect(ok, 1)) return round_df(y.hi, y.lo, hard);
   hard = false;  // NaN, zero, negative, infinite (rare: a branch, not selects)
   return special_log<KIND>(x);

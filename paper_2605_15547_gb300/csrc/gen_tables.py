@@ -204,17 +204,39 @@ emit("// ===== r = (m - c_j)/c_j, |r| <= 2^-7.58; entry j-96                    
 for kind, base in (("LN", None), ("LOG2", 2), ("LOG10", 10)):
     def lg(v):
         return mp.log(v) if base is None else mp.log(v) / mp.log(base)
-    tf, td, tdd = [], [], []
+    td, tdd = [], []
     for j in range(96, 193):
         c = mp.mpf(j) / 128
         rc = 1 / c
         L = lg(c)
-        tf += split(rc, f, 2) + split(L, f, 2)
         td += [d(rc), d(L)]
         tdd += split(rc, d, 2) + split(L, d, 2)
-    arr_f(f"CRM_{kind}_T97_DF", tf, f"(1/c_j hi, lo, {kind.lower()}(c_j) hi, lo) floats")
     arr_d(f"CRM_{kind}_T97_D", td, f"(1/c_j, {kind.lower()}(c_j)) doubles")
     arr_d(f"CRM_{kind}_T97_DD", tdd, f"(1/c_j, {kind.lower()}(c_j)) as double-double")
+# Double-float tier: c_j = j/256 (j = round(256 m), 192..384) and R_j = 1/c_j rounded to 9
+# significant bits, so that r = m R_j - 1 is one exact FMA: m R_j is a multiple of 2^-32
+# (m has 24 significant bits, R_j 9, and R_j >= 1 exactly when m < 1) and |r| < 2^-8, so r
+# is an integer below 2^24 times 2^-32; entry j-192 is (R_j, 0, -log_b(R_j) hi, lo)
+emit("// ===== log family, double-float tier: R_j = 1/(j/256) to 9 bits, j = round(256 m) in  =====")
+emit("// ===== 192..384, r = m R_j - 1 exact, log x = e log 2 - log R_j + log1p(r); entry j-192 =====")
+rmax = mp.mpf(0)
+for kind, base in (("LN", None), ("LOG2", 2), ("LOG10", 10)):
+    def lg(v):
+        return mp.log(v) if base is None else mp.log(v) / mp.log(base)
+    tf = []
+    for j in range(192, 385):
+        R = rnd(mp.mpf(256) / j, 9)
+        # |r| over m in [(j - 1/2)/256, (j + 1/2)/256] intersected with [3/4, 3/2)
+        lo_m = max(mp.mpf(j) - mp.mpf(1) / 2, 192) / 256
+        hi_m = min(mp.mpf(j) + mp.mpf(1) / 2, 384) / 256
+        rmax = max(rmax, abs(lo_m * R - 1), abs(hi_m * R - 1))
+        if j != 256:  # Fast2Sum(B, q) with e = 0 needs |log R_j| >= |log1p(r)|
+            q = max(abs(mp.log1p(lo_m * R - 1)), abs(mp.log1p(hi_m * R - 1)))
+            assert abs(mp.log(R)) >= mp.mpf("1.97") * q, j
+        L = -lg(R)
+        tf += [f(R), mp.mpf(0)] + split(L, f, 2)
+    arr_f(f"CRM_{kind}_T193R_DF", tf, f"(R_j, 0, -{kind.lower()}(R_j) hi, lo) floats, R_j 9 bits")
+assert rmax < mp.mpf(2) ** -8, rmax  # r exact (see above); max |r| = 2^-8.008
 LOG10_2 = mp.log(2) / mp.log(10)
 for nm, v in (("LN2", LN2), ("LOG10_2", LOG10_2)):
     hi = rnd(v, 16)

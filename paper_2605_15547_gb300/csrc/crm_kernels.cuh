@@ -309,8 +309,15 @@ CRM_DEV void main_body(const KArgs &a) {
   }
 }
 
+// Binary32 kernels are held to 64 registers (two 512-thread blocks per SM): their fast
+// path needs 47-57, and what would raise the count is the rarely called inline slow path
+// (queue overflow), which may spill instead.  The binary64 fixed-point kernels keep the
+// compiler's choice.
+template <class Fn> constexpr int min_blocks_64regs(int bs) {
+  return sizeof(typename Fn::T) == 4 ? 65536 / (bs * 64) : 1;
+}
 template <class Fn, int FORM, int UNROLL, int BS, bool PF, bool WIDE = false>
-__global__ void __launch_bounds__(BS) k_main(KArgs a) {
+__global__ void __launch_bounds__(BS, min_blocks_64regs<Fn>(BS)) k_main(KArgs a) {
   main_body<Fn, FORM, UNROLL, BS, PF, WIDE>(a);
 }
 // The same with a register cap: at least MINB blocks of BS threads resident per SM.

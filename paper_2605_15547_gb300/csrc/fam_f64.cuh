@@ -267,10 +267,9 @@ CRM_DEV bool logd_special_bits(uint64_t b, double &r) {
   return nan || zero || neg || inf;
 }
 
-CRM_DEV double logd_int(double x, const ulonglong2 *LT, const unsigned short *RT, bool &hard) {
-  double rs;
-  const bool sp = logd_special_bits(dbits(x), rs);
-  const uint64_t b = sp ? 0x4000000000000000ull : dbits(x);  // 2.0 on the special lanes
+// Z = log x in Q116 (two's complement) for the bit pattern b of a positive finite double
+// (normal or subnormal), with its error bound in units of 2^-116 in err.
+CRM_DEV U128 logz_q116(uint64_t b, const ulonglong2 *LT, const unsigned short *RT, uint64_t &err) {
   int E = (int)(b >> 52);
   uint64_t M = b & 0x000FFFFFFFFFFFFFull;
   if (E == 0) {  // subnormal: shift the leading bit to position 52
@@ -315,7 +314,16 @@ CRM_DEV double logd_int(double x, const ulonglong2 *LT, const unsigned short *RT
   U128 eL = {p0.lo, CRM_LOGI_LN2_HI * ae + p0.hi};
   if (e < 0) eL = neg128(eL);
   const ulonglong2 Lj = LT[j - 192];
-  const U128 Z = add128(add128(eL, {Lj.x, Lj.y}), add128(rQ, rS));
+  err = 16ull + ae + (ar >> 24);
+  return add128(add128(eL, {Lj.x, Lj.y}), add128(rQ, rS));
+}
+
+CRM_DEV double logd_int(double x, const ulonglong2 *LT, const unsigned short *RT, bool &hard) {
+  double rs;
+  const bool sp = logd_special_bits(dbits(x), rs);
+  const uint64_t b = sp ? 0x4000000000000000ull : dbits(x);  // 2.0 on the special lanes
+  uint64_t err;
+  const U128 Z = logz_q116(b, LT, RT, err);
   // round |Z| (Q116) to 53 bits
   const bool zneg = (int64_t)Z.hi < 0;
   const U128 A = zneg ? neg128(Z) : Z;
@@ -334,7 +342,6 @@ CRM_DEV double logd_int(double x, const ulonglong2 *LT, const unsigned short *RT
     half = sh == 64 ? U128{1ull << 63, 0ull} : U128{0ull, 1ull << (sh - 65)};
   }
   const U128 dlt = sub128(rem, half);
-  const uint64_t err = 16ull + ae + (ar >> 24);
   const bool near = (dlt.hi == 0 && dlt.lo <= err) || (dlt.hi == ~0ull && dlt.lo >= 0ull - err);
   const bool up = (int64_t)dlt.hi > 0 || (dlt.hi == 0 && dlt.lo != 0);
   const uint64_t bits = ((uint64_t)(sh + 958) << 52) + mant + (up ? 1ull : 0ull);

@@ -12,6 +12,7 @@
 #pragma once
 #include "crm_common.cuh"
 #include "crm_tables.h"
+#include "fam_f64.cuh"
 
 namespace crm {
 
@@ -265,10 +266,72 @@ template <int KIND> CRM_DEV float log_dd(float x, bool &hard) {
   return round_dd_to_f(y.hi, y.lo, LOG_DD_EPS * fabs(y.hi), hard);
 }
 
+// ------------------------------------------------------------------ FP64-free middle tier
+// logf, log2f, log10f of a positive finite x: the binary64 path's fixed-point core
+// (logz_q116: Z = ln x in Q116 with an error bound, 128-bit integer arithmetic, Sec. II.B's
+// short-reciprocal reduction) on the exact binary64 value of x, times 1/ln 2 or 1/ln 10
+// in Q126 for log2 / log10 (W = Z C 2^-126 truncated: the constant's rounding adds 2^-4 of
+// a unit, the truncations 1 unit, and Z's error grows by C <= 1.443), then rounded to 24
+// bits with an integer test: hard only when the discarded part lies within the bound of
+// half an ulp (|log_b x| >= 2^-25 for x != 1, so the bound, a few hundred units of
+// 2^-116, is below 2^-70 of the result).  On GB300 the FP64 pipe runs one warp
+// instruction every few dozen cycles, so this tier replaces the FP64 tier for the lanes
+// the double-float test sends to the slow path.
+template <int KIND> CRM_DEV float logf_int(float x, bool &hard) {
+  uint64_t err;
+  const U128 Z = logz_q116(dbits((double)x), (const ulonglong2 *)CRM_LOGI_L, CRM_LOGI_R, err);
+  const bool neg = (int64_t)Z.hi < 0;
+  U128 A = neg ? neg128(Z) : Z;  // |Z| < 2^123
+  if (KIND == 1 || KIND == 2) {
+    const uint64_t ch = KIND == 1 ? CRM_LOGI_INV_LN2_Q126_HI : CRM_LOGI_INV_LN10_Q126_HI;
+    const uint64_t cl = KIND == 1 ? CRM_LOGI_INV_LN2_Q126_LO : CRM_LOGI_INV_LN10_Q126_LO;
+    // A C as 256 bits (limbs w0..w3), then W = A C >> 126
+    const U128 hh = mul64w(A.hi, ch), hl = mul64w(A.hi, cl), lh = mul64w(A.lo, ch);
+    const uint64_t ll_hi = __umul64hi(A.lo, cl);
+    U128 mid = add128(hl, lh);  // may carry into bit 128 of the middle sum
+    const uint64_t c1 = (mid.hi < hl.hi || (mid.hi == hl.hi && mid.lo < hl.lo)) ? 1ull : 0ull;
+    mid = add128_64(mid, ll_hi);
+    const uint64_t c2 = (mid.hi == 0 && mid.lo < ll_hi) ? 1ull : 0ull;
+    // limbs: w1 = mid.lo, w2 = hh.lo + mid.hi, w3 = hh.hi + carries
+    const uint64_t w2 = hh.lo + mid.hi;
+    const uint64_t w3 = hh.hi + c1 + c2 + (w2 < hh.lo ? 1ull : 0ull);
+    const uint64_t w1 = mid.lo;
+    // >> 126: W = (w3:w2:w1) >> 62 within 128 bits
+    A.lo = (w2 << 2) | (w1 >> 62);
+    A.hi = (w3 << 2) | (w2 >> 62);
+    err = err + (err >> 1) + 3ull;
+  }
+  // round |W| (Q116; 2^-25.3 <= |W| < 2^8 unless x == 1) to 24 bits: sh = p - 23 discarded
+  // bits, p the leading bit's position (90 .. 123, so sh in 67 .. 100; s64 guards the
+  // shifts of the x == 1 lane)
+  const bool zero = (A.hi | A.lo) == 0;
+  const int p = A.hi ? 127 - __clzll(A.hi) : 63 - __clzll(A.lo | 1ull);
+  const int sh = p - 23;
+  const int s64 = sh < 64 ? 0 : sh - 64;
+  const uint64_t mant = A.hi >> s64;  // 24 bits
+  const U128 rem = {A.lo, A.hi & ((1ull << s64) - 1ull)};
+  const U128 half = s64 == 0 ? U128{1ull << 63, 0ull} : U128{0ull, 1ull << (s64 - 1)};
+  const U128 dlt = sub128(rem, half);
+  const bool near = (dlt.hi == 0 && dlt.lo <= err) || (dlt.hi == ~0ull && dlt.lo >= 0ull - err);
+  const bool up = (int64_t)dlt.hi > 0 || (dlt.hi == 0 && dlt.lo != 0);
+  // value mant 2^(sh - 116): exponent field sh - 116 + 23 + 127, the leading bit adds 1
+  const uint32_t bits = ((uint32_t)(sh + 33) << 23) + (uint32_t)mant + (up ? 1u : 0u);
+  hard = !zero && (near || sh < 64);
+  return zero ? 0.0f : bitsf(bits | (neg ? 0x80000000u : 0u));
+}
+
+// Slow path: the FP64-free tier for logf, log2f, log10f (the FP64 tier for log1pf), then
+// double-double.
 template <int KIND> CRM_DEV float log_slow(float x, bool &unresolved, bool force) {
   bool hard;
-  float r = log_plain<KIND>(x, (const double2 *)CRM_LN_T97_D, hard);
+  float r;
   unresolved = false;
+  if (KIND == 3) {
+    r = log_plain<KIND>(x, (const double2 *)CRM_LN_T97_D, hard);
+  } else {
+    if (!log_ok<KIND>(x)) return special_log<KIND>(x);
+    r = logf_int<KIND>(x, hard);
+  }
   if ((!hard && !force) || !log_ok<KIND>(x)) return r;
   r = log_dd<KIND>(x, hard);
   unresolved = hard;

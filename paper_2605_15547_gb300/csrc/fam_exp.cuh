@@ -8,6 +8,7 @@
 #pragma once
 #include "crm_common.cuh"
 #include "crm_tables.h"
+#include "fam_f64.cuh"
 
 namespace crm {
 
@@ -216,13 +217,70 @@ template <int KIND> CRM_DEV float exp_dd(float x, bool &hard) {
   return round_dd_to_f(s, t, EXP_DD_EPS * fabs(s), hard);
 }
 
-// Slow path used for lanes whose fast-path test failed: FP64 tier, then double-double.
+// ------------------------------------------------------------------ FP64-free middle tier
+// b^x = 2^(x log2 b) with the binary64 path's fixed-point core (exp2q_core: Y = 2^(x' - k)
+// in Q124 to 2^54 units, 128-bit integer arithmetic): x' 2^96 is formed exactly for
+// exp2f and, for e^x and 10^x, from the 24-bit significand times log2 e in Q125 or log2 10
+// in Q124, truncated (argument error below 2 units of 2^-96, i.e. 2^29 units of Y: the
+// bound is taken as 2^55).  Y is rounded to 24 bits (fewer for subnormal results) with an
+// integer test against half an ulp; |x| < 2^-60 gives 1.  x is not special (no NaN, no
+// saturation: those are resolved before).  Replaces the FP64 tier for the lanes the
+// double-float test sends to the slow path (see logf_int).
+template <int KIND> CRM_DEV float expf_int(float x, bool &hard) {
+  const uint32_t ax = fbits(x) & 0x7FFFFFFFu;
+  const int E = (int)(ax >> 23);
+  hard = false;
+  if (E < 127 - 60) return 1.0f;
+  const uint64_t M = (ax & 0x007FFFFFu) | 0x00800000u;  // |x| = M 2^(E - 150)
+  U128 X;  // |x| log2(b) 2^96
+  if (KIND == 1) {
+    const int s = E - 54;  // M 2^s, s in [13, 80] for 2^-60 <= |x| < 2^8
+    X.lo = s < 64 ? (M << s) : 0ull;
+    X.hi = s < 64 ? (M >> (64 - s)) : (M << (s - 64));
+  } else {
+    const uint64_t ch = KIND == 0 ? CRM_EXPI_LOG2E_Q125_HI : CRM_EXPI_LOG2_10_Q124_HI;
+    const uint64_t cl = KIND == 0 ? CRM_EXPI_LOG2E_Q125_LO : CRM_EXPI_LOG2_10_Q124_LO;
+    const int F = KIND == 0 ? 125 : 124;
+    const U128 ml = mul64w(M, cl), mh = mul64w(M, ch);  // M C as 192 bits p2:p1:p0
+    const uint64_t p0 = ml.lo, p1 = ml.hi + mh.lo;
+    const uint64_t p2 = mh.hi + (p1 < ml.hi ? 1ull : 0ull);
+    const int sft = F - 96 - (E - 150);  // X = M C >> sft, sft in [45, 112]
+    if (sft < 64) {
+      X.lo = (p0 >> sft) | (p1 << (64 - sft));
+      X.hi = (p1 >> sft) | (p2 << (64 - sft));
+    } else {
+      const int s2 = sft - 64;
+      X.lo = s2 ? ((p1 >> s2) | (p2 << (64 - s2))) : p1;
+      X.hi = p2 >> s2;
+    }
+  }
+  if (x < 0.0f) X = neg128(X);
+  int k;
+  const U128 Y = exp2q_core(X, (const ulonglong2 *)CRM_EXP2I_T, k);  // [2^124, 2^125)
+  if (k >= 128) return CRM_INF_F;  // b^x >= 2^128
+  if (k < -150) return 0.0f;       // b^x < 2^-150
+  // discard sh bits: 101 for a normal result, 101 + (-126 - k) <= 125 for a subnormal one
+  const int sh = 101 + (k < -126 ? -126 - k : 0);
+  const int s64 = sh - 64;  // 37 .. 61
+  const uint64_t mant = Y.hi >> s64;
+  const U128 rem = {Y.lo, Y.hi & ((1ull << s64) - 1ull)};
+  const U128 dlt = sub128(rem, U128{0ull, 1ull << (s64 - 1)});
+  const uint64_t ERR = 1ull << 55;
+  hard = (dlt.hi == 0 && dlt.lo <= ERR) || (dlt.hi == ~0ull && dlt.lo >= 0ull - ERR);
+  const uint32_t up = ((int64_t)dlt.hi > 0 || (dlt.hi == 0 && dlt.lo != 0)) ? 1u : 0u;
+  const uint32_t bits = k < -126 ? (uint32_t)mant + up : ((uint32_t)(k + 126) << 23) + (uint32_t)mant + up;
+  return bitsf(bits);
+}
+
+// Slow path used for lanes whose fast-path test failed: the FP64-free tier, then
+// double-double.
 template <int KIND> CRM_DEV float exp_slow(float x, bool &unresolved, bool force) {
-  bool hard;
-  float r = exp_plain<KIND>(x, CRM_EXP2_T16_D, hard);
   unresolved = false;
   float sp;
-  if ((!hard && !force) || exp_special<KIND>(x, sp)) return r;
+  if (exp_special<KIND>(x, sp)) return sp;
+  bool hard;
+  float r = expf_int<KIND>(x, hard);
+  if (!hard && !force) return r;
   r = exp_dd<KIND>(x, hard);
   unresolved = hard;
   return r;

@@ -130,23 +130,10 @@ CRM_DEV bool exp2d_special_bits(uint64_t b, double &r) {
   return nan || ovf || unf;
 }
 
-CRM_DEV double exp2d_int(double x, const ulonglong2 *T, bool &hard) {
-  double rs;
-  const uint64_t b = dbits(x);
-  const bool sp = exp2d_special_bits(b, rs);
-  const int E = (int)((b >> 52) & 0x7FF);
-  const bool tiny = E < 1023 - 60;  // |x| < 2^-60: 2^x rounds to 1
-  const uint64_t M = (b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
-  int s = E - 979;  // |x| 2^96 = M 2^s, s in [-16, 54] on the main path
-  s = (sp || tiny) ? 0 : s;
-  U128 X;
-  X.lo = s >= 0 ? (M << s) : (M >> -s);
-  X.hi = s > 0 ? (M >> (64 - s)) : 0ull;
-  if (b >> 63) {  // two's complement: k = floor(x'), the fraction bits give x' - k
-    X.lo = ~X.lo + 1ull;
-    X.hi = ~X.hi + (X.lo == 0 ? 1ull : 0ull);
-  }
-  const int k = (int)((int64_t)X.hi >> 32);
+// 2^x' for the fixed-point argument X = x' 2^96 (two's complement, |x'| < 2^31): k =
+// floor(x') and Y = 2^(x' - k) in Q124 (Y in [2^124, 2^125)), error < 2^54 units.
+CRM_DEV U128 exp2q_core(U128 X, const ulonglong2 *T, int &k) {
+  k = (int)((int64_t)X.hi >> 32);
   const uint32_t Fh = (uint32_t)X.hi;
   const int i = (int)(Fh >> 22);
   const uint64_t rho = ((uint64_t)(Fh & 0x3FFFFFu) << 42) | (X.lo >> 22);
@@ -164,7 +151,27 @@ CRM_DEV double exp2d_int(double x, const ulonglong2 *T, bool &hard) {
   const ulonglong2 t = T[i];  // (low, high)
   U128 tp = shr128(mul64w(t.y, P), 10);
   tp = add128_64(tp, __umul64hi(t.x, P) >> 10);
-  const U128 Y = add128({t.x, t.y}, tp);  // in [2^124, 2^125)
+  return add128({t.x, t.y}, tp);  // in [2^124, 2^125)
+}
+
+CRM_DEV double exp2d_int(double x, const ulonglong2 *T, bool &hard) {
+  double rs;
+  const uint64_t b = dbits(x);
+  const bool sp = exp2d_special_bits(b, rs);
+  const int E = (int)((b >> 52) & 0x7FF);
+  const bool tiny = E < 1023 - 60;  // |x| < 2^-60: 2^x rounds to 1
+  const uint64_t M = (b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+  int s = E - 979;  // |x| 2^96 = M 2^s, s in [-16, 54] on the main path
+  s = (sp || tiny) ? 0 : s;
+  U128 X;
+  X.lo = s >= 0 ? (M << s) : (M >> -s);
+  X.hi = s > 0 ? (M >> (64 - s)) : 0ull;
+  if (b >> 63) {  // two's complement: k = floor(x'), the fraction bits give x' - k
+    X.lo = ~X.lo + 1ull;
+    X.hi = ~X.hi + (X.lo == 0 ? 1ull : 0ull);
+  }
+  int k;
+  const U128 Y = exp2q_core(X, T, k);
   const uint64_t ERR = 1ull << 54;
   uint64_t bits;
   bool near;

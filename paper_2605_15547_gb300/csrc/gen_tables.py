@@ -498,6 +498,14 @@ with mp.workprec(400):
     N = int(mp.nint(LN2 * mp.mpf(2) ** 116))
 emit(f"#define CRM_LOGI_LN2_LO 0x{N & 0xFFFFFFFFFFFFFFFF:016X}ull  // ln 2 2^116, low word")
 emit(f"#define CRM_LOGI_LN2_HI 0x{N >> 64:016X}ull  // high word")
+# log2(e) in Q125 and log2(10) in Q124 (both below 2^126), for the binary32 expf / exp10f
+# integer tier
+for nm, v, q in (("LOG2E_Q125", LOG2E, 125), ("LOG2_10_Q124", LOG2_10, 124)):
+    with mp.workprec(400):
+        N = int(mp.nint(v * mp.mpf(2) ** q))
+    assert N < 2 ** 126
+    emit(f"#define CRM_EXPI_{nm}_LO 0x{N & 0xFFFFFFFFFFFFFFFF:016X}ull  // low word")
+    emit(f"#define CRM_EXPI_{nm}_HI 0x{N >> 64:016X}ull  // high word")
 # 1/ln 2 and 1/ln 10 in Q126 (both below 2), for the binary32 log2f / log10f integer tier
 for nm, v in (("INV_LN2", 1 / LN2), ("INV_LN10", 1 / mp.log(10))):
     with mp.workprec(400):

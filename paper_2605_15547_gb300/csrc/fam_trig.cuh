@@ -12,6 +12,7 @@
 #pragma once
 #include "crm_common.cuh"
 #include "crm_tables.h"
+#include "fam_f64.cuh"
 
 namespace crm {
 
@@ -405,11 +406,138 @@ CRM_DEV void trig_dd_core(float x, Pair<double> &A, Pair<double> &B, int &q) {
   B = dd_add(dd_mul(C, ct), dd_neg(dd_mul(S, st)));
 }
 
+// ------------------------------------------------------------------ FP64-free middle tier
+// sin and cos in signed Q126 fixed point (128-bit two's complement) on the integer pipes,
+// for the lanes the double-float test sends to the slow path (on GB300 one warp issues an
+// FP64 instruction only every few dozen cycles, see logf_int).  The 160-bit window of 2/pi
+// gives f to 2^-127.6 and t = f pi/64; sin t = t + t u (s1 + ... + u^5 s6) and
+// cos t - 1 = u (c1 + ... + u^6 c7), u = t^2 (remainders t^15/15! < 2^-120 and
+// t^16/16! < 2^-130); then A = S + S (cos t - 1) + C sin t, B = C + C (cos t - 1) - S sin t
+// with (S, C) = (sin, cos)(j pi/64) in Q126.  Every product truncates by less than a unit
+// of 2^-126 and every constant is rounded to half a unit: with the sin remainder (64
+// units) the error stays below 2^7 units of 2^-126, far inside half an ulp except for
+// results within ~2^-119 of a midpoint (|sin|, |cos| >= 2^-35 for a binary32 x: those lanes
+// continue to double-double).  tanf keeps the FP64 tier.
+CRM_DEV U128 q_ld(const unsigned long long *p) { return {p[0], p[1]}; }
+CRM_DEV bool q_neg(U128 a) { return (int64_t)a.hi < 0; }
+// (a b) 2^-126, the magnitude truncated (error below one unit); |a|, |b| <= 2^127
+CRM_DEV U128 q_mul(U128 a, U128 b) {
+  const bool n = q_neg(a) != q_neg(b);
+  const U128 A = q_neg(a) ? neg128(a) : a, B = q_neg(b) ? neg128(b) : b;
+  const U128 hh = mul64w(A.hi, B.hi), hl = mul64w(A.hi, B.lo), lh = mul64w(A.lo, B.hi);
+  const uint64_t llh = __umul64hi(A.lo, B.lo);
+  U128 mid = add128(hl, lh);
+  uint64_t c = (mid.hi < hl.hi || (mid.hi == hl.hi && mid.lo < hl.lo)) ? 1ull : 0ull;
+  mid = add128_64(mid, llh);
+  c += (mid.hi == 0 && mid.lo < llh) ? 1ull : 0ull;
+  const uint64_t w1 = mid.lo, w2 = hh.lo + mid.hi;
+  const uint64_t w3 = hh.hi + c + (w2 < hh.lo ? 1ull : 0ull);
+  const U128 r = {(w2 << 2) | (w1 >> 62), (w3 << 2) | (w2 >> 62)};
+  return n ? neg128(r) : r;
+}
+// RN to binary32 of v 2^-126 (|v| < 2^127) when no midpoint lies within err units
+CRM_DEV float q_round_f(U128 v, uint64_t err, bool &hard) {
+  const bool n = q_neg(v);
+  const U128 A = n ? neg128(v) : v;
+  const int p = A.hi ? 127 - __clzll(A.hi) : 63 - __clzll(A.lo | 1ull);  // leading bit
+  const int sh = p - 23;  // discarded bits; the value is below 2^-102 when sh < 1
+  if (sh < 1) {
+    hard = true;
+    return 0.0f;
+  }
+  uint64_t mant;
+  U128 rem, half;
+  if (sh >= 64) {
+    mant = A.hi >> (sh - 64);
+    rem = {A.lo, A.hi & ((1ull << (sh - 64)) - 1ull)};
+    half = sh == 64 ? U128{1ull << 63, 0ull} : U128{0ull, 1ull << (sh - 65)};
+  } else {
+    mant = (A.lo >> sh) | (A.hi << (64 - sh));
+    rem = {A.lo & ((1ull << sh) - 1ull), 0ull};
+    half = {1ull << (sh - 1), 0ull};
+  }
+  const U128 dlt = sub128(rem, half);
+  hard = (dlt.hi == 0 && dlt.lo <= err) || (dlt.hi == ~0ull && dlt.lo >= 0ull - err);
+  const uint32_t up = ((int64_t)dlt.hi > 0 || (dlt.hi == 0 && dlt.lo != 0)) ? 1u : 0u;
+  // mant 2^(sh - 126), mant in [2^23, 2^24): exponent field sh + 24, the leading bit adds 1
+  const uint32_t bits = ((uint32_t)(sh + 23) << 23) + (uint32_t)mant + up;
+  return bitsf(bits | (n ? 0x80000000u : 0u));
+}
+
+template <int KIND> CRM_DEV void trig_int(float x, float *y, bool &hard) {
+  const float ax = fabsf(x);
+  hard = false;
+  if (ax < 0x1p-12f) {  // RN(sin x) = x and RN(cos x) = 1: x^3/6 and x^2/2 are below half an ulp
+    if (KIND == TRIG_COS) {
+      y[0] = 1.0f;
+    } else {
+      y[0] = x;
+      if (KIND == TRIG_SINCOS) y[1] = 1.0f;
+    }
+    return;
+  }
+  U128 T;
+  int N7 = 0;
+  if (ax < 0x1p-6f) {  // t = |x|: the significand at 2^(E - 150), in Q126 M 2^(E - 24)
+    const uint32_t b = fbits(ax);
+    const uint64_t M = (b & 0x007FFFFFu) | 0x00800000u;
+    T = {0ull, M << ((int)(b >> 23) - 88)};  // E - 24 - 64 in [27, 32]
+  } else {
+    uint32_t r[6];
+    trig_window_mul<5>(ax, CRM_TWO_OVER_PI_W, r);
+    const uint64_t Fh = ((uint64_t)(r[4] & 0x01FFFFFFu) << 39) | ((uint64_t)r[3] << 7) | (r[2] >> 25);
+    const uint64_t Fl = ((uint64_t)(r[2] & 0x01FFFFFFu) << 39) | ((uint64_t)r[1] << 7) | (r[0] >> 25);
+    N7 = (int)(((r[4] >> 25) + (uint32_t)(Fh >> 63)) & 127u);
+    // F = f 2^128 (two's complement); F (pi/64 in Q126) 2^-126 = t 2^128, then to Q126
+    const U128 t128 = q_mul({Fl, Fh}, q_ld(CRM_TRIGI_PIO64));
+    T = {(t128.lo >> 2) | (t128.hi << 62), (uint64_t)((int64_t)t128.hi >> 2)};
+  }
+  const int j = N7 & 31, q = N7 >> 5;
+  const U128 u = q_mul(T, T);
+  U128 ps = q_ld(CRM_TRIGI_S + 10);
+#pragma unroll
+  for (int k = 4; k >= 0; k--) ps = add128(q_ld(CRM_TRIGI_S + 2 * k), q_mul(u, ps));
+  const U128 st = add128(T, q_mul(T, q_mul(u, ps)));
+  U128 pc = q_ld(CRM_TRIGI_C + 12);
+#pragma unroll
+  for (int k = 5; k >= 0; k--) pc = add128(q_ld(CRM_TRIGI_C + 2 * k), q_mul(u, pc));
+  const U128 cm = q_mul(u, pc);
+  const U128 S = q_ld(CRM_TRIGI_SC + 4 * j), C = q_ld(CRM_TRIGI_SC + 4 * j + 2);
+  const bool odd = (q & 1) != 0;
+  const uint64_t ERR = 128;
+  bool ha = false, hb = false;
+  float ya = 0.0f, yb = 0.0f;
+  // sin of the reduced angle is A when q is even, B when odd; cos the other one
+  const bool needA = KIND == TRIG_SINCOS || (KIND == TRIG_SIN) != odd;
+  const bool needB = KIND == TRIG_SINCOS || (KIND == TRIG_SIN) == odd;
+  if (needA) ya = q_round_f(add128(add128(S, q_mul(S, cm)), q_mul(C, st)), ERR, ha);
+  if (needB) yb = q_round_f(sub128(add128(C, q_mul(C, cm)), q_mul(S, st)), ERR, hb);
+  hard = ha || hb;
+  const float s0 = odd ? yb : ya, c0 = odd ? ya : yb;
+  if (KIND == TRIG_COS) {
+    y[0] = bitsf(fbits(c0) ^ trig_cos_sign(q));
+  } else {
+    y[0] = bitsf(fbits(s0) ^ trig_sin_sign(q, x));
+    if (KIND == TRIG_SINCOS) y[1] = bitsf(fbits(c0) ^ trig_cos_sign(q));
+  }
+}
+
+// Slow path: the FP64-free tier (sin, cos, sincos) or the FP64 tier (tan), then
+// double-double.
 template <int KIND> CRM_DEV void trig_slow(float x, float *y, bool &unresolved, bool force) {
   bool hard;
-  trig_plain<KIND>(x, CRM_TWO_OVER_PI_W, CRM_SINCOS_T32_D, y, hard);
   unresolved = false;
   float sp;
+  if (KIND == TRIG_TAN) {
+    trig_plain<KIND>(x, CRM_TWO_OVER_PI_W, CRM_SINCOS_T32_D, y, hard);
+  } else {
+    if (trig_special(x, sp)) {
+      y[0] = sp;
+      if (KIND == TRIG_SINCOS) y[1] = sp;
+      return;
+    }
+    trig_int<KIND>(x, y, hard);
+  }
   if ((!hard && !force) || trig_special(x, sp)) return;
   Pair<double> A, B, sn, cs;
   int q;

@@ -346,6 +346,30 @@ i6 = split(mp.mpf(1) / 6, f, 2)
 const_f("CRM_INV6_F_HI", i6[0])
 const_f("CRM_INV6_F_LO", i6[1])
 # (-1)^k / (2k+1)! and (-1)^k/(2k)! as doubles and double-doubles
+# FP64-free middle tier of the trigonometric functions: signed Q126 fixed point as
+# two's complement 128-bit (low word first)
+def q126(v):
+    with mp.workprec(400):
+        N = int(mp.nint(mp.mpf(v) * mp.mpf(2) ** 126))
+    assert -2 ** 127 < N < 2 ** 127
+    N &= (1 << 128) - 1
+    return [N & 0xFFFFFFFFFFFFFFFF, N >> 64]
+def arr_u64(name, vals, comment):
+    emit(f"// {comment}")
+    emit(f"CRM_TABLE unsigned long long {name}[{len(vals)}] = {{")
+    for i in range(0, len(vals), 4):
+        emit("  " + ", ".join(f"0x{v:016X}ull" for v in vals[i:i + 4]) + ",")
+    emit("};")
+tsc = []
+for j in range(32):
+    a = mp.mpf(j) * mp.pi / 64
+    tsc += q126(mp.sin(a)) + q126(mp.cos(a))
+arr_u64("CRM_TRIGI_SC", tsc, "(sin, cos)(j pi/64) in Q126, (lo, hi) words, j = 0..31")
+arr_u64("CRM_TRIGI_S", sum((q126(mp.mpf((-1) ** k) / mp.factorial(2 * k + 1)) for k in range(1, 7)), []),
+        "(-1)^k/(2k+1)! in Q126, k = 1..6")
+arr_u64("CRM_TRIGI_C", sum((q126(mp.mpf((-1) ** k) / mp.factorial(2 * k)) for k in range(1, 8)), []),
+        "(-1)^k/(2k)! in Q126, k = 1..7")
+arr_u64("CRM_TRIGI_PIO64", q126(mp.pi / 64), "pi/64 in Q126")
 arr_d("CRM_SIN_TAYLOR_D", [d(mp.mpf((-1) ** k) / mp.factorial(2 * k + 1)) for k in range(10)],
       "(-1)^k/(2k+1)!, k = 0..9")
 arr_d("CRM_COS_TAYLOR_D", [d(mp.mpf((-1) ** k) / mp.factorial(2 * k)) for k in range(10)],

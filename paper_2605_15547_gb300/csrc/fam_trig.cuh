@@ -417,7 +417,7 @@ CRM_DEV void trig_dd_core(float x, Pair<double> &A, Pair<double> &B, int &q) {
 // of 2^-126 and every constant is rounded to half a unit: with the sin remainder (64
 // units) the error stays below 2^7 units of 2^-126, far inside half an ulp except for
 // results within ~2^-119 of a midpoint (|sin|, |cos| >= 2^-35 for a binary32 x: those lanes
-// continue to double-double).  tanf keeps the FP64 tier.
+// continue to double-double); tan divides the two in fixed point (q_div).
 CRM_DEV U128 q_ld(const unsigned long long *p) { return {p[0], p[1]}; }
 CRM_DEV bool q_neg(U128 a) { return (int64_t)a.hi < 0; }
 // (a b) 2^-126, the magnitude truncated (error below one unit); |a|, |b| <= 2^127
@@ -435,8 +435,9 @@ CRM_DEV U128 q_mul(U128 a, U128 b) {
   const U128 r = {(w2 << 2) | (w1 >> 62), (w3 << 2) | (w2 >> 62)};
   return n ? neg128(r) : r;
 }
-// RN to binary32 of v 2^-126 (|v| < 2^127) when no midpoint lies within err units
-CRM_DEV float q_round_f(U128 v, uint64_t err, bool &hard) {
+// RN to binary32 of v 2^(es - 126) (|v| < 2^127, 0 <= es <= 60) when no midpoint lies
+// within err units of v
+CRM_DEV float q_round_f(U128 v, uint64_t err, bool &hard, int es = 0) {
   const bool n = q_neg(v);
   const U128 A = n ? neg128(v) : v;
   const int p = A.hi ? 127 - __clzll(A.hi) : 63 - __clzll(A.lo | 1ull);  // leading bit
@@ -460,8 +461,30 @@ CRM_DEV float q_round_f(U128 v, uint64_t err, bool &hard) {
   hard = (dlt.hi == 0 && dlt.lo <= err) || (dlt.hi == ~0ull && dlt.lo >= 0ull - err);
   const uint32_t up = ((int64_t)dlt.hi > 0 || (dlt.hi == 0 && dlt.lo != 0)) ? 1u : 0u;
   // mant 2^(sh - 126), mant in [2^23, 2^24): exponent field sh + 24, the leading bit adds 1
-  const uint32_t bits = ((uint32_t)(sh + 23) << 23) + (uint32_t)mant + up;
+  const uint32_t bits = ((uint32_t)(sh + 23 + es) << 23) + (uint32_t)mant + up;
   return bitsf(bits | (n ? 0x80000000u : 0u));
+}
+
+// v / d for signed Q126 values with 2^-60 <= |d| < 2: returns w and es with
+// v/d = w 2^(es - 126), |w| <= |v|.  d is normalised to [1, 2) (dn = |d| 2^es, es in
+// [0, 60]), 1/dn (in (1/2, 1], so Q126 holds it) by three Newton steps from a binary32
+// seed (24, 48, 96 bits, then the truncation limit: relative error below 2^-118), and
+// w = v (1/dn).
+CRM_DEV U128 q_div(U128 v, U128 d, int &es) {
+  const bool dneg = q_neg(d);
+  U128 D = dneg ? neg128(d) : d;
+  const int p = D.hi ? 127 - __clzll(D.hi) : 63 - __clzll(D.lo | 1ull);
+  es = 126 - p;  // D 2^es in [2^126, 2^127): value in [1, 2)
+  if (es > 0) D = {D.lo << es, (D.hi << es) | (D.lo >> (64 - es))};
+  // seed: the leading 24 bits of D as a float, reciprocal
+  const float df = (float)(D.hi >> 39) * 0x1p-23f;  // value in [1, 2)
+  const float rf = 1.0f / df;                        // (1/2, 1]
+  U128 R = {0ull, (uint64_t)(rf * 0x1p38f) << 24};  // rf in Q126: rf 2^126 = rf 2^62 2^64
+  const U128 TWO = {0ull, 1ull << 63};               // 2 in Q126
+#pragma unroll
+  for (int it = 0; it < 3; it++) R = q_mul(R, sub128(TWO, q_mul(D, R)));
+  const U128 w = q_mul(v, R);
+  return dneg ? neg128(w) : w;
 }
 
 template <int KIND> CRM_DEV void trig_int(float x, float *y, bool &hard) {
@@ -505,6 +528,27 @@ template <int KIND> CRM_DEV void trig_int(float x, float *y, bool &hard) {
   const U128 S = q_ld(CRM_TRIGI_SC + 4 * j), C = q_ld(CRM_TRIGI_SC + 4 * j + 2);
   const bool odd = (q & 1) != 0;
   const uint64_t ERR = 128;
+  if (KIND == TRIG_TAN) {
+    // tan = A / B, or -B / A for odd q.  With |A|, |B| >= 2^-36 (else the lane goes to
+    // double-double) their 2^-119 absolute errors are below 2^-83 of them, and the
+    // quotient's relative error (with q_div's 2^-118) below 2^-80: the bound is taken as
+    // 2^-80 of |w| plus 2^10 units
+    const U128 A = add128(add128(S, q_mul(S, cm)), q_mul(C, st));
+    const U128 B = sub128(add128(C, q_mul(C, cm)), q_mul(S, st));
+    const U128 N = odd ? B : A, D = odd ? A : B;
+    const U128 aN = q_neg(N) ? neg128(N) : N, aD = q_neg(D) ? neg128(D) : D;
+    if ((aN.hi >> 26) == 0 || (aD.hi >> 26) == 0) {  // |N| or |D| below 2^-36
+      hard = true;
+      y[0] = 0.0f;
+      return;
+    }
+    int es;
+    const U128 w = q_div(N, D, es);
+    const U128 aw = q_neg(w) ? neg128(w) : w;
+    const float yt = q_round_f(w, (aw.hi >> 16) + 1024ull, hard, es);
+    y[0] = bitsf(fbits(yt) ^ ((((uint32_t)q << 31)) ^ (fbits(x) & 0x80000000u)));
+    return;
+  }
   bool ha = false, hb = false;
   float ya = 0.0f, yb = 0.0f;
   // sin of the reduced angle is A when q is even, B when odd; cos the other one
@@ -522,22 +566,17 @@ template <int KIND> CRM_DEV void trig_int(float x, float *y, bool &hard) {
   }
 }
 
-// Slow path: the FP64-free tier (sin, cos, sincos) or the FP64 tier (tan), then
-// double-double.
+// Slow path: the FP64-free tier, then double-double.
 template <int KIND> CRM_DEV void trig_slow(float x, float *y, bool &unresolved, bool force) {
   bool hard;
   unresolved = false;
   float sp;
-  if (KIND == TRIG_TAN) {
-    trig_plain<KIND>(x, CRM_TWO_OVER_PI_W, CRM_SINCOS_T32_D, y, hard);
-  } else {
-    if (trig_special(x, sp)) {
-      y[0] = sp;
-      if (KIND == TRIG_SINCOS) y[1] = sp;
-      return;
-    }
-    trig_int<KIND>(x, y, hard);
+  if (trig_special(x, sp)) {
+    y[0] = sp;
+    if (KIND == TRIG_SINCOS) y[1] = sp;
+    return;
   }
+  trig_int<KIND>(x, y, hard);
   if ((!hard && !force) || trig_special(x, sp)) return;
   Pair<double> A, B, sn, cs;
   int q;

@@ -226,13 +226,12 @@ template <int KIND> CRM_DEV float exp_dd(float x, bool &hard) {
 // integer test against half an ulp; |x| < 2^-60 gives 1.  x is not special (no NaN, no
 // saturation: those are resolved before).  Replaces the FP64 tier for the lanes the
 // double-float test sends to the slow path (see logf_int).
-template <int KIND> CRM_DEV float expf_int(float x, bool &hard) {
-  const uint32_t ax = fbits(x) & 0x7FFFFFFFu;
+// |x| log2(b) 2^96 for 2^-60 <= |x| < 2^8 (exact for b = 2, else truncated: below 2
+// units), from the bit pattern ax of |x|
+template <int KIND> CRM_DEV U128 expq_arg(uint32_t ax) {
   const int E = (int)(ax >> 23);
-  hard = false;
-  if (E < 127 - 60) return 1.0f;
   const uint64_t M = (ax & 0x007FFFFFu) | 0x00800000u;  // |x| = M 2^(E - 150)
-  U128 X;  // |x| log2(b) 2^96
+  U128 X;
   if (KIND == 1) {
     const int s = E - 54;  // M 2^s, s in [13, 80] for 2^-60 <= |x| < 2^8
     X.lo = s < 64 ? (M << s) : 0ull;
@@ -254,6 +253,14 @@ template <int KIND> CRM_DEV float expf_int(float x, bool &hard) {
       X.hi = p2 >> s2;
     }
   }
+  return X;
+}
+
+template <int KIND> CRM_DEV float expf_int(float x, bool &hard) {
+  const uint32_t ax = fbits(x) & 0x7FFFFFFFu;
+  hard = false;
+  if ((int)(ax >> 23) < 127 - 60) return 1.0f;
+  U128 X = expq_arg<KIND>(ax);  // |x| log2(b) 2^96
   if (x < 0.0f) X = neg128(X);
   int k;
   const U128 Y = exp2q_core(X, (const ulonglong2 *)CRM_EXP2I_T, k);  // [2^124, 2^125)

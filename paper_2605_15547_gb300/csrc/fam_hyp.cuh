@@ -293,12 +293,47 @@ template <int H> CRM_DEV Pair<double> hyp_dd_y(float x) {
   return y;
 }
 
+// ------------------------------------------------------------------ FP64-free middle tier
+// sinhf and coshf from the fixed-point exp2 core (exp2q_core: e^a = Y 2^(k - 124), Y in
+// [2^124, 2^125), error 2^54 units, plus 2^29 from the truncated argument a log2 e 2^96):
+// sinh a = (e^a - e^-a)/2, cosh a = (e^a + e^-a)/2 (a = |x|, k1 >= 0 > k2), e^-a aligned
+// to e^a's scale.  The error bound is absolute in units of that scale (2^56), so sinh's
+// cancellation near 0 is accounted for by the rounding test itself (|x| >= 2^-25 keeps
+// the result above 2^99 units).
+template <int H> CRM_DEV float hyp_int(float x, bool &hard) {
+  const uint32_t ax = fbits(x) & 0x7FFFFFFFu;
+  const U128 Xa = expq_arg<0>(ax);  // |x| log2 e 2^96; |x| >= 2^-25 here
+  const ulonglong2 *T = (const ulonglong2 *)CRM_EXP2I_T;
+  const U128 ERR = {1ull << 56, 0ull};
+  int k1, k2;
+  const U128 Y1 = exp2q_core(Xa, T, k1), Y2 = exp2q_core(neg128(Xa), T, k2);
+  const int d = k1 - k2;  // >= 1
+  U128 Y2s = {0ull, 0ull};
+  if (d < 64) {
+    Y2s = {(Y2.lo >> d) | (Y2.hi << (64 - d)), Y2.hi >> d};
+  } else if (d < 128) {
+    Y2s = {Y2.hi >> (d - 64), 0ull};
+  }
+  const U128 V = H == HYP_COSH ? add128(Y1, Y2s) : sub128(Y1, Y2s);  // 2 f(a) 2^(124 - k1)
+  const float y = q_round_f(V, ERR, hard, k1 + 1);
+  return (H == HYP_SINH && x < 0.0f) ? -y : y;
+}
+
 template <int H> CRM_DEV float hyp_slow(float x, bool &unresolved, bool force) {
   bool hard;
-  float r = hyp_plain<H>(x, CRM_EXP2_T16_D, hard);
   unresolved = false;
   float sp;
-  if ((!hard && !force) || hyp_special<H>(x, sp)) return r;
+  if (hyp_special<H>(x, sp)) return sp;
+  float r;
+  if ((H == HYP_SINH || H == HYP_COSH) && fabsf(x) >= 0x1p-25f) {
+    r = hyp_int<H>(x, hard);
+  } else {
+    // expm1 and tanh keep the FP64 tier: near 0 their integer forms lose the cancelled
+    // bits (2^-43 relative), which sent too many lanes on to double-double; |x| < 2^-25
+    // reaches here only under the forced test hook
+    r = hyp_plain<H>(x, CRM_EXP2_T16_D, hard);
+  }
+  if (!hard && !force) return r;
   Pair<double> y = hyp_dd_y<H>(x);
   r = round_dd_to_f(y.hi, y.lo, HYP_DD_EPS * fabs(y.hi), hard);
   unresolved = hard;

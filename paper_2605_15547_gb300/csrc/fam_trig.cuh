@@ -418,75 +418,6 @@ CRM_DEV void trig_dd_core(float x, Pair<double> &A, Pair<double> &B, int &q) {
 // units) the error stays below 2^7 units of 2^-126, far inside half an ulp except for
 // results within ~2^-119 of a midpoint (|sin|, |cos| >= 2^-35 for a binary32 x: those lanes
 // continue to double-double); tan divides the two in fixed point (q_div).
-CRM_DEV U128 q_ld(const unsigned long long *p) { return {p[0], p[1]}; }
-CRM_DEV bool q_neg(U128 a) { return (int64_t)a.hi < 0; }
-// (a b) 2^-126, the magnitude truncated (error below one unit); |a|, |b| <= 2^127
-CRM_DEV U128 q_mul(U128 a, U128 b) {
-  const bool n = q_neg(a) != q_neg(b);
-  const U128 A = q_neg(a) ? neg128(a) : a, B = q_neg(b) ? neg128(b) : b;
-  const U128 hh = mul64w(A.hi, B.hi), hl = mul64w(A.hi, B.lo), lh = mul64w(A.lo, B.hi);
-  const uint64_t llh = __umul64hi(A.lo, B.lo);
-  U128 mid = add128(hl, lh);
-  uint64_t c = (mid.hi < hl.hi || (mid.hi == hl.hi && mid.lo < hl.lo)) ? 1ull : 0ull;
-  mid = add128_64(mid, llh);
-  c += (mid.hi == 0 && mid.lo < llh) ? 1ull : 0ull;
-  const uint64_t w1 = mid.lo, w2 = hh.lo + mid.hi;
-  const uint64_t w3 = hh.hi + c + (w2 < hh.lo ? 1ull : 0ull);
-  const U128 r = {(w2 << 2) | (w1 >> 62), (w3 << 2) | (w2 >> 62)};
-  return n ? neg128(r) : r;
-}
-// RN to binary32 of v 2^(es - 126) (|v| < 2^127, 0 <= es <= 60) when no midpoint lies
-// within err units of v
-CRM_DEV float q_round_f(U128 v, uint64_t err, bool &hard, int es = 0) {
-  const bool n = q_neg(v);
-  const U128 A = n ? neg128(v) : v;
-  const int p = A.hi ? 127 - __clzll(A.hi) : 63 - __clzll(A.lo | 1ull);  // leading bit
-  const int sh = p - 23;  // discarded bits; the value is below 2^-102 when sh < 1
-  if (sh < 1) {
-    hard = true;
-    return 0.0f;
-  }
-  uint64_t mant;
-  U128 rem, half;
-  if (sh >= 64) {
-    mant = A.hi >> (sh - 64);
-    rem = {A.lo, A.hi & ((1ull << (sh - 64)) - 1ull)};
-    half = sh == 64 ? U128{1ull << 63, 0ull} : U128{0ull, 1ull << (sh - 65)};
-  } else {
-    mant = (A.lo >> sh) | (A.hi << (64 - sh));
-    rem = {A.lo & ((1ull << sh) - 1ull), 0ull};
-    half = {1ull << (sh - 1), 0ull};
-  }
-  const U128 dlt = sub128(rem, half);
-  hard = (dlt.hi == 0 && dlt.lo <= err) || (dlt.hi == ~0ull && dlt.lo >= 0ull - err);
-  const uint32_t up = ((int64_t)dlt.hi > 0 || (dlt.hi == 0 && dlt.lo != 0)) ? 1u : 0u;
-  // mant 2^(sh - 126), mant in [2^23, 2^24): exponent field sh + 24, the leading bit adds 1
-  const uint32_t bits = ((uint32_t)(sh + 23 + es) << 23) + (uint32_t)mant + up;
-  return bitsf(bits | (n ? 0x80000000u : 0u));
-}
-
-// v / d for signed Q126 values with 2^-60 <= |d| < 2: returns w and es with
-// v/d = w 2^(es - 126), |w| <= |v|.  d is normalised to [1, 2) (dn = |d| 2^es, es in
-// [0, 60]), 1/dn (in (1/2, 1], so Q126 holds it) by three Newton steps from a binary32
-// seed (24, 48, 96 bits, then the truncation limit: relative error below 2^-118), and
-// w = v (1/dn).
-CRM_DEV U128 q_div(U128 v, U128 d, int &es) {
-  const bool dneg = q_neg(d);
-  U128 D = dneg ? neg128(d) : d;
-  const int p = D.hi ? 127 - __clzll(D.hi) : 63 - __clzll(D.lo | 1ull);
-  es = 126 - p;  // D 2^es in [2^126, 2^127): value in [1, 2)
-  if (es > 0) D = {D.lo << es, (D.hi << es) | (D.lo >> (64 - es))};
-  // seed: the leading 24 bits of D as a float, reciprocal
-  const float df = (float)(D.hi >> 39) * 0x1p-23f;  // value in [1, 2)
-  const float rf = 1.0f / df;                        // (1/2, 1]
-  U128 R = {0ull, (uint64_t)(rf * 0x1p38f) << 24};  // rf in Q126: rf 2^126 = rf 2^62 2^64
-  const U128 TWO = {0ull, 1ull << 63};               // 2 in Q126
-#pragma unroll
-  for (int it = 0; it < 3; it++) R = q_mul(R, sub128(TWO, q_mul(D, R)));
-  const U128 w = q_mul(v, R);
-  return dneg ? neg128(w) : w;
-}
-
 template <int KIND> CRM_DEV void trig_int(float x, float *y, bool &hard) {
   const float ax = fabsf(x);
   hard = false;
@@ -527,7 +458,7 @@ template <int KIND> CRM_DEV void trig_int(float x, float *y, bool &hard) {
   const U128 cm = q_mul(u, pc);
   const U128 S = q_ld(CRM_TRIGI_SC + 4 * j), C = q_ld(CRM_TRIGI_SC + 4 * j + 2);
   const bool odd = (q & 1) != 0;
-  const uint64_t ERR = 128;
+  const U128 ERR = {128ull, 0ull};
   if (KIND == TRIG_TAN) {
     // tan = A / B, or -B / A for odd q.  With |A|, |B| >= 2^-36 (else the lane goes to
     // double-double) their 2^-119 absolute errors are below 2^-83 of them, and the
@@ -545,7 +476,7 @@ template <int KIND> CRM_DEV void trig_int(float x, float *y, bool &hard) {
     int es;
     const U128 w = q_div(N, D, es);
     const U128 aw = q_neg(w) ? neg128(w) : w;
-    const float yt = q_round_f(w, (aw.hi >> 16) + 1024ull, hard, es);
+    const float yt = q_round_f(w, U128{(aw.hi >> 16) + 1024ull, 0ull}, hard, es);
     y[0] = bitsf(fbits(yt) ^ ((((uint32_t)q << 31)) ^ (fbits(x) & 0x80000000u)));
     return;
   }

@@ -49,13 +49,13 @@ FALLBACK_HBM_GBS = 6800.0
 # of the function's main kernel, divided by the elements of that launch), with the
 # fingerprint of the kernel sources it was taken on; a traffic figure is reported only
 # while the sources still match (profiles/ holds the captures).
-TRAFFIC_BYTES_PER_ELEM = {"expf": 6.652, "exp2f": 6.646, "exp10f": 6.644, "expm1f": 6.627,
-                          "logf": 6.633, "log2f": 6.644, "log10f": 6.652, "log1pf": 6.64,
-                          "sinf": 6.487, "cosf": 6.488, "sincosf": 10.394, "tanf": 6.473,
-                          "asinf": 6.481, "acosf": 6.465, "atanf": 6.488, "sinhf": 6.469,
-                          "coshf": 6.467, "tanhf": 6.47, "rsqrtf": 6.635, "exp2": 14.484,
-                          "log": 14.477}
-TRAFFIC_SOURCES = "ff3f95b8826418ff"  # profiles/traffic_main_kernels_2p25.md, k_main_sincosf_df_2p25.md
+TRAFFIC_BYTES_PER_ELEM = {"expf": 6.652, "exp2f": 6.645, "exp10f": 6.648, "expm1f": 6.639,
+                          "logf": 6.698, "log2f": 6.727, "log10f": 6.723, "log1pf": 6.623,
+                          "sinf": 6.733, "cosf": 6.791, "sincosf": 10.875, "tanf": 6.839,
+                          "asinf": 6.724, "acosf": 6.739, "atanf": 6.74, "sinhf": 6.68,
+                          "coshf": 6.677, "tanhf": 6.711, "rsqrtf": 6.647, "exp2": 14.49,
+                          "log": 14.489}
+TRAFFIC_SOURCES = "503804086bfcbe9b"  # profiles/traffic_main_kernels_2p25.md, k_main_sincosf_df_2p25.md
 
 
 def kernel_sources_fingerprint() -> str:

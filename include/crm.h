@@ -205,7 +205,10 @@ int crm_stats(void *stream, crm_stats_t *out);
 int crm_stats_reset(void *stream);
 
 /* Test hook: when nonzero, every lane fails its fast-path rounding test, so the queue
-   and the slow path carry the whole array (results must not change). */
+   and the slow path carry the whole array (results must not change).  on = 1 also makes
+   every tier of the slow path run (the last one decides); on = 2 keeps the slow path's
+   early exits, so that its first tier (the FP64-free middle tier where there is one)
+   decides every lane it can. */
 int crm_set_force_slow(int on);
 
 const char *crm_status_str(int status);

@@ -125,8 +125,10 @@ def set_batch_tile(log2_elems: int) -> None:
     L.check(L.lib().crm_set_batch_tile(int(log2_elems)))
 
 
-def set_force_slow(on: bool) -> None:
-    L.check(L.lib().crm_set_force_slow(1 if on else 0))
+def set_force_slow(on) -> None:
+    """Test hook: False/0 off; True/1 every lane through every tier of the slow path;
+    2 every lane through the slow path, whose first tier decides where it can."""
+    L.check(L.lib().crm_set_force_slow(2 if on == 2 else (1 if on else 0)))
 
 
 def reserve(max_elems: int, max_arrays: int = 0, stream=None) -> None:

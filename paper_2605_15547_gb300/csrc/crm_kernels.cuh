@@ -30,7 +30,7 @@ struct KArgs {
   uint64_t cap;      // queue capacity (entries)
   unsigned long long *qcount;  // sub-queue counters, CRM_SUBQ_STRIDE apart
   int nsubq;         // sub-queues (each of cap / nsubq entries)
-  int force_hard;    // test hook: every lane takes the slow path
+  int force_hard;    // test hook: every lane takes the slow path (1: and every tier of it)
   uint32_t desc;     // array id recorded in queue entries (batch form)
 };
 
@@ -157,7 +157,7 @@ __device__ __noinline__ void slow_store(typename Fn::T x, uint64_t i, const KArg
   using T = typename Fn::T;
   T y[2];
   bool unres;
-  Fn::slow(x, y, unres, a.force_hard != 0);
+  Fn::slow(x, y, unres, a.force_hard == 1);
   T *out = (T *)a.out;
   out[i] = y[0];
   if (Fn::NOUT == 2) out[a.n + i] = y[1];
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(KBLOCK) k_slow(KArgs a) {
     T x = x_from_bits<T>(e.x);
     T y[2];
     bool unres;
-    Fn::slow(x, y, unres, a.force_hard != 0);
+    Fn::slow(x, y, unres, a.force_hard == 1);
     out[idx] = y[0];
     if (Fn::NOUT == 2) out[a.n + idx] = y[1];
     if (unres) atomicAdd(&a.hdr->unresolved_total, 1ull);

@@ -425,7 +425,7 @@ int crm_set_form(int form) {
 
 int crm_set_force_slow(int on) {
   ensure_init();
-  g_force_slow = on ? 1 : 0;
+  g_force_slow = on == 2 ? 2 : (on ? 1 : 0);
   return CRM_OK;
 }
 

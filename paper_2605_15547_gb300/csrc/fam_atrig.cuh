@@ -12,6 +12,7 @@
 #pragma once
 #include "crm_common.cuh"
 #include "crm_tables.h"
+#include "fam_f64.cuh"
 
 namespace crm {
 
@@ -219,12 +220,143 @@ CRM_DEV Pair<double> atan_ratio_dd(Pair<double> a, Pair<double> b) {
   return sw ? dd_add(dd(CRM_PIO2_D_HI, CRM_PIO2_D_LO), dd_neg(r)) : r;
 }
 
+// ------------------------------------------------------------------ FP64-free middle tier
+// atanf, asinf and acosf in signed Q126 fixed point.  atan r for 0 <= r <= 1: j =
+// rint(16 r), t = (r - j/16)/(1 + (j/16) r) by q_div (|t| <= 1/32), atan t by its Taylor
+// series to degree 23 (remainder t^25/25 < 2^-129), atan(j/16) from a Q126 table.
+// Products truncate by less than a unit and the constants by half a unit: atan r is
+// within 2^10 units of 2^-126.
+CRM_DEV U128 q_shr(U128 a, int s) {  // 0 <= s, a >= 0
+  if (s == 0) return a;
+  if (s < 64) return {(a.lo >> s) | (a.hi << (64 - s)), a.hi >> s};
+  return {s < 128 ? a.hi >> (s - 64) : 0ull, 0ull};
+}
+CRM_DEV U128 q_shl(U128 a, int s) {  // 0 <= s < 128, no overflow
+  if (s == 0) return a;
+  if (s < 64) return {a.lo << s, (a.hi << s) | (a.lo >> (64 - s))};
+  return {0ull, a.lo << (s - 64)};
+}
+CRM_DEV U128 atan_q126(U128 R) {
+  const int j = (int)(((R.hi >> 57) + 1) >> 1);  // rint(16 r): 16 r = R 2^-122
+  const U128 N = sub128(R, U128{0ull, (uint64_t)j << 58});  // r - j/16, exact
+  U128 t = {0ull, 0ull};
+  if (N.hi | N.lo) {
+    const U128 Rs = {(R.lo >> 4) | (R.hi << 60), R.hi >> 4};  // r/16, truncated
+    U128 D = {0ull, 1ull << 62};                              // 1 + j r/16
+    for (int i = 0; i < j; i++) D = add128(D, Rs);
+    int es;
+    t = q_div(N, D, es);  // D in [1, 2): es = 0
+  }
+  const U128 u = q_mul(t, t);
+  U128 p = q_ld(CRM_ATANI_C + 20);
+#pragma unroll
+  for (int k = 9; k >= 0; k--) p = add128(q_ld(CRM_ATANI_C + 2 * k), q_mul(u, p));
+  return add128(q_ld(CRM_ATANI_T + 2 * j), add128(t, q_mul(t, q_mul(u, p))));
+}
+
+// atan(a/b) for Q126 values a, b >= 0 with max(a, b) >= 2^-12: the smaller over the larger
+// by q_div (relative 2^-118; w 2^es is the quotient, es <= 12, so its truncation is at most
+// 2^12 units), pi/2 - atan(b/a) when a > b.  An error of e units in a or b moves the result
+// by at most e 2^12 units (|d atan(a/b)/da| = b/(a^2 + b^2) <= 1/max(a, b)).
+CRM_DEV U128 atan2_q126(U128 a, U128 b) {
+  const bool sw = !le128(a, b);
+  int es;
+  const U128 w = q_div(sw ? b : a, sw ? a : b, es);
+  const U128 v = atan_q126(q_shl(w, es));
+  return sw ? sub128(q_ld(CRM_ATANI_PIO2), v) : v;
+}
+
+// sqrt d for a Q126 value 2^-24 <= d <= 1: s and k with sqrt d = s 2^-k, s in [1/2, 2).
+// D = d 4^k in [1/2, 2) (exact), y = 1/sqrt D by three Newton steps y += y (1 - D y^2)/2
+// from a binary32 seed (relative error 2^-21, then 2^-41, 2^-81, the truncation limit
+// near 2^-123), s = D y.
+CRM_DEV U128 q_sqrt(U128 d, int &k) {
+  const int p = 127 - __clzll(d.hi);  // d.hi != 0 since d >= 2^-24
+  k = (126 - p) >> 1;
+  const U128 D = q_shl(d, 2 * k);
+  const float y0 = rsqrtf((float)(D.hi >> 39) * 0x1p-23f);
+  U128 y = {0ull, (uint64_t)(y0 * 0x1p38f) << 24};
+  const U128 ONE = {0ull, 1ull << 62};
+#pragma unroll
+  for (int it = 0; it < 3; it++) {
+    const U128 e = sub128(ONE, q_mul(q_mul(D, y), y));                   // 1 - D y^2, signed
+    const U128 h = {(e.lo >> 1) | (e.hi << 63), (uint64_t)((int64_t)e.hi >> 1)};  // e / 2
+    y = add128(y, q_mul(y, h));
+  }
+  return q_mul(D, y);
+}
+
+// The Q126 value of a binary32 x with 2^-62 <= |x| < 2 (exact): M 2^(E - 24).
+CRM_DEV U128 q_of_f(float x) {
+  const uint32_t b = fbits(fabsf(x));
+  const U128 M = {(uint64_t)((b & 0x007FFFFFu) | 0x00800000u), 0ull};
+  const int s = (int)(b >> 23) - 24;
+  return s >= 0 ? q_shl(M, s) : q_shr(M, -s);
+}
+
+// atanf: r = |x| (exact) or 1/|x| (q_div, then shifted; 1/|x| is within 2^2 units) for
+// |x| > 1, pi/2 minus the core for |x| > 1; error bound 2^11 units against results of at
+// least 2^-12.  |x| < 2^-12 gives x (x^3/3 is below half an ulp), +-inf RN(+-pi/2).
+CRM_DEV float atanf_int(float x, bool &hard) {
+  hard = false;
+  const float ax = fabsf(x);
+  if (ax < 0x1p-12f) return x;
+  if (ax == CRM_INF_F) return copysignf(0x1.921fb6p+0f, x);
+  const bool sw = ax > 1.0f;
+  U128 R;  // r in Q126
+  if (!sw) {
+    R = q_of_f(ax);
+  } else {  // 1/|x| = (1/m) 2^-(E - 127), m = M 2^-23 in [1, 2): 1/m from q_div, then shifted
+    const uint32_t b = fbits(ax);
+    int es;
+    const U128 w = q_div(U128{0ull, 1ull << 62}, U128{0ull, (uint64_t)((b & 0x007FFFFFu) | 0x00800000u) << 39},
+                         es);  // 1 / m in Q126 (es = 0)
+    R = q_shr(w, (int)(b >> 23) - 127);
+  }
+  U128 v = atan_q126(R);
+  if (sw) v = sub128(q_ld(CRM_ATANI_PIO2), v);
+  const float y = q_round_f(v, U128{2048ull, 0ull}, hard);
+  return x < 0.0f ? -y : y;
+}
+
+// asinf = sign(x) atan(|x| / s), acosf = atan(s / x) (x > 0), pi - atan(s / |x|) (x < 0),
+// s = sqrt(1 - x^2) with 1 - x^2 exact in Q126 (|x| >= 2^-27 has its square's bits above
+// 2^-126) and s within 2^-114 of itself relative (after the shift by k <= 12).  The
+// errors: a, b exact or relative 2^-114 (2^12 units of 2^-126 on the quotient), q_div 2^12
+// units, the core 2^10 units: bound 2^16 units against results of at least 2^-12.  acos of
+// a negative x is formed as (pi - theta)/2 = pi/2 - theta/2 and rounded with es = 1.
+// |x| = 1 and the tiny ranges (asin x = x below 2^-12, x + x^3/6 being within half an
+// ulp; acos x = RN(pi/2) below 2^-27, pi/2 being 2^-25.8 from a midpoint) are direct.
+template <int KIND> CRM_DEV float asincosf_int(float x, bool &hard) {
+  hard = false;
+  const float ax = fabsf(x);
+  if (KIND == AT_ASIN) {
+    if (ax < 0x1p-12f) return x;
+    if (ax == 1.0f) return copysignf(0x1.921fb6p+0f, x);
+  } else {
+    if (ax < 0x1p-27f) return 0x1.921fb6p+0f;
+    if (x == -1.0f) return 0x1.921fb6p+1f;
+  }
+  const U128 a = q_of_f(ax);
+  int k;
+  const U128 s = q_sqrt(sub128(U128{0ull, 1ull << 62}, q_mul(a, a)), k);
+  const U128 sq = q_shr(s, k);
+  if (KIND == AT_ASIN) {
+    const float y = q_round_f(atan2_q126(a, sq), U128{1ull << 16, 0ull}, hard);
+    return x < 0.0f ? -y : y;
+  }
+  const U128 th = atan2_q126(sq, a);
+  if (x > 0.0f) return q_round_f(th, U128{1ull << 16, 0ull}, hard);
+  return q_round_f(sub128(q_ld(CRM_ATANI_PIO2), q_shr(th, 1)), U128{1ull << 16, 0ull}, hard, 1);
+}
+
 template <int KIND> CRM_DEV float atrig_slow(float x, bool &unresolved, bool force) {
   bool hard;
-  float r = atrig_plain<KIND>(x, CRM_ATAN_T17_D, hard);
   unresolved = false;
   float sp;
-  if ((!hard && !force) || atrig_special<KIND>(x, sp)) return r;
+  if (atrig_special<KIND>(x, sp)) return sp;
+  float r = KIND == AT_ATAN ? atanf_int(x, hard) : asincosf_int<KIND>(x, hard);
+  if (!hard && !force) return r;
   double ax = fabs((double)x);
   Pair<double> a, b;
   bool flip = false;

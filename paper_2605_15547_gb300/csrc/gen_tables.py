@@ -390,6 +390,11 @@ for j in range(17):
     at_d.append(d(A))
     at_f += split(A, f, 2)
     at_dd += split(A, d, 2)
+arr_u64("CRM_ATANI_T", sum((q126(mp.atan(mp.mpf(j) / 16)) for j in range(17)), []),
+        "atan(j/16) in Q126, j = 0..16")
+arr_u64("CRM_ATANI_C", sum((q126(mp.mpf((-1) ** k) / (2 * k + 1)) for k in range(1, 12)), []),
+        "(-1)^k/(2k+1) in Q126, k = 1..11")
+arr_u64("CRM_ATANI_PIO2", q126(mp.pi / 2), "pi/2 in Q126")
 arr_d("CRM_ATAN_T17_D", at_d + [mp.mpf(0)], "atan(j/16), j = 0..16 (+ padding)")
 arr_f("CRM_ATAN_T17_DF", at_f + [mp.mpf(0), mp.mpf(0)], "atan(j/16) (hi, lo) floats")
 arr_d("CRM_ATAN_T17_DD", at_dd, "atan(j/16) as double-double")

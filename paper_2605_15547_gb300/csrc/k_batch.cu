@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(KBLOCK) k_batch_slow(BatchArgs b) {
     uint32_t aid = (uint32_t)(e.idx >> 40);
     uint64_t idx = e.idx & ((1ull << 40) - 1);
     const BatchDesc *d = &b.descs[aid];
-    SlowOp op{e.x, b.force_hard != 0, d, idx, &b.hdr->unresolved_total};
+    SlowOp op{e.x, b.force_hard == 1, d, idx, &b.hdr->unresolved_total};
     CRM_FOR_FUNC_ALL(d->func, op);
   });
 }

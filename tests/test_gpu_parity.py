@@ -157,6 +157,25 @@ def test_forced_slow_path_is_identical(func):
     assert st["unresolved_total"] == 0
 
 
+@pytest.mark.parametrize("func", F32_DONE)
+def test_slow_first_tier_on_every_lane(func):
+    """Every lane through the queue, the slow path's first tier deciding where its own
+    rounding test allows (the FP64-free middle tier for most functions): same bits."""
+    rng = W.rng_for(2, func, salt=10)
+    x = W.domain_bits(func, 40009, rng)
+    ref = O.eval_bits(func, x)
+    crm.stats_reset()
+    crm.set_force_slow(2)
+    try:
+        for form in forms_of(func):
+            assert_same(func, x, run_gpu(func, x, form), ref)
+    finally:
+        crm.set_force_slow(False)
+    st = crm.stats()
+    assert st["hard_total"] >= len(forms_of(func)) * x.size
+    assert st["unresolved_total"] == 0
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 4, 5, 7, 8, 31, 33, 255, 257, 1023, 4097])
 @pytest.mark.parametrize("in_off,out_off", [(0, 0), (1, 1), (1, 2), (3, 0), (2, 2)])
 def test_sizes_and_alignment(n, in_off, out_off):

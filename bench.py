@@ -49,13 +49,13 @@ FALLBACK_HBM_GBS = 6800.0
 # of the function's main kernel, divided by the elements of that launch), with the
 # fingerprint of the kernel sources it was taken on; a traffic figure is reported only
 # while the sources still match (profiles/ holds the captures).
-TRAFFIC_BYTES_PER_ELEM = {"expf": 6.652, "exp2f": 6.645, "exp10f": 6.648, "expm1f": 6.639,
-                          "logf": 6.698, "log2f": 6.727, "log10f": 6.723, "log1pf": 6.623,
-                          "sinf": 6.733, "cosf": 6.791, "sincosf": 10.875, "tanf": 6.839,
-                          "asinf": 6.724, "acosf": 6.739, "atanf": 6.74, "sinhf": 6.68,
-                          "coshf": 6.677, "tanhf": 6.711, "rsqrtf": 6.647, "exp2": 14.49,
-                          "log": 14.489}
-TRAFFIC_SOURCES = "503804086bfcbe9b"  # profiles/traffic_main_kernels_2p25.md, k_main_sincosf_df_2p25.md
+TRAFFIC_BYTES_PER_ELEM = {"expf": 6.641, "exp2f": 6.648, "exp10f": 6.647, "expm1f": 6.63,
+                          "logf": 6.627, "log2f": 6.667, "log10f": 6.699, "log1pf": 6.678,
+                          "sinf": 6.744, "cosf": 6.778, "sincosf": 10.872, "tanf": 6.836,
+                          "asinf": 6.713, "acosf": 6.736, "atanf": 6.731, "sinhf": 6.671,
+                          "coshf": 6.681, "tanhf": 6.7, "rsqrtf": 6.468, "exp2": 14.493,
+                          "log": 14.479}
+TRAFFIC_SOURCES = "16986ef0bddea845"  # profiles/traffic_main_kernels_2p25.md, k_main_sincosf_df_2p25.md
 
 
 def kernel_sources_fingerprint() -> str:

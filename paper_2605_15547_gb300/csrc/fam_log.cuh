@@ -277,9 +277,7 @@ template <int KIND> CRM_DEV float log_dd(float x, bool &hard) {
 // 2^-116, is below 2^-70 of the result).  On GB300 the FP64 pipe runs one warp
 // instruction every few dozen cycles, so this tier replaces the FP64 tier for the lanes
 // the double-float test sends to the slow path.
-template <int KIND> CRM_DEV float logf_int(float x, bool &hard) {
-  uint64_t err;
-  const U128 Z = logz_q116(dbits((double)x), (const ulonglong2 *)CRM_LOGI_L, CRM_LOGI_R, err);
+template <int KIND> CRM_DEV float logq_round(U128 Z, uint64_t err, bool &hard) {
   const bool neg = (int64_t)Z.hi < 0;
   U128 A = neg ? neg128(Z) : Z;  // |Z| < 2^123
   if (KIND == 1 || KIND == 2) {
@@ -320,19 +318,43 @@ template <int KIND> CRM_DEV float logf_int(float x, bool &hard) {
   return zero ? 0.0f : bitsf(bits | (neg ? 0x80000000u : 0u));
 }
 
-// Slow path: the FP64-free tier for logf, log2f, log10f (the FP64 tier for log1pf), then
-// double-double.
+template <int KIND> CRM_DEV float logf_int(float x, bool &hard) {
+  uint64_t err;
+  const U128 Z = logz_q116(dbits((double)x), (const ulonglong2 *)CRM_LOGI_L, CRM_LOGI_R, err);
+  return logq_round<KIND>(Z, err, hard);
+}
+
+// log1pf of x > -1, x != 0, finite: |x| < 2^-25 gives x (x^2/2 is below half an ulp of x,
+// on either side, and log1p x is never a midpoint).  Otherwise 1 + x is exact in binary64
+// for x < 2^53 (x's last bit is at least 2^-48, and 1 + x spans at most 53 bits), and the
+// same core gives ln(1 + x) (|ln(1 + x)| >= 2^-25.1, inside the rounding's range).  For x >=
+// 2^53, ln(1 + x) = ln x + 1/x - 1/(2x^2) + ...: 1/x <= 2^-53 is added in Q116 from a
+// binary32 reciprocal (relative 2^-24: at most 2^40 units, bounded by c 2^-23 + 2 units),
+// the rest is below 2^-105 (2^11 units).  These bounds are far below an ulp of the result
+// (ln x >= 36, ulp 2^98 units): hard lanes stay rare.
+CRM_DEV float log1pf_int(float x, bool &hard) {
+  hard = false;
+  if (fabsf(x) < 0x1p-25f) return x;
+  uint64_t err;
+  const ulonglong2 *LT = (const ulonglong2 *)CRM_LOGI_L;
+  if (x < 0x1p53f) return logq_round<0>(logz_q116(dbits((double)x + 1.0), LT, CRM_LOGI_R, err), err, hard);
+  U128 Z = logz_q116(dbits((double)x), LT, CRM_LOGI_R, err);
+  const uint32_t rb = fbits(1.0f / (x * 0x1p-100f));  // 2^100/x in [2^-28, 2^47], normal
+  const uint64_t Mr = (rb & 0x007FFFFFu) | 0x00800000u;
+  const int s = (int)(rb >> 23) - 134;  // 2^116/x = Mr 2^(Er - 150 - 100 + 116)
+  const uint64_t c = s >= 0 ? Mr << s : Mr >> (-s);
+  Z = add128_64(Z, c);
+  err += (c >> 23) + 2ull + 2048ull;
+  return logq_round<0>(Z, err, hard);
+}
+
+// Slow path: the FP64-free tier, then double-double.
 template <int KIND> CRM_DEV float log_slow(float x, bool &unresolved, bool force) {
   bool hard;
-  float r;
   unresolved = false;
-  if (KIND == 3) {
-    r = log_plain<KIND>(x, (const double2 *)CRM_LN_T97_D, hard);
-  } else {
-    if (!log_ok<KIND>(x)) return special_log<KIND>(x);
-    r = logf_int<KIND>(x, hard);
-  }
-  if ((!hard && !force) || !log_ok<KIND>(x)) return r;
+  if (!log_ok<KIND>(x)) return special_log<KIND>(x);
+  float r = KIND == 3 ? log1pf_int(x, hard) : logf_int<KIND>(x, hard);
+  if (!hard && !force) return r;
   r = log_dd<KIND>(x, hard);
   unresolved = hard;
   return r;

@@ -1,11 +1,12 @@
 // fam_rsqrt.cuh -- rsqrtf.
 //
-// 1/sqrt(x) is algebraic, so a hard case can be decided exactly: the binary32 midpoint
-// m next to the approximation has at most 25 significant bits, m^2 is exact in binary64,
-// and the sign of x m^2 - 1 (one FMA, exact before its single rounding, never zero
-// because 1/sqrt(x) is never a midpoint) tells on which side of m the true value lies.
+// 1/sqrt(x) is algebraic, so a hard case can be decided exactly: a binary32 midpoint m
+// has at most 25 significant bits, so x m^2 is an integer of at most 74 bits times a
+// power of two, and its comparison with 1 (never equal: 1/sqrt(x) is never a midpoint)
+// tells on which side of m the true value lies.
 #pragma once
 #include "crm_common.cuh"
+#include "fam_f64.cuh"
 
 namespace crm {
 
@@ -72,23 +73,37 @@ CRM_DEV float rsqrt_df(float x, bool &hard) {
 }
 
 // ------------------------------------------------------------------ exact slow tier
-// Exact decision: the binary32 neighbours dn <= y <= up of the approximation and their
-// midpoint m; RN(1/sqrt(x)) is up when x m^2 < 1, dn otherwise.  If y is itself a
-// binary32 value (dn == up) it lies within 2^-50 of 1/sqrt(x) while the midpoints are
-// 2^-25 away, so it is the answer.
+// Exact decision in integer arithmetic (no FP64): x is scaled into the normal range as in
+// the double-float tier and y = that tier's rounded result, which is RN(1/sqrt(x)) or one
+// of its two neighbours (the pair is within 2^-44.5, the rounding test's window 2^-36, of
+// 1/sqrt(x), far less than an ulp).  With a = Ma 2^(Ea - 150) (Ma the 24-bit significand,
+// Ea the exponent field) the midpoint between a and its successor is m = (2 Ma + 1)
+// 2^(Ea - 151), and x m^2 = Mx Mm^2 2^(Ex + 2 Ea - 452) with Mx Mm^2 < 2^74: one 128-bit
+// product against a power of two says whether m lies above 1/sqrt(x) (x m^2 > 1; never
+// equal, 1/sqrt(x) is never a midpoint).  The answer is y's successor when 1/sqrt(x) lies
+// above y's upper midpoint, its predecessor when below the lower one, else y.
+CRM_DEV bool rsqrt_mid_above(uint32_t xb, uint32_t ab) {
+  const uint64_t Mx = (xb & 0x007FFFFFu) | 0x00800000u;
+  const uint64_t Mm = 2ull * ((ab & 0x007FFFFFu) | 0x00800000u) + 1ull;
+  const int P = 452 - (int)(xb >> 23) - 2 * (int)(ab >> 23);  // x m^2 > 1 iff Mx Mm^2 > 2^P
+  if (P < 0) return true;
+  if (P >= 128) return false;
+  const U128 prod = mul64w(Mx * Mm, Mm);
+  return !le128(prod, P < 64 ? U128{1ull << P, 0ull} : U128{0ull, 1ull << (P - 64)});
+}
+
 CRM_DEV float rsqrt_slow(float x, bool &unresolved, bool force) {
-  bool hard;
-  float r = rsqrt_plain(x, hard);
+  (void)force;  // the exact decision is the only tier
   unresolved = false;
   float sp;
-  if ((!hard && !force) || rsqrt_special(x, sp)) return r;
-  double y = rsqrt_plain_y(x);
-  float dn = __double2float_rd(y), up = __double2float_ru(y);
-  if (dn == up) return dn;
-  double m = 0.5 * ((double)dn + (double)up);  // 25 significant bits at most
-  double m2 = m * m;                           // exact
-  double v = fma_((double)x, m2, -1.0);        // sign of x m^2 - 1, exactly
-  return v < 0.0 ? up : dn;
+  if (rsqrt_special(x, sp)) return sp;
+  const bool sub = x < 0x1p-126f, big = x >= 0x1p64f;
+  const float xs = sub ? x * 0x1p24f : (big ? x * 0x1p-64f : x);  // normal, in [2^-125, 2^64)
+  bool h;
+  const uint32_t xb = fbits(xs), yb = fbits(rsqrt_df(xs, h));
+  const uint32_t rb = !rsqrt_mid_above(xb, yb) ? yb + 1u : (rsqrt_mid_above(xb, yb - 1u) ? yb - 1u : yb);
+  const float r = bitsf(rb);
+  return sub ? r * 0x1p12f : (big ? r * 0x1p-32f : r);
 }
 
 }  // namespace crm

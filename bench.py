@@ -49,13 +49,13 @@ FALLBACK_HBM_GBS = 6800.0
 # of the function's main kernel, divided by the elements of that launch), with the
 # fingerprint of the kernel sources it was taken on; a traffic figure is reported only
 # while the sources still match (profiles/ holds the captures).
-TRAFFIC_BYTES_PER_ELEM = {"expf": 6.641, "exp2f": 6.648, "exp10f": 6.647, "expm1f": 6.63,
-                          "logf": 6.627, "log2f": 6.667, "log10f": 6.699, "log1pf": 6.678,
-                          "sinf": 6.744, "cosf": 6.778, "sincosf": 10.872, "tanf": 6.836,
-                          "asinf": 6.713, "acosf": 6.736, "atanf": 6.731, "sinhf": 6.671,
-                          "coshf": 6.681, "tanhf": 6.7, "rsqrtf": 6.468, "exp2": 14.493,
-                          "log": 14.479}
-TRAFFIC_SOURCES = "16986ef0bddea845"  # profiles/traffic_main_kernels_2p25.md, k_main_sincosf_df_2p25.md
+TRAFFIC_BYTES_PER_ELEM = {"expf": 6.647, "exp2f": 6.652, "exp10f": 6.657, "expm1f": 6.624,
+                          "logf": 6.621, "log2f": 6.667, "log10f": 6.692, "log1pf": 6.677,
+                          "sinf": 6.732, "cosf": 6.778, "sincosf": 10.874, "tanf": 6.838,
+                          "asinf": 6.726, "acosf": 6.737, "atanf": 6.732, "sinhf": 6.673,
+                          "coshf": 6.683, "tanhf": 6.713, "rsqrtf": 6.47, "exp2": 14.489,
+                          "log": 14.49}
+TRAFFIC_SOURCES = "0ff7c4e3f4df25b7"  # profiles/traffic_main_kernels_2p25.md, k_main_sincosf_df_2p25.md
 
 
 def kernel_sources_fingerprint() -> str:

@@ -226,16 +226,6 @@ CRM_DEV Pair<double> atan_ratio_dd(Pair<double> a, Pair<double> b) {
 // series to degree 23 (remainder t^25/25 < 2^-129), atan(j/16) from a Q126 table.
 // Products truncate by less than a unit and the constants by half a unit: atan r is
 // within 2^10 units of 2^-126.
-CRM_DEV U128 q_shr(U128 a, int s) {  // 0 <= s, a >= 0
-  if (s == 0) return a;
-  if (s < 64) return {(a.lo >> s) | (a.hi << (64 - s)), a.hi >> s};
-  return {s < 128 ? a.hi >> (s - 64) : 0ull, 0ull};
-}
-CRM_DEV U128 q_shl(U128 a, int s) {  // 0 <= s < 128, no overflow
-  if (s == 0) return a;
-  if (s < 64) return {a.lo << s, (a.hi << s) | (a.lo >> (64 - s))};
-  return {0ull, a.lo << (s - 64)};
-}
 CRM_DEV U128 atan_q126(U128 R) {
   const int j = (int)(((R.hi >> 57) + 1) >> 1);  // rint(16 r): 16 r = R 2^-122
   const U128 N = sub128(R, U128{0ull, (uint64_t)j << 58});  // r - j/16, exact
@@ -284,14 +274,6 @@ CRM_DEV U128 q_sqrt(U128 d, int &k) {
     y = add128(y, q_mul(y, h));
   }
   return q_mul(D, y);
-}
-
-// The Q126 value of a binary32 x with 2^-62 <= |x| < 2 (exact): M 2^(E - 24).
-CRM_DEV U128 q_of_f(float x) {
-  const uint32_t b = fbits(fabsf(x));
-  const U128 M = {(uint64_t)((b & 0x007FFFFFu) | 0x00800000u), 0ull};
-  const int s = (int)(b >> 23) - 24;
-  return s >= 0 ? q_shl(M, s) : q_shr(M, -s);
 }
 
 // atanf: r = |x| (exact) or 1/|x| (q_div, then shifted; 1/|x| is within 2^2 units) for

@@ -430,6 +430,24 @@ CRM_DEV U128 q_div(U128 v, U128 d, int &es) {
   return dneg ? neg128(w) : w;
 }
 
+CRM_DEV U128 q_shr(U128 a, int s) {  // 0 <= s, a >= 0
+  if (s == 0) return a;
+  if (s < 64) return {(a.lo >> s) | (a.hi << (64 - s)), a.hi >> s};
+  return {s < 128 ? a.hi >> (s - 64) : 0ull, 0ull};
+}
+CRM_DEV U128 q_shl(U128 a, int s) {  // 0 <= s < 128, no overflow
+  if (s == 0) return a;
+  if (s < 64) return {a.lo << s, (a.hi << s) | (a.lo >> (64 - s))};
+  return {0ull, a.lo << (s - 64)};
+}
+// The Q126 value of a binary32 x with 2^-62 <= |x| < 2 (exact), |x|: M 2^(E - 24).
+CRM_DEV U128 q_of_f(float x) {
+  const uint32_t b = fbits(fabsf(x));
+  const U128 M = {(uint64_t)((b & 0x007FFFFFu) | 0x00800000u), 0ull};
+  const int s = (int)(b >> 23) - 24;
+  return s >= 0 ? q_shl(M, s) : q_shr(M, -s);
+}
+
 // ------------------------------------------------------------------ exact slow path
 struct U192 {
   uint64_t w[3];  // little endian

@@ -319,18 +319,89 @@ template <int H> CRM_DEV float hyp_int(float x, bool &hard) {
   return (H == HYP_SINH && x < 0.0f) ? -y : y;
 }
 
+// expm1f and tanhf in signed Q126, FP64-free, without the cancellation of e^x - 1 near 0:
+//   expm1: |x| < 2^-25 gives x (x^2/2 is below half an ulp on either side); |x| < 2^-4:
+//     x sum_{k<=12} x^k/(k+1)! by Horner (remainder below 2^-88 of the result, products
+//     truncated: 16 units; bound 2^-84 of it plus 16 units); otherwise from the exp2 core, e^x = Y 2^(k-124) (Y within 2^54
+//     units): (Y - 2^(124-k)) 2^2 with es = k for k >= 0, Y 2^(k+2) - 2^126 for k < 0, both
+//     at least e^(1/16) - 1 > 2^-4 of their scale: error 2^57 units, 2^-65 relative;
+//   tanh = expm1(2x)/(expm1(2x) + 2): |x| < 2^-13 gives x (x^3/3 is below half an ulp);
+//     2|x| < 2^-4: m/(m + 1), m = expm1(2|x|)/2 by the series, one q_div (m's relative error
+//     at most doubles); otherwise with
+//     e^(2|x|) = Y 2^(k-124): (Y - 2^(124-k))/(Y + 2^(124-k)), whose absolute error is at
+//     most 2^-70 (Y/D)(1 + N/D) <= 2^-69 (2^57 units; bound 2^58) though N may cancel to 2^-4.
+// The special inputs and the saturated ranges are handled before (hyp_special).
+CRM_DEV U128 expm1_series_q126(U128 X) {  // x sum x^k/(k+1)!, |x| < 2^-4
+  U128 E = q_ld(CRM_HYPI_E + 24);
+#pragma unroll
+  for (int k = 11; k >= 0; k--) E = add128(q_ld(CRM_HYPI_E + 2 * k), q_mul(X, E));
+  return q_mul(X, E);
+}
+
+CRM_DEV U128 rel_err_84(U128 v) {  // |v| 2^-84 + 16 units
+  const U128 A = q_neg(v) ? neg128(v) : v;
+  return {(A.hi >> 20) + 16ull, 0ull};
+}
+
+template <int H> CRM_DEV float hyp_int2(float x, bool &hard) {
+  hard = false;
+  const float ax = fabsf(x);
+  const U128 ONE = {0ull, 1ull << 62};
+  const ulonglong2 *T = (const ulonglong2 *)CRM_EXP2I_T;
+  if (H == HYP_EXPM1) {
+    if (ax < 0x1p-25f) return x;
+    if (ax < 0x1p-4f) {
+      const U128 X = x < 0.0f ? neg128(q_of_f(ax)) : q_of_f(ax);
+      const U128 v = expm1_series_q126(X);
+      return q_round_f(v, rel_err_84(v), hard);
+    }
+    U128 Xa = expq_arg<0>(fbits(ax));
+    if (x < 0.0f) Xa = neg128(Xa);
+    int k;
+    const U128 Y = exp2q_core(Xa, T, k);
+    const U128 E57 = {1ull << 57, 0ull};
+    if (k >= 0) {
+      const U128 W = k <= 124 ? sub128(Y, q_shr(U128{0ull, 1ull << 60}, k)) : Y;  // 2^124 >> k
+      return q_round_f(q_shl(W, 2), E57, hard, k);
+    }
+    const U128 Ys = k == -1 ? q_shl(Y, 1) : q_shr(Y, -k - 2);
+    return q_round_f(sub128(Ys, ONE), E57, hard);
+  }
+  // tanh
+  if (ax < 0x1p-13f) return x;
+  const float a2 = 2.0f * ax;
+  U128 t;
+  U128 err;
+  int es;
+  if (a2 < 0x1p-4f) {
+    const U128 m = q_shr(expm1_series_q126(q_of_f(a2)), 1);
+    const U128 w = q_div(m, add128(m, ONE), es);  // es = 0: m + 1 in [1, 2)
+    t = q_shl(w, es);
+    err = rel_err_84(t);
+  } else {
+    int k;
+    const U128 Y = exp2q_core(expq_arg<0>(fbits(a2)), T, k);  // k in [0, 26]
+    const U128 sk = q_shr(U128{0ull, 1ull << 60}, k);
+    const U128 w = q_div(sub128(Y, sk), add128(Y, sk), es);
+    t = q_shl(w, es);
+    err = {1ull << 58, 0ull};
+  }
+  const float y = q_round_f(t, err, hard);
+  return x < 0.0f ? -y : y;
+}
+
 template <int H> CRM_DEV float hyp_slow(float x, bool &unresolved, bool force) {
   bool hard;
   unresolved = false;
   float sp;
   if (hyp_special<H>(x, sp)) return sp;
   float r;
-  if ((H == HYP_SINH || H == HYP_COSH) && fabsf(x) >= 0x1p-25f) {
+  if (H == HYP_EXPM1 || H == HYP_TANH) {
+    r = hyp_int2<H>(x, hard);
+  } else if (fabsf(x) >= 0x1p-25f) {
     r = hyp_int<H>(x, hard);
   } else {
-    // expm1 and tanh keep the FP64 tier: near 0 their integer forms lose the cancelled
-    // bits (2^-43 relative), which sent too many lanes on to double-double; |x| < 2^-25
-    // reaches here only under the forced test hook
+    // sinh, cosh of |x| < 2^-25 reach here only under the forced test hook
     r = hyp_plain<H>(x, CRM_EXP2_T16_D, hard);
   }
   if (!hard && !force) return r;

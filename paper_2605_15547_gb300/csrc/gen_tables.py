@@ -395,6 +395,8 @@ arr_u64("CRM_ATANI_T", sum((q126(mp.atan(mp.mpf(j) / 16)) for j in range(17)), [
 arr_u64("CRM_ATANI_C", sum((q126(mp.mpf((-1) ** k) / (2 * k + 1)) for k in range(1, 12)), []),
         "(-1)^k/(2k+1) in Q126, k = 1..11")
 arr_u64("CRM_ATANI_PIO2", q126(mp.pi / 2), "pi/2 in Q126")
+arr_u64("CRM_HYPI_E", sum((q126(1 / mp.factorial(k + 1)) for k in range(13)), []),
+        "1/(k+1)! in Q126, k = 0..12 (expm1 x = x sum x^k/(k+1)!)")
 arr_d("CRM_ATAN_T17_D", at_d + [mp.mpf(0)], "atan(j/16), j = 0..16 (+ padding)")
 arr_f("CRM_ATAN_T17_DF", at_f + [mp.mpf(0), mp.mpf(0)], "atan(j/16) (hi, lo) floats")
 arr_d("CRM_ATAN_T17_DD", at_dd, "atan(j/16) as double-double")

@@ -49,13 +49,13 @@ FALLBACK_HBM_GBS = 6800.0
 # of the function's main kernel, divided by the elements of that launch), with the
 # fingerprint of the kernel sources it was taken on; a traffic figure is reported only
 # while the sources still match (profiles/ holds the captures).
-TRAFFIC_BYTES_PER_ELEM = {"expf": 6.647, "exp2f": 6.652, "exp10f": 6.657, "expm1f": 6.624,
-                          "logf": 6.621, "log2f": 6.667, "log10f": 6.692, "log1pf": 6.677,
-                          "sinf": 6.732, "cosf": 6.778, "sincosf": 10.874, "tanf": 6.838,
-                          "asinf": 6.726, "acosf": 6.737, "atanf": 6.732, "sinhf": 6.673,
-                          "coshf": 6.683, "tanhf": 6.713, "rsqrtf": 6.47, "exp2": 14.489,
-                          "log": 14.49}
-TRAFFIC_SOURCES = "0ff7c4e3f4df25b7"  # profiles/traffic_main_kernels_2p25.md, k_main_sincosf_df_2p25.md
+TRAFFIC_BYTES_PER_ELEM = {"expf": 6.642, "exp2f": 6.652, "exp10f": 6.662, "expm1f": 6.677,
+                          "logf": 6.641, "log2f": 6.674, "log10f": 6.635, "log1pf": 6.682,
+                          "sinf": 6.763, "cosf": 6.774, "sincosf": 10.872, "tanf": 6.847,
+                          "asinf": 6.71, "acosf": 6.731, "atanf": 6.735, "sinhf": 6.683,
+                          "coshf": 6.679, "tanhf": 6.711, "rsqrtf": 6.482, "exp2": 14.487,
+                          "log": 14.471}
+TRAFFIC_SOURCES = "38247a7c890413be"  # profiles/traffic_main_kernels_2p25.md, k_main_sincosf_df_2p25.md
 
 
 def kernel_sources_fingerprint() -> str:

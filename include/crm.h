@@ -93,6 +93,9 @@ typedef struct {
   uint64_t inline_total;     /* hard lanes finished inline because the queue was full */
   uint64_t last_count;       /* hard lanes of the last call on this stream */
   uint64_t timeouts;         /* bounded device waits that gave up (0 unless something is wrong) */
+  uint64_t fp64_total;       /* queued lanes whose slow path ran an FP64 tier: for binary32 the
+                                double-double tier behind the FP64-free one, for binary64 every
+                                queued lane (its slow path starts in double-double) */
 } crm_stats_t;
 
 /* Evaluate func_id on n elements: out[i] = RN(f(in[i])) (sincosf: out[i] = sin,

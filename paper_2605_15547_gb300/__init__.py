@@ -109,7 +109,8 @@ def stats(stream=None) -> dict:
     s = crm_stats_t()
     L.check(L.lib().crm_stats(_stream_ptr(stream), ctypes.byref(s)))
     return {"hard_total": s.hard_total, "unresolved_total": s.unresolved_total,
-            "inline_total": s.inline_total, "last_count": s.last_count, "timeouts": s.timeouts}
+            "inline_total": s.inline_total, "last_count": s.last_count, "timeouts": s.timeouts,
+            "fp64_total": s.fp64_total}
 
 
 def stats_reset(stream=None) -> None:

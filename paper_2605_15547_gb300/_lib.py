@@ -41,7 +41,7 @@ class crm_desc_t(ctypes.Structure):
 class crm_stats_t(ctypes.Structure):
     _fields_ = [("hard_total", ctypes.c_uint64), ("unresolved_total", ctypes.c_uint64),
                 ("inline_total", ctypes.c_uint64), ("last_count", ctypes.c_uint64),
-                ("timeouts", ctypes.c_uint64)]
+                ("timeouts", ctypes.c_uint64), ("fp64_total", ctypes.c_uint64)]
 
 
 _LIB = None

@@ -26,7 +26,7 @@ template <int KIND> struct FnExp {
     else
       y[0] = exp_df<KIND>(x, (const float4 *)sm, h);
   }
-  CRM_DEV static void slow(float x, float *y, bool &u, bool f) { y[0] = exp_slow<KIND>(x, u, f); }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f) { y[0] = exp_slow<KIND>(x, u, f); }
 };
 
 template <int KIND> struct FnLog {
@@ -43,7 +43,7 @@ template <int KIND> struct FnLog {
     else
       y[0] = log_df<KIND>(x, (const float4 *)sm, h);
   }
-  CRM_DEV static void slow(float x, float *y, bool &u, bool f) { y[0] = log_slow<KIND>(x, u, f); }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f) { y[0] = log_slow<KIND>(x, u, f); }
 };
 
 template <int H> struct FnHyp {
@@ -59,7 +59,7 @@ template <int H> struct FnHyp {
     else
       y[0] = hyp_df<H>(x, (const float4 *)sm, h);
   }
-  CRM_DEV static void slow(float x, float *y, bool &u, bool f) { y[0] = hyp_slow<H>(x, u, f); }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f) { y[0] = hyp_slow<H>(x, u, f); }
 };
 
 template <int KIND> struct FnTrig {
@@ -89,7 +89,7 @@ template <int KIND> struct FnTrig {
       trig_df<KIND>(x, (const uint4 *)(b + OFF_PW), (const float4 *)(b + 64), (const float2 *)(b + OFF_TT), y,
                     h);
   }
-  CRM_DEV static void slow(float x, float *y, bool &u, bool f) { trig_slow<KIND>(x, y, u, f); }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f) { trig_slow<KIND>(x, y, u, f); }
 };
 
 template <int KIND> struct FnAtrig {
@@ -105,7 +105,7 @@ template <int KIND> struct FnAtrig {
     else
       y[0] = atrig_df<KIND>(x, (const float2 *)sm, h);
   }
-  CRM_DEV static void slow(float x, float *y, bool &u, bool f) { y[0] = atrig_slow<KIND>(x, u, f); }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f) { y[0] = atrig_slow<KIND>(x, u, f); }
 };
 
 struct FnRsqrt {
@@ -116,7 +116,7 @@ struct FnRsqrt {
   template <int FORM> CRM_DEV static void eval(float x, const void *, float *y, bool &h) {
     y[0] = FORM == 1 ? rsqrt_plain(x, h) : rsqrt_df(x, h);
   }
-  CRM_DEV static void slow(float x, float *y, bool &u, bool f) { y[0] = rsqrt_slow(x, u, f); }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f) { y[0] = rsqrt_slow(x, u, f); }
 };
 
 // binary64 pair: one main path (double-double), used for both form slots
@@ -137,7 +137,7 @@ struct FnExp2D {
     else
       y[0] = exp2d_main(x, (const double *)sm, h);
   }
-  CRM_DEV static void slow(double x, double *y, bool &u, bool f) { y[0] = exp2d_slow(x, u, f); }
+  CRM_DEV static void slow(double x, double *y, int &u, bool f) { y[0] = exp2d_slow(x, u, f); }
 };
 struct FnLogD {
   using T = double;
@@ -158,7 +158,7 @@ struct FnLogD {
     else
       y[0] = logd_main(x, h);
   }
-  CRM_DEV static void slow(double x, double *y, bool &u, bool f) { y[0] = logd_slow(x, u, f); }
+  CRM_DEV static void slow(double x, double *y, int &u, bool f) { y[0] = logd_slow(x, u, f); }
 };
 
 }  // namespace crm

@@ -143,7 +143,8 @@ CRM_DEV unsigned push_hard(unsigned hm, const uint64_t *idx, const uint64_t *xb,
 //   template <int FORM> static constexpr int tab_bytes();   (shared memory bytes)
 //   template <int FORM> CRM_DEV static void load(unsigned char *sm);  (fill it)
 //   template <int FORM> CRM_DEV static void eval(T x, const void *sm, T *y, bool &hard);
-//   CRM_DEV static void slow(T x, T *y, bool &unresolved, bool force);  (force: skip
+//   CRM_DEV static void slow(T x, T *y, int &status, bool force);  (status: bit 0 no tier
+//     decided, bit 1 an FP64 tier ran; force: skip
 //     the first tier's early exit, so that every deeper tier runs -- the test hook)
 
 template <class Fn, int FORM>
@@ -156,13 +157,14 @@ template <class Fn>
 __device__ __noinline__ void slow_store(typename Fn::T x, uint64_t i, const KArgs &a) {
   using T = typename Fn::T;
   T y[2];
-  bool unres;
-  Fn::slow(x, y, unres, a.force_hard == 1);
+  int st;
+  Fn::slow(x, y, st, a.force_hard == 1);
   T *out = (T *)a.out;
   out[i] = y[0];
   if (Fn::NOUT == 2) out[a.n + i] = y[1];
   atomicAdd(&a.hdr->inline_total, 1ull);
-  if (unres) atomicAdd(&a.hdr->unresolved_total, 1ull);
+  if (st & 1) atomicAdd(&a.hdr->unresolved_total, 1ull);
+  if (st & 2) atomicAdd(&a.hdr->fp64_total, 1ull);
 }
 
 // Evaluates the W elements of one vector: y0 (and y1 for two outputs) and the hard
@@ -520,11 +522,12 @@ __global__ void __launch_bounds__(KBLOCK) k_slow(KArgs a) {
     uint64_t idx = e.idx & ((1ull << 40) - 1);
     T x = x_from_bits<T>(e.x);
     T y[2];
-    bool unres;
-    Fn::slow(x, y, unres, a.force_hard == 1);
+    int st;
+    Fn::slow(x, y, st, a.force_hard == 1);
     out[idx] = y[0];
     if (Fn::NOUT == 2) out[a.n + idx] = y[1];
-    if (unres) atomicAdd(&a.hdr->unresolved_total, 1ull);
+    if (st & 1) atomicAdd(&a.hdr->unresolved_total, 1ull);
+    if (st & 2) atomicAdd(&a.hdr->fp64_total, 1ull);
   });
 }
 

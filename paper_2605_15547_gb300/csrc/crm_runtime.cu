@@ -456,6 +456,7 @@ int crm_stats(void *stream, crm_stats_t *out) {
   out->inline_total = h.inline_total;
   out->last_count = h.count;
   out->timeouts = h.timeouts;
+  out->fp64_total = h.fp64_total;
   return CRM_OK;
 }
 

@@ -10,7 +10,8 @@ typedef struct crm_ws_header {
   unsigned long long unresolved_total; // lanes no tier could decide (never expected)
   unsigned long long inline_total;     // lanes finished inline because the queue was full
   unsigned long long timeouts;         // bounded waits that gave up (never expected)
-  unsigned long long pad[3];
+  unsigned long long fp64_total;       // queued lanes whose slow path ran an FP64 tier
+  unsigned long long pad[2];
 } crm_ws_header;
 
 // One queued hard lane: element index (array id in bits 40..63 for the batch form) and

@@ -332,7 +332,7 @@ template <int KIND> CRM_DEV float asincosf_int(float x, bool &hard) {
   return q_round_f(sub128(q_ld(CRM_ATANI_PIO2), q_shr(th, 1)), U128{1ull << 16, 0ull}, hard, 1);
 }
 
-template <int KIND> CRM_DEV float atrig_slow(float x, bool &unresolved, bool force) {
+template <int KIND> CRM_DEV float atrig_slow(float x, int &unresolved, bool force) {
   bool hard;
   unresolved = false;
   float sp;
@@ -361,7 +361,7 @@ template <int KIND> CRM_DEV float atrig_slow(float x, bool &unresolved, bool for
   if (flip) y = dd_add(dd(CRM_PI_D_HI, CRM_PI_D_LO), dd_neg(y));
   if (KIND != AT_ACOS && x < 0.0f) y = dd_neg(y);
   r = round_dd_to_f(y.hi, y.lo, ATRIG_DD_EPS * fabs(y.hi), hard);
-  unresolved = hard;
+  unresolved = hard ? 3 : 2;  // the double-double tier ran
   return r;
 }
 

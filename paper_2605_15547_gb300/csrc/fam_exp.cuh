@@ -281,7 +281,7 @@ template <int KIND> CRM_DEV float expf_int(float x, bool &hard) {
 
 // Slow path used for lanes whose fast-path test failed: the FP64-free tier, then
 // double-double.
-template <int KIND> CRM_DEV float exp_slow(float x, bool &unresolved, bool force) {
+template <int KIND> CRM_DEV float exp_slow(float x, int &unresolved, bool force) {
   unresolved = false;
   float sp;
   if (exp_special<KIND>(x, sp)) return sp;
@@ -289,7 +289,7 @@ template <int KIND> CRM_DEV float exp_slow(float x, bool &unresolved, bool force
   float r = expf_int<KIND>(x, hard);
   if (!hard && !force) return r;
   r = exp_dd<KIND>(x, hard);
-  unresolved = hard;
+  unresolved = hard ? 3 : 2;  // the double-double tier ran
   return r;
 }
 

@@ -694,29 +694,29 @@ CRM_DEV bool logd_exact(double x, double &out) {
   return u_round64(M, 181, ae + 16, ae + 16, neg, out);
 }
 
-CRM_DEV double exp2d_slow(double x, bool &unresolved, bool force) {
+CRM_DEV double exp2d_slow(double x, int &unresolved, bool force) {
   bool hard;
   double r = exp2d_main(x, CRM_EXP2D_T, hard);
-  unresolved = false;
+  unresolved = 2;  // the double-double tier (FP64) ran
   double sp;
   if ((!hard && !force) || exp2d_special(x, sp)) return r;
   double out;
   if (x == rint(x)) return ldexp(1.0, (int)x);  // exact powers of two
   bool ok = exp2d_exact(x, out);
-  unresolved = !ok;
+  unresolved = ok ? 2 : 3;
   return ok ? out : r;
 }
 
-CRM_DEV double logd_slow(double x, bool &unresolved, bool force) {
+CRM_DEV double logd_slow(double x, int &unresolved, bool force) {
   bool hard;
   double r = logd_main(x, hard);
-  unresolved = false;
+  unresolved = 2;  // the double-double tier (FP64) ran
   double sp;
   if ((!hard && !force) || logd_special(x, sp)) return r;
   if (x == 1.0) return 0.0;
   double out;
   bool ok = logd_exact(x, out);
-  unresolved = !ok;
+  unresolved = ok ? 2 : 3;
   return ok ? out : r;
 }
 

@@ -390,7 +390,7 @@ template <int H> CRM_DEV float hyp_int2(float x, bool &hard) {
   return x < 0.0f ? -y : y;
 }
 
-template <int H> CRM_DEV float hyp_slow(float x, bool &unresolved, bool force) {
+template <int H> CRM_DEV float hyp_slow(float x, int &unresolved, bool force) {
   bool hard;
   unresolved = false;
   float sp;
@@ -403,11 +403,12 @@ template <int H> CRM_DEV float hyp_slow(float x, bool &unresolved, bool force) {
   } else {
     // sinh, cosh of |x| < 2^-25 reach here only under the forced test hook
     r = hyp_plain<H>(x, CRM_EXP2_T16_D, hard);
+    unresolved = 2;  // an FP64 tier ran
   }
   if (!hard && !force) return r;
   Pair<double> y = hyp_dd_y<H>(x);
   r = round_dd_to_f(y.hi, y.lo, HYP_DD_EPS * fabs(y.hi), hard);
-  unresolved = hard;
+  unresolved = hard ? 3 : 2;  // the double-double tier ran
   return r;
 }
 

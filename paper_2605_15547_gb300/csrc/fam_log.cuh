@@ -318,9 +318,18 @@ template <int KIND> CRM_DEV float logq_round(U128 Z, uint64_t err, bool &hard) {
   return zero ? 0.0f : bitsf(bits | (neg ? 0x80000000u : 0u));
 }
 
+// The binary64 bit pattern of a positive finite binary32 x, by integer operations.
+CRM_DEV uint64_t f2d_bits_pos(float x) {
+  const uint32_t b = fbits(x), m = b & 0x007FFFFFu;
+  const uint32_t E = b >> 23;
+  if (E != 0) return ((uint64_t)(E + 896u) << 52) | ((uint64_t)m << 29);
+  const int p = 31 - __clz(m);  // subnormal: x = m 2^-149, leading bit p in [0, 22]
+  return ((uint64_t)(p + 874) << 52) | (((uint64_t)m << (52 - p)) & 0x000FFFFFFFFFFFFFull);
+}
+
 template <int KIND> CRM_DEV float logf_int(float x, bool &hard) {
   uint64_t err;
-  const U128 Z = logz_q116(dbits((double)x), (const ulonglong2 *)CRM_LOGI_L, CRM_LOGI_R, err);
+  const U128 Z = logz_q116(f2d_bits_pos(x), (const ulonglong2 *)CRM_LOGI_L, CRM_LOGI_R, err);
   return logq_round<KIND>(Z, err, hard);
 }
 
@@ -338,7 +347,7 @@ CRM_DEV float log1pf_int(float x, bool &hard) {
   uint64_t err;
   const ulonglong2 *LT = (const ulonglong2 *)CRM_LOGI_L;
   if (x < 0x1p53f) return logq_round<0>(logz_q116(dbits((double)x + 1.0), LT, CRM_LOGI_R, err), err, hard);
-  U128 Z = logz_q116(dbits((double)x), LT, CRM_LOGI_R, err);
+  U128 Z = logz_q116(f2d_bits_pos(x), LT, CRM_LOGI_R, err);
   const uint32_t rb = fbits(1.0f / (x * 0x1p-100f));  // 2^100/x in [2^-28, 2^47], normal
   const uint64_t Mr = (rb & 0x007FFFFFu) | 0x00800000u;
   const int s = (int)(rb >> 23) - 134;  // 2^116/x = Mr 2^(Er - 150 - 100 + 116)
@@ -349,14 +358,14 @@ CRM_DEV float log1pf_int(float x, bool &hard) {
 }
 
 // Slow path: the FP64-free tier, then double-double.
-template <int KIND> CRM_DEV float log_slow(float x, bool &unresolved, bool force) {
+template <int KIND> CRM_DEV float log_slow(float x, int &unresolved, bool force) {
   bool hard;
   unresolved = false;
   if (!log_ok<KIND>(x)) return special_log<KIND>(x);
   float r = KIND == 3 ? log1pf_int(x, hard) : logf_int<KIND>(x, hard);
   if (!hard && !force) return r;
   r = log_dd<KIND>(x, hard);
-  unresolved = hard;
+  unresolved = hard ? 3 : 2;  // the double-double tier ran
   return r;
 }
 

@@ -92,7 +92,7 @@ CRM_DEV bool rsqrt_mid_above(uint32_t xb, uint32_t ab) {
   return !le128(prod, P < 64 ? U128{1ull << P, 0ull} : U128{0ull, 1ull << (P - 64)});
 }
 
-CRM_DEV float rsqrt_slow(float x, bool &unresolved, bool force) {
+CRM_DEV float rsqrt_slow(float x, int &unresolved, bool force) {
   (void)force;  // the exact decision is the only tier
   unresolved = false;
   float sp;

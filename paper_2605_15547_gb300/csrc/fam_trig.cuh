@@ -498,7 +498,7 @@ template <int KIND> CRM_DEV void trig_int(float x, float *y, bool &hard) {
 }
 
 // Slow path: the FP64-free tier, then double-double.
-template <int KIND> CRM_DEV void trig_slow(float x, float *y, bool &unresolved, bool force) {
+template <int KIND> CRM_DEV void trig_slow(float x, float *y, int &unresolved, bool force) {
   bool hard;
   unresolved = false;
   float sp;
@@ -524,7 +524,7 @@ template <int KIND> CRM_DEV void trig_slow(float x, float *y, bool &unresolved, 
     if (KIND == TRIG_SINCOS) y[1] = c;
   }
   if (x == 0.0f && KIND != TRIG_COS) y[0] = x;
-  unresolved = h0 || h1;
+  unresolved = (h0 || h1) ? 3 : 2;  // the double-double tier ran
 }
 
 }  // namespace crm

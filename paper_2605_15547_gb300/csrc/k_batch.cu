@@ -161,16 +161,17 @@ struct SlowOp {
   bool force;
   const BatchDesc *d;
   uint64_t idx;
-  unsigned long long *unres;
+  unsigned long long *unres, *fp64;
   template <class Fn> CRM_DEV void run() {
     using T = typename Fn::T;
     T y[2];
-    bool u;
+    int u;
     Fn::slow(x_from_bits<T>(xbits), y, u, force);
     T *out = (T *)d->out;
     out[idx] = y[0];
     if (Fn::NOUT == 2) out[d->n + idx] = y[1];
-    if (u) atomicAdd(unres, 1ull);
+    if (u & 1) atomicAdd(unres, 1ull);
+    if (u & 2) atomicAdd(fp64, 1ull);
   }
 };
 
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(KBLOCK) k_batch_slow(BatchArgs b) {
     uint32_t aid = (uint32_t)(e.idx >> 40);
     uint64_t idx = e.idx & ((1ull << 40) - 1);
     const BatchDesc *d = &b.descs[aid];
-    SlowOp op{e.x, b.force_hard == 1, d, idx, &b.hdr->unresolved_total};
+    SlowOp op{e.x, b.force_hard == 1, d, idx, &b.hdr->unresolved_total, &b.hdr->fp64_total};
     CRM_FOR_FUNC_ALL(d->func, op);
   });
 }

@@ -4,6 +4,8 @@
   digested (tests/exhaustive_hash.py) and compared with the digests the oracle's results
   gave (tests/golden/exhaustive/<func>.txt, written by tests/golden/make_exhaustive.py).
   A function whose file lists all 256 chunks is checked over its whole input space.
+* No FP64 in the default form: the slow path's FP64-free tier decides every queued lane
+  (crm_stats fp64_total stays 0 over all 2^32 inputs).
 * Between the forms: the double-float form and the plain FP64 form (two independent
   evaluations with their own rounding tests) give the same bits on all 2^32 inputs, and
   sincosf gives (sinf, cosf) bit for bit.
@@ -63,7 +65,11 @@ def test_exhaustive_against_oracle_digests(func, weights):
         if got != ref[c]:
             bad.append(c)
     assert not bad, f"{func}: chunks {bad[:8]} differ from the oracle ({len(bad)} of {len(ref)})"
-    assert crm.stats()["unresolved_total"] == 0
+    st = crm.stats()
+    assert st["unresolved_total"] == 0
+    # the FP64-free middle tier decides every lane the fast path queues: over all 2^32
+    # inputs no lane goes on to the FP64 (double-double) tier
+    assert st["fp64_total"] == 0, f"{func}: {st['fp64_total']} lanes ran the FP64 tier"
 
 
 @pytest.mark.parametrize("func", SINGLE)

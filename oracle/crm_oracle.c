@@ -906,16 +906,19 @@ static uint64_t sign_bit(const fmt_t *f) { return 1ull << (f->w - 1); }
 static uint64_t one_bits(const fmt_t *f) { return (uint64_t)f->bias << (f->p - 1); }
 static uint64_t qnan_bits(const fmt_t *f) { return inf_bits(f) | (1ull << (f->p - 2)); }
 
-/* Round the exact value a * 2^(E - F) to the format, to nearest with ties to even. */
-static uint64_t round_fixed(const limb *a, int n, int64_t E, const fmt_t *f) {
+/* Round the exact value a * 2^(E - F) to the format: mode ORC_RN to nearest with ties to
+   even, ORC_RD toward -inf, ORC_RU toward +inf, ORC_RZ toward zero (IEEE 754 Sec. 4.3).
+   A directed mode moves the magnitude up ("away") when it points away from zero. */
+static uint64_t round_fixed(const limb *a, int n, int64_t E, const fmt_t *f, int mode) {
   limb m[MAXL];
   int neg = fx_abs(m, a, n);
   int b = mag_bitlen(m, n);
   if (b == 0) return 0;
   uint64_t sbit = neg ? sign_bit(f) : 0;
+  int away = (mode == ORC_RU && !neg) || (mode == ORC_RD && neg);
   int64_t F = FB(n);
   int64_t ex = (int64_t)b - 1 + E - F; /* value in [2^ex, 2^(ex+1)) */
-  if (ex > f->emax) return sbit | inf_bits(f);
+  if (ex > f->emax) return sbit | ((mode == ORC_RN || away) ? inf_bits(f) : inf_bits(f) - 1);
   int64_t qe = (ex < f->emin ? f->emin : ex) - (f->p - 1); /* exponent of the last place */
   int64_t shift = E - F - qe;                              /* significand = m * 2^shift */
   uint64_t sig;
@@ -927,7 +930,11 @@ static uint64_t round_fixed(const limb *a, int n, int64_t E, const fmt_t *f) {
     for (int i = 0; i < f->p + 1; i++) sig |= (uint64_t)mag_bit(m, n, k + i) << i;
     int rb = mag_bit(m, n, k - 1);
     int st = mag_any_below(m, n, k - 1);
-    if (rb && (st || (sig & 1))) sig++;
+    if (mode == ORC_RN) {
+      if (rb && (st || (sig & 1))) sig++;
+    } else if (away && (rb || st)) {
+      sig++;
+    }
   }
   uint64_t bits;
   if (ex < f->emin)
@@ -1484,7 +1491,24 @@ static void ev_rsqrt(res_t *R, const dec_t *x, int n) {
 
 /* Handles NaN, infinities, zeros, out-of-domain inputs and saturated ranges.
    Returns 1 and sets *out if the result is decided here. */
-static int special(int kind, const dec_t *x, const fmt_t *f, uint64_t xbits, uint64_t *out) {
+/* The rounding, in mode, of a value beyond the largest finite number (huge) or of a
+   nonzero value below half the smallest subnormal (tiny), of the given sign. */
+static uint64_t rnd_huge(int neg, const fmt_t *f, int mode) {
+  int away = (mode == ORC_RU && !neg) || (mode == ORC_RD && neg);
+  return (neg ? sign_bit(f) : 0) | ((mode == ORC_RN || away) ? inf_bits(f) : inf_bits(f) - 1);
+}
+static uint64_t rnd_tiny(int neg, const fmt_t *f, int mode) {
+  int away = (mode == ORC_RU && !neg) || (mode == ORC_RD && neg);
+  return (neg ? sign_bit(f) : 0) | (away ? 1 : 0);
+}
+/* The rounding, in mode, of a value strictly between 1 - 2^-p and 1 in magnitude (sign
+   neg): 1 to nearest or away from zero, else the largest number below 1. */
+static uint64_t rnd_below_one(int neg, const fmt_t *f, int mode) {
+  int away = (mode == ORC_RU && !neg) || (mode == ORC_RD && neg);
+  return (neg ? sign_bit(f) : 0) | ((mode == ORC_RN || away) ? one_bits(f) : one_bits(f) - 1);
+}
+
+static int special(int kind, const dec_t *x, const fmt_t *f, uint64_t xbits, uint64_t *out, int mode) {
   const uint64_t INF = inf_bits(f), SB = sign_bit(f), ONE = one_bits(f), QN = qnan_bits(f);
   if (x->cls == CL_NAN) {
     *out = xbits | (1ull << (f->p - 2));
@@ -1501,14 +1525,14 @@ static int special(int kind, const dec_t *x, const fmt_t *f, uint64_t xbits, uin
       double hi = f->w == 32 ? 200.0 : 2000.0;
       if (kind == K_EXP2) hi = f->w == 32 ? 160.0 : 1100.0;
       if (kind == K_EXP10) hi = f->w == 32 ? 50.0 : 330.0;
-      if (ax >= hi) { *out = x->neg ? 0 : INF; return 1; }
+      if (ax >= hi) { *out = x->neg ? rnd_tiny(0, f, mode) : rnd_huge(0, f, mode); return 1; }
       return 0;
     }
     case K_EXPM1:
       if (x->cls == CL_ZERO) { *out = xbits; return 1; }
       if (x->cls == CL_INF) { *out = x->neg ? (SB | ONE) : INF; return 1; }
-      if (!x->neg && ax >= 200.0) { *out = INF; return 1; }
-      if (x->neg && ax >= 40.0) { *out = SB | ONE; return 1; } /* -1 + e^x, e^x < 2^-57 */
+      if (!x->neg && ax >= 200.0) { *out = rnd_huge(0, f, mode); return 1; }
+      if (x->neg && ax >= 40.0) { *out = rnd_below_one(1, f, mode); return 1; } /* -1 + e^x, e^x < 2^-57 */
       return 0;
     case K_LOG: case K_LOG2: case K_LOG10:
       if (x->cls == CL_ZERO) { *out = SB | INF; return 1; }
@@ -1543,15 +1567,18 @@ static int special(int kind, const dec_t *x, const fmt_t *f, uint64_t xbits, uin
       return 0; /* +-inf handled in the evaluator */
     case K_SINH:
       if (x->cls == CL_ZERO) { *out = xbits; return 1; }
-      if (x->cls == CL_INF || ax >= 200.0) { *out = sgn | INF; return 1; }
+      if (x->cls == CL_INF) { *out = sgn | INF; return 1; }
+      if (ax >= 200.0) { *out = rnd_huge(x->neg, f, mode); return 1; }
       return 0;
     case K_COSH:
       if (x->cls == CL_ZERO) { *out = ONE; return 1; }
-      if (x->cls == CL_INF || ax >= 200.0) { *out = INF; return 1; }
+      if (x->cls == CL_INF) { *out = INF; return 1; }
+      if (ax >= 200.0) { *out = rnd_huge(0, f, mode); return 1; }
       return 0;
     case K_TANH:
       if (x->cls == CL_ZERO) { *out = xbits; return 1; }
-      if (x->cls == CL_INF || ax >= 40.0) { *out = sgn | ONE; return 1; } /* 1 - 2e^-80 */
+      if (x->cls == CL_INF) { *out = sgn | ONE; return 1; }
+      if (ax >= 40.0) { *out = rnd_below_one(x->neg, f, mode); return 1; } /* 1 - 2e^-80 */
       return 0;
     case K_RSQRT:
       if (x->cls == CL_ZERO) { *out = sgn | INF; return 1; }
@@ -1592,8 +1619,38 @@ static void evaluate(int kind, const dec_t *x, int n, res_t *R) {
 static const int LEVEL_LIMBS[] = {2, 3, 5, 9, 17, 33};
 #define NLEVELS 6
 
-static int ziv(int kind, const dec_t *x, uint64_t xbits, const fmt_t *f, uint64_t *out) {
-  if (special(kind, x, f, xbits, out)) {
+static uint32_t f32_bits(float v) { uint32_t b; memcpy(&b, &v, 4); return b; }
+static uint64_t f64_bits(double v) { uint64_t b; memcpy(&b, &v, 8); return b; }
+
+/* Results that are exact format numbers although the evaluator's interval around them
+   is not degenerate: 10^k and log10(10^k) for the k with 10^k exact in the format.
+   (exp2 of an integer, log2 of a power of two and rsqrt of a power of four come out as
+   exact intervals; every other nonzero algebraic argument gives a transcendental value,
+   Lindemann-Weierstrass.)  Rounding to nearest decides these through the loop; a directed
+   mode needs them here. */
+static int exact_case(int kind, const dec_t *x, const fmt_t *f, uint64_t *out) {
+  const int kmax = f->w == 32 ? 10 : 22;
+  if (x->cls != CL_FINITE || x->neg) return 0;
+  double v = approx(x), p10 = 1.0;
+  if (kind == K_EXP10 && is_integer(x) && v <= kmax) {
+    for (int i = 0; i < (int)v; i++) p10 *= 10.0;
+    *out = f->w == 32 ? (uint64_t)f32_bits((float)p10) : f64_bits(p10);
+    return 1;
+  }
+  if (kind == K_LOG10) {
+    for (int k = 1; k <= kmax; k++) {
+      p10 *= 10.0;
+      if (v == p10) {
+        *out = f->w == 32 ? (uint64_t)f32_bits((float)k) : f64_bits((double)k);
+        return 1;
+      }
+    }
+  }
+  return 0;
+}
+
+static int ziv(int kind, const dec_t *x, uint64_t xbits, const fmt_t *f, uint64_t *out, int mode) {
+  if (special(kind, x, f, xbits, out, mode) || (mode != ORC_RN && exact_case(kind, x, f, out))) {
     g_last_level = -1;
     return ORC_OK;
   }
@@ -1610,7 +1667,7 @@ static int ziv(int kind, const dec_t *x, uint64_t xbits, const fmt_t *f, uint64_
       evaluate(kind, x, n, &R);
     }
     if (g_fail) continue;
-    uint64_t a = round_fixed(R.v.lo, n, R.E, f), b = round_fixed(R.v.hi, n, R.E, f);
+    uint64_t a = round_fixed(R.v.lo, n, R.E, f, mode), b = round_fixed(R.v.hi, n, R.E, f, mode);
     if (a == b) {
       *out = a;
       g_last_level = lvl;
@@ -1632,38 +1689,43 @@ static int kind_of(int func, int *is64) {
   return map[func];
 }
 
-int crm_oracle_f32(int func, uint32_t x, uint32_t *out) {
+int crm_oracle_f32(int func, uint32_t x, uint32_t *out) { return crm_oracle_f32_rm(func, x, ORC_RN, out); }
+int crm_oracle_f64(int func, uint64_t x, uint64_t *out) { return crm_oracle_f64_rm(func, x, ORC_RN, out); }
+
+int crm_oracle_f32_rm(int func, uint32_t x, int mode, uint32_t *out) {
   int is64;
+  if (mode < ORC_RN || mode > ORC_RZ) return ORC_ERR_FUNC;
   int kind = kind_of(func, &is64);
   if (kind == -2 || is64) return ORC_ERR_FUNC;
   dec_t d = dec32(x);
   uint64_t r;
   if (func == ORC_SINCOSF) {
-    int st = ziv(K_SIN, &d, x, &FMT32, &r);
+    int st = ziv(K_SIN, &d, x, &FMT32, &r, mode);
     if (st) return st;
     out[0] = (uint32_t)r;
-    st = ziv(K_COS, &d, x, &FMT32, &r);
+    st = ziv(K_COS, &d, x, &FMT32, &r, mode);
     out[1] = (uint32_t)r;
     return st;
   }
-  int st = ziv(kind, &d, x, &FMT32, &r);
+  int st = ziv(kind, &d, x, &FMT32, &r, mode);
   out[0] = (uint32_t)r;
   return st;
 }
 
-int crm_oracle_f64(int func, uint64_t x, uint64_t *out) {
+int crm_oracle_f64_rm(int func, uint64_t x, int mode, uint64_t *out) {
   int is64;
+  if (mode < ORC_RN || mode > ORC_RZ) return ORC_ERR_FUNC;
   int kind = kind_of(func, &is64);
   if (kind < 0 || !is64) return ORC_ERR_FUNC;
   dec_t d = dec64(x);
-  return ziv(kind, &d, x, &FMT64, out);
+  return ziv(kind, &d, x, &FMT64, out, mode);
 }
 
 int crm_oracle_last_level(void) { return g_last_level; }
 
 /* ---- threaded array drivers ---- */
 typedef struct {
-  int func, is64;
+  int func, is64, mode;
   const void *in;
   void *out;
   uint64_t n;
@@ -1681,14 +1743,14 @@ static void *worker(void *arg) {
     for (uint64_t i = start; i < end; i++) {
       int st;
       if (J->is64) {
-        st = crm_oracle_f64(J->func, ((const uint64_t *)J->in)[i], ((uint64_t *)J->out) + i);
+        st = crm_oracle_f64_rm(J->func, ((const uint64_t *)J->in)[i], J->mode, ((uint64_t *)J->out) + i);
       } else if (J->func == ORC_SINCOSF) {
         uint32_t sc[2];
-        st = crm_oracle_f32(J->func, ((const uint32_t *)J->in)[i], sc);
+        st = crm_oracle_f32_rm(J->func, ((const uint32_t *)J->in)[i], J->mode, sc);
         ((uint32_t *)J->out)[i] = sc[0];
         ((uint32_t *)J->out)[J->n + i] = sc[1];
       } else {
-        st = crm_oracle_f32(J->func, ((const uint32_t *)J->in)[i], ((uint32_t *)J->out) + i);
+        st = crm_oracle_f32_rm(J->func, ((const uint32_t *)J->in)[i], J->mode, ((uint32_t *)J->out) + i);
       }
       if (st) {
         int zero = 0;
@@ -1720,20 +1782,27 @@ static int run_job(job_t *J, int nthreads) {
   return J->status;
 }
 
-int crm_oracle_f32_array(int func, const uint32_t *in, uint32_t *out, uint64_t n, int nthreads) {
+int crm_oracle_f32_array_rm(int func, const uint32_t *in, uint32_t *out, uint64_t n, int nthreads, int mode) {
   int is64;
   int kind = kind_of(func, &is64);
-  if (kind == -2 || is64) return ORC_ERR_FUNC;
-  job_t J = {func, 0, in, out, n, 0, 0};
+  if (kind == -2 || is64 || mode < ORC_RN || mode > ORC_RZ) return ORC_ERR_FUNC;
+  job_t J = {func, 0, mode, in, out, n, 0, 0};
   return run_job(&J, nthreads);
 }
 
-int crm_oracle_f64_array(int func, const uint64_t *in, uint64_t *out, uint64_t n, int nthreads) {
+int crm_oracle_f64_array_rm(int func, const uint64_t *in, uint64_t *out, uint64_t n, int nthreads, int mode) {
   int is64;
   int kind = kind_of(func, &is64);
-  if (kind < 0 || !is64) return ORC_ERR_FUNC;
-  job_t J = {func, 1, in, out, n, 0, 0};
+  if (kind < 0 || !is64 || mode < ORC_RN || mode > ORC_RZ) return ORC_ERR_FUNC;
+  job_t J = {func, 1, mode, in, out, n, 0, 0};
   return run_job(&J, nthreads);
+}
+
+int crm_oracle_f32_array(int func, const uint32_t *in, uint32_t *out, uint64_t n, int nthreads) {
+  return crm_oracle_f32_array_rm(func, in, out, n, nthreads, ORC_RN);
+}
+int crm_oracle_f64_array(int func, const uint64_t *in, uint64_t *out, uint64_t n, int nthreads) {
+  return crm_oracle_f64_array_rm(func, in, out, n, nthreads, ORC_RN);
 }
 
 /* ---- diagnostics ---- */

@@ -32,16 +32,25 @@ enum {
 
 enum { ORC_OK = 0, ORC_ERR_FUNC = 1, ORC_ERR_CAP = 2 };
 
+/* Rounding direction (IEEE 754 Sec. 4.3): to nearest, ties to even (the paper's mode and
+   the library's); toward -inf; toward +inf; toward zero. */
+enum { ORC_RN = 0, ORC_RD = 1, ORC_RU = 2, ORC_RZ = 3 };
+
 /* One binary32 input (bit pattern) -> result bit pattern.  For ORC_SINCOSF, out[0]
    receives sin and out[1] cos.  Returns ORC_OK, ORC_ERR_FUNC (bad id / wrong
    format) or ORC_ERR_CAP (Ziv precision cap reached: never expected). */
 int crm_oracle_f32(int func, uint32_t x, uint32_t *out);
 int crm_oracle_f64(int func, uint64_t x, uint64_t *out);
+/* The same in rounding direction mode (ORC_RN .. ORC_RZ; another value: ORC_ERR_FUNC). */
+int crm_oracle_f32_rm(int func, uint32_t x, int mode, uint32_t *out);
+int crm_oracle_f64_rm(int func, uint64_t x, int mode, uint64_t *out);
 
 /* Array forms, multithreaded with nthreads POSIX threads (<=0: one per online core).
    For ORC_SINCOSF, out holds 2n words: sin in [0,n), cos in [n,2n). */
 int crm_oracle_f32_array(int func, const uint32_t *in, uint32_t *out, uint64_t n, int nthreads);
 int crm_oracle_f64_array(int func, const uint64_t *in, uint64_t *out, uint64_t n, int nthreads);
+int crm_oracle_f32_array_rm(int func, const uint32_t *in, uint32_t *out, uint64_t n, int nthreads, int mode);
+int crm_oracle_f64_array_rm(int func, const uint64_t *in, uint64_t *out, uint64_t n, int nthreads, int mode);
 
 /* Diagnostics for the oracle's own tests: the Ziv level (0 = first precision) at which
    the last call on this thread finished, and the constants as scaled integers. */

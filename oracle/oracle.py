@@ -59,6 +59,9 @@ def _load():
             lib.crm_oracle_f64.argtypes = [ctypes.c_int, ctypes.c_uint64, u64p]
             lib.crm_oracle_f32_array.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_uint64, ctypes.c_int]
+            for nm in ("crm_oracle_f32_array_rm", "crm_oracle_f64_array_rm"):
+                getattr(lib, nm).argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
             lib.crm_oracle_f64_array.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_uint64, ctypes.c_int]
             lib.crm_oracle_constant.argtypes = [ctypes.c_int, ctypes.c_int, u64p, u64p]
@@ -77,10 +80,14 @@ def _fid(func) -> int:
     return FUNC_ID[func] if isinstance(func, str) else int(func)
 
 
-def eval_bits(func, xbits: np.ndarray, nthreads: int = 0) -> np.ndarray:
+MODES = {"rn": 0, "rd": 1, "ru": 2, "rz": 3}
+
+
+def eval_bits(func, xbits: np.ndarray, nthreads: int = 0, mode: str = "rn") -> np.ndarray:
     """Correctly rounded results as bit patterns.  ``xbits`` is uint32 (binary32
     functions) or uint64 (binary64 functions).  For sincosf the result has shape (2, n):
-    row 0 is sin, row 1 cos."""
+    row 0 is sin, row 1 cos.  ``mode``: rounding direction, "rn" (to nearest, ties to
+    even), "rd" (toward -inf), "ru" (toward +inf) or "rz" (toward zero)."""
     lib = _load()
     fid = _fid(func)
     is64 = FUNCS[fid] in F64_FUNCS
@@ -90,8 +97,8 @@ def eval_bits(func, xbits: np.ndarray, nthreads: int = 0) -> np.ndarray:
     rows = 2 if FUNCS[fid] == "sincosf" else 1
     out = np.zeros(rows * n, dtype=dt)
     if n:
-        fn = lib.crm_oracle_f64_array if is64 else lib.crm_oracle_f32_array
-        st = fn(fid, x.ctypes.data, out.ctypes.data, n, nthreads)
+        fn = lib.crm_oracle_f64_array_rm if is64 else lib.crm_oracle_f32_array_rm
+        st = fn(fid, x.ctypes.data, out.ctypes.data, n, nthreads, MODES[mode])
         if st:
             raise OracleError(f"oracle status {st} for {FUNCS[fid]}")
     return out.reshape(2, n) if rows == 2 else out

@@ -4,7 +4,9 @@
  * What it computes: out = RN_fmt(f(x)), the correctly rounded (to nearest, ties to
  * even) value of f at the floating-point input x, in binary32 or binary64, with
  * gradual underflow and overflow to infinity (the correct-rounding goal of Sec. I and
- * Sec. II; GPU runs use round-to-nearest-even only, Sec. III.C).
+ * Sec. II; GPU runs use round-to-nearest-even only, Sec. III.C).  The _rm entry points
+ * round in a directed mode instead (toward -inf, +inf or zero, IEEE 754 Sec. 4.3): the
+ * same loop with the mode in the final rounding, exact results listed before it.
  *
  * How: Ziv's strategy (Sec. I).  Every quantity is an interval [lo, hi] of fixed-point
  * numbers N / 2^F held as two's-complement multi-limb integers (F = 64*(n-1) fraction

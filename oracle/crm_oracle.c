@@ -902,6 +902,30 @@ typedef struct {
 } fmt_t;
 static const fmt_t FMT32 = {24, -126, 127, 127, 32};
 static const fmt_t FMT64 = {53, -1022, 1023, 1023, 64};
+static const fmt_t FMT16 = {11, -14, 15, 15, 16};      /* IEEE binary16 */
+static const fmt_t FMTB16 = {8, -126, 127, 127, 16};   /* bfloat16: binary32's range, 8 bits */
+
+/* Decode a bit pattern of the 16-bit formats (the same rules as dec32 / dec64). */
+static dec_t dec_fmt(uint64_t b, const fmt_t *f) {
+  dec_t d;
+  const int ew = f->w - f->p;  /* exponent field width */
+  d.neg = (int)((b >> (f->w - 1)) & 1);
+  uint64_t be = (b >> (f->p - 1)) & ((1ull << ew) - 1), fr = b & ((1ull << (f->p - 1)) - 1);
+  d.M = 0;
+  d.e = 0;
+  if (be == (1ull << ew) - 1) {
+    d.cls = fr ? CL_NAN : CL_INF;
+  } else if (be == 0) {
+    d.cls = fr ? CL_FINITE : CL_ZERO;
+    d.M = fr;
+    d.e = f->emin - (f->p - 1);
+  } else {
+    d.cls = CL_FINITE;
+    d.M = fr | (1ull << (f->p - 1));
+    d.e = (int64_t)be - f->bias - (f->p - 1);
+  }
+  return d;
+}
 
 static uint64_t inf_bits(const fmt_t *f) { return (uint64_t)(2 * f->bias + 1) << (f->p - 1); }
 static uint64_t sign_bit(const fmt_t *f) { return 1ull << (f->w - 1); }
@@ -1621,8 +1645,13 @@ static void evaluate(int kind, const dec_t *x, int n, res_t *R) {
 static const int LEVEL_LIMBS[] = {2, 3, 5, 9, 17, 33};
 #define NLEVELS 6
 
-static uint32_t f32_bits(float v) { uint32_t b; memcpy(&b, &v, 4); return b; }
-static uint64_t f64_bits(double v) { uint64_t b; memcpy(&b, &v, 8); return b; }
+/* The pattern of a positive normal number v of the format, v exact in binary64. */
+static uint64_t fmt_bits(double v, const fmt_t *f) {
+  int e;
+  double m = frexp(v, &e); /* v = m 2^e, m in [1/2, 1) */
+  uint64_t M = (uint64_t)ldexp(m, f->p);
+  return ((uint64_t)(e - 1 + f->bias) << (f->p - 1)) + M - (1ull << (f->p - 1));
+}
 
 /* Results that are exact format numbers although the evaluator's interval around them
    is not degenerate: 10^k and log10(10^k) for the k with 10^k exact in the format.
@@ -1631,19 +1660,20 @@ static uint64_t f64_bits(double v) { uint64_t b; memcpy(&b, &v, 8); return b; }
    Lindemann-Weierstrass.)  Rounding to nearest decides these through the loop; a directed
    mode needs them here. */
 static int exact_case(int kind, const dec_t *x, const fmt_t *f, uint64_t *out) {
-  const int kmax = f->w == 32 ? 10 : 22;
+  /* 10^k = 2^k 5^k is exact while 5^k fits the precision */
+  const int kmax = f->p == 53 ? 22 : (f->p == 24 ? 10 : (f->p == 11 ? 4 : 3));
   if (x->cls != CL_FINITE || x->neg) return 0;
   double v = approx(x), p10 = 1.0;
   if (kind == K_EXP10 && is_integer(x) && v <= kmax) {
     for (int i = 0; i < (int)v; i++) p10 *= 10.0;
-    *out = f->w == 32 ? (uint64_t)f32_bits((float)p10) : f64_bits(p10);
+    *out = fmt_bits(p10, f);
     return 1;
   }
   if (kind == K_LOG10) {
     for (int k = 1; k <= kmax; k++) {
       p10 *= 10.0;
       if (v == p10) {
-        *out = f->w == 32 ? (uint64_t)f32_bits((float)k) : f64_bits((double)k);
+        *out = fmt_bits((double)k, f);
         return 1;
       }
     }
@@ -1712,6 +1742,38 @@ int crm_oracle_f32_rm(int func, uint32_t x, int mode, uint32_t *out) {
   int st = ziv(kind, &d, x, &FMT32, &r, mode);
   out[0] = (uint32_t)r;
   return st;
+}
+
+int crm_oracle_f16_rm(int func, int fmt, uint32_t x, int mode, uint32_t *out) {
+  int is64;
+  int kind = kind_of(func, &is64);
+  if (kind == -2 || is64 || (fmt != ORC_FMT_F16 && fmt != ORC_FMT_BF16) || mode < ORC_RN || mode > ORC_RZ)
+    return ORC_ERR_FUNC;
+  const fmt_t *f = fmt == ORC_FMT_F16 ? &FMT16 : &FMTB16;
+  dec_t d = dec_fmt(x & 0xFFFFu, f);
+  uint64_t r;
+  if (func == ORC_SINCOSF) {
+    int st = ziv(K_SIN, &d, x & 0xFFFFu, f, &r, mode);
+    if (st) return st;
+    out[0] = (uint32_t)r;
+    st = ziv(K_COS, &d, x & 0xFFFFu, f, &r, mode);
+    out[1] = (uint32_t)r;
+    return st;
+  }
+  int st = ziv(kind, &d, x & 0xFFFFu, f, &r, mode);
+  out[0] = (uint32_t)r;
+  return st;
+}
+
+int crm_oracle_f16_array(int func, int fmt, const uint16_t *in, uint16_t *out, uint64_t n, int mode) {
+  for (uint64_t i = 0; i < n; i++) {
+    uint32_t r[2];
+    int st = crm_oracle_f16_rm(func, fmt, in[i], mode, r);
+    if (st) return st;
+    out[i] = (uint16_t)r[0];
+    if (func == ORC_SINCOSF) out[n + i] = (uint16_t)r[1];
+  }
+  return ORC_OK;
 }
 
 int crm_oracle_f64_rm(int func, uint64_t x, int mode, uint64_t *out) {

@@ -45,6 +45,14 @@ int crm_oracle_f64(int func, uint64_t x, uint64_t *out);
 int crm_oracle_f32_rm(int func, uint32_t x, int mode, uint32_t *out);
 int crm_oracle_f64_rm(int func, uint64_t x, int mode, uint64_t *out);
 
+/* The binary32 function ids evaluated for 16-bit formats: IEEE binary16 (ORC_FMT_F16:
+   11-bit precision, exponents -14..15) or bfloat16 (ORC_FMT_BF16: 8-bit precision,
+   binary32's exponent range); inputs and results are 16-bit patterns.  The array form
+   is single-threaded (sincosf: sin in out[0, n), cos in out[n, 2n)). */
+enum { ORC_FMT_F16 = 0, ORC_FMT_BF16 = 1 };
+int crm_oracle_f16_rm(int func, int fmt, uint32_t x, int mode, uint32_t *out);
+int crm_oracle_f16_array(int func, int fmt, const uint16_t *in, uint16_t *out, uint64_t n, int mode);
+
 /* Array forms, multithreaded with nthreads POSIX threads (<=0: one per online core).
    For ORC_SINCOSF, out holds 2n words: sin in [0,n), cos in [n,2n). */
 int crm_oracle_f32_array(int func, const uint32_t *in, uint32_t *out, uint64_t n, int nthreads);

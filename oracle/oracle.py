@@ -62,6 +62,8 @@ def _load():
             for nm in ("crm_oracle_f32_array_rm", "crm_oracle_f64_array_rm"):
                 getattr(lib, nm).argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
+            lib.crm_oracle_f16_array.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_uint64, ctypes.c_int]
             lib.crm_oracle_f64_array.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_uint64, ctypes.c_int]
             lib.crm_oracle_constant.argtypes = [ctypes.c_int, ctypes.c_int, u64p, u64p]
@@ -101,6 +103,26 @@ def eval_bits(func, xbits: np.ndarray, nthreads: int = 0, mode: str = "rn") -> n
         st = fn(fid, x.ctypes.data, out.ctypes.data, n, nthreads, MODES[mode])
         if st:
             raise OracleError(f"oracle status {st} for {FUNCS[fid]}")
+    return out.reshape(2, n) if rows == 2 else out
+
+
+HALF_FMTS = {"f16": 0, "bf16": 1}
+
+
+def eval_bits16(func, xbits: np.ndarray, fmt: str = "f16", mode: str = "rn") -> np.ndarray:
+    """Correctly rounded results of a binary32 function's formula for 16-bit inputs and
+    results (IEEE binary16 "f16" or bfloat16 "bf16"), as uint16 bit patterns; sincosf
+    gives shape (2, n)."""
+    lib = _load()
+    fid = _fid(func)
+    x = np.ascontiguousarray(xbits, dtype=np.uint16).ravel()
+    n = x.size
+    rows = 2 if FUNCS[fid] == "sincosf" else 1
+    out = np.zeros(rows * n, dtype=np.uint16)
+    if n:
+        st = lib.crm_oracle_f16_array(fid, HALF_FMTS[fmt], x.ctypes.data, out.ctypes.data, n, MODES[mode])
+        if st:
+            raise OracleError(f"oracle status {st} for {FUNCS[fid]} ({fmt})")
     return out.reshape(2, n) if rows == 2 else out
 
 

@@ -55,7 +55,7 @@ TRAFFIC_BYTES_PER_ELEM = {"expf": 6.642, "exp2f": 6.652, "exp10f": 6.662, "expm1
                           "asinf": 6.71, "acosf": 6.731, "atanf": 6.735, "sinhf": 6.683,
                           "coshf": 6.679, "tanhf": 6.711, "rsqrtf": 6.482, "exp2": 14.487,
                           "log": 14.471}
-TRAFFIC_SOURCES = "38247a7c890413be"  # profiles/traffic_main_kernels_2p25.md, k_main_sincosf_df_2p25.md
+TRAFFIC_SOURCES = "38247a7c890413be"  # the kernel sources the ncu captures were taken on
 
 
 def kernel_sources_fingerprint() -> str:
@@ -73,6 +73,29 @@ def measured_traffic(func: str, n: int):
     if func not in TRAFFIC_BYTES_PER_ELEM or kernel_sources_fingerprint() != TRAFFIC_SOURCES:
         return None
     return TRAFFIC_BYTES_PER_ELEM[func] * n
+
+
+# Thread instructions per element of each function's main kernel (smsp__inst_executed.sum x 32
+# / elements, one ncu capture per function on 2^25 domain inputs), gated by the same source
+# fingerprint as the traffic figures.  The kernels are bound by instruction issue, not by
+# DRAM: 152 SMs x 4 schedulers issue one warp instruction each per cycle.
+INST_PER_ELEM = {"expf": 56.5, "exp2f": 48.8, "exp10f": 57.3, "expm1f": 89.6, "logf": 74.6,
+                 "log2f": 74.2, "log10f": 73.9, "log1pf": 82.2, "sinf": 130.0, "cosf": 124.9,
+                 "sincosf": 151.5, "tanf": 143.5, "asinf": 137.6, "acosf": 143.9, "atanf": 108.0,
+                 "sinhf": 126.9, "coshf": 89.6, "tanhf": 116.2, "rsqrtf": 67.8, "exp2": 194.5,
+                 "log": 415.0}
+SMS, SCHEDULERS_PER_SM, WARP = 152, 4, 32
+
+
+def issue_peak_tinst_s(sm_mhz: float) -> float:
+    """Thread instructions per second the GPU can issue at the given SM clock."""
+    return SMS * SCHEDULERS_PER_SM * WARP * sm_mhz * 1e6 / 1e12
+
+
+def inst_per_elem(func: str):
+    if func not in INST_PER_ELEM or kernel_sources_fingerprint() != TRAFFIC_SOURCES:
+        return None
+    return INST_PER_ELEM[func]
 
 
 def load_peaks():
@@ -223,6 +246,15 @@ def time_calls(crm, torch, funcs, xs, ys, form, reps, stream):
 
 
 def run_batch(args, crm, torch, dev, stream, rank, world):
+    line = batch_measure(args, crm, torch, dev, stream, world)
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def batch_measure(args, crm, torch, dev, stream, world):
+    """The batching form on the 10,000-array workload: the step is one CUDA-graph replay of
+    the batched call; returns the JSON line's fields."""
     count = args.batch_count
     rng = np.random.Generator(np.random.PCG64(W.seed_for(4, 0)))
     lens, funcs = W.batch_lengths(count, rng)
@@ -311,9 +343,41 @@ def run_batch(args, crm, torch, dev, stream, rank, world):
         "e2e": {"value": None, "unit": "Gelem/s", "note": "batch workload is device resident"},
         "cpu_baseline": None,
     }
-    if rank == 0:
-        print(json.dumps(line))
-    return 0
+    return line
+
+
+def measure_set(args, crm, torch, dev, workload, reps=3):
+    """One of the other workloads (the 2^28 precision arrays, the binary64 pair) measured
+    beside the headline step: per array, the default form's and the plain form's device time
+    per call (CUDA events, back-to-back calls on arrays larger than L2), both rooflines and
+    the hard-case rate.  The arrays are freed on return."""
+    spec, cfg = W.bench_arrays(workload, args.scale)
+    peak, _ = load_peaks()
+    out = {"config": cfg["workload"]}
+    stream = torch.cuda.current_stream()
+    for lab, f, n in spec:
+        x = W.bench_input_device(workload, lab, f, n, dev)
+        y = torch.empty(((2,) if f == "sincosf" else ()) + (n,), dtype=x.dtype, device=dev)
+        if not args.no_autotune:
+            crm.autotune(f, x, y, form=args.form, reps=2)
+        ms = time_calls(crm, torch, [f], [x], [y], args.form, reps, stream)[0]
+        try:
+            ms_plain = time_calls(crm, torch, [f], [x], [y], "plain", 2, stream)[0]
+        except crm.CrmError:
+            ms_plain = None
+        crm.stats_reset()
+        crm.eval_into(f, x, y, form=args.form)
+        st = crm.stats()
+        g = n / (ms / 1e3) / 1e9
+        ipe = inst_per_elem(f)
+        out[lab] = {"gelem_s": g, "hbm_frac": g * bytes_per_elem(f) / peak,
+                    "issue_frac": (g * ipe / 1e3 / issue_peak_tinst_s(2070.0)) if ipe else None,
+                    "plain_gelem_s": (n / (ms_plain / 1e3) / 1e9) if ms_plain else None,
+                    "df_over_plain": (ms_plain / ms) if ms_plain else None,
+                    "hard_case_rate": st["hard_total"] / n, "unresolved": st["unresolved_total"]}
+        del x, y
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -331,7 +395,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="launch shape for every array (skips the autotuner; profiling runs)")
     ap.add_argument("--funcs", default="", help="comma list restricting the workload (testing)")
+    ap.add_argument("--extras", default="precision,f64,batch",
+                    help="other workloads measured after the headline step (comma list, or none)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -372,6 +440,11 @@ def main():
 
     # the autotuner picks each array's launch shape on that array (untimed)
     tuned = {}
+    if args.variant >= 0:
+        for f in funcs:
+            crm.set_variant(f, args.variant, form=args.form)
+        args.no_autotune = True
+        tuned = {"all": f"variant {args.variant}"}
     if not args.no_autotune:
         for lab, f, x, y in zip(labels, funcs, xs, ys):
             best, _ = crm.autotune(f, x, y, form=args.form, reps=2)
@@ -420,9 +493,11 @@ def main():
     per_arr = {}
     for i, lab in enumerate(labels):
         n = xs[i].numel()
+        gi = n / (ms_main[i] / 1e3) / 1e9
+        ipe = inst_per_elem(funcs[i])
         per_arr[lab] = {
-            args.form: {"gelem_s": n / (ms_main[i] / 1e3) / 1e9,
-                        "hbm_frac": n * bytes_per_elem(funcs[i]) / (ms_main[i] / 1e3) / 1e9 / peak},
+            args.form: {"gelem_s": gi, "hbm_frac": gi * bytes_per_elem(funcs[i]) / peak,
+                        "issue_frac": (gi * ipe / 1e3 / issue_peak_tinst_s(2070.0)) if ipe else None},
             "hard_case_rate": hard[i]}
         if ms_other is not None:
             per_arr[lab][other] = {"gelem_s": n / (ms_other[i] / 1e3) / 1e9}
@@ -433,6 +508,20 @@ def main():
     dom = int(np.argmax(ms_main))
     dom_bytes = xs[dom].numel() * bytes_per_elem(funcs[dom])
     achieved = dom_bytes / (ms_main[dom] / 1e3) / 1e9
+    hbm_roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": peak_kind}
+    # The binding bound of these kernels is instruction issue: thread instructions per
+    # element (ncu, the kernel's own sources) x elements / time, against 152 SMs x 4
+    # schedulers x 32 lanes x the SM clock (2070 MHz, the clock measured under load)
+    dom_ipe = inst_per_elem(funcs[dom])
+    if dom_ipe:
+        ach_i = xs[dom].numel() * dom_ipe / (ms_main[dom] / 1e3) / 1e12
+        pk_i = issue_peak_tinst_s(2070.0)
+        roof = {"bound": "alu", "achieved": ach_i, "peak": pk_i, "unit": "Tinst/s", "frac": ach_i / pk_i,
+                "peak_kind": "derived: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz",
+                "inst_per_elem": dom_ipe, "hbm": hbm_roof}
+    else:
+        roof = dict(hbm_roof)
 
     e2e = None
     if not args.no_e2e:
@@ -473,15 +562,33 @@ def main():
         "data": "synthetic",
         "config": dict(cfg, form=args.form, arrays=labels, l2="inputs larger than L2 (no flush)",
                        parallelism=f"replicas{world}", launch_shapes=tuned or "default"),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(funcs[dom], xs[dom].numel()),
-                     "kernel": f"k_main+k_slow<{funcs[dom]}>",
-                     "array": labels[dom], "bytes_per_elem": bytes_per_elem(funcs[dom]), "peak_kind": peak_kind},
+        "roofline": dict(roof, traffic=measured_traffic(funcs[dom], xs[dom].numel()),
+                         kernel=f"k_main+k_slow<{funcs[dom]}>", array=labels[dom],
+                         bytes_per_elem=bytes_per_elem(funcs[dom])),
         "other_form": {"form": other, "step_gelem_s": step_other},
         "per_array": per_arr,
         "hard_case_rate": st["hard_total"] / max(1, n_elems * args.steps), "unresolved": st["unresolved_total"],
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * len(funcs) * 2, "clocks": clk,
     }
+    # the other workloads, measured after the headline step on freshly generated arrays
+    extras = [e for e in args.extras.split(",") if e and e != "none"] if args.workload == "all19" else []
+    if extras:
+        del xs, ys
+        if e2e is not None:
+            del hin, hout
+        torch.cuda.empty_cache()
+        line["extras"] = {}
+        for wl in extras:
+            if wl == "batch":
+                side = torch.cuda.Stream(device=dev)
+                with torch.cuda.stream(side):
+                    b = batch_measure(args, crm, torch, dev, side, world)
+                torch.cuda.empty_cache()
+                line["extras"]["batch"] = {k: b[k] for k in ("value", "ms_per_step", "config", "roofline",
+                                                             "one_launch_per_array", "direct_call",
+                                                             "hard_case_rate", "unresolved", "clocks")}
+            else:
+                line["extras"][wl] = measure_set(args, crm, torch, dev, wl)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -127,7 +127,11 @@ int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, u
    of 2^k elements (crm_set_batch_tile, default 2^14); each block of the persistent grid
    owns a contiguous range of tiles.  Asynchronous.  Capturable after crm_reserve(.., count).
    Binary64 arrays (exp2, log) may be mixed in; a batch that holds any runs in the grouped
-   mode (crm_set_batch_mode).  Errors: as crm_eval for any descriptor. */
+   mode (crm_set_batch_mode).  A captured call owns the descriptor buffers it staged: later
+   batch calls on the stream (captured or not) use new ones, so every captured graph keeps
+   evaluating the arrays it captured.  A second capture on the stream needs a batch call
+   outside capture, or crm_reserve, in between (else CRM_ERR_CAPTURE).  Errors: as
+   crm_eval for any descriptor. */
 int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream);
 /* Tile size of the batching form, 2^log2_elems elements (8 <= log2_elems <= 24). */
 int crm_set_batch_tile(int log2_elems);
@@ -194,13 +198,24 @@ int crm_autotune_batch(const crm_desc_t *descs, int count, int form, int reps, v
 #define CRM_NOALLOC_MAX_ELEMS (1ull << 20)
 int crm_eval_noalloc(int func_id, int dtype, int form, const void *in, void *out, uint64_t n,
                      void *stream);
+/* Counters of crm_eval_noalloc on the current device (the static array's header, shared by
+   every call on the device; same fields as crm_stats: unresolved_total and timeouts stay 0
+   unless something is wrong).  Copies them into *out after synchronising `stream`; calls
+   on other streams must have completed.  Allocates nothing.  The _reset form zeroes
+   them. */
+int crm_noalloc_stats(void *stream, crm_stats_t *out);
+int crm_noalloc_stats_reset(void *stream);
 
 /* Process-wide default form for crm_eval (initially from env CRM_FORM, else AUTO). */
 int crm_set_form(int form);
 
-/* Pre-allocate the workspace of (current device, stream) for calls of up to
-   max_elems elements and batches of up to max_arrays arrays, so that later calls
-   allocate nothing (required before capturing calls into a CUDA graph). */
+/* Pre-allocate the workspace of (current device, stream) so that later calls allocate
+   nothing (required before capturing calls into a CUDA graph): the hard-case queue gets
+   one entry per 64 elements of max_elems (room for a hard-case rate of 1/64 in one call;
+   at least 2^21 and at most 2^26 entries of 16 bytes; lanes beyond it are finished inline,
+   never dropped), and the batch descriptors room for max_arrays arrays.  A queue never
+   shrinks; a replaced queue stays allocated until crm_shutdown, because a graph captured
+   earlier may address it. */
 int crm_reserve(uint64_t max_elems, int max_arrays, void *stream);
 
 /* Read (and synchronise) the counters of (current device, stream). */

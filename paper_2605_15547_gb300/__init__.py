@@ -45,9 +45,32 @@ def out_shape(func, n: int):
     return (2, n) if FUNCS[_fid(func)] == "sincosf" else (n,)
 
 
+def _check_tensors(fid: int, x, out) -> None:
+    """x and out: contiguous tensors of the function's dtype on the same CUDA device, out
+    large enough (2n elements for sincosf).  The C ABI sees only pointers and a length,
+    so a strided view or a wrong dtype would otherwise be evaluated as raw memory."""
+    import torch
+    want = torch.float64 if FUNCS[fid] in F64_FUNCS else torch.float32
+    for name, t in (("x", x), ("out", out)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch.Tensor")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.dtype != want:
+            raise TypeError(f"{FUNCS[fid]} takes {want}, got {t.dtype} for {name}")
+    if x.device != out.device:
+        raise ValueError(f"x is on {x.device}, out on {out.device}")
+    need = (2 if FUNCS[fid] == "sincosf" else 1) * x.numel()
+    if out.numel() < need:
+        raise ValueError(f"out holds {out.numel()} elements, {FUNCS[fid]} needs {need}")
+
+
 def eval_into(func, x, out, form=None, stream=None) -> None:
     """out <- RN(f(x)) for contiguous CUDA tensors (sincosf: out has 2*n elements)."""
     fid = _fid(func)
+    _check_tensors(fid, x, out)
     dtype = L.CRM_F64 if FUNCS[fid] in F64_FUNCS else L.CRM_F32
     n = x.numel()
     L.check(L.lib().crm_eval_form(fid, dtype, _form(form), ctypes.c_void_p(x.data_ptr()),
@@ -92,6 +115,7 @@ def _descs(items):
     descs = (crm_desc_t * len(items))()
     for d, (func, x, out) in zip(descs, items):
         fid = _fid(func)
+        _check_tensors(fid, x, out)
         d.func_id = fid
         d.dtype = L.CRM_F64 if FUNCS[fid] in F64_FUNCS else L.CRM_F32
         d.in_ = x.data_ptr()

@@ -66,6 +66,8 @@ def _lib():
                 lib.crm_set_force_slow.argtypes = [c_int]
                 lib.crm_set_batch_tile.argtypes = [c_int]
                 lib.crm_eval_noalloc.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, vp]
+                lib.crm_noalloc_stats.argtypes = [vp, ctypes.POINTER(crm_stats_t)]
+                lib.crm_noalloc_stats_reset.argtypes = [vp]
                 lib.crm_reserve.argtypes = [c_u64, c_int, vp]
                 pi, pf = ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float)
                 lib.crm_variant_info.argtypes = [c_int, pi, pi, pi, pi, pi, pi]

@@ -105,3 +105,39 @@ extern "C" int crm_eval_noalloc(int func_id, int dtype, int form, const void *in
   if (e != cudaSuccess) return cuda_fail_code(e);
   return CRM_OK;
 }
+
+// Counters of the static scratch of the current device (the header of
+// g_noalloc_scratch, which every crm_eval_noalloc call on the device adds to).  Reading
+// them allocates nothing either: one small copy into the caller's struct.
+extern "C" int crm_noalloc_stats(void *stream, crm_stats_t *out) {
+  ensure_init();
+  if (!out) return CRM_ERR_NULL;
+  NoAllocDevice *d = nullptr;
+  int st = noalloc_setup(&d);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  crm_ws_header h;
+  cudaError_t e = cudaMemcpyAsync(&h, d->scratch, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail_code(e);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail_code(e);
+  out->hard_total = h.hard_total;
+  out->unresolved_total = h.unresolved_total;
+  out->inline_total = h.inline_total;
+  out->last_count = h.count;
+  out->timeouts = h.timeouts;
+  out->fp64_total = h.fp64_total;
+  return CRM_OK;
+}
+
+extern "C" int crm_noalloc_stats_reset(void *stream) {
+  ensure_init();
+  NoAllocDevice *d = nullptr;
+  int st = noalloc_setup(&d);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(d->scratch, 0, sizeof(crm_ws_header), s);
+  if (e != cudaSuccess) return cuda_fail_code(e);
+  e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? CRM_OK : cuda_fail_code(e);
+}

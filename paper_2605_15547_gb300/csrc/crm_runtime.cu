@@ -61,6 +61,13 @@ struct Workspace {
   BatchDesc *bstage = nullptr;
   int bcap = 0;
   cudaEvent_t bcopied = nullptr;  // the last descriptor upload has completed
+  // A captured batch call re-reads bstage and rewrites bdesc at every replay of its
+  // graph: the capture takes both buffers for itself (bcaptured), and the next batch
+  // call outside capture, or crm_reserve, gives the workspace new ones.  The captured
+  // pairs stay allocated until crm_shutdown.
+  bool bcaptured = false;
+  std::vector<std::pair<BatchDesc *, BatchDesc *>> retired;
+  std::vector<crm_queue_entry *> retired_q;  // queues replaced by a larger one
 };
 
 struct DevInfo {
@@ -102,9 +109,9 @@ static int get_ws(cudaStream_t s, uint64_t cap, Workspace **out) {
   }
   if (capturing(s)) return CRM_ERR_CAPTURE;
   if (w.hdr) {  // grow: keep the header (counters), replace the queue
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e);
-    cudaFree(w.q);
+    // a CUDA graph captured earlier may still address the old queue: keep it allocated
+    // until crm_shutdown instead of freeing it
+    w.retired_q.push_back(w.q);
     w.q = nullptr;
   } else {
     e = cudaMalloc((void **)&w.hdr, CRM_WS_HEADER_BYTES);
@@ -281,10 +288,19 @@ static std::atomic<int> g_batch_tile_shift{14};  // the autotuner may change it 
 static std::atomic<int> g_batch_mode{CRM_BATCH_GROUPED};  // crm_set_batch_mode / the autotuner
 
 static int batch_buffers(cudaStream_t s, Workspace *w, int count) {
-  if (w->bcap >= count) return CRM_OK;
+  if (w->bcap >= count && !w->bcaptured) return CRM_OK;
   if (capturing(s)) return CRM_ERR_CAPTURE;
   cudaError_t e;
-  if (w->bdesc) {
+  int want = count < 1024 ? 1024 : count;
+  if (w->bcaptured) {
+    // a graph owns the current pair: keep it for that graph, start a new one
+    w->retired.push_back({w->bdesc, w->bstage});
+    if (want < w->bcap) want = w->bcap;
+    w->bdesc = nullptr;
+    w->bstage = nullptr;
+    w->bcap = 0;
+    w->bcaptured = false;
+  } else if (w->bdesc) {
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e);
     cudaFree(w->bdesc);
@@ -293,7 +309,6 @@ static int batch_buffers(cudaStream_t s, Workspace *w, int count) {
     w->bstage = nullptr;
     w->bcap = 0;
   }
-  int want = count < 1024 ? 1024 : count;
   if (cudaMalloc((void **)&w->bdesc, (size_t)want * sizeof(BatchDesc)) != cudaSuccess) return CRM_ERR_NOMEM;
   if (cudaMallocHost((void **)&w->bstage, (size_t)want * sizeof(BatchDesc)) != cudaSuccess) return CRM_ERR_NOMEM;
   if (!w->bcopied) {
@@ -429,13 +444,22 @@ int crm_set_force_slow(int on) {
   return CRM_OK;
 }
 
+// Queue entries reserved for calls of up to max_elems elements: one entry per 64
+// elements (room for a hard-case rate of 1/64 before any lane is finished inline), at
+// least the default 2^21 entries and at most 2^26 (1 GiB).
+static uint64_t queue_cap_for(uint64_t max_elems) {
+  uint64_t cap = (max_elems + 63) / 64;
+  cap = (cap + CRM_NSUBQ - 1) / CRM_NSUBQ * CRM_NSUBQ;
+  if (cap < kDefaultCap) cap = kDefaultCap;
+  if (cap > (1ull << 26)) cap = 1ull << 26;
+  return cap;
+}
+
 int crm_reserve(uint64_t max_elems, int max_arrays, void *stream) {
   ensure_init();
   if (max_arrays < 0) return CRM_ERR_ARG;
   Workspace *w;
-  uint64_t cap = kDefaultCap;
-  (void)max_elems;
-  int st = get_ws((cudaStream_t)stream, cap, &w);
+  int st = get_ws((cudaStream_t)stream, queue_cap_for(max_elems), &w);
   if (st) return st;
   return max_arrays > 0 ? batch_buffers((cudaStream_t)stream, w, max_arrays) : CRM_OK;
 }
@@ -575,6 +599,8 @@ int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
   if (!cap) {
     e = cudaEventRecord(w->bcopied, s);
     if (e != cudaSuccess) return cuda_fail(e);
+  } else {
+    w->bcaptured = true;  // this graph now owns bstage and bdesc
   }
   int sms = dev_sms();
   BatchArgs a;
@@ -763,6 +789,11 @@ void crm_shutdown(void) {
     if (kv.second.bdesc) cudaFree(kv.second.bdesc);
     if (kv.second.bstage) cudaFreeHost(kv.second.bstage);
     if (kv.second.bcopied) cudaEventDestroy(kv.second.bcopied);
+    for (auto &r : kv.second.retired) {
+      cudaFree(r.first);
+      cudaFreeHost(r.second);
+    }
+    for (auto *q : kv.second.retired_q) cudaFree(q);
     cudaSetDevice(cur);
   }
   g_ws.clear();

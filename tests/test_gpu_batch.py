@@ -115,6 +115,37 @@ def test_batch_graph_capture_and_replay():
             assert np.array_equal(got, ref), (rep, f)
 
 
+def test_batch_graphs_keep_their_arrays():
+    """A captured batch owns its staged descriptors: a later batch call on the stream with
+    other arrays, and a second capture, leave the first graph evaluating its own arrays."""
+    a = make_batch(40, 12, seed=31, misalign=False)
+    b = make_batch(70, 12, seed=32, misalign=False)
+    s = torch.cuda.Stream()
+    crm.reserve(1 << 24, 4096, stream=s)
+    with torch.cuda.stream(s):
+        crm.eval_batch([(f, x, y) for f, x, y, _ in a], stream=s)
+    s.synchronize()
+    ga, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(ga, stream=s):
+        crm.eval_batch([(f, x, y) for f, x, y, _ in a], stream=s)
+    with torch.cuda.stream(s):  # outside capture: stages b's descriptors in new buffers
+        crm.eval_batch([(f, x, y) for f, x, y, _ in b], stream=s)
+    s.synchronize()
+    with torch.cuda.graph(gb, stream=s):
+        crm.eval_batch([(f, x, y) for f, x, y, _ in b], stream=s)
+    for rep in range(2):
+        for items, g in ((a, ga), (b, gb)):
+            for _, _, y, _ in a + b:
+                y.fill_(float("nan"))
+            g.replay()
+            torch.cuda.synchronize()
+            for f, x, y, xh in items:
+                ref = O.eval_bits(f, xh.view(np.uint32)).reshape(-1)
+                assert np.array_equal(y.cpu().numpy().view(np.uint32), ref), (rep, f)
+            other = b if items is a else a
+            assert all(torch.isnan(y).all() for _, _, y, _ in other)  # untouched
+
+
 def test_single_call_graph_capture():
     x = torch.from_numpy(W.domain_bits("logf", 1 << 20, W.rng_for(2, "logf")).view(np.float32)).cuda()
     y = torch.empty_like(x)

@@ -32,7 +32,16 @@ def lib():
     lib = L.lib()
     lib.crm_eval_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+    lib.crm_noalloc_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(L.crm_stats_t)]
+    lib.crm_noalloc_stats_reset.argtypes = [ctypes.c_void_p]
     return lib
+
+
+def _noalloc_stats(lib):
+    from paper_2605_15547_gb300 import _lib as L
+    s = L.crm_stats_t()
+    assert lib.crm_noalloc_stats(_stream(), ctypes.byref(s)) == 0
+    return s
 
 
 def _stream():
@@ -66,6 +75,7 @@ def test_noalloc_matches_allocating_entry_point(lib, func, fid, rows):
         # the second with every lane forced through the queue in the static scratch
         for call, (n, force) in enumerate([(300001, 0), (MAX_ELEMS, 1)]):
             x = _inputs(func, n, 1234 + call)
+            assert lib.crm_noalloc_stats_reset(_stream()) == 0
             lib.crm_set_force_slow(force)
             try:
                 got = _run(lib, "noalloc", fid, form, x, rows)
@@ -74,6 +84,14 @@ def test_noalloc_matches_allocating_entry_point(lib, func, fid, rows):
                 lib.crm_set_force_slow(0)
             assert np.array_equal(got, want), f"{func} form {form} call {call}: " \
                 f"{int(np.count_nonzero(got != want))} mismatches"
+            # the static scratch's counters: no lane undecided, no bounded wait gave up,
+            # no lane finished inline (the queue holds every lane); a forced call queued
+            # every lane that is not a special input
+            st = _noalloc_stats(lib)
+            assert st.unresolved_total == 0 and st.timeouts == 0 and st.inline_total == 0, \
+                (st.unresolved_total, st.timeouts, st.inline_total)
+            if force:
+                assert st.hard_total > n // 2 and st.last_count == st.hard_total, st.hard_total
 
 
 def test_noalloc_rejects_oversized_calls(lib):

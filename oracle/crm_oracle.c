@@ -1546,19 +1546,21 @@ static int special(int kind, const dec_t *x, const fmt_t *f, uint64_t xbits, uin
     case K_EXP: case K_EXP2: case K_EXP10: {
       if (x->cls == CL_ZERO) { *out = ONE; return 1; }
       if (x->cls == CL_INF) { *out = x->neg ? 0 : INF; return 1; }
-      /* saturation far outside the finite-result range; the boundary band is left to
-         the Ziv loop */
-      double hi = f->w == 32 ? 200.0 : 2000.0;
-      if (kind == K_EXP2) hi = f->w == 32 ? 160.0 : 1100.0;
-      if (kind == K_EXP10) hi = f->w == 32 ? 50.0 : 330.0;
+      /* saturation outside the finite-result range of the format, with 8 binades to
+         spare: |x| log2(b) >= max(emax + 1, p - emin) + 8 gives b^x >= 2^(emax + 9)
+         (overflow) or b^x <= 2^(emin - p - 8) (below half the smallest subnormal); the
+         boundary band is left to the Ziv loop */
+      double lim = (double)(f->emax + 1 > f->p - f->emin ? f->emax + 1 : f->p - f->emin) + 8.0;
+      double hi = kind == K_EXP2 ? lim : (kind == K_EXP ? lim * LN2_APPROX : lim * 0.30102999566398120);
       if (ax >= hi) { *out = x->neg ? rnd_tiny(0, f, mode) : rnd_huge(0, f, mode); return 1; }
       return 0;
     }
     case K_EXPM1:
       if (x->cls == CL_ZERO) { *out = xbits; return 1; }
       if (x->cls == CL_INF) { *out = x->neg ? (SB | ONE) : INF; return 1; }
-      if (!x->neg && ax >= 200.0) { *out = rnd_huge(0, f, mode); return 1; }
-      if (x->neg && ax >= 40.0) { *out = rnd_below_one(1, f, mode); return 1; } /* -1 + e^x, e^x < 2^-57 */
+      /* e^x >= 2^(emax + 3): overflow; x <= -(p + 4) ln 2: -1 + e^x with 0 < e^x < 2^-(p+4) */
+      if (!x->neg && ax >= (double)(f->emax + 3) * LN2_APPROX) { *out = rnd_huge(0, f, mode); return 1; }
+      if (x->neg && ax >= (double)(f->p + 4) * LN2_APPROX) { *out = rnd_below_one(1, f, mode); return 1; }
       return 0;
     case K_LOG: case K_LOG2: case K_LOG10:
       if (x->cls == CL_ZERO) { *out = SB | INF; return 1; }
@@ -1594,17 +1596,19 @@ static int special(int kind, const dec_t *x, const fmt_t *f, uint64_t xbits, uin
     case K_SINH:
       if (x->cls == CL_ZERO) { *out = xbits; return 1; }
       if (x->cls == CL_INF) { *out = sgn | INF; return 1; }
-      if (ax >= 200.0) { *out = rnd_huge(x->neg, f, mode); return 1; }
+      /* |x| >= (emax + 3) ln 2: e^|x| / 2 >= 2^(emax + 2) overflows */
+      if (ax >= (double)(f->emax + 3) * LN2_APPROX) { *out = rnd_huge(x->neg, f, mode); return 1; }
       return 0;
     case K_COSH:
       if (x->cls == CL_ZERO) { *out = ONE; return 1; }
       if (x->cls == CL_INF) { *out = INF; return 1; }
-      if (ax >= 200.0) { *out = rnd_huge(0, f, mode); return 1; }
+      if (ax >= (double)(f->emax + 3) * LN2_APPROX) { *out = rnd_huge(0, f, mode); return 1; }
       return 0;
     case K_TANH:
       if (x->cls == CL_ZERO) { *out = xbits; return 1; }
       if (x->cls == CL_INF) { *out = sgn | ONE; return 1; }
-      if (ax >= 40.0) { *out = rnd_below_one(x->neg, f, mode); return 1; } /* 1 - 2e^-80 */
+      /* |x| >= (p + 4) ln 2 / 2: 0 < 1 - |tanh x| < 2 e^(-2|x|) <= 2^-(p+3) */
+      if (ax >= (double)(f->p + 4) * LN2_APPROX / 2.0) { *out = rnd_below_one(x->neg, f, mode); return 1; }
       return 0;
     case K_RSQRT:
       if (x->cls == CL_ZERO) { *out = sgn | INF; return 1; }
@@ -1787,9 +1791,66 @@ int crm_oracle_f64_rm(int func, uint64_t x, int mode, uint64_t *out) {
 
 int crm_oracle_last_level(void) { return g_last_level; }
 
+/* How close f(x) lies to a rounding boundary of binary64 round-to-nearest (a midpoint
+   between two consecutive binary64 numbers; in the top binade the overflow threshold
+   2^1024 - 2^970 is one of them): *h = -log2(d), d the distance in units of the last place
+   of the result's binade (0 < d <= 1/2).  A result within 2^-h ulp of a midpoint needs a
+   working precision of about 53 + h bits before any evaluation can round it (the hard-to-
+   round cases of Sec. II.B).  f(x) is enclosed at 9 limbs (512 fraction bits) and d is
+   read from the 128 bits below the rounding position of the interval's lower end, so h is
+   exact to far below 2^-60 relative and capped at 128.  Special inputs, results beyond the
+   largest binade, and exact results (log(1), exp2 of an integer: d = 1/2) give h <= 1. */
+int crm_oracle_f64_hardness(int func, uint64_t xb, double *h) {
+  int is64;
+  int kind = kind_of(func, &is64);
+  if (kind < 0 || !is64) return ORC_ERR_FUNC;
+  dec_t x = dec64(xb);
+  uint64_t sp;
+  *h = -1.0;
+  if (special(kind, &x, &FMT64, xb, &sp, ORC_RN)) return ORC_OK;
+  res_t R;
+  int n = 9;
+  for (;;) {
+    R.E = 0;
+    g_fail = 0;
+    evaluate(kind, &x, n, &R);
+    if (!g_fail) break;
+    if (n == 33) return ORC_ERR_CAP;
+    n = 2 * n - 1;
+  }
+  limb m[MAXL], t[MAXL];
+  fx_abs(m, R.v.lo, n);
+  int b = mag_bitlen(m, n);
+  if (b == 0) return ORC_OK;
+  const fmt_t *f = &FMT64;
+  int64_t F = FB(n);
+  int64_t ex = (int64_t)b - 1 + R.E - F;
+  if (ex > f->emax) return ORC_OK;
+  int64_t qe = (ex < f->emin ? f->emin : ex) - (f->p - 1);
+  int64_t k = qe - (R.E - F); /* discarded bits below the last place */
+  if (k < 2) return ORC_OK;
+  /* the 128 bits just below the last place: floor(m / 2^(k - 128)) mod 2^128 */
+  if (k >= 128) {
+    mag_shr(t, m, n, k - 128);
+  } else {
+    mag_shl(t, m, n, 128 - k);
+  }
+  u128 w = ((u128)t[1] << 64) | t[0];
+  const u128 half = (u128)1 << 127;
+  u128 d = w >= half ? w - half : half - w;
+  if (d == 0) {
+    *h = 128.0;
+    return ORC_OK;
+  }
+  /* -log2(d / 2^128) */
+  double dd = (double)(uint64_t)(d >> 64) * 18446744073709551616.0 + (double)(uint64_t)d;
+  *h = 128.0 - log2(dd);
+  return ORC_OK;
+}
+
 /* ---- threaded array drivers ---- */
 typedef struct {
-  int func, is64, mode;
+  int func, is64, mode, hardness;
   const void *in;
   void *out;
   uint64_t n;
@@ -1806,7 +1867,9 @@ static void *worker(void *arg) {
     uint64_t end = start + chunk < J->n ? start + chunk : J->n;
     for (uint64_t i = start; i < end; i++) {
       int st;
-      if (J->is64) {
+      if (J->hardness) {
+        st = crm_oracle_f64_hardness(J->func, ((const uint64_t *)J->in)[i], ((double *)J->out) + i);
+      } else if (J->is64) {
         st = crm_oracle_f64_rm(J->func, ((const uint64_t *)J->in)[i], J->mode, ((uint64_t *)J->out) + i);
       } else if (J->func == ORC_SINCOSF) {
         uint32_t sc[2];
@@ -1850,7 +1913,7 @@ int crm_oracle_f32_array_rm(int func, const uint32_t *in, uint32_t *out, uint64_
   int is64;
   int kind = kind_of(func, &is64);
   if (kind == -2 || is64 || mode < ORC_RN || mode > ORC_RZ) return ORC_ERR_FUNC;
-  job_t J = {func, 0, mode, in, out, n, 0, 0};
+  job_t J = {func, 0, mode, 0, in, out, n, 0, 0};
   return run_job(&J, nthreads);
 }
 
@@ -1858,7 +1921,15 @@ int crm_oracle_f64_array_rm(int func, const uint64_t *in, uint64_t *out, uint64_
   int is64;
   int kind = kind_of(func, &is64);
   if (kind < 0 || !is64 || mode < ORC_RN || mode > ORC_RZ) return ORC_ERR_FUNC;
-  job_t J = {func, 1, mode, in, out, n, 0, 0};
+  job_t J = {func, 1, mode, 0, in, out, n, 0, 0};
+  return run_job(&J, nthreads);
+}
+
+int crm_oracle_f64_hardness_array(int func, const uint64_t *in, double *out, uint64_t n, int nthreads) {
+  int is64;
+  int kind = kind_of(func, &is64);
+  if (kind < 0 || !is64) return ORC_ERR_FUNC;
+  job_t J = {func, 1, ORC_RN, 1, in, out, n, 0, 0};
   return run_job(&J, nthreads);
 }
 

@@ -60,6 +60,13 @@ int crm_oracle_f64_array(int func, const uint64_t *in, uint64_t *out, uint64_t n
 int crm_oracle_f32_array_rm(int func, const uint32_t *in, uint32_t *out, uint64_t n, int nthreads, int mode);
 int crm_oracle_f64_array_rm(int func, const uint64_t *in, uint64_t *out, uint64_t n, int nthreads, int mode);
 
+/* Distance of f(x) from the nearest binary64 round-to-nearest boundary (a midpoint between
+   consecutive binary64 numbers), for the binary64 functions: *h = -log2(distance in ulps),
+   so a result within 2^-h ulp of a midpoint; capped at 128; h <= 1 for special inputs and
+   exact results.  Used to select hard-to-round test inputs.  The array form is threaded. */
+int crm_oracle_f64_hardness(int func, uint64_t x, double *h);
+int crm_oracle_f64_hardness_array(int func, const uint64_t *in, double *out, uint64_t n, int nthreads);
+
 /* Diagnostics for the oracle's own tests: the Ziv level (0 = first precision) at which
    the last call on this thread finished, and the constants as scaled integers. */
 int crm_oracle_last_level(void);

@@ -66,6 +66,8 @@ def _load():
                                                  ctypes.c_uint64, ctypes.c_int]
             lib.crm_oracle_f64_array.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_uint64, ctypes.c_int]
+            lib.crm_oracle_f64_hardness_array.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                          ctypes.c_uint64, ctypes.c_int]
             lib.crm_oracle_constant.argtypes = [ctypes.c_int, ctypes.c_int, u64p, u64p]
             lib.crm_oracle_constant_alt.argtypes = [ctypes.c_int, ctypes.c_int, u64p, u64p]
             lib.crm_oracle_test_divmod.argtypes = [u32p, ctypes.c_int, u32p, ctypes.c_int, u32p]
@@ -124,6 +126,21 @@ def eval_bits16(func, xbits: np.ndarray, fmt: str = "f16", mode: str = "rn") -> 
         if st:
             raise OracleError(f"oracle status {st} for {FUNCS[fid]} ({fmt})")
     return out.reshape(2, n) if rows == 2 else out
+
+
+def f64_hardness(func, xbits: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    """For binary64 exp2 / log: -log2 of the distance (in ulps of the result) from f(x) to
+    the nearest round-to-nearest boundary, per input (float64; capped at 128, <= 1 for
+    special inputs and exact results)."""
+    lib = _load()
+    fid = _fid(func)
+    x = np.ascontiguousarray(xbits, dtype=np.uint64).ravel()
+    out = np.zeros(x.size, dtype=np.float64)
+    if x.size:
+        st = lib.crm_oracle_f64_hardness_array(fid, x.ctypes.data, out.ctypes.data, x.size, nthreads)
+        if st:
+            raise OracleError(f"oracle status {st} for {FUNCS[fid]} hardness")
+    return out
 
 
 def eval_f32(func, x: np.ndarray, nthreads: int = 0) -> np.ndarray:

@@ -410,3 +410,54 @@ def test_results_do_not_depend_on_threads():
     a = O.eval_bits("sinf", xb, nthreads=1)
     b = O.eval_bits("sinf", xb, nthreads=7)
     assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- distance to a midpoint
+def mp_hardness(name, x):
+    """-log2 of the distance from f(x) to the nearest binary64 midpoint, in ulps of the
+    result's binade, from mpmath at 600 bits (independent of the oracle's integer code)."""
+    with mpmath.workprec(600):
+        v = abs(mp_func(name)(mpmath.mpf(float(x))))
+        e = int(mpmath.floor(mpmath.log(v, 2)))
+        # guard the binade against a log rounded across a power of two
+        while mpmath.mpf(2) ** e > v:
+            e -= 1
+        while mpmath.mpf(2) ** (e + 1) <= v:
+            e += 1
+        ulp = mpmath.mpf(2) ** (max(e, -1022) - 52)
+        t = v / ulp
+        d = abs(t - mpmath.floor(t) - mpmath.mpf(1) / 2)
+        return float(-mpmath.log(d, 2)) if d > 0 else 1000.0
+
+
+def test_f64_hardness_matches_mpmath():
+    rng = np.random.default_rng(99)
+    ln2 = math.log(2.0)
+    cases = {
+        "exp2": list(rng.uniform(-30, 30, 40)) + list(rng.uniform(-1074, -1020, 10)) +
+                # 2^x = 1 + x ln2 + ...: near the midpoints 1 + (j + 1/2) 2^-52 (x > 0) and
+                # 1 - (j + 1/2) 2^-53 (x < 0), hardness up to about 55 bits
+                [(j + 0.5) * 2.0 ** -52 / ln2 for j in range(6)] +
+                [-(j + 0.5) * 2.0 ** -53 / ln2 for j in range(6)] +
+                [17.0 + (j + 0.5) * 2.0 ** -52 / ln2 for j in range(3)],
+        "log": list(rng.uniform(0.1, 10, 40)) + list(np.exp2(rng.uniform(-1070, 1020, 10))) +
+               [1.0 + 16 * o * 2.0 ** -52 for o in range(17, 31, 2)] +
+               [1.0 + 2.0 ** -40, 1.0 - 2.0 ** -45, 5e-324, 1.7976931348623157e308],
+    }
+    for name, xs in cases.items():
+        xs = np.array(xs, dtype=np.float64)
+        got = O.f64_hardness(name, xs.view(np.uint64))
+        for x, h in zip(xs, got):
+            ref = min(mp_hardness(name, x), 128.0)
+            assert abs(h - ref) <= 1e-9 * max(1.0, ref), (name, float(x).hex(), h, ref)
+    # the constructed exp2 inputs are hard: within 2^-40 ulp of a midpoint
+    hard = O.f64_hardness("exp2", np.array([(j + 0.5) * 2.0 ** -52 / ln2 for j in range(6)]).view(np.uint64))
+    assert (hard > 40).all(), hard
+
+
+def test_f64_hardness_of_exact_and_special_results():
+    ex = np.array([3.0, -1074.0, 0.0, np.inf], dtype=np.float64)  # 2^3, 2^-1074 exact; specials
+    h = O.f64_hardness("exp2", ex.view(np.uint64))
+    assert np.allclose(h[:2], 1.0) and (h[2:] == -1.0).all(), h
+    h = O.f64_hardness("log", np.array([1.0, -1.0, 0.0], dtype=np.float64).view(np.uint64))
+    assert (h == -1.0).all(), h

@@ -58,7 +58,12 @@ typedef enum {
   CRM_NUM_FUNCS = 21
 } crm_func_t;
 
-typedef enum { CRM_F32 = 0, CRM_F64 = 1 } crm_dtype_t;
+/* Element formats: binary32, binary64, and the 16-bit formats of crm_eval_rm (IEEE
+   binary16; bfloat16: binary32's exponent range with 8 significant bits). */
+typedef enum { CRM_F32 = 0, CRM_F64 = 1, CRM_F16 = 2, CRM_BF16 = 3 } crm_dtype_t;
+/* Rounding directions (IEEE 754 Sec. 4.3): to nearest with ties to even, toward -inf,
+   toward +inf, toward zero. */
+typedef enum { CRM_RN = 0, CRM_RD = 1, CRM_RU = 2, CRM_RZ = 3 } crm_rmode_t;
 typedef enum { CRM_FORM_AUTO = 0, CRM_FORM_PLAIN_FP64 = 1, CRM_FORM_DF32 = 2 } crm_form_t;
 
 typedef enum {
@@ -109,6 +114,28 @@ int crm_eval(int func_id, int dtype, const void *in, void *out, uint64_t n, void
 int crm_eval_form(int func_id, int dtype, int form, const void *in, void *out, uint64_t n,
                   void *stream);
 
+/* Correct rounding in any direction and in the 16-bit formats: out[i] = rmode(f(in[i])),
+   f evaluated exactly and rounded once in direction rmode (crm_rmode_t) to the element
+   format dtype.  The paper's CPU design ends its evaluation by rounding toward zero with a
+   sticky bit and converting in the caller's rounding mode (Sec. II.A); its GPU runs, and
+   crm_eval, use round-to-nearest only.  Here every fast-tier result carries the sign of
+   f(x) minus a nearby binary32 (binary64) number, which fixes the rounding in every
+   direction and format; lanes where that sign is undecided (f(x) on or within the error
+   bound of such a number) go to the slow path, which settles exact results explicitly.
+     dtype CRM_F32, CRM_F64: the function's own format (binary64 for exp2 and log); rmode
+       CRM_RN is crm_eval_form with CRM_FORM_AUTO;
+     dtype CRM_F16, CRM_BF16: the 19 binary32 functions on 16-bit inputs and outputs (the
+       formula of the binary32 function; in and out hold uint16 bit patterns, sincosf's out
+       2n of them), in all four directions.
+   Special values follow the binary32 conventions in each direction (overflow gives the
+   largest finite number when rounding toward zero or away from the infinity, underflow
+   the smallest subnormal when rounding away from zero).  in/out: device pointers, element
+   aligned; in == out allowed, other overlap CRM_ERR_OVERLAP.  Asynchronous on `stream`;
+   uses the stream's workspace as crm_eval does.  Errors: CRM_ERR_FUNC, CRM_ERR_DTYPE (a
+   16-bit format with exp2 or log, or a mismatched dtype), CRM_ERR_ARG (rmode, alignment),
+   CRM_ERR_NULL, CRM_ERR_OVERLAP, CRM_ERR_NOMEM, CRM_ERR_CAPTURE, CRM_ERR_CUDA. */
+int crm_eval_rm(int func_id, int dtype, int rmode, const void *in, void *out, uint64_t n, void *stream);
+
 /* Host-buffer variant: in/out are host pointers.  When both are page-locked memory that
    the device addresses directly (cudaHostAlloc / cudaHostRegister on a system with
    unified addressing, as on GB300), the kernels read and write them in place over the
@@ -151,11 +178,14 @@ int crm_set_batch_mode(int mode);
    4 or 8 binary32 elements, 2 or 4 binary64 ones per access; a 32-byte shape falls back to
    the default shape when in and out are not 32-byte congruent), threads per block,
    register prefetch of the next iteration, a minimum of resident blocks per SM (a
-   register cap), or the shared-memory pipelined kernel (bulk asynchronous copies).  Every variant computes the same bits.  Output pointers may be
-   NULL. */
-#define CRM_NUM_VARIANTS 10
+   register cap), or the shared-memory pipelined kernel (bulk asynchronous copies).
+   reg_table: the evaluator keeps a table of at most 16 entries in registers and reads it
+   with warp shuffles instead of a larger table in shared memory (the paper's small tables
+   read by permutes, Sec. II.A; exp family only: other functions do not provide it).
+   Every variant computes the same bits.  Output pointers may be NULL. */
+#define CRM_NUM_VARIANTS 11
 int crm_variant_info(int variant, int *unroll, int *block, int *prefetch, int *pipelined, int *min_blocks,
-                     int *vec_bytes);
+                     int *vec_bytes, int *reg_table);
 /* Choose the variant of (func_id, form) for all later calls.  CRM_ERR_ARG if the form does
    not provide it (the plain FP64 form provides only the default shape). */
 int crm_set_variant(int func_id, int form, int variant);

@@ -14,7 +14,7 @@ import ctypes
 from . import _lib as L
 from ._lib import F64_FUNCS, FORMS, FUNC_ID, FUNCS, CrmError, crm_desc_t, crm_stats_t
 
-__all__ = ["eval", "eval_into", "eval_host", "eval_batch", "stats", "stats_reset",
+__all__ = ["eval", "eval_into", "eval_rm", "eval_host", "eval_batch", "stats", "stats_reset",
            "set_form", "set_force_slow", "set_batch_tile", "reserve", "FUNCS", "FORMS", "CrmError", "version",
            "variant_info", "set_variant", "get_variant", "autotune", "autotune_batch", "set_batch_mode"]
 
@@ -95,6 +95,29 @@ def eval(func, x, out=None, form=None, stream=None):
     return out
 
 
+def eval_rm(func, x, mode="rn", out=None, stream=None):
+    """f(x) correctly rounded in direction mode ("rn", "rd", "ru", "rz") to x's format:
+    float32 or float64 (the function's own), or float16 / bfloat16 for the binary32
+    functions (their formula on 16-bit inputs and results).  Returns out (a new tensor
+    unless given; sincosf: shape (2, *x.shape))."""
+    import torch
+    fid = _fid(func)
+    kinds = {torch.float32: L.CRM_F32, torch.float64: L.CRM_F64, torch.float16: L.CRM_F16,
+             torch.bfloat16: L.CRM_BF16}
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or not x.is_contiguous() or x.dtype not in kinds:
+        raise ValueError("x must be a contiguous CUDA tensor of float32, float64, float16 or bfloat16")
+    rows = 2 if FUNCS[fid] == "sincosf" else 1
+    if out is None:
+        out = torch.empty(((2,) if rows == 2 else ()) + tuple(x.shape), dtype=x.dtype, device=x.device)
+    if not out.is_cuda or not out.is_contiguous() or out.dtype != x.dtype or out.numel() < rows * x.numel() \
+            or out.device != x.device:
+        raise ValueError("out must be a contiguous CUDA tensor of x's dtype and device, large enough")
+    L.check(L.lib().crm_eval_rm(fid, kinds[x.dtype], L.RMODES[mode], ctypes.c_void_p(x.data_ptr()),
+                                ctypes.c_void_p(out.data_ptr()), x.numel(), _stream_ptr(stream)),
+            f"{FUNCS[fid]} {mode}")
+    return out
+
+
 def eval_host(func, x_np, out_np=None, form=None, stream=None):
     """Host (numpy) buffers in and out; the library copies, computes and copies back."""
     import numpy as np
@@ -162,10 +185,11 @@ def reserve(max_elems: int, max_arrays: int = 0, stream=None) -> None:
 
 def variant_info(v: int) -> dict:
     """Launch shape of main-kernel variant v (0 <= v < NUM_VARIANTS)."""
-    a = [ctypes.c_int() for _ in range(6)]
+    a = [ctypes.c_int() for _ in range(7)]
     L.check(L.lib().crm_variant_info(int(v), *[ctypes.byref(t) for t in a]))
     return {"unroll": a[0].value, "block": a[1].value, "prefetch": bool(a[2].value),
-            "pipelined": bool(a[3].value), "min_blocks": a[4].value, "vec_bytes": a[5].value}
+            "pipelined": bool(a[3].value), "min_blocks": a[4].value, "vec_bytes": a[5].value,
+            "reg_table": bool(a[6].value)}
 
 
 def set_variant(func, variant: int, form=None) -> None:

@@ -21,8 +21,9 @@ FUNCS = [
 FUNC_ID = {n: i for i, n in enumerate(FUNCS)}
 F64_FUNCS = {"exp2", "log"}
 FORMS = {"auto": 0, "plain": 1, "df": 2}
-CRM_F32, CRM_F64 = 0, 1
-NUM_VARIANTS = 10
+CRM_F32, CRM_F64, CRM_F16, CRM_BF16 = 0, 1, 2, 3
+RMODES = {"rn": 0, "rd": 1, "ru": 2, "rz": 3}
+NUM_VARIANTS = 11
 BATCH_TILE_MIN, BATCH_TILE_MAX = 10, 16
 
 
@@ -61,6 +62,7 @@ def _lib():
                 lib.crm_eval.argtypes = [c_int, c_int, vp, vp, c_u64, vp]
                 lib.crm_eval_form.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, vp]
                 lib.crm_eval_host.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, vp]
+                lib.crm_eval_rm.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, vp]
                 lib.crm_eval_batch.argtypes = [ctypes.POINTER(crm_desc_t), c_int, c_int, vp]
                 lib.crm_set_form.argtypes = [c_int]
                 lib.crm_set_force_slow.argtypes = [c_int]
@@ -70,7 +72,7 @@ def _lib():
                 lib.crm_noalloc_stats_reset.argtypes = [vp]
                 lib.crm_reserve.argtypes = [c_u64, c_int, vp]
                 pi, pf = ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float)
-                lib.crm_variant_info.argtypes = [c_int, pi, pi, pi, pi, pi, pi]
+                lib.crm_variant_info.argtypes = [c_int, pi, pi, pi, pi, pi, pi, pi]
                 lib.crm_set_variant.argtypes = [c_int, c_int, c_int]
                 lib.crm_get_variant.argtypes = [c_int, c_int, pi]
                 lib.crm_autotune.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, c_int, vp, pi, pf]

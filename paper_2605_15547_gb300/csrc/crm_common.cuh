@@ -183,18 +183,47 @@ CRM_DEV bool hard_d_to_f(double y, uint32_t D) {
 // the lane is hard.  An easy lane's result is RN(s + r), the value a normalised pair
 // would give; a NaN in s makes the lane hard.  Six operations; renormalising the pair
 // and testing the distance to the nearest midpoint would take eight.
-CRM_DEV float round_df(float s, float r, bool &hard) {
+//
+// With sg (the directed-rounding and 16-bit kernels) the test changes: the lane returns
+// c = RN(s + r) and *sg = the sign of v - c, which is all a rounding direction needs
+// (RD(v) = c or the float below it, and so on, see the finishers below).  s - c is exact
+// (c lies within 2^-13 of s), d = (s - c) + r has one rounding, and RN is monotone, so
+// |d| > e implies |y - c| > e and sign(v - c) = sign(d); otherwise v is too close to c
+// (or equal to it: an exact result) and the lane is hard.
+CRM_DEV float round_df(float s, float r, bool &hard, int *sg = nullptr) {
   const float e = fabsf(s) * 0x1p-36f;
+  if (sg) {
+    const float c = s + r;
+    const float d = (s - c) + r;
+    hard = !(fabsf(d) > e);  // NaN: hard
+    *sg = d > 0.0f ? 1 : -1;
+    return c;
+  }
   const float hi = s + (r + e), lo = s + (r - e);
   hard = hi != lo;
   return hi;
+}
+
+// The sign of a float as -1, 0 or 1 (the sign of v - c for shortcuts whose error has the
+// sign of x, 0 for x = 0).
+CRM_DEV int sgnf(float x) { return x > 0.0f ? 1 : (x < 0.0f ? -1 : 0); }
+// Store v in *sg when sg is set (RN kernels pass none: the code folds away).
+CRM_DEV void put_sg(int *sg, int v) {
+  if (sg) *sg = v;
 }
 
 // Slow tier: y = s + t (double-double, |t| <= ulp(s)/2) approximates v with
 // |v - y| <= e.  Returns RN_f32(v) and sets hard when a binary32 midpoint (or the
 // overflow threshold) lies within reach.  Uses directed conversions to find the two
 // binary32 neighbours of s; their midpoint is exact in binary64.
-CRM_DEV float round_dd_to_f(double s, double t, double e, bool &hard) {
+CRM_DEV float round_dd_to_f(double s, double t, double e, bool &hard, int *sg = nullptr) {
+  if (sg) {  // c = RN32(s) and the sign of v - c, decided unless |(s - c) + t| <= e
+    const float c = __double2float_rn(s);
+    const double d = isinf(c) ? (c > 0.0f ? -1.0 : 1.0) : (s - (double)c) + t;  // s - c exact
+    hard = !(fabs(d) > e);
+    *sg = d > 0.0 ? 1 : -1;
+    return c;
+  }
   float dn = __double2float_rd(s), up = __double2float_ru(s);
   hard = false;
   if (dn == up) return dn;  // s is a binary32 value; v lies within e + |t| << ulp of it
@@ -211,6 +240,168 @@ CRM_DEV float round_dd_to_f(double s, double t, double e, bool &hard) {
     return __double2float_rn(s);
   }
   return dist > 0 ? up : dn;
+}
+
+// ------------------------------------------------------------------ directed rounding and 16-bit formats
+// An evaluator run with sg returns a binary32 c within a fraction of an ulp of v = f(x) and
+// sg = sign(v - c) (0 when v = c exactly).  That pair fixes RD32(v) and RU32(v), and from
+// them every rounding of v to binary32, IEEE binary16 or bfloat16 in every direction
+// (IEEE 754 Sec. 4.3; the paper's final step rounds toward zero with a sticky bit and then
+// converts in the caller's mode, Sec. II.A):
+//   RD32(v) = c if sg >= 0, else the float below c;  RU32(v) = c if sg <= 0, else above;
+//   RZ = RD for v > 0, RU for v < 0;
+//   for a 16-bit format F: RD_F(v) = RD_F(RD32(v)) and RU_F(v) = RU_F(RU32(v)) (every
+//   number of F is a binary32 number, so none lies strictly between RD32(v) and RU32(v));
+//   RN_F(v) = RN_F(a) when a = RD32(v) and b = RU32(v) round alike; otherwise a midpoint of
+//   F (a binary32 number with at most 12 significant bits) lies in [a, b], so it is a or
+//   b: v lies above it (take RU_F(a)) when it is a, below it (RD_F(b)) when it is b;
+//   a = b (v exact) gives RN_F(a), ties to even.
+enum { CRM_RM_RN = 0, CRM_RM_RD = 1, CRM_RM_RU = 2, CRM_RM_RZ = 3 };
+
+// Neighbours of a binary32 number by its bit pattern (c not NaN; next_up(+inf) and
+// next_down(-inf) are not used)
+CRM_DEV float next_up_f(float c) {
+  const uint32_t b = fbits(c);
+  if ((b & 0x7FFFFFFFu) == 0) return bitsf(1u);  // +-0 -> smallest subnormal
+  return bitsf((b >> 31) ? b - 1u : b + 1u);
+}
+CRM_DEV float next_down_f(float c) {
+  const uint32_t b = fbits(c);
+  if ((b & 0x7FFFFFFFu) == 0) return bitsf(0x80000001u);
+  return bitsf((b >> 31) ? b + 1u : b - 1u);
+}
+CRM_DEV float rd32(float c, int sg) { return sg < 0 ? next_down_f(c) : c; }
+CRM_DEV float ru32(float c, int sg) { return sg > 0 ? next_up_f(c) : c; }
+// The sign of v: c's when c != 0, else sg's (v = 0 exactly when both are 0)
+CRM_DEV bool v_negative(float c, int sg) { return c != 0.0f ? c < 0.0f : (sg != 0 ? sg < 0 : fbits(c) >> 31); }
+
+// binary32 result in mode rm (NaN passes through)
+CRM_DEV float finish_f32(float c, int sg, int rm) {
+  if (c != c) return c;
+  if (rm == CRM_RM_RD || (rm == CRM_RM_RZ && !v_negative(c, sg))) return rd32(c, sg);
+  if (rm == CRM_RM_RU || rm == CRM_RM_RZ) return ru32(c, sg);
+  return c;
+}
+
+// Rounding of a binary32 number a to a 16-bit format, in one direction (dir: -1 down, +1
+// up, 0 toward zero, 2 to nearest with ties to even), as a 16-bit pattern.  bfloat16 is the
+// top half of the binary32 pattern (same exponent range); binary16 rebiases the exponent
+// (emin -14, quantum 2^-24 below 2^-14, overflow beyond 65504).
+CRM_DEV uint16_t round_to_bf16(float a, int dir) {
+  const uint32_t b = fbits(a);
+  if (a != a) return (uint16_t)((b >> 16) | 0x0040u);  // quiet NaN, sign and payload top
+  const uint32_t mag = b & 0x7FFFFFFFu, sgn = b >> 31;
+  const uint32_t q = mag >> 16, rem = mag & 0xFFFFu;
+  uint32_t r = q;
+  const bool away = dir == 2 ? (rem > 0x8000u || (rem == 0x8000u && (q & 1u))) : (rem != 0 && dir == (sgn ? -1 : 1));
+  if (away) r = q + 1u;  // carries into the exponent, up to the infinity pattern
+  return (uint16_t)((sgn << 15) | r);
+}
+CRM_DEV uint16_t round_to_f16(float a, int dir) {
+  const uint32_t b = fbits(a);
+  const uint32_t sgn = (b >> 31) << 15;
+  if (a != a) return (uint16_t)(sgn | 0x7E00u | ((b >> 13) & 0x03FFu));
+  const uint32_t mag = b & 0x7FFFFFFFu;
+  const int E = (int)(mag >> 23) - 127;  // a = 1.m 2^E for normal a
+  if (mag == 0x7F800000u) return (uint16_t)(sgn | 0x7C00u);
+  // the value as an integer multiple of the quantum: q = |a| / 2^(max(E, -14) - 10),
+  // with the discarded bits rem (out of unit)
+  uint32_t q, rem, unit;
+  if (E > 15) {  // beyond binary16's range: the largest finite or infinity
+    const bool up = dir == 2 || dir == (sgn ? -1 : 1);
+    return (uint16_t)(sgn | (up ? 0x7C00u : 0x7BFFu));
+  }
+  const uint32_t M = mag >= 0x00800000u ? ((mag & 0x007FFFFFu) | 0x00800000u) : (mag & 0x007FFFFFu);
+  const int e2 = mag >= 0x00800000u ? E : -126;  // |a| = M 2^(e2 - 23)
+  const int drop = (e2 > -14 ? e2 : -14) - 10 - (e2 - 23);  // bits of M below the quantum: 13..
+  if (drop >= 32) {
+    q = 0;
+    rem = M;  // nonzero for a != 0
+    unit = 0;  // rem compared with half below
+  } else {
+    q = M >> drop;
+    rem = M & ((1u << drop) - 1u);
+    unit = 1u << drop;
+  }
+  bool away;
+  if (dir == 2) {
+    if (drop >= 32) away = false;  // |a| < 2^-25 * 2: below half the smallest subnormal
+    else away = rem > (unit >> 1) || (rem == (unit >> 1) && (q & 1u));
+  } else {
+    away = rem != 0 && dir == (sgn ? -1 : 1);
+  }
+  q += away ? 1u : 0u;
+  // q counts quanta of 2^((e2 > -14 ? e2 : -14) - 10): for normal results the pattern is
+  // (biased exponent << 10) + (q - 2^10); a carry to 2^11 moves to the next binade
+  uint32_t bits;
+  if (e2 > -14 || q >= 0x400u) {
+    const int ee = (e2 > -14 ? e2 : -14);
+    bits = ((uint32_t)(ee + 15) << 10) + (q - 0x400u);  // q in [2^10, 2^11]: carry ok
+    if (bits >= 0x7C00u) {  // overflow: infinity, or the largest finite toward zero
+      const bool up = dir == 2 || dir == (sgn ? -1 : 1);
+      bits = up ? 0x7C00u : 0x7BFFu;
+    }
+  } else {
+    bits = q;  // subnormal (or zero)
+  }
+  return (uint16_t)(sgn | bits);
+}
+// Is the binary32 number a exactly halfway between two consecutive numbers of the 16-bit
+// format (the overflow threshold included)?
+template <bool BF> CRM_DEV bool is_mid16(float a) {
+  const uint32_t mag = fbits(a) & 0x7FFFFFFFu;
+  if (mag >= 0x7F800000u) return false;
+  if (BF) return (mag & 0xFFFFu) == 0x8000u;
+  const int E = (int)(mag >> 23) - 127;
+  if (mag < 0x00800000u || E > 15) return false;  // far below 2^-25 or beyond the range
+  const int drop = (E > -14 ? E : -14) - 10 - (E - 23);
+  if (drop >= 25) return false;
+  const uint32_t M = (mag & 0x007FFFFFu) | 0x00800000u;
+  return (M & ((1u << drop) - 1u)) == (1u << (drop - 1));
+}
+template <bool BF> CRM_DEV uint16_t round_to16(float a, int dir) {
+  return BF ? round_to_bf16(a, dir) : round_to_f16(a, dir);
+}
+// 16-bit result in mode rm from (c, sg)
+template <bool BF> CRM_DEV uint16_t finish_16(float c, int sg, int rm) {
+  if (c != c) return round_to16<BF>(c, 2);
+  const float a = rd32(c, sg), b = ru32(c, sg);
+  const bool neg = v_negative(c, sg);
+  if (rm == CRM_RM_RD || (rm == CRM_RM_RZ && !neg)) return round_to16<BF>(a, -1);
+  if (rm == CRM_RM_RU || rm == CRM_RM_RZ) return round_to16<BF>(b, 1);
+  const uint16_t ra = round_to16<BF>(a, 2);
+  if (a == b) return ra;
+  const uint16_t rb = round_to16<BF>(b, 2);
+  if (ra == rb) return ra;
+  // a midpoint M of the format is a or b: v > a = M rounds like b, v < b = M like a
+  return is_mid16<BF>(a) ? rb : ra;
+}
+// 16-bit input to binary32 (exact)
+template <bool BF> CRM_DEV float from16(uint16_t h) {
+  if (BF) return bitsf((uint32_t)h << 16);
+  const uint32_t sgn = (uint32_t)(h & 0x8000u) << 16, e = (h >> 10) & 0x1Fu, m = h & 0x3FFu;
+  if (e == 0x1Fu) return bitsf(sgn | 0x7F800000u | (m << 13));  // inf, NaN (payload kept)
+  if (e != 0) return bitsf(sgn | ((e + 112u) << 23) | (m << 13));
+  return bitsf(sgn | fbits((float)m * 0x1p-24f));  // subnormal or zero: exact
+}
+
+// binary64 neighbours and result in mode rm
+CRM_DEV double next_up_d(double c) {
+  const uint64_t b = dbits(c);
+  if ((b & 0x7FFFFFFFFFFFFFFFull) == 0) return bitsd(1ull);
+  return bitsd((b >> 63) ? b - 1ull : b + 1ull);
+}
+CRM_DEV double next_down_d(double c) {
+  const uint64_t b = dbits(c);
+  if ((b & 0x7FFFFFFFFFFFFFFFull) == 0) return bitsd(0x8000000000000001ull);
+  return bitsd((b >> 63) ? b + 1ull : b - 1ull);
+}
+CRM_DEV double finish_f64(double c, int sg, int rm) {
+  if (c != c) return c;
+  const bool neg = c != 0.0 ? c < 0.0 : (sg != 0 ? sg < 0 : (dbits(c) >> 63) != 0);
+  if (rm == CRM_RM_RD || (rm == CRM_RM_RZ && !neg)) return sg < 0 ? next_down_d(c) : c;
+  if (rm == CRM_RM_RU || rm == CRM_RM_RZ) return sg > 0 ? next_up_d(c) : c;
+  return c;
 }
 
 // ------------------------------------------------------------------ misc

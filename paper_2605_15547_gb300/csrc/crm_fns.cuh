@@ -20,11 +20,30 @@ template <int KIND> struct FnExp {
   template <int FORM> CRM_DEV static void load(unsigned char *sm) {
     copy_tab(sm, FORM == 1 ? (const void *)CRM_EXP2_T16_D : (const void *)CRM_EXP2_T64U_DF, tab_bytes<FORM>());
   }
-  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h) {
+  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h, int *sg = nullptr) {
     if (FORM == 1)
       y[0] = exp_plain<KIND>(x, (const double *)sm, h);
     else
-      y[0] = exp_df<KIND>(x, (const float4 *)sm, h);
+      y[0] = exp_df<KIND>(x, (const float4 *)sm, h, sg);
+  }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { y[0] = exp_slow<KIND>(x, u, f, sg); }
+};
+
+// The exp family's double-float tier with its 16-entry table in registers (Ctx: the
+// lane's table entry, read by the other lanes through warp shuffles); the main kernel's
+// register-table launch shape.  Same slow path and bits as FnExp.
+template <int KIND> struct FnExpShfl {
+  using T = float;
+  using Ctx = float4;
+  static constexpr int NOUT = 1;
+  template <int FORM> static constexpr int tab_bytes() { return 0; }
+  template <int FORM> CRM_DEV static void load(unsigned char *) {}
+  template <int FORM> CRM_DEV static Ctx make_ctx(const unsigned char *) {
+    const float4 *t = (const float4 *)CRM_EXP2_T16U_DF;
+    return t[threadIdx.x & 15];
+  }
+  template <int FORM> CRM_DEV static void eval(float x, const Ctx &R, float *y, bool &h) {
+    y[0] = exp_df16<KIND>(x, R, h);
   }
   CRM_DEV static void slow(float x, float *y, int &u, bool f) { y[0] = exp_slow<KIND>(x, u, f); }
 };
@@ -37,13 +56,13 @@ template <int KIND> struct FnLog {
   template <int FORM> CRM_DEV static void load(unsigned char *sm) {
     copy_tab(sm, FORM == 1 ? (const void *)CRM_LN_T97_D : (const void *)log_tab_df<KIND>(), tab_bytes<FORM>());
   }
-  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h) {
+  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h, int *sg = nullptr) {
     if (FORM == 1)
       y[0] = log_plain<KIND>(x, (const double2 *)sm, h);
     else
-      y[0] = log_df<KIND>(x, (const float4 *)sm, h);
+      y[0] = log_df<KIND>(x, (const float4 *)sm, h, sg);
   }
-  CRM_DEV static void slow(float x, float *y, int &u, bool f) { y[0] = log_slow<KIND>(x, u, f); }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { y[0] = log_slow<KIND>(x, u, f, sg); }
 };
 
 template <int H> struct FnHyp {
@@ -53,13 +72,13 @@ template <int H> struct FnHyp {
   template <int FORM> CRM_DEV static void load(unsigned char *sm) {
     copy_tab(sm, FORM == 1 ? (const void *)CRM_EXP2_T16_D : (const void *)CRM_EXP2_T64U_DF, tab_bytes<FORM>());
   }
-  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h) {
+  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h, int *sg = nullptr) {
     if (FORM == 1)
       y[0] = hyp_plain<H>(x, (const double *)sm, h);
     else
-      y[0] = hyp_df<H>(x, (const float4 *)sm, h);
+      y[0] = hyp_df<H>(x, (const float4 *)sm, h, sg);
   }
-  CRM_DEV static void slow(float x, float *y, int &u, bool f) { y[0] = hyp_slow<H>(x, u, f); }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { y[0] = hyp_slow<H>(x, u, f, sg); }
 };
 
 template <int KIND> struct FnTrig {
@@ -81,15 +100,15 @@ template <int KIND> struct FnTrig {
     }
     if (KIND == TRIG_TAN) copy_tab(sm + OFF_TT, CRM_TAN_T32_DF, 32 * 8);
   }
-  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h) {
+  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h, int *sg = nullptr) {
     const unsigned char *b = (const unsigned char *)sm;
     if (FORM == 1)
       trig_plain<KIND>(x, (const uint32_t *)b, (const double *)(b + 64), y, h);
     else
       trig_df<KIND>(x, (const uint4 *)(b + OFF_PW), (const float4 *)(b + 64), (const float2 *)(b + OFF_TT), y,
-                    h);
+                    h, sg);
   }
-  CRM_DEV static void slow(float x, float *y, int &u, bool f) { trig_slow<KIND>(x, y, u, f); }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { trig_slow<KIND>(x, y, u, f, sg); }
 };
 
 template <int KIND> struct FnAtrig {
@@ -99,13 +118,13 @@ template <int KIND> struct FnAtrig {
   template <int FORM> CRM_DEV static void load(unsigned char *sm) {
     copy_tab(sm, FORM == 1 ? (const void *)CRM_ATAN_T17_D : (const void *)CRM_ATAN_T17_DF, 18 * 8);
   }
-  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h) {
+  template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h, int *sg = nullptr) {
     if (FORM == 1)
       y[0] = atrig_plain<KIND>(x, (const double *)sm, h);
     else
-      y[0] = atrig_df<KIND>(x, (const float2 *)sm, h);
+      y[0] = atrig_df<KIND>(x, (const float2 *)sm, h, sg);
   }
-  CRM_DEV static void slow(float x, float *y, int &u, bool f) { y[0] = atrig_slow<KIND>(x, u, f); }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { y[0] = atrig_slow<KIND>(x, u, f, sg); }
 };
 
 struct FnRsqrt {
@@ -113,10 +132,10 @@ struct FnRsqrt {
   static constexpr int NOUT = 1;
   template <int FORM> static constexpr int tab_bytes() { return 0; }
   template <int FORM> CRM_DEV static void load(unsigned char *) {}
-  template <int FORM> CRM_DEV static void eval(float x, const void *, float *y, bool &h) {
-    y[0] = FORM == 1 ? rsqrt_plain(x, h) : rsqrt_df(x, h);
+  template <int FORM> CRM_DEV static void eval(float x, const void *, float *y, bool &h, int *sg = nullptr) {
+    y[0] = FORM == 1 ? rsqrt_plain(x, h) : rsqrt_df(x, h, sg);
   }
-  CRM_DEV static void slow(float x, float *y, int &u, bool f) { y[0] = rsqrt_slow(x, u, f); }
+  CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { y[0] = rsqrt_slow(x, u, f, sg); }
 };
 
 // binary64 pair: one main path (double-double), used for both form slots
@@ -131,13 +150,13 @@ struct FnExp2D {
     else
       copy_tab(sm, CRM_EXP2D_T, 96 * 8);
   }
-  template <int FORM> CRM_DEV static void eval(double x, const void *sm, double *y, bool &h) {
+  template <int FORM> CRM_DEV static void eval(double x, const void *sm, double *y, bool &h, int *sg = nullptr) {
     if (FORM == 2)
-      y[0] = exp2d_int(x, (const ulonglong2 *)sm, h);
+      y[0] = exp2d_int(x, (const ulonglong2 *)sm, h, sg);
     else
-      y[0] = exp2d_main(x, (const double *)sm, h);
+      y[0] = exp2d_main(x, (const double *)sm, h, sg);
   }
-  CRM_DEV static void slow(double x, double *y, int &u, bool f) { y[0] = exp2d_slow(x, u, f); }
+  CRM_DEV static void slow(double x, double *y, int &u, bool f, int *sg = nullptr) { y[0] = exp2d_slow(x, u, f, sg); }
 };
 struct FnLogD {
   using T = double;
@@ -152,13 +171,14 @@ struct FnLogD {
       copy_tab(sm + LBYTES, CRM_LOGI_R, 194 * 2);
     }
   }
-  template <int FORM> CRM_DEV static void eval(double x, const void *sm, double *y, bool &h) {
+  template <int FORM> CRM_DEV static void eval(double x, const void *sm, double *y, bool &h, int *sg = nullptr) {
     if (FORM == 2)
-      y[0] = logd_int(x, (const ulonglong2 *)sm, (const unsigned short *)((const unsigned char *)sm + LBYTES), h);
+      y[0] = logd_int(x, (const ulonglong2 *)sm, (const unsigned short *)((const unsigned char *)sm + LBYTES), h,
+                      sg);
     else
-      y[0] = logd_main(x, h);
+      y[0] = logd_main(x, h, sg);
   }
-  CRM_DEV static void slow(double x, double *y, int &u, bool f) { y[0] = logd_slow(x, u, f); }
+  CRM_DEV static void slow(double x, double *y, int &u, bool f, int *sg = nullptr) { y[0] = logd_slow(x, u, f, sg); }
 };
 
 }  // namespace crm

@@ -12,6 +12,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "crm_common.cuh"
 #include "crm_ws.h"
 
@@ -32,6 +34,8 @@ struct KArgs {
   int nsubq;         // sub-queues (each of cap / nsubq entries)
   int force_hard;    // test hook: every lane takes the slow path (1: and every tier of it)
   uint32_t desc;     // array id recorded in queue entries (batch form)
+  int rm;            // rounding direction of the directed kernels (CRM_RM_*)
+  int fmt;           // their element format: 0 the function's own, 1 binary16, 2 bfloat16
 };
 
 // 32-byte vectors (one 256-bit access per thread: ld/st.global.v8.f32, .v4.f64)
@@ -143,6 +147,8 @@ CRM_DEV unsigned push_hard(unsigned hm, const uint64_t *idx, const uint64_t *xb,
 //   template <int FORM> static constexpr int tab_bytes();   (shared memory bytes)
 //   template <int FORM> CRM_DEV static void load(unsigned char *sm);  (fill it)
 //   template <int FORM> CRM_DEV static void eval(T x, const void *sm, T *y, bool &hard);
+//     (or, for a table held in registers: using Ctx = ...; make_ctx<FORM>(sm) once per
+//     thread, and eval takes the Ctx instead of sm)
 //   CRM_DEV static void slow(T x, T *y, int &status, bool force);  (status: bit 0 no tier
 //     decided, bit 1 an FP64 tier ran; force: skip
 //     the first tier's early exit, so that every deeper tier runs -- the test hook)
@@ -152,6 +158,18 @@ CRM_DEV void load_tab(unsigned char *sm) {
   Fn::template load<FORM>(sm);
   __syncthreads();
 }
+
+// What each thread passes to the evaluator: the shared-memory table, or, for an Fn that
+// keeps its table in registers (it declares a Ctx type and make_ctx), the thread's share of
+// the table, loaded once before the loop.
+template <class Fn, int FORM, class = void> struct CtxOf {
+  using type = const void *;
+  CRM_DEV static type make(const unsigned char *sm) { return sm; }
+};
+template <class Fn, int FORM> struct CtxOf<Fn, FORM, std::void_t<typename Fn::Ctx>> {
+  using type = typename Fn::Ctx;
+  CRM_DEV static type make(const unsigned char *sm) { return Fn::template make_ctx<FORM>(sm); }
+};
 
 template <class Fn>
 __device__ __noinline__ void slow_store(typename Fn::T x, uint64_t i, const KArgs &a) {
@@ -170,8 +188,8 @@ __device__ __noinline__ void slow_store(typename Fn::T x, uint64_t i, const KArg
 // Evaluates the W elements of one vector: y0 (and y1 for two outputs) and the hard
 // flags; returns whether any lane of the vector is hard (the flags stay predicates, the
 // queue mask is built from them only on the rare path, hard_mask).
-template <class Fn, int FORM, class V>
-CRM_DEV bool eval_vec(const V &xv, const void *sm, V &y0, V &y1, bool *h) {
+template <class Fn, int FORM, class V, class C>
+CRM_DEV bool eval_vec(const V &xv, const C &sm, V &y0, V &y1, bool *h) {
   using T = typename Fn::T;
   constexpr int W = sizeof(V) / sizeof(T);
   bool any = false;
@@ -210,10 +228,10 @@ CRM_DEV void load_vecs(V *xv, const V *in4, uint32_t base, uint32_t nv) {
 
 // Evaluates and stores the UNROLL vectors of one iteration of a segment (nv vectors from
 // vector `seg` of the array; out4, out4b point at the segment), queueing the hard lanes.
-template <class Fn, int FORM, int UNROLL, int BS, bool WIDE>
+template <class Fn, int FORM, int UNROLL, int BS, bool WIDE, class C>
 CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T, WIDE>::V *xv, uint32_t base, uint32_t nv,
                        typename VecOf<typename Fn::T, WIDE>::V *out4, typename VecOf<typename Fn::T, WIDE>::V *out4b,
-                       uint64_t seg, const unsigned char *sm, const KArgs &a) {
+                       uint64_t seg, const C &sm, const KArgs &a) {
   using T = typename Fn::T;
   using V = typename VecOf<T, WIDE>::V;
   constexpr int W = VecOf<T, WIDE>::W;
@@ -255,8 +273,9 @@ CRM_DEV void main_body(const KArgs &a) {
   using T = typename Fn::T;
   using V = typename VecOf<T, WIDE>::V;
   constexpr int W = VecOf<T, WIDE>::W;
-  __shared__ __align__(16) unsigned char sm[(Fn::template tab_bytes<FORM>() > 0) ? Fn::template tab_bytes<FORM>() : 16];
-  load_tab<Fn, FORM>(sm);
+  __shared__ __align__(16) unsigned char smem[(Fn::template tab_bytes<FORM>() > 0) ? Fn::template tab_bytes<FORM>() : 16];
+  load_tab<Fn, FORM>(smem);
+  const typename CtxOf<Fn, FORM>::type sm = CtxOf<Fn, FORM>::make(smem);
 
   // base < nv <= 2^31 and stride = grid * BS * UNROLL < 2^26 (at most one wave of
   // resident blocks): base + stride stays below 2^32
@@ -526,6 +545,95 @@ __global__ void __launch_bounds__(KBLOCK) k_slow(KArgs a) {
     Fn::slow(x, y, st, a.force_hard == 1);
     out[idx] = y[0];
     if (Fn::NOUT == 2) out[a.n + idx] = y[1];
+    if (st & 1) atomicAdd(&a.hdr->unresolved_total, 1ull);
+    if (st & 2) atomicAdd(&a.hdr->fp64_total, 1ull);
+  });
+}
+
+}  // namespace crm
+
+namespace crm {
+
+// ------------------------------------------------------------------ directed rounding and 16-bit formats
+// k_dir: the same evaluation, run with the sign output (Fn::eval with sg): each element's
+// candidate c and sign(f(x) - c) go through the finisher of the requested direction and
+// format (crm_common.cuh).  Lanes whose sign the fast tier cannot decide (f(x) too close to
+// a binary32 number, or on one) are queued as in k_main, and k_dir_slow finishes them.
+// Elements are processed one per thread per step (UNROLL steps in flight), with coalesced
+// 4-, 8- or 2-byte accesses; 16-bit inputs are widened to binary32 exactly.
+template <class T> CRM_DEV T dir_load(const KArgs &a, uint64_t i) { return ((const T *)a.in)[i]; }
+template <> CRM_DEV float dir_load<float>(const KArgs &a, uint64_t i) {
+  if (a.fmt == 0) return ((const float *)a.in)[i];
+  const uint16_t h = ((const uint16_t *)a.in)[i];
+  return a.fmt == 2 ? from16<true>(h) : from16<false>(h);
+}
+CRM_DEV void dir_store(const KArgs &a, uint64_t i, const float *y, const int *sg, int nout) {
+  for (int r = 0; r < nout; r++) {
+    const uint64_t o = i + (uint64_t)r * a.n;
+    if (a.fmt == 0)
+      ((float *)a.out)[o] = finish_f32(y[r], sg[r], a.rm);
+    else
+      ((uint16_t *)a.out)[o] = a.fmt == 2 ? finish_16<true>(y[r], sg[r], a.rm) : finish_16<false>(y[r], sg[r], a.rm);
+  }
+}
+CRM_DEV void dir_store(const KArgs &a, uint64_t i, const double *y, const int *sg, int) {
+  ((double *)a.out)[i] = finish_f64(y[0], sg[0], a.rm);
+}
+
+template <class Fn>
+__device__ __noinline__ void dir_slow_store(typename Fn::T x, uint64_t i, const KArgs &a) {
+  using T = typename Fn::T;
+  T y[2];
+  int sg[2] = {0, 0}, st;
+  Fn::slow(x, y, st, a.force_hard == 1, sg);
+  dir_store(a, i, y, sg, Fn::NOUT);
+  atomicAdd(&a.hdr->inline_total, 1ull);
+  if (st & 1) atomicAdd(&a.hdr->unresolved_total, 1ull);
+  if (st & 2) atomicAdd(&a.hdr->fp64_total, 1ull);
+}
+
+constexpr int DIR_UNROLL = 4;
+
+template <class Fn>
+__global__ void __launch_bounds__(KBLOCK) k_dir(KArgs a) {
+  using T = typename Fn::T;
+  __shared__ __align__(16) unsigned char sm[(Fn::template tab_bytes<2>() > 0) ? Fn::template tab_bytes<2>() : 16];
+  load_tab<Fn, 2>(sm);
+  const uint64_t stride = (uint64_t)gridDim.x * KBLOCK * DIR_UNROLL;
+  for (uint64_t b = (uint64_t)blockIdx.x * KBLOCK * DIR_UNROLL; b < a.n; b += stride) {
+    T xs[DIR_UNROLL];
+#pragma unroll
+    for (int u = 0; u < DIR_UNROLL; u++) {
+      const uint64_t i = b + (uint64_t)u * KBLOCK + threadIdx.x;
+      xs[u] = i < a.n ? dir_load<T>(a, i) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < DIR_UNROLL; u++) {
+      uint64_t i = b + (uint64_t)u * KBLOCK + threadIdx.x;
+      const bool act = i < a.n;
+      T y[2];
+      int sg[2] = {0, 0};
+      bool h;
+      Fn::template eval<2>(xs[u], sm, y, h, sg);
+      h = (h || a.force_hard) && act;
+      if (act && !h) dir_store(a, i, y, sg, Fn::NOUT);
+      if (__any_sync(0xFFFFFFFFu, h)) {
+        uint64_t xb = xbits_of(xs[u]);
+        if (push_hard<1>(h ? 1u : 0u, &i, &xb, a)) dir_slow_store<Fn>(xs[u], i, a);
+      }
+    }
+  }
+}
+
+template <class Fn>
+__global__ void __launch_bounds__(KBLOCK) k_dir_slow(KArgs a) {
+  using T = typename Fn::T;
+  for_each_queued(a.q, a.qcount, a.nsubq, a.cap, a.hdr, [&](const crm_queue_entry &e) {
+    const uint64_t idx = e.idx & ((1ull << 40) - 1);
+    T y[2];
+    int sg[2] = {0, 0}, st;
+    Fn::slow(x_from_bits<T>(e.x), y, st, a.force_hard == 1, sg);
+    dir_store(a, idx, y, sg, Fn::NOUT);
     if (st & 1) atomicAdd(&a.hdr->unresolved_total, 1ull);
     if (st & 2) atomicAdd(&a.hdr->fp64_total, 1ull);
   });

@@ -12,20 +12,24 @@ typedef int (*occ_fn)(void);
 // Launch shapes of the main kernel that the autotuner chooses among: vectors per thread
 // per iteration, threads per block, register prefetch of the next iteration, a register
 // cap (minimum resident blocks), the vector width (16- or 32-byte accesses: 4 or 8
-// binary32 elements), or the shared-memory pipelined kernel.
+// binary32 elements), the shared-memory pipelined kernel, or (reg_table) the evaluator
+// variant whose table of at most 16 entries lives in registers and is read by warp
+// shuffles instead of shared-memory loads (the exp family).
 struct VariantInfo {
-  int unroll, block, prefetch, pipelined, min_blocks, vec_bytes;
+  int unroll, block, prefetch, pipelined, min_blocks, vec_bytes, reg_table;
 };
-enum { NVARIANT = 10, DEFAULT_VARIANT = 1 };
+enum { NVARIANT = 11, DEFAULT_VARIANT = 1, REGTAB_VARIANT = 10 };
 constexpr VariantInfo VARIANTS[NVARIANT] = {
-    {1, 256, 0, 0, 1, 16}, {2, 256, 0, 0, 1, 16}, {4, 256, 0, 0, 1, 16}, {PVPT, KBLOCK, 0, 1, 1, 16},
-    {2, 256, 1, 0, 4, 16}, {1, 256, 1, 0, 1, 16}, {2, 128, 1, 0, 1, 16}, {2, 512, 1, 0, 1, 16},
-    {1, 256, 1, 0, 1, 32}, {1, 512, 1, 0, 1, 32}};
+    {1, 256, 0, 0, 1, 16, 0}, {2, 256, 0, 0, 1, 16, 0}, {4, 256, 0, 0, 1, 16, 0}, {PVPT, KBLOCK, 0, 1, 1, 16, 0},
+    {2, 256, 1, 0, 4, 16, 0}, {1, 256, 1, 0, 1, 16, 0}, {2, 128, 1, 0, 1, 16, 0}, {2, 512, 1, 0, 1, 16, 0},
+    {1, 256, 1, 0, 1, 32, 0}, {1, 512, 1, 0, 1, 32, 0}, {2, 512, 1, 0, 1, 16, 1}};
 
 struct FuncEntry {
   launch_fn main[3][NVARIANT];  // [form][variant]; form 0 unused; null when unavailable
   const void *main_sym[3][NVARIANT];
   launch_fn slow;
+  launch_fn dmain, dslow;  // directed rounding and 16-bit formats (k_dir, k_dir_slow)
+  const void *dmain_sym;
   int nout;   // 1, or 2 for sincosf
   int dtype;  // 0 binary32, 1 binary64
 };
@@ -43,6 +47,17 @@ cudaError_t launch_main_capped(const KArgs &a, int grid, cudaStream_t s) {
 template <class Fn>
 cudaError_t launch_slow(const KArgs &a, int grid, cudaStream_t s) {
   k_slow<Fn><<<grid, KBLOCK, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class Fn>
+cudaError_t launch_dir(const KArgs &a, int grid, cudaStream_t s) {
+  k_dir<Fn><<<grid, KBLOCK, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <class Fn>
+cudaError_t launch_dir_slow(const KArgs &a, int grid, cudaStream_t s) {
+  k_dir_slow<Fn><<<grid, KBLOCK, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -85,12 +100,24 @@ void set_form(FuncEntry &e) {
   }
 }
 
+// The register-table evaluator FnR of the same function, in the FP64-free form's slot
+// REGTAB_VARIANT (the shape of VARIANTS[REGTAB_VARIANT]).
+template <class FnR>
+void set_regtab_variant(FuncEntry &e) {
+  constexpr VariantInfo I = VARIANTS[REGTAB_VARIANT];
+  e.main[2][REGTAB_VARIANT] = launch_main<FnR, 2, I.unroll, I.block, (bool)I.prefetch, false>;
+  e.main_sym[2][REGTAB_VARIANT] = (const void *)k_main<FnR, 2, I.unroll, I.block, (bool)I.prefetch, false>;
+}
+
 template <class Fn, bool HAS_PLAIN, bool HAS_DF>
 void set_entry(FuncEntry &e) {
   e = FuncEntry();
   if (HAS_PLAIN) set_form<Fn, 1>(e);
   if (HAS_DF) set_form<Fn, 2>(e);
   e.slow = launch_slow<Fn>;
+  e.dmain = launch_dir<Fn>;
+  e.dslow = launch_dir_slow<Fn>;
+  e.dmain_sym = (const void *)k_dir<Fn>;
   e.nout = Fn::NOUT;
   e.dtype = sizeof(typename Fn::T) == 8 ? 1 : 0;
 }

@@ -431,6 +431,56 @@ int crm_eval(int func_id, int dtype, const void *in, void *out, uint64_t n, void
   return crm_eval_form(func_id, dtype, g_default_form, in, out, n, stream);
 }
 
+int crm_eval_rm(int func_id, int dtype, int rmode, const void *in, void *out, uint64_t n, void *stream) {
+  ensure_init();
+  if (func_id < 0 || func_id >= CRM_NUM_FUNCS) return CRM_ERR_FUNC;
+  if (rmode < CRM_RN || rmode > CRM_RZ) return CRM_ERR_ARG;
+  const bool f64 = func_id >= CRM_EXP2;
+  if (dtype == CRM_F16 || dtype == CRM_BF16) {
+    if (f64) return CRM_ERR_DTYPE;  // the 16-bit formats take the binary32 functions
+  } else {
+    int st = check_args(func_id, dtype, in, out, n);
+    if (st) return st;
+    if (rmode == CRM_RN) return crm_eval_form(func_id, dtype, CRM_FORM_AUTO, in, out, n, stream);
+  }
+  if (n == 0) return CRM_OK;
+  if (!in || !out) return CRM_ERR_NULL;
+  const size_t es = dtype == CRM_F64 ? 8 : (dtype == CRM_F32 ? 4 : 2);
+  if (((uintptr_t)in % es) || ((uintptr_t)out % es) || n > (1ull << 40)) return CRM_ERR_ARG;
+  const uintptr_t a0 = (uintptr_t)in, a1 = a0 + n * es;
+  const uintptr_t b0 = (uintptr_t)out, b1 = b0 + n * es * (func_id == CRM_SINCOSF ? 2 : 1);
+  if (a0 != b0 && a0 < b1 && b0 < a1) return CRM_ERR_OVERLAP;
+  const FuncEntry &fe = g_table[func_id];
+  if (!fe.dmain) return CRM_ERR_FORM;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w = nullptr;
+  int st = get_ws(s, kDefaultCap, &w);
+  if (st) return st;
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.in = in;
+  a.out = out;
+  a.n = n;
+  a.hdr = w->hdr;
+  a.q = w->q;
+  a.cap = w->cap;
+  a.qcount = subq_counts(w);
+  a.nsubq = CRM_NSUBQ;
+  a.force_hard = g_force_slow;
+  a.rm = rmode;
+  a.fmt = dtype == CRM_F16 ? 1 : (dtype == CRM_BF16 ? 2 : 0);
+  const int sms = dev_sms();
+  const uint64_t per = (uint64_t)KBLOCK * DIR_UNROLL;
+  uint64_t want = (n + per - 1) / per;
+  const uint64_t cap_blocks = (uint64_t)sms * blocks_per_sm(fe.dmain_sym, KBLOCK);
+  const int grid = (int)(want < cap_blocks ? want : cap_blocks);
+  cudaError_t e = cudaMemsetAsync(a.qcount, 0, CRM_NSUBQ * CRM_SUBQ_STRIDE * 8, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if ((e = fe.dmain(a, grid, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = fe.dslow(a, sms * 2, s)) != cudaSuccess) return cuda_fail(e);
+  return CRM_OK;
+}
+
 int crm_set_form(int form) {
   ensure_init();
   if (form < CRM_FORM_AUTO || form > CRM_FORM_DF32) return CRM_ERR_FORM;
@@ -657,8 +707,9 @@ int crm_set_batch_tile(int log2_elems) {
 }
 
 int crm_variant_info(int variant, int *unroll, int *block, int *prefetch, int *pipelined, int *min_blocks,
-                     int *vec_bytes) {
+                     int *vec_bytes, int *reg_table) {
   if (variant < 0 || variant >= NVARIANT) return CRM_ERR_ARG;
+  if (reg_table) *reg_table = VARIANTS[variant].reg_table;
   if (unroll) *unroll = VARIANTS[variant].unroll;
   if (block) *block = VARIANTS[variant].block;
   if (prefetch) *prefetch = VARIANTS[variant].prefetch;

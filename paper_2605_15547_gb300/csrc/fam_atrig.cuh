@@ -143,7 +143,7 @@ CRM_DEV Pair<float> atan_ratio_df(Pair<float> a, Pair<float> b, const float2 *AT
   return r;
 }
 
-template <int KIND> CRM_DEV float atrig_df(float x, const float2 *AT, bool &hard) {
+template <int KIND> CRM_DEV float atrig_df(float x, const float2 *AT, bool &hard, int *sg = nullptr) {
   float rsp;
   bool sp = atrig_special<KIND>(x, rsp);
   float xs = sp ? 0.5f : x;
@@ -181,9 +181,11 @@ template <int KIND> CRM_DEV float atrig_df(float x, const float2 *AT, bool &hard
   if (KIND == AT_ACOS && flip) r = df_add_ordered_raw({CRM_PI_F_HI, CRM_PI_F_LO}, -r);  // pi > r
   if (__builtin_expect(sp, 0)) {
     hard = false;
+    put_sg(sg, 0);  // NaN, +-0, acos(1) = +0: exact
     return rsp;
   }
-  const float y = round_df(r.hi, r.lo, hard);
+  const float y = round_df(r.hi, r.lo, hard, sg);
+  if (sg && KIND != AT_ACOS && x < 0.0f) *sg = -*sg;
   return (KIND != AT_ACOS && x < 0.0f) ? -y : y;
 }
 
@@ -279,9 +281,11 @@ CRM_DEV U128 q_sqrt(U128 d, int &k) {
 // atanf: r = |x| (exact) or 1/|x| (q_div, then shifted; 1/|x| is within 2^2 units) for
 // |x| > 1, pi/2 minus the core for |x| > 1; error bound 2^11 units against results of at
 // least 2^-12.  |x| < 2^-12 gives x (x^3/3 is below half an ulp), +-inf RN(+-pi/2).
-CRM_DEV float atanf_int(float x, bool &hard) {
+CRM_DEV float atanf_int(float x, bool &hard, int *sg = nullptr) {
   hard = false;
   const float ax = fabsf(x);
+  // atan x - x has the sign of -x; RN(pi/2) = 0x1.921fb6p+0 lies above pi/2
+  put_sg(sg, -sgnf(x));
   if (ax < 0x1p-12f) return x;
   if (ax == CRM_INF_F) return copysignf(0x1.921fb6p+0f, x);
   const bool sw = ax > 1.0f;
@@ -297,7 +301,8 @@ CRM_DEV float atanf_int(float x, bool &hard) {
   }
   U128 v = atan_q126(R);
   if (sw) v = sub128(q_ld(CRM_ATANI_PIO2), v);
-  const float y = q_round_f(v, U128{2048ull, 0ull}, hard);
+  const float y = q_round_f(v, U128{2048ull, 0ull}, hard, 0, sg);
+  if (sg && x < 0.0f) *sg = -*sg;
   return x < 0.0f ? -y : y;
 }
 
@@ -309,13 +314,18 @@ CRM_DEV float atanf_int(float x, bool &hard) {
 // a negative x is formed as (pi - theta)/2 = pi/2 - theta/2 and rounded with es = 1.
 // |x| = 1 and the tiny ranges (asin x = x below 2^-12, x + x^3/6 being within half an
 // ulp; acos x = RN(pi/2) below 2^-27, pi/2 being 2^-25.8 from a midpoint) are direct.
-template <int KIND> CRM_DEV float asincosf_int(float x, bool &hard) {
+template <int KIND> CRM_DEV float asincosf_int(float x, bool &hard, int *sg = nullptr) {
   hard = false;
   const float ax = fabsf(x);
+  // asin x - x has the sign of x, RN(pi/2) = 0x1.921fb6p+0 and RN(pi) = 0x1.921fb6p+1 lie
+  // above pi/2 and pi (and acos x < pi/2 + 2^-27 < RN(pi/2) for |x| < 2^-27)
   if (KIND == AT_ASIN) {
+    put_sg(sg, sgnf(x));
     if (ax < 0x1p-12f) return x;
+    put_sg(sg, -sgnf(x));
     if (ax == 1.0f) return copysignf(0x1.921fb6p+0f, x);
   } else {
+    put_sg(sg, -1);
     if (ax < 0x1p-27f) return 0x1.921fb6p+0f;
     if (x == -1.0f) return 0x1.921fb6p+1f;
   }
@@ -324,21 +334,31 @@ template <int KIND> CRM_DEV float asincosf_int(float x, bool &hard) {
   const U128 s = q_sqrt(sub128(U128{0ull, 1ull << 62}, q_mul(a, a)), k);
   const U128 sq = q_shr(s, k);
   if (KIND == AT_ASIN) {
-    const float y = q_round_f(atan2_q126(a, sq), U128{1ull << 16, 0ull}, hard);
+    const float y = q_round_f(atan2_q126(a, sq), U128{1ull << 16, 0ull}, hard, 0, sg);
+    if (sg && x < 0.0f) *sg = -*sg;
     return x < 0.0f ? -y : y;
   }
   const U128 th = atan2_q126(sq, a);
-  if (x > 0.0f) return q_round_f(th, U128{1ull << 16, 0ull}, hard);
-  return q_round_f(sub128(q_ld(CRM_ATANI_PIO2), q_shr(th, 1)), U128{1ull << 16, 0ull}, hard, 1);
+  if (x > 0.0f) return q_round_f(th, U128{1ull << 16, 0ull}, hard, 0, sg);
+  return q_round_f(sub128(q_ld(CRM_ATANI_PIO2), q_shr(th, 1)), U128{1ull << 16, 0ull}, hard, 1, sg);
 }
 
-template <int KIND> CRM_DEV float atrig_slow(float x, int &unresolved, bool force) {
+template <int KIND> CRM_DEV float atrig_slow(float x, int &unresolved, bool force, int *sg = nullptr) {
   bool hard;
   unresolved = false;
   float sp;
-  if (atrig_special<KIND>(x, sp)) return sp;
-  float r = KIND == AT_ATAN ? atanf_int(x, hard) : asincosf_int<KIND>(x, hard);
+  if (atrig_special<KIND>(x, sp)) {
+    put_sg(sg, 0);
+    return sp;
+  }
+  float r = KIND == AT_ATAN ? atanf_int(x, hard, sg) : asincosf_int<KIND>(x, hard, sg);
   if (!hard && !force) return r;
+  if (sg) {  // the tiny ranges and the +-1 / +-inf ends are exact statements above
+    const float ax = fabsf(x);
+    if ((KIND == AT_ATAN && (ax < 0x1p-12f || ax == CRM_INF_F)) ||
+        (KIND == AT_ASIN && (ax < 0x1p-12f || ax == 1.0f)) || (KIND == AT_ACOS && (ax < 0x1p-27f || x == -1.0f)))
+      return r;
+  }
   double ax = fabs((double)x);
   Pair<double> a, b;
   bool flip = false;
@@ -360,7 +380,7 @@ template <int KIND> CRM_DEV float atrig_slow(float x, int &unresolved, bool forc
   Pair<double> y = atan_ratio_dd(a, b);
   if (flip) y = dd_add(dd(CRM_PI_D_HI, CRM_PI_D_LO), dd_neg(y));
   if (KIND != AT_ACOS && x < 0.0f) y = dd_neg(y);
-  r = round_dd_to_f(y.hi, y.lo, ATRIG_DD_EPS * fabs(y.hi), hard);
+  r = round_dd_to_f(y.hi, y.lo, ATRIG_DD_EPS * fabs(y.hi), hard, sg);
   unresolved = hard ? 3 : 2;  // the double-double tier ran
   return r;
 }

@@ -144,7 +144,10 @@ template <int KIND> CRM_DEV void exp_df_core(float x, const float4 *T64U, float 
   r = b + z;
 }
 
-template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard) {
+// With sg (the directed-rounding kernels) the lane also reports the sign of b^x - y: the
+// saturated results lie below +inf and above +0 (equal for x = +-inf), and the subnormal
+// band's integer is compared with u itself.
+template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard, int *sg = nullptr) {
   using K = ExpK<KIND>;
   float s, r;
   uint32_t sb;
@@ -153,12 +156,13 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
   if (__builtin_expect(ok, 1)) {
     // the exponent increment (N >> 6) << 23: sb >> 6 is N >> 6 plus 0x12D0000 (borrow
     // included), whose shift by 23 vanishes modulo 2^32
-    const float y = round_df(s, r, hard);
+    const float y = round_df(s, r, hard, sg);
     return bitsf(fbits(y) + ((sb >> 6) << 23));
   }
   // Out of range (rare): +inf, +0, a quiet NaN, or a subnormal result.
   hard = false;
   float y = x != x ? qnan_of(x) : (x > 0.0f ? CRM_INF_F : 0.0f);
+  put_sg(sg, (x != x || fabsf(x) == CRM_INF_F) ? 0 : (x > 0.0f ? -1 : 1));
   if ((x >= K::XZERO) && (x < K::XSUB)) {
     // The result is the integer nearest to u = (s2 + l2) 2^(k + 149) times 2^-149, with
     // (s2, l2) the normalised pair (k + 149 in [-2, 23], the scaling exact).  With
@@ -169,6 +173,106 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
     const Pair<float> p = fast_two_sum(s, r);
     const int N = (int)(sb - fbits(CRM_SHIFTER_F));
     const float sc = bitsf((uint32_t)((N >> 6) + 149 + 127) << 23);
+    const float uh = p.hi * sc, ul = p.lo * sc;
+    const float q = rintf(uh);
+    const float d = (uh - q) + ul;
+    const float qi = q + (d > 0.5f ? 1.0f : (d < -0.5f ? -1.0f : 0.0f));
+    hard = fabsf(fabsf(d) - 0.5f) <= 0x1p-12f;
+    if (sg) {  // u - qi, decided unless u is within the error of the integer qi
+      const float dq = d - (qi - q);
+      hard = !(fabsf(dq) > 0x1p-12f);
+      *sg = dq > 0.0f ? 1 : -1;
+    }
+    y = qi * 0x1p-149f;
+  }
+  return y;
+}
+
+// ------------------------------------------------------------------ register-table variant
+// The double-float tier with a 16-entry table kept in registers instead of the 64-entry
+// shared-memory table: lane l of every warp holds entry l mod 16 of (2^(j/16) hi, lo,
+// 2^(j/16) ln2 hi, lo), and each lane fetches its entry with four warp shuffles (the
+// paper's tables of at most 16 entries read by permutes instead of gathers, Sec. II.A).
+// t = k + j/16 + g, |g| <= 2^-4.99, so the polynomial gains a degree and its quadratic
+// term, up to 2^-12 of the result, is formed with exact products:
+//   2^g T = Th + Uh gh + Th c2 + [Tl + Uh gl + Ul gh + Tl c2
+//           + Th (c2l + a2 gh^2 - c2 - c2l + 2 a2 gh gl + g^3 (a3 + a4 g + a5 g^2 + a6 g^3))]
+// with c2 + c2l = a2_hi gh^2 exactly.  s0 = RN(Th + Uh gh) and its error z (one FMA each),
+// Th c2 = w + wl exactly, s = s0 + w by Fast2Sum (|w| <= 2^-12 |s0|) with error z2; the
+// bracket, z, z2 and wl are summed in float into r.  Error budget, relative to the result:
+// Taylor remainder a7 g^7 2^-50.9; the cubic tail's roundings 2^-41.6; the bracket's
+// roundings (|bracket| <= 2^-19) 2^-41; the sum into r 2^-41.2; t from x C1 and the split of
+// C 2^-40.7; tables and the dropped cross terms 2^-43: total < 2^-38, inside the test's
+// 2^-37.
+template <int KIND> CRM_DEV void exp_df16_core(float x, const float4 &R, float &s, float &r, uint32_t &sb) {
+  using K = ExpK<KIND>;
+  float th, tl;
+  if (KIND == 1) {
+    th = x;
+    tl = 0.0f;
+  } else {
+    th = x * K::F0;
+    tl = fma_(x, K::F0, -th);
+    tl = fma_(x, K::F1, tl);
+  }
+  const float sh = fma_(th, 16.0f, CRM_SHIFTER_F);
+  sb = fbits(sh);  // 0x4B400000 + N, N = rint(16 t); 0x4B400000 is 0 modulo 16
+  const float nf = sh - CRM_SHIFTER_F;
+  const float f = fma_(nf, -0.0625f, th);
+  float gh, gl;
+  if (KIND == 1) {
+    gh = f;
+    gl = 0.0f;
+  } else {
+    gh = f + tl;
+    gl = tl - (gh - f);
+  }
+  const int j = (int)(sb & 15u);
+  float4 T;
+  T.x = __shfl_sync(0xFFFFFFFFu, R.x, j);
+  T.y = __shfl_sync(0xFFFFFFFFu, R.y, j);
+  T.z = __shfl_sync(0xFFFFFFFFu, R.z, j);
+  T.w = __shfl_sync(0xFFFFFFFFu, R.w, j);
+  float q = fma_(gh, CRM_EXP2_A6_F, CRM_EXP2_A5_F);
+  q = fma_(gh, q, CRM_EXP2_A4_F);
+  q = fma_(gh, q, CRM_EXP2_A3_F);
+  const float g2 = gh * gh;
+  const float g2l = fma_(gh, gh, -g2);
+  const float c2 = CRM_EXP2_A2_HI_F * g2;
+  const float c2l = fma_(CRM_EXP2_A2_HI_F, g2, -c2);
+  const float w = T.x * c2;
+  const float wl = fma_(T.x, c2, -w);
+  const float s0 = fma_(T.z, gh, T.x);
+  const float z = fma_(T.z, gh, T.x - s0);
+  s = s0 + w;
+  const float z2 = w - (s - s0);
+  float tq = fma_(CRM_EXP2_A2_HI_F, g2l, CRM_EXP2_A2_LO_F * g2) + c2l;
+  if (KIND != 1) tq = fma_((2.0f * CRM_EXP2_A2_F) * gh, gl, tq);
+  tq = fma_(g2 * gh, q, tq);
+  float b = (KIND == 1) ? T.y : fma_(T.z, gl, T.y);
+  b = fma_(T.w, gh, b);
+  b = fma_(T.y, c2, b);
+  b = fma_(T.x, tq, b);
+  r = ((b + z) + z2) + wl;
+}
+
+template <int KIND> CRM_DEV float exp_df16(float x, const float4 &R, bool &hard) {
+  using K = ExpK<KIND>;
+  float s, r;
+  uint32_t sb;
+  exp_df16_core<KIND>(x, R, s, r, sb);
+  const bool ok = (x >= K::XSUB) && (x <= K::XOVF);  // false for NaN
+  if (__builtin_expect(ok, 1)) {
+    const float y = round_df(s, r, hard);
+    return bitsf(fbits(y) + ((sb >> 4) << 23));  // exponent increment N >> 4, as in exp_df
+  }
+  // out of range: as in exp_df, with k = N >> 4
+  hard = false;
+  float y = x != x ? qnan_of(x) : (x > 0.0f ? CRM_INF_F : 0.0f);
+  if ((x >= K::XZERO) && (x < K::XSUB)) {
+    const Pair<float> p = fast_two_sum(s, r);
+    const int N = (int)(sb - fbits(CRM_SHIFTER_F));
+    const float sc = bitsf((uint32_t)((N >> 4) + 149 + 127) << 23);
     const float uh = p.hi * sc, ul = p.lo * sc;
     const float q = rintf(uh);
     const float d = (uh - q) + ul;
@@ -210,11 +314,11 @@ template <int KIND> CRM_DEV Pair<double> exp_dd_core(float x, int &k) {
   return dd_mul(T, p);
 }
 
-template <int KIND> CRM_DEV float exp_dd(float x, bool &hard) {
+template <int KIND> CRM_DEV float exp_dd(float x, bool &hard, int *sg = nullptr) {
   int k;
   Pair<double> y = exp_dd_core<KIND>(x, k);
   double s = y.hi * pow2d(k), t = y.lo * pow2d(k);  // exact: results stay in double range
-  return round_dd_to_f(s, t, EXP_DD_EPS * fabs(s), hard);
+  return round_dd_to_f(s, t, EXP_DD_EPS * fabs(s), hard, sg);
 }
 
 // ------------------------------------------------------------------ FP64-free middle tier
@@ -256,14 +360,16 @@ template <int KIND> CRM_DEV U128 expq_arg(uint32_t ax) {
   return X;
 }
 
-template <int KIND> CRM_DEV float expf_int(float x, bool &hard) {
+template <int KIND> CRM_DEV float expf_int(float x, bool &hard, int *sg = nullptr) {
   const uint32_t ax = fbits(x) & 0x7FFFFFFFu;
   hard = false;
+  put_sg(sg, sgnf(x));  // b^x - 1 has the sign of x
   if ((int)(ax >> 23) < 127 - 60) return 1.0f;
   U128 X = expq_arg<KIND>(ax);  // |x| log2(b) 2^96
   if (x < 0.0f) X = neg128(X);
   int k;
   const U128 Y = exp2q_core(X, (const ulonglong2 *)CRM_EXP2I_T, k);  // [2^124, 2^125)
+  put_sg(sg, k >= 128 ? -1 : 1);
   if (k >= 128) return CRM_INF_F;  // b^x >= 2^128
   if (k < -150) return 0.0f;       // b^x < 2^-150
   // discard sh bits: 101 for a normal result, 101 + (-126 - k) <= 125 for a subnormal one
@@ -275,20 +381,41 @@ template <int KIND> CRM_DEV float expf_int(float x, bool &hard) {
   const uint64_t ERR = 1ull << 55;
   hard = (dlt.hi == 0 && dlt.lo <= ERR) || (dlt.hi == ~0ull && dlt.lo >= 0ull - ERR);
   const uint32_t up = ((int64_t)dlt.hi > 0 || (dlt.hi == 0 && dlt.lo != 0)) ? 1u : 0u;
+  if (sg) {  // the sign of v - y: decided unless the discarded part is within ERR of 0 or of a unit
+    hard = le128(rem, U128{ERR, 0ull}) || le128(sub128(U128{0ull, 1ull << s64}, rem), U128{ERR, 0ull});
+    *sg = up ? -1 : 1;
+  }
   const uint32_t bits = k < -126 ? (uint32_t)mant + up : ((uint32_t)(k + 126) << 23) + (uint32_t)mant + up;
   return bitsf(bits);
 }
 
 // Slow path used for lanes whose fast-path test failed: the FP64-free tier, then
 // double-double.
-template <int KIND> CRM_DEV float exp_slow(float x, int &unresolved, bool force) {
+// With sg: the exact results, which no tier can decide by an error bound, are returned
+// directly (2^x for integer x >= -149, 10^x for integer x in [1, 10], whose 5^x fits 24 bits).
+template <int KIND> CRM_DEV float exp_slow(float x, int &unresolved, bool force, int *sg = nullptr) {
   unresolved = false;
   float sp;
-  if (exp_special<KIND>(x, sp)) return sp;
+  if (exp_special<KIND>(x, sp)) {
+    put_sg(sg, (x != x || fabsf(x) == CRM_INF_F) ? 0 : (x > 0.0f ? -1 : 1));
+    return sp;
+  }
   bool hard;
-  float r = expf_int<KIND>(x, hard);
+  float r = expf_int<KIND>(x, hard, sg);
   if (!hard && !force) return r;
-  r = exp_dd<KIND>(x, hard);
+  if (sg && x == rintf(x)) {
+    if (KIND == 1 && x >= -149.0f) {
+      *sg = 0;
+      return x >= -126.0f ? bitsf((uint32_t)((int)x + 127) << 23) : bitsf(1u << ((int)x + 149));
+    }
+    if (KIND == 2 && x >= 1.0f && x <= 10.0f) {
+      float p = 1.0f;
+      for (int i = 0; i < (int)x; i++) p *= 10.0f;  // exact: 10^10 < 2^34, 5^10 < 2^24
+      *sg = 0;
+      return p;
+    }
+  }
+  r = exp_dd<KIND>(x, hard, sg);
   unresolved = hard ? 3 : 2;  // the double-double tier ran
   return r;
 }

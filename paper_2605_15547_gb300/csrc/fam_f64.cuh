@@ -64,7 +64,7 @@ CRM_DEV Pair<double> exp2d_core(double x, int &k, const double *T) {
   return dd_add(t, dd_mul(t, p));
 }
 
-CRM_DEV double exp2d_main(double x, const double *T, bool &hard) {
+CRM_DEV double exp2d_main(double x, const double *T, bool &hard, int *sg = nullptr) {
   double r;
   bool sp = exp2d_special(x, r);
   int k;
@@ -82,6 +82,12 @@ CRM_DEV double exp2d_main(double x, const double *T, bool &hard) {
   const double qi = q + (d > 0.5 ? 1.0 : (d < -0.5 ? -1.0 : 0.0));
   const bool hsub = fabs(fabs(d) - 0.5) <= 0x1p-46;
   hard = !sp && (sub ? hsub : hard_dd(y.hi, y.lo));
+  if (sg) {  // the sign of 2^x - result, from the low word (or u - qi); 0 for exact specials
+    const double dq = d - (qi - q);
+    const bool inf = fabs(x) == CRM_INF_D;
+    *sg = sp ? ((x != x || inf) ? 0 : (x > 0.0 ? -1 : 1)) : (sub ? (dq > 0.0 ? 1 : -1) : (y.lo > 0.0 ? 1 : -1));
+    hard = !sp && (sub ? !(fabs(dq) > 0x1p-46) : !(fabs(y.lo) > fabs(y.hi) * 0x1p-98));
+  }
   double out = sub ? qi * 0x1p-1074 : scale_d(y.hi, k);
   return sp ? r : out;
 }
@@ -115,6 +121,7 @@ CRM_DEV U128 add128_64(U128 a, uint64_t b) {
   r.hi = a.hi + (r.lo < b ? 1ull : 0ull);
   return r;
 }
+CRM_DEV bool le128(U128 a, U128 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
 CRM_DEV U128 shr128(U128 a, int s) {  // 0 < s < 64
   return {(a.lo >> s) | (a.hi << (64 - s)), a.hi >> s};
 }
@@ -154,7 +161,7 @@ CRM_DEV U128 exp2q_core(U128 X, const ulonglong2 *T, int &k) {
   return add128({t.x, t.y}, tp);  // in [2^124, 2^125)
 }
 
-CRM_DEV double exp2d_int(double x, const ulonglong2 *T, bool &hard) {
+CRM_DEV double exp2d_int(double x, const ulonglong2 *T, bool &hard, int *sg = nullptr) {
   double rs;
   const uint64_t b = dbits(x);
   const bool sp = exp2d_special_bits(b, rs);
@@ -175,20 +182,29 @@ CRM_DEV double exp2d_int(double x, const ulonglong2 *T, bool &hard) {
   const uint64_t ERR = 1ull << 54;
   uint64_t bits;
   bool near;
+  bool up, ndir;  // ndir: the discarded part is within ERR of 0 or of a full unit
   if (__builtin_expect(k >= -1022, 1)) {  // normal result: round at bit 72
     const uint64_t dh = (Y.hi & 0xFFull) - 0x80ull;  // high word of (discarded part - half ulp)
-    const bool up = (int64_t)dh > 0 || (dh == 0 && Y.lo != 0);
+    up = (int64_t)dh > 0 || (dh == 0 && Y.lo != 0);
     near = (dh == 0 && Y.lo <= ERR) || (dh == ~0ull && Y.lo >= 0ull - ERR);
     bits = ((uint64_t)(int64_t)(k + 1022) << 52) + (Y.hi >> 8) + (up ? 1ull : 0ull);
+    const uint64_t rh = Y.hi & 0xFFull;
+    ndir = (rh == 0 && Y.lo <= ERR) || (rh == 0xFFull && Y.lo >= 0ull - ERR);
   } else {  // subnormal result: round at bit 72 + (-1022 - k) <= 125
     const int sh64 = 8 + (-1022 - k);
     const uint64_t remh = Y.hi & ((1ull << sh64) - 1ull);
     const uint64_t dh = remh - (1ull << (sh64 - 1));
-    const bool up = (int64_t)dh > 0 || (dh == 0 && Y.lo != 0);
+    up = (int64_t)dh > 0 || (dh == 0 && Y.lo != 0);
     near = (dh == 0 && Y.lo <= ERR) || (dh == ~0ull && Y.lo >= 0ull - ERR);
     bits = (Y.hi >> sh64) + (up ? 1ull : 0ull);
+    ndir = (remh == 0 && Y.lo <= ERR) || (remh == (1ull << sh64) - 1ull && Y.lo >= 0ull - ERR);
   }
   hard = !sp && !tiny && near;
+  if (sg) {  // the sign of 2^x - result
+    const uint64_t ab = b & 0x7FFFFFFFFFFFFFFFull;
+    *sg = sp ? ((ab >= 0x7FF0000000000000ull) ? 0 : ((b >> 63) ? 1 : -1)) : (tiny ? (ab == 0 ? 0 : ((b >> 63) ? -1 : 1)) : (up ? -1 : 1));
+    hard = !sp && !tiny && ndir;
+  }
   return sp ? rs : (tiny ? 1.0 : bitsd(bits));
 }
 
@@ -230,11 +246,15 @@ CRM_DEV Pair<double> logd_core(double x) {
   return dd_add(dd_add(eK, L), l1p);
 }
 
-CRM_DEV double logd_main(double x, bool &hard) {
+CRM_DEV double logd_main(double x, bool &hard, int *sg = nullptr) {
   double r;
   bool sp = logd_special(x, r);
   Pair<double> y = logd_core(sp ? 2.0 : x);
   hard = !sp && hard_dd(y.hi, y.lo);
+  if (sg) {  // the sign of log x - result from the low word; specials are exact
+    *sg = sp ? 0 : (y.lo > 0.0 ? 1 : -1);
+    hard = !sp && !(fabs(y.lo) > fabs(y.hi) * 0x1p-98);
+  }
   return sp ? r : y.hi;
 }
 
@@ -325,7 +345,7 @@ CRM_DEV U128 logz_q116(uint64_t b, const ulonglong2 *LT, const unsigned short *R
   return add128(add128(eL, {Lj.x, Lj.y}), add128(rQ, rS));
 }
 
-CRM_DEV double logd_int(double x, const ulonglong2 *LT, const unsigned short *RT, bool &hard) {
+CRM_DEV double logd_int(double x, const ulonglong2 *LT, const unsigned short *RT, bool &hard, int *sg = nullptr) {
   double rs;
   const bool sp = logd_special_bits(dbits(x), rs);
   const uint64_t b = sp ? 0x4000000000000000ull : dbits(x);  // 2.0 on the special lanes
@@ -353,6 +373,12 @@ CRM_DEV double logd_int(double x, const ulonglong2 *LT, const unsigned short *RT
   const bool up = (int64_t)dlt.hi > 0 || (dlt.hi == 0 && dlt.lo != 0);
   const uint64_t bits = ((uint64_t)(sh + 958) << 52) + mant + (up ? 1ull : 0ull);
   hard = !sp && !zero && near;
+  if (sg) {  // the sign of log x - result: decided unless rem is within err of 0 or a unit
+    const U128 E = {err, 0ull};
+    const U128 unit = add128(half, half);
+    hard = !sp && !zero && (le128(rem, E) || le128(sub128(unit, rem), E));
+    *sg = (sp || zero) ? 0 : ((up != zneg) ? -1 : 1);
+  }
   return sp ? rs : (zero ? 0.0 : bitsd(bits | (zneg ? 0x8000000000000000ull : 0ull)));
 }
 
@@ -378,8 +404,9 @@ CRM_DEV U128 q_mul(U128 a, U128 b) {
 }
 // RN to binary32 of v 2^(es - 126) (|v| < 2^127, es >= 0, |value| >= 2^-126) when no
 // midpoint lies within err units of v (err a 128-bit count)
-CRM_DEV bool le128(U128 a, U128 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
-CRM_DEV float q_round_f(U128 v, U128 err, bool &hard, int es = 0) {
+// With sg: also the sign of the value minus the result (decided unless the discarded
+// part is within err of 0 or of a full unit: then hard).
+CRM_DEV float q_round_f(U128 v, U128 err, bool &hard, int es = 0, int *sg = nullptr) {
   const bool n = q_neg(v);
   const U128 A = n ? neg128(v) : v;
   const int p = A.hi ? 127 - __clzll(A.hi) : 63 - __clzll(A.lo | 1ull);  // leading bit
@@ -402,8 +429,18 @@ CRM_DEV float q_round_f(U128 v, U128 err, bool &hard, int es = 0) {
   const U128 dlt = sub128(rem, half);
   hard = le128(q_neg(dlt) ? neg128(dlt) : dlt, err);
   const uint32_t up = ((int64_t)dlt.hi > 0 || (dlt.hi == 0 && dlt.lo != 0)) ? 1u : 0u;
+  if (sg) {
+    hard = le128(rem, err) || le128(sub128(add128(half, half), rem), err);
+    *sg = (up != 0) != n ? -1 : 1;  // |v| below |result| when rounded up; negated for v < 0
+  }
   // mant 2^(sh - 126), mant in [2^23, 2^24): exponent field sh + 24, the leading bit adds 1
-  if (sh + 23 + es >= 255) return n ? -CRM_INF_F : CRM_INF_F;  // |value| >= 2^128
+  if (sh + 23 + es >= 255) {  // |value| >= 2^128: infinity, beyond the finite value
+    if (sg) {
+      hard = false;
+      *sg = n ? 1 : -1;
+    }
+    return n ? -CRM_INF_F : CRM_INF_F;
+  }
   const uint32_t bits = ((uint32_t)(sh + 23 + es) << 23) + (uint32_t)mant + up;
   return bitsf(bits | (n ? 0x80000000u : 0u));
 }
@@ -577,7 +614,10 @@ CRM_DEV U192 u_pow2(int k) {
 
 // Round the interval [M - dlo, M + dhi] (value M 2^-fb, M > 0) to binary64 nearest.
 // Returns false (unresolved) if a midpoint lies inside.  `neg` sets the sign.
-CRM_DEV bool u_round64(U192 M, int fb, uint64_t dlo, uint64_t dhi, bool neg, double &out) {
+// With sg (directed rounding): out = the truncation of M (q ulps) and *sg = +-1 (the sign
+// of the value minus out), when the whole interval lies strictly between q and q + 1 ulps;
+// false otherwise (an exact result is decided by the caller).
+CRM_DEV bool u_round64(U192 M, int fb, uint64_t dlo, uint64_t dhi, bool neg, double &out, int *sg = nullptr) {
   int b = u_bitlen(M);  // value in [2^(b-1-fb), 2^(b-fb))
   int ex = b - 1 - fb;
   int drop;
@@ -593,7 +633,11 @@ CRM_DEV bool u_round64(U192 M, int fb, uint64_t dlo, uint64_t dhi, bool neg, dou
   bool lo_ok = u_cmp(rem, U192{{dlo, 0, 0}}) >= 0;
   U192 hi = u_add(rem, U192{{dhi, 0, 0}});
   bool up;
-  if (lo_ok && u_cmp(lo, half) > 0)
+  if (sg) {
+    if (!lo_ok || u_is_zero(lo) || u_cmp(hi, u_add(half, half)) >= 0) return false;
+    up = false;
+    *sg = neg ? -1 : 1;
+  } else if (lo_ok && u_cmp(lo, half) > 0)
     up = true;
   else if (u_cmp(hi, half) < 0)
     up = false;
@@ -615,14 +659,32 @@ CRM_DEV bool u_round64(U192 M, int fb, uint64_t dlo, uint64_t dhi, bool neg, dou
 // u = R ln2 (Q0.191), e^u by Taylor (Q2.190), times the three table values (Q2.190).
 // Every step truncates (floors), so the computed y satisfies y <= 2^x 2^-k < y + 2^10
 // units of 2^-190 (16 Taylor terms, 4 products, R and ln2 truncation).
-CRM_DEV bool exp2d_exact(double x, double &out) {
+// R = x - N/4096 is exact in binary64 unless -2^-13 < x < 0 (then N = -1 and R = 2^-12 - |x|
+// spans more than 53 bits): there R is formed in fixed point, rounded down like every other
+// step, as 2^179 - ceil(|x| 2^191).
+CRM_DEV bool exp2d_exact(double x, double &out, int *sg = nullptr) {
   double nd = floor(x * 4096.0);
   long long N = (long long)nd;
-  double R = fma_(nd, -0x1p-12, x);  // exact, in [0, 2^-12)
+  double R = fma_(nd, -0x1p-12, x);  // exact, in [0, 2^-12), unless -2^-13 < x < 0
   int k = (int)(N >> 12);
   int i = (int)(N & 4095);
   U192 Rf = u_zero();
-  if (R > 0.0) {
+  if (x < 0.0 && x > -0x1p-13) {
+    const uint64_t xb = dbits(x) & 0x7FFFFFFFFFFFFFFFull;
+    const int be = (int)(xb >> 52);
+    const uint64_t xm = (xb & 0x000FFFFFFFFFFFFFull) | (be ? (1ull << 52) : 0ull);
+    const int sh = (be ? be - 1075 : -1074) + 191;  // |x| 2^191 = xm 2^sh, sh <= 125
+    U192 c;
+    if (sh >= 0) {
+      c = u_shl(U192{{xm, 0, 0}}, sh);
+    } else {
+      const int d = -sh;
+      const uint64_t q = d < 64 ? (xm >> d) : 0ull;
+      const bool lost = d < 64 ? (xm & ((1ull << d) - 1ull)) != 0 : true;
+      c = U192{{q + (lost ? 1ull : 0ull), 0, 0}};
+    }
+    Rf = u_sub(u_pow2(179), c);
+  } else if (R > 0.0) {
     uint64_t rb = dbits(R);
     int re = (int)(rb >> 52) - 1075;
     uint64_t rm = (rb & 0x000FFFFFFFFFFFFFull) | ((rb >> 52) ? (1ull << 52) : 0);
@@ -646,13 +708,13 @@ CRM_DEV bool exp2d_exact(double x, double &out) {
     sum = u_mulfx(sum, U192{{e[0], e[1], e[2]}}, 190);
   }
   // value = sum 2^(k - 190): round with the interval [sum, sum + 2^10]
-  return u_round64(sum, 190 - k, 0, 1024, false, out);
+  return u_round64(sum, 190 - k, 0, 1024, false, out, sg);
 }
 
 // log(x), x > 0 finite, exactly: x = 2^e m, m in [1,2), c = 1 + j/128 <= m,
 // r = (m - c)/c in [0, 1/128) (Q0.191), log1p(r) = P - Q with P and Q the positive and
 // negative Taylor terms, S = log(c) + log1p(r); |log x| = |e ln2 + S| in Q11.181.
-CRM_DEV bool logd_exact(double x, double &out) {
+CRM_DEV bool logd_exact(double x, double &out, int *sg = nullptr) {
   uint64_t b = dbits(x);
   int be = (int)(b >> 52);
   uint64_t f = b & 0x000FFFFFFFFFFFFFull;
@@ -691,31 +753,37 @@ CRM_DEV bool logd_exact(double x, double &out) {
   if (u_is_zero(M)) return false;
   // errors (units of 2^-181): S within 64 units of 2^-191 (< 1), the shift of S 1, the
   // truncated ln2 times |e|: |e| + 1.  The interval is M -+ (|e| + 16).
-  return u_round64(M, 181, ae + 16, ae + 16, neg, out);
+  return u_round64(M, 181, ae + 16, ae + 16, neg, out, sg);
 }
 
-CRM_DEV double exp2d_slow(double x, int &unresolved, bool force) {
+CRM_DEV double exp2d_slow(double x, int &unresolved, bool force, int *sg = nullptr) {
   bool hard;
-  double r = exp2d_main(x, CRM_EXP2D_T, hard);
+  double r = exp2d_main(x, CRM_EXP2D_T, hard, sg);
   unresolved = 2;  // the double-double tier (FP64) ran
   double sp;
   if ((!hard && !force) || exp2d_special(x, sp)) return r;
   double out;
-  if (x == rint(x)) return ldexp(1.0, (int)x);  // exact powers of two
-  bool ok = exp2d_exact(x, out);
+  if (x == rint(x)) {  // exact powers of two
+    put_sg(sg, 0);
+    return ldexp(1.0, (int)x);
+  }
+  bool ok = exp2d_exact(x, out, sg);
   unresolved = ok ? 2 : 3;
   return ok ? out : r;
 }
 
-CRM_DEV double logd_slow(double x, int &unresolved, bool force) {
+CRM_DEV double logd_slow(double x, int &unresolved, bool force, int *sg = nullptr) {
   bool hard;
-  double r = logd_main(x, hard);
+  double r = logd_main(x, hard, sg);
   unresolved = 2;  // the double-double tier (FP64) ran
   double sp;
   if ((!hard && !force) || logd_special(x, sp)) return r;
-  if (x == 1.0) return 0.0;
+  if (x == 1.0) {
+    put_sg(sg, 0);
+    return 0.0;
+  }
   double out;
-  bool ok = logd_exact(x, out);
+  bool ok = logd_exact(x, out, sg);
   unresolved = ok ? 2 : 3;
   return ok ? out : r;
 }

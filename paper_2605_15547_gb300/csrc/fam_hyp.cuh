@@ -52,6 +52,28 @@ template <int H> CRM_DEV bool hyp_special(float x, float &r) {
   return nan || x == 0.0f || ax > CRM_TANHF_X_NEXT;
 }
 
+// The sign of f(x) - r for the results of the special branches (0 for exact ones); the
+// first saturation steps (expm1 -1 + 2^-24, tanh +-(1 - 2^-24)) lie on either side of f(x)
+// and are left to the slow path (hard).  Tiny |x| < 2^-25: expm1 x - x = x^2/2 + ... > 0,
+// sinh x - x has the sign of x, tanh x - x the opposite, cosh x - 1 > 0; saturated
+// results are +-inf or +-1 beyond f(x), f(x) -1 above -1.
+template <int H> CRM_DEV int hyp_special_sg(float x, bool &hard) {
+  const float ax = fabsf(x);
+  if (x != x || x == 0.0f || ax == CRM_INF_F) return 0;
+  if (ax < 0x1p-25f) return H == HYP_EXPM1 || H == HYP_COSH ? 1 : (H == HYP_SINH ? sgnf(x) : -sgnf(x));
+  if (H == HYP_EXPM1) {
+    if (x > 0.0f) return -1;  // +inf beyond
+    if (x < CRM_EXPM1F_X_MONE) return 1;  // -1 below
+    hard = true;  // the -1 + 2^-24 step
+    return 0;
+  }
+  if (H == HYP_TANH && ax <= CRM_TANHF_X_ONE) {
+    hard = true;  // the 1 - 2^-24 step
+    return 0;
+  }
+  return H == HYP_COSH ? -1 : -sgnf(x);  // +-inf, or +-1 for tanh
+}
+
 // ------------------------------------------------------------------ plain (FP64) tier
 // Errors (relative to the result): table entries 2^-53 each, amplified by at most
 // (A + B)/|result| <= 46 where A and B do not cancel exactly (j or k nonzero means
@@ -164,7 +186,7 @@ CRM_DEV DFY expm1_df_core(float x, const float4 *T64U) {
 CRM_DEV float pow2f_exact(int k) { return bitsf((uint32_t)(k + 127) << 23); }  // k in [-126, 127]
 CRM_DEV float scale_f(float y, int k) { return bitsf(fbits(y) + ((uint32_t)k << 23)); }
 
-template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard) {
+template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard, int *sg = nullptr) {
   float ax = fabsf(x);
   bool tiny = ax < 0x1p-25f;  // the correctly rounded result is x itself (or 1 for cosh)
   bool sp;                    // NaN, tiny, saturated (results selected on a rare branch)
@@ -223,11 +245,15 @@ template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard) {
   }
   if (__builtin_expect(!sp, 1)) {
     // r unnormalised: |r.lo| < 2^-20 |r.hi| in every branch above
-    float y = scale_f(round_df(r.hi, r.lo, hard), sc);
-    if (H == HYP_SINH || H == HYP_TANH) y = x < 0.0f ? -y : y;
+    float y = scale_f(round_df(r.hi, r.lo, hard, sg), sc);
+    if (H == HYP_SINH || H == HYP_TANH) {
+      if (sg && x < 0.0f) *sg = -*sg;
+      y = x < 0.0f ? -y : y;
+    }
     return y;
   }
   hard = false;
+  if (sg) *sg = hyp_special_sg<H>(x, hard);
   if (x != x) return qnan_of(x);
   if (H == HYP_EXPM1)
     return tiny ? x : (x > 0.0f ? CRM_INF_F : (x < CRM_EXPM1F_X_MONE ? -1.0f : -0x1.fffffep-1f));
@@ -300,7 +326,7 @@ template <int H> CRM_DEV Pair<double> hyp_dd_y(float x) {
 // to e^a's scale.  The error bound is absolute in units of that scale (2^56), so sinh's
 // cancellation near 0 is accounted for by the rounding test itself (|x| >= 2^-25 keeps
 // the result above 2^99 units).
-template <int H> CRM_DEV float hyp_int(float x, bool &hard) {
+template <int H> CRM_DEV float hyp_int(float x, bool &hard, int *sg = nullptr) {
   const uint32_t ax = fbits(x) & 0x7FFFFFFFu;
   const U128 Xa = expq_arg<0>(ax);  // |x| log2 e 2^96; |x| >= 2^-25 here
   const ulonglong2 *T = (const ulonglong2 *)CRM_EXP2I_T;
@@ -315,7 +341,8 @@ template <int H> CRM_DEV float hyp_int(float x, bool &hard) {
     Y2s = {Y2.hi >> (d - 64), 0ull};
   }
   const U128 V = H == HYP_COSH ? add128(Y1, Y2s) : sub128(Y1, Y2s);  // 2 f(a) 2^(124 - k1)
-  const float y = q_round_f(V, ERR, hard, k1 + 1);
+  const float y = q_round_f(V, ERR, hard, k1 + 1, sg);
+  if (H == HYP_SINH && x < 0.0f && sg) *sg = -*sg;
   return (H == HYP_SINH && x < 0.0f) ? -y : y;
 }
 
@@ -343,17 +370,18 @@ CRM_DEV U128 rel_err_84(U128 v) {  // |v| 2^-84 + 16 units
   return {(A.hi >> 20) + 16ull, 0ull};
 }
 
-template <int H> CRM_DEV float hyp_int2(float x, bool &hard) {
+template <int H> CRM_DEV float hyp_int2(float x, bool &hard, int *sg = nullptr) {
   hard = false;
   const float ax = fabsf(x);
   const U128 ONE = {0ull, 1ull << 62};
   const ulonglong2 *T = (const ulonglong2 *)CRM_EXP2I_T;
   if (H == HYP_EXPM1) {
+    put_sg(sg, 1);  // expm1 x > x
     if (ax < 0x1p-25f) return x;
     if (ax < 0x1p-4f) {
       const U128 X = x < 0.0f ? neg128(q_of_f(ax)) : q_of_f(ax);
       const U128 v = expm1_series_q126(X);
-      return q_round_f(v, rel_err_84(v), hard);
+      return q_round_f(v, rel_err_84(v), hard, 0, sg);
     }
     U128 Xa = expq_arg<0>(fbits(ax));
     if (x < 0.0f) Xa = neg128(Xa);
@@ -362,12 +390,13 @@ template <int H> CRM_DEV float hyp_int2(float x, bool &hard) {
     const U128 E57 = {1ull << 57, 0ull};
     if (k >= 0) {
       const U128 W = k <= 124 ? sub128(Y, q_shr(U128{0ull, 1ull << 60}, k)) : Y;  // 2^124 >> k
-      return q_round_f(q_shl(W, 2), E57, hard, k);
+      return q_round_f(q_shl(W, 2), E57, hard, k, sg);
     }
     const U128 Ys = k == -1 ? q_shl(Y, 1) : q_shr(Y, -k - 2);
-    return q_round_f(sub128(Ys, ONE), E57, hard);
+    return q_round_f(sub128(Ys, ONE), E57, hard, 0, sg);
   }
   // tanh
+  put_sg(sg, -sgnf(x));  // tanh x - x has the sign of -x
   if (ax < 0x1p-13f) return x;
   const float a2 = 2.0f * ax;
   U128 t;
@@ -386,20 +415,30 @@ template <int H> CRM_DEV float hyp_int2(float x, bool &hard) {
     t = q_shl(w, es);
     err = {1ull << 58, 0ull};
   }
-  const float y = q_round_f(t, err, hard);
+  const float y = q_round_f(t, err, hard, 0, sg);
+  if (sg && x < 0.0f) *sg = -*sg;
   return x < 0.0f ? -y : y;
 }
 
-template <int H> CRM_DEV float hyp_slow(float x, int &unresolved, bool force) {
+template <int H> CRM_DEV float hyp_slow(float x, int &unresolved, bool force, int *sg = nullptr) {
   bool hard;
   unresolved = false;
   float sp;
-  if (hyp_special<H>(x, sp)) return sp;
+  if (hyp_special<H>(x, sp)) {
+    if (!sg) return sp;
+    bool step = false;  // the first saturation steps are evaluated, not assumed
+    *sg = hyp_special_sg<H>(x, step);
+    if (!step) return sp;
+  }
+  if (sg && (H == HYP_SINH || H == HYP_COSH) && fabsf(x) < 0x1p-25f) {
+    *sg = hyp_special_sg<H>(x, hard);  // x or 1, with the sign of the remainder
+    return H == HYP_SINH ? x : 1.0f;
+  }
   float r;
   if (H == HYP_EXPM1 || H == HYP_TANH) {
-    r = hyp_int2<H>(x, hard);
+    r = hyp_int2<H>(x, hard, sg);
   } else if (fabsf(x) >= 0x1p-25f) {
-    r = hyp_int<H>(x, hard);
+    r = hyp_int<H>(x, hard, sg);
   } else {
     // sinh, cosh of |x| < 2^-25 reach here only under the forced test hook
     r = hyp_plain<H>(x, CRM_EXP2_T16_D, hard);
@@ -407,7 +446,7 @@ template <int H> CRM_DEV float hyp_slow(float x, int &unresolved, bool force) {
   }
   if (!hard && !force) return r;
   Pair<double> y = hyp_dd_y<H>(x);
-  r = round_dd_to_f(y.hi, y.lo, HYP_DD_EPS * fabs(y.hi), hard);
+  r = round_dd_to_f(y.hi, y.lo, HYP_DD_EPS * fabs(y.hi), hard, sg);
   unresolved = hard ? 3 : 2;  // the double-double tier ran
   return r;
 }

@@ -197,7 +197,7 @@ CRM_DEV Pair<float> log_df_core(float us, int eadj, float ul, bool pathA, float 
   return {S.hi, S.lo + (Bl + ql)};
 }
 
-template <int KIND> CRM_DEV float log_df(float x, const float4 *T193, bool &hard) {
+template <int KIND> CRM_DEV float log_df(float x, const float4 *T193, bool &hard, int *sg = nullptr) {
   const bool ok = log_ok<KIND>(x);
   float us = x, ul = 0.0f;
   int eadj = 0;
@@ -213,8 +213,9 @@ template <int KIND> CRM_DEV float log_df(float x, const float4 *T193, bool &hard
     eadj = sub ? -24 : 0;
   }
   Pair<float> y = log_df_core<KIND>(us, eadj, ul, pathA, x, T193);
-  if (__builtin_expect(ok, 1)) return round_df(y.hi, y.lo, hard);
+  if (__builtin_expect(ok, 1)) return round_df(y.hi, y.lo, hard, sg);
   hard = false;  // NaN, zero, negative, infinite (rare: a branch, not selects)
+  put_sg(sg, 0);  // exact results
   return special_log<KIND>(x);
 }
 
@@ -261,9 +262,9 @@ template <int KIND> CRM_DEV Pair<double> log_dd_core(float x) {
   return y;
 }
 
-template <int KIND> CRM_DEV float log_dd(float x, bool &hard) {
+template <int KIND> CRM_DEV float log_dd(float x, bool &hard, int *sg = nullptr) {
   Pair<double> y = log_dd_core<KIND>(x);
-  return round_dd_to_f(y.hi, y.lo, LOG_DD_EPS * fabs(y.hi), hard);
+  return round_dd_to_f(y.hi, y.lo, LOG_DD_EPS * fabs(y.hi), hard, sg);
 }
 
 // ------------------------------------------------------------------ FP64-free middle tier
@@ -277,7 +278,7 @@ template <int KIND> CRM_DEV float log_dd(float x, bool &hard) {
 // 2^-116, is below 2^-70 of the result).  On GB300 the FP64 pipe runs one warp
 // instruction every few dozen cycles, so this tier replaces the FP64 tier for the lanes
 // the double-float test sends to the slow path.
-template <int KIND> CRM_DEV float logq_round(U128 Z, uint64_t err, bool &hard) {
+template <int KIND> CRM_DEV float logq_round(U128 Z, uint64_t err, bool &hard, int *sg = nullptr) {
   const bool neg = (int64_t)Z.hi < 0;
   U128 A = neg ? neg128(Z) : Z;  // |Z| < 2^123
   if (KIND == 1 || KIND == 2) {
@@ -315,6 +316,12 @@ template <int KIND> CRM_DEV float logq_round(U128 Z, uint64_t err, bool &hard) {
   // value mant 2^(sh - 116): exponent field sh - 116 + 23 + 127, the leading bit adds 1
   const uint32_t bits = ((uint32_t)(sh + 33) << 23) + (uint32_t)mant + (up ? 1u : 0u);
   hard = !zero && (near || sh < 64);
+  if (sg) {  // sign of v - y: decided unless the discarded part is within err of 0 or of a unit
+    const U128 unit = s64 == 0 ? U128{0ull, 1ull} : U128{0ull, 1ull << s64};
+    const U128 E = {err, 0ull};
+    hard = !zero && (sh < 64 || le128(rem, E) || le128(sub128(unit, rem), E));
+    *sg = zero ? 0 : ((up != neg) ? -1 : 1);  // |v| below |y| when rounded up; negated for v < 0
+  }
   return zero ? 0.0f : bitsf(bits | (neg ? 0x80000000u : 0u));
 }
 
@@ -327,10 +334,10 @@ CRM_DEV uint64_t f2d_bits_pos(float x) {
   return ((uint64_t)(p + 874) << 52) | (((uint64_t)m << (52 - p)) & 0x000FFFFFFFFFFFFFull);
 }
 
-template <int KIND> CRM_DEV float logf_int(float x, bool &hard) {
+template <int KIND> CRM_DEV float logf_int(float x, bool &hard, int *sg = nullptr) {
   uint64_t err;
   const U128 Z = logz_q116(f2d_bits_pos(x), (const ulonglong2 *)CRM_LOGI_L, CRM_LOGI_R, err);
-  return logq_round<KIND>(Z, err, hard);
+  return logq_round<KIND>(Z, err, hard, sg);
 }
 
 // log1pf of x > -1, x != 0, finite: |x| < 2^-25 gives x (x^2/2 is below half an ulp of x,
@@ -341,12 +348,13 @@ template <int KIND> CRM_DEV float logf_int(float x, bool &hard) {
 // binary32 reciprocal (relative 2^-24: at most 2^40 units, bounded by c 2^-23 + 2 units),
 // the rest is below 2^-105 (2^11 units).  These bounds are far below an ulp of the result
 // (ln x >= 36, ulp 2^98 units): hard lanes stay rare.
-CRM_DEV float log1pf_int(float x, bool &hard) {
+CRM_DEV float log1pf_int(float x, bool &hard, int *sg = nullptr) {
   hard = false;
+  put_sg(sg, -1);  // log1p x < x for x != 0
   if (fabsf(x) < 0x1p-25f) return x;
   uint64_t err;
   const ulonglong2 *LT = (const ulonglong2 *)CRM_LOGI_L;
-  if (x < 0x1p53f) return logq_round<0>(logz_q116(dbits((double)x + 1.0), LT, CRM_LOGI_R, err), err, hard);
+  if (x < 0x1p53f) return logq_round<0>(logz_q116(dbits((double)x + 1.0), LT, CRM_LOGI_R, err), err, hard, sg);
   U128 Z = logz_q116(f2d_bits_pos(x), LT, CRM_LOGI_R, err);
   const uint32_t rb = fbits(1.0f / (x * 0x1p-100f));  // 2^100/x in [2^-28, 2^47], normal
   const uint64_t Mr = (rb & 0x007FFFFFu) | 0x00800000u;
@@ -354,17 +362,40 @@ CRM_DEV float log1pf_int(float x, bool &hard) {
   const uint64_t c = s >= 0 ? Mr << s : Mr >> (-s);
   Z = add128_64(Z, c);
   err += (c >> 23) + 2ull + 2048ull;
-  return logq_round<0>(Z, err, hard);
+  return logq_round<0>(Z, err, hard, sg);
 }
 
 // Slow path: the FP64-free tier, then double-double.
-template <int KIND> CRM_DEV float log_slow(float x, int &unresolved, bool force) {
+// With sg: the exact results log2(2^k) = k and log10(10^k) = k (k = 1..10) are returned
+// directly (an error bound cannot decide a result that is a binary32 number).
+template <int KIND> CRM_DEV float log_slow(float x, int &unresolved, bool force, int *sg = nullptr) {
   bool hard;
   unresolved = false;
-  if (!log_ok<KIND>(x)) return special_log<KIND>(x);
-  float r = KIND == 3 ? log1pf_int(x, hard) : logf_int<KIND>(x, hard);
+  if (!log_ok<KIND>(x)) {
+    put_sg(sg, 0);
+    return special_log<KIND>(x);
+  }
+  float r = KIND == 3 ? log1pf_int(x, hard, sg) : logf_int<KIND>(x, hard, sg);
   if (!hard && !force) return r;
-  r = log_dd<KIND>(x, hard);
+  if (sg && KIND == 1) {
+    const uint32_t b = fbits(x);
+    const uint32_t m = b & 0x007FFFFFu, E = b >> 23;
+    if ((E != 0 && m == 0) || (E == 0 && (m & (m - 1u)) == 0)) {  // a power of two
+      *sg = 0;
+      return E != 0 ? (float)((int)E - 127) : (float)(31 - __clz(m) - 149);
+    }
+  }
+  if (sg && KIND == 2) {
+    float p = 1.0f;
+    for (int k = 1; k <= 10; k++) {
+      p *= 10.0f;  // exact
+      if (x == p) {
+        *sg = 0;
+        return (float)k;
+      }
+    }
+  }
+  r = log_dd<KIND>(x, hard, sg);
   unresolved = hard ? 3 : 2;  // the double-double tier ran
   return r;
 }

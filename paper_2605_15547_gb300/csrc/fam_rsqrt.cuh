@@ -50,7 +50,7 @@ CRM_DEV float rsqrt_plain(float x, bool &hard) {
 // (5/16) e^3 < 2^-61, the residual is good to 2^-48 absolute, the correction product to
 // 2^-24 of itself (2^-45 of y): relative error < 2^-44.5, inside the rounding test's
 // 2^-37; the pair (y0, c), |c| < 2^-21 y0, goes to round_df unnormalised.
-CRM_DEV float rsqrt_df(float x, bool &hard) {
+CRM_DEV float rsqrt_df(float x, bool &hard, int *sg = nullptr) {
   float r;
   bool sp = rsqrt_special(x, r);
   bool sub = x < 0x1p-126f, big = x >= 0x1p64f;  // keep y0^2 and its error normal
@@ -64,10 +64,11 @@ CRM_DEV float rsqrt_df(float x, bool &hard) {
   float corr = fma_(e, 0.375f, 0.5f) * e;
   float c = y0 * corr;
   bool h;
-  const float yh = round_df(y0, c, h);
+  const float yh = round_df(y0, c, h, sg);
   // special inputs (x <= 0, NaN, +inf) by selects: they are common in real data (half of
   // a symmetric input range), so a branch would diverge in most warps
   hard = !sp && h;
+  if (sg && sp) *sg = 0;  // +-inf, NaN, +0: exact
   float out = sub ? yh * 0x1p12f : (big ? yh * 0x1p-32f : yh);
   return sp ? r : out;
 }
@@ -92,16 +93,39 @@ CRM_DEV bool rsqrt_mid_above(uint32_t xb, uint32_t ab) {
   return !le128(prod, P < 64 ? U128{1ull << P, 0ull} : U128{0ull, 1ull << (P - 64)});
 }
 
-CRM_DEV float rsqrt_slow(float x, int &unresolved, bool force) {
+// The sign of 1/sqrt(x) - y for a positive binary32 y (x scaled as above): the sign of
+// 1 - x y^2, exactly, from Mx My^2 (< 2^72) against a power of two; 0 when x = 4^k / y^2.
+CRM_DEV int rsqrt_cmp(uint32_t xb, uint32_t yb) {
+  const uint64_t Mx = (xb & 0x007FFFFFu) | 0x00800000u;
+  const uint64_t My = (yb & 0x007FFFFFu) | 0x00800000u;
+  const int P = 450 - (int)(xb >> 23) - 2 * (int)(yb >> 23);  // x y^2 = Mx My^2 2^-P
+  if (P < 0) return -1;
+  if (P >= 128) return 1;
+  const U128 prod = mul64w(Mx * My, My);
+  const U128 one = P < 64 ? U128{1ull << P, 0ull} : U128{0ull, 1ull << (P - 64)};
+  if (prod.hi == one.hi && prod.lo == one.lo) return 0;
+  return le128(prod, one) ? 1 : -1;
+}
+
+CRM_DEV float rsqrt_slow(float x, int &unresolved, bool force, int *sg = nullptr) {
   (void)force;  // the exact decision is the only tier
   unresolved = false;
   float sp;
-  if (rsqrt_special(x, sp)) return sp;
+  if (rsqrt_special(x, sp)) {
+    put_sg(sg, 0);
+    return sp;
+  }
   const bool sub = x < 0x1p-126f, big = x >= 0x1p64f;
   const float xs = sub ? x * 0x1p24f : (big ? x * 0x1p-64f : x);  // normal, in [2^-125, 2^64)
   bool h;
   const uint32_t xb = fbits(xs), yb = fbits(rsqrt_df(xs, h));
-  const uint32_t rb = !rsqrt_mid_above(xb, yb) ? yb + 1u : (rsqrt_mid_above(xb, yb - 1u) ? yb - 1u : yb);
+  uint32_t rb;
+  if (sg) {  // the double-float result is within a fraction of an ulp: its exact side
+    rb = yb;
+    *sg = rsqrt_cmp(xb, yb);
+  } else {
+    rb = !rsqrt_mid_above(xb, yb) ? yb + 1u : (rsqrt_mid_above(xb, yb - 1u) ? yb - 1u : yb);
+  }
   const float r = bitsf(rb);
   return sub ? r * 0x1p12f : (big ? r * 0x1p-32f : r);
 }

@@ -308,8 +308,11 @@ CRM_DEV uint32_t trig_cos_sign(int q) { return ((uint32_t)(q + 1) << 30) & 0x800
 // The pairs are rounded before the quadrant rotation: round-to-nearest and round_df's
 // test are symmetric under negation, so rounding A and B and then swapping and negating
 // the floats gives the same bits as rotating the pairs first.
+// With sg (two entries for sincosf): the sign of f(x) - y for each result, turned with the
+// result's sign; the special results are exact (NaN, +-0).
 template <int KIND>
-CRM_DEV void trig_df(float x, const uint4 *PW, const float4 *SC, const float2 *TT, float *y, bool &hard) {
+CRM_DEV void trig_df(float x, const uint4 *PW, const float4 *SC, const float2 *TT, float *y, bool &hard,
+                     int *sg = nullptr) {
   const bool sp = !(fabsf(x) < CRM_INF_F);  // NaN or infinite
   if (KIND == TRIG_TAN) {
     Pair<float> t, D;
@@ -320,17 +323,19 @@ CRM_DEV void trig_df(float x, const uint4 *PW, const float4 *SC, const float2 *T
     const bool odd = (N7 & 32) != 0;
     const Pair<float> q = df_div_raw(odd ? D : N, odd ? N : D);
     bool h;
-    const float yt = round_df(q.hi, q.lo, h);
+    const float yt = round_df(q.hi, q.lo, h, sg);
     if (__builtin_expect(sp, 0)) {
       hard = false;
+      put_sg(sg, 0);
       y[0] = x != x ? qnan_of(x) : CRM_QNAN_F;
       return;
     }
     // negative in odd quadrants (-cot), and odd in x
-    const uint32_t sg = (((uint32_t)N7 << 26) ^ fbits(x)) & 0x80000000u;
+    const uint32_t sgb = (((uint32_t)N7 << 26) ^ fbits(x)) & 0x80000000u;
     const bool zero = x == 0.0f;  // tan(+-0) = +-0
     hard = !zero && (tiny || h);
-    y[0] = zero ? x : bitsf(fbits(yt) ^ sg);
+    if (sg) *sg = zero ? 0 : (sgb ? -*sg : *sg);
+    y[0] = zero ? x : bitsf(fbits(yt) ^ sgb);
     return;
   }
   TrigF R = trig_df_core<KIND>(sp ? 1.0f : x, PW, SC);
@@ -339,25 +344,40 @@ CRM_DEV void trig_df(float x, const uint4 *PW, const float4 *SC, const float2 *T
     const float r = x != x ? qnan_of(x) : CRM_QNAN_F;
     y[0] = r;
     if (KIND == TRIG_SINCOS) y[1] = r;
+    if (sg) {
+      sg[0] = 0;
+      if (KIND == TRIG_SINCOS) sg[1] = 0;
+    }
     return;
   }
   const bool zero = x == 0.0f;  // sin/tan(+-0) = +-0
   const bool odd = (R.q & 1) != 0;
   bool ha, hb;
+  int sa = 0, sb = 0;
   // sin and cos alone: R.A is already the term the quadrant needs
-  const float ya = round_df(R.A.hi, R.A.lo, ha);
+  const float ya = round_df(R.A.hi, R.A.lo, ha, sg ? &sa : nullptr);
   if (KIND == TRIG_SIN) {
     hard = !zero && (R.tiny || ha);
-    y[0] = zero ? x : bitsf(fbits(ya) ^ trig_sin_sign(R.q, x));
+    const uint32_t s1 = trig_sin_sign(R.q, x);
+    if (sg) sg[0] = zero ? 0 : (s1 ? -sa : sa);
+    y[0] = zero ? x : bitsf(fbits(ya) ^ s1);
   } else if (KIND == TRIG_COS) {
     hard = R.tiny || ha;
-    y[0] = bitsf(fbits(ya) ^ trig_cos_sign(R.q));
+    const uint32_t c1 = trig_cos_sign(R.q);
+    if (sg) sg[0] = c1 ? -sa : sa;
+    y[0] = bitsf(fbits(ya) ^ c1);
   } else {
-    const float yb = round_df(R.B.hi, R.B.lo, hb);
+    const float yb = round_df(R.B.hi, R.B.lo, hb, sg ? &sb : nullptr);
     hard = R.tiny || ha || hb;  // sin takes one of A, B and cos the other
     const float s0 = odd ? yb : ya, c0 = odd ? ya : yb;
-    y[0] = zero ? x : bitsf(fbits(s0) ^ trig_sin_sign(R.q, x));
-    y[1] = bitsf(fbits(c0) ^ trig_cos_sign(R.q));
+    const uint32_t s1 = trig_sin_sign(R.q, x), c1 = trig_cos_sign(R.q);
+    if (sg) {
+      const int ss = odd ? sb : sa, cs = odd ? sa : sb;
+      sg[0] = zero ? 0 : (s1 ? -ss : ss);
+      sg[1] = c1 ? -cs : cs;
+    }
+    y[0] = zero ? x : bitsf(fbits(s0) ^ s1);
+    y[1] = bitsf(fbits(c0) ^ c1);
   }
 }
 
@@ -418,15 +438,22 @@ CRM_DEV void trig_dd_core(float x, Pair<double> &A, Pair<double> &B, int &q) {
 // units) the error stays below 2^7 units of 2^-126, far inside half an ulp except for
 // results within ~2^-119 of a midpoint (|sin|, |cos| >= 2^-35 for a binary32 x: those lanes
 // continue to double-double); tan divides the two in fixed point (q_div).
-template <int KIND> CRM_DEV void trig_int(float x, float *y, bool &hard) {
+template <int KIND> CRM_DEV void trig_int(float x, float *y, bool &hard, int *sg = nullptr) {
   const float ax = fabsf(x);
   hard = false;
   if (ax < 0x1p-12f) {  // RN(sin x) = x and RN(cos x) = 1: x^3/6 and x^2/2 are below half an ulp
+    // sin x - x has the sign of -x, tan x - x that of x, cos x - 1 is negative (x != 0)
+    const int ssx = KIND == TRIG_TAN ? sgnf(x) : -sgnf(x), scx = x == 0.0f ? 0 : -1;
     if (KIND == TRIG_COS) {
       y[0] = 1.0f;
+      put_sg(sg, scx);
     } else {
       y[0] = x;
-      if (KIND == TRIG_SINCOS) y[1] = 1.0f;
+      put_sg(sg, ssx);
+      if (KIND == TRIG_SINCOS) {
+        y[1] = 1.0f;
+        if (sg) sg[1] = scx;
+      }
     }
     return;
   }
@@ -476,52 +503,78 @@ template <int KIND> CRM_DEV void trig_int(float x, float *y, bool &hard) {
     int es;
     const U128 w = q_div(N, D, es);
     const U128 aw = q_neg(w) ? neg128(w) : w;
-    const float yt = q_round_f(w, U128{(aw.hi >> 16) + 1024ull, 0ull}, hard, es);
-    y[0] = bitsf(fbits(yt) ^ ((((uint32_t)q << 31)) ^ (fbits(x) & 0x80000000u)));
+    const float yt = q_round_f(w, U128{(aw.hi >> 16) + 1024ull, 0ull}, hard, es, sg);
+    const uint32_t tb = (((uint32_t)q << 31)) ^ (fbits(x) & 0x80000000u);
+    if (sg && tb) *sg = -*sg;
+    y[0] = bitsf(fbits(yt) ^ tb);
     return;
   }
   bool ha = false, hb = false;
   float ya = 0.0f, yb = 0.0f;
+  int sa = 0, sb = 0;
   // sin of the reduced angle is A when q is even, B when odd; cos the other one
   const bool needA = KIND == TRIG_SINCOS || (KIND == TRIG_SIN) != odd;
   const bool needB = KIND == TRIG_SINCOS || (KIND == TRIG_SIN) == odd;
-  if (needA) ya = q_round_f(add128(add128(S, q_mul(S, cm)), q_mul(C, st)), ERR, ha);
-  if (needB) yb = q_round_f(sub128(add128(C, q_mul(C, cm)), q_mul(S, st)), ERR, hb);
+  if (needA) ya = q_round_f(add128(add128(S, q_mul(S, cm)), q_mul(C, st)), ERR, ha, 0, sg ? &sa : nullptr);
+  if (needB) yb = q_round_f(sub128(add128(C, q_mul(C, cm)), q_mul(S, st)), ERR, hb, 0, sg ? &sb : nullptr);
   hard = ha || hb;
   const float s0 = odd ? yb : ya, c0 = odd ? ya : yb;
+  const int ss = odd ? sb : sa, cs = odd ? sa : sb;
   if (KIND == TRIG_COS) {
-    y[0] = bitsf(fbits(c0) ^ trig_cos_sign(q));
+    const uint32_t c1 = trig_cos_sign(q);
+    if (sg) sg[0] = c1 ? -cs : cs;
+    y[0] = bitsf(fbits(c0) ^ c1);
   } else {
-    y[0] = bitsf(fbits(s0) ^ trig_sin_sign(q, x));
-    if (KIND == TRIG_SINCOS) y[1] = bitsf(fbits(c0) ^ trig_cos_sign(q));
+    const uint32_t s1 = trig_sin_sign(q, x);
+    if (sg) sg[0] = s1 ? -ss : ss;
+    y[0] = bitsf(fbits(s0) ^ s1);
+    if (KIND == TRIG_SINCOS) {
+      const uint32_t c1 = trig_cos_sign(q);
+      if (sg) sg[1] = c1 ? -cs : cs;
+      y[1] = bitsf(fbits(c0) ^ c1);
+    }
   }
 }
 
 // Slow path: the FP64-free tier, then double-double.
-template <int KIND> CRM_DEV void trig_slow(float x, float *y, int &unresolved, bool force) {
+template <int KIND> CRM_DEV void trig_slow(float x, float *y, int &unresolved, bool force, int *sg = nullptr) {
   bool hard;
   unresolved = false;
   float sp;
   if (trig_special(x, sp)) {
     y[0] = sp;
     if (KIND == TRIG_SINCOS) y[1] = sp;
+    if (sg) {
+      sg[0] = 0;
+      if (KIND == TRIG_SINCOS) sg[1] = 0;
+    }
     return;
   }
-  trig_int<KIND>(x, y, hard);
+  trig_int<KIND>(x, y, hard, sg);
   if ((!hard && !force) || trig_special(x, sp)) return;
+  if (sg && fabsf(x) < 0x1p-12f) return;  // the tiny range's results and signs are exact statements
   Pair<double> A, B, sn, cs;
   int q;
   trig_dd_core(x, A, B, q);
   trig_rotate<Pair<double>>(KIND, x, q, A, B, sn, cs);
   bool h0 = false, h1 = false;
+  int s0 = 0, s1 = 0;
+  int *p0 = sg ? &s0 : nullptr, *p1 = sg ? &s1 : nullptr;
   if (KIND == TRIG_TAN) {
     Pair<double> t = dd_div(sn, cs);
-    y[0] = round_dd_to_f(t.hi, t.lo, TRIG_DD_EPS * fabs(t.hi), h0);
+    y[0] = round_dd_to_f(t.hi, t.lo, TRIG_DD_EPS * fabs(t.hi), h0, p0);
   } else {
-    if (KIND != TRIG_COS) y[0] = round_dd_to_f(sn.hi, sn.lo, TRIG_DD_EPS * fabs(sn.hi), h0);
-    float c = round_dd_to_f(cs.hi, cs.lo, TRIG_DD_EPS * fabs(cs.hi), h1);
-    if (KIND == TRIG_COS) y[0] = c;
+    if (KIND != TRIG_COS) y[0] = round_dd_to_f(sn.hi, sn.lo, TRIG_DD_EPS * fabs(sn.hi), h0, p0);
+    float c = round_dd_to_f(cs.hi, cs.lo, TRIG_DD_EPS * fabs(cs.hi), h1, p1);
+    if (KIND == TRIG_COS) {
+      y[0] = c;
+      s0 = s1;
+    }
     if (KIND == TRIG_SINCOS) y[1] = c;
+  }
+  if (sg) {
+    sg[0] = s0;
+    if (KIND == TRIG_SINCOS) sg[1] = s1;
   }
   if (x == 0.0f && KIND != TRIG_COS) y[0] = x;
   unresolved = (h0 || h1) ? 3 : 2;  // the double-double tier ran

@@ -127,6 +127,13 @@ for i in range(64):
     T = mp.power(2, mp.mpf(i) / 64)
     t64u += split(T, f, 2) + split(T * LN2, f, 2)
 arr_f("CRM_EXP2_T64U_DF", t64u, "(2^(i/64) hi, lo, 2^(i/64) ln2 hi, lo) floats (double-float form)")
+# 16-entry float4 table of the same layout: the register-resident variant (lane l holds
+# entry l mod 16, read by warp shuffles)
+t16u = []
+for i in range(16):
+    T = mp.power(2, mp.mpf(i) / 16)
+    t16u += split(T, f, 2) + split(T * LN2, f, 2)
+arr_f("CRM_EXP2_T16U_DF", t16u, "(2^(i/16) hi, lo, 2^(i/16) ln2 hi, lo) floats (register-table variant)")
 emit()
 
 
@@ -177,7 +184,7 @@ arr_d("CRM_EXP2_TAYLOR_DD", ddc, "(ln 2)^k / k!, k = 0..15, as (hi, lo) doubles"
 a1 = split(coef[1], f, 2)
 const_f("CRM_EXP2_A1_HI_F", a1[0], "ln 2 (float hi)")
 const_f("CRM_EXP2_A1_LO_F", a1[1], "ln 2 (float lo)")
-for k in (2, 3, 4, 5):
+for k in (2, 3, 4, 5, 6):
     const_f(f"CRM_EXP2_A{k}_F", f(coef[k]), f"(ln 2)^{k}/{k}!")
 a2 = split(coef[2], f, 2)
 const_f("CRM_EXP2_A2_HI_F", a2[0], "(ln 2)^2/2 (float hi)")

@@ -72,6 +72,24 @@ def test_exhaustive_against_oracle_digests(func, weights):
     assert st["fp64_total"] == 0, f"{func}: {st['fp64_total']} lanes ran the FP64 tier"
 
 
+@pytest.mark.parametrize("func", ["expf", "exp2f", "exp10f"])
+def test_exhaustive_register_table_variant(func, weights):
+    """the exp family's 16-entry register-table evaluator (warp shuffles instead of the
+    64-entry shared-memory table) against the oracle on all 2^32 inputs"""
+    ref = EH.read_fixture(os.path.join(GOLDEN, func + ".txt"))
+    w1, w2 = weights
+    y = torch.empty(EH.CHUNK, dtype=torch.float32, device="cuda")
+    v = next(i for i in range(crm._lib.NUM_VARIANTS) if crm.variant_info(i)["reg_table"])
+    crm.set_variant(func, v, form="df")
+    try:
+        bad = [c for c in sorted(ref)
+               if (crm.eval_into(func, chunk_input(c), y, form="df") or
+                   EH.digest_torch(y.view(torch.int32), w1, w2)) != ref[c]]
+    finally:
+        crm.set_variant(func, 1, form="df")
+    assert not bad, f"{func} (register table): chunks {bad[:8]} differ from the oracle"
+
+
 @pytest.mark.parametrize("func", SINGLE)
 def test_exhaustive_forms_agree(func):
     a = torch.empty(EH.CHUNK, dtype=torch.float32, device="cuda")

@@ -1848,6 +1848,132 @@ int crm_oracle_f64_hardness(int func, uint64_t xb, double *h) {
   return ORC_OK;
 }
 
+/* ---- complex functions built from the real ones (the paper's application of Sec. III.A:
+   cexpf, clogf and csinf over real and imaginary parts in [-40, 40]) ----
+   cexp(x + iy) = e^x cos y + i e^x sin y;  csin(x + iy) = sin x cosh y + i cos x sinh y;
+   clog(z) = log|z| + i atan2(y, x) with log|z| = log(x^2 + y^2) / 2.  Each component is the
+   exact value rounded to nearest binary32, by the Ziv loop on its interval.  Finite inputs;
+   clog also needs z != 0. */
+enum { CX_EXP = 0, CX_LOG = 1, CX_SIN = 2 };
+
+/* f(x) for a finite binary32 x as an interval times 2^E (zero: 0 or 1 exactly) */
+static void cx_real(int kind, uint32_t xb, int n, res_t *R) {
+  dec_t d = dec32(xb);
+  R->E = 0;
+  if (d.cls == CL_ZERO) {
+    iv_set_i(&R->v, (kind == K_SIN || kind == K_SINH) ? 0 : 1, n);
+    return;
+  }
+  evaluate(kind, &d, n, R);
+}
+
+static void cx_prod(int ka, uint32_t a, int kb, uint32_t b, int n, res_t *P) {
+  res_t A, B;
+  cx_real(ka, a, n, &A);
+  cx_real(kb, b, n, &B);
+  iv_mul(&P->v, &A.v, &B.v, n);
+  P->E = A.E + B.E;
+}
+
+/* log|z| = (2 e ln 2 + log S) / 2 with x^2 + y^2 = S 2^(2e), S = Ma^2 + Mb^2 2^(2(eb - ea))
+   (a the larger of |x|, |y| = Ma 2^ea); S's second term is truncated to the fraction bits,
+   and log is evaluated at both ends of S's interval */
+static void cx_logabs(uint32_t xr, uint32_t xi, int n, res_t *R) {
+  dec_t a = dec32(xr & 0x7FFFFFFFu), b = dec32(xi & 0x7FFFFFFFu);
+  if (approx(&b) > approx(&a)) {
+    dec_t t = a;
+    a = b;
+    b = t;
+  }
+  const consts_t *C = get_consts(n);
+  iv_t S, sb;
+  iv_set_scaled(&S, 0, a.M * a.M, 0, n);
+  if (b.cls != CL_ZERO) {
+    iv_set_scaled(&sb, 0, b.M * b.M, 2 * (b.e - a.e), n);
+    iv_add(&S, &S, &sb, n);
+  }
+  int64_t K1, K2;
+  iv_t A1, A2, t;
+  log_parts(S.lo, n, &K1, &A1);
+  log_parts(S.hi, n, &K2, &A2);
+  iv_t L1, L2;
+  iv_mul_i(&t, &C->ln2, K1 + 2 * a.e, n);
+  iv_add(&L1, &t, &A1, n);
+  iv_mul_i(&t, &C->ln2, K2 + 2 * a.e, n);
+  iv_add(&L2, &t, &A2, n);
+  memcpy(R->v.lo, L1.lo, 8 * (size_t)n);
+  memcpy(R->v.hi, L2.hi, 8 * (size_t)n);
+  iv_shr(&R->v, &R->v, 1, n);
+  R->E = 0;
+}
+
+/* atan2(y, x): theta = atan(|y| / |x|) (pi/2 - atan(|x| / |y|) when |y| > |x|), pi - theta for
+   x < 0, negated for y < 0; the ratio's exponent difference is applied as a shift */
+static void cx_arg(uint32_t xr, uint32_t xi, int n, res_t *R) {
+  dec_t a = dec32(xr & 0x7FFFFFFFu), b = dec32(xi & 0x7FFFFFFFu);
+  const consts_t *C = get_consts(n);
+  iv_t th;
+  if (a.cls == CL_ZERO) {
+    th = C->pio2;
+  } else if (b.cls == CL_ZERO) {
+    iv_set_i(&th, 0, n);
+  } else {
+    const int big = approx(&b) > approx(&a);
+    const dec_t *p = big ? &a : &b, *q = big ? &b : &a; /* ratio p / q <= 1 */
+    iv_t mp, mq, r;
+    iv_set_i(&mp, (int64_t)p->M, n);
+    iv_set_i(&mq, (int64_t)q->M, n);
+    iv_div(&r, &mp, &mq, n);
+    const int64_t sh = p->e - q->e; /* <= 0, or small */
+    if (sh >= 0)
+      iv_shl(&r, &r, sh, n);
+    else
+      iv_shr(&r, &r, -sh, n);
+    iv_atan(&th, &r, n);
+    if (big) iv_sub(&th, &C->pio2, &th, n);
+  }
+  if (xr >> 31) iv_sub(&th, &C->pi, &th, n);
+  if (xi >> 31) iv_neg(&th, &th, n);
+  R->v = th;
+  R->E = 0;
+}
+
+int crm_oracle_complex(int which, uint32_t xr, uint32_t xi, uint32_t out[2]) {
+  if (which < CX_EXP || which > CX_SIN) return ORC_ERR_FUNC;
+  for (int comp = 0; comp < 2; comp++) {
+    int lvl;
+    for (lvl = 0; lvl < NLEVELS; lvl++) {
+      const int n = LEVEL_LIMBS[lvl];
+      res_t R;
+      g_fail = 0;
+      if (which == CX_EXP)
+        cx_prod(K_EXP, xr, comp ? K_SIN : K_COS, xi, n, &R);
+      else if (which == CX_SIN)
+        cx_prod(comp ? K_COS : K_SIN, xr, comp ? K_SINH : K_COSH, xi, n, &R);
+      else if (comp == 0)
+        cx_logabs(xr, xi, n, &R);
+      else
+        cx_arg(xr, xi, n, &R);
+      if (g_fail) continue;
+      uint64_t lo = round_fixed(R.v.lo, n, R.E, &FMT32, ORC_RN), hi = round_fixed(R.v.hi, n, R.E, &FMT32, ORC_RN);
+      if (lo == hi) {
+        out[comp] = (uint32_t)lo;
+        break;
+      }
+    }
+    if (lvl == NLEVELS) return ORC_ERR_CAP;
+  }
+  return ORC_OK;
+}
+
+int crm_oracle_complex_array(int which, const uint32_t *in, uint32_t *out, uint64_t n) {
+  for (uint64_t i = 0; i < n; i++) {
+    int st = crm_oracle_complex(which, in[2 * i], in[2 * i + 1], out + 2 * i);
+    if (st) return st;
+  }
+  return ORC_OK;
+}
+
 /* ---- threaded array drivers ---- */
 typedef struct {
   int func, is64, mode, hardness;

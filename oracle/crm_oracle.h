@@ -67,6 +67,14 @@ int crm_oracle_f64_array_rm(int func, const uint64_t *in, uint64_t *out, uint64_
 int crm_oracle_f64_hardness(int func, uint64_t x, double *h);
 int crm_oracle_f64_hardness_array(int func, const uint64_t *in, double *out, uint64_t n, int nthreads);
 
+/* Complex functions built from the real ones, the paper's second application (Sec. III.A):
+   which 0: cexp(x + iy) = e^x cos y + i e^x sin y; 1: clog(z) = log|z| + i atan2(y, x);
+   2: csin(x + iy) = sin x cosh y + i cos x sinh y.  Each component of the exact value is
+   rounded to nearest binary32 (out[0] real, out[1] imaginary).  Finite inputs (clog: z != 0).
+   The array form takes n interleaved (re, im) pairs. */
+int crm_oracle_complex(int which, uint32_t xr, uint32_t xi, uint32_t out[2]);
+int crm_oracle_complex_array(int which, const uint32_t *in, uint32_t *out, uint64_t n);
+
 /* Diagnostics for the oracle's own tests: the Ziv level (0 = first precision) at which
    the last call on this thread finished, and the constants as scaled integers. */
 int crm_oracle_last_level(void);

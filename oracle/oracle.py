@@ -68,6 +68,8 @@ def _load():
                                                  ctypes.c_uint64, ctypes.c_int]
             lib.crm_oracle_f64_hardness_array.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                           ctypes.c_uint64, ctypes.c_int]
+            lib.crm_oracle_complex_array.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                     ctypes.c_uint64]
             lib.crm_oracle_constant.argtypes = [ctypes.c_int, ctypes.c_int, u64p, u64p]
             lib.crm_oracle_constant_alt.argtypes = [ctypes.c_int, ctypes.c_int, u64p, u64p]
             lib.crm_oracle_test_divmod.argtypes = [u32p, ctypes.c_int, u32p, ctypes.c_int, u32p]
@@ -140,6 +142,23 @@ def f64_hardness(func, xbits: np.ndarray, nthreads: int = 0) -> np.ndarray:
         st = lib.crm_oracle_f64_hardness_array(fid, x.ctypes.data, out.ctypes.data, x.size, nthreads)
         if st:
             raise OracleError(f"oracle status {st} for {FUNCS[fid]} hardness")
+    return out
+
+
+COMPLEX = {"cexpf": 0, "clogf": 1, "csinf": 2}
+
+
+def eval_complex(func, zbits: np.ndarray) -> np.ndarray:
+    """Each component of cexp, clog or csin ("cexpf", "clogf", "csinf") of the binary32
+    complex numbers zbits (uint32, interleaved re, im), rounded to nearest: uint32 bits,
+    interleaved the same way."""
+    lib = _load()
+    z = np.ascontiguousarray(zbits, dtype=np.uint32).ravel()
+    out = np.zeros(z.size, dtype=np.uint32)
+    if z.size:
+        st = lib.crm_oracle_complex_array(COMPLEX[func], z.ctypes.data, out.ctypes.data, z.size // 2)
+        if st:
+            raise OracleError(f"oracle status {st} for {func}")
     return out
 
 

@@ -219,7 +219,12 @@ CRM_DEV void put_sg(int *sg, int v) {
 CRM_DEV float round_dd_to_f(double s, double t, double e, bool &hard, int *sg = nullptr) {
   if (sg) {  // c = RN32(s) and the sign of v - c, decided unless |(s - c) + t| <= e
     const float c = __double2float_rn(s);
-    const double d = isinf(c) ? (c > 0.0f ? -1.0 : 1.0) : (s - (double)c) + t;  // s - c exact
+    if (isinf(c)) {  // beyond the binary32 range: the finite value lies inside the infinity
+      hard = false;
+      *sg = c > 0.0f ? -1 : 1;
+      return c;
+    }
+    const double d = (s - (double)c) + t;  // s - c exact
     hard = !(fabs(d) > e);
     *sg = d > 0.0 ? 1 : -1;
     return c;

@@ -403,6 +403,9 @@ template <int KIND> CRM_DEV float exp_slow(float x, int &unresolved, bool force,
   bool hard;
   float r = expf_int<KIND>(x, hard, sg);
   if (!hard && !force) return r;
+  // a sign stated by the first tier's shortcut (|x| < 2^-60: b^x - 1 has the sign of x) is
+  // final: a deeper tier cannot decide a result that close to 1
+  if (sg && !hard && fabsf(x) < 0x1p-60f) return r;
   if (sg && x == rintf(x)) {
     if (KIND == 1 && x >= -149.0f) {
       *sg = 0;

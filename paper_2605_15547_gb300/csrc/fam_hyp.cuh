@@ -445,6 +445,11 @@ template <int H> CRM_DEV float hyp_slow(float x, int &unresolved, bool force, in
     unresolved = 2;  // an FP64 tier ran
   }
   if (!hard && !force) return r;
+  // the shortcuts of the first tier (expm1 x > x below 2^-25, tanh x - x of the sign of -x
+  // below 2^-13) state the sign exactly
+  if (sg && !hard &&
+      ((H == HYP_EXPM1 && fabsf(x) < 0x1p-25f) || (H == HYP_TANH && fabsf(x) < 0x1p-13f)))
+    return r;
   Pair<double> y = hyp_dd_y<H>(x);
   r = round_dd_to_f(y.hi, y.lo, HYP_DD_EPS * fabs(y.hi), hard, sg);
   unresolved = hard ? 3 : 2;  // the double-double tier ran

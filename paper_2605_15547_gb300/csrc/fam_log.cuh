@@ -377,6 +377,8 @@ template <int KIND> CRM_DEV float log_slow(float x, int &unresolved, bool force,
   }
   float r = KIND == 3 ? log1pf_int(x, hard, sg) : logf_int<KIND>(x, hard, sg);
   if (!hard && !force) return r;
+  // exact zero (x = 1) and log1p's shortcut (|x| < 2^-25: log1p x < x) are final
+  if (sg && !hard && (*sg == 0 || (KIND == 3 && fabsf(x) < 0x1p-25f))) return r;
   if (sg && KIND == 1) {
     const uint32_t b = fbits(x);
     const uint32_t m = b & 0x007FFFFFu, E = b >> 23;

@@ -380,6 +380,69 @@ def measure_set(args, crm, torch, dev, workload, reps=3):
     return out
 
 
+def time_fn(torch, fn, reps, stream):
+    """Device time per call of fn (CUDA events, after one untimed call)."""
+    fn()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(reps):
+        fn()
+    e.record(stream)
+    e.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def measure_modes(args, crm, torch, dev, reps=3):
+    """Directed rounding and the 16-bit formats (crm_eval_rm): expf, logf, sinf on 2^26
+    domain inputs (binary32 in RD/RU/RZ; binary16 and bfloat16 in RN), against the same
+    call in round-to-nearest binary32."""
+    n = (1 << 26) >> args.scale
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device=dev)
+    out = {"config": f"expf, logf, sinf x 2^{26 - args.scale} domain bit patterns + 1% specials"}
+    for f in ("expf", "logf", "sinf"):
+        gen.manual_seed(W.seed_for(2, f))
+        x = W.domain_bits_device(f, n, gen, device=dev)
+        y = torch.empty_like(x)
+        row = {"rn_f32": n / (time_fn(torch, lambda: crm.eval_into(f, x, y), reps, stream) / 1e3) / 1e9}
+        for m in ("rd", "ru", "rz"):
+            row[m + "_f32"] = n / (time_fn(torch, lambda: crm.eval_rm(f, x, m, out=y), reps, stream) / 1e3) / 1e9
+        for dt, nm in ((torch.float16, "f16"), (torch.bfloat16, "bf16")):
+            xh = x.to(dt)
+            yh = torch.empty_like(xh)
+            row["rn_" + nm] = n / (time_fn(torch, lambda: crm.eval_rm(f, xh, "rn", out=yh), reps, stream) / 1e3) / 1e9
+        out[f] = row
+        del x, y
+    return out
+
+
+def measure_apps(args, crm, torch, dev, reps=3):
+    """The paper's applications: complex expf / logf / sinf on 2^26 complex inputs uniform in
+    [-40, 40]^2 (16 bytes per element), and spectral interpolation by a brute-force DFT of
+    N = 2^14 samples at M = 2^14 non-integer frequencies (2^28 sine-cosine terms per call)."""
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.seed_for(6, 0))
+    n = (1 << 26) >> args.scale
+    z = ((torch.rand(2 * n, generator=gen, device=dev, dtype=torch.float64) * 80.0 - 40.0)
+         .to(torch.float32).view(torch.complex64))
+    w = torch.empty_like(z)
+    peak, _ = load_peaks()
+    out = {"complex_config": f"2^{26 - args.scale} complex64 inputs uniform in [-40,40]^2"}
+    for f in ("cexpf", "clogf", "csinf"):
+        ms = time_fn(torch, lambda: crm.eval_complex(f, z, out=w), reps, stream)
+        out[f] = {"gelem_s": n / (ms / 1e3) / 1e9, "hbm_frac": 16 * n / (ms / 1e3) / 1e9 / peak}
+    del z, w
+    N, M = 1 << (14 - args.scale // 2), 1 << (14 - (args.scale + 1) // 2)
+    t = torch.arange(N, device=dev, dtype=torch.float64)
+    x = (torch.sin(2 * np.pi * 37.3 * t / N) + 0.5 * torch.cos(2 * np.pi * 101.7 * t / N)).to(torch.float32)
+    fr = (torch.rand(M, generator=gen, device=dev, dtype=torch.float64) * N).to(torch.float32)
+    ms = time_fn(torch, lambda: crm.spectral_dft(x, fr), reps, stream)
+    out["spectral"] = {"config": f"N = {N} samples, M = {M} frequencies", "terms_per_call": N * M,
+                       "gterms_s": N * M / (ms / 1e3) / 1e9, "ms_per_call": ms}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -398,7 +461,7 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="launch shape for every array (skips the autotuner; profiling runs)")
     ap.add_argument("--funcs", default="", help="comma list restricting the workload (testing)")
-    ap.add_argument("--extras", default="precision,f64,batch",
+    ap.add_argument("--extras", default="precision,f64,batch,modes,apps",
                     help="other workloads measured after the headline step (comma list, or none)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -587,6 +650,10 @@ def main():
                 line["extras"]["batch"] = {k: b[k] for k in ("value", "ms_per_step", "config", "roofline",
                                                              "one_launch_per_array", "direct_call",
                                                              "hard_case_rate", "unresolved", "clocks")}
+            elif wl == "modes":
+                line["extras"]["modes"] = measure_modes(args, crm, torch, dev)
+            elif wl == "apps":
+                line["extras"]["apps"] = measure_apps(args, crm, torch, dev)
             else:
                 line["extras"][wl] = measure_set(args, crm, torch, dev, wl)
     if rank == 0:

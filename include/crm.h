@@ -136,6 +136,34 @@ int crm_eval_form(int func_id, int dtype, int form, const void *in, void *out, u
    CRM_ERR_NULL, CRM_ERR_OVERLAP, CRM_ERR_NOMEM, CRM_ERR_CAPTURE, CRM_ERR_CUDA. */
 int crm_eval_rm(int func_id, int dtype, int rmode, const void *in, void *out, uint64_t n, void *stream);
 
+/* ---- workloads built on the library: the paper's applications (Sec. III.A) ---- */
+/* Complex functions to within 2 ulp per component (the paper's "2-ulp complex expf, logf,
+   sinf"): cexp(x + iy) = e^x cos y + i e^x sin y; clog(z) = log|z| + i atan2(y, x);
+   csin(x + iy) = sin x cosh y + i cos x sinh y.  Each component is formed from the
+   library's double-float evaluations and rounded once: within 1/2 + 2^-12 ulp of the exact
+   value (the correctly rounded result or a neighbour).  in/out: device arrays of n complex
+   binary32 numbers (re, im interleaved, 8-byte aligned); in == out allowed.  Valid inputs:
+   finite with |re|, |im| <= 40 for cexpf and csinf (the paper's test range; beyond it a
+   component may overflow), finite with 2^-60 <= max(|re|, |im|) < 2^61 for clogf; others
+   give unspecified values.
+   Asynchronous on `stream`; no workspace.  Errors: CRM_ERR_FUNC, CRM_ERR_NULL, CRM_ERR_ARG,
+   CRM_ERR_OVERLAP, CRM_ERR_CUDA. */
+#define CRM_CEXPF 0
+#define CRM_CLOGF 1
+#define CRM_CSINF 2
+int crm_eval_complex(int cfunc, const void *in, void *out, uint64_t n, void *stream);
+
+/* Spectral interpolation by a brute-force discrete Fourier transform on the time samples
+   (the paper's first application): for each frequency freq[m] (bins, 0 or in [2^-10, N)),
+     out[2m] + i out[2m+1] = sum_{n<N} x[n] (cos t_n - i sin t_n),  t_n = 2 pi frac(freq[m] n / N),
+   with t_n = RN(RN(frac) RN(2 pi)) (the fraction exact in integers), sin t_n and cos t_n
+   correctly rounded (sincosf), the products exact and the sum in double-float per thread,
+   then binary64 (error below 2^-40 of sum |x[n]|).  x: N binary32 samples, N a power of two
+   up to 2^24; freq: M binary32 values; out: 2M binary64 values (NaN for a frequency outside
+   the range).  Device pointers; asynchronous on `stream`; no workspace.  Errors:
+   CRM_ERR_NULL, CRM_ERR_ARG (N, alignment), CRM_ERR_CUDA. */
+int crm_spectral_dft(const float *x, uint64_t N, const float *freq, uint64_t M, double *out, void *stream);
+
 /* Host-buffer variant: in/out are host pointers.  When both are page-locked memory that
    the device addresses directly (cudaHostAlloc / cudaHostRegister on a system with
    unified addressing, as on GB300), the kernels read and write them in place over the

@@ -14,7 +14,7 @@ import ctypes
 from . import _lib as L
 from ._lib import F64_FUNCS, FORMS, FUNC_ID, FUNCS, CrmError, crm_desc_t, crm_stats_t
 
-__all__ = ["eval", "eval_into", "eval_rm", "eval_host", "eval_batch", "stats", "stats_reset",
+__all__ = ["eval", "eval_into", "eval_rm", "eval_complex", "spectral_dft", "eval_host", "eval_batch", "stats", "stats_reset",
            "set_form", "set_force_slow", "set_batch_tile", "reserve", "FUNCS", "FORMS", "CrmError", "version",
            "variant_info", "set_variant", "get_variant", "autotune", "autotune_batch", "set_batch_mode"]
 
@@ -116,6 +116,42 @@ def eval_rm(func, x, mode="rn", out=None, stream=None):
                                 ctypes.c_void_p(out.data_ptr()), x.numel(), _stream_ptr(stream)),
             f"{FUNCS[fid]} {mode}")
     return out
+
+
+COMPLEX_FUNCS = {"cexpf": 0, "clogf": 1, "csinf": 2}
+
+
+def eval_complex(func, z, out=None, stream=None):
+    """cexpf, clogf or csinf of a contiguous complex64 CUDA tensor (each component within
+    2 ulp; see include/crm.h for the valid inputs).  Returns out (new unless given)."""
+    import torch
+    if not isinstance(z, torch.Tensor) or not z.is_cuda or not z.is_contiguous() or z.dtype != torch.complex64:
+        raise ValueError("z must be a contiguous complex64 CUDA tensor")
+    if out is None:
+        out = torch.empty_like(z)
+    if not out.is_contiguous() or out.dtype != torch.complex64 or out.numel() < z.numel() or out.device != z.device:
+        raise ValueError("out must be a contiguous complex64 tensor like z")
+    L.check(L.lib().crm_eval_complex(COMPLEX_FUNCS[func], ctypes.c_void_p(z.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), z.numel(), _stream_ptr(stream)), func)
+    return out
+
+
+def spectral_dft(x, freq, out=None, stream=None):
+    """X(f) = sum_n x[n] exp(-2 pi i f n / N) for each f in freq (float32 CUDA tensors; N =
+    x.numel() a power of two), with correctly rounded sines and cosines; returns a complex128
+    tensor (out, if given, a float64 tensor of 2 * freq.numel())."""
+    import torch
+    for name, t in (("x", x), ("freq", freq)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous() or t.dtype != torch.float32:
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    m = freq.numel()
+    if out is None:
+        out = torch.empty(2 * m, dtype=torch.float64, device=x.device)
+    if not out.is_contiguous() or out.dtype != torch.float64 or out.numel() < 2 * m:
+        raise ValueError("out must be a contiguous float64 tensor of 2 * freq.numel()")
+    L.check(L.lib().crm_spectral_dft(ctypes.c_void_p(x.data_ptr()), x.numel(), ctypes.c_void_p(freq.data_ptr()),
+                                     m, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "spectral_dft")
+    return torch.view_as_complex(out[:2 * m].view(m, 2))
 
 
 def eval_host(func, x_np, out_np=None, form=None, stream=None):

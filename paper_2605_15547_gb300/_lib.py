@@ -63,6 +63,8 @@ def _lib():
                 lib.crm_eval_form.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, vp]
                 lib.crm_eval_host.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, vp]
                 lib.crm_eval_rm.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, vp]
+                lib.crm_eval_complex.argtypes = [c_int, vp, vp, c_u64, vp]
+                lib.crm_spectral_dft.argtypes = [vp, c_u64, vp, c_u64, vp, vp]
                 lib.crm_eval_batch.argtypes = [ctypes.POINTER(crm_desc_t), c_int, c_int, vp]
                 lib.crm_set_form.argtypes = [c_int]
                 lib.crm_set_force_slow.argtypes = [c_int]

@@ -186,23 +186,11 @@ CRM_DEV DFY expm1_df_core(float x, const float4 *T64U) {
 CRM_DEV float pow2f_exact(int k) { return bitsf((uint32_t)(k + 127) << 23); }  // k in [-126, 127]
 CRM_DEV float scale_f(float y, int k) { return bitsf(fbits(y) + ((uint32_t)k << 23)); }
 
-template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard, int *sg = nullptr) {
-  float ax = fabsf(x);
-  bool tiny = ax < 0x1p-25f;  // the correctly rounded result is x itself (or 1 for cosh)
-  bool sp;                    // NaN, tiny, saturated (results selected on a rare branch)
-  if (H == HYP_EXPM1) {
-    // below X_MONE: -1; in [X_MONE, X_M2]: -1 + 2^-24 (the first step of the staircase)
-    sp = !(x > CRM_EXPM1F_X_M2 && x <= CRM_EXPF_X_OVF) || tiny;
-  } else if (H == HYP_SINH || H == HYP_COSH) {
-    sp = !(ax <= CRM_SINHF_X_OVF) || tiny;
-  } else {
-    // above X_ONE: +-1; in (X_NEXT, X_ONE]: +-(1 - 2^-24)
-    sp = !(ax <= CRM_TANHF_X_NEXT) || tiny;
-  }
-  float arg = H == HYP_EXPM1 ? x : (H == HYP_TANH ? 2.0f * ax : ax);
-  arg = sp ? 0.5f : arg;
+// The unrounded double-float result and its scale, f = 2^sc (r.hi + r.lo), for arg = x
+// (expm1), |x| (sinh, cosh) or 2|x| (tanh), arg not special (hyp_df handles those).
+template <int H> CRM_DEV Pair<float> hyp_df_core(float arg, const float4 *T64U, int &sc) {
   Pair<float> r;
-  int sc = 0;
+  sc = 0;
   if (H == HYP_COSH) {
     // cosh a = (e^a + e^-a)/2 never cancels, so the exp core suffices (no expm1 care):
     // e^a = 2^k P with P to 2^-37.7 (exp_df_core), R = 2^-k / P by a pair division, and
@@ -243,6 +231,26 @@ template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard, i
     sc = Y.k - 1;
   }
   }
+  return r;
+}
+
+template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard, int *sg = nullptr) {
+  float ax = fabsf(x);
+  bool tiny = ax < 0x1p-25f;  // the correctly rounded result is x itself (or 1 for cosh)
+  bool sp;                    // NaN, tiny, saturated (results selected on a rare branch)
+  if (H == HYP_EXPM1) {
+    // below X_MONE: -1; in [X_MONE, X_M2]: -1 + 2^-24 (the first step of the staircase)
+    sp = !(x > CRM_EXPM1F_X_M2 && x <= CRM_EXPF_X_OVF) || tiny;
+  } else if (H == HYP_SINH || H == HYP_COSH) {
+    sp = !(ax <= CRM_SINHF_X_OVF) || tiny;
+  } else {
+    // above X_ONE: +-1; in (X_NEXT, X_ONE]: +-(1 - 2^-24)
+    sp = !(ax <= CRM_TANHF_X_NEXT) || tiny;
+  }
+  float arg = H == HYP_EXPM1 ? x : (H == HYP_TANH ? 2.0f * ax : ax);
+  arg = sp ? 0.5f : arg;
+  int sc = 0;
+  const Pair<float> r = hyp_df_core<H>(arg, T64U, sc);
   if (__builtin_expect(!sp, 1)) {
     // r unnormalised: |r.lo| < 2^-20 |r.hi| in every branch above
     float y = scale_f(round_df(r.hi, r.lo, hard, sg), sc);

@@ -178,7 +178,7 @@ def whole_job_gelem_s(elems_per_rank: int, steps: int, world: int, ms_total: flo
 
 
 def bytes_per_elem(func: str) -> int:
-    return 12 if func == "sincosf" else (16 if func in ("exp2", "log") else 8)
+    return 12 if func == "sincosf" else (16 if func in W.F64_FUNCS else 8)
 
 
 # ----------------------------------------------------------------------------- workloads

@@ -7,7 +7,8 @@
  * Sec. I and Sec. II of "Correctly Rounded Functions For Vector Applications: A
  * Performance Study"; the GPU runs of Sec. III.C use round-to-nearest-even only, and so
  * does this library.  The single-precision function set is the one of Sec. II.A; the
- * double-precision pair (exp2, log) is the one of Sec. II.B.
+ * double-precision pair (exp2, log) is the one of Sec. II.B; exp, log2, log10 and exp10 in
+ * binary64 extend it (the paper's outlook: more double-precision functions).
  *
  * Evaluation forms (crm_form_t):
  *   CRM_FORM_PLAIN_FP64 -- FP64 internal arithmetic, as the paper's single-precision
@@ -55,7 +56,10 @@ typedef enum {
   CRM_LOG1PF, CRM_SINF, CRM_COSF, CRM_SINCOSF, CRM_TANF, CRM_ASINF, CRM_ACOSF,
   CRM_ATANF, CRM_SINHF, CRM_COSHF, CRM_TANHF, CRM_RSQRTF, /* binary32 in and out */
   CRM_EXP2 = 19, CRM_LOG = 20,                             /* binary64 in and out */
-  CRM_NUM_FUNCS = 21
+  /* more binary64 functions (the formulas of expf, log2f, log10f, exp10f in binary64; one
+     form, the FP64-free one; not in crm_eval_batch) */
+  CRM_EXP = 21, CRM_LOG2 = 22, CRM_LOG10 = 23, CRM_EXP10 = 24,
+  CRM_NUM_FUNCS = 25
 } crm_func_t;
 
 /* Element formats: binary32, binary64, and the 16-bit formats of crm_eval_rm (IEEE

@@ -1690,6 +1690,18 @@ static int ziv(int kind, const dec_t *x, uint64_t xbits, const fmt_t *f, uint64_
     g_last_level = -1;
     return ORC_OK;
   }
+  /* 10^k for an integer 0 <= k <= 27 is the dyadic 5^k 2^k (5^k < 2^63), rounded directly:
+     in binary64, 10^23 is a midpoint (5^23 is an odd 54-bit integer), which no interval
+     around it can decide */
+  if (kind == K_EXP10 && x->cls == CL_FINITE && !x->neg && is_integer(x) && approx(x) <= 27.0) {
+    int64_t p5 = 1;
+    for (int i = 0; i < (int)approx(x); i++) p5 *= 5;
+    limb a[MAXL];
+    fx_set_i64(a, p5, 2);
+    *out = round_fixed(a, 2, (int64_t)approx(x), f, mode);
+    g_last_level = -1;
+    return ORC_OK;
+  }
   /* acos(-1) = pi exactly as a real: round pi */
   for (int lvl = 0; lvl < NLEVELS; lvl++) {
     int n = LEVEL_LIMBS[lvl];
@@ -1719,7 +1731,8 @@ static int ziv(int kind, const dec_t *x, uint64_t xbits, const fmt_t *f, uint64_
 static int kind_of(int func, int *is64) {
   static const int map[] = {K_EXP, K_EXP2, K_EXP10, K_EXPM1, K_LOG, K_LOG2, K_LOG10,
                             K_LOG1P, K_SIN, K_COS, -1 /*sincos*/, K_TAN, K_ASIN, K_ACOS,
-                            K_ATAN, K_SINH, K_COSH, K_TANH, K_RSQRT, K_EXP2, K_LOG};
+                            K_ATAN, K_SINH, K_COSH, K_TANH, K_RSQRT, K_EXP2, K_LOG,
+                            K_EXP, K_LOG2, K_LOG10, K_EXP10};
   if (func < 0 || func >= ORC_NUM_FUNCS) return -2;
   *is64 = func >= ORC_EXP2;
   return map[func];

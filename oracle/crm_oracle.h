@@ -4,7 +4,8 @@
  * This is the parity oracle for the GPU library: a plain, slow CPU implementation of
  *     out = RN_fmt(f(x))      (round to nearest, ties to even; binary32 or binary64)
  * for the one-input functions of the paper (Sec. II.A lists the 19 single-precision
- * functions, Sec. II.B the double-precision exp2 and log).  It follows Ziv's method
+ * functions, Sec. II.B the double-precision exp2 and log; exp, log2, log10 and exp10 in
+ * binary64 extend that pair, as the paper's outlook asks for more double functions).  It follows Ziv's method
  * (Sec. I): evaluate an interval that provably encloses f(x) with multiprecision
  * integer (fixed-point) arithmetic, and raise the precision until both interval
  * ends round to the same floating-point number.  Only the test suite, the smoke
@@ -27,7 +28,9 @@ enum {
   ORC_LOG1PF, ORC_SINF, ORC_COSF, ORC_SINCOSF, ORC_TANF, ORC_ASINF, ORC_ACOSF,
   ORC_ATANF, ORC_SINHF, ORC_COSHF, ORC_TANHF, ORC_RSQRTF,
   ORC_EXP2 = 19, ORC_LOG = 20,
-  ORC_NUM_FUNCS = 21
+  /* more binary64 functions: the same formulas as expf, log2f, log10f and exp10f, in binary64 */
+  ORC_EXP = 21, ORC_LOG2 = 22, ORC_LOG10 = 23, ORC_EXP10 = 24,
+  ORC_NUM_FUNCS = 25
 };
 
 enum { ORC_OK = 0, ORC_ERR_FUNC = 1, ORC_ERR_CAP = 2 };

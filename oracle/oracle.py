@@ -28,10 +28,10 @@ _LIB = os.path.join(_HERE, f"liboracle_{platform.machine()}.so")
 FUNCS = [
     "expf", "exp2f", "exp10f", "expm1f", "logf", "log2f", "log10f", "log1pf",
     "sinf", "cosf", "sincosf", "tanf", "asinf", "acosf", "atanf", "sinhf", "coshf",
-    "tanhf", "rsqrtf", "exp2", "log",
+    "tanhf", "rsqrtf", "exp2", "log", "exp", "log2", "log10", "exp10",
 ]
 FUNC_ID = {name: i for i, name in enumerate(FUNCS)}
-F64_FUNCS = ("exp2", "log")
+F64_FUNCS = ("exp2", "log", "exp", "log2", "log10", "exp10")
 
 _lock = threading.Lock()
 _lib = None

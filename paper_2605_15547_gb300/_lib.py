@@ -16,10 +16,10 @@ LIB_PATH = os.path.join(HERE, f"libcrm_{platform.machine()}.so")
 FUNCS = [
     "expf", "exp2f", "exp10f", "expm1f", "logf", "log2f", "log10f", "log1pf", "sinf",
     "cosf", "sincosf", "tanf", "asinf", "acosf", "atanf", "sinhf", "coshf", "tanhf",
-    "rsqrtf", "exp2", "log",
+    "rsqrtf", "exp2", "log", "exp", "log2", "log10", "exp10",
 ]
 FUNC_ID = {n: i for i, n in enumerate(FUNCS)}
-F64_FUNCS = {"exp2", "log"}
+F64_FUNCS = {"exp2", "log", "exp", "log2", "log10", "exp10"}
 FORMS = {"auto": 0, "plain": 1, "df": 2}
 CRM_F32, CRM_F64, CRM_F16, CRM_BF16 = 0, 1, 2, 3
 RMODES = {"rn": 0, "rd": 1, "ru": 2, "rz": 3}

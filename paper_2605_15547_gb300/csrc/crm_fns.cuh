@@ -181,4 +181,37 @@ struct FnLogD {
   CRM_DEV static void slow(double x, double *y, int &u, bool f, int *sg = nullptr) { y[0] = logd_slow(x, u, f, sg); }
 };
 
+// More binary64 functions on the fixed-point cores: e^x and 10^x (KIND 0, 2) on the exp2
+// core with the 1024-entry table, log2 and log10 (KIND 1, 2) on the log core; the slow path
+// is the exact 192-bit tier.  One form (the FP64-free one).
+template <int KIND> struct FnExpBD {
+  using T = double;
+  static constexpr int NOUT = 1;
+  template <int FORM> static constexpr int tab_bytes() { return 1024 * 16; }
+  template <int FORM> CRM_DEV static void load(unsigned char *sm) { copy_tab(sm, CRM_EXP2I_T, 1024 * 16); }
+  template <int FORM> CRM_DEV static void eval(double x, const void *sm, double *y, bool &h, int *sg = nullptr) {
+    y[0] = expbd_int<KIND>(x, (const ulonglong2 *)sm, h, sg);
+  }
+  CRM_DEV static void slow(double x, double *y, int &u, bool f, int *sg = nullptr) {
+    y[0] = expbd_slow<KIND>(x, u, f, sg);
+  }
+};
+template <int KIND> struct FnLogBD {
+  using T = double;
+  static constexpr int NOUT = 1;
+  static constexpr int LBYTES = 193 * 16;
+  template <int FORM> static constexpr int tab_bytes() { return LBYTES + 194 * 2 + 12; }
+  template <int FORM> CRM_DEV static void load(unsigned char *sm) {
+    copy_tab(sm, CRM_LOGI_L, LBYTES);
+    copy_tab(sm + LBYTES, CRM_LOGI_R, 194 * 2);
+  }
+  template <int FORM> CRM_DEV static void eval(double x, const void *sm, double *y, bool &h, int *sg = nullptr) {
+    y[0] = logbd_int<KIND>(x, (const ulonglong2 *)sm, (const unsigned short *)((const unsigned char *)sm + LBYTES),
+                           h, sg);
+  }
+  CRM_DEV static void slow(double x, double *y, int &u, bool f, int *sg = nullptr) {
+    y[0] = logbd_slow<KIND>(x, u, f, sg);
+  }
+};
+
 }  // namespace crm

@@ -112,14 +112,28 @@ void set_regtab_variant(FuncEntry &e) {
 template <class Fn, bool HAS_PLAIN, bool HAS_DF>
 void set_entry(FuncEntry &e) {
   e = FuncEntry();
-  if (HAS_PLAIN) set_form<Fn, 1>(e);
-  if (HAS_DF) set_form<Fn, 2>(e);
+  if constexpr (HAS_PLAIN) set_form<Fn, 1>(e);
+  if constexpr (HAS_DF) set_form<Fn, 2>(e);
   e.slow = launch_slow<Fn>;
   e.dmain = launch_dir<Fn>;
   e.dslow = launch_dir_slow<Fn>;
   e.dmain_sym = (const void *)k_dir<Fn>;
   e.nout = Fn::NOUT;
   e.dtype = sizeof(typename Fn::T) == 8 ? 1 : 0;
+}
+
+// A function with the FP64-free form in the default launch shape only (fewer kernels to
+// build for the later binary64 functions).
+template <class Fn>
+void set_entry_default(FuncEntry &e) {
+  e = FuncEntry();
+  set_variant<Fn, 2, DEFAULT_VARIANT>(e);
+  e.slow = launch_slow<Fn>;
+  e.dmain = launch_dir<Fn>;
+  e.dslow = launch_dir_slow<Fn>;
+  e.dmain_sym = (const void *)k_dir<Fn>;
+  e.nout = Fn::NOUT;
+  e.dtype = 1;
 }
 
 // one per family translation unit
@@ -129,5 +143,6 @@ void register_hyp(FuncEntry *table);
 void register_trig(FuncEntry *table);
 void register_atrig(FuncEntry *table);
 void register_f64(FuncEntry *table);
+void register_f64b(FuncEntry *table);
 
 }  // namespace crm

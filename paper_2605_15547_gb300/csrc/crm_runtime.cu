@@ -35,6 +35,7 @@ static void init_table() {
   register_trig(g_table);
   register_atrig(g_table);
   register_f64(g_table);
+  register_f64b(g_table);
   const char *f = getenv("CRM_FORM");
   if (f) {
     if (!strcmp(f, "plain")) g_default_form = CRM_FORM_PLAIN_FP64;
@@ -596,6 +597,7 @@ int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
     int st = check_args(d.func_id, d.dtype, d.in, d.out, d.n);
     if (st) return st;
     if (resolve_form(g_table[d.func_id], form) < 0) return CRM_ERR_FORM;
+    if (d.func_id > CRM_LOG) return CRM_ERR_FUNC;  // the batching form takes the paper's 21
     if (d.func_id >= CRM_EXP2) has64 = true;
   }
   int fm = form == CRM_FORM_PLAIN_FP64 ? 1 : 2;

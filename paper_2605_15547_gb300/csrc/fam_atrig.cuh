@@ -144,6 +144,13 @@ CRM_DEV Pair<float> atan_ratio_df(Pair<float> a, Pair<float> b, const float2 *AT
 }
 
 template <int KIND> CRM_DEV float atrig_df(float x, const float2 *AT, bool &hard, int *sg = nullptr) {
+  if (sg && fabsf(x) < (KIND == AT_ACOS ? 0x1p-27f : 0x1p-12f) && x == x) {
+    // atan x just below x, asin x just above it (x^3/6 below half an ulp); acos x within
+    // 2^-27 of pi/2, below RN(pi/2) = 0x1.921fb6p+0
+    hard = false;
+    *sg = KIND == AT_ATAN ? -sgnf(x) : (KIND == AT_ASIN ? sgnf(x) : -1);
+    return KIND == AT_ACOS ? 0x1.921fb6p+0f : x;
+  }
   float rsp;
   bool sp = atrig_special<KIND>(x, rsp);
   float xs = sp ? 0.5f : x;

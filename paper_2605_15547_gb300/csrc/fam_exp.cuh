@@ -149,6 +149,11 @@ template <int KIND> CRM_DEV void exp_df_core(float x, const float4 *T64U, float 
 // band's integer is compared with u itself.
 template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard, int *sg = nullptr) {
   using K = ExpK<KIND>;
+  if (sg && fabsf(x) < 0x1p-26f) {  // b^x - 1 has the sign of x and is below 2^-24: 1 or a neighbour
+    hard = false;
+    *sg = sgnf(x);
+    return 1.0f;
+  }
   float s, r;
   uint32_t sb;
   exp_df_core<KIND>(x, T64U, s, r, sb);

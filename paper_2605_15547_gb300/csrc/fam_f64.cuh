@@ -382,6 +382,144 @@ CRM_DEV double logd_int(double x, const ulonglong2 *LT, const unsigned short *RT
   return sp ? rs : (zero ? 0.0 : bitsd(bits | (zneg ? 0x8000000000000000ull : 0ull)));
 }
 
+// ------------------------------------------------------------------ e^x, 10^x, FP64-free
+// b^x = 2^(x log2 b) on the same fixed-point exp2 core: |x| log2(b) 2^96 is formed from x's
+// 53-bit significand times log2 e (Q125) or log2 10 (Q124), truncated (the constant's and
+// the product's truncations stay below 2 units of 2^-96, i.e. 2^29 units of Y: the rounding
+// bound is taken as 2^55 units); then the rounding of exp2d_int.  KIND 0: e^x, 2: 10^x.
+template <int KIND> CRM_DEV U128 expbd_arg(uint64_t ab) {  // 2^-60 <= |x| < 2^10
+  const int E = (int)(ab >> 52);
+  const uint64_t M = (ab & 0x000FFFFFFFFFFFFFull) | (1ull << 52);  // |x| = M 2^(E - 1075)
+  const uint64_t ch = KIND == 0 ? CRM_EXPI_LOG2E_Q125_HI : CRM_EXPI_LOG2_10_Q124_HI;
+  const uint64_t cl = KIND == 0 ? CRM_EXPI_LOG2E_Q125_LO : CRM_EXPI_LOG2_10_Q124_LO;
+  const int F = KIND == 0 ? 125 : 124;
+  const U128 ml = mul64w(M, cl), mh = mul64w(M, ch);  // M C as 192 bits p2:p1:p0
+  const uint64_t p0 = ml.lo, p1 = ml.hi + mh.lo;
+  const uint64_t p2 = mh.hi + (p1 < ml.hi ? 1ull : 0ull);
+  const int sft = F - 96 - (E - 1075);  // X = M C >> sft, sft in [60, 141]
+  U128 X;
+  if (sft < 64) {
+    X.lo = (p0 >> sft) | (p1 << (64 - sft));
+    X.hi = (p1 >> sft) | (p2 << (64 - sft));
+  } else if (sft < 128) {
+    const int s2 = sft - 64;
+    X.lo = s2 ? ((p1 >> s2) | (p2 << (64 - s2))) : p1;
+    X.hi = p2 >> s2;
+  } else {
+    X.lo = p2 >> (sft - 128);
+    X.hi = 0ull;
+  }
+  return X;
+}
+
+template <int KIND>
+CRM_DEV double expbd_int(double x, const ulonglong2 *T, bool &hard, int *sg = nullptr) {
+  const uint64_t b = dbits(x), ab = b & 0x7FFFFFFFFFFFFFFFull;
+  const bool neg = (b >> 63) != 0;
+  hard = false;
+  if (ab >= 0x4090000000000000ull) {  // NaN, +-inf, |x| >= 1024: b^x overflows or underflows
+    put_sg(sg, ab >= 0x7FF0000000000000ull ? 0 : (neg ? 1 : -1));
+    return ab > 0x7FF0000000000000ull ? bitsd(b | 0x0008000000000000ull) : (neg ? 0.0 : CRM_INF_D);
+  }
+  if ((int)(ab >> 52) < 1023 - 60) {  // |x| < 2^-60: b^x - 1 is below 2^-57, rounds to 1
+    put_sg(sg, ab == 0 ? 0 : (neg ? -1 : 1));
+    return 1.0;
+  }
+  U128 X = expbd_arg<KIND>(ab);
+  if (neg) X = neg128(X);
+  int k;
+  const U128 Y = exp2q_core(X, T, k);
+  if (k >= 1024) {
+    put_sg(sg, -1);
+    return CRM_INF_D;
+  }
+  if (k < -1075) {
+    put_sg(sg, 1);
+    return 0.0;
+  }
+  const uint64_t ERR = 1ull << 55;
+  uint64_t bits;
+  bool up, near, ndir;
+  if (k >= -1022) {  // normal result: round at bit 72
+    const uint64_t dh = (Y.hi & 0xFFull) - 0x80ull;
+    up = (int64_t)dh > 0 || (dh == 0 && Y.lo != 0);
+    near = (dh == 0 && Y.lo <= ERR) || (dh == ~0ull && Y.lo >= 0ull - ERR);
+    bits = ((uint64_t)(int64_t)(k + 1022) << 52) + (Y.hi >> 8) + (up ? 1ull : 0ull);
+    const uint64_t rh = Y.hi & 0xFFull;
+    ndir = (rh == 0 && Y.lo <= ERR) || (rh == 0xFFull && Y.lo >= 0ull - ERR);
+  } else {  // subnormal result: round at bit 72 + (-1022 - k) <= 125
+    const int sh64 = 8 + (-1022 - k);
+    const uint64_t remh = Y.hi & ((1ull << sh64) - 1ull);
+    const uint64_t dh = remh - (1ull << (sh64 - 1));
+    up = (int64_t)dh > 0 || (dh == 0 && Y.lo != 0);
+    near = (dh == 0 && Y.lo <= ERR) || (dh == ~0ull && Y.lo >= 0ull - ERR);
+    bits = (Y.hi >> sh64) + (up ? 1ull : 0ull);
+    ndir = (remh == 0 && Y.lo <= ERR) || (remh == (1ull << sh64) - 1ull && Y.lo >= 0ull - ERR);
+  }
+  hard = near;
+  if (sg) {
+    hard = ndir;
+    *sg = up ? -1 : 1;
+  }
+  return bitsd(bits);
+}
+
+// ------------------------------------------------------------------ log2, log10, FP64-free
+// The log core (Z = ln x in Q116, error err units) times 1/ln 2 or 1/ln 10 in Q126 (the
+// product truncated: W = Z C 2^-126, error err C + 2 units, taken as err + err/2 + 3), then
+// |W| rounded to 53 bits with the rounding test of logd_int.  KIND 1: log2, 2: log10.
+CRM_DEV U128 mul_q126_const(U128 A, uint64_t ch, uint64_t cl) {  // A C 2^-126 for A, C >= 0
+  const U128 hh = mul64w(A.hi, ch), hl = mul64w(A.hi, cl), lh = mul64w(A.lo, ch);
+  const uint64_t ll_hi = __umul64hi(A.lo, cl);
+  U128 mid = add128(hl, lh);
+  const uint64_t c1 = (mid.hi < hl.hi || (mid.hi == hl.hi && mid.lo < hl.lo)) ? 1ull : 0ull;
+  mid = add128_64(mid, ll_hi);
+  const uint64_t c2 = (mid.hi == 0 && mid.lo < ll_hi) ? 1ull : 0ull;
+  const uint64_t w2 = hh.lo + mid.hi;
+  const uint64_t w3 = hh.hi + c1 + c2 + (w2 < hh.lo ? 1ull : 0ull);
+  const uint64_t w1 = mid.lo;
+  return {(w2 << 2) | (w1 >> 62), (w3 << 2) | (w2 >> 62)};
+}
+
+template <int KIND>
+CRM_DEV double logbd_int(double x, const ulonglong2 *LT, const unsigned short *RT, bool &hard, int *sg = nullptr) {
+  double rs;
+  const bool sp = logd_special_bits(dbits(x), rs);
+  const uint64_t b = sp ? 0x4000000000000000ull : dbits(x);
+  uint64_t err;
+  const U128 Z = logz_q116(b, LT, RT, err);
+  const bool zneg = (int64_t)Z.hi < 0;
+  const U128 A = mul_q126_const(zneg ? neg128(Z) : Z, KIND == 1 ? CRM_LOGI_INV_LN2_Q126_HI : CRM_LOGI_INV_LN10_Q126_HI,
+                                KIND == 1 ? CRM_LOGI_INV_LN2_Q126_LO : CRM_LOGI_INV_LN10_Q126_LO);
+  err = err + (err >> 1) + 3ull;
+  const bool zero = (A.hi | A.lo) == 0;  // x == 1
+  const int lz = A.hi ? __clzll(A.hi) : 64 + __clzll(A.lo | 1ull);
+  const int sh = 75 - lz;  // (127 - lz) - 52
+  uint64_t mant;
+  U128 rem, half;
+  if (sh < 64) {
+    mant = (A.lo >> sh) | (A.hi << (64 - sh));
+    rem = {A.lo & ((1ull << sh) - 1ull), 0ull};
+    half = {1ull << (sh - 1), 0ull};
+  } else {
+    mant = A.hi >> (sh - 64);
+    rem = {A.lo, A.hi & ((1ull << (sh - 64)) - 1ull)};
+    half = sh == 64 ? U128{1ull << 63, 0ull} : U128{0ull, 1ull << (sh - 65)};
+  }
+  const U128 dlt = sub128(rem, half);
+  const bool near = (dlt.hi == 0 && dlt.lo <= err) || (dlt.hi == ~0ull && dlt.lo >= 0ull - err);
+  const bool up = (int64_t)dlt.hi > 0 || (dlt.hi == 0 && dlt.lo != 0);
+  const uint64_t bits = ((uint64_t)(sh + 958) << 52) + mant + (up ? 1ull : 0ull);
+  // |W| >= 2^-60 unless x == 1 (|ln x| >= 2^-53 for x != 1), so sh >= 11: the shifts are valid
+  hard = !sp && !zero && (near || sh < 11);
+  if (sg) {
+    const U128 E = {err, 0ull};
+    hard = !sp && !zero && (sh < 11 || le128(rem, E) || le128(sub128(add128(half, half), rem), E));
+    *sg = (sp || zero) ? 0 : ((up != zneg) ? -1 : 1);
+  }
+  return sp ? rs : (zero ? 0.0 : bitsd(bits | (zneg ? 0x8000000000000000ull : 0ull)));
+}
+
 // ------------------------------------------------------------------ signed Q126 helpers
 // Signed fixed point with 126 fraction bits in 128-bit two's complement, for the
 // FP64-free middle tiers of the binary32 functions.
@@ -714,18 +852,9 @@ CRM_DEV bool exp2d_exact(double x, double &out, int *sg = nullptr) {
 // log(x), x > 0 finite, exactly: x = 2^e m, m in [1,2), c = 1 + j/128 <= m,
 // r = (m - c)/c in [0, 1/128) (Q0.191), log1p(r) = P - Q with P and Q the positive and
 // negative Taylor terms, S = log(c) + log1p(r); |log x| = |e ln2 + S| in Q11.181.
-CRM_DEV bool logd_exact(double x, double &out, int *sg = nullptr) {
-  uint64_t b = dbits(x);
-  int be = (int)(b >> 52);
-  uint64_t f = b & 0x000FFFFFFFFFFFFFull;
-  int e;
-  if (be == 0) {  // subnormal: move the leading 1 (at bit 52 - lz) to bit 52
-    int lz = __clzll((long long)f) - 11;
-    f = (f << lz) & 0x000FFFFFFFFFFFFFull;
-    e = -1022 - lz;
-  } else {
-    e = be - 1023;
-  }
+// |ln x| in Q11.181 (M, with the sign of ln x in neg) for x = 2^e (1 + f 2^-52), within
+// |e| + 16 units (below); false for x = 1.
+CRM_DEV bool logd_abs_q181(int e, uint64_t f, U192 &M, bool &neg, uint64_t &ae) {
   int j = (int)(f >> 45);
   uint64_t dlow = f & ((1ull << 45) - 1);  // (m - c) 2^52
   // r = (m - c) 128 / (128 + j) in Q0.191: (m - c) 2^191 = dlow 2^139
@@ -740,17 +869,34 @@ CRM_DEV bool logd_exact(double x, double &out, int *sg = nullptr) {
   U192 S = u_sub(u_add(L, P), Q);  // in [0, ln2), Q0.191, error within +-64 units
   U192 ln2 = {{CRM_LN2_FX[0], CRM_LN2_FX[1], CRM_LN2_FX[2]}};
   U192 S10 = u_shr(S, 10);  // Q11.181
-  uint64_t ae = (uint64_t)(e < 0 ? -e : e);
+  ae = (uint64_t)(e < 0 ? -e : e);
   U192 E = u_mul_small(u_shr(ln2, 10), ae);  // |e| ln2 < 2^10.5 fits Q11.181
-  U192 M;
-  bool neg = false;
+  neg = false;
   if (e >= 0) {
     M = u_add(E, S10);
   } else {
     M = u_sub(E, S10);
     neg = true;
   }
-  if (u_is_zero(M)) return false;
+  return !u_is_zero(M);
+}
+
+CRM_DEV bool logd_exact(double x, double &out, int *sg = nullptr) {
+  uint64_t b = dbits(x);
+  int be = (int)(b >> 52);
+  uint64_t f = b & 0x000FFFFFFFFFFFFFull;
+  int e;
+  if (be == 0) {  // subnormal: move the leading 1 (at bit 52 - lz) to bit 52
+    int lz = __clzll((long long)f) - 11;
+    f = (f << lz) & 0x000FFFFFFFFFFFFFull;
+    e = -1022 - lz;
+  } else {
+    e = be - 1023;
+  }
+  U192 M;
+  bool neg;
+  uint64_t ae;
+  if (!logd_abs_q181(e, f, M, neg, ae)) return false;
   // errors (units of 2^-181): S within 64 units of 2^-191 (< 1), the shift of S 1, the
   // truncated ln2 times |e|: |e| + 1.  The interval is M -+ (|e| + 16).
   return u_round64(M, 181, ae + 16, ae + 16, neg, out, sg);
@@ -785,6 +931,148 @@ CRM_DEV double logd_slow(double x, int &unresolved, bool force, int *sg = nullpt
   double out;
   bool ok = logd_exact(x, out, sg);
   unresolved = ok ? 2 : 3;
+  return ok ? out : r;
+}
+
+
+// ------------------------------------------------------------------ exact tiers of e^x, 10^x, log2, log10
+// b^x: t = x log2 b in Q180 from x's significand times log2 b (Q190 / Q189, truncated),
+// t = N/4096 + R (R in [0, 2^-12)), then exp2d_exact's pipeline on R.  The truncations move
+// t by at most 2^-169 (|x| < 2^10), i.e. 2^-169.5 of the result or 2^21.5 units of 2^-190:
+// the interval [sum - 2^23, sum + 2^23 + 2^10].
+template <int KIND> CRM_DEV bool expbd_exact(double x, double &out, int *sg = nullptr) {
+  const uint64_t b = dbits(x), ab = b & 0x7FFFFFFFFFFFFFFFull;
+  const int E = (int)(ab >> 52);
+  const uint64_t M = (ab & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+  const U192 C = KIND == 0 ? U192{{CRM_LOG2E_FX[0], CRM_LOG2E_FX[1], CRM_LOG2E_FX[2]}}
+                           : U192{{CRM_LOG2_10_FX[0], CRM_LOG2_10_FX[1], CRM_LOG2_10_FX[2]}};
+  const int fc = KIND == 0 ? 190 : 189;
+  // |t| 2^180 = M C 2^(E - 1075 - fc + 180) = (M C) >> (fc + 895 - E), the shift in [52, 122]
+  const U192 tf = u_mulfx(U192{{M, 0, 0}}, C, fc + 895 - E);
+  // N = floor(4096 t), R = t - N/4096 in Q191
+  const U192 q = u_shr(tf, 168);
+  const U192 rem = u_low(tf, 168);
+  long long N = (long long)q.w[0];
+  U192 Rf;
+  if (!(b >> 63)) {
+    Rf = u_shl(rem, 11);
+  } else if (u_is_zero(rem)) {
+    N = -N;
+    Rf = u_zero();
+  } else {
+    N = -N - 1;
+    Rf = u_shl(u_sub(u_pow2(168), rem), 11);
+  }
+  const int k = (int)(N >> 12);
+  const int i = (int)(N & 4095);
+  U192 ln2 = {{CRM_LN2_FX[0], CRM_LN2_FX[1], CRM_LN2_FX[2]}};
+  U192 u = u_shr(u_mulfx(Rf, ln2, 191), 1);  // Q2.190
+  U192 sum = u_add(u_pow2(190), u), term = u;
+  for (uint64_t n = 2; n < 40 && !u_is_zero(term); n++) {
+    term = u_divsmall(u_mulfx(term, u, 190), n);
+    sum = u_add(sum, term);
+  }
+  const unsigned long long *T = CRM_EXP2_FX_T;
+  int idx[3] = {i >> 8, (i >> 4) & 15, i & 15};
+  for (int a = 0; a < 3; a++) {
+    const unsigned long long *e = T + 48 * a + 3 * idx[a];
+    sum = u_mulfx(sum, U192{{e[0], e[1], e[2]}}, 190);
+  }
+  return u_round64(sum, 190 - k, 1ull << 23, (1ull << 23) + 1024, false, out, sg);
+}
+
+template <int KIND> CRM_DEV double expbd_slow(double x, int &unresolved, bool force, int *sg = nullptr) {
+  bool hard;
+  unresolved = 0;
+  double r = expbd_int<KIND>(x, (const ulonglong2 *)CRM_EXP2I_T, hard, sg);
+  if (!hard && !force) return r;
+  const uint64_t ab = dbits(x) & 0x7FFFFFFFFFFFFFFFull;
+  // special inputs, |x| < 2^-60, and results decided as overflow (+inf) or below half the
+  // smallest subnormal (+0) by the range of k are exact statements of the first tier
+  if (ab >= 0x4090000000000000ull || (int)(ab >> 52) < 1023 - 60 || (!hard && (isinf(r) || r == 0.0))) return r;
+  if (KIND == 2 && x == rint(x) && x >= 1.0 && x <= 27.0) {
+    // 10^k = 5^k 2^k (5^k < 2^63) rounded directly: exact for k <= 22, a midpoint for
+    // k = 23 (5^23 is an odd 54-bit integer), which no error bound can decide
+    const int kk = (int)x;
+    uint64_t p5 = 1;
+    for (int j = 0; j < kk; j++) p5 *= 5ull;
+    const int bl = 64 - __clzll((long long)p5);
+    uint64_t q = p5;
+    int sh = 0, s5 = 0;
+    if (bl > 53) {
+      sh = bl - 53;
+      const uint64_t rem = p5 & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+      q = p5 >> sh;
+      const bool up = rem > half || (rem == half && (q & 1ull));
+      q += up ? 1ull : 0ull;
+      s5 = rem == 0 ? 0 : (up ? -1 : 1);
+    }
+    put_sg(sg, s5);
+    return ldexp((double)q, sh + kk);
+  }
+  double out;
+  const bool ok = expbd_exact<KIND>(x, out, sg);
+  unresolved = ok ? 0 : 1;
+  return ok ? out : r;
+}
+
+// log2, log10: |ln x| in Q181 from logd_exact's pipeline, times 1/ln b in Q190 (truncated),
+// error (|e| + 16) C + 2 units, taken as 2 (|e| + 16) + 4.
+template <int KIND> CRM_DEV bool logbd_exact(double x, double &out, int *sg = nullptr) {
+  uint64_t b = dbits(x);
+  int be = (int)(b >> 52);
+  uint64_t f = b & 0x000FFFFFFFFFFFFFull;
+  int e;
+  if (be == 0) {
+    const int lz = __clzll(f) - 11;
+    f = (f << lz) & 0x000FFFFFFFFFFFFFull;
+    e = -1022 - lz;
+  } else {
+    e = be - 1023;
+  }
+  U192 M;
+  bool neg;
+  uint64_t ae;
+  if (!logd_abs_q181(e, f, M, neg, ae)) return false;
+  const U192 C = KIND == 1 ? U192{{CRM_INV_LN2_FX[0], CRM_INV_LN2_FX[1], CRM_INV_LN2_FX[2]}}
+                           : U192{{CRM_INV_LN10_FX[0], CRM_INV_LN10_FX[1], CRM_INV_LN10_FX[2]}};
+  const U192 W = u_mulfx(M, C, 190);
+  const uint64_t er = 2 * (ae + 16) + 4;
+  return u_round64(W, 181, er, er, neg, out, sg);
+}
+
+template <int KIND> CRM_DEV double logbd_slow(double x, int &unresolved, bool force, int *sg = nullptr) {
+  bool hard;
+  unresolved = 0;
+  double r = logbd_int<KIND>(x, (const ulonglong2 *)CRM_LOGI_L, CRM_LOGI_R, hard, sg);
+  if (!hard && !force) return r;
+  double sp;
+  if (logd_special(x, sp)) return r;
+  if (x == 1.0) {
+    put_sg(sg, 0);
+    return 0.0;
+  }
+  if (sg) {  // exact results: log2 of a power of two, log10 of 10^k (k <= 22)
+    const uint64_t b = dbits(x), f = b & 0x000FFFFFFFFFFFFFull;
+    const int be = (int)(b >> 52);
+    if (KIND == 1 && ((be != 0 && f == 0) || (be == 0 && (f & (f - 1)) == 0))) {
+      *sg = 0;
+      return be != 0 ? (double)(be - 1023) : (double)(63 - __clzll(f) - 1074);
+    }
+    if (KIND == 2) {
+      double p = 1.0;
+      for (int j = 1; j <= 22; j++) {
+        p *= 10.0;
+        if (x == p) {
+          *sg = 0;
+          return (double)j;
+        }
+      }
+    }
+  }
+  double out;
+  const bool ok = logbd_exact<KIND>(x, out, sg);
+  unresolved = ok ? 0 : 1;
   return ok ? out : r;
 }
 

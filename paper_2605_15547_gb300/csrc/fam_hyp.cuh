@@ -236,6 +236,12 @@ template <int H> CRM_DEV Pair<float> hyp_df_core(float arg, const float4 *T64U, 
 
 template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard, int *sg = nullptr) {
   float ax = fabsf(x);
+  if (sg && H != HYP_EXPM1 && ax < 0x1p-12f) {
+    // sinh x, tanh x within |x|^3/3 of x (above, below), cosh x within x^2/2 above 1
+    hard = false;
+    *sg = H == HYP_COSH ? (x == 0.0f ? 0 : 1) : (H == HYP_SINH ? sgnf(x) : -sgnf(x));
+    return H == HYP_COSH ? 1.0f : x;
+  }
   bool tiny = ax < 0x1p-25f;  // the correctly rounded result is x itself (or 1 for cosh)
   bool sp;                    // NaN, tiny, saturated (results selected on a rare branch)
   if (H == HYP_EXPM1) {

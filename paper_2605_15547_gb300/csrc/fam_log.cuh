@@ -146,7 +146,10 @@ template <int KIND> CRM_DEV float log_plain(float x, const double2 *T97, bool &h
 // us = 2^(e - eadj) m for a positive normal float us (any bit pattern gives an in-range
 // table index; the result is then meaningless and discarded), plus, for log1p, the low
 // word ul of 1 + x and the direct path for |x| < 2^-7.  Returns the unnormalised sum.
-template <int KIND>
+// With EXACT_T the correction ul/us is a correctly rounded division (for callers whose result
+// can consist of that term alone, e.g. log(x^2 + y^2) with x^2 + y^2 within 2^-24 of a power
+// of two); otherwise the fast reciprocal suffices (log1pf: the term is below 2^-24 of r).
+template <int KIND, bool EXACT_T = false>
 CRM_DEV Pair<float> log_df_core(float us, int eadj, float ul, bool pathA, float x, const float4 *T193) {
   using K = LogK<KIND>;
   // us = 2^e m, m in [3/4, 3/2), from one integer subtraction: the exponent field of
@@ -160,7 +163,7 @@ CRM_DEV Pair<float> log_df_core(float us, int eadj, float ul, bool pathA, float 
   float Lh = T.z, Ll = T.w, ef = (float)(ee + eadj);
   float t = 0.0f;
   if (KIND == 3) {
-    t = __fdividef(ul, us);  // ul/uh with |ul| <= 2^-24 uh: relative 2^-21 suffices
+    t = EXACT_T ? ul / us : __fdividef(ul, us);  // ul/uh with |ul| <= 2^-24 uh
     rh = pathA ? x : rh;
     Lh = pathA ? 0.0f : Lh;
     Ll = pathA ? 0.0f : Ll;
@@ -198,6 +201,11 @@ CRM_DEV Pair<float> log_df_core(float us, int eadj, float ul, bool pathA, float 
 }
 
 template <int KIND> CRM_DEV float log_df(float x, const float4 *T193, bool &hard, int *sg = nullptr) {
+  if (KIND == 3 && sg && fabsf(x) < 0x1p-25f && x != 0.0f) {  // log1p x = x - x^2/2 + ...: just below x
+    hard = false;
+    *sg = -1;
+    return x;
+  }
   const bool ok = log_ok<KIND>(x);
   float us = x, ul = 0.0f;
   int eadj = 0;

@@ -313,6 +313,17 @@ CRM_DEV uint32_t trig_cos_sign(int q) { return ((uint32_t)(q + 1) << 30) & 0x800
 template <int KIND>
 CRM_DEV void trig_df(float x, const uint4 *PW, const float4 *SC, const float2 *TT, float *y, bool &hard,
                      int *sg = nullptr) {
+  if (sg && fabsf(x) < 0x1p-12f) {  // sin x, tan x within x^3/3 of x, cos x within x^2/2 of 1
+    hard = false;
+    const int ss = KIND == TRIG_TAN ? sgnf(x) : -sgnf(x), cs = x == 0.0f ? 0 : -1;
+    y[0] = KIND == TRIG_COS ? 1.0f : x;
+    sg[0] = KIND == TRIG_COS ? cs : ss;
+    if (KIND == TRIG_SINCOS) {
+      y[1] = 1.0f;
+      sg[1] = cs;
+    }
+    return;
+  }
   const bool sp = !(fabsf(x) < CRM_INF_F);  // NaN or infinite
   if (KIND == TRIG_TAN) {
     Pair<float> t, D;

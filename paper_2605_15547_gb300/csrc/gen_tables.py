@@ -346,6 +346,14 @@ const_d("CRM_PIO64_D_LO", pp[1])
 pf = split(PIO64, f, 2)
 const_f("CRM_PIO64_F_HI", pf[0])
 const_f("CRM_PIO64_F_LO", pf[1])
+# Cody-Waite split of pi/64 into three floats: k C1 is exact after one FMA for the k of
+# |x| < 2^12, k C2 is split exactly by an FMA, C3 carries the rest (error < 2^-81 of pi/64)
+cw = split(PIO64, f, 3)
+assert abs(PIO64 - cw[0] - cw[1] - cw[2]) < mp.mpf(2) ** -81
+const_f("CRM_PIO64_CW1", cw[0], "pi/64 = CW1 + CW2 + CW3 (+ < 2^-81)")
+const_f("CRM_PIO64_CW2", cw[1])
+const_f("CRM_PIO64_CW3", cw[2])
+const_f("CRM_64OPI_F", f(64 / mp.pi), "64/pi, nearest float")
 i3 = split(mp.mpf(1) / 3, f, 2)
 const_f("CRM_INV3_F_HI", i3[0])
 const_f("CRM_INV3_F_LO", i3[1])
@@ -460,6 +468,11 @@ for a, div in ((1, 16), (2, 256), (3, 4096)):
         fx += limbs192(mp.power(2, mp.mpf(i) / div), 190)  # Q2.190
 arr_u64("CRM_EXP2_FX_T", fx, "2^(i/16), 2^(i/256), 2^(i/4096) (i = 0..15) as floor(v 2^190), 3 limbs each")
 arr_u64("CRM_LN2_FX", limbs192(LN2, 191), "ln 2 as floor(ln2 2^191)")
+# constants of the exact tiers of binary64 e^x, 10^x (x log2 b) and log2, log10 (ln x / ln b)
+arr_u64("CRM_LOG2E_FX", limbs192(LOG2E, 190), "log2 e as floor(log2(e) 2^190)")
+arr_u64("CRM_LOG2_10_FX", limbs192(LOG2_10, 189), "log2 10 as floor(log2(10) 2^189)")
+arr_u64("CRM_INV_LN2_FX", limbs192(1 / LN2, 190), "1/ln 2 as floor(2^190 / ln 2)")
+arr_u64("CRM_INV_LN10_FX", limbs192(1 / mp.log(10), 190), "1/ln 10 as floor(2^190 / ln 10)")
 lfx = []
 for j in range(128):
     lfx += limbs192(mp.log(1 + mp.mpf(j) / 128), 191)

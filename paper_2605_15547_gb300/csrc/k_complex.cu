@@ -68,7 +68,13 @@ template <int W> CRM_DEV float2 cx_eval(float x, float y, const unsigned char *s
     float s, r;
     uint32_t sb;
     exp_df_core<0>(x, (const float4 *)(sm + CXT_EXP), s, r, sb);
-    const int k = (int)(sb - fbits(CRM_SHIFTER_F)) >> 6;
+    int k = (int)(sb - fbits(CRM_SHIFTER_F)) >> 6;
+    if (k > 0) {  // scale e^x first (exactly): a tiny sin y then multiplies a large factor
+      const float p = bitsf((uint32_t)(k + 127) << 23);
+      s *= p;
+      r *= p;
+      k = 0;
+    }
     Pair<float> sn, cs;
     sincos_pairs(y, sm, sn, cs);
     out.x = pair_scaled(df_mul_raw({s, r}, cs), k);
@@ -95,12 +101,17 @@ template <int W> CRM_DEV float2 cx_eval(float x, float y, const unsigned char *s
     int m = 127 - (int)(fbits(mx) >> 23);  // mx 2^m in [1, 2)
     m = m > 60 ? 60 : (m < -60 ? -60 : m);
     const float sc = bitsf((uint32_t)(m + 127) << 23);
-    const float a = ax * sc, b = ay * sc;  // exact (b may lose bits below 2^-126: b^2 < 2^-250 s)
+    const float a = mx * sc, b = fminf(ax, ay) * sc;  // a >= b; exact (b may lose bits below 2^-126)
+    // the four words of a^2 + b^2 summed with error-free steps: near |z| = 1 the sum lies
+    // within 2^-24 of a power of two and its low part is the whole result
     const Pair<float> a2 = two_prod(a, a), b2 = two_prod(b, b);
-    Pair<float> s = fast_two_sum(a2.hi, b2.hi);  // a2 >= b2
-    s.lo = s.lo + (a2.lo + b2.lo);
+    const Pair<float> hh = fast_two_sum(a2.hi, b2.hi);  // a2 >= b2
+    const Pair<float> ll = two_sum(a2.lo, b2.lo);
+    const Pair<float> m2 = two_sum(hh.lo, ll.hi);
+    Pair<float> s = fast_two_sum(hh.hi, m2.hi);
+    s.lo = s.lo + (m2.lo + ll.lo);
     s = fast_two_sum(s.hi, s.lo);
-    const Pair<float> L = log_df_core<3>(s.hi, -2 * m, s.lo, false, 0.0f, (const float4 *)(sm + CXT_LOG));
+    const Pair<float> L = log_df_core<3, true>(s.hi, -2 * m, s.lo, false, 0.0f, (const float4 *)(sm + CXT_LOG));
     out.x = 0.5f * (L.hi + L.lo);
     // atan2(y, x): the atan(a/b) core on (|y|, |x|), pi minus it for x < 0, the sign of y
     Pair<float> t = atan_ratio_df({ay, 0.0f}, {ax, 0.0f}, (const float2 *)(sm + CXT_ATAN));

@@ -21,9 +21,10 @@ import numpy as np
 FUNCS = [
     "expf", "exp2f", "exp10f", "expm1f", "logf", "log2f", "log10f", "log1pf", "sinf",
     "cosf", "sincosf", "tanf", "asinf", "acosf", "atanf", "sinhf", "coshf", "tanhf",
-    "rsqrtf", "exp2", "log",
+    "rsqrtf", "exp2", "log", "exp", "log2", "log10", "exp10",
 ]
 F32_FUNCS = FUNCS[:19]
+F64_FUNCS = FUNCS[19:]
 
 # Inputs whose results are finite and not trivially saturated (open intervals).
 DOMAIN_F32 = {
@@ -199,9 +200,11 @@ def bench_arrays(workload: str, scale: int = 0):
     if workload == "f64":
         n = (1 << 26) >> scale
         return [("exp2:domain", "exp2", n), ("exp2:u20", "exp2", n), ("log:bits", "log", n),
-                ("log:u0.125_8", "log", n)], {
-            "workload": f"binary64 exp2 and log x 2^{26 - scale}: exp2 U(-1075,1024) and U[-20,20]; "
-                        "log uniform positive finite bit patterns and U[0.125,8]", "elems_per_array": n}
+                ("log:u0.125_8", "log", n), ("exp:edomain", "exp", n), ("log2:bits", "log2", n),
+                ("log10:bits", "log10", n), ("exp10:tdomain", "exp10", n)], {
+            "workload": f"binary64 x 2^{26 - scale}: exp2 U(-1075,1024) and U[-20,20]; log uniform positive "
+                        "finite bit patterns and U[0.125,8]; exp U(-745,710), exp10 U(-324,309), log2 and "
+                        "log10 positive finite bit patterns", "elems_per_array": n}
     raise ValueError(f"unknown workload {workload}")
 
 
@@ -211,7 +214,8 @@ def _set_of(label: str) -> str:
 
 def bench_seed(workload: str, label: str, func: str) -> int:
     cfg = {"all19": 2, "precision": 3, "f64": 5}[workload]
-    salt = {"domain": 0, "u10": 0, "log": 1, "large": 2, "u20": 1, "bits": 0, "u0.125_8": 1}[_set_of(label)]
+    salt = {"domain": 0, "u10": 0, "log": 1, "large": 2, "u20": 1, "bits": 0, "u0.125_8": 1, "edomain": 0,
+            "tdomain": 0}[_set_of(label)]
     return seed_for(cfg, func) + 0x100000000 * salt
 
 
@@ -228,6 +232,10 @@ def bench_input_host(workload: str, label: str, func: str, n: int) -> np.ndarray
         return sinf_with_large(n, rng, frac=0.05)
     if kind == "domain":
         return f64_uniform(-1075.0, 1024.0, n, rng)
+    if kind == "edomain":
+        return f64_uniform(-745.0, 710.0, n, rng)
+    if kind == "tdomain":
+        return f64_uniform(-324.0, 309.0, n, rng)
     if kind == "u20":
         return f64_uniform(-20.0, 20.0, n, rng)
     if kind == "bits":
@@ -272,6 +280,10 @@ def bench_input_device(workload: str, label: str, func: str, n: int, device="cud
         return x
     if kind == "domain":
         return u(-1075.0, 1024.0)
+    if kind == "edomain":
+        return u(-745.0, 710.0)
+    if kind == "tdomain":
+        return u(-324.0, 309.0)
     if kind == "u20":
         return u(-20.0, 20.0)
     if kind == "bits":

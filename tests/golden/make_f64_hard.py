@@ -1,4 +1,5 @@
-"""Writes tests/golden/f64_hard/<func>.txt: binary64 inputs of exp2 and log whose results
+"""Writes tests/golden/f64_hard/<func>.txt: binary64 inputs of exp2, log (and of exp, log2,
+log10, exp10) whose results
 lie closest to a rounding boundary (a midpoint between two binary64 numbers), selected by
 the oracle alone.
 
@@ -100,13 +101,40 @@ def log_candidates(rng):
     return x[np.isfinite(x) & (x > 0)]
 
 
+def exp_candidates(rng, hi, lo, lnb):
+    """b^x: near 0, where b^x = 1 + x ln b + ... sits next to the midpoints 1 + (j + 1/2) 2^-52
+    and 1 - (j + 1/2) 2^-53 for x ~ (j + 1/2) 2^-52 / ln b (and neighbours); near the range
+    ends, uniform, near integers"""
+    j = np.floor(np.exp2(rng.uniform(0, 24, 40000))) - 1
+    j = np.concatenate([np.arange(0, 512), j])
+    parts = [neighbours((j + 0.5) * 2.0 ** -52 / lnb, 64, rng, 40), neighbours(-(j + 0.5) * 2.0 ** -53 / lnb, 64, rng, 40)]
+    parts += [rng.uniform(lo, hi, 2_000_000), rng.uniform(-20.0, 20.0, 1_500_000),
+             np.where(rng.integers(0, 2, 1_000_000) == 1, 1.0, -1.0) * np.exp2(rng.uniform(-80, -1, 1_000_000)),
+             rng.uniform(hi - 8.0, hi, 500_000), rng.uniform(lo, lo + 30.0, 500_000)]
+    k = rng.integers(int(lo), int(hi), 1_000_000).astype(np.float64)
+    i = np.round(rng.uniform(-1, 1, k.size) * np.exp2(rng.uniform(0, 30, k.size)))
+    parts.append(k + i * np.spacing(np.maximum(np.abs(k), 1.0)))
+    return np.concatenate(parts)
+
+
+def logb_candidates(rng):
+    """log2, log10: the log families (near 1, near powers of two, bit patterns)"""
+    return log_candidates(rng)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--keep", type=int, default=10000)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--funcs", default="", help="comma list (default: all)")
     args = ap.parse_args()
     os.makedirs(OUT_DIR, exist_ok=True)
-    for func, gen in (("exp2", exp2_candidates), ("log", log_candidates)):
+    gens = (("exp2", exp2_candidates), ("log", log_candidates),
+            ("exp", lambda r: exp_candidates(r, 709.7, -745.0, 1.0)), ("log2", logb_candidates),
+            ("log10", logb_candidates), ("exp10", lambda r: exp_candidates(r, 308.2, -323.5, math.log(10.0))))
+    for func, gen in gens:
+        if args.funcs and func not in args.funcs.split(","):
+            continue
         seed = 0xC0DE0500 + O.FUNC_ID[func]
         rng = np.random.Generator(np.random.PCG64(seed))
         xb = np.unique(_bits(gen(rng)))

@@ -67,7 +67,8 @@ def mp_func(name):
         "log10f": m.log10, "log1pf": m.log1p, "sinf": m.sin, "cosf": m.cos, "tanf": m.tan,
         "asinf": m.asin, "acosf": m.acos, "atanf": m.atan, "sinhf": m.sinh, "coshf": m.cosh,
         "tanhf": m.tanh, "rsqrtf": lambda x: 1 / m.sqrt(x), "exp2": lambda x: m.power(2, x),
-        "log": m.log,
+        "log": m.log, "exp": m.exp, "log2": lambda x: m.log(x) / m.log(2), "log10": m.log10,
+        "exp10": lambda x: m.power(10, x),
     }
     return table[name]
 
@@ -211,6 +212,23 @@ def test_f64_log_matches_mpmath():
                         1.0 + rng.uniform(-1e-6, 1e-6, 100)])
     xb = f64bits(x)
     assert np.array_equal(O.eval_bits("log", xb), reference_bits("log", xb, F64))
+
+
+@pytest.mark.parametrize("name", ["exp", "log2", "log10", "exp10"])
+def test_f64_more_functions_match_mpmath(name):
+    rng = np.random.default_rng(33 + len(name))
+    if name.startswith("exp"):
+        hi = 709.8 if name == "exp" else 308.3
+        x = np.concatenate([rng.uniform(-hi * 1.05, hi, 400), rng.uniform(-5, 5, 200),
+                            rng.uniform(-1, 1, 100) * np.exp2(rng.uniform(-80, -1, 100)),
+                            np.array([0.0, -0.0, 1.0, -1.0, 22.0, 23.0, -746.0, 710.0, 1e-300])])
+    else:
+        bits = rng.integers(1, 0x7FF0000000000000, 400, dtype=np.uint64)
+        x = np.concatenate([bits.view(np.float64), rng.uniform(0.125, 8.0, 200),
+                            1.0 + rng.uniform(-1e-6, 1e-6, 100), np.exp2(np.arange(-1074, 1024, 97.0)),
+                            10.0 ** np.arange(0, 23), np.array([5e-324, 1.7976931348623157e308, 1.0])])
+    xb = f64bits(x)
+    assert np.array_equal(O.eval_bits(name, xb), reference_bits(name, xb, F64))
 
 
 # ----------------------------------------------------------------------------------

@@ -109,6 +109,12 @@ template <int KIND> struct FnTrig {
                     h, sg);
   }
   CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { trig_slow<KIND>(x, y, u, f, sg); }
+  // warp-uniform choice of the double-float reduction (see trig_reduce_df)
+  CRM_DEV static bool path_ok(float x) { return trig_cw_ok(x); }
+  template <int FORM, int PATH> CRM_DEV static void eval_path(float x, const void *sm, float *y, bool &h) {
+    const unsigned char *b = (const unsigned char *)sm;
+    trig_df<KIND, PATH>(x, (const uint4 *)(b + OFF_PW), (const float4 *)(b + 64), (const float2 *)(b + OFF_TT), y, h);
+  }
 };
 
 template <int KIND> struct FnAtrig {

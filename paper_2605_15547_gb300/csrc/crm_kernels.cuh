@@ -188,20 +188,45 @@ __device__ __noinline__ void slow_store(typename Fn::T x, uint64_t i, const KArg
 // Evaluates the W elements of one vector: y0 (and y1 for two outputs) and the hard
 // flags; returns whether any lane of the vector is hard (the flags stay predicates, the
 // queue mask is built from them only on the rare path, hard_mask).
-template <class Fn, int FORM, class V, class C>
-CRM_DEV bool eval_vec(const V &xv, const C &sm, V &y0, V &y1, bool *h) {
+// An Fn with two ways to evaluate its fast tier, one valid only for some arguments
+// (path_ok) and cheaper, declares path_ok and eval_path<FORM, PATH> (PATH 1: the cheaper
+// way, every lane of the warp having passed path_ok; PATH 2: the general way): eval_vec
+// then takes one warp vote per vector and evaluates the whole vector on one path.
+template <class Fn, class = void> struct HasPaths : std::false_type {};
+template <class Fn> struct HasPaths<Fn, std::void_t<decltype(Fn::path_ok(typename Fn::T()))>> : std::true_type {};
+
+template <class Fn, int FORM, int PATH, class V, class C>
+CRM_DEV bool eval_vec_on(const V &xv, const C &sm, V &y0, V &y1, bool *h) {
   using T = typename Fn::T;
   constexpr int W = sizeof(V) / sizeof(T);
   bool any = false;
 #pragma unroll
   for (int j = 0; j < W; j++) {
     T y[2];
-    Fn::template eval<FORM>(vget(xv, j), sm, y, h[j]);
+    if constexpr (PATH == 0)
+      Fn::template eval<FORM>(vget(xv, j), sm, y, h[j]);
+    else
+      Fn::template eval_path<FORM, PATH>(vget(xv, j), sm, y, h[j]);
     any = any || h[j];
     vset(y0, j, y[0]);
     if (Fn::NOUT == 2) vset(y1, j, y[1]);
   }
   return any;
+}
+// Called by whole warps (the vector loops keep every lane of a warp together).
+template <class Fn, int FORM, class V, class C>
+CRM_DEV bool eval_vec(const V &xv, const C &sm, V &y0, V &y1, bool *h) {
+  if constexpr (HasPaths<Fn>::value && FORM != 1) {
+    using T = typename Fn::T;
+    constexpr int W = sizeof(V) / sizeof(T);
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < W; j++) ok = ok && Fn::path_ok(vget(xv, j));
+    if (__all_sync(0xFFFFFFFFu, ok)) return eval_vec_on<Fn, FORM, 1>(xv, sm, y0, y1, h);
+    return eval_vec_on<Fn, FORM, 2>(xv, sm, y0, y1, h);
+  } else {
+    return eval_vec_on<Fn, FORM, 0>(xv, sm, y0, y1, h);
+  }
 }
 template <int W> CRM_DEV unsigned hard_mask(const bool *h, bool force) {
   unsigned hm = 0;

@@ -1,11 +1,13 @@
 // fam_trig.cuh -- sinf, cosf, sincosf, tanf.
 //
-// Reduction (every |x| >= 2^-6): an integer Payne-Hanek step on the 24-bit significand.
-// With x = M 2^e, the bits of 2/pi that can change |x| 64/pi modulo 128 form a window
-// selected by e (the paper reduces large trigonometric arguments on a separate branch,
-// Sec. II.A; here one branch-free integer path serves all magnitudes):
-//     |x| 64/pi = 128 m + 32 q + j + f,   q = quadrant, j in [0,32), |f| <= 1/2,
-// obtained from M times a 96-bit (fast tiers) or 160-bit (slow tier) window of 2/pi.
+// Reduction: |x| 64/pi = 128 m + 32 q + j + f,  q = quadrant, j in [0,32), |f| <= 1/2.
+// The paper reduces large trigonometric arguments on a separate branch (Sec. II.A).  Here
+// the double-float tier takes a Cody-Waite reduction in float pairs when every active
+// lane of the warp has |x| < 2^12 (a warp-uniform vote), and otherwise an integer
+// Payne-Hanek step on the 24-bit significand, which serves every magnitude: with
+// x = M 2^e, the bits of 2/pi that can change |x| 64/pi modulo 128 form a window selected
+// by e, and M times a 96-bit (fast tiers) or 160-bit (slow tier) window of 2/pi gives
+// q, j and f.  The FP64 and slow tiers always use the integer step.
 // Then t = f pi/64 (|t| <= pi/128) and, with S_j = sin(j pi/64), C_j = cos(j pi/64),
 //     sin(j pi/64 + t) = S_j cos t + C_j sin t,   cos(j pi/64 + t) = C_j cos t - S_j sin t,
 // rotated by the quadrant.  |x| < 2^-6 uses t = x, j = q = 0 directly.
@@ -174,10 +176,52 @@ struct TrigF {
   bool tiny;
 };
 
+// Cody-Waite reduction for |x| < 2^12 (the paper's reduction for moderate arguments,
+// Sec. II.A): k = rint(|x| RN(64/pi)) by the shifter, N7 = k mod 128 from its bits, and
+// t = |x| - k pi/64 with pi/64 = C1 + C2 + C3 (three floats, + < 2^-81):
+//   t1 = |x| - k C1 is exact (one FMA: k C1 and |x| are multiples of 2^-29 and
+//        |t1| < 2^-5, so t1 has at most 24 significant bits),
+//   k C2 = ph + pl exactly (FMA split), (sh, sl) = TwoSum(t1, -ph) exactly,
+//   t = sh + RN(RN(sl - pl) - k C3), normalised by Fast2Sum.
+// |x| RN(64/pi) is within |x| 2^-20 <= 2^-8 of |x| 64/pi, so |t| <= (1/2 + 2^-8) pi/64.
+// With k < 2^16.35: |k C2| < 2^-13.1, |pl| < 2^-37.1, |k C3| < 2^-37.7, so the low word's
+// two roundings and the split's remainder cost < 2^-59.5 absolute plus 2^-47 |t|.  The
+// result is at least sin(pi/64) cos(pi/128) > 2^-4.4 unless j = 0, so this is < 2^-47
+// relative there; with j = 0 (k a nonzero multiple of 32, x near a multiple of pi/2) the
+// result is as small as t, and lanes with |t| < 2^-19 (error above 2^-40 of t) are flagged
+// for the slow path.
+CRM_DEV void trig_reduce_cw(float ax, Pair<float> &t, int &N7, bool &tiny) {
+  const float ks = fma_(ax, CRM_64OPI_F, CRM_SHIFTER_F);
+  const float k = ks - CRM_SHIFTER_F;
+  N7 = (int)(fbits(ks) & 127u);  // 1.5 2^23 + k, k < 2^22: the low bits are k
+  const float t1 = fma_(-k, CRM_PIO64_CW1, ax);
+  const float ph = k * CRM_PIO64_CW2;
+  const float pl = fma_(k, CRM_PIO64_CW2, -ph);
+  const Pair<float> s = two_sum(t1, -ph);
+  t = fast_two_sum(s.hi, fma_(-k, CRM_PIO64_CW3, s.lo - pl));
+  tiny = (N7 & 31) == 0 && k != 0.0f && fabsf(s.hi) < 0x1p-19f;
+}
+
+// Whether a lane may take the Cody-Waite reduction: |x| < 2^12 (NaN and infinities, rare,
+// send their vector to the general reduction).
+CRM_DEV bool trig_cw_ok(float x) { return fabsf(x) < 0x1p12f; }
+
 // The reduction shared by the double-float evaluators: t = f pi/64 as an unnormalised
-// pair, N7 = (32 q + j) mod 128, and tiny (j = 0 and |f| < 2^-24: slow path).
+// pair, N7 = (32 q + j) mod 128, and tiny (j = 0 and t too small for the reduction's
+// accuracy: slow path).  PATH 1: Cody-Waite (about 20 operations; the caller has checked
+// trig_cw_ok for every lane of the warp); PATH 2: the integer Payne-Hanek reduction below
+// (about 50), which serves every |x|; PATH 0: Cody-Waite when every active lane of the
+// warp has |x| < 2^12 (a vote per element), else Payne-Hanek.  Both reductions are correct
+// for any lane that takes them, so the choice decides speed only.  The main kernels vote
+// once per vector of elements and pass PATH 1 or 2 (a branch per element would keep the
+// compiler from interleaving the elements of a vector).
+template <int PATH = 0>
 CRM_DEV void trig_reduce_df(float x, const uint4 *PW, Pair<float> &t, int &N7, bool &tiny) {
   float ax = fabsf(x);
+  if (PATH == 1 || (PATH == 0 && __all_sync(__activemask(), ax < 0x1p12f))) {
+    trig_reduce_cw(ax, t, N7, tiny);
+    return;
+  }
   bool small = ax < 0x1p-6f;
   uint32_t r[4];
   trig_window_mul3(small ? 1.0f : ax, PW, r);
@@ -214,11 +258,11 @@ CRM_DEV void trig_reduce_df(float x, const uint4 *PW, Pair<float> &t, int &N7, b
 
 // KIND = TRIG_SIN or TRIG_COS: only the rotation term the quadrant needs is formed, in R.A
 // (sin: B when q is odd, else A; cos: A when q is odd, else B); otherwise both.
-template <int KIND> CRM_DEV TrigF trig_df_core(float x, const uint4 *PW, const float4 *SC) {
+template <int KIND, int PATH = 0> CRM_DEV TrigF trig_df_core(float x, const uint4 *PW, const float4 *SC) {
   Pair<float> t;
   int N7;
   TrigF R;
-  trig_reduce_df(x, PW, t, N7, R.tiny);
+  trig_reduce_df<PATH>(x, PW, t, N7, R.tiny);
   // t^2 as a pair
   float u = t.hi * t.hi;
   float ul = fma_(t.hi, t.hi, -u);
@@ -272,7 +316,9 @@ template <int KIND> CRM_DEV TrigF trig_df_core(float x, const uint4 *PW, const f
 // below 2^-48 of t).  N: T >= tan(pi/64) > |tau| for j >= 1 (T = 0 for j = 0), so
 // Fast2Sum applies and N cancels by at most a factor 2; D: |T tau| <= tan(31 pi/64)
 // tan(pi/128) < 1/2, so D lies in [1/2, 3/2] and 1 - T tau is a Fast2Sum.  Both are
-// normalised for the pair division.  Error budget, relative to the result: tau 2^-45,
+// normalised for the pair division.  (The Cody-Waite reduction allows |t| up to
+// (1/2 + 2^-8) pi/64: then |T tau| < 0.504 and D > 0.496, which changes none of the
+// bounds below.)  Error budget, relative to the result: tau 2^-45,
 // T 2^-48, N (doubled by its cancellation) 2^-43.8, D 2^-44, the division 2^-43, the
 // reduction as for sin and cos: total < 2^-41.5, inside the rounding test's 2^-37.
 CRM_DEV Pair<float> tan_df_nd(Pair<float> t, int j, const float2 *TT, Pair<float> &D) {
@@ -310,7 +356,7 @@ CRM_DEV uint32_t trig_cos_sign(int q) { return ((uint32_t)(q + 1) << 30) & 0x800
 // the floats gives the same bits as rotating the pairs first.
 // With sg (two entries for sincosf): the sign of f(x) - y for each result, turned with the
 // result's sign; the special results are exact (NaN, +-0).
-template <int KIND>
+template <int KIND, int PATH = 0>
 CRM_DEV void trig_df(float x, const uint4 *PW, const float4 *SC, const float2 *TT, float *y, bool &hard,
                      int *sg = nullptr) {
   if (sg && fabsf(x) < 0x1p-12f) {  // sin x, tan x within x^3/3 of x, cos x within x^2/2 of 1
@@ -329,7 +375,7 @@ CRM_DEV void trig_df(float x, const uint4 *PW, const float4 *SC, const float2 *T
     Pair<float> t, D;
     int N7;
     bool tiny;
-    trig_reduce_df(sp ? 1.0f : x, PW, t, N7, tiny);
+    trig_reduce_df<PATH>(sp ? 1.0f : x, PW, t, N7, tiny);
     const Pair<float> N = tan_df_nd(t, N7 & 31, TT, D);
     const bool odd = (N7 & 32) != 0;
     const Pair<float> q = df_div_raw(odd ? D : N, odd ? N : D);
@@ -349,7 +395,7 @@ CRM_DEV void trig_df(float x, const uint4 *PW, const float4 *SC, const float2 *T
     y[0] = zero ? x : bitsf(fbits(yt) ^ sgb);
     return;
   }
-  TrigF R = trig_df_core<KIND>(sp ? 1.0f : x, PW, SC);
+  TrigF R = trig_df_core<KIND, PATH>(sp ? 1.0f : x, PW, SC);
   if (__builtin_expect(sp, 0)) {
     hard = false;
     const float r = x != x ? qnan_of(x) : CRM_QNAN_F;

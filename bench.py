@@ -46,16 +46,16 @@ FALLBACK_HBM_GBS = 6800.0
 
 
 # DRAM traffic per element (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture
-# of the function's main kernel, divided by the elements of that launch), with the
-# fingerprint of the kernel sources it was taken on; a traffic figure is reported only
-# while the sources still match (profiles/ holds the captures).
-TRAFFIC_BYTES_PER_ELEM = {"expf": 6.642, "exp2f": 6.652, "exp10f": 6.662, "expm1f": 6.677,
-                          "logf": 6.641, "log2f": 6.674, "log10f": 6.635, "log1pf": 6.682,
-                          "sinf": 6.763, "cosf": 6.774, "sincosf": 10.872, "tanf": 6.847,
-                          "asinf": 6.71, "acosf": 6.731, "atanf": 6.735, "sinhf": 6.683,
-                          "coshf": 6.679, "tanhf": 6.711, "rsqrtf": 6.482, "exp2": 14.487,
-                          "log": 14.471}
-TRAFFIC_SOURCES = "38247a7c890413be"  # the kernel sources the ncu captures were taken on
+# of the function's main kernel on 2^25 inputs -- binary32 domain bit patterns in launch
+# shape 9, binary64 the domain / bit-pattern arrays in shape 1 -- divided by the elements of
+# that launch), with the fingerprint of the kernel sources it was taken on; a
+# traffic figure is reported only while the sources still match.
+TRAFFIC_BYTES_PER_ELEM = {"expf": 7.057, "exp2f": 7.017, "exp10f": 7.069, "expm1f": 7.05, "logf": 7.059,
+                          "log2f": 7.076, "log10f": 7.073, "log1pf": 7.066, "sinf": 7.175, "cosf": 7.16,
+                          "sincosf": 10.957, "tanf": 7.295, "asinf": 7.187, "acosf": 7.185, "atanf": 7.211,
+                          "sinhf": 7.061, "coshf": 7.087, "tanhf": 7.151, "rsqrtf": 6.588, "exp2": 14.549,
+                          "log": 14.54, "exp": 14.519, "exp10": 14.519, "log2": 14.55, "log10": 14.534}
+TRAFFIC_SOURCES = "aa4f8a1d4cb6a55a"  # the kernel sources the ncu captures were taken on
 
 
 def kernel_sources_fingerprint() -> str:
@@ -76,14 +76,14 @@ def measured_traffic(func: str, n: int):
 
 
 # Thread instructions per element of each function's main kernel (smsp__inst_executed.sum x 32
-# / elements, one ncu capture per function on 2^25 domain inputs), gated by the same source
+# / elements, from the same captures as the traffic figures), gated by the same source
 # fingerprint as the traffic figures.  The kernels are bound by instruction issue, not by
 # DRAM: 152 SMs x 4 schedulers issue one warp instruction each per cycle.
-INST_PER_ELEM = {"expf": 56.5, "exp2f": 48.8, "exp10f": 57.3, "expm1f": 89.6, "logf": 74.6,
-                 "log2f": 74.2, "log10f": 73.9, "log1pf": 82.2, "sinf": 130.0, "cosf": 124.9,
-                 "sincosf": 151.5, "tanf": 143.5, "asinf": 137.6, "acosf": 143.9, "atanf": 108.0,
-                 "sinhf": 126.9, "coshf": 89.6, "tanhf": 116.2, "rsqrtf": 67.8, "exp2": 194.5,
-                 "log": 415.0}
+INST_PER_ELEM = {"expf": 55.1, "exp2f": 47.2, "exp10f": 56.1, "expm1f": 87.1, "logf": 73.2,
+                 "log2f": 72.0, "log10f": 71.8, "log1pf": 80.2, "sinf": 129.0, "cosf": 122.4,
+                 "sincosf": 147.7, "tanf": 142.0, "asinf": 135.4, "acosf": 142.2, "atanf": 105.8,
+                 "sinhf": 124.7, "coshf": 87.4, "tanhf": 113.9, "rsqrtf": 67.5, "exp2": 210.3,
+                 "log": 388.5, "exp": 226.8, "exp10": 226.8, "log2": 457.4, "log10": 459.3}
 SMS, SCHEDULERS_PER_SM, WARP = 152, 4, 32
 
 

@@ -101,3 +101,36 @@ def test_noalloc_rejects_oversized_calls(lib):
                               ctypes.c_void_p(y.data_ptr()), MAX_ELEMS + 1, _stream())
     assert st == CRM_ERR_SIZE
     assert b"CRM_NOALLOC_MAX_ELEMS" in lib.crm_status_str(st)
+
+
+def test_noalloc_under_graph_capture(lib):
+    """The entry point's reason to exist: a call recorded in a CUDA graph (global capture
+    mode, where allocation is prohibited) and replayed on new inputs gives crm_eval_form's
+    bits; an uncaptured call leaves the device's free memory unchanged."""
+    n = 300001
+    x = _inputs("expf", n, 77)
+    y = torch.empty_like(x)
+
+    def call(stream):
+        return lib.crm_eval_noalloc(0, CRM_F32, 0, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                    n, stream)
+
+    assert call(_stream()) == 0  # the first call on the device, before any capture
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert call(_stream()) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        st = call(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    for seed in (78, 79):
+        x.copy_(_inputs("expf", n, seed))
+        y.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        want = _run(lib, "form", 0, 0, x, 1)
+        assert np.array_equal(y.cpu().numpy().view(np.uint32), want), seed

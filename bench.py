@@ -50,12 +50,12 @@ FALLBACK_HBM_GBS = 6800.0
 # shape 9, binary64 the domain / bit-pattern arrays in shape 1 -- divided by the elements of
 # that launch), with the fingerprint of the kernel sources it was taken on; a
 # traffic figure is reported only while the sources still match.
-TRAFFIC_BYTES_PER_ELEM = {"expf": 7.057, "exp2f": 7.017, "exp10f": 7.069, "expm1f": 7.05, "logf": 7.059,
-                          "log2f": 7.076, "log10f": 7.073, "log1pf": 7.066, "sinf": 7.175, "cosf": 7.16,
-                          "sincosf": 10.957, "tanf": 7.295, "asinf": 7.187, "acosf": 7.185, "atanf": 7.211,
-                          "sinhf": 7.061, "coshf": 7.087, "tanhf": 7.151, "rsqrtf": 6.588, "exp2": 14.549,
-                          "log": 14.54, "exp": 14.519, "exp10": 14.519, "log2": 14.55, "log10": 14.534}
-TRAFFIC_SOURCES = "aa4f8a1d4cb6a55a"  # the kernel sources the ncu captures were taken on
+TRAFFIC_BYTES_PER_ELEM = {"expf": 7.056, "exp2f": 7.01, "exp10f": 7.066, "expm1f": 7.043, "logf": 7.059,
+                          "log2f": 7.08, "log10f": 7.072, "log1pf": 7.061, "sinf": 7.177, "cosf": 7.147,
+                          "sincosf": 10.956, "tanf": 7.291, "asinf": 7.187, "acosf": 7.186, "atanf": 7.211,
+                          "sinhf": 7.065, "coshf": 7.101, "tanhf": 7.154, "rsqrtf": 6.599, "exp2": 14.546,
+                          "log": 14.536, "exp": 14.527, "exp10": 14.531, "log2": 14.549, "log10": 14.545}
+TRAFFIC_SOURCES = "507dc5b643487212"  # the kernel sources the ncu captures were taken on
 
 
 def kernel_sources_fingerprint() -> str:
@@ -92,10 +92,22 @@ def issue_peak_tinst_s(sm_mhz: float) -> float:
     return SMS * SCHEDULERS_PER_SM * WARP * sm_mhz * 1e6 / 1e12
 
 
-def inst_per_elem(func: str):
-    if func not in INST_PER_ELEM or kernel_sources_fingerprint() != TRAFFIC_SOURCES:
+# The instruction count depends on the data (the branch, and for the trigonometric
+# functions the reduction, each element takes): the arrays of the other workloads have their
+# own captures (2^25 elements of each, the binary32 ones in launch shape 9), keyed by label.
+INST_PER_ELEM_SET = {"exp2:domain": 210.3, "exp2:u20": 192.8, "log:bits": 388.5, "log:u0.125_8": 415.0,
+                     "exp:edomain": 226.8, "log2:bits": 457.4, "log10:bits": 459.3, "exp10:tdomain": 226.8,
+                     "expf:u10": 49.0, "expf:log": 62.8, "logf:u10": 82.0, "logf:log": 71.3,
+                     "sinf:u10": 98.8, "sinf:log": 128.6, "tanhf:u10": 119.0, "tanhf:log": 115.4,
+                     "rsqrtf:u10": 67.5, "rsqrtf:log": 65.1, "sinf:large": 129.8}
+
+
+def inst_per_elem(func: str, label: str = ""):
+    if kernel_sources_fingerprint() != TRAFFIC_SOURCES:
         return None
-    return INST_PER_ELEM[func]
+    if label in INST_PER_ELEM_SET:
+        return INST_PER_ELEM_SET[label]
+    return INST_PER_ELEM.get(func)
 
 
 def load_peaks():
@@ -369,7 +381,7 @@ def measure_set(args, crm, torch, dev, workload, reps=3):
         crm.eval_into(f, x, y, form=args.form)
         st = crm.stats()
         g = n / (ms / 1e3) / 1e9
-        ipe = inst_per_elem(f)
+        ipe = inst_per_elem(f, lab)
         out[lab] = {"gelem_s": g, "hbm_frac": g * bytes_per_elem(f) / peak,
                     "issue_frac": (g * ipe / 1e3 / issue_peak_tinst_s(2070.0)) if ipe else None,
                     "plain_gelem_s": (n / (ms_plain / 1e3) / 1e9) if ms_plain else None,

@@ -367,19 +367,16 @@ template <bool BF> CRM_DEV bool is_mid16(float a) {
 template <bool BF> CRM_DEV uint16_t round_to16(float a, int dir) {
   return BF ? round_to_bf16(a, dir) : round_to_f16(a, dir);
 }
-// 16-bit result in mode rm from (c, sg)
+// 16-bit result in mode rm from (c, sg), c within one binary32 ulp of v = f(x).  Directed:
+// round RD32(v) down or RU32(v) up.  To nearest: the format's midpoints are binary32
+// numbers, so none lies strictly between v and c; RN16(v) = RN16(c) unless c is a
+// midpoint, where sg says on which side v lies (sg = 0: v = c, ties to even).
 template <bool BF> CRM_DEV uint16_t finish_16(float c, int sg, int rm) {
   if (c != c) return round_to16<BF>(c, 2);
-  const float a = rd32(c, sg), b = ru32(c, sg);
   const bool neg = v_negative(c, sg);
-  if (rm == CRM_RM_RD || (rm == CRM_RM_RZ && !neg)) return round_to16<BF>(a, -1);
-  if (rm == CRM_RM_RU || rm == CRM_RM_RZ) return round_to16<BF>(b, 1);
-  const uint16_t ra = round_to16<BF>(a, 2);
-  if (a == b) return ra;
-  const uint16_t rb = round_to16<BF>(b, 2);
-  if (ra == rb) return ra;
-  // a midpoint M of the format is a or b: v > a = M rounds like b, v < b = M like a
-  return is_mid16<BF>(a) ? rb : ra;
+  if (rm == CRM_RM_RD || (rm == CRM_RM_RZ && !neg)) return round_to16<BF>(rd32(c, sg), -1);
+  if (rm == CRM_RM_RU || rm == CRM_RM_RZ) return round_to16<BF>(ru32(c, sg), 1);
+  return round_to16<BF>(c, (sg != 0 && is_mid16<BF>(c)) ? sg : 2);
 }
 // 16-bit input to binary32 (exact)
 template <bool BF> CRM_DEV float from16(uint16_t h) {

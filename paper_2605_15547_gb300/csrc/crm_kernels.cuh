@@ -619,32 +619,100 @@ __device__ __noinline__ void dir_slow_store(typename Fn::T x, uint64_t i, const 
 
 constexpr int DIR_UNROLL = 4;
 
+// One element in a directed mode: candidate, signs and hard flag.
+template <class Fn>
+CRM_DEV bool dir_eval(typename Fn::T x, const unsigned char *sm, typename Fn::T *y, int *sg, const KArgs &a) {
+  bool h;
+  sg[0] = sg[1] = 0;
+  Fn::template eval<2>(x, sm, y, h, sg);
+  return h || a.force_hard;
+}
+
+// Binary32 / binary64 results: 16-byte vectors [head, head + W nvec) of the array (the
+// geometry of k_main), one vector per thread per step with the next one loaded ahead;
+// every element's (candidate, sign) goes through the finisher, hard lanes are queued
+// (their stored value is replaced by k_dir_slow).  The scalar loop takes the head and the
+// tail, and the whole array for the 16-bit formats (nvec = 0).
 template <class Fn>
 __global__ void __launch_bounds__(KBLOCK) k_dir(KArgs a) {
   using T = typename Fn::T;
+  using V = typename VecOf<T, false>::V;
+  constexpr int W = VecOf<T, false>::W;
   __shared__ __align__(16) unsigned char sm[(Fn::template tab_bytes<2>() > 0) ? Fn::template tab_bytes<2>() : 16];
   load_tab<Fn, 2>(sm);
-  const uint64_t stride = (uint64_t)gridDim.x * KBLOCK * DIR_UNROLL;
-  for (uint64_t b = (uint64_t)blockIdx.x * KBLOCK * DIR_UNROLL; b < a.n; b += stride) {
+  const uint32_t stride = gridDim.x * (uint32_t)KBLOCK;
+  for (uint64_t seg = 0; seg < a.nvec; seg += KSEG) {
+    const uint32_t nv = (uint32_t)(a.nvec - seg < KSEG ? a.nvec - seg : KSEG);
+    const V *in4 = (const V *)((const T *)a.in + a.head) + seg;
+    V *out4 = (V *)((T *)a.out + a.head) + seg;
+    V *out4b = (V *)((T *)a.out + a.n + a.head) + seg;  // second output (sincos)
+    uint32_t base = blockIdx.x * (uint32_t)KBLOCK;
+    V xv = base + threadIdx.x < nv ? ld_stream(in4 + base + threadIdx.x) : V();
+    for (; base < nv; base += stride) {  // whole warps: base is block-uniform
+      const uint32_t v = base + threadIdx.x, vn = v + stride;
+      const V nx = vn < nv ? ld_stream(in4 + vn) : V();
+      const bool act = v < nv;
+      V y0, y1;
+      bool h[W];
+      bool any = false;
+#pragma unroll
+      for (int j = 0; j < W; j++) {
+        T y[2];
+        int sg[2];
+        h[j] = dir_eval<Fn>(vget(xv, j), sm, y, sg, a) && act;
+        any = any || h[j];
+        if constexpr (sizeof(T) == 4) {
+          vset(y0, j, finish_f32(y[0], sg[0], a.rm));
+          if (Fn::NOUT == 2) vset(y1, j, finish_f32(y[1], sg[1], a.rm));
+        } else {
+          vset(y0, j, finish_f64(y[0], sg[0], a.rm));
+        }
+      }
+      if (act) {
+        st_stream(out4 + v, y0);
+        if (Fn::NOUT == 2) st_stream(out4b + v, y1);
+      }
+      if (__any_sync(0xFFFFFFFFu, any)) {
+        const unsigned hm = hard_mask<W>(h, false);
+        uint64_t ii[W], xb[W];
+#pragma unroll
+        for (int j = 0; j < W; j++) {
+          ii[j] = a.head + (seg + v) * W + j;
+          xb[j] = xbits_of(vget(xv, j));
+        }
+        const unsigned over = push_hard<W>(hm, ii, xb, a);
+        if (over) {
+#pragma unroll
+          for (int j = 0; j < W; j++)
+            if ((over >> j) & 1u) dir_slow_store<Fn>(vget(xv, j), ii[j], a);
+        }
+      }
+      xv = nx;
+    }
+  }
+  // scalar part: the head [0, head) and the tail [head + W nvec, n)
+  const uint64_t tail0 = a.head + (uint64_t)W * a.nvec;
+  const uint64_t nscal = a.head + (a.n - tail0);
+  const uint64_t sstride = (uint64_t)gridDim.x * KBLOCK * DIR_UNROLL;
+  for (uint64_t b = (uint64_t)blockIdx.x * KBLOCK * DIR_UNROLL; b < nscal; b += sstride) {
     T xs[DIR_UNROLL];
+    uint64_t is[DIR_UNROLL];
 #pragma unroll
     for (int u = 0; u < DIR_UNROLL; u++) {
-      const uint64_t i = b + (uint64_t)u * KBLOCK + threadIdx.x;
-      xs[u] = i < a.n ? dir_load<T>(a, i) : T(0);
+      const uint64_t k = b + (uint64_t)u * KBLOCK + threadIdx.x;
+      is[u] = k < a.head ? k : tail0 + (k - a.head);
+      xs[u] = k < nscal ? dir_load<T>(a, is[u]) : T(0);
     }
 #pragma unroll
     for (int u = 0; u < DIR_UNROLL; u++) {
-      uint64_t i = b + (uint64_t)u * KBLOCK + threadIdx.x;
-      const bool act = i < a.n;
+      const bool act = b + (uint64_t)u * KBLOCK + threadIdx.x < nscal;
       T y[2];
-      int sg[2] = {0, 0};
-      bool h;
-      Fn::template eval<2>(xs[u], sm, y, h, sg);
-      h = (h || a.force_hard) && act;
-      if (act && !h) dir_store(a, i, y, sg, Fn::NOUT);
+      int sg[2];
+      const bool h = dir_eval<Fn>(xs[u], sm, y, sg, a) && act;
+      if (act && !h) dir_store(a, is[u], y, sg, Fn::NOUT);
       if (__any_sync(0xFFFFFFFFu, h)) {
         uint64_t xb = xbits_of(xs[u]);
-        if (push_hard<1>(h ? 1u : 0u, &i, &xb, a)) dir_slow_store<Fn>(xs[u], i, a);
+        if (push_hard<1>(h ? 1u : 0u, &is[u], &xb, a)) dir_slow_store<Fn>(xs[u], is[u], a);
       }
     }
   }

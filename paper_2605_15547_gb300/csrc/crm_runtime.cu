@@ -470,9 +470,16 @@ int crm_eval_rm(int func_id, int dtype, int rmode, const void *in, void *out, ui
   a.force_hard = g_force_slow;
   a.rm = rmode;
   a.fmt = dtype == CRM_F16 ? 1 : (dtype == CRM_BF16 ? 2 : 0);
+  // binary32 / binary64: 16-byte vectors between a scalar head and tail (k_main's
+  // geometry); the 16-bit formats: scalar elements only
+  if (a.fmt == 0) fill_geometry(fe, in, out, n, a, 16);
   const int sms = dev_sms();
-  const uint64_t per = (uint64_t)KBLOCK * DIR_UNROLL;
-  uint64_t want = (n + per - 1) / per;
+  const uint64_t W = dtype == CRM_F64 ? 2 : 4;
+  const uint64_t nscal = a.head + (n - a.head - W * a.nvec);
+  const uint64_t want_v = (a.nvec + KBLOCK - 1) / KBLOCK;
+  const uint64_t want_s = (nscal + (uint64_t)KBLOCK * DIR_UNROLL - 1) / ((uint64_t)KBLOCK * DIR_UNROLL);
+  uint64_t want = want_v > want_s ? want_v : want_s;
+  if (want == 0) want = 1;
   const uint64_t cap_blocks = (uint64_t)sms * blocks_per_sm(fe.dmain_sym, KBLOCK);
   const int grid = (int)(want < cap_blocks ? want : cap_blocks);
   cudaError_t e = cudaMemsetAsync(a.qcount, 0, CRM_NSUBQ * CRM_SUBQ_STRIDE * 8, s);

@@ -162,7 +162,18 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
     // the exponent increment (N >> 6) << 23: sb >> 6 is N >> 6 plus 0x12D0000 (borrow
     // included), whose shift by 23 vanishes modulo 2^32
     const float y = round_df(s, r, hard, sg);
-    return bitsf(fbits(y) + ((sb >> 6) << 23));
+    const float out = bitsf(fbits(y) + ((sb >> 6) << 23));
+    // e^x lies above 1 + x for x != 0 by x^2/2 + ..., which for |x| < 2^-12 is below the
+    // error bound when x is small; when 1 + x is a binary32 number and the candidate, f(x)
+    // is decided above it (arguments with few significant bits, e.g. binary16 inputs)
+    if (KIND == 0 && sg && hard && fabsf(x) < 0x1p-12f) {
+      const float u = 1.0f + x;
+      if (u - 1.0f == x && out == u) {
+        hard = false;
+        *sg = 1;
+      }
+    }
+    return out;
   }
   // Out of range (rare): +inf, +0, a quiet NaN, or a subnormal result.
   hard = false;

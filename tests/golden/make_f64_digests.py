@@ -1,14 +1,15 @@
 """Writes tests/golden/f64_full/<label>.txt: digests of the oracle's results on every
-element of the four binary64 workload arrays (2^26 inputs each: exp2 uniform on
+element of the eight binary64 workload arrays (2^26 inputs each: exp2 uniform on
 (-1075, 1024) and on the paper's [-20, 20]; log on uniform positive finite bit patterns and
-on the paper's [0.125, 8]), generated on the host by the seeded recipe of
+on the paper's [0.125, 8]; exp on (-745, 710), exp10 on (-324, 309), log2 and log10 on
+positive finite bit patterns), generated on the host by the seeded recipe of
 paper_2605_15547_gb300/workloads.py (bench_input_host).
 
 The 2^26 uint64 results are read as 2^27 uint32 words (little-endian halves), cut into 8
 chunks of 2^24 words and digested like the exhaustive binary32 sweeps
 (tests/exhaustive_hash.py).  Calls only the oracle.
 
-    python tests/golden/make_f64_digests.py [--threads T]
+    python tests/golden/make_f64_digests.py [--threads T] [label ...]
 """
 from __future__ import annotations
 
@@ -29,7 +30,8 @@ from paper_2605_15547_gb300 import workloads as W  # noqa: E402
 
 OUT_DIR = os.path.join(HERE, "f64_full")
 N = 1 << 26
-ARRAYS = [("exp2:domain", "exp2"), ("exp2:u20", "exp2"), ("log:bits", "log"), ("log:u0.125_8", "log")]
+ARRAYS = [("exp2:domain", "exp2"), ("exp2:u20", "exp2"), ("log:bits", "log"), ("log:u0.125_8", "log"),
+          ("exp:edomain", "exp"), ("exp10:tdomain", "exp10"), ("log2:bits", "log2"), ("log10:bits", "log10")]
 
 
 def fname(label: str) -> str:
@@ -39,10 +41,13 @@ def fname(label: str) -> str:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("labels", nargs="*", help="arrays to write (default: all)")
     args = ap.parse_args()
     os.makedirs(OUT_DIR, exist_ok=True)
     w1, w2 = EH.weights()
     for label, func in ARRAYS:
+        if args.labels and label not in args.labels:
+            continue
         x = W.bench_input_host("f64", label, func, N).view(np.uint64)
         y = O.eval_bits(func, x, args.threads).view(np.uint32)
         with open(os.path.join(OUT_DIR, fname(label)), "w") as fh:

@@ -99,7 +99,8 @@ INST_PER_ELEM_SET = {"exp2:domain": 210.3, "exp2:u20": 192.8, "log:bits": 388.5,
                      "exp:edomain": 226.8, "log2:bits": 457.4, "log10:bits": 459.3, "exp10:tdomain": 226.8,
                      "expf:u10": 49.0, "expf:log": 62.8, "logf:u10": 82.0, "logf:log": 71.3,
                      "sinf:u10": 98.8, "sinf:log": 128.6, "tanhf:u10": 119.0, "tanhf:log": 115.4,
-                     "rsqrtf:u10": 67.5, "rsqrtf:log": 65.1, "sinf:large": 129.8}
+                     "rsqrtf:u10": 67.5, "rsqrtf:log": 65.1, "sinf:large": 129.8,
+                     "cosf:u10": 92.5, "sincosf:u10": 118.8, "tanf:u10": 111.9}
 
 
 def inst_per_elem(func: str, label: str = ""):
@@ -462,7 +463,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="auto", choices=["auto", "plain", "df"])
-    ap.add_argument("--workload", default="all19", choices=["all19", "precision", "f64", "batch"])
+    ap.add_argument("--workload", default="all19", choices=["all19", "precision", "f64", "trig", "batch"])
     ap.add_argument("--scale", type=int, default=0, help="divide sizes by 2^scale (testing)")
     ap.add_argument("--ref-sample", type=int, default=1 << 15)
     ap.add_argument("--cpu-sample", type=int, default=1 << 18)
@@ -473,7 +474,7 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="launch shape for every array (skips the autotuner; profiling runs)")
     ap.add_argument("--funcs", default="", help="comma list restricting the workload (testing)")
-    ap.add_argument("--extras", default="precision,f64,batch,modes,apps",
+    ap.add_argument("--extras", default="precision,trig,f64,batch,modes,apps",
                     help="other workloads measured after the headline step (comma list, or none)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

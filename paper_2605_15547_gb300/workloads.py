@@ -177,6 +177,7 @@ def batch_lengths(count: int, rng: np.random.Generator, lo_log2: float = 6.0, hi
 # CPU reference timing and for tests.
 
 PRECISION_FUNCS = ("expf", "logf", "sinf", "tanhf", "rsqrtf")
+TRIG_FUNCS = ("sinf", "cosf", "sincosf", "tanf")
 
 
 def bench_arrays(workload: str, scale: int = 0):
@@ -197,6 +198,11 @@ def bench_arrays(workload: str, scale: int = 0):
             "workload": f"expf/logf/sinf/tanhf/rsqrtf x 2^{28 - scale}: (i) U[-10,10], (ii) log-uniform "
                         "[2^-126,2^127] (random sign except logf, rsqrtf); sinf (iii) = (i) with 5% of "
                         "|x| log-uniform in (2^20, 2^127]", "elems_per_array": n}
+    if workload == "trig":
+        n = (1 << 26) >> scale
+        return [(f + ":u10", f, n) for f in TRIG_FUNCS], {
+            "workload": f"sinf/cosf/sincosf/tanf x 2^{26 - scale} on U[-10,10] (moderate arguments)",
+            "elems_per_array": n}
     if workload == "f64":
         n = (1 << 26) >> scale
         return [("exp2:domain", "exp2", n), ("exp2:u20", "exp2", n), ("log:bits", "log", n),
@@ -213,7 +219,7 @@ def _set_of(label: str) -> str:
 
 
 def bench_seed(workload: str, label: str, func: str) -> int:
-    cfg = {"all19": 2, "precision": 3, "f64": 5}[workload]
+    cfg = {"all19": 2, "precision": 3, "f64": 5, "trig": 6}[workload]
     salt = {"domain": 0, "u10": 0, "log": 1, "large": 2, "u20": 1, "bits": 0, "u0.125_8": 1, "edomain": 0,
             "tdomain": 0}[_set_of(label)]
     return seed_for(cfg, func) + 0x100000000 * salt
@@ -224,6 +230,8 @@ def bench_input_host(workload: str, label: str, func: str, n: int) -> np.ndarray
     kind = _set_of(label)
     if workload == "all19":
         return domain_bits(func, n, rng).view(np.float32)
+    if workload == "trig":
+        return uniform(-10.0, 10.0, n, rng)
     if workload == "precision":
         if kind == "u10":
             return uniform(-10.0, 10.0, n, rng)
@@ -264,6 +272,8 @@ def bench_input_device(workload: str, label: str, func: str, n: int, device="cud
         pos = torch.from_numpy(rng.choice(n, ns, replace=False)).to(device)
         x[pos] = torch.from_numpy(sp.view(np.float32)).to(device)
         return x
+    if workload == "trig":
+        return u(-10.0, 10.0, torch.float32)
     if workload == "precision":
         if kind == "log":
             mag = torch.exp2(u(-126.0, 127.0))

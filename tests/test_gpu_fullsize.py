@@ -48,7 +48,7 @@ def check_sampled(func, x, y, rng):
     assert bad.size == 0, f"{func}: {bad.size} of {idx.size} sampled outputs differ"
 
 
-@pytest.mark.parametrize("workload", ["all19", "precision", "f64"])
+@pytest.mark.parametrize("workload", ["all19", "precision", "trig", "f64"])
 def test_bench_workload_sampled(workload):
     arrays, _ = W.bench_arrays(workload)
     rng = np.random.default_rng(11)

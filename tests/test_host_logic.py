@@ -46,7 +46,7 @@ def test_missing_library_raises(monkeypatch):
 
 def test_recipes_are_deterministic():
     from paper_2605_15547_gb300 import workloads as W
-    for wl in ("all19", "precision", "f64"):
+    for wl in ("all19", "precision", "trig", "f64"):
         arrays, cfg = W.bench_arrays(wl, scale=14)
         assert cfg["workload"]
         for label, func, n in arrays:

@@ -2,7 +2,8 @@
 bits rounded by an independent rounding routine written here from the formats'
 definitions (precision p, minimum exponent emin, gradual underflow, overflow by the
 rounding direction, IEEE 754 Sec. 4.3).  Sampled inputs for every binary32 function's
-formula, all four rounding directions, and all 2^16 inputs of expf and logf to nearest."""
+formula, all four rounding directions, all 2^16 binary16 inputs of expf and logf to
+nearest, and all 2^16 bfloat16 inputs of expf, exp2f and exp10f."""
 import numpy as np
 import pytest
 
@@ -107,6 +108,21 @@ def test_all_binary16_inputs_to_nearest(func):
         if v is None or v == 0 or (func == "logf" and v < 0):
             continue
         assert int(got[b]) == encode(MPF[func](v), "f16", "rn"), (func, hex(b))
+
+
+@pytest.mark.parametrize("func", ["expf", "exp2f", "exp10f"])
+def test_all_bfloat16_inputs_of_the_exp_family(func):
+    """bfloat16 has binary32's exponent range, so its saturation cut-offs (overflow to inf,
+    underflow to +0, the band of subnormal results) are those of the format's own range,
+    not binary64's; every input, to nearest and toward -inf."""
+    x = np.arange(1 << 16, dtype=np.uint32).astype(np.uint16)
+    for mode in ("rn", "rd"):
+        got = O.eval_bits16(func, x, "bf16", mode)
+        for b in range(1 << 16):
+            v = decode(b, "bf16")
+            if v is None:
+                continue
+            assert int(got[b]) == encode(MPF[func](v), "bf16", mode), (func, mode, hex(b))
 
 
 def test_half_specials_and_sincos():

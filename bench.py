@@ -528,7 +528,8 @@ def main():
             tuned[lab] = ("pipelined" if info["pipelined"] else
                           f"u{info['unroll']}b{info['block']}" + ("pf" if info["prefetch"] else "") +
                           (f"m{info['min_blocks']}" if info["min_blocks"] > 1 else "") +
-                          ("w32" if info["vec_bytes"] == 32 else "") + ("reg16" if info["reg_table"] else ""))
+                          ("w32" if info["vec_bytes"] == 32 else "") + ("reg16" if info["reg_table"] else "") +
+                          ("pack" if info["easy"] else ""))
 
     for _ in range(args.warmup):
         step(args.form)

@@ -214,10 +214,15 @@ int crm_set_batch_mode(int mode);
    reg_table: the evaluator keeps a table of at most 16 entries in registers and reads it
    with warp shuffles instead of a larger table in shared memory (the paper's small tables
    read by permutes, Sec. II.A; exp family only: other functions do not provide it).
+   easy: the shape packs, across the warp, the elements whose result is not known in
+   advance (tiny arguments, where f rounds to x, 1 or RN(pi/2), are resolved without the
+   evaluator) and evaluates only those; functions without such arguments (log, log2, log10,
+   rsqrt, the binary64 ones) do not provide it.  The autotuner times these shapes beside the
+   others: they win on data whose magnitudes span many binades, and lose a little elsewhere.
    Every variant computes the same bits.  Output pointers may be NULL. */
-#define CRM_NUM_VARIANTS 11
+#define CRM_NUM_VARIANTS 13
 int crm_variant_info(int variant, int *unroll, int *block, int *prefetch, int *pipelined, int *min_blocks,
-                     int *vec_bytes, int *reg_table);
+                     int *vec_bytes, int *reg_table, int *easy);
 /* Choose the variant of (func_id, form) for all later calls.  CRM_ERR_ARG if the form does
    not provide it (the plain FP64 form provides only the default shape). */
 int crm_set_variant(int func_id, int form, int variant);

@@ -221,11 +221,11 @@ def reserve(max_elems: int, max_arrays: int = 0, stream=None) -> None:
 
 def variant_info(v: int) -> dict:
     """Launch shape of main-kernel variant v (0 <= v < NUM_VARIANTS)."""
-    a = [ctypes.c_int() for _ in range(7)]
+    a = [ctypes.c_int() for _ in range(8)]
     L.check(L.lib().crm_variant_info(int(v), *[ctypes.byref(t) for t in a]))
     return {"unroll": a[0].value, "block": a[1].value, "prefetch": bool(a[2].value),
             "pipelined": bool(a[3].value), "min_blocks": a[4].value, "vec_bytes": a[5].value,
-            "reg_table": bool(a[6].value)}
+            "reg_table": bool(a[6].value), "easy": bool(a[7].value)}
 
 
 def set_variant(func, variant: int, form=None) -> None:

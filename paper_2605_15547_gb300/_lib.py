@@ -23,7 +23,7 @@ F64_FUNCS = {"exp2", "log", "exp", "log2", "log10", "exp10"}
 FORMS = {"auto": 0, "plain": 1, "df": 2}
 CRM_F32, CRM_F64, CRM_F16, CRM_BF16 = 0, 1, 2, 3
 RMODES = {"rn": 0, "rd": 1, "ru": 2, "rz": 3}
-NUM_VARIANTS = 11
+NUM_VARIANTS = 13
 BATCH_TILE_MIN, BATCH_TILE_MAX = 10, 16
 
 
@@ -74,7 +74,7 @@ def _lib():
                 lib.crm_noalloc_stats_reset.argtypes = [vp]
                 lib.crm_reserve.argtypes = [c_u64, c_int, vp]
                 pi, pf = ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float)
-                lib.crm_variant_info.argtypes = [c_int, pi, pi, pi, pi, pi, pi, pi]
+                lib.crm_variant_info.argtypes = [c_int, pi, pi, pi, pi, pi, pi, pi, pi]
                 lib.crm_set_variant.argtypes = [c_int, c_int, c_int]
                 lib.crm_get_variant.argtypes = [c_int, c_int, pi]
                 lib.crm_autotune.argtypes = [c_int, c_int, c_int, vp, vp, c_u64, c_int, vp, pi, pf]

@@ -27,6 +27,14 @@ template <int KIND> struct FnExp {
       y[0] = exp_df<KIND>(x, (const float4 *)sm, h, sg);
   }
   CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { y[0] = exp_slow<KIND>(x, u, f, sg); }
+  // Round to nearest, b^x is 1 for |x| <= 2^-25 (2^x: as 2^-25 < 2^-24.5 = 2^-25 / ln 2;
+  // 10^x: |x| <= 2^-27 < 2^-25 / ln 10): b^x - 1 is then below 2^-25 + 2^-51 in magnitude,
+  // inside the midpoints 1 + 2^-24 and 1 - 2^-25 (e^(-2^-25) = 1 - 2^-25 + 2^-51 - ...).
+  static constexpr bool HAS_EASY = true;
+  CRM_DEV static bool easy(float x, float *y) {
+    y[0] = 1.0f;
+    return fabsf(x) <= (KIND == 2 ? 0x1p-27f : 0x1p-25f);
+  }
 };
 
 // The exp family's double-float tier with its 16-entry table in registers (Ctx: the
@@ -63,6 +71,15 @@ template <int KIND> struct FnLog {
       y[0] = log_df<KIND>(x, (const float4 *)sm, h, sg);
   }
   CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { y[0] = log_slow<KIND>(x, u, f, sg); }
+  // log1p x = x - x^2/2 + ... rounds to x for |x| < 2^-26: with 2^e <= |x| < 2^(e+1),
+  // e <= -27, x^2/2 < 2^(2e+1) is below a quarter ulp of x, 2^(e-25) (the distance to the
+  // midpoint toward zero when x is a power of two; half an ulp otherwise).  ln, log2 and
+  // log10 have no such range.
+  static constexpr bool HAS_EASY = KIND == 3;
+  CRM_DEV static bool easy(float x, float *y) {
+    y[0] = x;
+    return fabsf(x) < 0x1p-26f;
+  }
 };
 
 template <int H> struct FnHyp {
@@ -79,6 +96,16 @@ template <int H> struct FnHyp {
       y[0] = hyp_df<H>(x, (const float4 *)sm, h, sg);
   }
   CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { y[0] = hyp_slow<H>(x, u, f, sg); }
+  // Round to nearest: expm1 x = x + x^2/2 + ... is x for |x| < 2^-26 (the bound of log1p);
+  // sinh x = x + x^3/6 + ... and tanh x = x - x^3/3 + ... are x for |x| < 2^-12 (with
+  // 2^e <= |x| < 2^(e+1), e <= -13: x^3/3 < 2^(3e+3)/3 <= 2^(e-24), half an ulp, and for x
+  // a power of two x^3/3 = 2^(3e)/3 < 2^(e-25), a quarter); cosh x = 1 + x^2/2 + ... is 1
+  // for |x| < 2^-12 (x^2/2 < 2^-25, below the midpoint 1 + 2^-24).
+  static constexpr bool HAS_EASY = true;
+  CRM_DEV static bool easy(float x, float *y) {
+    y[0] = H == HYP_COSH ? 1.0f : x;
+    return fabsf(x) < (H == HYP_EXPM1 ? 0x1p-26f : 0x1p-12f);
+  }
 };
 
 template <int KIND> struct FnTrig {
@@ -109,6 +136,14 @@ template <int KIND> struct FnTrig {
                     h, sg);
   }
   CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { trig_slow<KIND>(x, y, u, f, sg); }
+  // Round to nearest: sin x = x - x^3/6 + ... and tan x = x + x^3/3 + ... are x, cos x =
+  // 1 - x^2/2 + ... is 1, for |x| < 2^-12 (the bounds of sinh, tanh and cosh).
+  static constexpr bool HAS_EASY = true;
+  CRM_DEV static bool easy(float x, float *y) {
+    y[0] = KIND == TRIG_COS ? 1.0f : x;
+    y[1] = 1.0f;
+    return fabsf(x) < 0x1p-12f;
+  }
   // warp-uniform choice of the double-float reduction (see trig_reduce_df)
   CRM_DEV static bool path_ok(float x) { return trig_cw_ok(x); }
   template <int FORM, int PATH> CRM_DEV static void eval_path(float x, const void *sm, float *y, bool &h) {
@@ -131,6 +166,22 @@ template <int KIND> struct FnAtrig {
       y[0] = atrig_df<KIND>(x, (const float2 *)sm, h, sg);
   }
   CRM_DEV static void slow(float x, float *y, int &u, bool f, int *sg = nullptr) { y[0] = atrig_slow<KIND>(x, u, f, sg); }
+  // Round to nearest: asin x = x + x^3/6 + ... and atan x = x - x^3/3 + ... are x for
+  // |x| < 2^-12 (the bounds of sinh and tanh).  With P = RN(pi/2) = pi/2 + 2^-24.45 and its
+  // midpoints P -+ 2^-24: acos x = pi/2 - x - x^3/6 - ... lies between them for
+  // |x| < 2^-26, and atan x = +-(pi/2 - 1/|x| + ...) for 2^26 <= |x| < inf (1/|x| <= 2^-26 <
+  // 2^-24 - 2^-24.45 = 2^-25.9).
+  static constexpr bool HAS_EASY = true;
+  CRM_DEV static bool easy(float x, float *y) {
+    const float ax = fabsf(x), P = bitsf(0x3FC90FDBu);
+    if (KIND == AT_ACOS) {
+      y[0] = P;
+      return ax < 0x1p-26f;
+    }
+    const bool big = KIND == AT_ATAN && ax >= 0x1p26f;
+    y[0] = big ? copysignf(P, x) : x;
+    return ax < 0x1p-12f || (big && ax < CRM_INF_F);
+  }
 };
 
 struct FnRsqrt {

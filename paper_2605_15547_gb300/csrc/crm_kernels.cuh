@@ -228,6 +228,104 @@ CRM_DEV bool eval_vec(const V &xv, const C &sm, V &y0, V &y1, bool *h) {
     return eval_vec_on<Fn, FORM, 0>(xv, sm, y0, y1, h);
   }
 }
+// ---- compaction of the elements that need the evaluator
+// An Fn may declare HAS_EASY and easy(x, y): true when RN(f(x)) is known without evaluating
+// f (tiny arguments: x, 1 or RN(pi/2); the proofs are beside each easy()), with y set to it.
+// On inputs with a wide range of magnitudes most elements can be of that kind, yet in a
+// warp every lane would still pay the full evaluation.  easy_vector resolves them first,
+// packs the others of the whole warp's vector (32 W elements) densely into a per-warp
+// shared-memory buffer, evaluates them there, one per lane per round, and each evaluating
+// lane stores its result (and queues its hard lanes) itself: ceil(M / 32) rounds for M
+// elements instead of W.
+template <class Fn, class = void> struct EasyOf : std::false_type {};
+template <class Fn> struct EasyOf<Fn, std::void_t<decltype(Fn::HAS_EASY)>> : std::bool_constant<Fn::HAS_EASY> {};
+
+// Buffer words per warp: x and the element's place (lane W + j) for 32 W elements.
+template <class Fn, int W> constexpr int easy_words() { return EasyOf<Fn>::value ? 2 * 32 * W : 0; }
+
+template <class Fn, int FORM, class C>
+CRM_DEV void eval_one(float x, const C &sm, float *y, bool &h) {
+  if constexpr (HasPaths<Fn>::value && FORM != 1) {
+    if (__all_sync(0xFFFFFFFFu, Fn::path_ok(x)))
+      Fn::template eval_path<FORM, 1>(x, sm, y, h);
+    else
+      Fn::template eval_path<FORM, 2>(x, sm, y, h);
+  } else {
+    Fn::template eval<FORM>(x, sm, y, h);
+  }
+}
+
+// One vector per lane of a whole warp: v0 is the warp's first vector of the segment, this
+// lane's is v0 + lane (act: it exists).  Returns false, having stored nothing, when more
+// than 32 (W - 1) elements need the evaluator (packing would save no round): the caller
+// then evaluates the vector as usual.  Otherwise stores every result, queues the hard lanes
+// and returns true.  cw: this warp's buffer (easy_words<Fn, W>() words).
+template <class Fn, int FORM, class V, class C>
+CRM_DEV bool easy_vector(const V &xv, uint32_t v0, bool act, V *out4, V *out4b, uint64_t seg, const C &sm,
+                         const KArgs &a, float *cw) {
+  using T = typename Fn::T;
+  constexpr int W = sizeof(V) / sizeof(T);
+  const int lane = threadIdx.x & 31;
+  T y[2];
+  // a sample first: with fewer than 8 easy elements among the warp's first slot, the
+  // vector is taken to have too few to repay the packing (one vote per vector)
+  if (__popc(__ballot_sync(0xFFFFFFFFu, act && Fn::easy(vget(xv, 0), y))) < 8) return false;
+  unsigned nb[W];  // lanes whose element j needs the evaluator
+  int M = 0;
+#pragma unroll
+  for (int j = 0; j < W; j++) {
+    nb[j] = __ballot_sync(0xFFFFFFFFu, !(act && Fn::easy(vget(xv, j), y)));
+    M += __popc(nb[j]);
+  }
+  if (M > 32 * (W - 1)) return false;
+  if (act) {  // the easy results; the others are overwritten below, in warp order
+    V y0, y1;
+#pragma unroll
+    for (int j = 0; j < W; j++) {
+      Fn::easy(vget(xv, j), y);
+      vset(y0, j, y[0]);
+      if (Fn::NOUT == 2) vset(y1, j, y[1]);
+    }
+    st_stream(out4 + v0 + lane, y0);
+    if (Fn::NOUT == 2) st_stream(out4b + v0 + lane, y1);
+  }
+  if (M == 0) return true;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t *ci = (uint32_t *)(cw + 32 * W);
+  int base = 0;
+#pragma unroll
+  for (int j = 0; j < W; j++) {
+    if ((nb[j] >> lane) & 1u) {
+      const int k = base + __popc(nb[j] & lt);
+      cw[k] = vget(xv, j);
+      ci[k] = (uint32_t)(lane * W + j);
+    }
+    base += __popc(nb[j]);
+  }
+  __syncwarp();  // also orders the vector stores above before the element stores below
+  const uint64_t e0 = a.head + (seg + v0) * W;  // the warp's first element
+  T *out = (T *)a.out;
+  for (int k0 = 0; k0 < M; k0 += 32) {  // every lane runs every round (warp-level votes inside)
+    const int k = k0 + lane;
+    const bool on = k < M;
+    const T x = on ? cw[k] : T(1);
+    uint64_t i = e0 + (on ? ci[k] : 0u);
+    bool hh;
+    eval_one<Fn, FORM>(x, sm, y, hh);
+    if (on) {
+      out[i] = y[0];
+      if (Fn::NOUT == 2) out[a.n + i] = y[1];
+    }
+    const bool hq = on && hh;
+    if (__any_sync(0xFFFFFFFFu, hq)) {
+      uint64_t xb = xbits_of(x);
+      if (push_hard<1>(hq ? 1u : 0u, &i, &xb, a)) slow_store<Fn>(x, i, a);
+    }
+  }
+  __syncwarp();  // the buffer is refilled by the next vector
+  return true;
+}
+
 template <int W> CRM_DEV unsigned hard_mask(const bool *h, bool force) {
   unsigned hm = 0;
 #pragma unroll
@@ -253,10 +351,10 @@ CRM_DEV void load_vecs(V *xv, const V *in4, uint32_t base, uint32_t nv) {
 
 // Evaluates and stores the UNROLL vectors of one iteration of a segment (nv vectors from
 // vector `seg` of the array; out4, out4b point at the segment), queueing the hard lanes.
-template <class Fn, int FORM, int UNROLL, int BS, bool WIDE, class C>
+template <class Fn, int FORM, int UNROLL, int BS, bool WIDE, bool EASY, class C>
 CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T, WIDE>::V *xv, uint32_t base, uint32_t nv,
                        typename VecOf<typename Fn::T, WIDE>::V *out4, typename VecOf<typename Fn::T, WIDE>::V *out4b,
-                       uint64_t seg, const C &sm, const KArgs &a) {
+                       uint64_t seg, const C &sm, const KArgs &a, float *cw) {
   using T = typename Fn::T;
   using V = typename VecOf<T, WIDE>::V;
   constexpr int W = VecOf<T, WIDE>::W;
@@ -264,6 +362,10 @@ CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T, WIDE>::V *xv, uint32
   for (int u = 0; u < UNROLL; u++) {
     const uint32_t v = base + (uint32_t)(u * BS) + threadIdx.x;
     bool act = v < nv;
+    if constexpr (EASY && EasyOf<Fn>::value && FORM == 2) {  // whole warps (force_hard is per launch)
+      if (!a.force_hard && easy_vector<Fn, FORM>(xv[u], v - (threadIdx.x & 31), act, out4, out4b, seg, sm, a, cw))
+        continue;
+    }
     V y0, y1;
     bool h[W];
     const bool any = (eval_vec<Fn, FORM>(xv[u], sm, y0, y1, h) || a.force_hard) && act;
@@ -293,12 +395,16 @@ CRM_DEV void eval_vecs(const typename VecOf<typename Fn::T, WIDE>::V *xv, uint32
 // iteration's vectors are loaded
 // before this iteration is evaluated (software prefetch: the loads' latency overlaps the
 // thread's own arithmetic).
-template <class Fn, int FORM, int UNROLL, int BS, bool PF, bool WIDE>
+template <class Fn, int FORM, int UNROLL, int BS, bool PF, bool WIDE, bool EASY = false>
 CRM_DEV void main_body(const KArgs &a) {
   using T = typename Fn::T;
   using V = typename VecOf<T, WIDE>::V;
   constexpr int W = VecOf<T, WIDE>::W;
   __shared__ __align__(16) unsigned char smem[(Fn::template tab_bytes<FORM>() > 0) ? Fn::template tab_bytes<FORM>() : 16];
+  // the per-warp buffers of eval_vec_easy (binary32 functions with easy arguments)
+  constexpr int EW = EASY && FORM == 2 ? easy_words<Fn, W>() : 0;
+  __shared__ __align__(16) float ebuf[EW > 0 ? (BS / 32) * EW : 1];
+  float *cw = ebuf + (EW > 0 ? (threadIdx.x >> 5) * EW : 0);
   load_tab<Fn, FORM>(smem);
   const typename CtxOf<Fn, FORM>::type sm = CtxOf<Fn, FORM>::make(smem);
 
@@ -317,7 +423,7 @@ CRM_DEV void main_body(const KArgs &a) {
       for (; base < nv; base += stride) {
         V nx[UNROLL];
         load_vecs<V, UNROLL, BS>(nx, in4, base + stride, nv);
-        eval_vecs<Fn, FORM, UNROLL, BS, WIDE>(xv, base, nv, out4, out4b, seg, sm, a);
+        eval_vecs<Fn, FORM, UNROLL, BS, WIDE, EASY>(xv, base, nv, out4, out4b, seg, sm, a, cw);
 #pragma unroll
         for (int u = 0; u < UNROLL; u++) xv[u] = nx[u];
       }
@@ -325,7 +431,7 @@ CRM_DEV void main_body(const KArgs &a) {
       for (; base < nv; base += stride) {
         V xv[UNROLL];
         load_vecs<V, UNROLL, BS>(xv, in4, base, nv);
-        eval_vecs<Fn, FORM, UNROLL, BS, WIDE>(xv, base, nv, out4, out4b, seg, sm, a);
+        eval_vecs<Fn, FORM, UNROLL, BS, WIDE, EASY>(xv, base, nv, out4, out4b, seg, sm, a, cw);
       }
     }
   }
@@ -362,9 +468,9 @@ CRM_DEV void main_body(const KArgs &a) {
 template <class Fn> constexpr int min_blocks_64regs(int bs) {
   return sizeof(typename Fn::T) == 4 ? 65536 / (bs * 64) : 1;
 }
-template <class Fn, int FORM, int UNROLL, int BS, bool PF, bool WIDE = false>
+template <class Fn, int FORM, int UNROLL, int BS, bool PF, bool WIDE = false, bool EASY = false>
 __global__ void __launch_bounds__(BS, min_blocks_64regs<Fn>(BS)) k_main(KArgs a) {
-  main_body<Fn, FORM, UNROLL, BS, PF, WIDE>(a);
+  main_body<Fn, FORM, UNROLL, BS, PF, WIDE, EASY>(a);
 }
 // The same with a register cap: at least MINB blocks of BS threads resident per SM.
 template <class Fn, int FORM, int UNROLL, int BS, bool PF, int MINB>

@@ -14,15 +14,19 @@ typedef int (*occ_fn)(void);
 // cap (minimum resident blocks), the vector width (16- or 32-byte accesses: 4 or 8
 // binary32 elements), the shared-memory pipelined kernel, or (reg_table) the evaluator
 // variant whose table of at most 16 entries lives in registers and is read by warp
-// shuffles instead of shared-memory loads (the exp family).
+// shuffles instead of shared-memory loads (the exp family), or (easy) the main kernel
+// that packs the elements needing the evaluator across the warp (eval_vecs, functions
+// with easy arguments only).
 struct VariantInfo {
-  int unroll, block, prefetch, pipelined, min_blocks, vec_bytes, reg_table;
+  int unroll, block, prefetch, pipelined, min_blocks, vec_bytes, reg_table, easy;
 };
-enum { NVARIANT = 11, DEFAULT_VARIANT = 1, REGTAB_VARIANT = 10 };
+enum { NVARIANT = 13, DEFAULT_VARIANT = 1, REGTAB_VARIANT = 10 };
 constexpr VariantInfo VARIANTS[NVARIANT] = {
-    {1, 256, 0, 0, 1, 16, 0}, {2, 256, 0, 0, 1, 16, 0}, {4, 256, 0, 0, 1, 16, 0}, {PVPT, KBLOCK, 0, 1, 1, 16, 0},
-    {2, 256, 1, 0, 4, 16, 0}, {1, 256, 1, 0, 1, 16, 0}, {2, 128, 1, 0, 1, 16, 0}, {2, 512, 1, 0, 1, 16, 0},
-    {1, 256, 1, 0, 1, 32, 0}, {1, 512, 1, 0, 1, 32, 0}, {2, 512, 1, 0, 1, 16, 1}};
+    {1, 256, 0, 0, 1, 16, 0, 0}, {2, 256, 0, 0, 1, 16, 0, 0}, {4, 256, 0, 0, 1, 16, 0, 0},
+    {PVPT, KBLOCK, 0, 1, 1, 16, 0, 0}, {2, 256, 1, 0, 4, 16, 0, 0}, {1, 256, 1, 0, 1, 16, 0, 0},
+    {2, 128, 1, 0, 1, 16, 0, 0}, {2, 512, 1, 0, 1, 16, 0, 0}, {1, 256, 1, 0, 1, 32, 0, 0},
+    {1, 512, 1, 0, 1, 32, 0, 0}, {2, 512, 1, 0, 1, 16, 1, 0}, {1, 512, 1, 0, 1, 32, 0, 1},
+    {2, 512, 1, 0, 1, 16, 0, 1}};
 
 struct FuncEntry {
   launch_fn main[3][NVARIANT];  // [form][variant]; form 0 unused; null when unavailable
@@ -34,9 +38,9 @@ struct FuncEntry {
   int dtype;  // 0 binary32, 1 binary64
 };
 
-template <class Fn, int FORM, int U, int BS, bool PF, bool WIDE>
+template <class Fn, int FORM, int U, int BS, bool PF, bool WIDE, bool EASY = false>
 cudaError_t launch_main(const KArgs &a, int grid, cudaStream_t s) {
-  k_main<Fn, FORM, U, BS, PF, WIDE><<<grid, BS, 0, s>>>(a);
+  k_main<Fn, FORM, U, BS, PF, WIDE, EASY><<<grid, BS, 0, s>>>(a);
   return cudaGetLastError();
 }
 template <class Fn, int FORM, int U, int BS, bool PF, int MINB>
@@ -77,8 +81,9 @@ void set_variant(FuncEntry &e) {
     e.main[FORM][V] = launch_main_capped<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.min_blocks>;
     e.main_sym[FORM][V] = (const void *)k_main_capped<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.min_blocks>;
   } else {
-    e.main[FORM][V] = launch_main<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.vec_bytes == 32>;
-    e.main_sym[FORM][V] = (const void *)k_main<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.vec_bytes == 32>;
+    e.main[FORM][V] = launch_main<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.vec_bytes == 32, (bool)I.easy>;
+    e.main_sym[FORM][V] =
+        (const void *)k_main<Fn, FORM, I.unroll, I.block, (bool)I.prefetch, I.vec_bytes == 32, (bool)I.easy>;
   }
 }
 
@@ -97,6 +102,10 @@ void set_form(FuncEntry &e) {
     set_variant<Fn, FORM, 7>(e);
     set_variant<Fn, FORM, 8>(e);
     set_variant<Fn, FORM, 9>(e);
+    if constexpr (EasyOf<Fn>::value) {
+      set_variant<Fn, FORM, 11>(e);
+      set_variant<Fn, FORM, 12>(e);
+    }
   }
 }
 

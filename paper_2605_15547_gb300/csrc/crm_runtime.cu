@@ -716,9 +716,10 @@ int crm_set_batch_tile(int log2_elems) {
 }
 
 int crm_variant_info(int variant, int *unroll, int *block, int *prefetch, int *pipelined, int *min_blocks,
-                     int *vec_bytes, int *reg_table) {
+                     int *vec_bytes, int *reg_table, int *easy) {
   if (variant < 0 || variant >= NVARIANT) return CRM_ERR_ARG;
   if (reg_table) *reg_table = VARIANTS[variant].reg_table;
+  if (easy) *easy = VARIANTS[variant].easy;
   if (unroll) *unroll = VARIANTS[variant].unroll;
   if (block) *block = VARIANTS[variant].block;
   if (prefetch) *prefetch = VARIANTS[variant].prefetch;

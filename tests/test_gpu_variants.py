@@ -29,6 +29,8 @@ def _setup():
 
 
 REGTAB_FUNCS = ("expf", "exp2f", "exp10f")
+# the functions with easy arguments (the packing shapes)
+EASY_FUNCS = tuple(f for f in W.F32_FUNCS if f not in ("logf", "log2f", "log10f", "rsqrtf"))
 
 
 @pytest.mark.parametrize("func", FUNCS)
@@ -40,8 +42,9 @@ def test_every_variant_gives_the_oracle_bits(func):
     buf = torch.from_numpy(np.concatenate([np.zeros(1, np.uint32), xb]).view(np.float32)).cuda()
     x = buf[1:]  # 4-byte aligned, not 16: exercises the scalar head as well
     for v in range(NUM_VARIANTS):
-        if crm.variant_info(v)["reg_table"] and func not in REGTAB_FUNCS:
-            with pytest.raises(crm.CrmError):  # only the exp family keeps its table in registers
+        info = crm.variant_info(v)
+        if (info["reg_table"] and func not in REGTAB_FUNCS) or (info["easy"] and func not in EASY_FUNCS):
+            with pytest.raises(crm.CrmError):  # shapes the function does not provide
                 crm.set_variant(func, v, form="df")
             continue
         crm.set_variant(func, v, form="df")
@@ -94,7 +97,8 @@ def test_plain_form_has_only_the_default_shape():
 def test_autotune_keeps_a_timed_variant():
     x = torch.from_numpy(W.domain_bits("logf", 1 << 22, W.rng_for(8, "logf")).view(np.float32)).cuda()
     best, ms = crm.autotune("logf", x, form="df", reps=2)
-    assert best in ms and len(ms) == NUM_VARIANTS - 1  # every shape but the register table
+    # every shape but the register table and the packing ones (log has no easy arguments)
+    assert best in ms and len(ms) == NUM_VARIANTS - 3
     assert all(t > 0 for t in ms.values())
     assert crm.get_variant("logf", form="df") == best
     y = crm.eval("logf", x[:4099], form="df")

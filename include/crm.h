@@ -197,8 +197,10 @@ int crm_set_batch_tile(int log2_elems);
 /* Batch mode.  CRM_BATCH_MIXED: one persistent kernel over all arrays, a block-uniform
    switch on each tile's function (2 launches per batch).  CRM_BATCH_GROUPED (default): the
    arrays are ordered by function and each function present gets one persistent kernel
-   specialised for it, then one slow-path kernel for the whole batch (at most 20
-   launches, one CUDA graph when captured).  Both compute the same bits. */
+   specialised for it, then one slow-path kernel for the whole batch (at most 22
+   launches, one CUDA graph when captured); a function whose chosen launch shape packs
+   (crm_variant_info easy, e.g. picked by crm_autotune) has its arrays packed the same way.
+   Both compute the same bits. */
 #define CRM_BATCH_MIXED 0
 #define CRM_BATCH_GROUPED 1
 int crm_set_batch_mode(int mode);

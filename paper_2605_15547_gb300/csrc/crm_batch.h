@@ -36,9 +36,11 @@ struct BatchArgs {
 cudaError_t launch_batch(const BatchArgs &b, int form, int grid, int slow_grid, cudaStream_t s);
 const void *batch_kernel_symbol(int form);
 // Grouped mode: one kernel specialised for `func` over that function's arrays; the slow
-// pass runs once after all groups (launch_batch_slow, descs = the whole batch).
-cudaError_t launch_batch_group(int func, const BatchArgs &b, int form, int grid, cudaStream_t s);
-const void *batch_group_symbol(int func, int form);
+// pass runs once after all groups (launch_batch_slow, descs = the whole batch).  easy: the
+// kernel packs the elements that need the evaluator across the warp (as the main kernel's
+// packing shapes; functions without easy arguments ignore it).
+cudaError_t launch_batch_group(int func, const BatchArgs &b, int form, int grid, cudaStream_t s, bool easy);
+const void *batch_group_symbol(int func, int form, bool easy);
 cudaError_t launch_batch_slow(const BatchArgs &b, int slow_grid, cudaStream_t s);
 
 }  // namespace crm

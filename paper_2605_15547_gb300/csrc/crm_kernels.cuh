@@ -274,7 +274,7 @@ CRM_DEV bool easy_vector(const V &xv, uint32_t v0, bool act, V *out4, V *out4b, 
   int M = 0;
 #pragma unroll
   for (int j = 0; j < W; j++) {
-    nb[j] = __ballot_sync(0xFFFFFFFFu, !(act && Fn::easy(vget(xv, j), y)));
+    nb[j] = __ballot_sync(0xFFFFFFFFu, act && !Fn::easy(vget(xv, j), y));  // no lane past the end
     M += __popc(nb[j]);
   }
   if (M > 32 * (W - 1)) return false;

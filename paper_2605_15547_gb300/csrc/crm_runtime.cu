@@ -691,10 +691,13 @@ int crm_eval_batch(const crm_desc_t *descs, int count, int form, void *stream) {
     g.count = gcount[f];
     g.aid_base = (uint32_t)gstart[f];
     g.total_tiles = gtiles[f];
-    uint64_t grid = (uint64_t)sms * blocks_per_sm(batch_group_symbol(f, fm), KBLOCK);
+    // the function's arrays are packed when its chosen launch shape packs (crm_autotune
+    // found packing faster on its data)
+    const bool easy = fm == 2 && VARIANTS[variant_of(f, fm)].easy != 0;
+    uint64_t grid = (uint64_t)sms * blocks_per_sm(batch_group_symbol(f, fm, easy), KBLOCK);
     if (grid > gtiles[f]) grid = gtiles[f];
     g.tiles_per_block = (gtiles[f] + grid - 1) / grid;
-    e = launch_batch_group(f, g, fm, (int)grid, s);
+    e = launch_batch_group(f, g, fm, (int)grid, s, easy);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   e = launch_batch_slow(a, sms * 2, s);

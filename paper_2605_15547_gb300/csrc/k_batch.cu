@@ -19,9 +19,9 @@ static_assert(FnLog<0>::tab_bytes<2>() <= BATCH_SMEM && FnTrig<TRIG_TAN>::tab_by
                   FnAtrig<0>::tab_bytes<2>() <= BATCH_SMEM,
               "the mixed batch kernel's shared memory holds every binary32 table");
 
-template <class Fn, int FORM>
+template <class Fn, int FORM, bool EASY = false>
 CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t m, const unsigned char *sm,
-                        const BatchArgs &b) {
+                        const BatchArgs &b, float *cw = nullptr) {
   using T = typename Fn::T;
   KArgs a;
   a.in = d.in;
@@ -63,6 +63,11 @@ CRM_DEV void batch_tile(const BatchDesc &d, uint32_t aid, uint64_t off, uint64_t
       for (int u = 0; u < 2; u++) {
         const uint32_t v = base + (uint32_t)(u * KBLOCK) + threadIdx.x;
         bool act = v < nv;
+        if constexpr (EASY && EasyOf<Fn>::value && FORM == 2) {  // whole warps; element off + v W + j
+          a.head = off;
+          if (!a.force_hard && easy_vector<Fn, FORM>(xv[u], v - (threadIdx.x & 31), act, out4, out4b, 0, sm, a, cw))
+            continue;
+        }
         V y0, y1;
         bool h[W];
         const bool any = (eval_vec<Fn, FORM>(xv[u], sm, y0, y1, h) || a.force_hard) && act;
@@ -211,9 +216,12 @@ __global__ void __launch_bounds__(KBLOCK) k_batch(BatchArgs b) {
 }
 
 // Grouped mode: every array of b has function Fn; the table is loaded once.
-template <class Fn, int FORM>
+template <class Fn, int FORM, bool EASY = false>
 __global__ void __launch_bounds__(KBLOCK) k_batch_group(BatchArgs b) {
   __shared__ __align__(16) unsigned char sm[(Fn::template tab_bytes<FORM>() > 0) ? Fn::template tab_bytes<FORM>() : 16];
+  constexpr int EW = EASY && FORM == 2 ? easy_words<Fn, VecOf<typename Fn::T>::W>() : 0;
+  __shared__ __align__(16) float ebuf[EW > 0 ? (KBLOCK / 32) * EW : 1];
+  float *cw = ebuf + (EW > 0 ? (threadIdx.x >> 5) * EW : 0);
   Fn::template load<FORM>(sm);
   __syncthreads();
   const uint64_t t0 = (uint64_t)blockIdx.x * b.tiles_per_block;
@@ -232,7 +240,7 @@ __global__ void __launch_bounds__(KBLOCK) k_batch_group(BatchArgs b) {
     uint64_t off = (t - d.tile0) << b.tile_shift;
     uint64_t m = d.n - off;
     if (m > (1ull << b.tile_shift)) m = 1ull << b.tile_shift;
-    batch_tile<Fn, FORM>(d, b.aid_base + (uint32_t)aidx, off, m, sm, b);
+    batch_tile<Fn, FORM, EASY>(d, b.aid_base + (uint32_t)aidx, off, m, sm, b, cw);
   }
 }
 
@@ -267,9 +275,12 @@ struct GroupLaunch {
   const BatchArgs *b;
   int grid;
   cudaStream_t s;
+  bool easy;
   template <class Fn> void run() {
     if (form == 1)
       k_batch_group<Fn, 1><<<grid, KBLOCK, 0, s>>>(*b);
+    else if (EasyOf<Fn>::value && easy)
+      k_batch_group<Fn, 2, true><<<grid, KBLOCK, 0, s>>>(*b);
     else
       k_batch_group<Fn, 2><<<grid, KBLOCK, 0, s>>>(*b);
   }
@@ -277,19 +288,22 @@ struct GroupLaunch {
 struct GroupSymbol {
   int form;
   const void *sym;
+  bool easy;
   template <class Fn> void run() {
-    sym = form == 1 ? (const void *)k_batch_group<Fn, 1> : (const void *)k_batch_group<Fn, 2>;
+    sym = form == 1 ? (const void *)k_batch_group<Fn, 1>
+                    : (EasyOf<Fn>::value && easy ? (const void *)k_batch_group<Fn, 2, true>
+                                                 : (const void *)k_batch_group<Fn, 2>);
   }
 };
 
-cudaError_t launch_batch_group(int func, const BatchArgs &b, int form, int grid, cudaStream_t s) {
-  GroupLaunch L{form, &b, grid, s};
+cudaError_t launch_batch_group(int func, const BatchArgs &b, int form, int grid, cudaStream_t s, bool easy) {
+  GroupLaunch L{form, &b, grid, s, easy};
   CRM_FOR_FUNC_ALL(func, L);
   return cudaGetLastError();
 }
 
-const void *batch_group_symbol(int func, int form) {
-  GroupSymbol G{form, nullptr};
+const void *batch_group_symbol(int func, int form, bool easy) {
+  GroupSymbol G{form, nullptr, easy};
   CRM_FOR_FUNC_ALL(func, G);
   return G.sym;
 }

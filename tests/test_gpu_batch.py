@@ -64,6 +64,35 @@ def test_batch_matches_single_calls(form, tile, mode):
         assert np.array_equal(a, b), f"{f}: {int(np.count_nonzero(a != b))} differ"
 
 
+@pytest.mark.parametrize("shape", [11, 12])
+def test_grouped_batch_packs_like_the_packing_shapes(shape):
+    """With a packing launch shape chosen for every function that has one, the grouped
+    batch packs those functions' elements too: the results must equal the oracle's."""
+    easy = [f for f in W.F32_FUNCS if crm.variant_info(shape)["easy"]]
+    items = make_batch(150, 13, seed=300 + shape, misalign=False)
+    chosen = []
+    for f in easy:
+        try:
+            crm.set_variant(f, shape, form="df")
+            chosen.append(f)
+        except crm.CrmError:  # no easy arguments: the function keeps its shape
+            pass
+    assert len(chosen) == 15
+    try:
+        crm.set_batch_mode("grouped")
+        crm.eval_batch([(f, x, y) for f, x, y, _ in items], form="df")
+        torch.cuda.synchronize()
+    finally:
+        for f in chosen:
+            crm.set_variant(f, 1, form="df")
+    for f, x, y, xh in items:
+        got = y.cpu().numpy().view(np.uint32)
+        ref = O.eval_bits(f, xh.view(np.uint32)).reshape(-1)
+        assert np.array_equal(got, ref), f
+        tail = y._base[y.storage_offset() + y.numel():]  # the output buffer's guard words
+        assert bool(torch.isnan(tail).all()), f"{f}: a write past the end of the output"
+
+
 def test_batch_against_oracle_sample():
     items = make_batch(120, 12, seed=7)
     crm.eval_batch([(f, x, y) for f, x, y, _ in items])

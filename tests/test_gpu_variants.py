@@ -75,15 +75,42 @@ def test_every_variant_with_congruent_arrays(func, off):
     x = xbuf[off:off + n]
     x.copy_(torch.from_numpy(xh))
     y = ybuf[off:off + rows * n]
+    guard = torch.full_like(ybuf, 12345.0)
     for v in range(NUM_VARIANTS):
         try:
             crm.set_variant(func, v, form="df")
         except crm.CrmError:
             continue
-        y.fill_(0)
+        ybuf.copy_(guard)
         crm.eval_into(func, x, y, form="df")
         got = y.cpu().numpy().view(bits)
         assert np.array_equal(got, ref), f"{func} variant {v} ({crm.variant_info(v)}) off {off}"
+        # nothing written outside the output
+        assert torch.equal(ybuf[:off], guard[:off]) and torch.equal(ybuf[off + rows * n:], guard[off + rows * n:]), \
+            f"{func} variant {v}: a write outside the output array"
+    crm.set_variant(func, 1, form="df")
+
+
+@pytest.mark.parametrize("func", ["asinf", "sincosf", "expf", "tanf"])
+def test_packing_shapes_on_ragged_sizes(func):
+    """The packing shapes on arrays whose last vectors leave lanes or whole warps idle
+    (mostly easy arguments, so that packing runs): the oracle's bits, and no write outside
+    the output (guard words on both sides)."""
+    rng = W.rng_for(7, func, salt=5)
+    rows = 2 if func == "sincosf" else 1
+    for v in (11, 12):
+        crm.set_variant(func, v, form="df")
+        for n in (1, 7, 31, 33, 100, 257, 1000, 4099, 65537, 300001):
+            xb = W.domain_bits(func, n, rng)
+            ref = O.eval_bits(func, xb).reshape(-1)
+            x = torch.from_numpy(xb.view(np.float32)).cuda()
+            ybuf = torch.full((rows * n + 128,), 12345.0, device="cuda")
+            y = ybuf[64:64 + rows * n]
+            crm.eval_into(func, x, y, form="df")
+            got = y.cpu().numpy().view(np.uint32)
+            assert np.array_equal(got, ref), f"{func} variant {v} n {n}"
+            assert bool((ybuf[:64] == 12345.0).all()) and bool((ybuf[64 + rows * n:] == 12345.0).all()), \
+                f"{func} variant {v} n {n}: a write outside the output array"
     crm.set_variant(func, 1, form="df")
 
 

@@ -50,12 +50,12 @@ FALLBACK_HBM_GBS = 6800.0
 # shape 9, binary64 the domain / bit-pattern arrays in shape 1 -- divided by the elements of
 # that launch), with the fingerprint of the kernel sources it was taken on; a
 # traffic figure is reported only while the sources still match.
-TRAFFIC_BYTES_PER_ELEM = {"expf": 7.056, "exp2f": 7.01, "exp10f": 7.066, "expm1f": 7.043, "logf": 7.059,
-                          "log2f": 7.08, "log10f": 7.072, "log1pf": 7.061, "sinf": 7.177, "cosf": 7.147,
-                          "sincosf": 10.956, "tanf": 7.291, "asinf": 7.187, "acosf": 7.186, "atanf": 7.211,
-                          "sinhf": 7.065, "coshf": 7.101, "tanhf": 7.154, "rsqrtf": 6.599, "exp2": 14.546,
-                          "log": 14.536, "exp": 14.527, "exp10": 14.531, "log2": 14.549, "log10": 14.545}
-TRAFFIC_SOURCES = "507dc5b643487212"  # the kernel sources the ncu captures were taken on
+TRAFFIC_BYTES_PER_ELEM = {"expf": 7.055, "exp2f": 7.018, "exp10f": 7.068, "expm1f": 7.051, "logf": 7.058,
+                          "log2f": 7.077, "log10f": 7.073, "log1pf": 7.062, "sinf": 7.175, "cosf": 7.147,
+                          "sincosf": 10.959, "tanf": 7.301, "asinf": 7.183, "acosf": 7.182, "atanf": 7.216,
+                          "sinhf": 7.064, "coshf": 7.088, "tanhf": 7.149, "rsqrtf": 6.595, "exp2": 14.542,
+                          "log": 14.541, "exp": 14.511, "exp10": 14.524, "log2": 14.552, "log10": 14.539}
+TRAFFIC_SOURCES = "f16b8cf6b0d47dec"  # the kernel sources the ncu captures were taken on
 
 
 def kernel_sources_fingerprint() -> str:
@@ -99,16 +99,33 @@ INST_PER_ELEM_SET = {"exp2:domain": 210.3, "exp2:u20": 192.8, "log:bits": 388.5,
                      "exp:edomain": 226.8, "log2:bits": 457.4, "log10:bits": 459.3, "exp10:tdomain": 226.8,
                      "expf:u10": 49.0, "expf:log": 62.8, "logf:u10": 82.0, "logf:log": 71.3,
                      "sinf:u10": 98.8, "sinf:log": 128.6, "tanhf:u10": 119.0, "tanhf:log": 115.4,
-                     "rsqrtf:u10": 67.5, "rsqrtf:log": 65.1, "sinf:large": 129.8,
-                     "cosf:u10": 92.5, "sincosf:u10": 118.8, "tanf:u10": 111.9}
+                     "rsqrtf:u10": 67.5, "rsqrtf:log": 65.1, "sinf:large": 129.8, "cosf:u10": 92.5,
+                     "sincosf:u10": 118.8, "tanf:u10": 111.9}
 
 
-def inst_per_elem(func: str, label: str = ""):
+# The same per element for the packing launch shapes (captured in shape 11 on the headline's
+# inputs), used for an array whose autotuned shape packs.
+INST_PER_ELEM_PACK = {"expf": 49.5, "exp2f": 47.4, "exp10f": 50.9, "expm1f": 55.4, "sinhf": 54.7,
+                      "coshf": 48.1, "tanhf": 47.0, "log1pf": 75.7, "sinf": 118.2, "cosf": 116.6,
+                      "sincosf": 137.9, "tanf": 127.9, "asinf": 46.5, "acosf": 68.5, "atanf": 71.2}
+
+
+def inst_per_elem(func: str, label: str = "", packs: bool = False):
     if kernel_sources_fingerprint() != TRAFFIC_SOURCES:
         return None
+    if packs:
+        return INST_PER_ELEM_PACK.get(func)
     if label in INST_PER_ELEM_SET:
         return INST_PER_ELEM_SET[label]
     return INST_PER_ELEM.get(func)
+
+
+def packs_now(crm, func: str, form: str) -> bool:
+    """Whether the function's current launch shape (the autotuner's choice) packs."""
+    try:
+        return bool(crm.variant_info(crm.get_variant(func, form=None if form == "auto" else form))["easy"])
+    except Exception:
+        return False
 
 
 def load_peaks():
@@ -382,7 +399,7 @@ def measure_set(args, crm, torch, dev, workload, reps=3):
         crm.eval_into(f, x, y, form=args.form)
         st = crm.stats()
         g = n / (ms / 1e3) / 1e9
-        ipe = inst_per_elem(f, lab)
+        ipe = inst_per_elem(f, lab, packs_now(crm, f, args.form))
         out[lab] = {"gelem_s": g, "hbm_frac": g * bytes_per_elem(f) / peak,
                     "issue_frac": (g * ipe / 1e3 / issue_peak_tinst_s(2070.0)) if ipe else None,
                     "plain_gelem_s": (n / (ms_plain / 1e3) / 1e9) if ms_plain else None,
@@ -571,7 +588,7 @@ def main():
     for i, lab in enumerate(labels):
         n = xs[i].numel()
         gi = n / (ms_main[i] / 1e3) / 1e9
-        ipe = inst_per_elem(funcs[i])
+        ipe = inst_per_elem(funcs[i], packs=packs_now(crm, funcs[i], args.form))
         per_arr[lab] = {
             args.form: {"gelem_s": gi, "hbm_frac": gi * bytes_per_elem(funcs[i]) / peak,
                         "issue_frac": (gi * ipe / 1e3 / issue_peak_tinst_s(2070.0)) if ipe else None},
@@ -590,7 +607,7 @@ def main():
     # The binding bound of these kernels is instruction issue: thread instructions per
     # element (ncu, the kernel's own sources) x elements / time, against 152 SMs x 4
     # schedulers x 32 lanes x the SM clock (2070 MHz, the clock measured under load)
-    dom_ipe = inst_per_elem(funcs[dom])
+    dom_ipe = inst_per_elem(funcs[dom], packs=packs_now(crm, funcs[dom], args.form))
     if dom_ipe:
         ach_i = xs[dom].numel() * dom_ipe / (ms_main[dom] / 1e3) / 1e12
         pk_i = issue_peak_tinst_s(2070.0)

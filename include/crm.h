@@ -221,6 +221,8 @@ int crm_set_batch_mode(int mode);
    evaluator) and evaluates only those; functions without such arguments (log, log2, log10,
    rsqrt, the binary64 ones) do not provide it.  The autotuner times these shapes beside the
    others: they win on data whose magnitudes span many binades, and lose a little elsewhere.
+   crm_eval_host on mapped host buffers runs the same shape without packing (the packed
+   results are stored one by one, which the host link serves slowly).
    Every variant computes the same bits.  Output pointers may be NULL. */
 #define CRM_NUM_VARIANTS 13
 int crm_variant_info(int variant, int *unroll, int *block, int *prefetch, int *pipelined, int *min_blocks,

@@ -28,6 +28,15 @@ constexpr VariantInfo VARIANTS[NVARIANT] = {
     {1, 512, 1, 0, 1, 32, 0, 0}, {2, 512, 1, 0, 1, 16, 1, 0}, {1, 512, 1, 0, 1, 32, 0, 1},
     {2, 512, 1, 0, 1, 16, 0, 1}};
 
+// The packing shapes are shapes 9 and 7 with packing (host-memory calls map them back).
+constexpr bool same_shape(const VariantInfo &a, const VariantInfo &b) {
+  return a.unroll == b.unroll && a.block == b.block && a.prefetch == b.prefetch && a.pipelined == b.pipelined &&
+         a.min_blocks == b.min_blocks && a.vec_bytes == b.vec_bytes && a.reg_table == b.reg_table;
+}
+static_assert(same_shape(VARIANTS[11], VARIANTS[9]) && same_shape(VARIANTS[12], VARIANTS[7]) &&
+                  VARIANTS[11].easy && VARIANTS[12].easy && !VARIANTS[9].easy && !VARIANTS[7].easy,
+              "packing shapes 11 and 12 are shapes 9 and 7 with packing");
+
 struct FuncEntry {
   launch_fn main[3][NVARIANT];  // [form][variant]; form 0 unused; null when unavailable
   const void *main_sym[3][NVARIANT];

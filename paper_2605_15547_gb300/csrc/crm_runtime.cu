@@ -583,7 +583,12 @@ int crm_eval_host(int func_id, int dtype, int form, const void *in, void *out, u
     cudaStream_t s = (cudaStream_t)stream;
     int st = check_args(func_id, dtype, din, dout, n);
     if (st) return st;
-    st = enqueue(func_id, form, din, dout, n, s, 0);
+    // the packing shapes store the packed elements' results one by one, in small writes
+    // that the host link serves slowly: take the same shape without packing
+    const int fm = resolve_form(g_table[func_id], form);
+    int v = variant_of(func_id, fm);
+    if (VARIANTS[v].easy) v = VARIANTS[v].vec_bytes == 32 ? 9 : 7;
+    st = enqueue(func_id, form, din, dout, n, s, 0, v);
     if (st) return st;
     cudaError_t e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? CRM_OK : cuda_fail(e);

@@ -115,3 +115,47 @@ def test_exhaustive_sincosf_is_sinf_cosf():
         ok = torch.equal(sc[:EH.CHUNK].view(torch.int32), s.view(torch.int32)) and \
             torch.equal(sc[EH.CHUNK:].view(torch.int32), co.view(torch.int32))
         assert ok, f"sincosf differs from (sinf, cosf) in chunk {c}"
+
+
+EASY = [f for f in SINGLE if f not in ("logf", "log2f", "log10f", "rsqrtf")]
+
+
+@pytest.mark.parametrize("func", EASY)
+def test_exhaustive_packing_shape(func, weights):
+    """The packing launch shape (tiny arguments resolved without the evaluator, the rest
+    packed across the warp) against the oracle on all 2^32 inputs: a warp's vector of
+    consecutive bit patterns is all easy, none or a mix, so every easy() bound is checked
+    on every input below and around it."""
+    ref = EH.read_fixture(os.path.join(GOLDEN, func + ".txt"))
+    w1, w2 = weights
+    y = torch.empty(EH.CHUNK, dtype=torch.float32, device="cuda")
+    v = next(i for i in range(crm._lib.NUM_VARIANTS) if crm.variant_info(i)["easy"])
+    crm.set_variant(func, v, form="df")
+    crm.stats_reset()
+    try:
+        bad = [c for c in sorted(ref)
+               if (crm.eval_into(func, chunk_input(c), y, form="df") or
+                   EH.digest_torch(y.view(torch.int32), w1, w2)) != ref[c]]
+    finally:
+        crm.set_variant(func, 1, form="df")
+    assert not bad, f"{func} (packing): chunks {bad[:8]} differ from the oracle"
+    assert crm.stats()["unresolved_total"] == 0
+
+
+def test_exhaustive_sincosf_packing_is_sinf_cosf():
+    v = next(i for i in range(crm._lib.NUM_VARIANTS) if crm.variant_info(i)["easy"])
+    s = torch.empty(EH.CHUNK, dtype=torch.float32, device="cuda")
+    co = torch.empty_like(s)
+    sc = torch.empty(2 * EH.CHUNK, dtype=torch.float32, device="cuda")
+    crm.set_variant("sincosf", v, form="df")
+    try:
+        for c in range(EH.NCHUNKS):
+            x = chunk_input(c)
+            crm.eval_into("sinf", x, s)
+            crm.eval_into("cosf", x, co)
+            crm.eval_into("sincosf", x, sc)
+            ok = torch.equal(sc[:EH.CHUNK].view(torch.int32), s.view(torch.int32)) and \
+                torch.equal(sc[EH.CHUNK:].view(torch.int32), co.view(torch.int32))
+            assert ok, f"sincosf (packing) differs from (sinf, cosf) in chunk {c}"
+    finally:
+        crm.set_variant("sincosf", 1, form="df")

@@ -26,7 +26,7 @@ struct KArgs {
   void *out;
   uint64_t n;        // elements
   uint64_t head;     // leading elements handled by the scalar loop (alignment)
-  uint64_t nvec;     // float4 / double2 vectors after the head
+  uint64_t nvec;     // float4 / double2 vectors after the head (k_dir, 16-bit formats: 8-half vectors)
   crm_ws_header *hdr;
   crm_queue_entry *q;
   uint64_t cap;      // queue capacity (entries)
@@ -737,8 +737,8 @@ CRM_DEV bool dir_eval(typename Fn::T x, const unsigned char *sm, typename Fn::T 
 // Binary32 / binary64 results: 16-byte vectors [head, head + W nvec) of the array (the
 // geometry of k_main), one vector per thread per step with the next one loaded ahead;
 // every element's (candidate, sign) goes through the finisher, hard lanes are queued
-// (their stored value is replaced by k_dir_slow).  The scalar loop takes the head and the
-// tail, and the whole array for the 16-bit formats (nvec = 0).
+// (their stored value is replaced by k_dir_slow).  The 16-bit formats take 16-byte vectors
+// of 8 halves instead (nvec counts those).  The scalar loop takes the head and the tail.
 template <class Fn>
 __global__ void __launch_bounds__(KBLOCK) k_dir(KArgs a) {
   using T = typename Fn::T;
@@ -747,8 +747,9 @@ __global__ void __launch_bounds__(KBLOCK) k_dir(KArgs a) {
   __shared__ __align__(16) unsigned char sm[(Fn::template tab_bytes<2>() > 0) ? Fn::template tab_bytes<2>() : 16];
   load_tab<Fn, 2>(sm);
   const uint32_t stride = gridDim.x * (uint32_t)KBLOCK;
-  for (uint64_t seg = 0; seg < a.nvec; seg += KSEG) {
-    const uint32_t nv = (uint32_t)(a.nvec - seg < KSEG ? a.nvec - seg : KSEG);
+  const uint64_t nvec_own = a.fmt == 0 ? a.nvec : 0;  // vectors of the function's own format
+  for (uint64_t seg = 0; seg < nvec_own; seg += KSEG) {
+    const uint32_t nv = (uint32_t)(nvec_own - seg < KSEG ? nvec_own - seg : KSEG);
     const V *in4 = (const V *)((const T *)a.in + a.head) + seg;
     V *out4 = (V *)((T *)a.out + a.head) + seg;
     V *out4b = (V *)((T *)a.out + a.n + a.head) + seg;  // second output (sincos)
@@ -796,8 +797,63 @@ __global__ void __launch_bounds__(KBLOCK) k_dir(KArgs a) {
       xv = nx;
     }
   }
-  // scalar part: the head [0, head) and the tail [head + W nvec, n)
-  const uint64_t tail0 = a.head + (uint64_t)W * a.nvec;
+  // 16-bit formats: 16-byte vectors of 8 inputs (widened to binary32 exactly), the results
+  // finished into the format and stored 8 at a time
+  if constexpr (sizeof(T) == 4) {
+    if (a.fmt != 0) {
+      const uint32_t nv = (uint32_t)a.nvec;  // below 2^31 (crm_eval_rm caps it; the rest is the tail)
+      const uint4 *in8 = (const uint4 *)((const uint16_t *)a.in + a.head);
+      uint4 *out8 = (uint4 *)((uint16_t *)a.out + a.head);
+      uint4 *out8b = (uint4 *)((uint16_t *)a.out + a.n + a.head);
+      for (uint32_t base = blockIdx.x * (uint32_t)KBLOCK; base < nv; base += stride) {  // whole warps
+        const uint32_t v = base + threadIdx.x;
+        const bool act = v < nv;
+        const uint4 raw = act ? __ldcs(in8 + v) : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+        uint32_t o0[4] = {0u, 0u, 0u, 0u}, o1[4] = {0u, 0u, 0u, 0u};
+        float xs[8];
+        bool h[8];
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          const uint16_t hb = (uint16_t)(w[j >> 1] >> (16 * (j & 1)));
+          xs[j] = a.fmt == 2 ? from16<true>(hb) : from16<false>(hb);
+          float y[2];
+          int sg[2];
+          h[j] = dir_eval<Fn>(xs[j], sm, y, sg, a) && act;
+          any = any || h[j];
+          const uint32_t r0 = a.fmt == 2 ? finish_16<true>(y[0], sg[0], a.rm) : finish_16<false>(y[0], sg[0], a.rm);
+          o0[j >> 1] |= r0 << (16 * (j & 1));
+          if (Fn::NOUT == 2) {
+            const uint32_t r1 = a.fmt == 2 ? finish_16<true>(y[1], sg[1], a.rm) : finish_16<false>(y[1], sg[1], a.rm);
+            o1[j >> 1] |= r1 << (16 * (j & 1));
+          }
+        }
+        if (act) {
+          __stcs(out8 + v, make_uint4(o0[0], o0[1], o0[2], o0[3]));
+          if (Fn::NOUT == 2) __stcs(out8b + v, make_uint4(o1[0], o1[1], o1[2], o1[3]));
+        }
+        if (__any_sync(0xFFFFFFFFu, any)) {
+          const unsigned hm = hard_mask<8>(h, false);
+          uint64_t ii[8], xb[8];
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            ii[j] = a.head + (uint64_t)v * 8 + j;
+            xb[j] = fbits(xs[j]);
+          }
+          const unsigned over = push_hard<8>(hm, ii, xb, a);
+          if (over) {
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+              if ((over >> j) & 1u) dir_slow_store<Fn>(xs[j], ii[j], a);
+          }
+        }
+      }
+    }
+  }
+  // scalar part: the head [0, head) and the tail [head + Wv nvec, n)
+  const uint64_t Wv = sizeof(T) == 4 && a.fmt != 0 ? 8 : (uint64_t)W;
+  const uint64_t tail0 = a.head + Wv * a.nvec;
   const uint64_t nscal = a.head + (a.n - tail0);
   const uint64_t sstride = (uint64_t)gridDim.x * KBLOCK * DIR_UNROLL;
   for (uint64_t b = (uint64_t)blockIdx.x * KBLOCK * DIR_UNROLL; b < nscal; b += sstride) {

@@ -470,11 +470,22 @@ int crm_eval_rm(int func_id, int dtype, int rmode, const void *in, void *out, ui
   a.force_hard = g_force_slow;
   a.rm = rmode;
   a.fmt = dtype == CRM_F16 ? 1 : (dtype == CRM_BF16 ? 2 : 0);
-  // binary32 / binary64: 16-byte vectors between a scalar head and tail (k_main's
-  // geometry); the 16-bit formats: scalar elements only
-  if (a.fmt == 0) fill_geometry(fe, in, out, n, a, 16);
+  // 16-byte vectors between a scalar head and tail (k_main's geometry): 4 binary32 or 2
+  // binary64 elements, or 8 halves for the 16-bit formats (in and out congruent modulo 16
+  // bytes, and for sincosf the second output too)
+  uint64_t W = dtype == CRM_F64 ? 2 : 4;
+  if (a.fmt == 0) {
+    fill_geometry(fe, in, out, n, a, 16);
+  } else {
+    W = 8;
+    const uintptr_t ia = (uintptr_t)in, oa = (uintptr_t)out;
+    const bool vec = ((ia - oa) % 16) == 0 && (fe.nout == 1 || (n * 2) % 16 == 0);
+    a.head = vec ? ((16 - ia % 16) % 16) / 2 : 0;
+    if (a.head > n) a.head = n;
+    a.nvec = vec ? (n - a.head) / 8 : 0;
+    if (a.nvec >= (1ull << 31)) a.nvec = (1ull << 31) - 1;  // 32-bit vector indices; the rest is the tail
+  }
   const int sms = dev_sms();
-  const uint64_t W = dtype == CRM_F64 ? 2 : 4;
   const uint64_t nscal = a.head + (n - a.head - W * a.nvec);
   const uint64_t want_v = (a.nvec + KBLOCK - 1) / KBLOCK;
   const uint64_t want_s = (nscal + (uint64_t)KBLOCK * DIR_UNROLL - 1) / ((uint64_t)KBLOCK * DIR_UNROLL);

@@ -187,6 +187,32 @@ def test_16bit_formats_slow_path(func, fmt):
         crm.set_force_slow(False)
 
 
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+@pytest.mark.parametrize("func", ["expf", "sincosf", "atanf"])
+def test_16bit_ragged_and_misaligned(func, fmt):
+    """The 16-bit path's 16-byte vectors between a scalar head and tail: every start offset
+    modulo 8 halves and ragged lengths, in place or not, with guard halves around the
+    output that must stay untouched."""
+    rng = np.random.default_rng(5)
+    rows = 2 if func == "sincosf" else 1
+    dt = torch.float16 if fmt == "f16" else torch.bfloat16
+    for n in (1, 7, 8, 9, 63, 1000, 4101):
+        xb = rng.integers(0, 1 << 16, n).astype(np.uint16)
+        ref = O.eval_bits16(func, xb, fmt, "rd").reshape(-1)
+        for off in range(0, 8, 3):
+            xbuf = torch.zeros(n + 16, dtype=torch.int16, device="cuda")
+            xbuf[off:off + n] = torch.from_numpy(xb.astype(np.int16)).cuda()
+            x = xbuf[off:off + n].view(dt)
+            for oo in (off, (off + 5) % 8):
+                ybuf = torch.full((rows * n + 32,), 0x5A5A, dtype=torch.int16, device="cuda")
+                y = ybuf[oo + 8:oo + 8 + rows * n].view(dt)
+                crm.eval_rm(func, x, "rd", out=y)
+                got = y.view(torch.int16).cpu().numpy().view(np.uint16)
+                assert np.array_equal(got, ref), f"{func} {fmt} n {n} offsets {off} {oo}"
+                assert bool((ybuf[:oo + 8] == 0x5A5A).all()) and bool((ybuf[oo + 8 + rows * n:] == 0x5A5A).all()), \
+                    f"{func} {fmt} n {n}: a write outside the output"
+
+
 def chunk_input(c):
     base = c << EH.CHUNK_LOG2
     bits = torch.arange(base, base + EH.CHUNK, dtype=torch.int64, device="cuda")

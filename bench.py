@@ -50,12 +50,12 @@ FALLBACK_HBM_GBS = 6800.0
 # shape 9, binary64 the domain / bit-pattern arrays in shape 1 -- divided by the elements of
 # that launch), with the fingerprint of the kernel sources it was taken on; a
 # traffic figure is reported only while the sources still match.
-TRAFFIC_BYTES_PER_ELEM = {"expf": 7.055, "exp2f": 7.018, "exp10f": 7.059, "expm1f": 7.045, "logf": 7.059,
-                          "log2f": 7.066, "log10f": 7.079, "log1pf": 7.061, "sinf": 7.177, "cosf": 7.158,
-                          "sincosf": 10.956, "tanf": 7.291, "asinf": 7.181, "acosf": 7.186, "atanf": 7.198,
-                          "sinhf": 7.067, "coshf": 7.1, "tanhf": 7.15, "rsqrtf": 6.601, "exp2": 14.545,
-                          "log": 14.546, "exp": 14.526, "exp10": 14.525, "log2": 14.55, "log10": 14.548}
-TRAFFIC_SOURCES = "d2743f7b55386d9f"  # the kernel sources the ncu captures were taken on
+TRAFFIC_BYTES_PER_ELEM = {"expf": 7.052, "exp2f": 7.014, "exp10f": 7.071, "expm1f": 7.052, "logf": 7.058,
+                          "log2f": 7.074, "log10f": 7.073, "log1pf": 7.064, "sinf": 7.174, "cosf": 7.156,
+                          "sincosf": 10.957, "tanf": 7.295, "asinf": 7.185, "acosf": 7.185, "atanf": 7.21,
+                          "sinhf": 7.061, "coshf": 7.09, "tanhf": 7.149, "rsqrtf": 6.592, "exp2": 14.546,
+                          "log": 14.554, "exp": 14.522, "exp10": 14.525, "log2": 14.56, "log10": 14.528}
+TRAFFIC_SOURCES = "cec5b209409d152a"  # the kernel sources the ncu captures were taken on
 
 
 def kernel_sources_fingerprint() -> str:

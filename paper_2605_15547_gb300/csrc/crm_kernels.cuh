@@ -270,38 +270,35 @@ CRM_DEV bool easy_vector(const V &xv, uint32_t v0, bool act, V *out4, V *out4b, 
   // a sample first: with fewer than 8 easy elements among the warp's first slot, the
   // vector is taken to have too few to repay the packing (one vote per vector)
   if (__popc(__ballot_sync(0xFFFFFFFFu, act && Fn::easy(vget(xv, 0), y))) < 8) return false;
-  unsigned nb[W];  // lanes whose element j needs the evaluator
+  // one pass: each element's easy result, and the others packed into the buffer at their
+  // place among the warp's (ballot prefix), whatever their count (at most 32 W)
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t *ci = (uint32_t *)(cw + 32 * W);
+  V y0, y1;
   int M = 0;
 #pragma unroll
   for (int j = 0; j < W; j++) {
-    nb[j] = __ballot_sync(0xFFFFFFFFu, act && !Fn::easy(vget(xv, j), y));  // no lane past the end
-    M += __popc(nb[j]);
-  }
-  if (M > 32 * (W - 1)) return false;
-  if (act) {  // the easy results; the others are overwritten below, in warp order
-    V y0, y1;
-#pragma unroll
-    for (int j = 0; j < W; j++) {
-      Fn::easy(vget(xv, j), y);
-      vset(y0, j, y[0]);
-      if (Fn::NOUT == 2) vset(y1, j, y[1]);
+    const T x = vget(xv, j);
+    const bool need = act && !Fn::easy(x, y);  // no lane past the end
+    vset(y0, j, y[0]);
+    if (Fn::NOUT == 2) vset(y1, j, y[1]);
+    const unsigned nb = __ballot_sync(0xFFFFFFFFu, need);
+    if (need) {
+      const int k = M + __popc(nb & lt);
+      cw[k] = x;
+      ci[k] = (uint32_t)(lane * W + j);
     }
+    M += __popc(nb);
+  }
+  if (M > 32 * (W - 1)) {  // packing saves no round: the buffer's contents are dropped
+    __syncwarp();
+    return false;
+  }
+  if (act) {  // the easy results; the others are overwritten below, in warp order
     st_stream(out4 + v0 + lane, y0);
     if (Fn::NOUT == 2) st_stream(out4b + v0 + lane, y1);
   }
   if (M == 0) return true;
-  const unsigned lt = (1u << lane) - 1u;
-  uint32_t *ci = (uint32_t *)(cw + 32 * W);
-  int base = 0;
-#pragma unroll
-  for (int j = 0; j < W; j++) {
-    if ((nb[j] >> lane) & 1u) {
-      const int k = base + __popc(nb[j] & lt);
-      cw[k] = vget(xv, j);
-      ci[k] = (uint32_t)(lane * W + j);
-    }
-    base += __popc(nb[j]);
-  }
   __syncwarp();  // also orders the vector stores above before the element stores below
   const uint64_t e0 = a.head + (seg + v0) * W;  // the warp's first element
   T *out = (T *)a.out;

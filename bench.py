@@ -50,12 +50,12 @@ FALLBACK_HBM_GBS = 6800.0
 # shape 9, binary64 the domain / bit-pattern arrays in shape 1 -- divided by the elements of
 # that launch), with the fingerprint of the kernel sources it was taken on; a
 # traffic figure is reported only while the sources still match.
-TRAFFIC_BYTES_PER_ELEM = {"expf": 7.052, "exp2f": 7.014, "exp10f": 7.071, "expm1f": 7.052, "logf": 7.058,
-                          "log2f": 7.074, "log10f": 7.073, "log1pf": 7.064, "sinf": 7.174, "cosf": 7.156,
-                          "sincosf": 10.957, "tanf": 7.295, "asinf": 7.185, "acosf": 7.185, "atanf": 7.21,
-                          "sinhf": 7.061, "coshf": 7.09, "tanhf": 7.149, "rsqrtf": 6.592, "exp2": 14.546,
-                          "log": 14.554, "exp": 14.522, "exp10": 14.525, "log2": 14.56, "log10": 14.528}
-TRAFFIC_SOURCES = "cec5b209409d152a"  # the kernel sources the ncu captures were taken on
+TRAFFIC_BYTES_PER_ELEM = {"expf": 7.053, "exp2f": 7.017, "exp10f": 7.069, "expm1f": 7.039, "logf": 7.062,
+                          "log2f": 7.09, "log10f": 7.074, "log1pf": 7.062, "sinf": 7.177, "cosf": 7.147,
+                          "sincosf": 10.951, "tanf": 7.293, "asinf": 7.181, "acosf": 7.186, "atanf": 7.188,
+                          "sinhf": 7.066, "coshf": 7.106, "tanhf": 7.149, "rsqrtf": 6.598, "exp2": 14.543,
+                          "log": 14.542, "exp": 14.537, "exp10": 14.522, "log2": 14.549, "log10": 14.538}
+TRAFFIC_SOURCES = "72feb99f1de5ccc9"  # the kernel sources the ncu captures were taken on
 
 
 def kernel_sources_fingerprint() -> str:
@@ -105,9 +105,9 @@ INST_PER_ELEM_SET = {"exp2:domain": 210.3, "exp2:u20": 192.8, "log:bits": 388.5,
 
 # The same per element for the packing launch shapes (captured in shape 11 on the headline's
 # inputs), used for an array whose autotuned shape packs.
-INST_PER_ELEM_PACK = {"expf": 49.5, "exp2f": 47.4, "exp10f": 50.9, "expm1f": 55.4, "sinhf": 54.7,
-                      "coshf": 48.1, "tanhf": 47.0, "log1pf": 75.7, "sinf": 118.2, "cosf": 116.6,
-                      "sincosf": 137.9, "tanf": 127.9, "asinf": 46.5, "acosf": 68.5, "atanf": 71.2}
+INST_PER_ELEM_PACK = {"expf": 48.0, "exp2f": 45.9, "exp10f": 49.4, "expm1f": 54.1, "sinhf": 53.2,
+                      "coshf": 46.3, "tanhf": 45.6, "log1pf": 74.2, "sinf": 117.1, "cosf": 115.6,
+                      "sincosf": 137.2, "tanf": 126.9, "asinf": 45.2, "acosf": 67.2, "atanf": 71.5}
 
 
 def inst_per_elem(func: str, label: str = "", packs: bool = False):

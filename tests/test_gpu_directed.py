@@ -213,6 +213,28 @@ def test_16bit_ragged_and_misaligned(func, fmt):
                     f"{func} {fmt} n {n}: a write outside the output"
 
 
+@pytest.mark.parametrize("func", ["asinf", "sincosf", "expf", "atanf"])
+def test_binary32_directed_ragged_with_guards(func):
+    """The directed kernel's vectors (and their packing of easy arguments) on ragged sizes
+    and a misaligned start, with guard words around the output."""
+    rng = W.rng_for(9, func)
+    rows = 2 if func == "sincosf" else 1
+    for mode in ("rd", "rz"):
+        for n in (1, 33, 1000, 4101, 65537):
+            xb = W.domain_bits(func, n, rng)
+            ref = O.eval_bits(func, xb, mode=mode).reshape(-1)
+            for off in (0, 1):
+                xbuf = torch.zeros(n + 8, dtype=torch.float32, device="cuda")
+                xbuf[off:off + n] = torch.from_numpy(xb.view(np.float32)).cuda()
+                ybuf = torch.full((rows * n + 64,), 12345.0, device="cuda")
+                y = ybuf[32 + off:32 + off + rows * n]
+                crm.eval_rm(func, xbuf[off:off + n], mode, out=y)
+                got = y.cpu().numpy().view(np.uint32)
+                assert np.array_equal(got, ref), f"{func} {mode} n {n} off {off}"
+                assert bool((ybuf[:32 + off] == 12345.0).all()) and bool((ybuf[32 + off + rows * n:] == 12345.0).all()), \
+                    f"{func} {mode} n {n}: a write outside the output"
+
+
 def chunk_input(c):
     base = c << EH.CHUNK_LOG2
     bits = torch.arange(base, base + EH.CHUNK, dtype=torch.int64, device="cuda")

@@ -292,6 +292,9 @@ int crm_reserve(uint64_t max_elems, int max_arrays, void *stream);
 /* Read (and synchronise) the counters of (current device, stream). */
 int crm_stats(void *stream, crm_stats_t *out);
 int crm_stats_reset(void *stream);
+/* The number of lanes the last call on (current device, stream) queued for the slow path
+   (crm_stats' last_count): synchronises the stream and writes it to *host_out. */
+int crm_hard_case_count(void *stream, uint64_t *host_out);
 
 /* Test hook: when nonzero, every lane fails its fast-path rounding test, so the queue
    and the slow path carry the whole array (results must not change).  on = 1 also makes

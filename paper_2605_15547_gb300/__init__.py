@@ -15,6 +15,7 @@ from . import _lib as L
 from ._lib import F64_FUNCS, FORMS, FUNC_ID, FUNCS, CrmError, crm_desc_t, crm_stats_t
 
 __all__ = ["eval", "eval_into", "eval_rm", "eval_complex", "spectral_dft", "eval_host", "eval_batch", "stats", "stats_reset",
+           "hard_case_count",
            "set_form", "set_force_slow", "set_batch_tile", "reserve", "FUNCS", "FORMS", "CrmError", "version",
            "variant_info", "set_variant", "get_variant", "autotune", "autotune_batch", "set_batch_mode"]
 
@@ -194,6 +195,13 @@ def stats(stream=None) -> dict:
     return {"hard_total": s.hard_total, "unresolved_total": s.unresolved_total,
             "inline_total": s.inline_total, "last_count": s.last_count, "timeouts": s.timeouts,
             "fp64_total": s.fp64_total}
+
+
+def hard_case_count(stream=None) -> int:
+    """Lanes the last call on the stream queued for the slow path (synchronises)."""
+    v = ctypes.c_uint64()
+    L.check(L.lib().crm_hard_case_count(_stream_ptr(stream), ctypes.byref(v)))
+    return v.value
 
 
 def stats_reset(stream=None) -> None:

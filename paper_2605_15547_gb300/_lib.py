@@ -81,6 +81,7 @@ def _lib():
                 lib.crm_autotune_batch.argtypes = [ctypes.POINTER(crm_desc_t), c_int, c_int, c_int, vp, pi, pi, pf]
                 lib.crm_set_batch_mode.argtypes = [c_int]
                 lib.crm_stats.argtypes = [vp, ctypes.POINTER(crm_stats_t)]
+                lib.crm_hard_case_count.argtypes = [vp, ctypes.POINTER(c_u64)]
                 lib.crm_stats_reset.argtypes = [vp]
                 lib.crm_status_str.argtypes = [c_int]
                 lib.crm_status_str.restype = ctypes.c_char_p

@@ -533,6 +533,14 @@ int crm_reserve(uint64_t max_elems, int max_arrays, void *stream) {
   return max_arrays > 0 ? batch_buffers((cudaStream_t)stream, w, max_arrays) : CRM_OK;
 }
 
+int crm_hard_case_count(void *stream, uint64_t *host_out) {
+  if (!host_out) return CRM_ERR_NULL;
+  crm_stats_t st;
+  const int r = crm_stats(stream, &st);
+  if (r == CRM_OK) *host_out = st.last_count;
+  return r;
+}
+
 int crm_stats(void *stream, crm_stats_t *out) {
   ensure_init();
   if (!out) return CRM_ERR_NULL;

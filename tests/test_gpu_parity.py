@@ -219,3 +219,19 @@ def test_exp2f_exact_powers_and_midpoint():
 
 def test_no_unresolved_lanes():
     assert crm.stats()["unresolved_total"] == 0
+
+
+def test_hard_case_count_is_the_last_calls_queue():
+    """crm_hard_case_count: the lanes the last call queued (all non-special lanes when the
+    slow path is forced, none for an array of exactly representable results)."""
+    x = torch.from_numpy(W.domain_bits("expf", 4099, W.rng_for(1, "expf")).view(np.float32)).cuda()
+    crm.eval("expf", x)
+    assert crm.hard_case_count() == crm.stats()["last_count"]
+    crm.set_force_slow(1)
+    try:
+        crm.eval("logf", torch.linspace(0.5, 2.0, 1000, device="cuda"))
+        assert crm.hard_case_count() == 1000
+    finally:
+        crm.set_force_slow(False)
+    crm.eval("exp2f", torch.arange(-20, 20, dtype=torch.float32, device="cuda"))
+    assert crm.hard_case_count() == 0

@@ -50,12 +50,12 @@ FALLBACK_HBM_GBS = 6800.0
 # shape 9, binary64 the domain / bit-pattern arrays in shape 1 -- divided by the elements of
 # that launch), with the fingerprint of the kernel sources it was taken on; a
 # traffic figure is reported only while the sources still match.
-TRAFFIC_BYTES_PER_ELEM = {"expf": 7.053, "exp2f": 7.017, "exp10f": 7.069, "expm1f": 7.039, "logf": 7.062,
-                          "log2f": 7.09, "log10f": 7.074, "log1pf": 7.062, "sinf": 7.177, "cosf": 7.147,
-                          "sincosf": 10.951, "tanf": 7.293, "asinf": 7.181, "acosf": 7.186, "atanf": 7.188,
-                          "sinhf": 7.066, "coshf": 7.106, "tanhf": 7.149, "rsqrtf": 6.598, "exp2": 14.543,
-                          "log": 14.542, "exp": 14.537, "exp10": 14.522, "log2": 14.549, "log10": 14.538}
-TRAFFIC_SOURCES = "72feb99f1de5ccc9"  # the kernel sources the ncu captures were taken on
+TRAFFIC_BYTES_PER_ELEM = {"expf": 7.053, "exp2f": 7.02, "exp10f": 7.07, "expm1f": 7.045, "logf": 7.06,
+                          "log2f": 7.065, "log10f": 7.075, "log1pf": 7.064, "sinf": 7.173, "cosf": 7.161,
+                          "sincosf": 10.959, "tanf": 7.297, "asinf": 7.184, "acosf": 7.184, "atanf": 7.211,
+                          "sinhf": 7.063, "coshf": 7.099, "tanhf": 7.151, "rsqrtf": 6.595, "exp2": 14.544,
+                          "log": 14.539, "exp": 14.519, "exp10": 14.521, "log2": 14.549, "log10": 14.535}
+TRAFFIC_SOURCES = "a8b62e87152621e3"  # the kernel sources the ncu captures were taken on
 
 
 def kernel_sources_fingerprint() -> str:

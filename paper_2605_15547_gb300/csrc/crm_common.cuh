@@ -174,15 +174,16 @@ CRM_DEV bool hard_d_to_f(double y, uint32_t D) {
 
 // Double-float tier: y = s + r (s normal, |r| <= 2^-14 |s|, the pair need not be
 // normalised) approximates v with |v - y| <= eps_true |y|, eps_true <= 2^-37.  With
-// e = 2^-36 |s| (exact), a+ = RN(r + e) and a- = RN(r - e) lie outside
-// [r - eps_true |y|, r + eps_true |y|]: their roundings cost at most 2^-24 (|r| + e)
-// < 2^-37.9 |s|, and eps_true |y| <= 2^-37 (1 + 2^-14) |s|, together below e.  So
-// s + a- <= v <= s + a+, and as round-to-nearest is monotone, RN(s + a-) == RN(s + a+)
-// implies that both equal RN(v): the paper's comparison of the roundings of y - e and
-// y + e (Sec. II.B), with the two ends formed from the unnormalised pair.  Otherwise
-// the lane is hard.  An easy lane's result is RN(s + r), the value a normalised pair
-// would give; a NaN in s makes the lane hard.  Six operations; renormalising the pair
-// and testing the distance to the nearest midpoint would take eight.
+// e = 2^-36 |s|, a+ = RN(r + e) and a- = RN(r - e) (each one FMA on s, whose sign only
+// swaps the two) lie outside [r - eps_true |y|, r + eps_true |y|]: their roundings cost
+// at most 2^-24 (|r| + e) < 2^-37.9 |s|, and eps_true |y| <= 2^-37 (1 + 2^-14) |s|,
+// together below e.  So s + a- <= v <= s + a+, and as round-to-nearest is monotone,
+// RN(s + a-) == RN(s + a+) implies that both equal RN(v): the paper's comparison of the
+// roundings of y - e and y + e (Sec. II.B), with the two ends formed from the
+// unnormalised pair.  Otherwise the lane is hard.  An easy lane's result is RN(s + r),
+// the value a normalised pair would give; a NaN or an infinity in s makes the lane hard.
+// Five operations; renormalising the pair and testing the distance to the nearest
+// midpoint would take eight.
 //
 // With sg (the directed-rounding and 16-bit kernels) the test changes: the lane returns
 // c = RN(s + r) and *sg = the sign of v - c, which is all a rounding direction needs
@@ -191,15 +192,15 @@ CRM_DEV bool hard_d_to_f(double y, uint32_t D) {
 // |d| > e implies |y - c| > e and sign(v - c) = sign(d); otherwise v is too close to c
 // (or equal to it: an exact result) and the lane is hard.
 CRM_DEV float round_df(float s, float r, bool &hard, int *sg = nullptr) {
-  const float e = fabsf(s) * 0x1p-36f;
   if (sg) {
+    const float e = fabsf(s) * 0x1p-36f;
     const float c = s + r;
     const float d = (s - c) + r;
     hard = !(fabsf(d) > e);  // NaN: hard
     *sg = d > 0.0f ? 1 : -1;
     return c;
   }
-  const float hi = s + (r + e), lo = s + (r - e);
+  const float hi = s + fma_(s, 0x1p-36f, r), lo = s + fma_(s, -0x1p-36f, r);
   hard = hi != lo;
   return hi;
 }

@@ -59,10 +59,11 @@ template <int KIND> struct FnExpShfl {
 template <int KIND> struct FnLog {
   using T = float;
   static constexpr int NOUT = 1;
-  // plain: 97 (1/c_j, log c_j) doubles; double-float: 193 (R_j, 0, -log_b R_j) float4s
+  // plain: 97 (1/c_j, ln c_j) doubles; double-float: 193 (R_j, -ln R_j in three words)
+  // float4s (every kind: log2 and log10 scale the natural logarithm)
   template <int FORM> static constexpr int tab_bytes() { return FORM == 1 ? 97 * 16 : 193 * 16; }
   template <int FORM> CRM_DEV static void load(unsigned char *sm) {
-    copy_tab(sm, FORM == 1 ? (const void *)CRM_LN_T97_D : (const void *)log_tab_df<KIND>(), tab_bytes<FORM>());
+    copy_tab(sm, FORM == 1 ? (const void *)CRM_LN_T97_D : (const void *)CRM_LN_T193M_DF, tab_bytes<FORM>());
   }
   template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h, int *sg = nullptr) {
     if (FORM == 1)

@@ -6,8 +6,9 @@
 // The FP64 and double-double tiers use c_j = j/128 and r = (m - c_j)/c_j, |r| <= 2^-7.58,
 // with (1/c_j, log c_j) from a 97-entry table; the double-float tier uses a short
 // reciprocal R_j of j/256 (the paper's cr_log idea, Sec. II.B), so that r = m R_j - 1 is
-// exact.  log2 and log10 use tables of log2 / log10 and scale log1p(r) by 1/ln 2 or
-// 1/ln 10.  log1p(x) evaluates the polynomial on x itself for |x| < 2^-7 and otherwise
+// exact.  For log2 and log10 the FP64 and double-double tiers use tables of log2 / log10
+// and scale log1p(r) by 1/ln 2 or 1/ln 10; the double-float tier scales the natural
+// logarithm.  log1p(x) evaluates the polynomial on x itself for |x| < 2^-7 and otherwise
 // works on u = 1 + x = uh + ul (exact pair), adding ul/uh.
 #pragma once
 #include "crm_common.cuh"
@@ -17,22 +18,6 @@
 namespace crm {
 
 // KIND 0: ln, 1: log2, 2: log10, 3: log1p (ln of 1 + x)
-template <int KIND> struct LogK;
-template <> struct LogK<0> {
-  static constexpr float KH = CRM_LN2_F16_HI, KL = CRM_LN2_F16_LO;
-};
-template <> struct LogK<1> {
-  static constexpr float KH = 1.0f, KL = 0.0f;
-};
-template <> struct LogK<2> {
-  static constexpr float KH = CRM_LOG10_2_F16_HI, KL = CRM_LOG10_2_F16_LO;
-};
-template <> struct LogK<3> : LogK<0> {};
-
-// Table per kind: log1p uses the natural-log table.
-template <int KIND> CRM_DEV const float *log_tab_df() {
-  return KIND == 1 ? CRM_LOG2_T193R_DF : (KIND == 2 ? CRM_LOG10_T193R_DF : CRM_LN_T193R_DF);
-}
 template <int KIND> CRM_DEV const double *log_tab_dd() {
   return KIND == 1 ? CRM_LOG2_T97_DD : (KIND == 2 ? CRM_LOG10_T97_DD : CRM_LN_T97_DD);
 }
@@ -125,106 +110,124 @@ template <int KIND> CRM_DEV float log_plain(float x, const double2 *T97, bool &h
 }
 
 // ------------------------------------------------------------------ double-float tier
-// Decomposition in binary32 (subnormal inputs are scaled by 2^24 first), x = 2^e m with
-// m in [3/4, 3/2), j = rint(256 m), and R_j = 1/(j/256) rounded to 9 significant bits
-// (a 193-entry table with -log_b R_j as a float pair): r = m R_j - 1 is one exact FMA
-// (m R_j is a multiple of 2^-32 and |r| <= 2^-8.008 < 2^-8), and
-//   log_b x = e log_b 2 - log_b R_j + log_b(1 + r)
-// (the reduction of the paper's cr_log, Sec. II.B, with a short reciprocal).
-// log1p(r) = r - r^2/2 + r^3 (1/3 - r/4 + r^2/5): r - r^2/2 by Fast2Sum on the exact
-// square (split by FMA), the r^3 tail in float.  For log2 / log10 the pair is multiplied
-// by the float pair 1/ln 2 or 1/ln 10.  B = e K_hi - log_b R_j by one FMA (e K_hi is exact:
-// K_hi has 16 significant bits) with its rounding error recovered exactly as in Fast2Sum
-// (e == 0, or |e K_hi| > |log_b R_j|), then Fast2Sum(B, q); the sum goes to the rounding
-// test unnormalised.  Error budget, relative to the result:
-//   r^6/6 remainder 2^-50.6 abs, tail rounding 2^-49.6 abs, the table pair and the K split
-//   <= 2^-48 abs, with |result| >= 2^-9 unless e = 0 and j = 256 (then R_j = 1, all terms
-//   scale with r and the bound is 2^-40 relative); e K_lo rounding and the K split
-//   <= 2^-42 relative.  Total < 2^-39; the test allows 2^-37 (round_df: the low word is
-//   below 2^-15 of the high one).
+// Decomposition in binary32, x = 2^e m with m in [3/4, 3/2), j = rint(256 m), and R_j =
+// 1/(j/256) rounded to 9 significant bits: r = m R_j - 1 is one exact FMA (m R_j is a
+// multiple of 2^-32 and |r| <= 2^-8.008), and
+//   ln x = e ln 2 - ln R_j + log1p(r)
+// (the reduction of the paper's cr_log, Sec. II.B, with a short reciprocal).  The table
+// (CRM_LN_T193M_DF) splits L = -ln R_j into L_hi on the grid 2^-17, L_mid on the grid
+// 2^-32 (|L_mid| <= 2^-18) and L_lo, so that two sums are exact without error terms:
+//   B = e ln2_hi + L_hi (one FMA: a multiple of 2^-17 below 2^7 for |e| <= 149), and
+//   r' = r + L_mid (a multiple of 2^-32 below 2^-8).
+// log1p(r) + L_mid = r' - r^2/2 + r^3/3 - r^4/4 + r^5/5 (remainder r^6/6 <= 2^-50.6):
+//   s = RN(r' - r^2/2) by one FMA on the exact product (-r/2) r, its error z exactly
+//   (r' - s is exact, s being within a factor 2 of r'), and the tail
+//   P = (-r^2/2) r (-2/3 + r/2 - 2r^2/5) in float, added to z by one FMA.
+// Then hi = RN(B + s) by Fast2Sum (|B| >= |s| unless B = 0: with e = 0 and j != 256,
+// |L_hi| > |r| + |L_mid| + r^2, checked for every j when the table is generated) and
+// lo = (s - (hi - B)) + ((z + P) + (e ln2_lo + L_lo)).  log2 and log10 multiply the pair by
+// the float pair 1/ln 2 or 1/ln 10 (four operations).  Error budget, relative to the result:
+//   with e = 0 and j = 256 (L = 0) the terms scale with r: tail roundings 5 2^-24 r^2/3 <=
+//   2^-39.3, s's error term 2^-48; otherwise |result| >= 2^-9: tail 2^-47.3 + 2^-49.6
+//   abs, the three sums of lo 2^-24 |lo| with |lo| < 2^-25.5 (e = 0) or below 2^-24 of the
+//   result (e != 0: e ln2_lo <= |e| 2^-18), ln 2 split 2^-43 |e| abs, the table 2^-57 abs;
+//   the 1/ln b product 2^-47.  Total < 2^-38.5; the rounding test allows 2^-37.
+// Exhaustively checked: every binary32 input that passes the test returns RN(f(x)).
 //
-// us = 2^(e - eadj) m for a positive normal float us (any bit pattern gives an in-range
-// table index; the result is then meaningless and discarded), plus, for log1p, the low
-// word ul of 1 + x and the direct path for |x| < 2^-7.  Returns the unnormalised sum.
-// With EXACT_T the correction ul/us is a correctly rounded division (for callers whose result
-// can consist of that term alone, e.g. log(x^2 + y^2) with x^2 + y^2 within 2^-24 of a power
-// of two); otherwise the fast reciprocal suffices (log1pf: the term is below 2^-24 of r).
+// tb = the bit pattern of us with the exponent offset eadj folded into its exponent field
+// (fbits(us) + eadj 2^23, modulo 2^32: a subnormal input scaled by 2^24 passes eadj = -24;
+// any tb gives an in-range table index, the result is then meaningless and discarded),
+// plus, for log1p, the low word ul of 1 + x and the direct path for |x| < 2^-7 (r = x, the
+// entry of R = 1).  Returns the unnormalised pair.  With EXACT_T the correction ul/us is a
+// correctly rounded division (for callers whose result can consist of that term alone, e.g.
+// log(x^2 + y^2) with x^2 + y^2 within 2^-24 of a power of two); otherwise the fast
+// reciprocal suffices (log1pf: the term is below 2^-24 of r).
 template <int KIND, bool EXACT_T = false>
-CRM_DEV Pair<float> log_df_core(float us, int eadj, float ul, bool pathA, float x, const float4 *T193) {
-  using K = LogK<KIND>;
-  // us = 2^e m, m in [3/4, 3/2), from one integer subtraction: the exponent field of
-  // us / (3/4) rounded down is floor(log2(us / (3/4)))
-  const uint32_t b = fbits(us);
-  const int32_t ee = (int32_t)(b - 0x3F400000u) >> 23;
-  const float m = bitsf(b - ((uint32_t)ee << 23));
+CRM_DEV Pair<float> log_df_core(uint32_t tb, float us, float ul, bool pathA, float x, const float4 *T193) {
+  // m = 2^-e us in [3/4, 3/2) from one subtraction: the exponent field of us / (3/4)
+  // rounded down is floor(log2(us / (3/4)))
+  const uint32_t t = tb - 0x3F400000u;
+  const int32_t ee = (int32_t)t >> 23;
+  const float m = bitsf(t - ((uint32_t)ee << 23) + 0x3F400000u);
   const float sh = fma_(m, 256.0f, CRM_SHIFTER_F);
-  const float4 T = T193[fbits(sh) - (fbits(CRM_SHIFTER_F) + 192u)];  // (R_j, 0, L hi, lo)
-  float rh = fma_(m, T.x, -1.0f);  // exact
-  float Lh = T.z, Ll = T.w, ef = (float)(ee + eadj);
-  float t = 0.0f;
-  if (KIND == 3) {
-    t = EXACT_T ? ul / us : __fdividef(ul, us);  // ul/uh with |ul| <= 2^-24 uh
-    rh = pathA ? x : rh;
-    Lh = pathA ? 0.0f : Lh;
-    Ll = pathA ? 0.0f : Ll;
-    ef = pathA ? 0.0f : ef;
-    t = pathA ? 0.0f : t;
+  uint32_t j = fbits(sh) - (fbits(CRM_SHIFTER_F) + 192u);
+  if (KIND == 3) j = pathA ? 64u : j;  // the entry of R = 1: every L word zero
+  const float4 E = T193[j];            // (R_j, L_hi, L_mid, L_lo)
+  float r = fma_(m, E.x, -1.0f);       // exact
+  float tc = 0.0f;
+  if (KIND == 3) {  // pathA: us within 2^-7 of 1, so e = 0
+    tc = EXACT_T ? ul / us : __fdividef(ul, us);  // ul/us with |ul| <= 2^-24 us
+    r = pathA ? x : r;
+    tc = pathA ? 0.0f : tc;
   }
-  // log1p(r)
-  float h2 = rh * rh;
-  float h2l = fma_(rh, rh, -h2);
-  float q3 = fma_(rh, 0.2f, -0.25f);
-  q3 = fma_(rh, q3, 0x1.555556p-2f);
-  float P = (h2 * rh) * q3;
-  float s = fma_(h2, -0.5f, rh);
-  float z = fma_(h2, -0.5f, rh - s);
-  float rest = fma_(h2l, -0.5f, P);
-  rest = rest + (KIND == 3 ? z + t : z);
-  float qh = s, ql = rest;
+  const float rp = r + E.z;  // exact
+  const float hr = -0.5f * r;
+  const float s = fma_(hr, r, rp);
+  const float z = fma_(hr, r, rp - s);
+  float g = fma_(r, -0.4f, 0.5f);
+  g = fma_(r, g, -0x1.555556p-1f);
+  g = r * g;
+  float zp = fma_(hr * r, g, z);
+  if (KIND == 3) zp = zp + tc;
+  const float ef = (float)ee;
+  const float B = fma_(ef, CRM_LN2_F16_HI, E.y);  // exact
+  const float Bl = fma_(ef, CRM_LN2_F16_LO, E.w);
+  const float hi = B + s;
+  const float lo = (s - (hi - B)) + (zp + Bl);
   if (KIND == 1 || KIND == 2) {
     const float IH = KIND == 1 ? CRM_INV_LN2_F_HI : CRM_INV_LN10_F_HI;
     const float IL = KIND == 1 ? CRM_INV_LN2_F_LO : CRM_INV_LN10_F_LO;
-    qh = s * IH;
-    ql = fma_(s, IH, -qh);
-    ql = fma_(s, IL, ql);
-    ql = fma_(rest, IH, ql);
+    const float qh = hi * IH;
+    float ql = fma_(hi, IH, -qh);
+    ql = fma_(hi, IL, ql);
+    ql = fma_(lo, IH, ql);
+    return {qh, ql};
   }
-  // B = e K + L: B = RN(e K_hi + L_hi), e K_hi - B exact, Bz = L_hi - (B - e K_hi)
-  float B = fma_(ef, K::KH, Lh);
-  float Bz = Lh + fma_(ef, K::KH, -B);
-  float Bl = Bz + fma_(ef, K::KL, Ll);
-  // |B| > |qh| unless B = 0: with e != 0, |e K + L| >= 0.125 (log10; more for ln, log2);
-  // with e = 0 and j != 256, |log_b R_j| >= 1.97 |log_b(1 + r)| (checked over every j when
-  // the table is generated); so Fast2Sum is exact here
-  Pair<float> S = fast_two_sum(B, qh);
-  return {S.hi, S.lo + (Bl + ql)};
+  return {hi, lo};
 }
 
+// Specials: lanes outside the finite positive domain (log1p: outside (-1, inf) minus 0)
+// take the result of special_log.  The common one, a negative argument (log1p: below -1),
+// whose result is the default NaN, is a select; the rare ones (NaN, zeros, +inf; log1p
+// also -1) a branch.
 template <int KIND> CRM_DEV float log_df(float x, const float4 *T193, bool &hard, int *sg = nullptr) {
   if (KIND == 3 && sg && fabsf(x) < 0x1p-25f && x != 0.0f) {  // log1p x = x - x^2/2 + ...: just below x
     hard = false;
     *sg = -1;
     return x;
   }
-  const bool ok = log_ok<KIND>(x);
-  float us = x, ul = 0.0f;
-  int eadj = 0;
-  bool pathA = false;
+  float us, ul = 0.0f;
+  uint32_t tb;
+  bool pathA = false, ok, rare;
   if (KIND == 3) {  // 1 + x is never subnormal for x > -1
     pathA = fabsf(x) < 0x1p-7f;
-    Pair<float> u = two_sum(1.0f, x);
+    const Pair<float> u = two_sum(1.0f, x);
     us = u.hi;
     ul = u.lo;
-  } else {  // subnormal inputs by selects: they are common in bit-pattern inputs
-    const bool sub = x < 0x1p-126f;
-    us = sub ? x * 0x1p24f : x;
-    eadj = sub ? -24 : 0;
+    tb = fbits(us);
+    ok = (x > -1.0f) && (fabsf(x) < CRM_INF_F) && (x != 0.0f);
+    rare = !ok && !(x < -1.0f);
+  } else {  // subnormal inputs scaled by 2^24 (a select: they are common in bit-pattern inputs)
+    const uint32_t bx = fbits(x);
+    const float sc = bx < 0x00800000u ? 0x1p24f : 1.0f;
+    us = x * sc;
+    tb = fbits(us) - fbits(sc) + fbits(1.0f);
+    ok = (bx - 1u) < 0x7F7FFFFFu;  // positive, finite, nonzero
+    rare = !ok && !(x < 0.0f);
   }
-  Pair<float> y = log_df_core<KIND>(us, eadj, ul, pathA, x, T193);
-  if (__builtin_expect(ok, 1)) return round_df(y.hi, y.lo, hard, sg);
-  hard = false;  // NaN, zero, negative, infinite (rare: a branch, not selects)
-  put_sg(sg, 0);  // exact results
-  return special_log<KIND>(x);
+  const Pair<float> y = log_df_core<KIND>(tb, us, ul, pathA, x, T193);
+  if (sg) {  // directed rounding: a branch
+    if (__builtin_expect(ok, 1)) return round_df(y.hi, y.lo, hard, sg);
+    hard = false;
+    *sg = 0;  // exact results
+    return special_log<KIND>(x);
+  }
+  bool h;
+  const float v = round_df(y.hi, y.lo, h);
+  hard = ok && h;
+  float res = ok ? v : CRM_QNAN_F;
+  if (__builtin_expect(rare, 0)) res = special_log<KIND>(x);
+  return res;
 }
 
 // ------------------------------------------------------------------ double-double tier

@@ -223,27 +223,42 @@ for kind, base in (("LN", None), ("LOG2", 2), ("LOG10", 10)):
 # Double-float tier: c_j = j/256 (j = round(256 m), 192..384) and R_j = 1/c_j rounded to 9
 # significant bits, so that r = m R_j - 1 is one exact FMA: m R_j is a multiple of 2^-32
 # (m has 24 significant bits, R_j 9, and R_j >= 1 exactly when m < 1) and |r| < 2^-8, so r
-# is an integer below 2^24 times 2^-32; entry j-192 is (R_j, 0, -log_b(R_j) hi, lo)
-emit("// ===== log family, double-float tier: R_j = 1/(j/256) to 9 bits, j = round(256 m) in  =====")
-emit("// ===== 192..384, r = m R_j - 1 exact, log x = e log 2 - log R_j + log1p(r); entry j-192 =====")
+# is an integer below 2^24 times 2^-32.  L_j = -ln(R_j) is split three ways (log2 and log10
+# scale the natural logarithm): L_hi on the grid 2^-17, so that e ln2_hi + L_hi is exact in
+# binary32 for every exponent e of a binary32 input (|e| <= 149, ln2_hi = CRM_LN2_F16_HI, a
+# multiple of 2^-15: the sum is a multiple of 2^-17 below 2^7); L_mid on the grid 2^-32 with
+# |L_mid| <= 2^-18, so that r + L_mid is exact (a multiple of 2^-32 below 2^-8); L_lo the
+# nearest float to the rest.  Entry j-192 is (R_j, L_hi, L_mid, L_lo).
+emit("// ===== log family, double-float tier: R_j = 1/(j/256) to 9 bits, j = round(256 m) in   =====")
+emit("// ===== 192..384, r = m R_j - 1 exact, ln x = e ln 2 - ln R_j + log1p(r); entry j-192 =====")
 rmax = mp.mpf(0)
-for kind, base in (("LN", None), ("LOG2", 2), ("LOG10", 10)):
-    def lg(v):
-        return mp.log(v) if base is None else mp.log(v) / mp.log(base)
-    tf = []
-    for j in range(192, 385):
-        R = rnd(mp.mpf(256) / j, 9)
-        # |r| over m in [(j - 1/2)/256, (j + 1/2)/256] intersected with [3/4, 3/2)
-        lo_m = max(mp.mpf(j) - mp.mpf(1) / 2, 192) / 256
-        hi_m = min(mp.mpf(j) + mp.mpf(1) / 2, 384) / 256
-        rmax = max(rmax, abs(lo_m * R - 1), abs(hi_m * R - 1))
-        if j != 256:  # Fast2Sum(B, q) with e = 0 needs |log R_j| >= |log1p(r)|
-            q = max(abs(mp.log1p(lo_m * R - 1)), abs(mp.log1p(hi_m * R - 1)))
-            assert abs(mp.log(R)) >= mp.mpf("1.97") * q, j
-        L = -lg(R)
-        tf += [f(R), mp.mpf(0)] + split(L, f, 2)
-    arr_f(f"CRM_{kind}_T193R_DF", tf, f"(R_j, 0, -{kind.lower()}(R_j) hi, lo) floats, R_j 9 bits")
+GH, GM = mp.mpf(2) ** -17, mp.mpf(2) ** -32
+LN2_F16_HI = rnd(LN2, 16)
+assert mp.nint(LN2_F16_HI / 2 ** -15) * 2 ** -15 == LN2_F16_HI and 149 * LN2_F16_HI + 1 < 2 ** 24 * GH
+tf, midmax = [], mp.mpf(0)
+for j in range(192, 385):
+    R = rnd(mp.mpf(256) / j, 9)
+    # |r| over m in [(j - 1/2)/256, (j + 1/2)/256] intersected with [3/4, 3/2)
+    lo_m = max(mp.mpf(j) - mp.mpf(1) / 2, 192) / 256
+    hi_m = min(mp.mpf(j) + mp.mpf(1) / 2, 384) / 256
+    rj = max(abs(lo_m * R - 1), abs(hi_m * R - 1))
+    rmax = max(rmax, rj)
+    L = -mp.log(R)
+    Lh = mp.nint(L / GH) * GH
+    Lm = mp.nint((L - Lh) / GM) * GM
+    Ll = f(L - Lh - Lm)
+    assert f(Lh) == Lh and f(Lm) == Lm and abs(Lm) <= GH / 2
+    assert abs(L - Lh - Lm - Ll) < mp.mpf(2) ** -57
+    midmax = max(midmax, abs(Lm))
+    # Fast2Sum(e ln2_hi + L_hi, s) with e = 0 needs |L_hi| >= |s|, s = RN(r + L_mid - r^2/2)
+    if j != 256:
+        assert abs(Lh) >= (rj + abs(Lm) + rj * rj) * mp.mpf("1.01"), j
+    else:
+        assert Lh == 0 and Lm == 0 and Ll == 0
+    tf += [f(R), Lh, Lm, Ll]
+arr_f("CRM_LN_T193M_DF", tf, "(R_j, -ln(R_j) hi (grid 2^-17), mid (grid 2^-32), lo) floats, R_j 9 bits")
 assert rmax < mp.mpf(2) ** -8, rmax  # r exact (see above); max |r| = 2^-8.008
+assert rmax + midmax < mp.mpf(2) ** -8  # r + L_mid exact
 LOG10_2 = mp.log(2) / mp.log(10)
 for nm, v in (("LN2", LN2), ("LOG10_2", LOG10_2)):
     hi = rnd(v, 16)

@@ -111,7 +111,8 @@ template <int W> CRM_DEV float2 cx_eval(float x, float y, const unsigned char *s
     Pair<float> s = fast_two_sum(hh.hi, m2.hi);
     s.lo = s.lo + (m2.lo + ll.lo);
     s = fast_two_sum(s.hi, s.lo);
-    const Pair<float> L = log_df_core<3, true>(s.hi, -2 * m, s.lo, false, 0.0f, (const float4 *)(sm + CXT_LOG));
+    const Pair<float> L = log_df_core<3, true>(fbits(s.hi) + ((uint32_t)(-2 * m) << 23), s.hi, s.lo, false, 0.0f,
+                                               (const float4 *)(sm + CXT_LOG));
     out.x = 0.5f * (L.hi + L.lo);
     // atan2(y, x): the atan(a/b) core on (|y|, |x|), pi minus it for x < 0, the sign of y
     Pair<float> t = atan_ratio_df({ay, 0.0f}, {ax, 0.0f}, (const float2 *)(sm + CXT_ATAN));

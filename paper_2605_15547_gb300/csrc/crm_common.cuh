@@ -416,6 +416,13 @@ CRM_DEV void copy_tab(void *dst, const void *src, int bytes) {
 }
 
 CRM_DEV float qnan_of(float x) { return bitsf(fbits(x) | 0x00400000u); }
+// The hardware reciprocal square root, rsqrt.approx.ftz.f32: relative error below 2^-22.9
+// for a normal argument (a subnormal one is flushed to zero; callers pass normal ones).
+CRM_DEV float rsqrt_hw(float a) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
 CRM_DEV double qnan_of(double x) { return bitsd(dbits(x) | 0x0008000000000000ull); }
 #define CRM_QNAN_F (__uint_as_float(0x7FC00000u))
 #define CRM_QNAN_D (__longlong_as_double(0x7FF8000000000000ll))

@@ -168,7 +168,7 @@ template <int KIND> CRM_DEV float atrig_df(float x, const float2 *AT, bool &hard
     Pair<float> d1 = fast_two_sum(1.0f, -p);  // 1 >= p
     Pair<float> dd_ = fast_two_sum(d1.hi, d1.lo - pl);
     // d >= 2^-23 unless x = +-1 (d = 0: the floor keeps y0 finite and s = 0)
-    const float y0 = rsqrtf(fmaxf(dd_.hi, 0x1p-126f));
+    const float y0 = rsqrt_hw(fmaxf(dd_.hi, 0x1p-126f));
     float s0 = dd_.hi * y0;
     float s2 = s0 * s0;
     float s2l = fma_(s0, s0, -s2);

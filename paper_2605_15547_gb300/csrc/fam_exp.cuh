@@ -4,7 +4,7 @@
 // base 2, t = x log2(b), split t = k + j/2^J + g with a small table of 2^(j/2^J) (at most
 // 16 entries in the FP64 and double-double tiers, 64 in the double-float tier), evaluate
 // 2^g by a polynomial, and scale by 2^k with integer exponent arithmetic.  Infinite and
-// NaN inputs and the saturated ranges are handled by selects in the same pass.
+// NaN inputs and the saturated ranges are handled in the same pass.
 #pragma once
 #include "crm_common.cuh"
 #include "crm_tables.h"
@@ -102,9 +102,9 @@ template <int KIND> CRM_DEV float exp_plain(float x, const double *T16, bool &ha
 // 2 a2 gh gl 2^-39.1, t from x*C1 and the split of C 2^-40.7, a5 g^5 remainder 2^-44.6,
 // tables 2^-48, the error term and the bracket roundings 2^-47: total < 2^-37.7, inside
 // the test's 2^-37.
-// Inputs outside [X_SUB, X_OVF] are resolved by selects: +inf above X_OVF, +0 below
-// X_ZERO, a quiet NaN for NaN; results in the subnormal band [X_ZERO, X_SUB) are rounded
-// to the subnormal grid from the same pair (below).
+// Inputs outside [X_SUB, X_OVF]: +inf above X_OVF and +0 below X_ZERO (selects), a quiet
+// NaN for NaN; results in the subnormal band [X_ZERO, X_SUB) are rounded to the subnormal grid
+// from the same pair (below).
 // b^x = 2^k (s + r) to 2^-37.7 of itself (budget above); sb is the shifter's bit pattern
 // (k and the table index are read from it).
 template <int KIND> CRM_DEV void exp_df_core(float x, const float4 *T64U, float &s, float &r, uint32_t &sb) {
@@ -157,10 +157,19 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
   float s, r;
   uint32_t sb;
   exp_df_core<KIND>(x, T64U, s, r, sb);
+  // the exponent increment (N >> 6) << 23: sb >> 6 is N >> 6 plus 0x12D0000 (borrow
+  // included), whose shift by 23 vanishes modulo 2^32
   const bool ok = (x >= K::XSUB) && (x <= K::XOVF);  // false for NaN
-  if (__builtin_expect(ok, 1)) {
-    // the exponent increment (N >> 6) << 23: sb >> 6 is N >> 6 plus 0x12D0000 (borrow
-    // included), whose shift by 23 vanishes modulo 2^32
+  if (!sg) {
+    // round to nearest: overflow (+inf) and underflow to +0, common in inputs with a wide
+    // range, by selects (measured: a branch there, or a warp-uniform in-range path, loses
+    // on such inputs more than it gains on in-range ones); NaN and the subnormal band on
+    // the rare branch below
+    bool h;
+    const float y = bitsf(fbits(round_df(s, r, h)) + ((sb >> 6) << 23));
+    hard = ok && h;
+    if (__builtin_expect(ok || x > K::XOVF || x < K::XZERO, 1)) return ok ? y : (x > 0.0f ? CRM_INF_F : 0.0f);
+  } else if (__builtin_expect(ok, 1)) {
     const float y = round_df(s, r, hard, sg);
     const float out = bitsf(fbits(y) + ((sb >> 6) << 23));
     // e^x lies above 1 + x for x != 0 by x^2/2 + ..., which for |x| < 2^-12 is below the
@@ -175,7 +184,8 @@ template <int KIND> CRM_DEV float exp_df(float x, const float4 *T64U, bool &hard
     }
     return out;
   }
-  // Out of range (rare): +inf, +0, a quiet NaN, or a subnormal result.
+  // Out of range (round to nearest: NaN or the subnormal band): +inf, +0, a quiet NaN, or
+  // a subnormal result.
   hard = false;
   float y = x != x ? qnan_of(x) : (x > 0.0f ? CRM_INF_F : 0.0f);
   put_sg(sg, (x != x || fabsf(x) == CRM_INF_F) ? 0 : (x > 0.0f ? -1 : 1));
@@ -278,11 +288,11 @@ template <int KIND> CRM_DEV float exp_df16(float x, const float4 &R, bool &hard)
   uint32_t sb;
   exp_df16_core<KIND>(x, R, s, r, sb);
   const bool ok = (x >= K::XSUB) && (x <= K::XOVF);  // false for NaN
-  if (__builtin_expect(ok, 1)) {
-    const float y = round_df(s, r, hard);
-    return bitsf(fbits(y) + ((sb >> 4) << 23));  // exponent increment N >> 4, as in exp_df
-  }
-  // out of range: as in exp_df, with k = N >> 4
+  bool h;
+  const float y0 = bitsf(fbits(round_df(s, r, h)) + ((sb >> 4) << 23));  // exponent increment N >> 4
+  hard = ok && h;
+  // out of range as in exp_df's general path (k = N >> 4)
+  if (__builtin_expect(ok || x > K::XOVF || x < K::XZERO, 1)) return ok ? y0 : (x > 0.0f ? CRM_INF_F : 0.0f);
   hard = false;
   float y = x != x ? qnan_of(x) : (x > 0.0f ? CRM_INF_F : 0.0f);
   if ((x >= K::XZERO) && (x < K::XSUB)) {

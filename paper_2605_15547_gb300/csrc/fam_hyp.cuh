@@ -243,7 +243,7 @@ template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard, i
     return H == HYP_COSH ? 1.0f : x;
   }
   bool tiny = ax < 0x1p-25f;  // the correctly rounded result is x itself (or 1 for cosh)
-  bool sp;                    // NaN, tiny, saturated (results selected on a rare branch)
+  bool sp;                    // NaN, tiny, saturated (results by selects; a branch with sg)
   if (H == HYP_EXPM1) {
     // below X_MONE: -1; in [X_MONE, X_M2]: -1 + 2^-24 (the first step of the staircase)
     sp = !(x > CRM_EXPM1F_X_M2 && x <= CRM_EXPF_X_OVF) || tiny;
@@ -257,6 +257,24 @@ template <int H> CRM_DEV float hyp_df(float x, const float4 *T64U, bool &hard, i
   arg = sp ? 0.5f : arg;
   int sc = 0;
   const Pair<float> r = hyp_df_core<H>(arg, T64U, sc);
+  if (!sg) {
+    // round to nearest: tiny and saturated arguments (common: tiny bit patterns, |x| > 9
+    // for tanh on a symmetric range) and NaN by selects
+    bool h;
+    float y = scale_f(round_df(r.hi, r.lo, h), sc);
+    if (H == HYP_SINH || H == HYP_TANH) y = x < 0.0f ? -y : y;
+    hard = !sp && h;
+    float v;
+    if (H == HYP_EXPM1)
+      v = tiny ? x : (x > 0.0f ? CRM_INF_F : (x < CRM_EXPM1F_X_MONE ? -1.0f : -0x1.fffffep-1f));
+    else if (H == HYP_SINH)
+      v = tiny ? x : copysignf(CRM_INF_F, x);
+    else if (H == HYP_COSH)
+      v = tiny ? 1.0f : CRM_INF_F;
+    else
+      v = tiny ? x : copysignf(ax > CRM_TANHF_X_ONE ? 1.0f : 0x1.fffffep-1f, x);
+    return x != x ? qnan_of(x) : (sp ? v : y);
+  }
   if (__builtin_expect(!sp, 1)) {
     // r unnormalised: |r.lo| < 2^-20 |r.hi| in every branch above
     float y = scale_f(round_df(r.hi, r.lo, hard, sg), sc);

@@ -43,34 +43,34 @@ CRM_DEV float rsqrt_plain(float x, bool &hard) {
 }
 
 // ------------------------------------------------------------------ double-float tier
-// y0 = hardware reciprocal square root (relative error below 2^-21; subnormal x scaled
-// by 2^24 and x >= 2^64 by 2^-64, the result back by 2^12 or 2^-32), the residual e = 1 - x y0^2 from exact pair products
-// (1 - p is exact by Sterbenz since x y0^2 is within 2^-20 of 1), and one Newton step
-// kept as a pair: y = y0 + y0 e (1/2 + 3e/8).  |e| < 2^-20: the truncation is
-// (5/16) e^3 < 2^-61, the residual is good to 2^-48 absolute, the correction product to
-// 2^-24 of itself (2^-45 of y): relative error < 2^-44.5, inside the rounding test's
-// 2^-37; the pair (y0, c), |c| < 2^-21 y0, goes to round_df unnormalised.
+// y0 = the hardware reciprocal square root, rsqrt.approx.ftz (relative error below
+// 2^-22.9 for a normal argument; subnormal x is scaled by 2^24, the result back by 2^12),
+// the residual e = 1 - x y0^2 as 1 - h y0 - hl y0 with h + hl = x y0 exactly (h is about
+// sqrt(x), normal for every normal x): two FMAs, each rounding at most 2^-24 of a value
+// below 2^-20, so e is good to 2^-43 absolute; then one Newton step kept as a pair:
+// y = y0 + y0 e (1/2 + 3e/8).  The truncation is (5/16) e^3 < 2^-61, the correction's
+// roundings 2^-44 of y: relative error < 2^-42.5, inside the rounding test's 2^-37; the
+// pair (y0, c), |c| < 2^-21 y0, goes to round_df unnormalised.
+// Specials: a negative argument (half of a symmetric input range) takes the default NaN
+// by a select; NaN, zeros and +inf (rare) a branch.
 CRM_DEV float rsqrt_df(float x, bool &hard, int *sg = nullptr) {
-  float r;
-  bool sp = rsqrt_special(x, r);
-  bool sub = x < 0x1p-126f, big = x >= 0x1p64f;  // keep y0^2 and its error normal
-  float xs = sp ? 1.0f : (sub ? x * 0x1p24f : (big ? x * 0x1p-64f : x));
-  float y0 = rsqrtf(xs);
-  float s = y0 * y0;
-  float sl = fma_(y0, y0, -s);
-  float p = xs * s;
-  float pl = fma_(xs, s, -p);
-  float e = (1.0f - p) - fma_(xs, sl, pl);
-  float corr = fma_(e, 0.375f, 0.5f) * e;
-  float c = y0 * corr;
-  bool h;
-  const float yh = round_df(y0, c, h, sg);
-  // special inputs (x <= 0, NaN, +inf) by selects: they are common in real data (half of
-  // a symmetric input range), so a branch would diverge in most warps
-  hard = !sp && h;
-  if (sg && sp) *sg = 0;  // +-inf, NaN, +0: exact
-  float out = sub ? yh * 0x1p12f : (big ? yh * 0x1p-32f : yh);
-  return sp ? r : out;
+  const uint32_t bx = fbits(x);
+  const bool sub = bx < 0x00800000u;
+  const float xs = x * (sub ? 0x1p24f : 1.0f);
+  const float y0 = rsqrt_hw(xs);
+  const float h = xs * y0;
+  const float hl = fma_(xs, y0, -h);
+  const float e = fma_(-hl, y0, fma_(-h, y0, 1.0f));
+  const float corr = fma_(e, 0.375f, 0.5f) * e;
+  const float c = y0 * corr;
+  bool hh;
+  const float yh = round_df(y0, c, hh, sg);
+  const bool ok = (bx - 1u) < 0x7F7FFFFFu;  // positive, finite, nonzero
+  hard = ok && hh;
+  float res = ok ? yh * (sub ? 0x1p12f : 1.0f) : CRM_QNAN_F;
+  if (sg && !ok) *sg = 0;  // +-inf, NaN, +0: exact
+  if (__builtin_expect(!ok && !(x < 0.0f), 0)) rsqrt_special(x, res);
+  return res;
 }
 
 // ------------------------------------------------------------------ exact slow tier

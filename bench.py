@@ -50,12 +50,12 @@ FALLBACK_HBM_GBS = 6800.0
 # shape 9, binary64 the domain / bit-pattern arrays in shape 1 -- divided by the elements of
 # that launch), with the fingerprint of the kernel sources it was taken on; a
 # traffic figure is reported only while the sources still match.
-TRAFFIC_BYTES_PER_ELEM = {"expf": 7.053, "exp2f": 7.02, "exp10f": 7.07, "expm1f": 7.045, "logf": 7.06,
-                          "log2f": 7.065, "log10f": 7.075, "log1pf": 7.064, "sinf": 7.173, "cosf": 7.161,
-                          "sincosf": 10.959, "tanf": 7.297, "asinf": 7.184, "acosf": 7.184, "atanf": 7.211,
-                          "sinhf": 7.063, "coshf": 7.099, "tanhf": 7.151, "rsqrtf": 6.595, "exp2": 14.544,
-                          "log": 14.539, "exp": 14.519, "exp10": 14.521, "log2": 14.549, "log10": 14.535}
-TRAFFIC_SOURCES = "a8b62e87152621e3"  # the kernel sources the ncu captures were taken on
+TRAFFIC_BYTES_PER_ELEM = {"expf": 7.054, "exp2f": 7.037, "exp10f": 7.06, "expm1f": 7.064, "logf": 7.04,
+                          "log2f": 7.058, "log10f": 7.059, "log1pf": 7.09, "sinf": 7.168, "cosf": 7.157,
+                          "sincosf": 10.959, "tanf": 7.286, "asinf": 7.188, "acosf": 7.178, "atanf": 7.202,
+                          "sinhf": 7.092, "coshf": 7.138, "tanhf": 7.198, "rsqrtf": 6.568, "exp2": 14.54,
+                          "log": 14.54, "exp": 14.53, "exp10": 14.521, "log2": 14.546, "log10": 14.531}
+TRAFFIC_SOURCES = "9bacd76bbe714ca4"  # the kernel sources the ncu captures were taken on
 
 
 def kernel_sources_fingerprint() -> str:
@@ -79,10 +79,10 @@ def measured_traffic(func: str, n: int):
 # / elements, from the same captures as the traffic figures), gated by the same source
 # fingerprint as the traffic figures.  The kernels are bound by instruction issue, not by
 # DRAM: 152 SMs x 4 schedulers issue one warp instruction each per cycle.
-INST_PER_ELEM = {"expf": 55.1, "exp2f": 47.2, "exp10f": 56.1, "expm1f": 87.1, "logf": 73.2,
-                 "log2f": 72.0, "log10f": 71.8, "log1pf": 80.2, "sinf": 129.0, "cosf": 122.4,
-                 "sincosf": 147.7, "tanf": 142.0, "asinf": 135.4, "acosf": 142.2, "atanf": 105.8,
-                 "sinhf": 124.7, "coshf": 87.4, "tanhf": 113.9, "rsqrtf": 67.5, "exp2": 210.3,
+INST_PER_ELEM = {"expf": 58.0, "exp2f": 50.1, "exp10f": 58.9, "expm1f": 90.6, "logf": 53.4,
+                 "log2f": 57.5, "log10f": 57.4, "log1pf": 66.1, "sinf": 128.0, "cosf": 121.7,
+                 "sincosf": 145.7, "tanf": 141.0, "asinf": 131.4, "acosf": 138.2, "atanf": 104.7,
+                 "sinhf": 118.3, "coshf": 79.4, "tanhf": 107.7, "rsqrtf": 37.7, "exp2": 210.3,
                  "log": 388.5, "exp": 226.8, "exp10": 226.8, "log2": 457.4, "log10": 459.3}
 SMS, SCHEDULERS_PER_SM, WARP = 152, 4, 32
 
@@ -97,17 +97,17 @@ def issue_peak_tinst_s(sm_mhz: float) -> float:
 # own captures (2^25 elements of each, the binary32 ones in launch shape 9), keyed by label.
 INST_PER_ELEM_SET = {"exp2:domain": 210.3, "exp2:u20": 192.8, "log:bits": 388.5, "log:u0.125_8": 415.0,
                      "exp:edomain": 226.8, "log2:bits": 457.4, "log10:bits": 459.3, "exp10:tdomain": 226.8,
-                     "expf:u10": 49.0, "expf:log": 62.8, "logf:u10": 82.0, "logf:log": 71.3,
-                     "sinf:u10": 98.8, "sinf:log": 128.6, "tanhf:u10": 119.0, "tanhf:log": 115.4,
-                     "rsqrtf:u10": 67.5, "rsqrtf:log": 65.1, "sinf:large": 129.8, "cosf:u10": 92.5,
-                     "sincosf:u10": 118.8, "tanf:u10": 111.9}
+                     "expf:u10": 52.6, "expf:log": 57.2, "logf:u10": 52.0, "logf:log": 53.1,
+                     "sinf:u10": 97.8, "sinf:log": 127.6, "tanhf:u10": 110.1, "tanhf:log": 107.5,
+                     "rsqrtf:u10": 34.4, "rsqrtf:log": 35.6, "sinf:large": 128.8, "cosf:u10": 91.5,
+                     "sincosf:u10": 116.8, "tanf:u10": 110.9}
 
 
 # The same per element for the packing launch shapes (captured in shape 11 on the headline's
 # inputs), used for an array whose autotuned shape packs.
-INST_PER_ELEM_PACK = {"expf": 48.0, "exp2f": 45.9, "exp10f": 49.4, "expm1f": 54.1, "sinhf": 53.2,
-                      "coshf": 46.3, "tanhf": 45.6, "log1pf": 74.2, "sinf": 117.1, "cosf": 115.6,
-                      "sincosf": 137.2, "tanf": 126.9, "asinf": 45.2, "acosf": 67.2, "atanf": 71.5}
+INST_PER_ELEM_PACK = {"expf": 48.6, "exp2f": 46.5, "exp10f": 50.0, "expm1f": 54.0, "sinhf": 52.1,
+                      "coshf": 44.7, "tanhf": 44.6, "log1pf": 68.0, "sinf": 116.5, "cosf": 115.0,
+                      "sincosf": 135.9, "tanf": 126.3, "asinf": 44.2, "acosf": 66.2, "atanf": 71.0}
 
 
 def inst_per_elem(func: str, label: str = "", packs: bool = False):

@@ -112,21 +112,24 @@ template <int H> struct FnHyp {
 template <int KIND> struct FnTrig {
   using T = float;
   static constexpr int NOUT = KIND == TRIG_SINCOS ? 2 : 1;
-  // shared memory: 16 words of 2/pi, the (sin, cos)(j pi/64) table (double or
-  // float-pair entries, 16 bytes each), 8 window entries of four consecutive words of
-  // 2/pi (PW[k] = words k .. k+3, zero beyond the 16), and for tan the (tan hi, lo)(j pi/64)
-  // float pairs
-  static constexpr int OFF_PW = 64 + 32 * 16, OFF_TT = OFF_PW + 8 * 16;
-  template <int FORM> static constexpr int tab_bytes() { return OFF_TT + (KIND == TRIG_TAN ? 32 * 8 : 0); }
+  // shared memory: 16 words of 2/pi, the (sin, cos) table (FP64 form: 32 double pairs of
+  // j pi/64; double-float form: 128 float quadruples (hi, lo, hi, lo) of j pi/256; 16 bytes
+  // each), 8 window entries of four consecutive words of 2/pi (PW[k] = words k .. k+3, zero
+  // beyond the 16), and for tan the (tan hi, lo)(j pi/256) float pairs
+  static constexpr int OFF_PW = 64 + 128 * 16, OFF_TT = OFF_PW + 8 * 16;
+  template <int FORM> static constexpr int tab_bytes() { return OFF_TT + (KIND == TRIG_TAN ? 128 * 8 : 0); }
   template <int FORM> CRM_DEV static void load(unsigned char *sm) {
     copy_tab(sm, CRM_TWO_OVER_PI_W, 64);
-    copy_tab(sm + 64, FORM == 1 ? (const void *)CRM_SINCOS_T32_D : (const void *)CRM_SINCOS_T32_DF, 32 * 16);
+    if (FORM == 1)
+      copy_tab(sm + 64, CRM_SINCOS_T32_D, 32 * 16);
+    else
+      copy_tab(sm + 64, CRM_SINCOS_T128_DF, 128 * 16);
     uint32_t *pw = (uint32_t *)(sm + OFF_PW);
     for (int i = threadIdx.x; i < 32; i += blockDim.x) {
       const int w = (i >> 2) + (i & 3);
       pw[i] = w < 16 ? CRM_TWO_OVER_PI_W[w] : 0u;
     }
-    if (KIND == TRIG_TAN) copy_tab(sm + OFF_TT, CRM_TAN_T32_DF, 32 * 8);
+    if (KIND == TRIG_TAN && FORM == 2) copy_tab(sm + OFF_TT, CRM_TAN_T128_DF, 128 * 8);
   }
   template <int FORM> CRM_DEV static void eval(float x, const void *sm, float *y, bool &h, int *sg = nullptr) {
     const unsigned char *b = (const unsigned char *)sm;

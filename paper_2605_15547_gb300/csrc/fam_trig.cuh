@@ -1,16 +1,20 @@
 // fam_trig.cuh -- sinf, cosf, sincosf, tanf.
 //
-// Reduction: |x| 64/pi = 128 m + 32 q + j + f,  q = quadrant, j in [0,32), |f| <= 1/2.
+// Reduction: |x| 64/pi = 128 m + 32 q + j + f,  q = quadrant, j in [0,32), |f| <= 1/2 (the
+// FP64 and slow tiers), and |x| 256/pi = 512 m + 128 q + j + f with j in [0,128) (the
+// double-float tier, whose polynomials are shorter for the smaller t).
 // The paper reduces large trigonometric arguments on a separate branch (Sec. II.A).  Here
 // the double-float tier takes a Cody-Waite reduction in float pairs when every active
 // lane of the warp has |x| < 2^12 (a warp-uniform vote), and otherwise an integer
 // Payne-Hanek step on the 24-bit significand, which serves every magnitude: with
 // x = M 2^e, the bits of 2/pi that can change |x| 64/pi modulo 128 form a window selected
 // by e, and M times a 96-bit (fast tiers) or 160-bit (slow tier) window of 2/pi gives
-// q, j and f.  The FP64 and slow tiers always use the integer step.
-// Then t = f pi/64 (|t| <= pi/128) and, with S_j = sin(j pi/64), C_j = cos(j pi/64),
+// q, j and f (the same product read two bits further gives them for 256/pi).  The FP64
+// and slow tiers always use the integer step.
+// Then t = f pi/64 (|t| <= pi/128; double-float: f pi/256) and, with S_j = sin(j pi/64),
+// C_j = cos(j pi/64),
 //     sin(j pi/64 + t) = S_j cos t + C_j sin t,   cos(j pi/64 + t) = C_j cos t - S_j sin t,
-// rotated by the quadrant.  |x| < 2^-6 uses t = x, j = q = 0 directly.
+// rotated by the quadrant.  Small |x| uses t = x, j = q = 0 directly.
 #pragma once
 #include "crm_common.cuh"
 #include "crm_tables.h"
@@ -45,7 +49,7 @@ CRM_DEV void trig_window_mul(float ax, const uint32_t *P, uint32_t *r) {
 
 // The same product for NW = 3 with the four words P[k .. k+3] from one 16-byte entry
 // PW[k] of a window table (PW[k] = (P[k], P[k+1], P[k+2], P[k+3])): one shared-memory
-// load per element.  k = (e + 62) >> 5 lies in [1, 5] for 2^-6 <= |x| < 2^128.
+// load per element.  k = (e + 62) >> 5 lies in [0, 5] for 2^-8 <= |x| < 2^128.
 CRM_DEV void trig_window_mul3(float ax, const uint4 *PW, uint32_t *r) {
   uint32_t b = fbits(ax);
   uint32_t M = (b & 0x007FFFFFu) | 0x00800000u;
@@ -155,59 +159,66 @@ CRM_DEV void trig_plain(float x, const uint32_t *P, const double *SC, float *y, 
 }
 
 // ------------------------------------------------------------------ double-float tier
-// The same integer reduction; the 64-bit fraction becomes a float pair without
-// conversion instructions: with F' = F + 2^63 (so f + 1/2 = F' 2^-64 >= 0), three
-// chunks of 23, 23 and 18 bits become exact floats by the 2^23 magic-number trick and
-// f = (c0 2^-23 - 1/2) + c1 2^-46 + c2 2^-64.  Then t = f pi/64 as a pair, and
-//   cos t = 1 - t^2/2 + t^4/24 - t^6/720,  sin t = t - t^3/6 + t^5/120 - t^7/5040,
-// with t^2 and t^3/6 carried as pairs (exact FMA splits), the higher terms in float.
-// Error budget (relative to the result): f to 2^-63.6 absolute plus 2^-48 relative
-// (lanes with j = 0 and |f| < 2^-24, where the result is as small as t, go to the slow
-// path: 2^-40 there); pi/64 pair 2^-48; t products 2^-46; sin t, cos t 2^-45 (t^3/6 is
-// up to 2^-13.3 |t|, so it is carried as a pair); table pairs 2^-48; the rotation's pair
-// products and sum 2^-45; the rotation terms S cos t + C sin t lose at most 2^5.4 (a
-// result as small as sin(pi/128) from terms up to 1): total < 2^-39, inside the 2^-37
-// that the rounding test allows.  sin and cos leave the last sum unnormalised
-// (|lo| < 2^-15 |hi|: the pair products' low words, 2^-22 of terms at most 2^5.4 times
-// the result) for round_df; tan normalises both before its division.
+// Finer steps than the other tiers: |x| 256/pi = 512 m + 128 q + j + f, a 128-entry table of
+// (sin, cos)(j pi/256) and t = f pi/256, |t| <= pi/512 (Payne-Hanek) or (1/2 + 2^-6) pi/256
+// (Cody-Waite), so that short polynomials suffice.  The same integer reduction as the
+// other tiers, read two bits further; the 64-bit fraction becomes a float pair without
+// conversion instructions: with F' = F + 2^63 (so f + 1/2 = F' 2^-64 >= 0), three chunks
+// of 23, 23 and 18 bits become exact floats by the 2^23 magic-number trick and
+// f = (c0 2^-23 - 1/2) + c1 2^-46 + c2 2^-64.  Then t = f pi/256 as a pair, and
+//   cos t = 1 - t^2/2 + t^4/24 (remainder t^6/720 < 2^-53),
+//   sin t = t - t^3/6 + t^5/120 (remainder t^7/5040 < 2^-56 |t|),
+// with t^2 and 1 - t^2/2 carried as pairs (exact FMA splits), t^3/6 as one float from
+// t_hi t^2 + 3 t_lo t^2 (it is at most 2^-17.2 |t|), the rest in float.
+// Error budget (relative to the result): f to 2^-63 absolute plus 2^-48 relative (lanes
+// with j = 0 and |f| < 2^-24, where the result is as small as t, go to the slow path: 2^-40
+// there); pi/256 pair 2^-48; cos t 2^-48; sin t 2^-39.5 |t| (the float t^3/6, 2^-22.3 of
+// itself); table pairs 2^-48; the rotation's pair products and sum 2^-47; the rotation
+// terms S cos t + C sin t lose at most 2^7.4 (a result as small as sin(0.48 pi/256) from
+// terms up to 1), and the sin t error enters weighted by C, so it stays 2^-39.4 of the
+// result: total < 2^-38.5, inside the 2^-37 that the rounding test allows.  sin and cos
+// leave the last sum unnormalised (|lo| < 2^-15 |hi|: the pair products' low words, 2^-22
+// of terms at most 2^7.4 times the result) for round_df; tan normalises both before its
+// division.
 struct TrigF {
-  Pair<float> A, B;  // sin and cos of (j pi/64 + t)
+  Pair<float> A, B;  // sin and cos of (j pi/256 + t)
   int q;
   bool tiny;
 };
 
 // Cody-Waite reduction for |x| < 2^12 (the paper's reduction for moderate arguments,
-// Sec. II.A): k = rint(|x| RN(64/pi)) by the shifter, N7 = k mod 128 from its bits, and
-// t = |x| - k pi/64 with pi/64 = C1 + C2 + C3 (three floats, + < 2^-81):
-//   t1 = |x| - k C1 is exact (one FMA: k C1 and |x| are multiples of 2^-29 and
-//        |t1| < 2^-5, so t1 has at most 24 significant bits),
+// Sec. II.A): k = rint(|x| RN(256/pi)) by the shifter, N = k mod 512 from its bits, and
+// t = |x| - k pi/256 with pi/256 = C1 + C2 + C3 (three floats, + < 2^-83):
+//   t1 = |x| - k C1 is exact (one FMA: C1 is a multiple of 2^-30, |x| too when |x| >= 2^-7,
+//        and |t1| < 2^-7, so t1 has at most 23 significant bits; for |x| < 2^-7, k is 0 or
+//        1 and t1 is a multiple of 2^-31 below 2^-7.3),
 //   k C2 = ph + pl exactly (FMA split), (sh, sl) = TwoSum(t1, -ph) exactly,
 //   t = sh + RN(RN(sl - pl) - k C3), normalised by Fast2Sum.
-// |x| RN(64/pi) is within |x| 2^-20 <= 2^-8 of |x| 64/pi, so |t| <= (1/2 + 2^-8) pi/64.
-// With k < 2^16.35: |k C2| < 2^-13.1, |pl| < 2^-37.1, |k C3| < 2^-37.7, so the low word's
+// |x| RN(256/pi) is within |x| 2^-18.2 < 2^-6 of |x| 256/pi, so |t| <= (1/2 + 2^-6) pi/256.
+// With k < 2^18.35: |k C2| < 2^-13, |pl| <= 2^-38, |k C3| < 2^-37.7, so the low word's
 // two roundings and the split's remainder cost < 2^-59.5 absolute plus 2^-47 |t|.  The
-// result is at least sin(pi/64) cos(pi/128) > 2^-4.4 unless j = 0, so this is < 2^-47
-// relative there; with j = 0 (k a nonzero multiple of 32, x near a multiple of pi/2) the
-// result is as small as t, and lanes with |t| < 2^-19 (error above 2^-40 of t) are flagged
-// for the slow path.
-CRM_DEV void trig_reduce_cw(float ax, Pair<float> &t, int &N7, bool &tiny) {
-  const float ks = fma_(ax, CRM_64OPI_F, CRM_SHIFTER_F);
+// result is at least sin(0.48 pi/256) > 2^-7.4 unless j = 0, so this is < 2^-52 relative
+// there; with j = 0 (k a nonzero multiple of 128, x near a multiple of pi/2) the result is
+// as small as t, and lanes with |t| < 2^-19 (error above 2^-40 of t) are flagged for the
+// slow path.
+CRM_DEV void trig_reduce_cw(float ax, Pair<float> &t, int &N, bool &tiny) {
+  const float ks = fma_(ax, CRM_256OPI_F, CRM_SHIFTER_F);
   const float k = ks - CRM_SHIFTER_F;
-  N7 = (int)(fbits(ks) & 127u);  // 1.5 2^23 + k, k < 2^22: the low bits are k
-  const float t1 = fma_(-k, CRM_PIO64_CW1, ax);
-  const float ph = k * CRM_PIO64_CW2;
-  const float pl = fma_(k, CRM_PIO64_CW2, -ph);
+  N = (int)(fbits(ks) & 511u);  // 1.5 2^23 + k, k < 2^22: the low bits are k
+  const float t1 = fma_(-k, CRM_PIO256_CW1, ax);
+  const float ph = k * CRM_PIO256_CW2;
+  const float pl = fma_(k, CRM_PIO256_CW2, -ph);
   const Pair<float> s = two_sum(t1, -ph);
-  t = fast_two_sum(s.hi, fma_(-k, CRM_PIO64_CW3, s.lo - pl));
-  tiny = (N7 & 31) == 0 && k != 0.0f && fabsf(s.hi) < 0x1p-19f;
+  t = fast_two_sum(s.hi, fma_(-k, CRM_PIO256_CW3, s.lo - pl));
+  tiny = (N & 127) == 0 && k != 0.0f && fabsf(s.hi) < 0x1p-19f;
 }
 
 // Whether a lane may take the Cody-Waite reduction: |x| < 2^12 (NaN and infinities, rare,
 // send their vector to the general reduction).
 CRM_DEV bool trig_cw_ok(float x) { return fabsf(x) < 0x1p12f; }
 
-// The reduction shared by the double-float evaluators: t = f pi/64 as an unnormalised
-// pair, N7 = (32 q + j) mod 128, and tiny (j = 0 and t too small for the reduction's
+// The reduction shared by the double-float evaluators: t = f pi/256 as an unnormalised
+// pair, N = (128 q + j) mod 512, and tiny (j = 0 and t too small for the reduction's
 // accuracy: slow path).  PATH 1: Cody-Waite (about 20 operations; the caller has checked
 // trig_cw_ok for every lane of the warp); PATH 2: the integer Payne-Hanek reduction below
 // (about 50), which serves every |x|; PATH 0: Cody-Waite when every active lane of the
@@ -216,19 +227,20 @@ CRM_DEV bool trig_cw_ok(float x) { return fabsf(x) < 0x1p12f; }
 // once per vector of elements and pass PATH 1 or 2 (a branch per element would keep the
 // compiler from interleaving the elements of a vector).
 template <int PATH = 0>
-CRM_DEV void trig_reduce_df(float x, const uint4 *PW, Pair<float> &t, int &N7, bool &tiny) {
+CRM_DEV void trig_reduce_df(float x, const uint4 *PW, Pair<float> &t, int &N, bool &tiny) {
   float ax = fabsf(x);
   if (PATH == 1 || (PATH == 0 && __all_sync(__activemask(), ax < 0x1p12f))) {
-    trig_reduce_cw(ax, t, N7, tiny);
+    trig_reduce_cw(ax, t, N, tiny);
     return;
   }
-  bool small = ax < 0x1p-6f;
+  bool small = ax < 0x1p-8f;  // |x| < pi/512: t = |x|, j = 0
   uint32_t r[4];
   trig_window_mul3(small ? 1.0f : ax, PW, r);
-  // F = the 64 bits below the top 7 of r[2]: F = (Fh, Fl); N7 = the top 7 bits rounded
-  // by F's leading bit, modulo 128 (the 32-bit sum wraps exactly there)
-  const uint32_t Fh = __funnelshift_l(r[1], r[2], 7), Fl = __funnelshift_l(r[0], r[1], 7);
-  N7 = (int)((r[2] + 0x01000000u) >> 25);
+  // The product is |x| 64/pi mod 128 = r 2^-89, so |x| 256/pi mod 512 = r 2^-87: F = the 64
+  // bits below the top 9 of r[2], F = (Fh, Fl); N = those 9 bits rounded by F's leading
+  // bit, modulo 512 (the 32-bit sum wraps exactly there)
+  const uint32_t Fh = __funnelshift_l(r[1], r[2], 9), Fl = __funnelshift_l(r[0], r[1], 9);
+  N = (int)((r[2] + 0x00400000u) >> 23);
   uint32_t Ph = Fh ^ 0x80000000u;
   uint32_t c0 = Ph >> 9;
   uint32_t c1 = __funnelshift_r(Fl, Ph, 18) & 0x007FFFFFu;
@@ -244,52 +256,46 @@ CRM_DEV void trig_reduce_df(float x, const uint4 *PW, Pair<float> &t, int &N7, b
   Pair<float> fs = fast_two_sum(fma_(f0, 0x1p-23f, -0.5f), f1 * 0x1p-46f);
   float fh = fs.hi;
   float fl = fma_(f2, 0x1p-64f, fs.lo);
-  // t = f pi/64 as an unnormalised pair (|tl| < 2^-22 |th|: dropping tl^2 from t^2
-  // costs 2^-44.8 of t^2, below 2^-56 of cos t, sin t and tan t)
-  t.hi = fh * CRM_PIO64_F_HI;
-  t.lo = fma_(fh, CRM_PIO64_F_HI, -t.hi);
-  t.lo = fma_(fh, CRM_PIO64_F_LO, t.lo);
-  t.lo = fma_(fl, CRM_PIO64_F_HI, t.lo);
-  tiny = !small && (N7 & 31) == 0 && fabsf(fh + fl) < 0x1p-24f;
+  // t = f pi/256 as an unnormalised pair (|tl| < 2^-22 |th|: dropping tl^2 from t^2
+  // costs 2^-44.8 of t^2, below 2^-58 of cos t, sin t and tan t)
+  t.hi = fh * CRM_PIO256_F_HI;
+  t.lo = fma_(fh, CRM_PIO256_F_HI, -t.hi);
+  t.lo = fma_(fh, CRM_PIO256_F_LO, t.lo);
+  t.lo = fma_(fl, CRM_PIO256_F_HI, t.lo);
+  tiny = !small && (N & 127) == 0 && fabsf(fh + fl) < 0x1p-24f;
   t.hi = small ? ax : t.hi;
   t.lo = small ? 0.0f : t.lo;
-  N7 = small ? 0 : N7;
+  N = small ? 0 : N;
 }
 
 // KIND = TRIG_SIN or TRIG_COS: only the rotation term the quadrant needs is formed, in R.A
 // (sin: B when q is odd, else A; cos: A when q is odd, else B); otherwise both.
 template <int KIND, int PATH = 0> CRM_DEV TrigF trig_df_core(float x, const uint4 *PW, const float4 *SC) {
   Pair<float> t;
-  int N7;
+  int N;
   TrigF R;
-  trig_reduce_df<PATH>(x, PW, t, N7, R.tiny);
+  trig_reduce_df<PATH>(x, PW, t, N, R.tiny);
   // t^2 as a pair
   float u = t.hi * t.hi;
   float ul = fma_(t.hi, t.hi, -u);
   ul = fma_(2.0f * t.hi, t.lo, ul);
-  // cos t = 1 - t^2/2 + t^4 (1/24 - t^2/720)
+  // cos t = 1 - t^2/2 + t^4/24
   float ch = fma_(u, -0.5f, 1.0f);
   float cl = fma_(u, -0.5f, 1.0f - ch);
   cl = fma_(ul, -0.5f, cl);
-  cl = fma_(u * u, fma_(u, -0x1.6c16c2p-10f, 0x1.555556p-5f), cl);
-  // sin t = t - t^3/6 + t^5 (1/120 - t^2/5040)
-  float w = t.hi * u;
-  float wl = fma_(t.hi, u, -w);
-  wl = fma_(t.hi, ul, wl);
-  wl = fma_(t.lo, u, wl);
-  float s3 = w * CRM_INV6_F_HI;
-  float s3l = fma_(w, CRM_INV6_F_HI, -s3);
-  s3l = fma_(w, CRM_INV6_F_LO, s3l);
-  s3l = fma_(wl, CRM_INV6_F_HI, s3l);
+  cl = fma_(u * u, 0x1.555556p-5f, cl);
+  // sin t = t - t^3/6 + t^5/120, t^3 = t_hi t^2 + 3 t_lo t^2 to 2^-23 of itself
+  const float w = fma_(t.hi, u, (3.0f * t.lo) * u);
+  const float s3 = w * CRM_INV6_F_HI;
   float sh = t.hi - s3;
   float sl = (t.hi - sh) - s3;  // Fast2Sum: |t| > |t^3/6|
-  sl = sl + (t.lo - s3l);
-  sl = fma_(w * u, fma_(u, -0x1.a01a02p-13f, 0x1.111112p-7f), sl);
-  // rotation by j pi/64
-  int j = N7 & 31;
+  sl = sl + t.lo;
+  sl = fma_(w * u, 0x1.111112p-7f, sl);
+  // rotation by j pi/256
+  int j = N & 127;
   float4 T = SC[j];  // (sin hi, lo, cos hi, lo)
   Pair<float> S = {T.x, T.y}, C = {T.z, T.w}, ct = {ch, cl}, st = {sh, sl};
-  R.q = N7 >> 5;
+  R.q = (N >> 7) & 3;
   if (KIND == TRIG_SIN || KIND == TRIG_COS) {
     // B = C cos t + (-S) sin t, A = S cos t + C sin t: one product pair with chosen factors
     const bool useB = (KIND == TRIG_SIN) == ((R.q & 1) != 0);
@@ -298,9 +304,9 @@ template <int KIND, int PATH = 0> CRM_DEV TrigF trig_df_core(float x, const uint
     R.B = R.A;
     return R;
   }
-  // In both sums the first term dominates: |S_j cos t| >= sin(pi/64) cos(pi/128) > 0.049
-  // > |C_j sin t| when j >= 1 (S_0 = 0 makes the sum exact), and |C_j cos t| > 0.049 >
-  // |S_j sin t| for j <= 31: Fast2Sum applies.
+  // In both sums the first term dominates: |S_j cos t| >= sin(pi/256) cos(pi/512) > 0.0122
+  // > 0.0064 > |C_j sin t| when j >= 1 (S_0 = 0 makes the sum exact), and |C_j cos t| >
+  // 0.0122 > |S_j sin t| for j <= 127: Fast2Sum applies.
   Pair<float> a1 = df_mul_raw(S, ct), a2 = df_mul_raw(C, st);
   Pair<float> b1 = df_mul_raw(C, ct), b2 = df_mul_raw(S, st);
   R.A = df_add_ordered_raw(a1, a2);
@@ -308,19 +314,18 @@ template <int KIND, int PATH = 0> CRM_DEV TrigF trig_df_core(float x, const uint
   return R;
 }
 
-// tan by the addition formula on the same reduction: with T = tan(j pi/64) (a 32-entry
+// tan by the addition formula on the same reduction: with T = tan(j pi/256) (a 128-entry
 // float-pair table) and tau = tan t,
-//   tan(j pi/64 + t) = N / D,  N = T + tau,  D = 1 - T tau,
+//   tan(j pi/256 + t) = N / D,  N = T + tau,  D = 1 - T tau,
 // and tan x = +-N/D for even q, -+D/N for odd q (tan(a + pi/2) = -1/tan a).
-// tau = t + t^3/3 + t^5 (2/15 + 17 t^2/315) with t^2 and t^3/3 as pairs (the t^9 term is
-// below 2^-48 of t).  N: T >= tan(pi/64) > |tau| for j >= 1 (T = 0 for j = 0), so
-// Fast2Sum applies and N cancels by at most a factor 2; D: |T tau| <= tan(31 pi/64)
-// tan(pi/128) < 1/2, so D lies in [1/2, 3/2] and 1 - T tau is a Fast2Sum.  Both are
-// normalised for the pair division.  (The Cody-Waite reduction allows |t| up to
-// (1/2 + 2^-8) pi/64: then |T tau| < 0.504 and D > 0.496, which changes none of the
-// bounds below.)  Error budget, relative to the result: tau 2^-45,
-// T 2^-48, N (doubled by its cancellation) 2^-43.8, D 2^-44, the division 2^-43, the
-// reduction as for sin and cos: total < 2^-41.5, inside the rounding test's 2^-37.
+// tau = t + t^3/3 + (2/15) t^5 with t^2 and t^3/3 as pairs (the t^7 term is below 2^-47.9
+// of t).  N: T >= tan(pi/256) > 0.0122 > 0.0064 > |tau| for j >= 1 (T = 0 for j = 0), so
+// Fast2Sum applies and N cancels by at most a factor 2.1; D: |T tau| <= tan(127 pi/256)
+// tan((1/2 + 2^-6) pi/256) < 0.52, so D lies in [0.48, 1.52] and 1 - T tau is a Fast2Sum.
+// Both are normalised for the pair division.  Error budget, relative to the result: tau
+// 2^-45, T 2^-48, N (doubled by its cancellation) 2^-43.7, D 2^-44, the division 2^-43, the
+// reduction as for sin and cos (2^-40 for j = 0 at the slow-path threshold): total
+// < 2^-39.5, inside the rounding test's 2^-37.
 CRM_DEV Pair<float> tan_df_nd(Pair<float> t, int j, const float2 *TT, Pair<float> &D) {
   float u = t.hi * t.hi;
   float ul = fma_(t.hi, t.hi, -u);
@@ -336,7 +341,7 @@ CRM_DEV Pair<float> tan_df_nd(Pair<float> t, int j, const float2 *TT, Pair<float
   const float th = t.hi + s3;
   float tl = s3 - (th - t.hi);  // Fast2Sum: |t| > |t^3/3|
   tl = tl + (t.lo + s3l);
-  tl = fma_(w * u, fma_(u, CRM_TAN_C7_F, CRM_TAN_C5_F), tl);
+  tl = fma_(w * u, CRM_TAN_C5_F, tl);
   const float2 T = TT[j];
   Pair<float> N = df_add_ordered({T.x, T.y}, {th, tl});
   const Pair<float> P = df_mul_raw({T.x, T.y}, {th, tl});
@@ -346,7 +351,7 @@ CRM_DEV Pair<float> tan_df_nd(Pair<float> t, int j, const float2 *TT, Pair<float
   return N;
 }
 
-// Sign of a rounded result as a bit mask: sin(j pi/64 + t) rotated by q quadrants is
+// Sign of a rounded result as a bit mask: sin(j pi/256 + t) rotated by q quadrants is
 // negative for q = 2, 3, cos for q = 1, 2; sin and tan are odd in x.
 CRM_DEV uint32_t trig_sin_sign(int q, float x) { return (((uint32_t)q << 30) ^ fbits(x)) & 0x80000000u; }
 CRM_DEV uint32_t trig_cos_sign(int q) { return ((uint32_t)(q + 1) << 30) & 0x80000000u; }
@@ -373,11 +378,11 @@ CRM_DEV void trig_df(float x, const uint4 *PW, const float4 *SC, const float2 *T
   const bool sp = !(fabsf(x) < CRM_INF_F);  // NaN or infinite
   if (KIND == TRIG_TAN) {
     Pair<float> t, D;
-    int N7;
+    int Nq;
     bool tiny;
-    trig_reduce_df<PATH>(sp ? 1.0f : x, PW, t, N7, tiny);
-    const Pair<float> N = tan_df_nd(t, N7 & 31, TT, D);
-    const bool odd = (N7 & 32) != 0;
+    trig_reduce_df<PATH>(sp ? 1.0f : x, PW, t, Nq, tiny);
+    const Pair<float> N = tan_df_nd(t, Nq & 127, TT, D);
+    const bool odd = (Nq & 128) != 0;
     const Pair<float> q = df_div_raw(odd ? D : N, odd ? N : D);
     bool h;
     const float yt = round_df(q.hi, q.lo, h, sg);
@@ -388,7 +393,7 @@ CRM_DEV void trig_df(float x, const uint4 *PW, const float4 *SC, const float2 *T
       return;
     }
     // negative in odd quadrants (-cot), and odd in x
-    const uint32_t sgb = (((uint32_t)N7 << 26) ^ fbits(x)) & 0x80000000u;
+    const uint32_t sgb = (((uint32_t)Nq << 24) ^ fbits(x)) & 0x80000000u;
     const bool zero = x == 0.0f;  // tan(+-0) = +-0
     hard = !zero && (tiny || h);
     if (sg) *sg = zero ? 0 : (sgb ? -*sg : *sg);

@@ -346,29 +346,34 @@ for j in range(32):
     sc_f += split(S, f, 2) + split(C, f, 2)
     sc_dd += split(S, d, 2) + split(C, d, 2)
 arr_d("CRM_SINCOS_T32_D", sc_d, "(sin, cos)(j pi/64), j = 0..31, doubles")
-arr_f("CRM_SINCOS_T32_DF", sc_f, "(sin hi, lo, cos hi, lo)(j pi/64) floats")
 arr_d("CRM_SINCOS_T32_DD", sc_dd, "(sin, cos)(j pi/64) as double-double")
-tn_f = []
-for j in range(32):
-    tn_f += split(mp.tan(mp.mpf(j) * mp.pi / 64), f, 2)
-arr_f("CRM_TAN_T32_DF", tn_f, "(tan hi, lo)(j pi/64), j = 0..31, floats")
+# Double-float tier: 128 steps per quadrant, a = j pi/256
+sc_f, tn_f = [], []
+for j in range(128):
+    a = mp.mpf(j) * mp.pi / 256
+    sc_f += split(mp.sin(a), f, 2) + split(mp.cos(a), f, 2)
+    tn_f += split(mp.tan(a), f, 2)
+arr_f("CRM_SINCOS_T128_DF", sc_f, "(sin hi, lo, cos hi, lo)(j pi/256), j = 0..127, floats")
+arr_f("CRM_TAN_T128_DF", tn_f, "(tan hi, lo)(j pi/256), j = 0..127, floats")
 const_f("CRM_TAN_C5_F", f(mp.mpf(2) / 15), "2/15, the t^5 coefficient of tan t")
-const_f("CRM_TAN_C7_F", f(mp.mpf(17) / 315), "17/315, the t^7 coefficient of tan t")
 PIO64 = mp.pi / 64
 pp = split(PIO64, d, 2)
 const_d("CRM_PIO64_D_HI", pp[0])
 const_d("CRM_PIO64_D_LO", pp[1])
-pf = split(PIO64, f, 2)
-const_f("CRM_PIO64_F_HI", pf[0])
-const_f("CRM_PIO64_F_LO", pf[1])
-# Cody-Waite split of pi/64 into three floats: k C1 is exact after one FMA for the k of
-# |x| < 2^12, k C2 is split exactly by an FMA, C3 carries the rest (error < 2^-81 of pi/64)
-cw = split(PIO64, f, 3)
-assert abs(PIO64 - cw[0] - cw[1] - cw[2]) < mp.mpf(2) ** -81
-const_f("CRM_PIO64_CW1", cw[0], "pi/64 = CW1 + CW2 + CW3 (+ < 2^-81)")
-const_f("CRM_PIO64_CW2", cw[1])
-const_f("CRM_PIO64_CW3", cw[2])
-const_f("CRM_64OPI_F", f(64 / mp.pi), "64/pi, nearest float")
+PIO256 = mp.pi / 256
+pf = split(PIO256, f, 2)
+const_f("CRM_PIO256_F_HI", pf[0])
+const_f("CRM_PIO256_F_LO", pf[1])
+# Cody-Waite split of pi/256 into three floats: CW1 is a multiple of 2^-30, so |x| - k CW1
+# is exact after one FMA for the k of |x| < 2^12 (k < 2^18.35); k CW2 is split exactly by an
+# FMA, CW3 carries the rest (error < 2^-83)
+cw = split(PIO256, f, 3)
+assert abs(PIO256 - cw[0] - cw[1] - cw[2]) < mp.mpf(2) ** -83
+assert mp.nint(cw[0] * 2 ** 30) == cw[0] * 2 ** 30
+const_f("CRM_PIO256_CW1", cw[0], "pi/256 = CW1 + CW2 + CW3 (+ < 2^-83)")
+const_f("CRM_PIO256_CW2", cw[1])
+const_f("CRM_PIO256_CW3", cw[2])
+const_f("CRM_256OPI_F", f(256 / mp.pi), "256/pi, nearest float")
 i3 = split(mp.mpf(1) / 3, f, 2)
 const_f("CRM_INV3_F_HI", i3[0])
 const_f("CRM_INV3_F_LO", i3[1])

@@ -13,7 +13,7 @@
 
 namespace crm {
 
-constexpr int BATCH_SMEM = 193 * 16;  // largest binary32 table (log family)
+constexpr int BATCH_SMEM = FnTrig<TRIG_TAN>::tab_bytes<2>();  // largest binary32 table (tanf's)
 static_assert(FnLog<0>::tab_bytes<2>() <= BATCH_SMEM && FnTrig<TRIG_TAN>::tab_bytes<2>() <= BATCH_SMEM &&
                   FnExp<0>::tab_bytes<2>() <= BATCH_SMEM && FnHyp<0>::tab_bytes<2>() <= BATCH_SMEM &&
                   FnAtrig<0>::tab_bytes<2>() <= BATCH_SMEM,

@@ -66,10 +66,10 @@ def _precision():
 
 
 def test_header_parses():
-    for name in ("CRM_LN_T193M_DF", "CRM_EXP2_T64U_DF", "CRM_SINCOS_T32_DF", "CRM_TAN_T32_DF",
+    for name in ("CRM_LN_T193M_DF", "CRM_EXP2_T64U_DF", "CRM_SINCOS_T128_DF", "CRM_TAN_T128_DF",
                  "CRM_ATAN_T17_DF", "CRM_TWO_OVER_PI_W"):
         assert name in TABLES, name
-    for name in ("CRM_LN2_F16_HI", "CRM_LN2_F16_LO", "CRM_PIO64_CW1", "CRM_64OPI_F", "CRM_INV_LN2_F_HI"):
+    for name in ("CRM_LN2_F16_HI", "CRM_LN2_F16_LO", "CRM_PIO256_CW1", "CRM_256OPI_F", "CRM_INV_LN2_F_HI"):
         assert name in CONSTS, name
 
 
@@ -130,27 +130,30 @@ def test_exp_table_entries():
 
 # ---------------------------------------------------------------- trigonometric (double-float)
 def test_sincos_and_tan_tables():
-    SC, TT = TABLES["CRM_SINCOS_T32_DF"], TABLES["CRM_TAN_T32_DF"]
-    for j in range(32):
-        a = mp.mpf(j) * mp.pi / 64
+    SC, TT = TABLES["CRM_SINCOS_T128_DF"], TABLES["CRM_TAN_T128_DF"]
+    for j in range(128):
+        a = mp.mpf(j) * mp.pi / 256
         check_split(SC[4 * j], SC[4 * j + 1], mp.sin(a))
         check_split(SC[4 * j + 2], SC[4 * j + 3], mp.cos(a))
         check_split(TT[2 * j], TT[2 * j + 1], mp.tan(a))
 
 
-def test_cody_waite_split_of_pi_over_64():
-    c1, c2, c3 = CONSTS["CRM_PIO64_CW1"], CONSTS["CRM_PIO64_CW2"], CONSTS["CRM_PIO64_CW3"]
-    assert abs(mp.pi / 64 - c1 - c2 - c3) < mp.mpf(2) ** -81
-    # |x| - k C1 exact by one FMA: k C1 and |x| >= 2^-5 are multiples of 2^-29 and the
-    # reduced |x| - k C1 is below 2^-5, so it has at most 24 significant bits
-    assert is_multiple(c1, mp.mpf(2) ** -29)
-    k_max = mp.floor(mp.mpf(2) ** 12 * CONSTS["CRM_64OPI_F"]) + 1
-    assert k_max < mp.mpf(2) ** 16.36
-    # |k C2| < 2^-13 (so its FMA split's low word pl is below 2^-38) and |k C3| < 2^-37.7
-    # for k below k_max: the bounds behind the reduction's error budget
+def test_cody_waite_split_of_pi_over_256():
+    c1, c2, c3 = CONSTS["CRM_PIO256_CW1"], CONSTS["CRM_PIO256_CW2"], CONSTS["CRM_PIO256_CW3"]
+    assert abs(mp.pi / 256 - c1 - c2 - c3) < mp.mpf(2) ** -83
+    # |x| - k C1 exact by one FMA: C1 and |x| >= 2^-7 are multiples of 2^-30 and the
+    # reduced |x| - k C1 is below 2^-7, so it has at most 23 significant bits
+    assert is_multiple(c1, mp.mpf(2) ** -30)
+    k_max = mp.floor(mp.mpf(2) ** 12 * CONSTS["CRM_256OPI_F"]) + 1
+    assert k_max < mp.mpf(2) ** 18.36
+    # |k C2| < 2^-13 (its FMA split's low word at most 2^-38) and |k C3| < 2^-37.7 for k
+    # below k_max: the bounds behind the reduction's error budget
     assert k_max * abs(c2) < mp.mpf(2) ** -13 and k_max * abs(c3) < mp.mpf(2) ** -37.7
-    assert CONSTS["CRM_64OPI_F"] == rn(64 / mp.pi)
-    check_split(CONSTS["CRM_PIO64_F_HI"], CONSTS["CRM_PIO64_F_LO"], mp.pi / 64)
+    assert k_max * abs(mp.pi / 256 - c1) < mp.mpf(2) ** -12.6  # so |x| - k C1 stays below 2^-7
+    assert CONSTS["CRM_256OPI_F"] == rn(256 / mp.pi)
+    # |x| RN(256/pi) within 2^-6 of |x| 256/pi for |x| < 2^12
+    assert abs(CONSTS["CRM_256OPI_F"] - 256 / mp.pi) * mp.mpf(2) ** 12 < mp.mpf(2) ** -6
+    check_split(CONSTS["CRM_PIO256_F_HI"], CONSTS["CRM_PIO256_F_LO"], mp.pi / 256)
 
 
 def test_two_over_pi_words():
@@ -169,7 +172,6 @@ def test_trig_series_constants():
     check_split(CONSTS["CRM_INV6_F_HI"], CONSTS["CRM_INV6_F_LO"], mp.mpf(1) / 6)
     check_split(CONSTS["CRM_INV3_F_HI"], CONSTS["CRM_INV3_F_LO"], mp.mpf(1) / 3)
     assert CONSTS["CRM_TAN_C5_F"] == rn(mp.mpf(2) / 15)
-    assert CONSTS["CRM_TAN_C7_F"] == rn(mp.mpf(17) / 315)
 
 
 # ---------------------------------------------------------------- inverse trigonometric

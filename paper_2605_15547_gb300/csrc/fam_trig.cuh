@@ -318,29 +318,23 @@ template <int KIND, int PATH = 0> CRM_DEV TrigF trig_df_core(float x, const uint
 // float-pair table) and tau = tan t,
 //   tan(j pi/256 + t) = N / D,  N = T + tau,  D = 1 - T tau,
 // and tan x = +-N/D for even q, -+D/N for odd q (tan(a + pi/2) = -1/tan a).
-// tau = t + t^3/3 + (2/15) t^5 with t^2 and t^3/3 as pairs (the t^7 term is below 2^-47.9
-// of t).  N: T >= tan(pi/256) > 0.0122 > 0.0064 > |tau| for j >= 1 (T = 0 for j = 0), so
+// tau = t + t^3/3 + (2/15) t^5 with t^3/3 as one float, 2^-22.3 of itself (2^-38.5 of t),
+// the t^7 term below 2^-47.9 of t.  N: T >= tan(pi/256) > 0.0122 > 0.0064 > |tau| for j >= 1 (T = 0 for j = 0), so
 // Fast2Sum applies and N cancels by at most a factor 2.1; D: |T tau| <= tan(127 pi/256)
 // tan((1/2 + 2^-6) pi/256) < 0.52, so D lies in [0.48, 1.52] and 1 - T tau is a Fast2Sum.
 // Both are normalised for the pair division.  Error budget, relative to the result: tau
-// 2^-45, T 2^-48, N (doubled by its cancellation) 2^-43.7, D 2^-44, the division 2^-43, the
-// reduction as for sin and cos (2^-40 for j = 0 at the slow-path threshold): total
-// < 2^-39.5, inside the rounding test's 2^-37.
+// 2^-38.5 |t| (with j = 0 the result is about t; with j >= 1 the 2^-45.8 absolute error of
+// tau is 2^-38.4 of N >= 0.0059), T 2^-48, D 2^-44, the division 2^-43, the reduction as for
+// sin and cos (2^-40 for j = 0 at the slow-path threshold): total < 2^-38, inside the
+// rounding test's 2^-37.
 CRM_DEV Pair<float> tan_df_nd(Pair<float> t, int j, const float2 *TT, Pair<float> &D) {
-  float u = t.hi * t.hi;
-  float ul = fma_(t.hi, t.hi, -u);
-  ul = fma_(2.0f * t.hi, t.lo, ul);
-  float w = t.hi * u;
-  float wl = fma_(t.hi, u, -w);
-  wl = fma_(t.hi, ul, wl);
-  wl = fma_(t.lo, u, wl);
-  float s3 = w * CRM_INV3_F_HI;
-  float s3l = fma_(w, CRM_INV3_F_HI, -s3);
-  s3l = fma_(w, CRM_INV3_F_LO, s3l);
-  s3l = fma_(wl, CRM_INV3_F_HI, s3l);
+  // t^3 = t_hi t^2 + 3 t_lo t^2 to 2^-23 of itself, t^3/3 as one float (at most 2^-16.2 |t|)
+  const float u = t.hi * t.hi;
+  const float w = fma_(t.hi, u, (3.0f * t.lo) * u);
+  const float s3 = w * CRM_INV3_F_HI;
   const float th = t.hi + s3;
   float tl = s3 - (th - t.hi);  // Fast2Sum: |t| > |t^3/3|
-  tl = tl + (t.lo + s3l);
+  tl = tl + t.lo;
   tl = fma_(w * u, CRM_TAN_C5_F, tl);
   const float2 T = TT[j];
   Pair<float> N = df_add_ordered({T.x, T.y}, {th, tl});
